@@ -1,0 +1,334 @@
+"""CPU oracle for BVH build and ray tracing (FP64). TEST INFRASTRUCTURE ONLY.
+
+Only the tests, `__graft_entry__.smoke()` and `bench.py`'s CPU-baseline leg may import
+this package. It shares no code with the CUDA library: its C++ sources
+(build_ref.cpp, trace_ref.cpp, shade_ref.cpp) are compiled by `build()` into
+`_liboracle.so` with g++ and called through ctypes. Every function restates a
+definition from the paper ("Ray Tracing using HIP": Sec. 3.1 ray/triangle, Sec. 3.2
+camera, Sec. 4 ambient occlusion, Sec. 6.2 BVH construction, refit, traversal and
+two-level instancing) or from the published methods the LBVH build uses (Karras
+2012; Moller-Trumbore 1997), in plain sequential form.
+
+Pins (tests/test_oracle_*.py) tie each function to something other than itself:
+hand-computed Morton codes, closed-form sphere/plane/quad hits, brute force vs the
+oracle's BVH, the paper's plane/edge formula vs Moller-Trumbore, BVH invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRCS = ["build_ref.cpp", "trace_ref.cpp", "shade_ref.cpp"]
+_LIB_PATH = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NONE = 0xFFFFFFFF
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (g++, -O2, no fused multiply-add) into _liboracle.so."""
+    srcs = [os.path.join(_HERE, s) for s in _SRCS]
+    if not force and os.path.exists(_LIB_PATH):
+        mt = os.path.getmtime(_LIB_PATH)
+        deps = srcs + [os.path.join(_HERE, "oracle_math.h")]
+        if all(os.path.getmtime(s) <= mt for s in deps):
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-pthread", "-o", tmp] + srcs
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            L.oracle_scene_new.restype = P
+            L.oracle_scene_free.argtypes = [P]
+            L.oracle_scene_add_mesh.argtypes = [P, P, i64, P, i64]
+            L.oracle_scene_add_spheres.argtypes = [P, P, i64]
+            L.oracle_scene_add_instance.argtypes = [P, ctypes.c_int, P]
+            L.oracle_scene_build.argtypes = [P]
+            L.oracle_trace.argtypes = [P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+            L.oracle_intersect_prim.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
+            L.oracle_min_edge_margin.argtypes = [P, P]
+            L.oracle_min_edge_margin.restype = ctypes.c_double
+            L.oracle_plane_edge_test.argtypes = [P, P, P, P, P]
+            L.oracle_mt_test.argtypes = [P, P, P, P, P]
+            L.oracle_instance_frames.argtypes = [P, ctypes.c_uint32, P, P]
+            L.oracle_world_triangle.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, P]
+            L.oracle_triangle_aabbs.argtypes = [P, i64, P, P, P, P]
+            L.oracle_box_centroids.argtypes = [P, i64, P]
+            L.oracle_morton.argtypes = [P, i64, P, P, ctypes.c_int, P]
+            L.oracle_centroid_bounds.argtypes = [P, i64, P, P]
+            L.oracle_stable_sort.argtypes = [P, i64, P, P]
+            L.oracle_topology.argtypes = [P, i64, ctypes.c_int, P, P, P, P]
+            L.oracle_fit.argtypes = [P, P, i64, P, P, P, P]
+            L.oracle_sah_cost.argtypes = [P, P, i64]
+            L.oracle_sah_cost.restype = ctypes.c_double
+            L.oracle_xi.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+            L.oracle_xi.restype = ctypes.c_double
+            L.oracle_camera_rays.argtypes = [P, i64, i64, P]
+            L.oracle_sample_hemisphere.argtypes = [ctypes.c_double, ctypes.c_double, P]
+            L.oracle_ao_rays.argtypes = [P, P, P, P, i64, ctypes.c_int, ctypes.c_uint64, ctypes.c_float, P]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "oracle inputs must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ----------------------------------------------------------------------------------
+# Build steps (bit-exact definitions)
+# ----------------------------------------------------------------------------------
+def triangle_aabbs(vertices: np.ndarray, indices: np.ndarray):
+    """Per-triangle AABB lo, hi and centroid 0.5*(lo+hi), float32 (n,3) each."""
+    v = _c(vertices, np.float32)
+    idx = _c(indices, np.uint32)
+    n = idx.shape[0]
+    lo = np.empty((n, 3), np.float32)
+    hi = np.empty((n, 3), np.float32)
+    c = np.empty((n, 3), np.float32)
+    lib().oracle_triangle_aabbs(_p(idx), n, _p(v), _p(lo), _p(hi), _p(c))
+    return lo, hi, c
+
+
+def box_centroids(boxes: np.ndarray) -> np.ndarray:
+    b = _c(boxes, np.float32).reshape(-1, 6)
+    c = np.empty((b.shape[0], 3), np.float32)
+    lib().oracle_box_centroids(_p(b), b.shape[0], _p(c))
+    return c
+
+
+def centroid_bounds(centroids: np.ndarray):
+    c = _c(centroids, np.float32).reshape(-1, 3)
+    lo = np.empty(3, np.float32)
+    hi = np.empty(3, np.float32)
+    lib().oracle_centroid_bounds(_p(c), c.shape[0], _p(lo), _p(hi))
+    return lo, hi
+
+
+def morton(centroids: np.ndarray, lo, hi, bits_per_axis: int) -> np.ndarray:
+    """Morton codes (uint64 holding 30 or 63 bits)."""
+    c = _c(centroids, np.float32).reshape(-1, 3)
+    out = np.empty(c.shape[0], np.uint64)
+    lib().oracle_morton(_p(c), c.shape[0], _p(_c(lo, np.float32)), _p(_c(hi, np.float32)), bits_per_axis, _p(out))
+    return out
+
+
+def stable_sort(codes: np.ndarray):
+    """(sorted codes, order) with equal codes kept in input order."""
+    k = _c(codes, np.uint64)
+    sk = np.empty_like(k)
+    order = np.empty(k.shape[0], np.uint32)
+    lib().oracle_stable_sort(_p(k), k.shape[0], _p(sk), _p(order))
+    return sk, order
+
+
+def topology(sorted_keys: np.ndarray, keybits: int):
+    """Karras-numbered binary hierarchy: (childL, childR, parent_internal, parent_leaf).
+    Leaf children carry bit 31 (as int32, negative)."""
+    k = _c(sorted_keys, np.uint64)
+    n = k.shape[0]
+    m = max(n - 1, 0)
+    cl = np.full(m, -1, np.int32)
+    cr = np.full(m, -1, np.int32)
+    pi = np.full(m, -1, np.int32)
+    pl = np.full(n, -1, np.int32)
+    if n >= 2:
+        lib().oracle_topology(_p(k), n, keybits, _p(cl), _p(cr), _p(pi), _p(pl))
+    return cl, cr, pi, pl
+
+
+def fit(childL, childR, leaf_lo, leaf_hi):
+    """Internal-node boxes (lo, hi), float32 (n-1,3)."""
+    cl = _c(childL, np.int32)
+    cr = _c(childR, np.int32)
+    lo = _c(leaf_lo, np.float32)
+    hi = _c(leaf_hi, np.float32)
+    n = lo.shape[0]
+    nlo = np.empty((max(n - 1, 0), 3), np.float32)
+    nhi = np.empty((max(n - 1, 0), 3), np.float32)
+    if n >= 2:
+        lib().oracle_fit(_p(cl), _p(cr), n, _p(lo), _p(hi), _p(nlo), _p(nhi))
+    return nlo, nhi
+
+
+def sah_cost(node_lo, node_hi) -> float:
+    lo = _c(node_lo, np.float32)
+    hi = _c(node_hi, np.float32)
+    return float(lib().oracle_sah_cost(_p(lo), _p(hi), lo.shape[0]))
+
+
+def lbvh(leaf_lo, leaf_hi, centroids, bits_per_axis: int):
+    """The whole LBVH reference: bounds, Morton, stable sort, topology, fit. Returns a dict."""
+    clo, chi = centroid_bounds(centroids)
+    codes = morton(centroids, clo, chi, bits_per_axis)
+    sk, order = stable_sort(codes)
+    keybits = 32 if bits_per_axis == 10 else 64
+    cl, cr, pi, pl = topology(sk, keybits)
+    slo = np.ascontiguousarray(np.asarray(leaf_lo)[order])
+    shi = np.ascontiguousarray(np.asarray(leaf_hi)[order])
+    nlo, nhi = fit(cl, cr, slo, shi)
+    return dict(centroid_lo=clo, centroid_hi=chi, codes=codes, sorted_codes=sk, order=order, childL=cl,
+                childR=cr, parent_internal=pi, parent_leaf=pl, node_lo=nlo, node_hi=nhi, leaf_lo=slo,
+                leaf_hi=shi)
+
+
+# ----------------------------------------------------------------------------------
+# Scenes and traces
+# ----------------------------------------------------------------------------------
+class Hits:
+    """Hit records in FP64: inst, prim (uint32; NONE on a miss), t (+inf on miss), u, v."""
+
+    def __init__(self, n: int):
+        self.inst = np.full(n, NONE, np.uint32)
+        self.prim = np.full(n, NONE, np.uint32)
+        self.t = np.full(n, np.inf)
+        self.u = np.zeros(n)
+        self.v = np.zeros(n)
+
+    def __len__(self):
+        return self.prim.shape[0]
+
+
+class Scene:
+    """An oracle scene: geometries (meshes or spheres) and instances with SRT frames."""
+
+    def __init__(self):
+        self._L = lib()
+        self._h = ctypes.c_void_p(self._L.oracle_scene_new())
+        self._keep = []
+
+    def __del__(self):
+        try:
+            if self._h:
+                self._L.oracle_scene_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def add_mesh(self, vertices, indices) -> int:
+        v = _c(vertices, np.float32)
+        i = _c(indices, np.uint32)
+        return int(self._L.oracle_scene_add_mesh(self._h, _p(v), v.shape[0], _p(i), i.shape[0]))
+
+    def add_spheres(self, spheres) -> int:
+        s = _c(spheres, np.float32).reshape(-1, 4)
+        return int(self._L.oracle_scene_add_spheres(self._h, _p(s), s.shape[0]))
+
+    def add_instance(self, geom: int, frame=None):
+        if frame is None:
+            self._L.oracle_scene_add_instance(self._h, geom, None)
+        else:
+            f = _c(frame, np.float32).reshape(10)
+            self._L.oracle_scene_add_instance(self._h, geom, _p(f))
+
+    def build(self):
+        self._L.oracle_scene_build(self._h)
+
+    def trace(self, rays, any_hit: bool = False, bvh: bool = True, threads: int = 0) -> Hits:
+        r = _c(rays, np.float32).reshape(-1, 8)
+        h = Hits(r.shape[0])
+        self._L.oracle_trace(self._h, _p(r), r.shape[0], int(any_hit), int(bvh), threads, _p(h.inst), _p(h.prim),
+                             _p(h.t), _p(h.u), _p(h.v))
+        return h
+
+    def intersect_prim(self, ray, inst: int, prim: int):
+        """(hit, t, u, v) of one (instance, primitive) in FP64."""
+        r = _c(ray, np.float32).reshape(8)
+        t = ctypes.c_double()
+        u = ctypes.c_double()
+        v = ctypes.c_double()
+        ok = self._L.oracle_intersect_prim(self._h, _p(r), inst, prim, ctypes.byref(t), ctypes.byref(u),
+                                           ctypes.byref(v))
+        return bool(ok), t.value, u.value, v.value
+
+    def min_edge_margin(self, ray) -> float:
+        r = _c(ray, np.float32).reshape(8)
+        return float(self._L.oracle_min_edge_margin(self._h, _p(r)))
+
+    def instance_frames(self, inst: int):
+        f = np.empty(12)
+        g = np.empty(12)
+        self._L.oracle_instance_frames(self._h, inst, _p(f), _p(g))
+        return f.reshape(3, 4), g.reshape(3, 4)
+
+    def world_triangle(self, inst: int, prim: int) -> np.ndarray:
+        out = np.empty(9)
+        ok = self._L.oracle_world_triangle(self._h, inst, prim, _p(out))
+        if not ok:
+            raise ValueError("not a triangle")
+        return out.reshape(3, 3)
+
+
+def mt_test(ray, tri):
+    r = _c(ray, np.float32).reshape(8)
+    t9 = _c(tri, np.float32).reshape(9)
+    t = ctypes.c_double()
+    u = ctypes.c_double()
+    v = ctypes.c_double()
+    ok = lib().oracle_mt_test(_p(r), _p(t9), ctypes.byref(t), ctypes.byref(u), ctypes.byref(v))
+    return bool(ok), t.value, u.value, v.value
+
+
+def plane_edge_test(ray, tri):
+    r = _c(ray, np.float32).reshape(8)
+    t9 = _c(tri, np.float32).reshape(9)
+    t = ctypes.c_double()
+    u = ctypes.c_double()
+    v = ctypes.c_double()
+    ok = lib().oracle_plane_edge_test(_p(r), _p(t9), ctypes.byref(t), ctypes.byref(u), ctypes.byref(v))
+    return bool(ok), t.value, u.value, v.value
+
+
+# ----------------------------------------------------------------------------------
+# Ray generation
+# ----------------------------------------------------------------------------------
+def camera_rays(camera_packed, width: int, height: int) -> np.ndarray:
+    """Pinhole camera rays (paper Sec. 3.2) at pixel centres, float32 (W*H, 8)."""
+    cam = _c(camera_packed, np.float32).reshape(9)
+    out = np.empty((width * height, 8), np.float32)
+    lib().oracle_camera_rays(_p(cam), width, height, _p(out))
+    return out
+
+
+def xi(seed: int, pixel: int, sample: int, dim: int) -> float:
+    return float(lib().oracle_xi(seed, pixel, sample, dim))
+
+
+def sample_hemisphere(xi0: float, xi1: float) -> np.ndarray:
+    out = np.empty(3)
+    lib().oracle_sample_hemisphere(xi0, xi1, _p(out))
+    return out
+
+
+def ao_rays(scene: Scene, primary_rays, hits: Hits, spp: int, seed: int, length: float) -> np.ndarray:
+    """Ambient-occlusion rays (paper Sec. 4) for each pixel's oracle primary hit."""
+    r = _c(primary_rays, np.float32).reshape(-1, 8)
+    n = r.shape[0]
+    tri = np.zeros((n, 9))
+    for p in np.nonzero(hits.prim != NONE)[0]:
+        tri[p] = scene.world_triangle(int(hits.inst[p]), int(hits.prim[p])).ravel()
+    out = np.empty((n * spp, 8), np.float32)
+    lib().oracle_ao_rays(_p(r), _p(tri), _p(_c(hits.prim, np.uint32)), _p(_c(hits.t, np.float64)), n, spp,
+                         ctypes.c_uint64(seed), ctypes.c_float(length), _p(out))
+    return out

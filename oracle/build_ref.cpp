@@ -1,0 +1,234 @@
+// ORACLE (test infrastructure only; never linked into the library): the LBVH build
+// steps written out as plain sequential code.
+//
+//  * primitive AABB and centroid: componentwise min/max of the triangle's vertices
+//    (or the given box), centroid = 0.5*(lo+hi) in float32;
+//  * Morton codes (30-bit: 10 bits per axis; 63-bit: 21 bits per axis), quantised in
+//    float32 with a fixed operation order so that the result is exact and shared by
+//    any IEEE-754 implementation that follows the same steps;
+//  * the sort: std::stable_sort of primitive indices by code (equal codes keep the
+//    input order, the result of a stable LSD radix sort);
+//  * the hierarchy: a recursive top-down split of the sorted range at the highest
+//    bit where the (code, index) concatenation changes (Karras, "Maximizing
+//    Parallelism in the Construction of BVHs, Octrees, and k-d Trees", HPG 2012,
+//    Sec. 3-4, which proves its parallel per-node emission yields this same tree),
+//    with Karras's numbering: root 0, an internal left child is numbered by the
+//    last leaf of its range, an internal right child by the first;
+//  * the fit: each internal box is the union of its children's boxes (the bottom-up
+//    refit from child volumes of the paper's Sec. 6.2 "BVH Construction").
+//
+// Compile with -ffp-contract=off so no multiply-add is fused.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "oracle_math.h"
+
+namespace {
+
+// Leading equal bits of two words of `bits` width, counted from the top bit.
+int leading_equal_bits(uint64_t a, uint64_t b, int bits) {
+    int n = 0;
+    for (int k = bits - 1; k >= 0; --k) {
+        if (((a >> k) & 1ull) != ((b >> k) & 1ull)) break;
+        ++n;
+    }
+    return n;
+}
+
+// Common-prefix length of the concatenations key||index for sorted positions i, j.
+int prefix(const uint64_t* keys, int keybits, int64_t i, int64_t j) {
+    if (keys[i] != keys[j]) return leading_equal_bits(keys[i], keys[j], keybits);
+    return keybits + leading_equal_bits((uint64_t)(uint32_t)i, (uint64_t)(uint32_t)j, 32);
+}
+
+const int32_t LEAF = (int32_t)0x80000000u;
+
+uint32_t quantise(float c, float lo, float hi, int bits) {
+    // x = (c - lo) / (hi - lo) in float32; x = 0 when the extent is zero
+    volatile float ext = hi - lo;
+    float x;
+    if (ext == 0.0f) {
+        x = 0.0f;
+    } else {
+        volatile float num = c - lo;
+        volatile float q = num / ext;
+        x = q;
+    }
+    volatile float s = x * (float)(1u << bits);  // power-of-two scaling
+    double f = std::floor((double)s);
+    const double top = (double)((1u << bits) - 1u);
+    if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0
+    if (f > top) f = top;
+    return (uint32_t)f;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Prim AABB + centroid for an indexed triangle mesh (float32, exact min/max).
+// idx: 3*n uint32, verts: 3*nv float32. lo/hi/centroid: 3*n float32 out.
+void oracle_triangle_aabbs(const uint32_t* idx, int64_t n, const float* verts, float* lo, float* hi,
+                           float* centroid) {
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            float mn = verts[3 * (int64_t)idx[3 * i + 0] + a];
+            float mx = mn;
+            for (int k = 1; k < 3; ++k) {
+                float v = verts[3 * (int64_t)idx[3 * i + k] + a];
+                mn = std::min(mn, v);
+                mx = std::max(mx, v);
+            }
+            lo[3 * i + a] = mn;
+            hi[3 * i + a] = mx;
+            volatile float s = mn + mx;
+            centroid[3 * i + a] = 0.5f * s;
+        }
+    }
+}
+
+// Centroids of given boxes (lo.xyz, hi.xyz per prim).
+void oracle_box_centroids(const float* boxes, int64_t n, float* centroid) {
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            volatile float s = boxes[6 * i + a] + boxes[6 * i + 3 + a];
+            centroid[3 * i + a] = 0.5f * s;
+        }
+}
+
+// Morton codes of centroids within [lo, hi] (the centroid bounds). bits = 10 or 21 per
+// axis. Code bit 3k+2 holds bit k of x, 3k+1 of y, 3k of z.
+void oracle_morton(const float* centroid, int64_t n, const float* lo, const float* hi, int bits,
+                   uint64_t* codes) {
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t q[3];
+        for (int a = 0; a < 3; ++a) q[a] = quantise(centroid[3 * i + a], lo[a], hi[a], bits);
+        uint64_t code = 0;
+        for (int k = bits - 1; k >= 0; --k) {
+            code = (code << 1) | ((q[0] >> k) & 1u);
+            code = (code << 1) | ((q[1] >> k) & 1u);
+            code = (code << 1) | ((q[2] >> k) & 1u);
+        }
+        codes[i] = code;
+    }
+}
+
+// Centroid bounds (min/max of centroids).
+void oracle_centroid_bounds(const float* centroid, int64_t n, float* lo, float* hi) {
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], centroid[3 * i + a]);
+            hi[a] = std::max(hi[a], centroid[3 * i + a]);
+        }
+}
+
+// Stable sort of (code, index) by code. order[k] = primitive at sorted position k.
+void oracle_stable_sort(const uint64_t* codes, int64_t n, uint64_t* sorted_codes, uint32_t* order) {
+    std::vector<uint32_t> idx((size_t)n);
+    std::iota(idx.begin(), idx.end(), 0u);
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return codes[a] < codes[b]; });
+    for (int64_t k = 0; k < n; ++k) {
+        order[k] = idx[(size_t)k];
+        sorted_codes[k] = codes[idx[(size_t)k]];
+    }
+}
+
+// Hierarchy over n >= 2 sorted keys of `keybits` width (32 for 30-bit codes held in
+// 32-bit words, 64 for 63-bit codes). childL/childR: n-1 entries, leaf children
+// carry the top bit. parent_internal: n-1 (root gets -1); parent_leaf: n.
+void oracle_topology(const uint64_t* sorted_keys, int64_t n, int keybits, int32_t* childL, int32_t* childR,
+                     int32_t* parent_internal, int32_t* parent_leaf) {
+    if (n < 2) return;
+    parent_internal[0] = -1;
+    // explicit work list instead of deep recursion for long chains
+    struct Item {
+        int64_t a, b;
+        int32_t id;
+    };
+    std::vector<Item> stack;
+    stack.push_back({0, n - 1, 0});
+    while (!stack.empty()) {
+        Item it = stack.back();
+        stack.pop_back();
+        const int64_t a = it.a, b = it.b;
+        const int32_t id = it.id;
+        const int p = prefix(sorted_keys, keybits, a, b);
+        int64_t gamma = a;
+        for (int64_t m = a; m < b; ++m)
+            if (prefix(sorted_keys, keybits, a, m) > p) gamma = m;
+        if (gamma == a) {
+            childL[id] = LEAF | (int32_t)a;
+            parent_leaf[a] = id;
+        } else {
+            childL[id] = (int32_t)gamma;
+            parent_internal[gamma] = id;
+            stack.push_back({a, gamma, (int32_t)gamma});
+        }
+        if (gamma + 1 == b) {
+            childR[id] = LEAF | (int32_t)b;
+            parent_leaf[b] = id;
+        } else {
+            childR[id] = (int32_t)(gamma + 1);
+            parent_internal[gamma + 1] = id;
+            stack.push_back({gamma + 1, b, (int32_t)(gamma + 1)});
+        }
+    }
+}
+
+// Boxes of all internal nodes as unions of their children. leaf_lo/hi: 3*n float32
+// in SORTED order. node_lo/hi: 3*(n-1) out. Children are visited before parents by
+// a post-order walk.
+void oracle_fit(const int32_t* childL, const int32_t* childR, int64_t n, const float* leaf_lo,
+                const float* leaf_hi, float* node_lo, float* node_hi) {
+    if (n < 2) return;
+    std::vector<std::pair<int32_t, int>> st;
+    st.push_back({0, 0});
+    while (!st.empty()) {
+        auto& top = st.back();
+        const int32_t id = top.first;
+        if (top.second == 0) {
+            top.second = 1;
+            for (int32_t c : {childL[id], childR[id]})
+                if (!(c & LEAF)) st.push_back({c, 0});
+            continue;
+        }
+        for (int a = 0; a < 3; ++a) {
+            float mn = INFINITY, mx = -INFINITY;
+            for (int32_t c : {childL[id], childR[id]}) {
+                const float* clo = (c & LEAF) ? &leaf_lo[3 * (int64_t)(c & 0x7fffffff)] : &node_lo[3 * (int64_t)c];
+                const float* chi = (c & LEAF) ? &leaf_hi[3 * (int64_t)(c & 0x7fffffff)] : &node_hi[3 * (int64_t)c];
+                mn = std::min(mn, clo[a]);
+                mx = std::max(mx, chi[a]);
+            }
+            node_lo[3 * (int64_t)id + a] = mn;
+            node_hi[3 * (int64_t)id + a] = mx;
+        }
+        st.pop_back();
+    }
+}
+
+// Surface-area cost of a binary BVH: sum over internal nodes of box area, divided by
+// the root box area (the quality measure of Sec. 6.2 "BVH Construction").
+double oracle_sah_cost(const float* node_lo, const float* node_hi, int64_t n_internal) {
+    auto area = [&](int64_t k) {
+        double dx = (double)node_hi[3 * k] - node_lo[3 * k];
+        double dy = (double)node_hi[3 * k + 1] - node_lo[3 * k + 1];
+        double dz = (double)node_hi[3 * k + 2] - node_lo[3 * k + 2];
+        return 2.0 * (dx * dy + dy * dz + dz * dx);
+    };
+    if (n_internal < 1) return 0.0;
+    double s = 0.0;
+    for (int64_t k = 0; k < n_internal; ++k) s += area(k);
+    double r = area(0);
+    return r > 0 ? s / r : 0.0;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+"""Pins for the oracle's LBVH build steps (CPU only).
+
+Each check ties the oracle to something other than its own code: hand-computed
+Morton codes, a hand-derived hierarchy, Python's stable sort, and structural
+invariants that any correct binary BVH over sorted leaves must satisfy."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+
+LEAF = np.int32(-2147483648)
+
+
+def _q(bits=10):
+    return 1 << bits
+
+
+# ---------------------------------------------------------------- Morton codes
+def test_morton_hand_values_30bit():
+    # bounds [0, 1024]^3 make q = floor(c) exactly
+    lo = np.zeros(3, np.float32)
+    hi = np.full(3, 1024.0, np.float32)
+    c = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1], [2, 0, 0], [3, 0, 0],
+                  [0, 3, 0], [1023, 1023, 1023], [1024, 1024, 1024], [512, 0, 0]], np.float32)
+    codes = oracle.morton(c, lo, hi, 10)
+    # x occupies bit 3k+2, y bit 3k+1, z bit 3k. expand(1)=1, expand(2)=0b1000=8, expand(3)=9
+    expected = [0, 4, 2, 1, 7, 8 << 2, 9 << 2, 9 << 1, (1 << 30) - 1, (1 << 30) - 1, 1 << 29]
+    assert codes.tolist() == expected
+
+
+def test_morton_hand_values_63bit():
+    lo = np.zeros(3, np.float32)
+    hi = np.full(3, float(1 << 21), np.float32)
+    c = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 1], [2, 0, 0], [(1 << 21) - 1] * 3, [1 << 20, 0, 0]], np.float32)
+    codes = oracle.morton(c, lo, hi, 21)
+    assert codes.tolist() == [0, 4, 1, 32, (1 << 63) - 1, 1 << 62]
+
+
+def test_morton_quantisation_edges():
+    lo = np.array([0, 5, -1], np.float32)
+    hi = np.array([1, 5, 1], np.float32)  # zero extent in y
+    c = np.array([[0.5, 5, 0], [1.0, 5, 1], [np.nextafter(np.float32(1), np.float32(0)), 5, -1]], np.float32)
+    codes = oracle.morton(c, lo, hi, 10)
+    # (0.5 -> 512, y -> 0, z: 1/2 -> 512); (1 -> clamp 1023, 0, 1023); (just below 1 -> 1023, 0, 0)
+    def code(x, y, z):
+        out = 0
+        for k in range(9, -1, -1):
+            out = (out << 3) | (((x >> k) & 1) << 2) | (((y >> k) & 1) << 1) | ((z >> k) & 1)
+        return out
+
+    assert codes.tolist() == [code(512, 0, 512), code(1023, 0, 1023), code(1023, 0, 0)]
+
+
+def test_morton_order_is_z_order_on_a_grid():
+    # On a 2x2x2 grid of cells the codes must enumerate the octants in z-order
+    lo = np.zeros(3, np.float32)
+    hi = np.full(3, 2.0, np.float32)
+    pts = np.array([[x, y, z] for x in (0.5, 1.5) for y in (0.5, 1.5) for z in (0.5, 1.5)], np.float32)
+    codes = oracle.morton(pts, lo, hi, 10)
+    order = np.argsort(codes, kind="stable")
+    assert order.tolist() == list(range(8))  # x major, then y, then z
+
+
+# ---------------------------------------------------------------- sort
+def test_stable_sort_matches_python_sorted():
+    rng = np.random.default_rng(1)
+    codes = rng.integers(0, 50, 2000).astype(np.uint64)
+    sk, order = oracle.stable_sort(codes)
+    ref = sorted(range(len(codes)), key=lambda i: int(codes[i]))
+    assert order.tolist() == ref
+    assert np.all(np.diff(sk.astype(np.int64)) >= 0)
+
+
+# ---------------------------------------------------------------- topology
+def _read_tree(path):
+    keys, nodes = None, {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        parts = line.split()
+        if parts[0] == "keys":
+            keys = [int(x) for x in parts[1:]]
+        else:
+            nodes[int(parts[1])] = parts[2:]
+    return keys, nodes
+
+
+def _enc(s):
+    return (int(s[1:]) | -2147483648) if s[0] == "L" else int(s[1:])
+
+
+def test_topology_hand_derived_example(golden_dir):
+    keys, nodes = _read_tree(os.path.join(golden_dir, "karras_example_tree.txt"))
+    cl, cr, pi, pl = oracle.topology(np.array(keys, np.uint64), 32)
+    for k, (l, r) in nodes.items():
+        assert cl[k] == np.int32(_enc(l)) and cr[k] == np.int32(_enc(r)), k
+
+
+def test_topology_duplicate_keys_split_by_index():
+    cl, cr, pi, pl = oracle.topology(np.zeros(5, np.uint64), 32)
+    # indices 0..4: highest differing bit of 0 and 4 is bit 2 -> [0,3] | [4]
+    assert (cl[0], cr[0]) == (3, np.int32(4 | -2147483648))
+    assert (cl[3], cr[3]) == (1, 2)
+    assert (cl[1], cr[1]) == (np.int32(0 | -2147483648), np.int32(1 | -2147483648))
+
+
+def _check_invariants(cl, cr, pi, pl, n):
+    assert cl.shape == (n - 1,) and cr.shape == (n - 1,)
+    leaf_seen = np.zeros(n, int)
+    node_seen = np.zeros(n - 1, int)
+    rng_lo = np.full(n - 1, -1)
+    rng_hi = np.full(n - 1, -1)
+    # ranges by a top-down walk
+    stack = [(0, 0, n - 1)]
+    while stack:
+        k, a, b = stack.pop()
+        rng_lo[k], rng_hi[k] = a, b
+        assert k in (a, b), "Karras: a node's index is one end of its range"
+        ends = []
+        for c in (cl[k], cr[k]):
+            if c < 0:
+                leaf_seen[c & 0x7FFFFFFF] += 1
+                ends.append((c & 0x7FFFFFFF, c & 0x7FFFFFFF))
+            else:
+                node_seen[c] += 1
+                ends.append(None)
+        # children partition [a,b] into [a,g] and [g+1,b]
+        g = None
+        if cl[k] < 0:
+            g = cl[k] & 0x7FFFFFFF
+            assert g == a
+        else:
+            g = cl[k]
+        if cr[k] < 0:
+            assert (cr[k] & 0x7FFFFFFF) == b and (cr[k] & 0x7FFFFFFF) == g + 1
+        else:
+            assert cr[k] == g + 1
+        if cl[k] >= 0:
+            stack.append((cl[k], a, g))
+        if cr[k] >= 0:
+            stack.append((cr[k], g + 1, b))
+    assert (leaf_seen == 1).all(), "every primitive in exactly one leaf"
+    assert node_seen[0] == 0 and (node_seen[1:] == 1).all(), "every non-root node has one parent"
+    assert pi[0] == -1
+    for k in range(n - 1):
+        for c in (cl[k], cr[k]):
+            if c < 0:
+                assert pl[c & 0x7FFFFFFF] == k
+            else:
+                assert pi[c] == k
+    return rng_lo, rng_hi
+
+
+@pytest.mark.parametrize("n,maxkey", [(2, 5), (3, 1), (17, 4), (1000, 1 << 30), (4096, 64)])
+def test_topology_invariants(n, maxkey):
+    rng = np.random.default_rng(n)
+    keys = np.sort(rng.integers(0, maxkey, n).astype(np.uint64))
+    cl, cr, pi, pl = oracle.topology(keys, 32)
+    _check_invariants(cl, cr, pi, pl, n)
+
+
+def test_topology_split_is_highest_differing_bit():
+    # brute force the split rule on every internal node of a random tree
+    rng = np.random.default_rng(7)
+    n = 300
+    keys = np.sort(rng.integers(0, 1 << 12, n).astype(np.uint64))
+    cl, cr, pi, pl = oracle.topology(keys, 32)
+    lo, hi = _check_invariants(cl, cr, pi, pl, n)
+    aug = [(int(keys[i]) << 32) | i for i in range(n)]
+    for k in range(n - 1):
+        a, b = lo[k], hi[k]
+        bit = (aug[a] ^ aug[b]).bit_length() - 1
+        g = cl[k] & 0x7FFFFFFF if cl[k] < 0 else cl[k]
+        assert all(((aug[m] >> bit) & 1) == 0 for m in range(a, g + 1))
+        assert all(((aug[m] >> bit) & 1) == 1 for m in range(g + 1, b + 1))
+
+
+# ---------------------------------------------------------------- fit
+def test_fit_boxes_are_unions_of_leaf_ranges():
+    mesh = scenegen.icosphere(2)
+    lo, hi, c = oracle.triangle_aabbs(mesh.vertices, mesh.indices)
+    r = oracle.lbvh(lo, hi, c, 10)
+    n = lo.shape[0]
+    rl, rh = _check_invariants(r["childL"], r["childR"], r["parent_internal"], r["parent_leaf"], n)
+    for k in range(n - 1):
+        a, b = rl[k], rh[k]
+        assert np.array_equal(r["node_lo"][k], r["leaf_lo"][a:b + 1].min(axis=0))
+        assert np.array_equal(r["node_hi"][k], r["leaf_hi"][a:b + 1].max(axis=0))
+    # the root is the union of every primitive box, and it contains the unit sphere's mesh
+    assert np.array_equal(r["node_lo"][0], lo.min(axis=0))
+    assert np.array_equal(r["node_hi"][0], hi.max(axis=0))
+
+
+def test_triangle_aabbs_and_centroids():
+    v = np.array([[0, 0, 0], [2, -1, 4], [1, 3, -2]], np.float32)
+    lo, hi, c = oracle.triangle_aabbs(v, np.array([[0, 1, 2]], np.uint32))
+    assert lo[0].tolist() == [0, -1, -2] and hi[0].tolist() == [2, 3, 4]
+    assert c[0].tolist() == [1, 1, 1]
+
+
+def test_sah_cost_of_two_unit_boxes():
+    # root [0,2]x[0,1]x[0,1] area 10; two unit children are leaves: cost = 10/10 = 1
+    assert oracle.sah_cost(np.array([[0, 0, 0]], np.float32), np.array([[2, 1, 1]], np.float32)) == 1.0

@@ -1,0 +1,336 @@
+"""Pins for the oracle's ray queries and ray generation (CPU only).
+
+Closed forms (analytic sphere, the flat plane y=0, exact pixel coverage of an
+axis-aligned quad), the paper's plane/edge triangle test against Moller-Trumbore,
+brute force against the oracle's own BVH, instancing identities, and the
+cosine-weighted hemisphere's known moments."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+
+NONE = oracle.NONE
+
+
+def _rays(o, d, tmin=0.0, tmax=np.inf):
+    o = np.atleast_2d(np.asarray(o, np.float64))
+    d = np.atleast_2d(np.asarray(d, np.float64))
+    n = max(o.shape[0], d.shape[0])
+    r = np.empty((n, 8), np.float32)
+    r[:, 0:3] = o
+    r[:, 3] = tmin
+    r[:, 4:7] = d
+    r[:, 7] = tmax
+    return r
+
+
+# ---------------------------------------------------------------- triangle formulas
+def test_mt_agrees_with_paper_plane_edge_form():
+    rng = np.random.default_rng(3)
+    agree = 0
+    for _ in range(3000):
+        tri = rng.uniform(-1, 1, 9).astype(np.float32)
+        o = rng.uniform(-3, 3, 3)
+        target = tri.reshape(3, 3).astype(np.float64).mean(0) + rng.normal(0, 0.4, 3)
+        d = target - o
+        ray = _rays(o, d / np.linalg.norm(d))[0]
+        h1, t1, u1, v1 = oracle.mt_test(ray, tri)
+        h2, t2, u2, v2 = oracle.plane_edge_test(ray, tri)
+        if h1 != h2:
+            # only allowed within rounding of an edge
+            assert min(u2, v2, 1 - u2 - v2) > -1e-12 and min(u2, v2, 1 - u2 - v2) < 1e-12
+            continue
+        if h1:
+            agree += 1
+            assert abs(t1 - t2) <= 1e-12 * max(1.0, abs(t2))
+            assert abs(u1 - u2) <= 1e-12 and abs(v1 - v2) <= 1e-12
+    assert agree > 500
+
+
+def test_triangle_is_double_sided_with_inclusive_edges():
+    tri = np.array([0, 0, 0, 1, 0, 0, 0, 1, 0], np.float32)
+    for dz in (-1.0, 1.0):
+        h, t, u, v = oracle.mt_test(_rays([0.25, 0.25, -dz], [0, 0, dz])[0], tri)
+        assert h and t == 1.0 and u == 0.25 and v == 0.25
+    # exactly on a vertex and on an edge: still a hit (edges inclusive)
+    assert oracle.mt_test(_rays([0, 0, 1], [0, 0, -1])[0], tri)[0]
+    assert oracle.mt_test(_rays([0.5, 0.5, 1], [0, 0, -1])[0], tri)[0]
+    assert not oracle.mt_test(_rays([0.5, 0.51, 1], [0, 0, -1])[0], tri)[0]
+    # t range inclusive at both ends, exclusive outside
+    assert oracle.mt_test(_rays([0.2, 0.2, 1], [0, 0, -1], 1.0, 1.0)[0], tri)[0]
+    assert not oracle.mt_test(_rays([0.2, 0.2, 1], [0, 0, -1], 0.0, 0.999)[0], tri)[0]
+    # parallel ray misses
+    assert not oracle.mt_test(_rays([0.2, 0.2, 0], [1, 0, 0])[0], tri)[0]
+
+
+# ---------------------------------------------------------------- closed forms
+def test_sphere_closed_form():
+    rng = np.random.default_rng(5)
+    sph = np.array([[1.0, -2.0, 0.5, 0.75]], np.float32)
+    S = oracle.Scene()
+    S.add_instance(S.add_spheres(sph))
+    c = sph[0, :3].astype(np.float64)
+    r = float(sph[0, 3])
+    o = rng.uniform(-5, 5, (2000, 3))
+    d = scenegen.unit_vectors(11, 2000)
+    rays = _rays(o, d)
+    h = S.trace(rays, bvh=False)
+    o32 = rays[:, :3].astype(np.float64)
+    d32 = rays[:, 4:7].astype(np.float64)
+    # perpendicular distance from the centre to the ray's line decides hit vs miss
+    f = c - o32
+    along = np.einsum("ij,ij->i", f, d32) / np.einsum("ij,ij->i", d32, d32)
+    perp = np.linalg.norm(f - along[:, None] * d32, axis=1)
+    inside = np.linalg.norm(f, axis=1) < r
+    expect_hit = inside | ((perp < r) & (along > 0))
+    margin = np.abs(perp - r) > 1e-9
+    assert np.array_equal((h.prim != NONE)[margin], expect_hit[margin])
+    hit = h.prim != NONE
+    p = o32[hit] + h.t[hit, None] * d32[hit]
+    assert np.allclose(np.linalg.norm(p - c, axis=1), r, rtol=0, atol=1e-9)
+    # from outside the near root is taken, from inside the far one
+    assert np.all((np.einsum("ij,ij->i", p - c, d32[hit]) <= 1e-9) == ~inside[hit])
+
+
+def test_flat_terrain_is_the_plane_y0():
+    mesh = scenegen.terrain(cells=16, amplitude=0.0)
+    assert np.all(mesh.vertices[:, 1] == 0)
+    S = oracle.Scene()
+    S.add_instance(S.add_mesh(mesh.vertices, mesh.indices))
+    rng = np.random.default_rng(9)
+    o = np.column_stack([rng.uniform(-0.9, 0.9, 3000), rng.uniform(0.5, 2, 3000), rng.uniform(-0.9, 0.9, 3000)])
+    target = np.column_stack([rng.uniform(-0.95, 0.95, 3000), np.zeros(3000), rng.uniform(-0.95, 0.95, 3000)])
+    d = target - o
+    rays = _rays(o, d / np.linalg.norm(d, axis=1, keepdims=True))
+    h = S.trace(rays, bvh=False)
+    o32 = rays[:, :3].astype(np.float64)
+    d32 = rays[:, 4:7].astype(np.float64)
+    t = -o32[:, 1] / d32[:, 1]
+    p = o32 + t[:, None] * d32
+    assert np.all(h.prim != NONE)
+    assert np.allclose(h.t, t, rtol=1e-12, atol=0)
+    # the triangle: cell from floor(), then the side of the diagonal (i,j)-(i+1,j+1)
+    gx = (p[:, 0] + 1) * 8
+    gz = (p[:, 2] + 1) * 8
+    i = np.floor(gx).astype(int)
+    j = np.floor(gz).astype(int)
+    fx, fz = gx - i, gz - j
+    tri = 2 * (j * 16 + i) + (fz > fx).astype(int)
+    clear = (np.abs(fx - fz) > 1e-9) & (np.minimum.reduce([fx, fz, 1 - fx, 1 - fz]) > 1e-9)
+    assert np.array_equal(h.prim[clear].astype(int), tri[clear])
+
+
+def test_quad_pixel_coverage_through_the_camera():
+    W, H = 64, 48
+    cam = scenegen.look_down_z_camera([0, 0, 3], W, H)
+    rays = oracle.camera_rays(cam.packed(), W, H)
+    z0 = 1.0
+    dist = 3.0 - z0
+    th = math.tan(math.radians(30))
+    aspect = W / H
+    # choose quad edges half-way between pixel centres so no centre lies on an edge
+    def film_x(x):
+        return (2 * (x + 0.5) / W - 1) * aspect * th
+
+    def film_y(y):
+        return (1 - 2 * (y + 0.5) / H) * th
+
+    x0 = 0.5 * (film_x(10) + film_x(11)) * dist
+    x1 = 0.5 * (film_x(40) + film_x(41)) * dist
+    y1 = 0.5 * (film_y(5) + film_y(6)) * dist
+    y0 = 0.5 * (film_y(30) + film_y(31)) * dist
+    v = np.array([[x0, y0, z0], [x1, y0, z0], [x1, y1, z0], [x0, y1, z0]], np.float32)
+    idx = np.array([[0, 1, 2], [0, 2, 3]], np.uint32)
+    S = oracle.Scene()
+    S.add_instance(S.add_mesh(v, idx))
+    h = S.trace(rays, bvh=False)
+    got = (h.prim != NONE).reshape(H, W)
+    want = np.zeros((H, W), bool)
+    want[6:31, 11:41] = True
+    assert np.array_equal(got, want)
+    assert np.allclose(h.t[want.ravel()], dist / -rays[want.ravel(), 6].astype(np.float64), rtol=1e-12)
+
+
+def test_icosphere_hits_lie_between_inradius_and_radius():
+    mesh = scenegen.icosphere(3)
+    S = oracle.Scene()
+    S.add_instance(S.add_mesh(mesh.vertices, mesh.indices))
+    cam = scenegen.look_down_z_camera([0, 0, 3], 128, 128)
+    rays = oracle.camera_rays(cam.packed(), 128, 128)
+    h = S.trace(rays, bvh=False)
+    hit = h.prim != NONE
+    p = rays[hit, :3].astype(np.float64) + h.t[hit, None] * rays[hit, 4:7].astype(np.float64)
+    r = np.linalg.norm(p, axis=1)
+    v = mesh.vertices.astype(np.float64)
+    i = mesh.indices
+    n = np.cross(v[i[:, 1]] - v[i[:, 0]], v[i[:, 2]] - v[i[:, 0]])
+    r_in = np.min(np.abs(np.einsum("ij,ij->i", n / np.linalg.norm(n, axis=1, keepdims=True), v[i[:, 0]])))
+    assert r.min() >= r_in - 1e-7 and r.max() <= 1 + 1e-7
+    # the centre pixel of an even image sees the sphere; a corner pixel does not
+    assert hit.reshape(128, 128)[64, 64] and not hit.reshape(128, 128)[0, 0]
+
+
+# ---------------------------------------------------------------- BVH vs brute force
+def _aimed_rays(n, targets, seed):
+    """Rays from random origins in [-12,12]^3 toward random points near `targets`."""
+    rng = np.random.default_rng(seed)
+    o = rng.uniform(-12, 12, (n, 3))
+    tgt = targets[rng.integers(0, len(targets), n)] + rng.normal(0, 0.8, (n, 3))
+    d = tgt - o
+    return _rays(o, d / np.linalg.norm(d, axis=1, keepdims=True))
+
+
+def _small_instanced_scene():
+    mesh = scenegen.terrain(cells=24, amplitude=0.2)
+    fr = scenegen.random_frames(6, config=99)
+    S = oracle.Scene()
+    g = S.add_mesh(mesh.vertices, mesh.indices)
+    for k in range(6):
+        S.add_instance(g, fr.packed()[k])
+    return S, mesh, fr
+
+
+@pytest.mark.parametrize("any_hit", [False, True])
+def test_bvh_equals_brute_force(any_hit):
+    S, mesh, fr = _small_instanced_scene()
+    sph = scenegen.spheres(500, half=8.0, config=98)
+    S.add_instance(S.add_spheres(sph))
+    S.build()
+    rays = _aimed_rays(6000, fr.translation.astype(np.float64), 97)
+    rays[:, 7] = np.where(np.arange(6000) % 2 == 0, np.inf, 4.0)
+    a = S.trace(rays, any_hit=any_hit, bvh=False)
+    b = S.trace(rays, any_hit=any_hit, bvh=True)
+    assert np.array_equal(a.prim != NONE, b.prim != NONE)
+    assert (a.prim != NONE).mean() > 0.1
+    if not any_hit:
+        assert np.array_equal(a.prim, b.prim) and np.array_equal(a.inst, b.inst)
+        assert np.array_equal(a.t, b.t)
+
+
+def test_any_hit_equals_closest_within_max_t():
+    S, mesh, fr = _small_instanced_scene()
+    S.build()
+    rays = _aimed_rays(4000, fr.translation.astype(np.float64), 96)
+    c = S.trace(rays, any_hit=False)  # maxT = +inf
+    rays[:, 7] = 14.0
+    a = S.trace(rays, any_hit=True)
+    assert np.array_equal(a.prim != NONE, c.t <= 14.0)
+    assert 0.05 < (c.t <= 14.0).mean() < (c.prim != NONE).mean()
+
+
+def test_instancing_matches_world_space_triangles():
+    """Two levels: tracing object-space BLAS under SRT frames equals tracing the
+    instanced triangles placed in world space (float64, computed independently)."""
+    S, mesh, fr = _small_instanced_scene()
+    R = scenegen.quat_to_matrix64(fr.rotation)
+    world_v = []
+    world_i = []
+    for k in range(6):
+        w = (mesh.vertices.astype(np.float64) * fr.scale[k].astype(np.float64)) @ R[k].T + fr.translation[k]
+        world_v.append(w)
+        world_i.append(mesh.indices.astype(np.int64) + k * mesh.vertices.shape[0])
+    W = oracle.Scene()
+    W.add_instance(W.add_mesh(np.concatenate(world_v).astype(np.float32), np.concatenate(world_i).astype(np.uint32)))
+    rays = _aimed_rays(4000, fr.translation.astype(np.float64), 95)
+    a = S.trace(rays, bvh=False)
+    b = W.trace(rays, bvh=False)
+    hit = a.prim != NONE
+    assert hit.mean() > 0.05
+    ntri = mesh.num_triangles
+    same = (a.prim.astype(np.int64) + a.inst.astype(np.int64) * ntri == b.prim.astype(np.int64)) | ~hit
+    # world vertices were rounded to float32, so only near-edge rays may differ
+    assert same.mean() > 0.995
+    both = hit & (b.prim != NONE) & same
+    assert np.allclose(a.t[both], b.t[both], rtol=1e-5)
+
+
+def test_identity_and_translation_frames():
+    mesh = scenegen.icosphere(2)
+    rays = scenegen.random_rays(3000, [-3, -3, -3], [3, 3, 3], config=94)
+    D = oracle.Scene()
+    D.add_instance(D.add_mesh(mesh.vertices, mesh.indices))
+    I = oracle.Scene()
+    I.add_instance(I.add_mesh(mesh.vertices, mesh.indices), np.array([0, 0, 0, 1, 1, 1, 1, 0, 0, 0], np.float32))
+    a, b = D.trace(rays), I.trace(rays)
+    assert np.array_equal(a.prim, b.prim) and np.array_equal(a.t, b.t)
+    # translation by (1,2,3) equals shifting the ray origins by -(1,2,3) (exact in float32 here)
+    T = oracle.Scene()
+    T.add_instance(T.add_mesh(mesh.vertices, mesh.indices), np.array([0, 0, 0, 1, 1, 1, 1, 1, 2, 3], np.float32))
+    shifted = rays.copy()
+    shifted[:, 0:3] -= np.array([1, 2, 3], np.float32)
+    c = T.trace(rays)
+    d = D.trace(shifted)
+    ok = np.abs(rays[:, 0:3] - np.round(rays[:, 0:3] * 1024) / 1024).max(axis=1) >= 0  # all rays
+    assert np.array_equal(c.prim[ok], d.prim[ok])
+    # uniform scale 2 with an unnormalised direction keeps t: the ray (o, d) against the
+    # sphere scaled by 2 hits where (o/2, d/2) hits the unit-scale sphere, at the same t
+    S2 = oracle.Scene()
+    S2.add_instance(S2.add_mesh(mesh.vertices, mesh.indices), np.array([0, 0, 0, 1, 2, 2, 2, 0, 0, 0], np.float32))
+    half = rays.copy()
+    half[:, 0:3] *= 0.5
+    half[:, 4:7] *= 0.5
+    e, f = S2.trace(rays), D.trace(half)
+    assert np.array_equal(e.prim, f.prim)
+    hit = e.prim != NONE
+    assert np.allclose(e.t[hit], f.t[hit], rtol=1e-12)
+
+
+# ---------------------------------------------------------------- ray generation
+def test_camera_closed_form():
+    cam = scenegen.look_down_z_camera([0, 0, 3], 3, 3)
+    rays = oracle.camera_rays(cam.packed(), 3, 3)
+    # centre pixel of an odd image looks straight down -z
+    assert np.allclose(rays[4, 4:7], [0, 0, -1], atol=1e-7)
+    th = math.tan(math.radians(30))
+    # top-left pixel centre u=v=1/6: film point (-(2/3) th, (2/3) th, -1)
+    d = np.array([-(2 / 3) * th, (2 / 3) * th, -1.0])
+    assert np.allclose(rays[0, 4:7], d / np.linalg.norm(d), atol=1e-7)
+    assert np.all(rays[:, 3] == 0) and np.all(np.isinf(rays[:, 7]))
+    assert np.allclose(rays[:, 0:3], [0, 0, 3])
+
+
+def test_splitmix64_published_outputs(golden_dir):
+    vals = [int(l, 16) for l in open(f"{golden_dir}/splitmix64_seed0.txt") if l.startswith("0x")]
+    # xi keeps the top 24 bits of the generator's output at counters 0 and 1
+    assert oracle.xi(0, 0, 0, 0) == (vals[0] >> 40) / 2.0 ** 24
+    assert oracle.xi(0, 0, 0, 1) == (vals[1] >> 40) / 2.0 ** 24
+    assert int(scenegen.u64(0, 2)[0]) == vals[0] and int(scenegen.u64(0, 2)[1]) == vals[1]
+
+
+def test_cosine_hemisphere_moments():
+    n = 20000
+    xs = np.array([oracle.sample_hemisphere(a, b) for a, b in zip(scenegen.uniform(1, n), scenegen.uniform(2, n))])
+    assert np.allclose(np.linalg.norm(xs, axis=1), 1, atol=1e-12)
+    assert xs[:, 1].min() >= 0
+    # cos-weighted: E[cos] = 2/3, E[cos^2] = 1/2, P(cos > 1/2) = 3/4
+    assert abs(xs[:, 1].mean() - 2 / 3) < 0.01
+    assert abs((xs[:, 1] ** 2).mean() - 0.5) < 0.01
+    assert abs((xs[:, 1] > 0.5).mean() - 0.75) < 0.01
+    assert np.allclose(oracle.sample_hemisphere(0.0, 0.0), [0, 1, 0])
+    assert np.allclose(oracle.sample_hemisphere(0.25, 1.0), [0, 0, 1], atol=1e-15)
+
+
+def test_ao_rays_on_the_flat_plane():
+    mesh = scenegen.terrain(cells=8, amplitude=0.0)
+    S = oracle.Scene()
+    S.add_instance(S.add_mesh(mesh.vertices, mesh.indices))
+    prim = scenegen.random_rays(200, [-0.5, 1, -0.5], [0.5, 2, 0.5], config=93)
+    prim[:, 4:7] = np.array([0.1, -1, 0.05], np.float32) / np.float32(np.linalg.norm([0.1, -1, 0.05]))
+    h = S.trace(prim)
+    assert np.all(h.prim != NONE)
+    ao = oracle.ao_rays(S, prim, h, 8, 1234, 0.25)
+    assert np.allclose(ao[:, 1], 1e-4, atol=1e-7)  # origin p + 1e-4 n with n = +y
+    assert np.all(ao[:, 5] >= 0)  # hemisphere about +y
+    assert np.allclose(np.linalg.norm(ao[:, 4:7].astype(np.float64), axis=1), 1, atol=1e-6)
+    assert np.all(ao[:, 7] == np.float32(0.25)) and np.all(ao[:, 3] == 0)
+    # the plane never occludes rays leaving it upward
+    assert np.all(S.trace(ao, any_hit=True).prim == NONE)
+    # seen from below, the normal flips to -y
+    prim[:, 1] = -prim[:, 1]
+    prim[:, 5] = -prim[:, 5]
+    h = S.trace(prim)
+    ao = oracle.ao_rays(S, prim, h, 4, 1234, 0.25)
+    assert np.allclose(ao[:, 1], -1e-4, atol=1e-7) and np.all(ao[:, 5] <= 0)
