@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GPU ray tracer on the two-level ambient-occlusion workload.
+
+Workload (synthetic, seeded): one procedural terrain mesh (256x256 cells, 131,072
+triangles, 4-octave value noise of amplitude 0.2) instanced 64 times under random SRT
+frames (uniform rotation, per-axis scale in [0.5, 2], translation in [-10, 10]^3);
+a 1920x1080 pinhole camera at the scene centre + (0, 0, 1.5 * extent) with 60 degree
+vertical field of view; at every primary hit 8 cosine-weighted hemisphere rays of
+length 0.05 * extent traced as any-hit queries.
+
+One step = the whole hot path: bottom-level LBVH build (primitive boxes, centroid
+bounds, Morton codes, radix sort, Karras emission, bottom-up fit), top-level build
+over the instances, camera ray generation, closest-hit traversal of the primary
+rays, and the fused ambient-occlusion kernel (ray generation + any-hit traversal).
+value = (primary rays + AO rays) / step time, in Mrays/s, all ranks together; each
+rank runs its own replica (the path shards by independent replicas, so no collective
+touches the data path). L2 is flushed (512 MB write) between timed steps, outside the
+timed region.
+
+`--impl reference` times the CPU oracle (FP64, oracle/) on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s closest/any-hit, % of mem roofline; batched & adjoint vs plain same GPU"
+UNIT = "Mrays/s"
+WORKLOAD = dict(workload="terrain64-ao-1080p", instances=64, terrain_cells=256, triangles_per_instance=131072,
+                width=1920, height=1080, ao_samples=8, ao_length="0.05*extent", seed=20260301)
+RAY_BYTES, HIT_BYTES = 32, 20
+NODE_BYTES, TRI_BYTES, INST_BYTES = 64, 48, 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="grt", choices=["grt", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    import scenegen
+
+    sc = scenegen.terrain_instances(WORKLOAD["instances"], WORKLOAD["terrain_cells"], 0.2, WORKLOAD["seed"])
+    cam = scenegen.overview_camera(sc, WORKLOAD["width"], WORKLOAD["height"])
+    return sc, cam
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_00292_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken from the current sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_grt(args, rank, world, local):
+    import torch
+
+    import paper_2603_00292_gb300 as grt
+    from paper_2603_00292_gb300 import build as grt_build
+    from paper_2603_00292_gb300.objects import Context, Geometry, Scene, device_tensor, new_hits, new_rays
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        grt_build.build()
+    if dist:
+        dist.barrier()
+
+    sc, cam = workload()
+    W, H, spp = WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["ao_samples"]
+    npix = W * H
+    length = float(np.float32(0.05 * sc.extent))
+    seed = WORKLOAD["seed"]
+    mesh = sc.meshes[0]
+    ctx = Context(local)
+    verts = device_tensor(mesh.vertices)
+    idx = device_tensor(mesh.indices)
+    frames = device_tensor(sc.frames.packed())
+    geom = Geometry(ctx, vertices=verts, indices=idx)
+    scene = Scene(ctx, [geom.handle] * WORKLOAD["instances"], frames)
+    rays = new_rays(npix)
+    hits = new_hits(npix)
+    ao = torch.empty(npix, dtype=torch.float32, device="cuda")
+    c = cam.packed()
+    gcam = grt.camera(c[0:3], c[3:6], c[6:9])
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ev = {k: torch.cuda.Event(enable_timing=True) for k in ("c0", "c1", "a0", "a1", "s0", "s1")}
+
+    def step(timed_kernels: bool):
+        geom.build(sh)
+        scene.build(sh)
+        grt.grtGenerateCameraRays(ctx.handle, gcam, W, H, rays, sh)
+        if timed_kernels:
+            ev["c0"].record(stream)
+        grt.grtTraceClosest(ctx.handle, scene.handle, None, rays, npix, hits, None, None, sh)
+        if timed_kernels:
+            ev["c1"].record(stream)
+            ev["a0"].record(stream)
+        grt.grtTraceAmbientOcclusion(ctx.handle, scene.handle, rays, hits, npix, spp, seed, length, ao, None, sh)
+        if timed_kernels:
+            ev["a1"].record(stream)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+    nhit = int((hits[:, 1].view(torch.int32) != -1).sum().item())
+    rays_per_step = npix + spp * nhit
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    step_ms, closest_ms, ao_ms = [], [], []
+    clocks = ClockSampler(local)
+    launches0 = grt.grtGetLaunchCount()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev["s0"].record(stream)
+        step(True)
+        ev["s1"].record(stream)
+        ev["s1"].synchronize()
+        step_ms.append(ev["s0"].elapsed_time(ev["s1"]))
+        closest_ms.append(ev["c0"].elapsed_time(ev["c1"]))
+        ao_ms.append(ev["a0"].elapsed_time(ev["a1"]))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = grt.grtGetLaunchCount() - launches0
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * rays_per_step * args.steps / total_s / 1e6
+
+    # --------------------------------------------------- traversal work per ray (counting pass)
+    cnt = grt.trace_options(flags=grt.GRT_TRACE_FLAG_COUNT)
+    grt.grtGetTraceStatistics(ctx.handle, sh)
+    grt.grtTraceClosest(ctx.handle, scene.handle, None, rays, npix, hits, None, cnt, sh)
+    st_c = grt.grtGetTraceStatistics(ctx.handle, sh)
+    grt.grtTraceAmbientOcclusion(ctx.handle, scene.handle, rays, hits, npix, spp, seed, length, ao, cnt, sh)
+    st_a = grt.grtGetTraceStatistics(ctx.handle, sh)
+    bytes_closest = (npix * (RAY_BYTES + HIT_BYTES) + NODE_BYTES * st_c["nodesVisited"] +
+                     TRI_BYTES * st_c["trianglesTested"] + INST_BYTES * st_c["instancesEntered"])
+    # AO: per pixel the primary ray and hit in, the AO value out; per hit pixel the
+    # instance record, geometry header, leaf index, triangle record and frame rows
+    bytes_ao = (npix * (RAY_BYTES + HIT_BYTES + 4) + nhit * (128 + 64 + 4 + 48 + 48) +
+                NODE_BYTES * st_a["nodesVisited"] + TRI_BYTES * st_a["trianglesTested"] +
+                INST_BYTES * st_a["instancesEntered"])
+    kern = {"closest": (statistics.mean(closest_ms), bytes_closest, "traceKernel<closest, scene>"),
+            "ao": (statistics.mean(ao_ms), bytes_ao, "aoTraceKernel")}
+    dom = max(kern, key=lambda k: kern[k][0])
+    ms, nbytes, kname = kern[dom]
+    peaks, how = measured_peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": how,
+                "traffic": ncu_traffic(kname), "algorithmic_bytes_per_launch": int(nbytes),
+                "launch_ms": round(ms, 4),
+                "per_ray": {k: round(v / max(1, (st_c if dom == "closest" else st_a)["rays"]), 3)
+                            for k, v in (st_c if dom == "closest" else st_a).items() if k != "rays"}}
+
+    # --------------------------------------------------- end to end through the C ABI, host buffers
+    vh = torch.from_numpy(mesh.vertices).pin_memory()
+    ih = torch.from_numpy(mesh.indices.view(np.int32)).pin_memory()
+    fh = torch.from_numpy(sc.frames.packed()).pin_memory()
+    ao_h = torch.empty(npix, dtype=torch.float32).pin_memory()
+    hits_h = torch.empty((npix, 5), dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        ev["s0"].record(stream)
+        verts.copy_(vh, non_blocking=True)
+        idx.copy_(ih, non_blocking=True)
+        frames.copy_(fh, non_blocking=True)
+        step(False)
+        hits_h.copy_(hits, non_blocking=True)
+        ao_h.copy_(ao, non_blocking=True)
+        ev["s1"].record(stream)
+        ev["s1"].synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(ev["s0"].elapsed_time(ev["s1"]))
+    e2e_s = sum(e2e_ms) / 1e3
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = vh.numel() * 4 + ih.numel() * 4 + fh.numel() * 4
+    d2h = ao_h.numel() * 4 + hits_h.numel() * 4
+    e2e = {"value": round(world * rays_per_step * args.steps / e2e_s / 1e6, 2), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(WORKLOAD, rays_per_step=rays_per_step, primary_hits=nhit, l2="flushed between steps",
+                           parallelism=f"replicas{world}"),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "kernel_ms": {"closest": round(statistics.mean(closest_ms), 4), "ao": round(statistics.mean(ao_ms), 4)}}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle(sc, cam, length, seed, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_scene(sc):
+    import oracle
+
+    S = oracle.Scene()
+    g = S.add_mesh(sc.meshes[0].vertices, sc.meshes[0].indices)
+    for k in range(len(sc.geom_of_instance)):
+        S.add_instance(g, sc.frames.packed()[k])
+    S.build()
+    return S
+
+
+def oracle_sample(S, sc, cam, length, seed, stride: int, offset: int = 0):
+    """Trace every `stride`-th pixel's primary ray (closest) and its AO rays (any-hit)
+    with the FP64 oracle. Returns (rays traced, seconds)."""
+    import oracle
+
+    W, H, spp = WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["ao_samples"]
+    rays = oracle.camera_rays(cam.packed(), W, H)[offset::stride]
+    t0 = time.perf_counter()
+    hits = S.trace(rays)
+    ao = oracle.ao_rays(S, rays, hits, spp, seed, length)
+    valid = ao[:, 7] > 0
+    S.trace(ao[valid], any_hit=True)
+    dt = time.perf_counter() - t0
+    return rays.shape[0] + int(valid.sum()), dt
+
+
+def cpu_oracle(sc, cam, length, seed, target_s: float):
+    S = oracle_scene(sc)
+    n, dt = oracle_sample(S, sc, cam, length, seed, stride=2003)
+    stride = max(1, int(2003 * dt / max(target_s, 1e-3)))
+    n, dt = oracle_sample(S, sc, cam, length, seed, stride=stride, offset=1)
+    return {"value": round(n / dt / 1e6, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"every {stride}th pixel of the 1920x1080 image: closest hit + 8 AO any-hit rays per hit, "
+                      f"{n} rays, FP64 oracle BVH on {os.cpu_count()} host threads ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return
+    sc, cam = workload()
+    length = float(np.float32(0.05 * sc.extent))
+    seed = WORKLOAD["seed"]
+    S = oracle_scene(sc)
+    budget = 120.0 / max(1, args.steps + args.warmup)  # seconds per step
+    n, dt = oracle_sample(S, sc, cam, length, seed, stride=4001)
+    stride = max(1, int(4001 * dt / budget))
+    times, count = [], 0
+    for k in range(args.warmup + args.steps):
+        n, dt = oracle_sample(S, sc, cam, length, seed, stride=stride, offset=k % stride)
+        if k >= args.warmup:
+            times.append(dt)
+            count += n
+    value = count / sum(times) / 1e6
+    cb = {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"per step every {stride}th pixel (closest + 8 AO any-hit rays per hit), FP64 oracle"}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism="host cores"), "cpu_baseline": cb,
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_grt(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,344 @@
+/*
+ * grt.h - C ABI of a GB300 (sm_103a) BVH builder and ray tracer.
+ *
+ * The API follows the problem statement of "Ray Tracing using HIP" (Yoshimura, Eto,
+ * Meister, Harada), Sec. 7: a context; bottom-level geometries built from an indexed
+ * triangle mesh or from a list of AABBs of custom primitives (Sec. 7.2); a two-level
+ * scene built from instances of geometries with SRT frames (Sec. 7.3); a function
+ * table that maps (geometry type, ray type) to a custom intersection (Sec. 7.4); and
+ * closest-hit / any-hit queries that write hit records (Sec. 7.6).
+ *
+ * Conventions for every call:
+ *  - Every function returns grtError. GRT_SUCCESS is 0.
+ *  - "device pointer" = an address in the current CUDA device's global memory owned
+ *    by the CALLER (the paper's Sec. 7.1: all input buffers live on the device). The
+ *    library never frees caller memory.
+ *  - Objects (context, geometry, scene, function table) are owned by the library and
+ *    released by the matching grtDestroy* call. A scene refers to its geometries,
+ *    which must outlive it.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Builds and traces are asynchronous on it; errors detected by device code
+ *    (stack overflow, step limit, wait timeout) are latched in the context and
+ *    read by grtGetLastDeviceError.
+ *  - Sizes are element counts unless the name says bytes.
+ *  - The library is single-device: a context binds the device given at creation,
+ *    and every call made with it must run with that device current.
+ */
+#ifndef GRT_H_
+#define GRT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRT_API_VERSION 1u
+
+typedef enum grtError {
+    GRT_SUCCESS = 0,
+    GRT_ERROR_INVALID_PARAMETER = 1, /* null handle/pointer, bad enum, count or stride */
+    GRT_ERROR_OUT_OF_MEMORY = 2,     /* a library-owned allocation failed */
+    GRT_ERROR_INVALID_API_VERSION = 3,
+    GRT_ERROR_NOT_BUILT = 4,         /* trace on a geometry/scene that was never built */
+    GRT_ERROR_STACK_OVERFLOW = 5,    /* device: a ray needed more stack than configured */
+    GRT_ERROR_STEP_LIMIT = 6,        /* device: a ray exceeded the traversal step bound */
+    GRT_ERROR_TIMEOUT = 7,           /* device: a bounded wait expired */
+    GRT_ERROR_CUDA = 8,              /* a CUDA runtime call or launch failed */
+    GRT_ERROR_INTERNAL = 9
+} grtError;
+
+/* Opaque handles. A grtGeometry and a grtScene are device addresses of small
+ * library-owned headers, so they may be stored in device memory (grtInstance). */
+typedef struct grtContext_* grtContext;
+typedef struct grtGeometry_* grtGeometry;
+typedef struct grtScene_* grtScene;
+typedef struct grtFuncTable_* grtFuncTable;
+
+/* ---------------------------------------------------------------- context (Sec. 7.1) */
+typedef struct grtContextCreationInput {
+    int32_t device; /* CUDA device ordinal; the paper's vendor/device fields reduce to this */
+} grtContextCreationInput;
+
+typedef enum grtLogLevel {
+    GRT_LOG_NONE = 0,
+    GRT_LOG_ERROR = 1,
+    GRT_LOG_WARN = 2,
+    GRT_LOG_INFO = 4
+} grtLogLevel;
+
+/* Creates a context on input->device. apiVersion must equal GRT_API_VERSION
+ * (else GRT_ERROR_INVALID_API_VERSION). Allocates the context's small device
+ * workspace (error word, work counters). */
+grtError grtCreateContext(uint32_t apiVersion, const grtContextCreationInput* input, grtContext* out);
+grtError grtDestroyContext(grtContext ctx);
+/* Bit set of grtLogLevel values printed to stderr (Sec. 7.1's log level). */
+grtError grtSetLogLevel(uint32_t levels);
+
+/* Reads and clears the device error latched by builds and traces enqueued on
+ * `stream` (synchronises the stream). *err = GRT_SUCCESS when none. */
+grtError grtGetLastDeviceError(grtContext ctx, void* stream, grtError* err);
+
+/* ---------------------------------------------------------------- geometry (Sec. 7.2) */
+typedef enum grtPrimitiveType {
+    GRT_PRIMITIVE_TRIANGLE_MESH = 0,
+    GRT_PRIMITIVE_AABB_LIST = 1
+} grtPrimitiveType;
+
+/* Indexed triangles: triangle i = three uint32 vertex indices at
+ * triangleIndices + i*triangleStride (stride >= 12 bytes, multiple of 4);
+ * vertex k = three float32 at vertices + k*vertexStride (stride >= 12, multiple
+ * of 4). Both are device pointers. */
+typedef struct grtTriangleMeshPrimitive {
+    uint32_t triangleCount;
+    uint32_t triangleStride;
+    const void* triangleIndices;
+    uint32_t vertexCount;
+    uint32_t vertexStride;
+    const void* vertices;
+} grtTriangleMeshPrimitive;
+
+/* Custom primitives given by their boxes: box i = float32 lo.xyz, hi.xyz at
+ * aabbs + i*aabbStride (stride >= 24, multiple of 4; device pointer). */
+typedef struct grtAABBListPrimitive {
+    uint32_t aabbCount;
+    uint32_t aabbStride;
+    const void* aabbs;
+} grtAABBListPrimitive;
+
+typedef struct grtGeometryBuildInput {
+    uint32_t type;     /* grtPrimitiveType */
+    uint32_t geomType; /* column of the function table for AABB lists */
+    grtTriangleMeshPrimitive triangleMesh;
+    grtAABBListPrimitive aabbList;
+} grtGeometryBuildInput;
+
+/* The paper's fast / balanced / high-quality flags (Sec. 7.2) are accepted; every
+ * flag builds the same linear BVH (LBVH). */
+typedef enum grtBuildFlags {
+    GRT_BUILD_PREFER_FAST = 0,
+    GRT_BUILD_PREFER_BALANCED = 1,
+    GRT_BUILD_PREFER_HIGH_QUALITY = 2
+} grtBuildFlags;
+
+typedef struct grtBuildOptions {
+    uint32_t buildFlags; /* grtBuildFlags */
+    uint32_t mortonBits; /* 30 or 63; 0 = 30 when count <= 2^20, else 63 */
+} grtBuildOptions;
+
+typedef enum grtBuildOperation {
+    GRT_BUILD_OPERATION_BUILD = 0, /* full rebuild */
+    GRT_BUILD_OPERATION_UPDATE = 1 /* refit: same topology, boxes recomputed bottom-up (Sec. 6.2) */
+} grtBuildOperation;
+
+/* Size in bytes of the caller-allocated temporary buffer for building `input`
+ * (Sec. 7.2); the buffer may be reused for other builds once a build completes. */
+grtError grtGetGeometryBuildTemporaryBufferSize(grtContext ctx, const grtGeometryBuildInput* input,
+                                                const grtBuildOptions* options, size_t* sizeBytes);
+/* Allocates the library-owned node and leaf arrays for `input`'s primitive count. */
+grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, const grtBuildOptions* options,
+                           grtGeometry* out);
+/* Enqueues the LBVH build (or, for UPDATE, the refit) on `stream`. `temp` is a
+ * device buffer of at least the queried size, 16-byte aligned. The primitive count
+ * must equal the one given to grtCreateGeometry. */
+grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInput* input,
+                          const grtBuildOptions* options, void* temp, void* stream, grtGeometry geom);
+grtError grtDestroyGeometry(grtContext ctx, grtGeometry geom);
+
+/* ---------------------------------------------------------------- scene (Sec. 7.3) */
+typedef enum grtInstanceType { GRT_INSTANCE_GEOMETRY = 0 } grtInstanceType;
+
+typedef struct grtInstance { /* 16 bytes */
+    uint32_t type;           /* grtInstanceType */
+    uint32_t mask;           /* reserved, 0 */
+    grtGeometry geometry;
+} grtInstance;
+
+/* Instance transform world = T * R * S * object. rotation is a quaternion x,y,z,w
+ * (normalised by the library; the paper leaves the encoding unspecified). 40 bytes. */
+typedef struct grtFrameSRT {
+    float rotation[4];
+    float scale[3];
+    float translation[3];
+} grtFrameSRT;
+
+typedef struct grtSceneBuildInput {
+    uint32_t instanceCount;
+    uint32_t frameCount;               /* must equal instanceCount */
+    const grtInstance* instances;      /* device pointer, instanceCount entries */
+    const grtFrameSRT* instanceFrames; /* device pointer, frameCount entries */
+} grtSceneBuildInput;
+
+grtError grtGetSceneBuildTemporaryBufferSize(grtContext ctx, const grtSceneBuildInput* input,
+                                             const grtBuildOptions* options, size_t* sizeBytes);
+grtError grtCreateScene(grtContext ctx, const grtSceneBuildInput* input, const grtBuildOptions* options,
+                        grtScene* out);
+/* Builds the top level over the instances' world boxes. The instances' geometries
+ * must have been built earlier on the same stream (or be complete). */
+grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* input, const grtBuildOptions* options,
+                       void* temp, void* stream, grtScene scene);
+grtError grtDestroyScene(grtContext ctx, grtScene scene);
+
+/* ---------------------------------------------------------------- custom intersection (Sec. 7.4) */
+typedef enum grtIntersectFunc {
+    GRT_INTERSECT_NONE = 0,  /* custom primitives of this (geomType, rayType) are never hit */
+    GRT_INTERSECT_SPHERE = 1 /* built-in: data = float4 {centre.xyz, radius} per primitive */
+} grtIntersectFunc;
+
+typedef struct grtFuncDataSet {
+    uint32_t intersectFunc;        /* grtIntersectFunc */
+    uint32_t reserved;
+    const void* intersectFuncData; /* device pointer handed to the intersector */
+} grtFuncDataSet;
+
+/* A numRayTypes x numGeomTypes table, row-major (row = ray type), as the paper's
+ * flattened function layout. */
+grtError grtCreateFuncTable(grtContext ctx, uint32_t numGeomTypes, uint32_t numRayTypes, grtFuncTable* out);
+grtError grtSetFuncTable(grtContext ctx, grtFuncTable table, uint32_t geomType, uint32_t rayType,
+                         grtFuncDataSet set);
+grtError grtDestroyFuncTable(grtContext ctx, grtFuncTable table);
+
+/* ---------------------------------------------------------------- traversal (Sec. 6.2, 7.5, 7.6) */
+/* R(t) = origin + t*direction, t in [minT, maxT] (both inclusive). 32 bytes. */
+typedef struct grtRay {
+    float origin[3];
+    float minT;
+    float direction[3];
+    float maxT;
+} grtRay;
+
+/* 20 bytes. A miss has instanceID = primID = 0xFFFFFFFF and t = +inf. Triangle
+ * barycentrics: hit point = (1-u-v)*v0 + u*v1 + v*v2; custom primitives: u = v = 0.
+ * Tracing a geometry directly reports instanceID 0. */
+typedef struct grtHit {
+    uint32_t instanceID;
+    uint32_t primID;
+    float t;
+    float u;
+    float v;
+} grtHit;
+
+#define GRT_INVALID_ID 0xFFFFFFFFu
+
+/* Traversal stack (Sec. 7.5): each thread keeps its first sharedStackDepth entries in
+ * shared memory and the next globalStackDepth entries in a global buffer sized for
+ * every thread of the persistent grid. A ray that needs more is finished with the
+ * entries it has and latches GRT_ERROR_STACK_OVERFLOW. */
+typedef struct grtTraceOptions {
+    uint32_t rayType;          /* row of the function table */
+    uint32_t blockSize;        /* threads per block: 0 = default (128); 64, 128 or 256 */
+    uint32_t sharedStackDepth; /* entries per thread in shared memory: 0 = default (16), 1..32 */
+    uint32_t globalStackDepth; /* further entries per thread in global memory: 0 = default (64) */
+    float compactThreshold;    /* warp refill threshold (fraction of live lanes), 0 = default (0.5) */
+    uint32_t flags;            /* GRT_TRACE_FLAG_COUNT: accumulate grtTraceStatistics (slower) */
+    void* globalStack;         /* optional caller-owned device buffer for the global entries; NULL = the
+                                  context's own (then traces on one context must not overlap in time) */
+    size_t globalStackBytes;   /* size of globalStack; must be >= grtGetTraceGlobalStackSize */
+} grtTraceOptions;
+
+/* Bytes of global stack a trace with `options` (NULL = defaults) needs. */
+grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* options, size_t* sizeBytes);
+
+/* Closest hit of each ray against a scene (two levels) or a single geometry (pass
+ * exactly one of scene / geom). rays and hits are device pointers of rayCount
+ * entries. table may be NULL when no custom primitives are reached. options may be
+ * NULL (defaults). */
+grtError grtTraceClosest(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
+                         grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream);
+/* Any hit in [minT, maxT]: primID = GRT_INVALID_ID means unoccluded; otherwise the
+ * record describes one (not necessarily the closest) valid hit. */
+grtError grtTraceAnyHit(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
+                        grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream);
+
+/* ---------------------------------------------------------------- ray generation (Sec. 3.2, 4) */
+/* Pinhole camera (Sec. 3.2): lens at origin, film at distance 1 along
+ * normalize(up x right), spanning +-right and +-up. */
+typedef struct grtCamera {
+    float origin[3];
+    float right[3];
+    float up[3];
+} grtCamera;
+
+/* width*height primary rays through pixel centres, row-major from the top row:
+ * ray y*width + x; minT = 0, maxT = +inf. rays: device pointer. */
+grtError grtGenerateCameraRays(grtContext ctx, const grtCamera* camera, uint32_t width, uint32_t height,
+                               grtRay* rays, void* stream);
+
+/* Ambient-occlusion rays (Sec. 4): for pixel p with a primary hit, samplesPerPixel
+ * cosine-weighted directions about the world face normal turned toward the viewer
+ * (tangent = world v1 - v0), origin = hit point + 1e-4 * normal, t in [0, length].
+ * Random numbers: splitmix64 of stream `seed` at counter
+ * (p << 32) | (sample << 1) | dim, top 24 bits. A pixel without a hit gets empty rays
+ * (direction 0, minT 0, maxT -1). primaryRays/primaryHits: pixelCount entries;
+ * aoRays: pixelCount*samplesPerPixel entries; all device pointers. The scene must be
+ * the one the primary hits came from (triangle geometries only). */
+grtError grtGenerateAORays(grtContext ctx, grtScene scene, const grtRay* primaryRays, const grtHit* primaryHits,
+                           uint32_t pixelCount, uint32_t samplesPerPixel, uint64_t seed, float length,
+                           grtRay* aoRays, void* stream);
+
+/* Fused ambient occlusion: generates the same rays as grtGenerateAORays in
+ * registers and traces them as any-hit queries without storing them; writes
+ * ao[p] = occluded samples / samplesPerPixel (0 for pixels without a primary hit). */
+grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* primaryRays,
+                                  const grtHit* primaryHits, uint32_t pixelCount, uint32_t samplesPerPixel,
+                                  uint64_t seed, float length, float* ao, const grtTraceOptions* options,
+                                  void* stream);
+
+/* ---------------------------------------------------------------- introspection and building blocks */
+/* Device-side layout of a built geometry or scene, for tests and tools. */
+typedef struct grtBvhInfo {
+    const void* nodes;   /* nodeCount x 64-byte binary nodes (layout below) */
+    const void* leaves;  /* triangles: primCount x 48 bytes; AABB lists: primCount x uint32 primitive IDs;
+                            scenes: primCount x 128-byte instance records */
+    const void* parents; /* (2*primCount - 1) int32: parent of internal node k at [k], of leaf k at [primCount-1+k] */
+    uint32_t nodeCount;
+    uint32_t primCount;
+    uint32_t primType;   /* grtPrimitiveType; 2 for a scene */
+    uint32_t mortonBits; /* key width used by the last build */
+} grtBvhInfo;
+/*
+ * Node (64 bytes, 4 x float4): children c0 and c1 of internal node k
+ *   [0] = c0.lo.x, c0.hi.x, c1.lo.x, c1.hi.x
+ *   [1] = c0.lo.y, c0.hi.y, c1.lo.y, c1.hi.y
+ *   [2] = c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z
+ *   [3] = (uint32) c0 index, c1 index, 0, 0 ; bit 31 set = leaf, low bits = sorted position
+ * Node 0 is the root. Triangle leaf k (48 bytes): {v0.xyz, primID}, {v1.xyz, 0}, {v2.xyz, 0}.
+ * A single-primitive geometry has one node whose second child is empty.
+ */
+grtError grtGetBvhInfo(grtContext ctx, grtGeometry geom, grtScene scene, grtBvhInfo* info);
+
+/* Offsets (bytes) inside the build temporary buffer where, after a geometry build
+ * of `count` primitives, the sorted Morton keys (uint32 for 30-bit, uint64 for
+ * 63-bit) and the sorted primitive indices (uint32) are left. */
+grtError grtGetBuildTemporaryLayout(uint32_t count, uint32_t mortonBits, size_t* sortedKeysOffset,
+                                    size_t* sortedValuesOffset, size_t* centroidBoundsOffset);
+
+/* Number of kernels the library has launched in this process, all contexts. */
+grtError grtGetLaunchCount(uint64_t* count);
+
+/* Traversal work counted by traces launched with GRT_TRACE_FLAG_COUNT, summed since
+ * the last read (the read synchronises `stream` and resets the sums). */
+#define GRT_TRACE_FLAG_COUNT 1u
+typedef struct grtTraceStatistics {
+    uint64_t rays;            /* rays traced */
+    uint64_t nodesVisited;    /* 64-byte internal nodes fetched */
+    uint64_t trianglesTested; /* 48-byte triangle records tested */
+    uint64_t customTested;    /* custom primitives tested */
+    uint64_t instancesEntered;/* 128-byte instance records read on entry */
+    uint64_t fp64Tests;       /* primitive tests decided again in FP64 */
+} grtTraceStatistics;
+grtError grtGetTraceStatistics(grtContext ctx, void* stream, grtTraceStatistics* stats);
+
+/* Stable LSD radix sort of (key, value) pairs in place (device pointers). keyBits =
+ * 32 (uint32 keys) or 64 (uint64 keys); only the low `significantBits` bits are
+ * sorted (<= keyBits). temp: device buffer of grtSortTemporaryBufferSize bytes. */
+grtError grtSortTemporaryBufferSize(uint32_t count, uint32_t keyBits, size_t* sizeBytes);
+grtError grtSortPairs(grtContext ctx, void* keys, uint32_t* values, uint32_t count, uint32_t keyBits,
+                      uint32_t significantBits, void* temp, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRT_H_ */

@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_intersect_prim.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
             L.oracle_min_edge_margin.argtypes = [P, P]
             L.oracle_min_edge_margin.restype = ctypes.c_double
+            L.oracle_min_sphere_margin.argtypes = [P, P]
+            L.oracle_min_sphere_margin.restype = ctypes.c_double
             L.oracle_plane_edge_test.argtypes = [P, P, P, P, P]
             L.oracle_mt_test.argtypes = [P, P, P, P, P]
             L.oracle_instance_frames.argtypes = [P, ctypes.c_uint32, P, P]
@@ -265,6 +267,10 @@ class Scene:
     def min_edge_margin(self, ray) -> float:
         r = _c(ray, np.float32).reshape(8)
         return float(self._L.oracle_min_edge_margin(self._h, _p(r)))
+
+    def min_sphere_margin(self, ray) -> float:
+        r = _c(ray, np.float32).reshape(8)
+        return float(self._L.oracle_min_sphere_margin(self._h, _p(r)))
 
     def instance_frames(self, inst: int):
         f = np.empty(12)

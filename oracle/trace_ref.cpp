@@ -459,6 +459,31 @@ double oracle_min_edge_margin(void* s, const float* ray) {
     return best;
 }
 
+// Smallest relative gap |r^2 - p^2| / (|f|^2 + r^2) over every sphere, where p is the
+// distance from the sphere's centre to the ray's line and f the offset from the ray
+// origin to the centre (object space), for spheres whose closest approach lies at a t
+// in [minT, maxT]; +inf if none. A value near 0 marks a ray grazing a silhouette.
+double oracle_min_sphere_margin(void* s, const float* ray) {
+    Scene* S = (Scene*)s;
+    const RayD w = load_ray(ray);
+    double best = INFINITY;
+    for (const Instance& I : S->inst) {
+        const Geom& g = S->geoms[(size_t)I.geom];
+        if (g.kind != 1) continue;
+        RayD r{I.inv.point(w.o), I.inv.vector(w.d), w.tmin, w.tmax};
+        const double a = dot(r.d, r.d);
+        for (size_t p = 0; p < g.count(); ++p) {
+            const V3 f = g.centre[p] - r.o;
+            const double along = dot(f, r.d) / a;
+            if (!(along >= r.tmin && along <= r.tmax)) continue;
+            const V3 l = f - r.d * along;
+            const double r2 = g.radius[p] * g.radius[p];
+            best = std::min(best, std::fabs(r2 - dot(l, l)) / (dot(f, f) + r2));
+        }
+    }
+    return best;
+}
+
 // The paper's plane + edge-test formula on one triangle (cross-check of MT).
 int oracle_plane_edge_test(const float* ray, const float* tri, double* t, double* u, double* v) {
     RayD r = load_ray(ray);

@@ -1,0 +1,379 @@
+"""Python binding of libgrt (include/grt.h): GPU BVH build and ray traversal on sm_103a.
+
+Argument marshalling only. Every function below calls the C function of the same
+name in libgrt.so, which runs the work in hand-written CUDA kernels; device buffers
+are passed as addresses (torch tensors' data_ptr()) and streams as cudaStream_t
+handles. There is no CPU fallback: loading fails loudly when the library has not
+been built (see build.py) or when no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrt.so")
+
+GRT_API_VERSION = 1
+GRT_SUCCESS = 0
+GRT_ERROR_INVALID_PARAMETER = 1
+GRT_ERROR_OUT_OF_MEMORY = 2
+GRT_ERROR_INVALID_API_VERSION = 3
+GRT_ERROR_NOT_BUILT = 4
+GRT_ERROR_STACK_OVERFLOW = 5
+GRT_ERROR_STEP_LIMIT = 6
+GRT_ERROR_TIMEOUT = 7
+GRT_ERROR_CUDA = 8
+GRT_ERROR_INTERNAL = 9
+ERROR_NAMES = {0: "SUCCESS", 1: "INVALID_PARAMETER", 2: "OUT_OF_MEMORY", 3: "INVALID_API_VERSION", 4: "NOT_BUILT",
+               5: "STACK_OVERFLOW", 6: "STEP_LIMIT", 7: "TIMEOUT", 8: "CUDA", 9: "INTERNAL"}
+
+GRT_PRIMITIVE_TRIANGLE_MESH = 0
+GRT_PRIMITIVE_AABB_LIST = 1
+GRT_BUILD_OPERATION_BUILD = 0
+GRT_BUILD_OPERATION_UPDATE = 1
+GRT_INSTANCE_GEOMETRY = 0
+GRT_INTERSECT_NONE = 0
+GRT_INTERSECT_SPHERE = 1
+GRT_INVALID_ID = 0xFFFFFFFF
+GRT_LOG_NONE, GRT_LOG_ERROR, GRT_LOG_WARN, GRT_LOG_INFO = 0, 1, 2, 4
+
+RAY_BYTES = 32
+HIT_BYTES = 20
+
+
+class GrtError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where} failed: GRT_ERROR_{ERROR_NAMES.get(code, code)}")
+        self.code = code
+
+
+# ------------------------------------------------------------------ C structures
+class grtContextCreationInput(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32)]
+
+
+class grtTriangleMeshPrimitive(ctypes.Structure):
+    _fields_ = [("triangleCount", ctypes.c_uint32), ("triangleStride", ctypes.c_uint32),
+                ("triangleIndices", ctypes.c_void_p), ("vertexCount", ctypes.c_uint32),
+                ("vertexStride", ctypes.c_uint32), ("vertices", ctypes.c_void_p)]
+
+
+class grtAABBListPrimitive(ctypes.Structure):
+    _fields_ = [("aabbCount", ctypes.c_uint32), ("aabbStride", ctypes.c_uint32), ("aabbs", ctypes.c_void_p)]
+
+
+class grtGeometryBuildInput(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_uint32), ("geomType", ctypes.c_uint32),
+                ("triangleMesh", grtTriangleMeshPrimitive), ("aabbList", grtAABBListPrimitive)]
+
+
+class grtBuildOptions(ctypes.Structure):
+    _fields_ = [("buildFlags", ctypes.c_uint32), ("mortonBits", ctypes.c_uint32)]
+
+
+class grtSceneBuildInput(ctypes.Structure):
+    _fields_ = [("instanceCount", ctypes.c_uint32), ("frameCount", ctypes.c_uint32),
+                ("instances", ctypes.c_void_p), ("instanceFrames", ctypes.c_void_p)]
+
+
+class grtFuncDataSet(ctypes.Structure):
+    _fields_ = [("intersectFunc", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("intersectFuncData", ctypes.c_void_p)]
+
+
+class grtTraceOptions(ctypes.Structure):
+    _fields_ = [("rayType", ctypes.c_uint32), ("blockSize", ctypes.c_uint32),
+                ("sharedStackDepth", ctypes.c_uint32), ("globalStackDepth", ctypes.c_uint32),
+                ("compactThreshold", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("globalStack", ctypes.c_void_p), ("globalStackBytes", ctypes.c_size_t)]
+
+
+class grtCamera(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("right", ctypes.c_float * 3), ("up", ctypes.c_float * 3)]
+
+
+class grtBvhInfo(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("parents", ctypes.c_void_p),
+                ("nodeCount", ctypes.c_uint32), ("primCount", ctypes.c_uint32), ("primType", ctypes.c_uint32),
+                ("mortonBits", ctypes.c_uint32)]
+
+
+# ------------------------------------------------------------------ loading
+_lib = None
+
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_SIGS = {
+    "grtCreateContext": [_U32, ctypes.POINTER(grtContextCreationInput), ctypes.POINTER(_P)],
+    "grtDestroyContext": [_P],
+    "grtSetLogLevel": [_U32],
+    "grtGetLastDeviceError": [_P, _P, ctypes.POINTER(ctypes.c_int)],
+    "grtGetGeometryBuildTemporaryBufferSize": [_P, ctypes.POINTER(grtGeometryBuildInput),
+                                               ctypes.POINTER(grtBuildOptions), ctypes.POINTER(ctypes.c_size_t)],
+    "grtCreateGeometry": [_P, ctypes.POINTER(grtGeometryBuildInput), ctypes.POINTER(grtBuildOptions),
+                          ctypes.POINTER(_P)],
+    "grtBuildGeometry": [_P, _U32, ctypes.POINTER(grtGeometryBuildInput), ctypes.POINTER(grtBuildOptions), _P, _P,
+                         _P],
+    "grtDestroyGeometry": [_P, _P],
+    "grtGetSceneBuildTemporaryBufferSize": [_P, ctypes.POINTER(grtSceneBuildInput), ctypes.POINTER(grtBuildOptions),
+                                            ctypes.POINTER(ctypes.c_size_t)],
+    "grtCreateScene": [_P, ctypes.POINTER(grtSceneBuildInput), ctypes.POINTER(grtBuildOptions), ctypes.POINTER(_P)],
+    "grtBuildScene": [_P, _U32, ctypes.POINTER(grtSceneBuildInput), ctypes.POINTER(grtBuildOptions), _P, _P, _P],
+    "grtDestroyScene": [_P, _P],
+    "grtCreateFuncTable": [_P, _U32, _U32, ctypes.POINTER(_P)],
+    "grtSetFuncTable": [_P, _P, _U32, _U32, grtFuncDataSet],
+    "grtDestroyFuncTable": [_P, _P],
+    "grtGetTraceGlobalStackSize": [_P, ctypes.POINTER(grtTraceOptions), ctypes.POINTER(ctypes.c_size_t)],
+    "grtTraceClosest": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
+    "grtTraceAnyHit": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
+    "grtGenerateCameraRays": [_P, ctypes.POINTER(grtCamera), _U32, _U32, _P, _P],
+    "grtGenerateAORays": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P, _P],
+    "grtTraceAmbientOcclusion": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P,
+                                 ctypes.POINTER(grtTraceOptions), _P],
+    "grtGetBvhInfo": [_P, _P, _P, ctypes.POINTER(grtBvhInfo)],
+    "grtGetBuildTemporaryLayout": [_U32, _U32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                   ctypes.POINTER(ctypes.c_size_t)],
+    "grtGetLaunchCount": [ctypes.POINTER(ctypes.c_uint64)],
+    "grtGetTraceStatistics": [_P, _P, ctypes.c_void_p],
+    "grtSortTemporaryBufferSize": [_U32, _U32, ctypes.POINTER(ctypes.c_size_t)],
+    "grtSortPairs": [_P, _P, _P, _U32, _U32, _U32, _P, _P],
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """dlopen libgrt.so and declare every signature (does not touch the GPU)."""
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2603_00292_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    return L
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def check(code: int, where: str = "grt call"):
+    if code != GRT_SUCCESS:
+        raise GrtError(code, where)
+
+
+def _ptr(x) -> int | None:
+    """Device address of a tensor (or an int address, or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------ thin wrappers (C names)
+def grtCreateContext(device: int = 0) -> int:
+    inp = grtContextCreationInput(device)
+    out = _P()
+    check(lib().grtCreateContext(GRT_API_VERSION, ctypes.byref(inp), ctypes.byref(out)), "grtCreateContext")
+    return out.value
+
+
+def grtDestroyContext(ctx: int):
+    check(lib().grtDestroyContext(ctx), "grtDestroyContext")
+
+
+def grtSetLogLevel(levels: int):
+    check(lib().grtSetLogLevel(levels), "grtSetLogLevel")
+
+
+def grtGetLastDeviceError(ctx: int, stream=None) -> int:
+    err = ctypes.c_int()
+    check(lib().grtGetLastDeviceError(ctx, _stream(stream), ctypes.byref(err)), "grtGetLastDeviceError")
+    return err.value
+
+
+def triangle_mesh_input(indices, vertices, triangle_count=None, vertex_count=None, triangle_stride=12,
+                        vertex_stride=12, geom_type=0) -> grtGeometryBuildInput:
+    """Build input of an indexed mesh from device tensors (uint32 (T,3) / float32 (V,3))."""
+    tc = indices.shape[0] if triangle_count is None else triangle_count
+    vc = vertices.shape[0] if vertex_count is None else vertex_count
+    m = grtTriangleMeshPrimitive(tc, triangle_stride, _ptr(indices), vc, vertex_stride, _ptr(vertices))
+    return grtGeometryBuildInput(GRT_PRIMITIVE_TRIANGLE_MESH, geom_type, m, grtAABBListPrimitive())
+
+
+def aabb_list_input(boxes, count=None, stride=24, geom_type=0) -> grtGeometryBuildInput:
+    """Build input of an AABB list from a device tensor float32 (N,6)."""
+    n = boxes.shape[0] if count is None else count
+    return grtGeometryBuildInput(GRT_PRIMITIVE_AABB_LIST, geom_type, grtTriangleMeshPrimitive(),
+                                 grtAABBListPrimitive(n, stride, _ptr(boxes)))
+
+
+def build_options(morton_bits: int = 0, flags: int = 1) -> grtBuildOptions:
+    return grtBuildOptions(flags, morton_bits)
+
+
+def grtGetGeometryBuildTemporaryBufferSize(ctx, inp, opts) -> int:
+    sz = ctypes.c_size_t()
+    check(lib().grtGetGeometryBuildTemporaryBufferSize(ctx, ctypes.byref(inp), ctypes.byref(opts), ctypes.byref(sz)),
+          "grtGetGeometryBuildTemporaryBufferSize")
+    return sz.value
+
+
+def grtCreateGeometry(ctx, inp, opts) -> int:
+    out = _P()
+    check(lib().grtCreateGeometry(ctx, ctypes.byref(inp), ctypes.byref(opts), ctypes.byref(out)), "grtCreateGeometry")
+    return out.value
+
+
+def grtBuildGeometry(ctx, op, inp, opts, temp, stream, geom):
+    check(lib().grtBuildGeometry(ctx, op, ctypes.byref(inp), ctypes.byref(opts), _ptr(temp), _stream(stream), geom),
+          "grtBuildGeometry")
+
+
+def grtDestroyGeometry(ctx, geom):
+    check(lib().grtDestroyGeometry(ctx, geom), "grtDestroyGeometry")
+
+
+def scene_input(instances, frames, count=None) -> grtSceneBuildInput:
+    """instances: device tensor of 16-byte grtInstance records; frames: float32 (I,10)."""
+    n = frames.shape[0] if count is None else count
+    return grtSceneBuildInput(n, n, _ptr(instances), _ptr(frames))
+
+
+def grtGetSceneBuildTemporaryBufferSize(ctx, inp, opts) -> int:
+    sz = ctypes.c_size_t()
+    check(lib().grtGetSceneBuildTemporaryBufferSize(ctx, ctypes.byref(inp), ctypes.byref(opts), ctypes.byref(sz)),
+          "grtGetSceneBuildTemporaryBufferSize")
+    return sz.value
+
+
+def grtCreateScene(ctx, inp, opts) -> int:
+    out = _P()
+    check(lib().grtCreateScene(ctx, ctypes.byref(inp), ctypes.byref(opts), ctypes.byref(out)), "grtCreateScene")
+    return out.value
+
+
+def grtBuildScene(ctx, op, inp, opts, temp, stream, scene):
+    check(lib().grtBuildScene(ctx, op, ctypes.byref(inp), ctypes.byref(opts), _ptr(temp), _stream(stream), scene),
+          "grtBuildScene")
+
+
+def grtDestroyScene(ctx, scene):
+    check(lib().grtDestroyScene(ctx, scene), "grtDestroyScene")
+
+
+def grtCreateFuncTable(ctx, num_geom_types: int, num_ray_types: int) -> int:
+    out = _P()
+    check(lib().grtCreateFuncTable(ctx, num_geom_types, num_ray_types, ctypes.byref(out)), "grtCreateFuncTable")
+    return out.value
+
+
+def grtSetFuncTable(ctx, table, geom_type: int, ray_type: int, func: int, data):
+    check(lib().grtSetFuncTable(ctx, table, geom_type, ray_type, grtFuncDataSet(func, 0, _ptr(data))),
+          "grtSetFuncTable")
+
+
+def grtDestroyFuncTable(ctx, table):
+    check(lib().grtDestroyFuncTable(ctx, table), "grtDestroyFuncTable")
+
+
+def trace_options(ray_type=0, block_size=0, shared_depth=0, global_depth=0, compact=0.0, global_stack=None,
+                  global_stack_bytes=0, flags=0) -> grtTraceOptions:
+    return grtTraceOptions(ray_type, block_size, shared_depth, global_depth, compact, flags, _ptr(global_stack),
+                           global_stack_bytes)
+
+
+def grtGetTraceGlobalStackSize(ctx, opts=None) -> int:
+    sz = ctypes.c_size_t()
+    check(lib().grtGetTraceGlobalStackSize(ctx, ctypes.byref(opts) if opts else None, ctypes.byref(sz)),
+          "grtGetTraceGlobalStackSize")
+    return sz.value
+
+
+def grtTraceClosest(ctx, scene, geom, rays, count, hits, table=None, opts=None, stream=None):
+    check(lib().grtTraceClosest(ctx, scene, geom, _ptr(rays), count, _ptr(hits), table,
+                                ctypes.byref(opts) if opts else None, _stream(stream)), "grtTraceClosest")
+
+
+def grtTraceAnyHit(ctx, scene, geom, rays, count, hits, table=None, opts=None, stream=None):
+    check(lib().grtTraceAnyHit(ctx, scene, geom, _ptr(rays), count, _ptr(hits), table,
+                               ctypes.byref(opts) if opts else None, _stream(stream)), "grtTraceAnyHit")
+
+
+def camera(origin, right, up) -> grtCamera:
+    return grtCamera((ctypes.c_float * 3)(*origin), (ctypes.c_float * 3)(*right), (ctypes.c_float * 3)(*up))
+
+
+def grtGenerateCameraRays(ctx, cam: grtCamera, width: int, height: int, rays, stream=None):
+    check(lib().grtGenerateCameraRays(ctx, ctypes.byref(cam), width, height, _ptr(rays), _stream(stream)),
+          "grtGenerateCameraRays")
+
+
+def grtGenerateAORays(ctx, scene, primary_rays, primary_hits, pixels, spp, seed, length, ao_rays, stream=None):
+    check(lib().grtGenerateAORays(ctx, scene, _ptr(primary_rays), _ptr(primary_hits), pixels, spp, seed, length,
+                                  _ptr(ao_rays), _stream(stream)), "grtGenerateAORays")
+
+
+def grtTraceAmbientOcclusion(ctx, scene, primary_rays, primary_hits, pixels, spp, seed, length, ao, opts=None,
+                             stream=None):
+    check(lib().grtTraceAmbientOcclusion(ctx, scene, _ptr(primary_rays), _ptr(primary_hits), pixels, spp, seed, length,
+                                         _ptr(ao), ctypes.byref(opts) if opts else None, _stream(stream)),
+          "grtTraceAmbientOcclusion")
+
+
+def grtGetBvhInfo(ctx, geom=None, scene=None) -> grtBvhInfo:
+    info = grtBvhInfo()
+    check(lib().grtGetBvhInfo(ctx, geom, scene, ctypes.byref(info)), "grtGetBvhInfo")
+    return info
+
+
+def grtGetBuildTemporaryLayout(count: int, morton_bits: int):
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    check(lib().grtGetBuildTemporaryLayout(count, morton_bits, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+          "grtGetBuildTemporaryLayout")
+    return a.value, b.value, c.value
+
+
+GRT_TRACE_FLAG_COUNT = 1
+
+
+class grtTraceStatistics(ctypes.Structure):
+    _fields_ = [("rays", ctypes.c_uint64), ("nodesVisited", ctypes.c_uint64), ("trianglesTested", ctypes.c_uint64),
+                ("customTested", ctypes.c_uint64), ("instancesEntered", ctypes.c_uint64),
+                ("fp64Tests", ctypes.c_uint64)]
+
+
+def grtGetLaunchCount() -> int:
+    v = ctypes.c_uint64()
+    check(lib().grtGetLaunchCount(ctypes.byref(v)), "grtGetLaunchCount")
+    return v.value
+
+
+def grtGetTraceStatistics(ctx, stream=None) -> dict:
+    st = grtTraceStatistics()
+    check(lib().grtGetTraceStatistics(ctx, _stream(stream), ctypes.byref(st)), "grtGetTraceStatistics")
+    return {name: getattr(st, name) for name, _ in grtTraceStatistics._fields_}
+
+
+def grtSortTemporaryBufferSize(count: int, key_bits: int) -> int:
+    sz = ctypes.c_size_t()
+    check(lib().grtSortTemporaryBufferSize(count, key_bits, ctypes.byref(sz)), "grtSortTemporaryBufferSize")
+    return sz.value
+
+
+def grtSortPairs(ctx, keys, values, count, key_bits, significant_bits, temp, stream=None):
+    check(lib().grtSortPairs(ctx, _ptr(keys), _ptr(values), count, key_bits, significant_bits, _ptr(temp),
+                             _stream(stream)), "grtSortPairs")

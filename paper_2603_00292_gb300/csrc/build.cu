@@ -1,0 +1,934 @@
+// LBVH construction on the GPU: primitive boxes and centroid bounds, Morton codes,
+// a stable LSD radix sort, Karras hierarchy emission and a bottom-up fit with
+// atomic visit counters, plus the top-level (instance) build.
+//
+// Method: the paper describes BVH construction, its surface-area cost and refitting
+// from child boxes (Sec. 6.2) and the geometry / scene build API (Sec. 7.2-7.3). The
+// linear build follows Karras, "Maximizing Parallelism in the Construction of BVHs,
+// Octrees, and k-d Trees" (HPG 2012): node i of the n-1 internal nodes finds its
+// range and split from the sorted codes alone, and leaves walk up to the root,
+// the second child to arrive at a node computing its box.
+#include <algorithm>
+
+#include "grt_internal.cuh"
+
+namespace grt {
+
+// ======================================================================= radix sort
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadix = 256;
+constexpr int kMaxSortBlocks = 1024;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+
+size_t sortScratchBytes(uint32_t) { return (size_t)kRadix * kMaxSortBlocks * sizeof(uint32_t); }
+
+struct SortGrid {
+    unsigned tiles, tilesPerBlock, blocks;
+};
+
+static SortGrid sortGrid(uint32_t n, int sms) {
+    SortGrid g;
+    g.tiles = std::max(1u, ceilDiv(n, kSortTile));
+    unsigned want = std::min<unsigned>(g.tiles, std::min<unsigned>(kMaxSortBlocks, (unsigned)std::max(1, sms) * 2));
+    g.tilesPerBlock = ceilDiv(g.tiles, want);
+    g.blocks = ceilDiv(g.tiles, g.tilesPerBlock);
+    return g;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) sortUpsweep(const K* __restrict__ keys, uint32_t n, int shift,
+                                                            uint32_t tilesPerBlock, uint32_t* __restrict__ counts,
+                                                            uint32_t blocks) {
+    __shared__ uint32_t h[kSortWarps][kRadix];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int d = tid; d < kSortWarps * kRadix; d += kSortThreads) (&h[0][0])[d] = 0;
+    __syncthreads();
+    const size_t begin = (size_t)blockIdx.x * tilesPerBlock * kSortTile;
+    const size_t end = min((size_t)n, begin + (size_t)tilesPerBlock * kSortTile);
+    for (size_t i = begin + tid; i < end; i += kSortThreads) {
+        const uint32_t d = (uint32_t)(keys[i] >> shift) & (kRadix - 1);
+        atomicAdd(&h[warp][d], 1u);
+    }
+    __syncthreads();
+    for (int d = tid; d < kRadix; d += kSortThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) s += h[w][d];
+        counts[(size_t)d * blocks + blockIdx.x] = s;
+    }
+}
+
+// Exclusive prefix sum in place over `total` counters (one block).
+__global__ void __launch_bounds__(kScanThreads) sortScan(uint32_t* __restrict__ counts, uint32_t total) {
+    __shared__ uint32_t warpSums[kScanThreads / 32];
+    __shared__ uint32_t carryS;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carryS = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < total; base += kScanThreads * kScanItems) {
+        uint32_t v[kScanItems];
+        uint32_t sum = 0;
+        const uint32_t my = base + (uint32_t)tid * kScanItems;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            v[i] = (my + i < total) ? counts[my + i] : 0u;
+            sum += v[i];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warpSums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = warpSums[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            warpSums[lane] = wi - w;  // exclusive
+        }
+        __syncthreads();
+        uint32_t run = carryS + warpSums[warp] + (incl - sum);
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            if (my + i < total) counts[my + i] = run;
+            run += v[i];
+        }
+        __syncthreads();
+        if (tid == kScanThreads - 1) carryS = run;
+        __syncthreads();
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) sortDownsweep(const K* __restrict__ keysIn,
+                                                              const uint32_t* __restrict__ valsIn,
+                                                              K* __restrict__ keysOut, uint32_t* __restrict__ valsOut,
+                                                              uint32_t n, int shift, uint32_t tilesPerBlock,
+                                                              uint32_t tiles, const uint32_t* __restrict__ offsets,
+                                                              uint32_t blocks) {
+    __shared__ uint32_t warpHist[kSortWarps][kRadix];
+    __shared__ uint32_t digitBase[kRadix];
+    __shared__ uint32_t tileTotal[kRadix];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t ltMask = (1u << lane) - 1u;
+    for (int d = tid; d < kRadix; d += kSortThreads) {
+        digitBase[d] = offsets[(size_t)d * blocks + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) warpHist[w][d] = 0;
+    }
+    __syncthreads();
+    const unsigned t0 = blockIdx.x * tilesPerBlock;
+    const unsigned t1 = min(tiles, t0 + tilesPerBlock);
+    for (unsigned tile = t0; tile < t1; ++tile) {
+        const size_t base = (size_t)tile * kSortTile + (size_t)warp * 32 * kSortItems;
+        K k[kSortItems];
+        uint32_t v[kSortItems], dg[kSortItems], rank[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const size_t idx = base + (size_t)i * 32 + lane;
+            const bool ok = idx < n;
+            k[i] = ok ? keysIn[idx] : (K)0;
+            v[i] = ok ? valsIn[idx] : 0u;
+            dg[i] = ok ? ((uint32_t)(k[i] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+        }
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg[i]);
+            const int leader = __ffs(peers) - 1;
+            const bool ok = dg[i] < kRadix;
+            const uint32_t b = ok ? warpHist[warp][dg[i]] : 0u;
+            __syncwarp();
+            if (ok && lane == leader) warpHist[warp][dg[i]] = b + __popc(peers);
+            __syncwarp();
+            rank[i] = b + __popc(peers & ltMask);
+        }
+        __syncthreads();
+        for (int d = tid; d < kRadix; d += kSortThreads) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t t = warpHist[w][d];
+                warpHist[w][d] = run;
+                run += t;
+            }
+            tileTotal[d] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            if (dg[i] < kRadix) {
+                const uint32_t pos = digitBase[dg[i]] + warpHist[warp][dg[i]] + rank[i];
+                keysOut[pos] = k[i];
+                valsOut[pos] = v[i];
+            }
+        }
+        __syncthreads();
+        for (int d = tid; d < kRadix; d += kSortThreads) {
+            digitBase[d] += tileTotal[d];
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) warpHist[w][d] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename K>
+static grtError radixSortT(Context* ctx, K* keys0, K* keys1, uint32_t* vals0, uint32_t* vals1, uint32_t n,
+                           int significantBits, uint32_t* hist, cudaStream_t s, int* finalBuf) {
+    const SortGrid g = sortGrid(n, smCount(ctx));
+    const int passes = (significantBits + 7) / 8;
+    K* kin = keys0;
+    K* kout = keys1;
+    uint32_t* vin = vals0;
+    uint32_t* vout = vals1;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        sortUpsweep<K><<<g.blocks, kSortThreads, 0, s>>>(kin, n, shift, g.tilesPerBlock, hist, g.blocks);
+        sortScan<<<1, kScanThreads, 0, s>>>(hist, kRadix * g.blocks);
+        sortDownsweep<K><<<g.blocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, g.tilesPerBlock, g.tiles,
+                                                            hist, g.blocks);
+        GRT_LAUNCH_CHECK();
+        noteLaunches(3);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    *finalBuf = passes & 1;
+    return GRT_SUCCESS;
+}
+
+grtError radixSort(Context* ctx, void* keys0, void* keys1, uint32_t* vals0, uint32_t* vals1, uint32_t n, int keyBytes,
+                   int significantBits, uint32_t* hist, cudaStream_t s, int* finalBuf) {
+    if (n == 0) {
+        *finalBuf = 0;
+        return GRT_SUCCESS;
+    }
+    if (keyBytes == 4)
+        return radixSortT<uint32_t>(ctx, (uint32_t*)keys0, (uint32_t*)keys1, vals0, vals1, n, significantBits, hist, s,
+                                    finalBuf);
+    return radixSortT<unsigned long long>(ctx, (unsigned long long*)keys0, (unsigned long long*)keys1, vals0, vals1, n,
+                                          significantBits, hist, s, finalBuf);
+}
+
+// ======================================================================= primitive boxes (A1) and bounds (A2)
+struct Box3 {
+    float3 lo, hi;
+};
+
+__device__ __forceinline__ float3 load3(const char* base, size_t byteOffset) {
+    const float* p = reinterpret_cast<const float*>(base + byteOffset);
+    return make_float3(p[0], p[1], p[2]);
+}
+
+__device__ __forceinline__ Box3 triangleBox(float3 a, float3 b, float3 c) {
+    Box3 r;
+    r.lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y), fminf(fminf(a.z, b.z), c.z));
+    r.hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y), fmaxf(fmaxf(a.z, b.z), c.z));
+    return r;
+}
+
+__device__ __forceinline__ float3 boxCentroid(const Box3& b) {
+    return make_float3(__fmul_rn(0.5f, __fadd_rn(b.lo.x, b.hi.x)), __fmul_rn(0.5f, __fadd_rn(b.lo.y, b.hi.y)),
+                       __fmul_rn(0.5f, __fadd_rn(b.lo.z, b.hi.z)));
+}
+
+struct PrimSource {
+    uint32_t kind;  // 0 triangles, 1 boxes at stride
+    uint32_t count;
+    const char* idx;
+    uint32_t idxStride;
+    const char* verts;
+    uint32_t vertStride;
+    const char* boxes;
+    uint32_t boxStride;
+};
+
+__device__ __forceinline__ Box3 primBox(const PrimSource& S, uint32_t i, float3* v) {
+    if (S.kind == 0) {
+        const uint32_t* t = reinterpret_cast<const uint32_t*>(S.idx + (size_t)i * S.idxStride);
+        v[0] = load3(S.verts, (size_t)t[0] * S.vertStride);
+        v[1] = load3(S.verts, (size_t)t[1] * S.vertStride);
+        v[2] = load3(S.verts, (size_t)t[2] * S.vertStride);
+        return triangleBox(v[0], v[1], v[2]);
+    }
+    const float* b = reinterpret_cast<const float*>(S.boxes + (size_t)i * S.boxStride);
+    Box3 r;
+    r.lo = make_float3(b[0], b[1], b[2]);
+    r.hi = make_float3(b[3], b[4], b[5]);
+    return r;
+}
+
+// Block-wide min/max reduction of centroids folded into 6 ordered-int atomics.
+__device__ __forceinline__ void reduceBounds(float3 c, bool valid, uint32_t* bounds) {
+    float mn[3] = {valid ? c.x : INFINITY, valid ? c.y : INFINITY, valid ? c.z : INFINITY};
+    float mx[3] = {valid ? c.x : -INFINITY, valid ? c.y : -INFINITY, valid ? c.z : -INFINITY};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    __shared__ float sm[32][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) sm[warp][a] = mn[a], sm[warp][3 + a] = mx[a];
+    __syncthreads();
+    if (warp == 0) {
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = lane < nw ? sm[lane][a] : INFINITY;
+            mx[a] = lane < nw ? sm[lane][3 + a] : -INFINITY;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+                mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+            }
+        if (lane == 0)
+            for (int a = 0; a < 3; ++a) {
+                atomicMin(&bounds[a], floatToOrdered(mn[a]));
+                atomicMax(&bounds[3 + a], floatToOrdered(mx[a]));
+            }
+    }
+}
+
+__global__ void __launch_bounds__(256) primCentroidKernel(PrimSource S, float4* __restrict__ centroids,
+                                                          uint32_t* __restrict__ bounds) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < S.count;
+    float3 c = make_float3(0.f, 0.f, 0.f);
+    if (valid) {
+        float3 v[3];
+        c = boxCentroid(primBox(S, i, v));
+        centroids[i] = make_float4(c.x, c.y, c.z, 0.f);
+    }
+    reduceBounds(c, valid, bounds);
+}
+
+// ======================================================================= Morton codes (A3)
+__device__ __forceinline__ uint32_t expand10(uint32_t x) {
+    x &= 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long expand21(uint32_t v) {
+    unsigned long long x = v & 0x1FFFFFull;
+    x = (x | (x << 32)) & 0x001F00000000FFFFull;
+    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// q = clamp(floor(((c - lo) / (hi - lo)) * 2^bits), 0, 2^bits - 1), each step rounded
+// to nearest in float32; a zero extent gives 0.
+template <int BITS>
+__device__ __forceinline__ uint32_t quantise(float c, float lo, float hi) {
+    const float ext = __fsub_rn(hi, lo);
+    const float x = (ext == 0.0f) ? 0.0f : __fdiv_rn(__fsub_rn(c, lo), ext);
+    const float s = __fmul_rn(x, (float)(1u << BITS));
+    const float f = floorf(s);
+    const float top = (float)((1u << BITS) - 1u);
+    if (!(f >= 0.0f)) return 0u;
+    return (uint32_t)(f > top ? top : f);
+}
+
+template <typename K, int BITS>
+__global__ void __launch_bounds__(256) mortonKernel(const float4* __restrict__ centroids, uint32_t n,
+                                                    const uint32_t* __restrict__ bounds, K* __restrict__ keys,
+                                                    uint32_t* __restrict__ vals) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 c = centroids[i];
+    const float lx = orderedToFloat(bounds[0]), ly = orderedToFloat(bounds[1]), lz = orderedToFloat(bounds[2]);
+    const float hx = orderedToFloat(bounds[3]), hy = orderedToFloat(bounds[4]), hz = orderedToFloat(bounds[5]);
+    const uint32_t qx = quantise<BITS>(c.x, lx, hx), qy = quantise<BITS>(c.y, ly, hy), qz = quantise<BITS>(c.z, lz, hz);
+    K code;
+    if constexpr (BITS == 10)
+        code = (K)((expand10(qx) << 2) | (expand10(qy) << 1) | expand10(qz));
+    else
+        code = (K)((expand21(qx) << 2) | (expand21(qy) << 1) | expand21(qz));
+    keys[i] = code;
+    vals[i] = i;
+}
+
+// ======================================================================= Karras emission (A5)
+template <typename K>
+__device__ __forceinline__ int commonPrefix(const K* __restrict__ keys, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    const K a = keys[i], b = keys[j];
+    constexpr int KB = (int)sizeof(K) * 8;
+    if (a != b) {
+        if (sizeof(K) == 4) return __clz((uint32_t)(a ^ b));
+        return __clzll((long long)(a ^ b));
+    }
+    return KB + __clz((uint32_t)i ^ (uint32_t)j);
+}
+
+// One thread per internal node i in [0, n-2]: direction, range end, split; writes
+// the node's child indices (word 3 of the node) and each child's parent entry
+// (parent << 1 | side).
+template <typename K>
+__global__ void __launch_bounds__(256) karrasKernel(const K* __restrict__ keys, int n, float4* __restrict__ nodes,
+                                                    uint32_t* __restrict__ parents) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (commonPrefix(keys, n, i, i + 1) - commonPrefix(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = commonPrefix(keys, n, i, i - d);
+    int lmax = 2;
+    while (commonPrefix(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (commonPrefix(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = commonPrefix(keys, n, i, j);
+    int s = 0;
+    int t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (commonPrefix(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int gamma = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
+    const uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
+    nodes[4 * (size_t)i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.f, 0.f);
+    const uint32_t leafBase = (uint32_t)n - 1u;
+    parents[(left & kLeafBit) ? leafBase + (left & ~kLeafBit) : left] = ((uint32_t)i << 1) | 0u;
+    parents[(right & kLeafBit) ? leafBase + (right & ~kLeafBit) : right] = ((uint32_t)i << 1) | 1u;
+    if (i == 0) parents[0] = kInvalid;
+}
+
+// ======================================================================= bottom-up fit (A6) + leaf layout (A7)
+struct FitParams {
+    PrimSource src;
+    uint32_t n;
+    const uint32_t* sortedPrims;  // nullptr for a refit (IDs read back from the leaves)
+    float4* nodes;
+    void* leaves;
+    uint32_t* primToLeaf;
+    const uint32_t* parents;
+    uint32_t* flags;
+    BvhHeader* header;
+    const float4* instBoxes;              // scene: world boxes (2 float4 per instance)
+    const InstanceRecord* instRecords;    // scene: unsorted records
+};
+
+__device__ __forceinline__ void writeChildBox(float4* nodes, uint32_t p, uint32_t side, const Box3& b) {
+    float2* n2 = reinterpret_cast<float2*>(nodes + 4 * (size_t)p);
+    n2[0 * 2 + side] = make_float2(b.lo.x, b.hi.x);
+    n2[1 * 2 + side] = make_float2(b.lo.y, b.hi.y);
+    n2[2 * 2 + side] = make_float2(b.lo.z, b.hi.z);
+}
+
+template <int KIND>  // 0 triangles, 1 AABB list, 2 instances
+__global__ void __launch_bounds__(256) fitKernel(FitParams P) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.n) return;
+    Box3 b;
+    if (KIND == 0) {
+        float4* rec = reinterpret_cast<float4*>(P.leaves) + 3 * (size_t)k;
+        const uint32_t prim = P.sortedPrims ? P.sortedPrims[k] : __float_as_uint(rec[0].w);
+        float3 v[3];
+        b = primBox(P.src, prim, v);
+        rec[0] = make_float4(v[0].x, v[0].y, v[0].z, __uint_as_float(prim));
+        // w slots: L1 norms of the edges v1-v0 and v2-v0 (scale of the traversal's error bounds)
+        const float e1 = fabsf(v[1].x - v[0].x) + fabsf(v[1].y - v[0].y) + fabsf(v[1].z - v[0].z);
+        const float e2 = fabsf(v[2].x - v[0].x) + fabsf(v[2].y - v[0].y) + fabsf(v[2].z - v[0].z);
+        rec[1] = make_float4(v[1].x, v[1].y, v[1].z, e1);
+        rec[2] = make_float4(v[2].x, v[2].y, v[2].z, e2);
+        P.primToLeaf[prim] = k;
+    } else if (KIND == 1) {
+        uint32_t* ids = reinterpret_cast<uint32_t*>(P.leaves);
+        const uint32_t prim = P.sortedPrims ? P.sortedPrims[k] : ids[k];
+        float3 v[3];
+        b = primBox(P.src, prim, v);
+        ids[k] = prim;
+    } else {
+        const uint32_t prim = P.sortedPrims[k];
+        const float4 lo = P.instBoxes[2 * (size_t)prim], hi = P.instBoxes[2 * (size_t)prim + 1];
+        b.lo = make_float3(lo.x, lo.y, lo.z);
+        b.hi = make_float3(hi.x, hi.y, hi.z);
+        reinterpret_cast<InstanceRecord*>(P.leaves)[k] = P.instRecords[prim];
+        P.primToLeaf[prim] = k;
+    }
+    if (P.n == 1) {
+        // a single primitive: node 0 holds it as both children
+        writeChildBox(P.nodes, 0, 0, b);
+        writeChildBox(P.nodes, 0, 1, b);
+        P.nodes[3] = make_float4(__uint_as_float(kLeafBit), __uint_as_float(kLeafBit), 0.f, 0.f);
+        P.header->rootLo[0] = b.lo.x, P.header->rootLo[1] = b.lo.y, P.header->rootLo[2] = b.lo.z;
+        P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
+        return;
+    }
+    uint32_t pe = P.parents[P.n - 1 + k];
+    for (;;) {
+        const uint32_t p = pe >> 1, side = pe & 1u;
+        writeChildBox(P.nodes, p, side, b);
+        __threadfence();
+        const uint32_t prev = atomicAdd(&P.flags[p], 1u);
+        if (prev == 0) return;  // the sibling is still on its way up
+        __threadfence();
+        const float4 x = __ldcg(&P.nodes[4 * (size_t)p + 0]);
+        const float4 y = __ldcg(&P.nodes[4 * (size_t)p + 1]);
+        const float4 z = __ldcg(&P.nodes[4 * (size_t)p + 2]);
+        b.lo = make_float3(fminf(x.x, x.z), fminf(y.x, y.z), fminf(z.x, z.z));
+        b.hi = make_float3(fmaxf(x.y, x.w), fmaxf(y.y, y.w), fmaxf(z.y, z.w));
+        if (p == 0) {
+            P.header->rootLo[0] = b.lo.x, P.header->rootLo[1] = b.lo.y, P.header->rootLo[2] = b.lo.z;
+            P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
+            return;
+        }
+        pe = __ldcg(&P.parents[p]);
+    }
+}
+
+// ======================================================================= instances (A8)
+struct InstanceInput {
+    const grtInstance* instances;
+    const grtFrameSRT* frames;
+    uint32_t count;
+    float4* boxes;             // 2 float4 per instance: world lo, hi
+    InstanceRecord* records;   // unsorted
+    InstanceFrames64* inv64;   // per instance ID
+    float4* fwd32;             // 3 rows per instance ID
+    float4* centroids;
+    uint32_t* bounds;
+};
+
+// Per instance: frame M = T R S and its inverse S^-1 R^T (x - T) in FP64 (rounded to
+// float32), the world box of the bottom level's root box (8 corners through M,
+// rounded outward), and the centroid of that box.
+__global__ void __launch_bounds__(128) instanceSetupKernel(InstanceInput I) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < I.count;
+    float3 c = make_float3(0.f, 0.f, 0.f);
+    if (valid) {
+        const grtInstance in = I.instances[i];
+        const grtFrameSRT f = I.frames[i];
+        const BvhHeader* g = reinterpret_cast<const BvhHeader*>(in.geometry);
+        double qx = f.rotation[0], qy = f.rotation[1], qz = f.rotation[2], qw = f.rotation[3];
+        const double qn = sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
+        qx /= qn, qy /= qn, qz /= qn, qw /= qn;
+        const double R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qz * qw), 2 * (qx * qz + qy * qw)},
+                                {2 * (qx * qy + qz * qw), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qx * qw)},
+                                {2 * (qx * qz - qy * qw), 2 * (qy * qz + qx * qw), 1 - 2 * (qx * qx + qy * qy)}};
+        const double S[3] = {f.scale[0], f.scale[1], f.scale[2]};
+        const double T[3] = {f.translation[0], f.translation[1], f.translation[2]};
+        double F[3][4], G[3][4];
+        for (int r = 0; r < 3; ++r) {
+            for (int q = 0; q < 3; ++q) {
+                F[r][q] = R[r][q] * S[q];
+                G[r][q] = R[q][r] / S[r];
+            }
+            F[r][3] = T[r];
+            G[r][3] = -(G[r][0] * T[0] + G[r][1] * T[1] + G[r][2] * T[2]);
+        }
+        InstanceRecord rec;
+        for (int r = 0; r < 3; ++r) {
+            rec.inv[r] = make_float4(__double2float_rn(G[r][0]), __double2float_rn(G[r][1]),
+                                     __double2float_rn(G[r][2]), __double2float_rn(G[r][3]));
+            I.fwd32[3 * (size_t)i + r] = make_float4(__double2float_rn(F[r][0]), __double2float_rn(F[r][1]),
+                                                     __double2float_rn(F[r][2]), __double2float_rn(F[r][3]));
+            for (int q = 0; q < 4; ++q) I.inv64[i].inv[r][q] = G[r][q];
+        }
+        rec.nodes = g->nodes;
+        rec.leaves = g->leaves;
+        rec.instanceID = i;
+        rec.typeBits = (g->geomType & 0xFFFFFFu) | (g->primType << 24) | (g->primCount == 0 ? kInstEmpty : 0u);
+        rec.geometry = g;
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        if (g->primCount > 0) {
+            for (int cnr = 0; cnr < 8; ++cnr) {
+                const double p[3] = {(cnr & 1) ? g->rootHi[0] : g->rootLo[0], (cnr & 2) ? g->rootHi[1] : g->rootLo[1],
+                                     (cnr & 4) ? g->rootHi[2] : g->rootLo[2]};
+                for (int r = 0; r < 3; ++r) {
+                    const double w = F[r][0] * p[0] + F[r][1] * p[1] + F[r][2] * p[2] + F[r][3];
+                    lo[r] = fmin(lo[r], w);
+                    hi[r] = fmax(hi[r], w);
+                }
+            }
+        } else {
+            for (int r = 0; r < 3; ++r) lo[r] = hi[r] = T[r];  // empty: a point box, skipped by traversal
+        }
+        Box3 b;
+        b.lo = make_float3(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]));
+        b.hi = make_float3(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]));
+        I.boxes[2 * (size_t)i] = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f);
+        I.boxes[2 * (size_t)i + 1] = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
+        rec.worldLo = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f);
+        rec.worldHi = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
+        rec.reserved = make_float4(0.f, 0.f, 0.f, 0.f);
+        I.records[i] = rec;
+        c = boxCentroid(b);
+        I.centroids[i] = make_float4(c.x, c.y, c.z, 0.f);
+    }
+    reduceBounds(c, valid, I.bounds);
+}
+
+// ======================================================================= host drivers
+static grtError validateGeometryInput(const grtGeometryBuildInput* in, uint32_t* count) {
+    if (!in) return GRT_ERROR_INVALID_PARAMETER;
+    if (in->type == GRT_PRIMITIVE_TRIANGLE_MESH) {
+        const grtTriangleMeshPrimitive& m = in->triangleMesh;
+        if (m.triangleCount && (!m.triangleIndices || !m.vertices || m.triangleStride < 12 || m.vertexStride < 12 ||
+                                (m.triangleStride & 3) || (m.vertexStride & 3)))
+            return GRT_ERROR_INVALID_PARAMETER;
+        if (m.triangleCount >= 0x7FFFFFFFu) return GRT_ERROR_INVALID_PARAMETER;
+        *count = m.triangleCount;
+        return GRT_SUCCESS;
+    }
+    if (in->type == GRT_PRIMITIVE_AABB_LIST) {
+        const grtAABBListPrimitive& a = in->aabbList;
+        if (a.aabbCount && (!a.aabbs || a.aabbStride < 24 || (a.aabbStride & 3))) return GRT_ERROR_INVALID_PARAMETER;
+        if (a.aabbCount >= 0x7FFFFFFFu) return GRT_ERROR_INVALID_PARAMETER;
+        *count = a.aabbCount;
+        return GRT_SUCCESS;
+    }
+    return GRT_ERROR_INVALID_PARAMETER;
+}
+
+static PrimSource primSource(const grtGeometryBuildInput* in, uint32_t count) {
+    PrimSource S{};
+    S.count = count;
+    if (in->type == GRT_PRIMITIVE_TRIANGLE_MESH) {
+        S.kind = 0;
+        S.idx = (const char*)in->triangleMesh.triangleIndices;
+        S.idxStride = in->triangleMesh.triangleStride;
+        S.verts = (const char*)in->triangleMesh.vertices;
+        S.vertStride = in->triangleMesh.vertexStride;
+    } else {
+        S.kind = 1;
+        S.boxes = (const char*)in->aabbList.aabbs;
+        S.boxStride = in->aabbList.aabbStride;
+    }
+    return S;
+}
+
+static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geomType, uint32_t mortonBits,
+                                BvhObject** out) {
+    BvhObject* o = new BvhObject();
+    o->primCount = count;
+    o->nodeCount = count == 0 ? 0 : std::max(count - 1, 1u);
+    o->primType = primType;
+    o->geomType = geomType;
+    o->mortonBits = mortonBits;
+    o->built = false;
+    size_t leafBytes = primType == GRT_PRIMITIVE_TRIANGLE_MESH ? 48 : (primType == kPrimScene ? 128 : 4);
+    cudaError_t e = cudaMalloc(&o->dHeader, sizeof(BvhHeader));
+    if (e == cudaSuccess && count) e = cudaMalloc(&o->nodes, (size_t)o->nodeCount * 64);
+    if (e == cudaSuccess && count) e = cudaMalloc(&o->leaves, (size_t)count * leafBytes);
+    if (e == cudaSuccess && count) e = cudaMalloc(&o->parents, (size_t)(2 * count - 1) * 4);
+    if (e == cudaSuccess && count && primType != GRT_PRIMITIVE_AABB_LIST) e = cudaMalloc(&o->primToLeaf, (size_t)count * 4);
+    if (e == cudaSuccess && count && primType == kPrimScene) e = cudaMalloc(&o->inv64, (size_t)count * sizeof(InstanceFrames64));
+    if (e == cudaSuccess && count && primType == kPrimScene) e = cudaMalloc(&o->fwd32, (size_t)count * 3 * sizeof(float4));
+    BvhHeader h{};
+    for (int a = 0; a < 3; ++a) h.rootLo[a] = INFINITY, h.rootHi[a] = -INFINITY;
+    h.primCount = count;
+    h.primType = primType;
+    h.nodes = (const float4*)o->nodes;
+    h.leaves = o->leaves;
+    h.nodeCount = o->nodeCount;
+    h.geomType = geomType;
+    h.primToLeaf = o->primToLeaf;
+    if (e == cudaSuccess) e = cudaMemcpy(o->dHeader, &h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(o->dHeader);
+        cudaFree(o->nodes);
+        cudaFree(o->leaves);
+        cudaFree(o->parents);
+        cudaFree(o->primToLeaf);
+        cudaFree(o->inv64);
+        cudaFree(o->fwd32);
+        delete o;
+        logf(GRT_LOG_ERROR, "allocation of a BVH with %u primitives failed: %s", count, cudaGetErrorString(e));
+        return GRT_ERROR_OUT_OF_MEMORY;
+    }
+    registerBvh(o);
+    *out = o;
+    return GRT_SUCCESS;
+}
+
+static void destroyBvhObject(BvhObject* o) {
+    unregisterBvh(o->dHeader);
+    cudaFree(o->dHeader);
+    cudaFree(o->nodes);
+    cudaFree(o->leaves);
+    cudaFree(o->parents);
+    cudaFree(o->primToLeaf);
+    cudaFree(o->inv64);
+    cudaFree(o->fwd32);
+    delete o;
+}
+
+// Morton + sort + Karras over the centroids already in temp (count >= 1).
+static grtError sortAndEmit(Context* ctx, BvhObject* o, const BuildLayout& L, char* temp, cudaStream_t s,
+                            const uint32_t** sortedOut) {
+    const uint32_t n = o->primCount;
+    const float4* cen = (const float4*)(temp + L.centroids);
+    const uint32_t* bounds = (const uint32_t*)(temp + L.bounds);
+    void* k0 = temp + L.keys[0];
+    uint32_t* v0 = (uint32_t*)(temp + L.vals[0]);
+    if (o->mortonBits == 30)
+        mortonKernel<uint32_t, 10><<<ceilDiv(n, 256), 256, 0, s>>>(cen, n, bounds, (uint32_t*)k0, v0);
+    else
+        mortonKernel<unsigned long long, 21><<<ceilDiv(n, 256), 256, 0, s>>>(cen, n, bounds, (unsigned long long*)k0,
+                                                                            v0);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    int fb = 0;
+    grtError err = radixSort(ctx, temp + L.keys[0], temp + L.keys[1], (uint32_t*)(temp + L.vals[0]),
+                             (uint32_t*)(temp + L.vals[1]), n, L.keyBytes, (int)o->mortonBits, (uint32_t*)(temp + L.hist),
+                             s, &fb);
+    if (err != GRT_SUCCESS) return err;
+    const void* sk = temp + L.keys[fb];
+    if (n >= 2) {
+        if (o->mortonBits == 30)
+            karrasKernel<uint32_t><<<ceilDiv(n - 1, 256), 256, 0, s>>>((const uint32_t*)sk, (int)n,
+                                                                        (float4*)o->nodes, (uint32_t*)o->parents);
+        else
+            karrasKernel<unsigned long long><<<ceilDiv(n - 1, 256), 256, 0, s>>>(
+                (const unsigned long long*)sk, (int)n, (float4*)o->nodes, (uint32_t*)o->parents);
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
+    }
+    *sortedOut = (const uint32_t*)(temp + L.vals[fb]);
+    return GRT_SUCCESS;
+}
+
+static grtError resetBuildScratch(const BuildLayout& L, char* temp, uint32_t n, cudaStream_t s) {
+    GRT_CUDA(cudaMemsetAsync(temp + L.bounds, 0xFF, 12, s));       // running minima start at the top
+    GRT_CUDA(cudaMemsetAsync(temp + L.bounds + 12, 0x00, 12, s));  // running maxima start at the bottom
+    GRT_CUDA(cudaMemsetAsync(temp + L.flags, 0, 4 * (size_t)std::max(n, 1u), s));
+    return GRT_SUCCESS;
+}
+
+}  // namespace grt
+
+using namespace grt;
+
+extern "C" {
+
+grtError grtGetGeometryBuildTemporaryBufferSize(grtContext ctx, const grtGeometryBuildInput* input,
+                                                const grtBuildOptions* options, size_t* sizeBytes) {
+    uint32_t n = 0;
+    if (!ctx || !sizeBytes) return GRT_ERROR_INVALID_PARAMETER;
+    grtError e = validateGeometryInput(input, &n);
+    if (e != GRT_SUCCESS) return e;
+    *sizeBytes = buildLayout(n, resolveMortonBits(n, options), false).total;
+    return GRT_SUCCESS;
+}
+
+grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, const grtBuildOptions* options,
+                           grtGeometry* out) {
+    uint32_t n = 0;
+    if (!ctx || !out) return GRT_ERROR_INVALID_PARAMETER;
+    grtError e = validateGeometryInput(input, &n);
+    if (e != GRT_SUCCESS) return e;
+    BvhObject* o = nullptr;
+    e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(n, options), &o);
+    if (e != GRT_SUCCESS) return e;
+    *out = reinterpret_cast<grtGeometry>(o->dHeader);
+    return GRT_SUCCESS;
+}
+
+grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInput* input,
+                          const grtBuildOptions* options, void* temp, void* stream, grtGeometry geom) {
+    uint32_t n = 0;
+    if (!ctx || !geom) return GRT_ERROR_INVALID_PARAMETER;
+    grtError e = validateGeometryInput(input, &n);
+    if (e != GRT_SUCCESS) return e;
+    BvhObject* o = findBvh(geom);
+    if (!o || o->primType == kPrimScene || o->primType != input->type || o->primCount != n)
+        return GRT_ERROR_INVALID_PARAMETER;
+    if (op != GRT_BUILD_OPERATION_BUILD && op != GRT_BUILD_OPERATION_UPDATE) return GRT_ERROR_INVALID_PARAMETER;
+    if (op == GRT_BUILD_OPERATION_UPDATE && !o->built) return GRT_ERROR_NOT_BUILT;
+    if (n > 0 && (!temp || ((uintptr_t)temp & 15))) return GRT_ERROR_INVALID_PARAMETER;
+    if (options && options->mortonBits && resolveMortonBits(n, options) != o->mortonBits)
+        return GRT_ERROR_INVALID_PARAMETER;
+    Context* c = asContext(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    o->geomType = input->geomType;
+    if (n == 0) {
+        o->built = true;
+        return GRT_SUCCESS;
+    }
+    const BuildLayout L = buildLayout(n, o->mortonBits, false);
+    char* t = (char*)temp;
+    e = resetBuildScratch(L, t, n, s);
+    if (e != GRT_SUCCESS) return e;
+    const PrimSource S = primSource(input, n);
+    const uint32_t* sorted = nullptr;
+    if (op == GRT_BUILD_OPERATION_BUILD) {
+        primCentroidKernel<<<ceilDiv(n, 256), 256, 0, s>>>(S, (float4*)(t + L.centroids), (uint32_t*)(t + L.bounds));
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
+        e = sortAndEmit(c, o, L, t, s, &sorted);
+        if (e != GRT_SUCCESS) return e;
+    }
+    FitParams P{};
+    P.src = S;
+    P.n = n;
+    P.sortedPrims = sorted;  // null for UPDATE: IDs come from the leaves
+    P.nodes = (float4*)o->nodes;
+    P.leaves = o->leaves;
+    P.primToLeaf = o->primToLeaf;
+    P.parents = (const uint32_t*)o->parents;
+    P.flags = (uint32_t*)(t + L.flags);
+    P.header = o->dHeader;
+    if (input->type == GRT_PRIMITIVE_TRIANGLE_MESH)
+        fitKernel<0><<<ceilDiv(n, 256), 256, 0, s>>>(P);
+    else
+        fitKernel<1><<<ceilDiv(n, 256), 256, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    o->built = true;
+    return GRT_SUCCESS;
+}
+
+grtError grtDestroyGeometry(grtContext ctx, grtGeometry geom) {
+    BvhObject* o = findBvh(geom);
+    if (!ctx || !o || o->primType == kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
+    destroyBvhObject(o);
+    return GRT_SUCCESS;
+}
+
+static grtError validateSceneInput(const grtSceneBuildInput* in) {
+    if (!in) return GRT_ERROR_INVALID_PARAMETER;
+    if (in->instanceCount != in->frameCount) return GRT_ERROR_INVALID_PARAMETER;
+    if (in->instanceCount && (!in->instances || !in->instanceFrames)) return GRT_ERROR_INVALID_PARAMETER;
+    if (in->instanceCount >= 0x7FFFFFFFu) return GRT_ERROR_INVALID_PARAMETER;
+    return GRT_SUCCESS;
+}
+
+grtError grtGetSceneBuildTemporaryBufferSize(grtContext ctx, const grtSceneBuildInput* input,
+                                             const grtBuildOptions* options, size_t* sizeBytes) {
+    if (!ctx || !sizeBytes) return GRT_ERROR_INVALID_PARAMETER;
+    grtError e = validateSceneInput(input);
+    if (e != GRT_SUCCESS) return e;
+    *sizeBytes = buildLayout(input->instanceCount, resolveMortonBits(input->instanceCount, options), true).total;
+    return GRT_SUCCESS;
+}
+
+grtError grtCreateScene(grtContext ctx, const grtSceneBuildInput* input, const grtBuildOptions* options,
+                        grtScene* out) {
+    if (!ctx || !out) return GRT_ERROR_INVALID_PARAMETER;
+    grtError e = validateSceneInput(input);
+    if (e != GRT_SUCCESS) return e;
+    BvhObject* o = nullptr;
+    e = createBvhObject(input->instanceCount, kPrimScene, 0, resolveMortonBits(input->instanceCount, options), &o);
+    if (e != GRT_SUCCESS) return e;
+    *out = reinterpret_cast<grtScene>(o->dHeader);
+    return GRT_SUCCESS;
+}
+
+grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* input, const grtBuildOptions* options,
+                       void* temp, void* stream, grtScene scene) {
+    if (!ctx || !scene) return GRT_ERROR_INVALID_PARAMETER;
+    grtError e = validateSceneInput(input);
+    if (e != GRT_SUCCESS) return e;
+    BvhObject* o = findBvh(scene);
+    if (!o || o->primType != kPrimScene || o->primCount != input->instanceCount) return GRT_ERROR_INVALID_PARAMETER;
+    if (op != GRT_BUILD_OPERATION_BUILD && op != GRT_BUILD_OPERATION_UPDATE) return GRT_ERROR_INVALID_PARAMETER;
+    const uint32_t n = o->primCount;
+    if (n > 0 && (!temp || ((uintptr_t)temp & 15))) return GRT_ERROR_INVALID_PARAMETER;
+    (void)options;
+    Context* c = asContext(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        o->built = true;
+        return GRT_SUCCESS;
+    }
+    // An update of a scene rebuilds its (small) top level: instance frames may move freely.
+    const BuildLayout L = buildLayout(n, o->mortonBits, true);
+    char* t = (char*)temp;
+    e = resetBuildScratch(L, t, n, s);
+    if (e != GRT_SUCCESS) return e;
+    InstanceInput I{};
+    I.instances = input->instances;
+    I.frames = input->instanceFrames;
+    I.count = n;
+    I.boxes = (float4*)(t + L.extra);
+    I.records = (InstanceRecord*)(t + L.extra + alignUp(32 * (size_t)n, 256));
+    I.centroids = (float4*)(t + L.centroids);
+    I.bounds = (uint32_t*)(t + L.bounds);
+    I.inv64 = o->inv64;
+    I.fwd32 = o->fwd32;
+    instanceSetupKernel<<<ceilDiv(n, 128), 128, 0, s>>>(I);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    const uint32_t* sorted = nullptr;
+    e = sortAndEmit(c, o, L, t, s, &sorted);
+    if (e != GRT_SUCCESS) return e;
+    FitParams P{};
+    P.n = n;
+    P.sortedPrims = sorted;
+    P.nodes = (float4*)o->nodes;
+    P.leaves = o->leaves;
+    P.parents = (const uint32_t*)o->parents;
+    P.flags = (uint32_t*)(t + L.flags);
+    P.header = o->dHeader;
+    P.primToLeaf = o->primToLeaf;
+    P.instBoxes = I.boxes;
+    P.instRecords = I.records;
+    fitKernel<2><<<ceilDiv(n, 256), 256, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    o->built = true;
+    return GRT_SUCCESS;
+}
+
+grtError grtDestroyScene(grtContext ctx, grtScene scene) {
+    BvhObject* o = findBvh(scene);
+    if (!ctx || !o || o->primType != kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
+    destroyBvhObject(o);
+    return GRT_SUCCESS;
+}
+
+grtError grtSortTemporaryBufferSize(uint32_t count, uint32_t keyBits, size_t* sizeBytes) {
+    if (!sizeBytes || (keyBits != 32 && keyBits != 64)) return GRT_ERROR_INVALID_PARAMETER;
+    const size_t kb = keyBits / 8;
+    *sizeBytes = alignUp(kb * std::max(count, 1u), 256) + alignUp(4 * (size_t)std::max(count, 1u), 256) +
+                 sortScratchBytes(count);
+    return GRT_SUCCESS;
+}
+
+grtError grtSortPairs(grtContext ctx, void* keys, uint32_t* values, uint32_t count, uint32_t keyBits,
+                      uint32_t significantBits, void* temp, void* stream) {
+    if (!ctx || (keyBits != 32 && keyBits != 64) || significantBits == 0 || significantBits > keyBits)
+        return GRT_ERROR_INVALID_PARAMETER;
+    if (count == 0) return GRT_SUCCESS;
+    if (!keys || !values || !temp || ((uintptr_t)temp & 15)) return GRT_ERROR_INVALID_PARAMETER;
+    const size_t kb = keyBits / 8;
+    char* t = (char*)temp;
+    void* k1 = t;
+    uint32_t* v1 = (uint32_t*)(t + alignUp(kb * count, 256));
+    uint32_t* hist = (uint32_t*)(t + alignUp(kb * count, 256) + alignUp(4 * (size_t)count, 256));
+    cudaStream_t s = (cudaStream_t)stream;
+    int fb = 0;
+    grtError e = radixSort(asContext(ctx), keys, k1, values, v1, count, (int)kb, (int)significantBits, hist, s, &fb);
+    if (e != GRT_SUCCESS) return e;
+    if (fb == 1) {
+        GRT_CUDA(cudaMemcpyAsync(keys, k1, kb * count, cudaMemcpyDeviceToDevice, s));
+        GRT_CUDA(cudaMemcpyAsync(values, v1, 4 * (size_t)count, cudaMemcpyDeviceToDevice, s));
+    }
+    return GRT_SUCCESS;
+}
+
+}  // extern "C"

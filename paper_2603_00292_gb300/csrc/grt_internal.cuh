@@ -1,0 +1,169 @@
+// Internal definitions shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "../../include/grt.h"
+
+namespace grt {
+
+constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr uint32_t kInvalid = 0xFFFFFFFFu;
+constexpr uint32_t kPrimScene = 2;  // primType of a scene header
+
+// Device-resident header that a grtGeometry / grtScene handle points to (64 B).
+struct alignas(16) BvhHeader {
+    float rootLo[3];      // box of everything below the root (written by the build)
+    uint32_t primCount;
+    float rootHi[3];
+    uint32_t primType;    // grtPrimitiveType, or kPrimScene
+    const float4* nodes;  // nodeCount x 4 float4
+    const void* leaves;   // triangle records / prim IDs / instance records
+    uint32_t nodeCount;
+    uint32_t geomType;
+    const uint32_t* primToLeaf;  // primitive (or instance) ID -> sorted leaf position
+};
+static_assert(sizeof(BvhHeader) == 64, "header size");
+
+// Instance record of a scene leaf (128 B): the float32 inverse frame and the bottom
+// level's arrays (read when a ray enters the instance), the instance's world box
+// (bounds the parameter range inside it), and the geometry header.
+struct alignas(16) InstanceRecord {
+    float4 inv[3];          // object = inv * world (rows; w = translation), rounded from FP64
+    const float4* nodes;    // bottom-level nodes
+    const void* leaves;     // bottom-level leaves
+    uint32_t instanceID;
+    uint32_t typeBits;      // geomType (bits 0-23) | primType << 24 | kInstEmpty
+    const BvhHeader* geometry;
+    float4 worldLo;         // xyz: world box (rounded outward)
+    float4 worldHi;
+    float4 reserved;
+};
+
+// Per-instance frames of a scene, indexed by instance ID.
+struct InstanceFrames64 {
+    double inv[3][4];  // object = inv * world, FP64 from the SRT frame
+};
+constexpr uint32_t kInstEmpty = 0x80000000u;
+__host__ __device__ inline uint32_t instGeomType(uint32_t bits) { return bits & 0xFFFFFFu; }
+__host__ __device__ inline uint32_t instPrimType(uint32_t bits) { return (bits >> 24) & 0x7Fu; }
+static_assert(sizeof(InstanceRecord) == 128, "instance record size");
+
+// Device error word values are grtError codes; the first nonzero one latched wins
+// by atomicCAS from 0.
+constexpr int kCounterSlots = 256;
+struct DeviceWorkspace {
+    uint32_t error;
+    uint32_t pad[31];
+    unsigned long long stats[16];  // traversal statistics (grtTraceStatistics order)
+    unsigned long long counters[kCounterSlots];  // per-launch work counters (round robin)
+};
+
+// ------------------------------------------------------------------ host helpers
+int logLevel();
+void noteLaunches(unsigned n);  // adds to the process-wide kernel launch count
+void logf(int level, const char* fmt, ...);
+
+#define GRT_CUDA(call)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ::grt::logf(GRT_LOG_ERROR, "%s:%d %s: %s", __FILE__, __LINE__, #call,       \
+                        cudaGetErrorString(e_));                                       \
+            return e_ == cudaErrorMemoryAllocation ? GRT_ERROR_OUT_OF_MEMORY : GRT_ERROR_CUDA; \
+        }                                                                              \
+    } while (0)
+
+#define GRT_LAUNCH_CHECK()                                                             \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            ::grt::logf(GRT_LOG_ERROR, "%s:%d launch: %s", __FILE__, __LINE__,           \
+                        cudaGetErrorString(e_));                                       \
+            return GRT_ERROR_CUDA;                                                     \
+        }                                                                              \
+    } while (0)
+
+inline size_t alignUp(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline unsigned ceilDiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Context internals used across files.
+struct Context;
+Context* asContext(grtContext c);
+DeviceWorkspace* workspace(Context* c);
+unsigned long long* nextCounter(Context* c);  // a zeroed-on-use work counter slot
+// Caller-or-context global stack memory for traversal spills (grown on demand).
+grtError contextScratch(Context* c, size_t bytes, void** ptr);
+int smCount(Context* c);
+int deviceOf(Context* c);
+
+// Host-side records of library-owned objects, looked up by handle.
+struct BvhObject {
+    BvhHeader* dHeader;  // == handle
+    void* nodes;
+    void* leaves;
+    int32_t* parents;
+    uint32_t* primToLeaf;  // primitive (instance) ID -> sorted position (triangles, scenes)
+    InstanceFrames64* inv64;  // scenes: FP64 inverse frame per instance ID
+    float4* fwd32;            // scenes: 3 float4 rows of the forward frame per instance ID
+    uint32_t primCount;
+    uint32_t nodeCount;
+    uint32_t primType;
+    uint32_t geomType;
+    uint32_t mortonBits;
+    bool built;
+};
+BvhObject* findBvh(const void* handle);
+grtError registerBvh(BvhObject* obj);
+void unregisterBvh(const void* handle);
+
+// Function-table record in device memory: one per (rayType, geomType).
+struct FuncEntry {
+    uint32_t func;
+    uint32_t pad;
+    const void* data;
+};
+struct FuncTableObject {
+    FuncEntry* dEntries;
+    uint32_t numGeomTypes;
+    uint32_t numRayTypes;
+};
+FuncTableObject* findFuncTable(grtFuncTable t);
+
+// Build-time temporary layout.
+struct BuildLayout {
+    size_t bounds;       // 8 x uint32 ordered-float centroid bounds
+    size_t centroids;    // float4 per prim
+    size_t keys[2];      // ping-pong keys
+    size_t vals[2];      // ping-pong values
+    size_t hist;         // sort histogram / offsets
+    size_t flags;        // fit visit counters
+    size_t extra;        // scene: instance world boxes and records
+    size_t total;
+    int passes;          // radix passes
+    int finalBuf;        // which ping-pong buffer holds the sorted result
+    int keyBytes;
+};
+BuildLayout buildLayout(uint32_t count, uint32_t mortonBits, bool scene);
+uint32_t resolveMortonBits(uint32_t count, const grtBuildOptions* opt);
+
+// Radix sort (build.cu).
+size_t sortScratchBytes(uint32_t count);
+grtError radixSort(Context* ctx, void* keys0, void* keys1, uint32_t* vals0, uint32_t* vals1, uint32_t count,
+                   int keyBytes, int significantBits, uint32_t* hist, cudaStream_t stream, int* finalBuf);
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ uint32_t floatToOrdered(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float orderedToFloat(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+__device__ __forceinline__ void latchError(uint32_t* err, uint32_t code) { atomicCAS(err, 0u, code); }
+
+}  // namespace grt

@@ -1,0 +1,341 @@
+// Ray-query kernels (closest hit, any hit, fused ambient occlusion), ray generation
+// (camera, ambient occlusion) and their host entry points. The traversal itself is in
+// traverse.cuh.
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
+#include "traverse.cuh"
+
+namespace grt {
+
+// Persistent kernel: warps take 32 rays at a time from a global counter until the
+// batch is exhausted.
+template <bool ANY, bool SCENE, bool COUNT>
+__global__ void traceKernel(TraceParams P) {
+    extern __shared__ uint32_t sstack[];
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
+    const uint32_t lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.counter, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= P.count) break;
+        const uint32_t r = (uint32_t)base + lane;
+        if (r < P.count) {
+            const float4 a = P.rays[2 * (size_t)r], b = P.rays[2 * (size_t)r + 1];
+            Visits v;
+            const Hit h = traceRay<ANY, SCENE, COUNT>(P, st, f3(a), f3(b), a.w, b.w, &v);
+            storeHit(P.hits, r, h);
+            if (COUNT) flushVisits(P.stats, v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- ambient occlusion (Sec. 4)
+__global__ void aoRayKernel(const InstanceRecord* sceneLeaves, const uint32_t* scenePrimToLeaf, const float4* fwd32,
+                            const float4* rays, const uint32_t* hits, uint32_t pixels, uint32_t spp,
+                            unsigned long long seed, float length, float4* out) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= pixels) return;
+    AoFrame F;
+    const bool ok = aoFrame(sceneLeaves, scenePrimToLeaf, fwd32, rays + 2 * (size_t)p, hits + 5 * (size_t)p, F);
+    for (uint32_t s = 0; s < spp; ++s) {
+        float4* o = out + 2 * ((size_t)p * spp + s);
+        if (!ok) {
+            o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            o[1] = make_float4(0.f, 0.f, 0.f, -1.f);
+            continue;
+        }
+        const float3 dir = aoDirection(F, seed, p, s);
+        o[0] = make_float4(F.org.x, F.org.y, F.org.z, 0.f);
+        o[1] = make_float4(dir.x, dir.y, dir.z, length);
+    }
+}
+
+// Fused AO: one thread per pixel, the pixel's samples traced in turn as any-hit
+// queries; no ray buffer is stored.
+template <bool COUNT>
+__global__ void aoTraceKernel(TraceParams P) {
+    extern __shared__ uint32_t sstack[];
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
+    const uint32_t lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.counter, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= P.count) break;
+        const uint32_t p = (uint32_t)base + lane;
+        if (p < P.count) {
+            AoFrame F;
+            uint32_t occluded = 0;
+            if (aoFrame(P.sceneLeaves, P.scenePrimToLeaf, P.fwd32, P.primaryRays + 2 * (size_t)p,
+                        P.primaryHits + 5 * (size_t)p, F)) {
+                for (uint32_t s = 0; s < P.spp; ++s) {
+                    const float3 dir = aoDirection(F, P.seed, p, s);
+                    Visits v;
+                    const Hit h = traceRay<true, true, COUNT>(P, st, F.org, dir, 0.0f, P.aoLength, &v);
+                    occluded += (h.prim != kInvalid) ? 1u : 0u;
+                    if (COUNT) flushVisits(P.stats, v);
+                }
+            }
+            P.ao[p] = (float)occluded / (float)P.spp;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- camera rays (Sec. 3.2)
+__global__ void cameraRayKernel(grtCamera cam, uint32_t W, uint32_t H, float4* out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * H) return;
+    const uint32_t x = i % W, y = i / W;
+    const float3 o = make_float3(cam.origin[0], cam.origin[1], cam.origin[2]);
+    const float3 right = make_float3(cam.right[0], cam.right[1], cam.right[2]);
+    const float3 up = make_float3(cam.up[0], cam.up[1], cam.up[2]);
+    const float3 fwd = normalize3(cross3(up, right));
+    const float u = ((float)x + 0.5f) / (float)W, v = ((float)y + 0.5f) / (float)H;
+    // lerp(-right, right, u) + lerp(up, -up, v)
+    const float3 to = o + fwd + right * (2.0f * u - 1.0f) + up * (1.0f - 2.0f * v);
+    const float3 d = normalize3(to - o);
+    out[2 * (size_t)i] = make_float4(o.x, o.y, o.z, 0.0f);
+    out[2 * (size_t)i + 1] = make_float4(d.x, d.y, d.z, INFINITY);
+}
+
+// ---------------------------------------------------------------- host side
+struct LaunchShape {
+    int blockSize;
+    int blocks;
+};
+
+template <class K>
+static LaunchShape persistentShape(Context* c, K kernel, int blockSize, size_t smem) {
+    static std::mutex m;
+    static std::unordered_map<size_t, int> cache;
+    const size_t key = ((size_t)(void*)kernel) ^ ((size_t)blockSize << 48) ^ (smem << 20);
+    int perSm = 0;
+    {
+        std::lock_guard<std::mutex> g(m);
+        auto it = cache.find(key);
+        if (it != cache.end()) perSm = it->second;
+    }
+    if (perSm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSm, kernel, blockSize, smem) != cudaSuccess || perSm < 1)
+            perSm = 1;
+        std::lock_guard<std::mutex> g(m);
+        cache[key] = perSm;
+    }
+    return LaunchShape{blockSize, perSm * smCount(c)};
+}
+
+static grtError resolveOptions(const grtTraceOptions* opt, int* blockSize, uint32_t* sh, uint32_t* gl) {
+    *blockSize = (opt && opt->blockSize) ? (int)opt->blockSize : 128;
+    *sh = (opt && opt->sharedStackDepth) ? opt->sharedStackDepth : 16u;
+    *gl = (opt && opt->globalStackDepth) ? opt->globalStackDepth : 64u;
+    if (*blockSize != 64 && *blockSize != 128 && *blockSize != 256) return GRT_ERROR_INVALID_PARAMETER;
+    if (*sh < 1 || *sh > 32 || *gl > 4096) return GRT_ERROR_INVALID_PARAMETER;
+    if (opt && (opt->flags & ~GRT_TRACE_FLAG_COUNT)) return GRT_ERROR_INVALID_PARAMETER;
+    return GRT_SUCCESS;
+}
+
+// Everything a launch needs except the kernel-specific fields.
+static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFuncTable table,
+                             const grtTraceOptions* opt, TraceParams& P, bool* isScene, int* blockSize) {
+    if ((scene != nullptr) == (geom != nullptr)) return GRT_ERROR_INVALID_PARAMETER;
+    BvhObject* o = findBvh(scene ? (const void*)scene : (const void*)geom);
+    if (!o) return GRT_ERROR_INVALID_PARAMETER;
+    if (scene && o->primType != kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
+    if (geom && o->primType == kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
+    if (!o->built) return GRT_ERROR_NOT_BUILT;
+    *isScene = scene != nullptr;
+    P.target.nodes = (const float4*)o->nodes;
+    P.target.leaves = o->leaves;
+    P.target.primType = o->primType;
+    P.target.geomType = o->geomType;
+    P.target.empty = o->primCount == 0;
+    P.maxSteps = 1u << 26;  // far above any legitimate walk; stops a corrupted (cyclic) hierarchy
+    P.inv64 = o->inv64;
+    if (table) {
+        FuncTableObject* t = findFuncTable(table);
+        if (!t) return GRT_ERROR_INVALID_PARAMETER;
+        P.table = t->dEntries;
+        P.numGeomTypes = t->numGeomTypes;
+        P.rayType = opt ? opt->rayType : 0u;
+        if (P.rayType >= t->numRayTypes) return GRT_ERROR_INVALID_PARAMETER;
+    }
+    uint32_t sh, gl;
+    grtError e = resolveOptions(opt, blockSize, &sh, &gl);
+    if (e != GRT_SUCCESS) return e;
+    P.sharedDepth = sh;
+    P.globalDepth = gl;
+    P.error = &workspace(c)->error;
+    P.stats = workspace(c)->stats;
+    return GRT_SUCCESS;
+}
+
+static grtError bindGlobalStack(Context* c, const grtTraceOptions* opt, int threads, TraceParams& P) {
+    const size_t need = (size_t)threads * P.globalDepth * sizeof(uint32_t);
+    P.globalStride = (uint32_t)threads;
+    if (opt && opt->globalStack) {
+        if (opt->globalStackBytes < need) return GRT_ERROR_INVALID_PARAMETER;
+        P.globalStack = (uint32_t*)opt->globalStack;
+        return GRT_SUCCESS;
+    }
+    void* p = nullptr;
+    grtError e = contextScratch(c, std::max<size_t>(need, 256), &p);
+    P.globalStack = (uint32_t*)p;
+    return e;
+}
+
+template <bool ANY, bool COUNT>
+static void traceKernelFor(bool scene, void (**k)(TraceParams)) {
+    *k = scene ? traceKernel<ANY, true, COUNT> : traceKernel<ANY, false, COUNT>;
+}
+
+template <bool ANY>
+static grtError launchTrace(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t n,
+                            grtHit* hits, grtFuncTable table, const grtTraceOptions* opt, void* stream) {
+    if (!ctx) return GRT_ERROR_INVALID_PARAMETER;
+    if (n && (!rays || !hits || ((uintptr_t)rays & 15))) return GRT_ERROR_INVALID_PARAMETER;
+    Context* c = asContext(ctx);
+    TraceParams P{};
+    bool isScene = false;
+    int bs = 128;
+    grtError e = prepareTrace(c, scene, geom, table, opt, P, &isScene, &bs);
+    if (e != GRT_SUCCESS || n == 0) return e;
+    const bool count = opt && (opt->flags & GRT_TRACE_FLAG_COUNT);
+    P.rays = (const float4*)rays;
+    P.hits = (uint32_t*)hits;
+    P.count = n;
+    void (*kernel)(TraceParams) = nullptr;
+    if (count)
+        traceKernelFor<ANY, true>(isScene, &kernel);
+    else
+        traceKernelFor<ANY, false>(isScene, &kernel);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    LaunchShape L = persistentShape(c, kernel, bs, smem);
+    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(n, bs));
+    e = bindGlobalStack(c, opt, L.blocks * bs, P);
+    if (e != GRT_SUCCESS) return e;
+    P.counter = nextCounter(c);
+    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
+    kernel<<<L.blocks, bs, smem, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+}  // namespace grt
+
+using namespace grt;
+
+extern "C" {
+
+grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* options, size_t* sizeBytes) {
+    if (!ctx || !sizeBytes) return GRT_ERROR_INVALID_PARAMETER;
+    int bs;
+    uint32_t sh, gl;
+    grtError e = resolveOptions(options, &bs, &sh, &gl);
+    if (e != GRT_SUCCESS) return e;
+    Context* c = asContext(ctx);
+    const size_t smem = (size_t)bs * sh * sizeof(uint32_t);
+    int threads = 0;
+    void (*kernels[])(TraceParams) = {traceKernel<false, false, false>, traceKernel<false, true, false>,
+                                      traceKernel<true, false, false>,  traceKernel<true, true, false>,
+                                      traceKernel<false, false, true>,  traceKernel<false, true, true>,
+                                      traceKernel<true, false, true>,   traceKernel<true, true, true>};
+    for (auto k : kernels) threads = std::max(threads, persistentShape(c, k, bs, smem).blocks * bs);
+    threads = std::max(threads, persistentShape(c, aoTraceKernel<false>, bs, smem).blocks * bs);
+    threads = std::max(threads, persistentShape(c, aoTraceKernel<true>, bs, smem).blocks * bs);
+    *sizeBytes = (size_t)threads * gl * sizeof(uint32_t);
+    return GRT_SUCCESS;
+}
+
+grtError grtTraceClosest(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
+                         grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream) {
+    return launchTrace<false>(ctx, scene, geom, rays, rayCount, hits, table, options, stream);
+}
+
+grtError grtTraceAnyHit(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
+                        grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream) {
+    return launchTrace<true>(ctx, scene, geom, rays, rayCount, hits, table, options, stream);
+}
+
+grtError grtGenerateCameraRays(grtContext ctx, const grtCamera* camera, uint32_t width, uint32_t height, grtRay* rays,
+                               void* stream) {
+    if (!ctx || !camera || (width && height && !rays)) return GRT_ERROR_INVALID_PARAMETER;
+    const size_t n = (size_t)width * height;
+    if (n == 0) return GRT_SUCCESS;
+    if (n > 0xFFFFFFFFull) return GRT_ERROR_INVALID_PARAMETER;
+    cameraRayKernel<<<ceilDiv(n, 256), 256, 0, (cudaStream_t)stream>>>(*camera, width, height, (float4*)rays);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+static grtError sceneForShading(grtScene scene, BvhObject** out) {
+    BvhObject* o = findBvh(scene);
+    if (!o || o->primType != kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
+    if (!o->built) return GRT_ERROR_NOT_BUILT;
+    *out = o;
+    return GRT_SUCCESS;
+}
+
+grtError grtGenerateAORays(grtContext ctx, grtScene scene, const grtRay* primaryRays, const grtHit* primaryHits,
+                           uint32_t pixelCount, uint32_t samplesPerPixel, uint64_t seed, float length, grtRay* aoRays,
+                           void* stream) {
+    if (!ctx || samplesPerPixel == 0) return GRT_ERROR_INVALID_PARAMETER;
+    BvhObject* o = nullptr;
+    grtError e = sceneForShading(scene, &o);
+    if (e != GRT_SUCCESS || pixelCount == 0) return e;
+    if (!primaryRays || !primaryHits || !aoRays) return GRT_ERROR_INVALID_PARAMETER;
+    if ((size_t)pixelCount * samplesPerPixel > 0xFFFFFFFFull) return GRT_ERROR_INVALID_PARAMETER;
+    aoRayKernel<<<ceilDiv(pixelCount, 128), 128, 0, (cudaStream_t)stream>>>(
+        (const InstanceRecord*)o->leaves, o->primToLeaf, (const float4*)o->fwd32, (const float4*)primaryRays,
+        (const uint32_t*)primaryHits, pixelCount, samplesPerPixel, seed, length, (float4*)aoRays);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* primaryRays, const grtHit* primaryHits,
+                                  uint32_t pixelCount, uint32_t samplesPerPixel, uint64_t seed, float length, float* ao,
+                                  const grtTraceOptions* options, void* stream) {
+    if (!ctx || samplesPerPixel == 0) return GRT_ERROR_INVALID_PARAMETER;
+    Context* c = asContext(ctx);
+    TraceParams P{};
+    bool isScene = false;
+    int bs = 128;
+    grtError e = prepareTrace(c, scene, nullptr, nullptr, options, P, &isScene, &bs);
+    if (e != GRT_SUCCESS || pixelCount == 0) return e;
+    if (!primaryRays || !primaryHits || !ao) return GRT_ERROR_INVALID_PARAMETER;
+    BvhObject* o = findBvh(scene);
+    P.count = pixelCount;
+    P.primaryRays = (const float4*)primaryRays;
+    P.primaryHits = (const uint32_t*)primaryHits;
+    P.sceneLeaves = (const InstanceRecord*)o->leaves;
+    P.scenePrimToLeaf = o->primToLeaf;
+    P.fwd32 = (const float4*)o->fwd32;
+    P.spp = samplesPerPixel;
+    P.seed = seed;
+    P.aoLength = length;
+    P.ao = ao;
+    const bool count = options && (options->flags & GRT_TRACE_FLAG_COUNT);
+    void (*kernel)(TraceParams) = count ? aoTraceKernel<true> : aoTraceKernel<false>;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    LaunchShape L = persistentShape(c, kernel, bs, smem);
+    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(pixelCount, bs));
+    e = bindGlobalStack(c, options, L.blocks * bs, P);
+    if (e != GRT_SUCCESS) return e;
+    P.counter = nextCounter(c);
+    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
+    kernel<<<L.blocks, bs, smem, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+}  // extern "C"

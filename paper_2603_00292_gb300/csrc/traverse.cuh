@@ -1,0 +1,577 @@
+// Device traversal core shared by the trace, ambient-occlusion, shading and batched
+// kernels.
+//
+// Method: stack-based BVH traversal (paper Sec. 6.2 "BVH Traversal") through a
+// two-level hierarchy whose instance leaves take the ray to object space with the
+// inverse frame (Sec. 6.2 "Two-Level Hierarchy and Instancing"); the stack keeps its
+// first entries in shared memory and spills to a global buffer (Sec. 7.5); closest-
+// hit and any-hit queries (Sec. 7.6; any-hit may stop at the first valid hit, Sec.
+// 4.2); custom primitives through a (ray type x geometry type) function table (Sec.
+// 7.4). Triangles: Moller-Trumbore (1997), double-sided with inclusive edges as the
+// paper's test (Sec. 3.1). Spheres: centre-relative discriminant of Haines et al.,
+// "Precision Improvements for Ray/Sphere Intersection" (Ray Tracing Gems, 2019).
+//
+// Precision design. Decisions are taken in float32 with certified error bounds:
+//  * box tests use the far-distance factor 1 + 2*gamma_3 of Ize, "Robust BVH Ray
+//    Traversal" (JCGT 2013), near/far planes chosen by the direction's sign so that a
+//    0*inf = NaN is dropped conservatively, and boxes are widened by the bound on the
+//    object-space ray's transform error;
+//  * a triangle or sphere test whose float32 edge functions (or discriminant) lie
+//    within their rounding bound of zero is decided again in FP64;
+//  * the closest hit's t, u, v are recomputed once in FP64.
+// FP64 runs far slower than FP32 on this GPU, so it is confined to these rare cases.
+#pragma once
+
+#include "grt_internal.cuh"
+
+namespace grt {
+
+constexpr uint32_t kSentinel = 0xFFFFFFFEu;  // stack marker: leave the current instance
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr float kEps = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of float32
+// 1 + 2*gamma(3) rounded up, gamma(n) = n*eps/(1 - n*eps)
+constexpr float kFarScale = 1.0000005f;
+// coefficient of the rounding terms of the triangle / sphere error bounds (about 4x
+// the worst-case count of roundings in each expression)
+constexpr float kBound = 32.0f * kEps;
+
+struct TraceTarget {
+    const float4* nodes;  // top-level nodes (scene) or the geometry's nodes
+    const void* leaves;
+    uint32_t primType;  // of the geometry when tracing one directly
+    uint32_t geomType;
+    uint32_t empty;
+};
+
+struct TraceParams {
+    TraceTarget target;
+    const float4* rays;  // 2 float4 per ray
+    uint32_t* hits;      // 5 words per ray
+    uint32_t count;
+    const FuncEntry* table;
+    uint32_t numGeomTypes;
+    uint32_t rayType;
+    uint32_t sharedDepth;
+    uint32_t globalDepth;
+    uint32_t* globalStack;  // [entry][thread]
+    uint32_t globalStride;  // threads in the grid
+    unsigned long long* counter;
+    uint32_t* error;
+    uint32_t maxSteps;
+    const InstanceFrames64* inv64;  // scene: FP64 inverse frames by instance ID
+    unsigned long long* stats;      // counting variants: grtTraceStatistics sums
+    // fused ambient occlusion
+    const float4* primaryRays;
+    const uint32_t* primaryHits;
+    const InstanceRecord* sceneLeaves;
+    const uint32_t* scenePrimToLeaf;
+    const float4* fwd32;
+    uint32_t spp;
+    unsigned long long seed;
+    float aoLength;
+    float* ao;
+};
+
+struct Hit {
+    uint32_t inst, prim;
+    float t, u, v;
+};
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float norm1(float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); }
+__device__ __forceinline__ float3 normalize3(float3 a) {
+    const float l = sqrtf(dot3(a, a));
+    return make_float3(a.x / l, a.y / l, a.z / l);
+}
+
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 d3(float3 a) { return D3{(double)a.x, (double)a.y, (double)a.z}; }
+__device__ __forceinline__ D3 operator-(D3 a, D3 b) { return D3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ double dotd(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ D3 crossd(D3 a, D3 b) {
+    return D3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Ray state at the current level.
+struct Level {
+    float3 o, d, id;  // float32 ray and reciprocal direction
+    float3 on, of;    // origins for the near and far slab planes (box widening applied)
+    float dO, dD;     // bounds on the error of each origin / direction component
+    float dl1;        // |d|_1
+};
+
+__device__ __forceinline__ void exactLevel(Level& L, float3 o, float3 d) {
+    L.o = o;
+    L.d = d;
+    L.id = make_float3(__frcp_rn(d.x), __frcp_rn(d.y), __frcp_rn(d.z));
+    L.on = o;
+    L.of = o;
+    L.dO = 0.f;
+    L.dD = 0.f;
+    L.dl1 = norm1(d);
+}
+
+// Slab test of both children of a node.
+__device__ __forceinline__ void slab2(const float4& nx, const float4& ny, const float4& nz, const Level& L,
+                                      float tmin, float tmax, bool& h0, bool& h1, float& tn0, float& tn1) {
+    const bool px = L.id.x >= 0.f, py = L.id.y >= 0.f, pz = L.id.z >= 0.f;
+    const float n0x = ((px ? nx.x : nx.y) - L.on.x) * L.id.x, f0x = ((px ? nx.y : nx.x) - L.of.x) * L.id.x;
+    const float n0y = ((py ? ny.x : ny.y) - L.on.y) * L.id.y, f0y = ((py ? ny.y : ny.x) - L.of.y) * L.id.y;
+    const float n0z = ((pz ? nz.x : nz.y) - L.on.z) * L.id.z, f0z = ((pz ? nz.y : nz.x) - L.of.z) * L.id.z;
+    const float n1x = ((px ? nx.z : nx.w) - L.on.x) * L.id.x, f1x = ((px ? nx.w : nx.z) - L.of.x) * L.id.x;
+    const float n1y = ((py ? ny.z : ny.w) - L.on.y) * L.id.y, f1y = ((py ? ny.w : ny.z) - L.of.y) * L.id.y;
+    const float n1z = ((pz ? nz.z : nz.w) - L.on.z) * L.id.z, f1z = ((pz ? nz.w : nz.z) - L.of.z) * L.id.z;
+    tn0 = fmaxf(fmaxf(n0x, n0y), fmaxf(n0z, tmin));
+    tn1 = fmaxf(fmaxf(n1x, n1y), fmaxf(n1z, tmin));
+    const float tf0 = fminf(fminf(f0x, f0y), fminf(f0z, tmax));
+    const float tf1 = fminf(fminf(f1x, f1y), fminf(f1z, tmax));
+    h0 = tn0 <= tf0 * kFarScale;
+    h1 = tn1 <= tf1 * kFarScale;
+}
+
+// Float32 Moller-Trumbore with certified bounds on the three edge values.
+// Returns 0 = miss, 1 = hit with t in range (t, u, v set), 2 = undecided in float32.
+__device__ __forceinline__ int triangleTest(const Level& L, float3 v0, float3 v1, float3 v2, float e1n, float e2n,
+                                           float tmin, float tmax, bool strict, float& t, float& u, float& v) {
+    const float3 e1 = v1 - v0, e2 = v2 - v0;
+    const float3 P = cross3(L.d, e2);
+    const float det = dot3(e1, P);
+    const float ad = fabsf(det);
+    const float Edet = (4.f * L.dD + kBound * L.dl1) * e1n * e2n;
+    if (ad <= Edet) return (ad == 0.f && Edet == 0.f) ? 0 : 2;
+    const float s = det > 0.f ? 1.f : -1.f;
+    const float3 T = L.o - v0;
+    const float Tn = norm1(T);
+    const float U = dot3(T, P) * s;
+    const float EU = 2.f * (L.dO * norm1(P) + 2.f * L.dD * Tn * e2n) + kBound * Tn * L.dl1 * e2n;
+    if (U < -EU) return 0;
+    const float3 Q = cross3(T, e1);
+    const float V = dot3(L.d, Q) * s;
+    const float EV = 4.f * (L.dO * L.dl1 + L.dD * Tn) * e1n + kBound * Tn * L.dl1 * e1n;
+    if (V < -EV) return 0;
+    const float W = ad - U - V;
+    const float EW = Edet + EU + EV + 4.f * kEps * (ad + fabsf(U) + fabsf(V));
+    if (W < -EW) return 0;
+    if (U <= EU || V <= EV || W <= EW) return 2;
+    t = dot3(e2, Q) / det;
+    u = U / ad;
+    v = V / ad;
+    return (t >= tmin && (strict ? t < tmax : t <= tmax)) ? 1 : 0;
+}
+
+// FP64 Moller-Trumbore with the same acceptance rules (u in [0,1], v >= 0, u+v <= 1).
+__device__ __noinline__ bool triangleTest64(D3 o, D3 d, float3 v0f, float3 v1f, float3 v2f, double tmin, double tmax,
+                                            bool strict, double& t, double& u, double& v) {
+    const D3 v0 = d3(v0f), e1 = d3(v1f) - v0, e2 = d3(v2f) - v0;
+    const D3 P = crossd(d, e2);
+    const double det = dotd(e1, P);
+    if (det == 0.0) return false;
+    const double inv = 1.0 / det;
+    const D3 T = o - v0;
+    u = dotd(T, P) * inv;
+    if (u < 0.0 || u > 1.0) return false;
+    const D3 Q = crossd(T, e1);
+    v = dotd(d, Q) * inv;
+    if (v < 0.0 || u + v > 1.0) return false;
+    t = dotd(e2, Q) * inv;
+    return t >= tmin && (strict ? t < tmax : t <= tmax);
+}
+
+// FP64 barycentrics and distance of a known hit (no acceptance test).
+__device__ __noinline__ bool triangleRefine64(D3 o, D3 d, float3 v0f, float3 v1f, float3 v2f, double& t, double& u,
+                                              double& v) {
+    const D3 v0 = d3(v0f), e1 = d3(v1f) - v0, e2 = d3(v2f) - v0;
+    const D3 P = crossd(d, e2);
+    const double det = dotd(e1, P);
+    if (det == 0.0) return false;
+    const double inv = 1.0 / det;
+    const D3 T = o - v0;
+    const D3 Q = crossd(T, e1);
+    u = dotd(T, P) * inv;
+    v = dotd(d, Q) * inv;
+    t = dotd(e2, Q) * inv;
+    return true;
+}
+
+// Float32 sphere test. Returns 0 = miss, 1 = hit (t set), 2 = undecided.
+__device__ __forceinline__ int sphereTest(const Level& L, const float4& s, float tmin, float tmax, bool strict, float& t) {
+    const float3 f = L.o - make_float3(s.x, s.y, s.z);
+    const float a = dot3(L.d, L.d);
+    if (a == 0.f) return L.dD > 0.f ? 2 : 0;
+    const float b = dot3(f, L.d);
+    const float tca = b / a;
+    const float3 l = f - L.d * tca;
+    const float r2 = s.w * s.w;
+    const float D = r2 - dot3(l, l);
+    const float fn = dot3(f, f);
+    // position error at the closest approach, then its effect on r^2 - |l|^2
+    const float ep = 1.7320508f * (L.dO + fabsf(tca) * L.dD);
+    const float E = kBound * (fn + r2) + 4.f * sqrtf(fn) * ep + ep * ep;
+    if (D < -E) return 0;
+    if (D <= E) return 2;
+    const float c = fn - r2;
+    const float q = -b - copysignf(sqrtf(a * D), b);
+    float t0 = (q != 0.0f) ? c / q : 0.0f;
+    float t1 = q / a;
+    if (t0 > t1) {
+        const float x = t0;
+        t0 = t1;
+        t1 = x;
+    }
+    // roots near the ray's range ends are left to the undecided path
+    const float et = 8.f * kEps * (fabsf(t0) + fabsf(t1)) + 4.f * ep / sqrtf(a);
+    if (fabsf(t0 - tmin) <= et || fabsf(t1 - tmin) <= et) return 2;
+    if (t0 >= tmin && (strict ? t0 < tmax : t0 <= tmax)) {
+        t = t0;
+        return 1;
+    }
+    if (t1 >= tmin && (strict ? t1 < tmax : t1 <= tmax)) {
+        t = t1;
+        return 1;
+    }
+    return 0;
+}
+
+// FP64 sphere: smallest root of |o + t d - c|^2 = r^2 in range.
+__device__ __noinline__ bool sphereTest64(D3 o, D3 d, float4 s, double tmin, double tmax, bool strict, double& t) {
+    const D3 f = o - D3{(double)s.x, (double)s.y, (double)s.z};
+    const double a = dotd(d, d);
+    const double b = dotd(f, d);
+    const double rr = (double)s.w * (double)s.w;
+    const double c = dotd(f, f) - rr;
+    const double disc = b * b - a * c;
+    if (disc < 0.0 || a == 0.0) return false;
+    const double sq = sqrt(disc);
+    const double t0 = (-b - sq) / a, t1 = (-b + sq) / a;
+    if (t0 >= tmin && (strict ? t0 < tmax : t0 <= tmax)) {
+        t = t0;
+        return true;
+    }
+    if (t1 >= tmin && (strict ? t1 < tmax : t1 <= tmax)) {
+        t = t1;
+        return true;
+    }
+    return false;
+}
+
+// FP64 ray at the current level: the world ray itself, or its image under the
+// instance's FP64 inverse frame.
+__device__ __forceinline__ void ray64(const InstanceFrames64* inv64, bool inInstance, uint32_t inst, float3 wo, float3 wd,
+                                      D3& o, D3& d) {
+    if (!inInstance) {
+        o = d3(wo);
+        d = d3(wd);
+        return;
+    }
+    const InstanceFrames64& F = inv64[inst];
+    double r[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r[k] = F.inv[k][0] * (double)wo.x + F.inv[k][1] * (double)wo.y + F.inv[k][2] * (double)wo.z + F.inv[k][3];
+        r[3 + k] = F.inv[k][0] * (double)wd.x + F.inv[k][1] * (double)wd.y + F.inv[k][2] * (double)wd.z;
+    }
+    o = D3{r[0], r[1], r[2]};
+    d = D3{r[3], r[4], r[5]};
+}
+
+// Enter an instance: float32 object-space ray with bounds on its error (matrix
+// entries rounded from FP64 plus three rounded FMAs per component), and boxes
+// widened by the worst position error over the instance's parameter range.
+__device__ __forceinline__ void instanceLevel(Level& L, const InstanceRecord* R, float3 wo, float3 wd, float3 wid,
+                                              float tmin, float lim) {
+    const float4 m[3] = {R->inv[0], R->inv[1], R->inv[2]};
+    const float4 blo = R->worldLo, bhi = R->worldHi;
+    float o[3], d[3], so = 0.f, sd = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o[k] = fmaf(m[k].x, wo.x, fmaf(m[k].y, wo.y, fmaf(m[k].z, wo.z, m[k].w)));
+        d[k] = fmaf(m[k].x, wd.x, fmaf(m[k].y, wd.y, m[k].z * wd.z));
+        so = fmaxf(so, fabsf(m[k].x * wo.x) + fabsf(m[k].y * wo.y) + fabsf(m[k].z * wo.z) + fabsf(m[k].w));
+        sd = fmaxf(sd, fabsf(m[k].x * wd.x) + fabsf(m[k].y * wd.y) + fabsf(m[k].z * wd.z));
+    }
+    L.o = make_float3(o[0], o[1], o[2]);
+    L.d = make_float3(d[0], d[1], d[2]);
+    L.id = make_float3(__frcp_rn(d[0]), __frcp_rn(d[1]), __frcp_rn(d[2]));
+    L.dl1 = norm1(L.d);
+    L.dO = 6.f * kEps * so;
+    L.dD = 6.f * kEps * sd;
+    // exit parameter of the instance's world box (exact world ray, conservative)
+    const bool px = wid.x >= 0.f, py = wid.y >= 0.f, pz = wid.z >= 0.f;
+    const float fx = ((px ? bhi.x : blo.x) - wo.x) * wid.x;
+    const float fy = ((py ? bhi.y : blo.y) - wo.y) * wid.y;
+    const float fz = ((pz ? bhi.z : blo.z) - wo.z) * wid.z;
+    const float texit = fminf(fminf(fx, fy), fminf(fz, lim)) * kFarScale;
+    const float slack = L.dO + fmaxf(texit, tmin) * L.dD +
+                        2.f * kEps * fmaxf(fmaxf(fabsf(o[0]), fabsf(o[1])), fabsf(o[2]));
+    const float3 sg = make_float3(copysignf(slack, L.id.x), copysignf(slack, L.id.y), copysignf(slack, L.id.z));
+    L.on = L.o + sg;
+    L.of = L.o - sg;
+}
+
+struct Stack {
+    uint32_t* sh;
+    uint32_t* gl;
+    uint32_t shDepth, glDepth, stride, sp;
+    __device__ __forceinline__ bool push(uint32_t x) {
+        if (sp < shDepth) {
+            sh[sp * blockDim.x] = x;
+        } else if (sp < shDepth + glDepth) {
+            gl[(size_t)(sp - shDepth) * stride] = x;
+        } else {
+            return false;
+        }
+        ++sp;
+        return true;
+    }
+    __device__ __forceinline__ uint32_t pop() {
+        --sp;
+        return sp < shDepth ? sh[sp * blockDim.x] : gl[(size_t)(sp - shDepth) * stride];
+    }
+};
+
+// Per-ray work counts (only with COUNT): nodes, triangles, customs, instances, FP64 tests.
+struct Visits {
+    uint32_t nodes = 0, tris = 0, customs = 0, insts = 0, fp64 = 0;
+};
+
+__device__ __forceinline__ void flushVisits(unsigned long long* stats, const Visits& v) {
+    atomicAdd(&stats[0], 1ull);
+    atomicAdd(&stats[1], (unsigned long long)v.nodes);
+    atomicAdd(&stats[2], (unsigned long long)v.tris);
+    atomicAdd(&stats[3], (unsigned long long)v.customs);
+    atomicAdd(&stats[4], (unsigned long long)v.insts);
+    atomicAdd(&stats[5], (unsigned long long)v.fp64);
+}
+
+// One ray through the target. Returns the hit (prim == kInvalid on a miss).
+template <bool ANY, bool SCENE, bool COUNT = false>
+__device__ Hit traceRay(const TraceParams& P, Stack& st, float3 wo, float3 wd, float tmin, float tmax,
+                        Visits* vis = nullptr) {
+    Hit best{kInvalid, kInvalid, INFINITY, 0.f, 0.f};
+    if (P.target.empty) return best;
+    Level L;
+    exactLevel(L, wo, wd);
+    const float3 wid = L.id;
+    const float4* nodes = P.target.nodes;
+    const void* leaves = P.target.leaves;
+    uint32_t primType = P.target.primType, geomType = P.target.geomType, instId = 0;
+    bool inBlas = !SCENE;
+    bool found = false;
+    const float4* bestRec = nullptr;  // closest hit's leaf record (triangle) or sphere data
+    bool bestSphere = false;
+    uint32_t steps = 0;
+    uint32_t next = 0;
+    st.sp = 0;
+    for (;;) {
+        if (next == kNone) {
+            if (st.sp == 0) break;
+            next = st.pop();
+            if (SCENE && next == kSentinel) {  // back to the top level
+                exactLevel(L, wo, wd);
+                nodes = P.target.nodes;
+                inBlas = false;
+                next = kNone;
+                continue;
+            }
+        }
+        if (SCENE && !inBlas && (next & kLeafBit)) {  // enter an instance
+            const InstanceRecord* R = reinterpret_cast<const InstanceRecord*>(P.target.leaves) + (next & ~kLeafBit);
+            const uint32_t bits = R->typeBits;
+            next = kNone;
+            if (bits & kInstEmpty) continue;
+            if (!st.push(kSentinel)) {
+                latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+                continue;
+            }
+            if (COUNT) ++vis->insts;
+            instanceLevel(L, R, wo, wd, wid, tmin, (ANY || !found) ? tmax : best.t);
+            nodes = R->nodes;
+            leaves = R->leaves;
+            primType = instPrimType(bits);
+            geomType = instGeomType(bits);
+            instId = R->instanceID;
+            inBlas = true;
+            next = 0;
+            continue;
+        }
+        if (++steps > P.maxSteps) {
+            latchError(P.error, GRT_ERROR_STEP_LIMIT);
+            break;
+        }
+        if (COUNT) ++vis->nodes;
+        const float4* N = nodes + 4 * (size_t)next;
+        const float4 nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2), nc = __ldg(N + 3);
+        bool h0, h1;
+        float tn0, tn1;
+        slab2(nx, ny, nz, L, tmin, (ANY || !found) ? tmax : best.t, h0, h1, tn0, tn1);
+        const uint32_t c0 = __float_as_uint(nc.x), c1 = __float_as_uint(nc.y);
+        if (c1 == c0) h1 = false;  // a one-primitive level stores its leaf twice
+        next = kNone;
+        if (inBlas) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const bool h = side ? h1 : h0;
+                const uint32_t c = side ? c1 : c0;
+                if (!h || !(c & kLeafBit)) continue;
+                const uint32_t k = c & ~kLeafBit;
+                const bool strict = found && !ANY;
+                const float cur = (ANY || !found) ? tmax : best.t;
+                float t = 0.f, u = 0.f, v = 0.f;
+                uint32_t prim;
+                int res = 0;
+                const float4* rec;
+                bool sphere = false;
+                if (primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
+                    rec = reinterpret_cast<const float4*>(leaves) + 3 * (size_t)k;
+                    const float4 a = __ldg(rec), b = __ldg(rec + 1), e = __ldg(rec + 2);
+                    prim = __float_as_uint(a.w);
+                    res = triangleTest(L, f3(a), f3(b), f3(e), b.w, e.w, tmin, cur, strict, t, u, v);
+                    if (COUNT) ++vis->tris;
+                    if (res == 2) {
+                        if (COUNT) ++vis->fp64;
+                        D3 o64, d64;
+                        ray64(P.inv64, SCENE, instId, wo, wd, o64, d64);
+                        double t64, u64, v64;
+                        res = triangleTest64(o64, d64, f3(a), f3(b), f3(e), tmin, cur, strict, t64, u64, v64) ? 1 : 0;
+                        t = (float)t64, u = (float)u64, v = (float)v64;
+                    }
+                } else {
+                    prim = __ldg(reinterpret_cast<const uint32_t*>(leaves) + k);
+                    rec = nullptr;
+                    if (P.table && geomType < P.numGeomTypes) {
+                        const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + geomType];
+                        if (fe.func == GRT_INTERSECT_SPHERE) {
+                            rec = reinterpret_cast<const float4*>(fe.data) + prim;
+                            sphere = true;
+                            const float4 s = __ldg(rec);
+                            res = sphereTest(L, s, tmin, cur, strict, t);
+                            if (COUNT) ++vis->customs;
+                            if (res == 2) {
+                                if (COUNT) ++vis->fp64;
+                                D3 o64, d64;
+                                ray64(P.inv64, SCENE, instId, wo, wd, o64, d64);
+                                double t64;
+                                res = sphereTest64(o64, d64, s, tmin, cur, strict, t64) ? 1 : 0;
+                                t = (float)t64;
+                            }
+                        }
+                    }
+                }
+                if (res == 1) {
+                    best = Hit{instId, prim, t, u, v};
+                    bestRec = rec;
+                    bestSphere = sphere;
+                    found = true;
+                    if (ANY) return best;
+                }
+            }
+            if (c0 & kLeafBit) h0 = false;
+            if (c1 & kLeafBit) h1 = false;
+        }
+        if (h0 && h1) {
+            const bool swap = tn1 < tn0;
+            const uint32_t nearC = swap ? c1 : c0, farC = swap ? c0 : c1;
+            if (!st.push(farC)) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+            next = nearC;
+        } else if (h0) {
+            next = c0;
+        } else if (h1) {
+            next = c1;
+        }
+    }
+    if (!ANY && found && bestRec) {
+        // the reported distance and barycentrics, recomputed in FP64
+        D3 o64, d64;
+        ray64(P.inv64, SCENE, best.inst, wo, wd, o64, d64);
+        if (bestSphere) {
+            double t64;
+            if (sphereTest64(o64, d64, __ldg(bestRec), (double)tmin, (double)tmax, false, t64)) best.t = (float)t64;
+        } else {
+            double t64, u64, v64;
+            if (triangleRefine64(o64, d64, f3(__ldg(bestRec)), f3(__ldg(bestRec + 1)), f3(__ldg(bestRec + 2)), t64,
+                                 u64, v64)) {
+                best.t = (float)t64;
+                best.u = (float)u64;
+                best.v = (float)v64;
+            }
+        }
+    }
+    return best;
+}
+
+__device__ __forceinline__ void storeHit(uint32_t* hits, uint32_t r, const Hit& h) {
+    uint32_t* p = hits + 5 * (size_t)r;
+    p[0] = h.inst;
+    p[1] = h.prim;
+    p[2] = __float_as_uint(h.t);
+    p[3] = __float_as_uint(h.u);
+    p[4] = __float_as_uint(h.v);
+}
+
+// ---------------------------------------------------------------- ambient occlusion rays (Sec. 4)
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// splitmix64 value at counter (pixel << 32 | sample << 1 | dim) of stream `seed`, top 24 bits.
+__device__ __forceinline__ float sampleXi(uint64_t seed, uint64_t pixel, uint32_t sample, uint32_t dim) {
+    const uint64_t c = (pixel << 32) | ((uint64_t)sample << 1) | dim;
+    const uint64_t h = mix64(seed + (c + 1ull) * 0x9E3779B97F4A7C15ull);
+    return (float)(uint32_t)(h >> 40) * 5.9604644775390625e-8f;
+}
+
+struct AoFrame {
+    float3 org, n, tg, bt;
+};
+
+// World hit point, face normal turned toward the viewer, and the tangent frame of
+// the triangle a primary ray hit.
+__device__ __forceinline__ bool aoFrame(const InstanceRecord* sceneLeaves, const uint32_t* scenePrimToLeaf,
+                                        const float4* fwd32, const float4* ray, const uint32_t* hit, AoFrame& F) {
+    const uint32_t inst = hit[0], prim = hit[1];
+    if (prim == kInvalid) return false;
+    const InstanceRecord* R = sceneLeaves + scenePrimToLeaf[inst];
+    if (instPrimType(R->typeBits) != GRT_PRIMITIVE_TRIANGLE_MESH) return false;
+    const BvhHeader* g = R->geometry;
+    const float4* rec = reinterpret_cast<const float4*>(g->leaves) + 3 * (size_t)g->primToLeaf[prim];
+    const float4 m0 = fwd32[3 * (size_t)inst], m1 = fwd32[3 * (size_t)inst + 1], m2 = fwd32[3 * (size_t)inst + 2];
+    // world edges = linear part of the frame applied to object-space edges (no
+    // cancellation against the translation)
+    const float3 v0 = f3(rec[0]), a1 = f3(rec[1]) - v0, a2 = f3(rec[2]) - v0;
+    const float3 e1 = make_float3(m0.x * a1.x + m0.y * a1.y + m0.z * a1.z, m1.x * a1.x + m1.y * a1.y + m1.z * a1.z,
+                                  m2.x * a1.x + m2.y * a1.y + m2.z * a1.z);
+    const float3 e2 = make_float3(m0.x * a2.x + m0.y * a2.y + m0.z * a2.z, m1.x * a2.x + m1.y * a2.y + m1.z * a2.z,
+                                  m2.x * a2.x + m2.y * a2.y + m2.z * a2.z);
+    const float4 a = ray[0], b = ray[1];
+    const float3 o = f3(a), d = f3(b);
+    float3 n = normalize3(cross3(e1, e2));
+    if (dot3(n, d) > 0.0f) n = n * -1.0f;
+    F.n = n;
+    F.tg = normalize3(e1);
+    F.bt = cross3(n, F.tg);
+    const float t = __uint_as_float(hit[2]);
+    F.org = (o + d * t) + n * 1e-4f;
+    return true;
+}
+
+__device__ __forceinline__ float3 aoDirection(const AoFrame& F, uint64_t seed, uint64_t pixel, uint32_t s) {
+    const float xi0 = sampleXi(seed, pixel, s, 0), xi1 = sampleXi(seed, pixel, s, 1);
+    float sn, cs;
+    sincospif(2.0f * xi0, &sn, &cs);
+    const float r = sqrtf(xi1);
+    const float x = cs * r, z = sn * r, y = sqrtf(fmaxf(1.0f - r * r, 0.0f));
+    return F.tg * x + F.bt * z + F.n * y;
+}
+
+}  // namespace grt

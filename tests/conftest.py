@@ -15,3 +15,20 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA library and a context on device 0 (skips where no GPU is present)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_00292_gb300 import build as grt_build
+    from paper_2603_00292_gb300.objects import Context
+
+    grt_build.build()
+    ctx = Context(0)
+    yield ctx
+    torch.cuda.synchronize()
+    ctx.close()

@@ -1,0 +1,181 @@
+"""GPU LBVH build vs the oracle: Morton codes, sort order, topology, parent links,
+boxes and leaf records must be bit-exact (CUDA path called through the C ABI)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2603_00292_gb300 as grt
+import scenegen
+from paper_2603_00292_gb300.objects import Geometry, device_tensor, empty_bytes, read_device
+
+pytestmark = pytest.mark.gpu
+
+LEAF = 0x80000000
+
+
+def _read(ptr: int, nbytes: int, dtype) -> np.ndarray:
+    return read_device(ptr, nbytes, dtype)
+
+
+def _tensor_bytes(t: torch.Tensor, offset: int, nbytes: int, dtype) -> np.ndarray:
+    return t[offset:offset + nbytes].cpu().numpy().view(dtype).copy()
+
+
+def _case(name):
+    if name == "icosphere":
+        m = scenegen.icosphere(3)
+        return dict(vertices=m.vertices, indices=m.indices)
+    if name == "terrain":
+        m = scenegen.terrain(cells=90, amplitude=0.2)
+        return dict(vertices=m.vertices, indices=m.indices)
+    if name == "flat":  # many identical y, exercises zero extent
+        m = scenegen.terrain(cells=40, amplitude=0.0)
+        return dict(vertices=m.vertices, indices=m.indices)
+    if name == "spheres":
+        s = scenegen.spheres(50_003, half=20.0, config=91)
+        return dict(boxes=scenegen.sphere_aabbs(s))
+    if name == "dupes":  # many primitives sharing one centroid -> equal Morton codes
+        rng = np.random.default_rng(4)
+        c = rng.integers(0, 4, (9000, 3)).astype(np.float32)
+        b = np.concatenate([c - 0.25, c + 0.25], axis=1).astype(np.float32)
+        return dict(boxes=b)
+    if name.startswith("n"):
+        n = int(name[1:])
+        rng = np.random.default_rng(n)
+        c = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+        return dict(boxes=np.concatenate([c - 0.1, c + 0.1], axis=1).astype(np.float32))
+    raise KeyError(name)
+
+
+def _oracle_for(case):
+    if "boxes" in case:
+        b = case["boxes"]
+        lo, hi = b[:, :3].copy(), b[:, 3:].copy()
+        c = oracle.box_centroids(b)
+    else:
+        lo, hi, c = oracle.triangle_aabbs(case["vertices"], case["indices"])
+    return lo, hi, c
+
+
+@pytest.mark.parametrize("name", ["icosphere", "terrain", "flat", "spheres", "dupes", "n1", "n2", "n3", "n17",
+                                  "n4097"])
+@pytest.mark.parametrize("bits", [30, 63])
+def test_build_matches_oracle_bit_exact(gpu, name, bits):
+    case = _case(name)
+    dev = {k: device_tensor(v) for k, v in case.items()}
+    g = Geometry(gpu, morton_bits=bits, **dev).build()
+    torch.cuda.synchronize()
+    info = g.info()
+    n = info.primCount
+    lo, hi, cen = _oracle_for(case)
+    ref = oracle.lbvh(lo, hi, cen, 10 if bits == 30 else 21)
+    assert info.mortonBits == bits
+    # sorted keys and order from the temporary buffer
+    koff, voff, boff = grt.grtGetBuildTemporaryLayout(n, bits)
+    kdt = np.uint32 if bits == 30 else np.uint64
+    keys = _tensor_bytes(g.temp, koff, n * (4 if bits == 30 else 8), kdt)
+    order = _tensor_bytes(g.temp, voff, n * 4, np.uint32)
+    assert np.array_equal(keys.astype(np.uint64), ref["sorted_codes"]), "Morton codes / sort"
+    assert np.array_equal(order, ref["order"]), "stable sort order"
+    nodes = _read(info.nodes, info.nodeCount * 64, np.float32).reshape(-1, 16)
+    children = nodes.view(np.uint32)[:, 12:14]
+    if n == 1:
+        assert children.tolist() == [[LEAF, LEAF]]
+        assert np.array_equal(nodes[0, [0, 4, 8]], lo[0]) and np.array_equal(nodes[0, [1, 5, 9]], hi[0])
+        return
+    cl = ref["childL"].view(np.uint32)
+    cr = ref["childR"].view(np.uint32)
+    assert np.array_equal(children[:, 0], cl) and np.array_equal(children[:, 1], cr), "topology"
+
+    def child_box(c):
+        c = np.asarray(c, np.uint32)
+        leaf = (c & LEAF) != 0
+        idx = (c & 0x7FFFFFFF).astype(np.int64)
+        blo = np.where(leaf[:, None], ref["leaf_lo"][np.minimum(idx, n - 1)], ref["node_lo"][np.minimum(idx, n - 2)])
+        bhi = np.where(leaf[:, None], ref["leaf_hi"][np.minimum(idx, n - 1)], ref["node_hi"][np.minimum(idx, n - 2)])
+        return blo, bhi
+
+    l0, h0 = child_box(cl)
+    l1, h1 = child_box(cr)
+    # node rows: x = (c0.lo, c0.hi, c1.lo, c1.hi) at 0..3, y at 4..7, z at 8..11
+    assert np.array_equal(nodes[:, [0, 4, 8]], l0) and np.array_equal(nodes[:, [1, 5, 9]], h0), "left boxes"
+    assert np.array_equal(nodes[:, [2, 6, 10]], l1) and np.array_equal(nodes[:, [3, 7, 11]], h1), "right boxes"
+    # parent links: (parent << 1 | side), root marked invalid
+    par = _read(info.parents, (2 * n - 1) * 4, np.uint32)
+    assert par[0] == 0xFFFFFFFF
+    for k in range(n - 1):
+        for side, c in enumerate((cl[k], cr[k])):
+            slot = (n - 1 + (c & 0x7FFFFFFF)) if c & LEAF else c
+            assert par[slot] == (k << 1 | side)
+    # leaves
+    if "indices" in case:
+        rec = _read(info.leaves, n * 48, np.float32).reshape(n, 12)
+        prim = rec[:, 3].view(np.uint32)
+        assert np.array_equal(prim, ref["order"])
+        v = case["vertices"][case["indices"][ref["order"]]]  # (n,3,3)
+        assert np.array_equal(rec[:, 0:3], v[:, 0]) and np.array_equal(rec[:, 4:7], v[:, 1])
+        assert np.array_equal(rec[:, 8:11], v[:, 2])
+    else:
+        ids = _read(info.leaves, n * 4, np.uint32)
+        assert np.array_equal(ids, ref["order"])
+    g.close()
+
+
+def test_rebuild_is_deterministic(gpu):
+    case = _case("spheres")
+    b = device_tensor(case["boxes"])
+    g1 = Geometry(gpu, boxes=b, morton_bits=30).build()
+    g2 = Geometry(gpu, boxes=b, morton_bits=30).build()
+    torch.cuda.synchronize()
+    i1, i2 = g1.info(), g2.info()
+    a = _read(i1.nodes, i1.nodeCount * 64, np.uint8)
+    c = _read(i2.nodes, i2.nodeCount * 64, np.uint8)
+    assert np.array_equal(a, c)
+
+
+def test_refit_after_moving_vertices(gpu):
+    m = scenegen.terrain(cells=32, amplitude=0.2)
+    v = device_tensor(m.vertices)
+    g = Geometry(gpu, vertices=v, indices=device_tensor(m.indices), morton_bits=30).build()
+    moved = m.vertices.copy()
+    moved[:, 1] *= 3.0
+    moved[:, 0] += 0.01 * np.sin(np.arange(len(moved)))
+    v.copy_(torch.from_numpy(moved))
+    g.build(op=grt.GRT_BUILD_OPERATION_UPDATE)
+    torch.cuda.synchronize()
+    info = g.info()
+    n = info.primCount
+    # topology kept, boxes refit from children: compare with the oracle fit on the same order
+    lo, hi, cen = oracle.triangle_aabbs(m.vertices, m.indices)
+    ref = oracle.lbvh(lo, hi, cen, 10)
+    lo2, hi2, _ = oracle.triangle_aabbs(moved, m.indices)
+    nlo, nhi = oracle.fit(ref["childL"], ref["childR"], lo2[ref["order"]], hi2[ref["order"]])
+    nodes = _read(info.nodes, info.nodeCount * 64, np.float32).reshape(-1, 16)
+    assert np.array_equal(nodes.view(np.uint32)[:, 12], ref["childL"].view(np.uint32))
+    root_lo = np.minimum(nodes[0, [0, 4, 8]], nodes[0, [2, 6, 10]])
+    root_hi = np.maximum(nodes[0, [1, 5, 9]], nodes[0, [3, 7, 11]])
+    assert np.array_equal(root_lo, nlo[0]) and np.array_equal(root_hi, nhi[0])
+    internal = ref["childL"] >= 0
+    k = np.nonzero(internal)[0]
+    cidx = ref["childL"][k]
+    assert np.array_equal(nodes[k][:, [0, 4, 8]], nlo[cidx]) and np.array_equal(nodes[k][:, [1, 5, 9]], nhi[cidx])
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 4096, 4097, 100_003, 1_000_003])
+@pytest.mark.parametrize("key_bits", [32, 64])
+def test_radix_sort_is_stable(gpu, n, key_bits):
+    rng = np.random.default_rng(n + key_bits)
+    hi = 1 << (20 if n > 1000 else 3)
+    keys = rng.integers(0, hi, n, dtype=np.uint64)
+    if key_bits == 64:
+        keys = keys | (rng.integers(0, 4, n, dtype=np.uint64) << np.uint64(60))
+    kd = np.uint32 if key_bits == 32 else np.uint64
+    k = device_tensor(keys.astype(kd).view(np.int32 if key_bits == 32 else np.int64))
+    v = device_tensor(np.arange(n, dtype=np.int32))
+    temp = empty_bytes(grt.grtSortTemporaryBufferSize(n, key_bits))
+    grt.grtSortPairs(gpu.handle, k, v, n, key_bits, 62 if key_bits == 64 else 32, temp)
+    torch.cuda.synchronize()
+    order = np.argsort(keys.astype(kd), kind="stable")
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
+    assert np.array_equal(k.cpu().numpy().view(kd), keys.astype(kd)[order])
