@@ -246,6 +246,34 @@ grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* optio
  * NULL (defaults). */
 grtError grtTraceClosest(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
                          grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream);
+/* The same closest-hit query as grtTraceClosest for callers that must not allocate
+ * device memory: code running while a stream is being captured into a CUDA graph
+ * (where cudaMalloc is not allowed), code whose memory is fully owned by another
+ * allocator or reserved up front, and latency-critical loops that cannot afford the
+ * device-wide synchronisation a cudaMalloc or cudaFree implies. grtTraceClosest may
+ * grow the context's global-stack area with cudaMalloc; this entry point never
+ * allocates or frees anything. (The paper has no counterpart: it is an addition of
+ * this library.)
+ *
+ * Its scratch (work counter and global traversal stack) is a 16 MiB array that the
+ * library keeps resident on every device that loads it, until the process exits.
+ * The caller still provides rays, hits and the built scene or geometry, as for
+ * grtTraceClosest; options->globalStack is ignored. The persistent grid is reduced
+ * so that every thread's global stack fits the array, down to one block per SM
+ * (or one block per blockSize rays, if that is fewer). A request that cannot fit
+ * that minimum grid (blocks * blockSize * globalStackDepth * 4 bytes > 16 MiB - 256;
+ * with 152 SMs and 128-thread blocks, globalStackDepth above 215) is rejected with
+ * GRT_ERROR_INVALID_PARAMETER and a logged message.
+ *
+ * The first call on each device looks up the array's device address and caches it;
+ * make that first call before any stream capture begins. Every call shares the one
+ * array (the work counter is cleared on `stream` at the start of each call): calls
+ * that overlap on the GPU race, so serialise them on one stream or order them with
+ * events. The device current at the call must be the context's. */
+grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays,
+                                uint32_t rayCount, grtHit* hits, grtFuncTable table, const grtTraceOptions* options,
+                                void* stream);
+
 /* Any hit in [minT, maxT]: primID = GRT_INVALID_ID means unoccluded; otherwise the
  * record describes one (not necessarily the closest) valid hit. */
 grtError grtTraceAnyHit(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,

@@ -127,6 +127,7 @@ _SIGS = {
     "grtGetTraceGlobalStackSize": [_P, ctypes.POINTER(grtTraceOptions), ctypes.POINTER(ctypes.c_size_t)],
     "grtTraceClosest": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
     "grtTraceAnyHit": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
+    "grtTraceClosestNoAlloc": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
     "grtGenerateCameraRays": [_P, ctypes.POINTER(grtCamera), _U32, _U32, _P, _P],
     "grtGenerateAORays": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P, _P],
     "grtTraceAmbientOcclusion": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P,
@@ -311,6 +312,15 @@ def grtTraceClosest(ctx, scene, geom, rays, count, hits, table=None, opts=None, 
 def grtTraceAnyHit(ctx, scene, geom, rays, count, hits, table=None, opts=None, stream=None):
     check(lib().grtTraceAnyHit(ctx, scene, geom, _ptr(rays), count, _ptr(hits), table,
                                ctypes.byref(opts) if opts else None, _stream(stream)), "grtTraceAnyHit")
+
+
+def grtTraceClosestNoAlloc(ctx, scene, geom, rays, count, hits, table=None, opts=None, stream=None):
+    """Closest hit without any device allocation (scratch in the library's static
+    16 MiB device array): for callers that cannot call cudaMalloc, e.g. during CUDA
+    graph capture or under an allocator that owns all device memory."""
+    check(lib().grtTraceClosestNoAlloc(ctx, scene, geom, _ptr(rays), count, _ptr(hits), table,
+                                       ctypes.byref(opts) if opts else None, _stream(stream)),
+          "grtTraceClosestNoAlloc")
 
 
 def camera(origin, right, up) -> grtCamera:

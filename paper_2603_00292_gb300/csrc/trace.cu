@@ -227,11 +227,94 @@ static grtError launchTrace(grtContext ctx, grtScene scene, grtGeometry geom, co
     return GRT_SUCCESS;
 }
 
+// ---------------------------------------------------------------- allocation-free closest hit
+// Scratch of grtTraceClosestNoAlloc, resident on every device that loads the library:
+// bytes [0, 256) hold the work counter, the rest the traversal's global stack.
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+constexpr size_t kNoAllocStackOffset = 256;
+static __device__ __align__(256) unsigned char g_noAllocScratch[kNoAllocScratchBytes];
+
+static std::mutex g_noAllocMutex;
+static std::unordered_map<int, void*> g_noAllocAddress;  // device ordinal -> device address of the array
+
+// Device address of the scratch array on the current device. Host code cannot use the
+// array's name as an address (it names a host-side stand-in), so the address is
+// looked up once per device with that device current and cached.
+static grtError noAllocScratchAddress(int device, void** out) {
+    std::lock_guard<std::mutex> g(g_noAllocMutex);
+    auto it = g_noAllocAddress.find(device);
+    if (it != g_noAllocAddress.end()) {
+        *out = it->second;
+        return GRT_SUCCESS;
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noAllocScratch);
+    if (e != cudaSuccess || p == nullptr) {
+        logf(GRT_LOG_ERROR, "grtTraceClosestNoAlloc: scratch address lookup failed: %s", cudaGetErrorString(e));
+        return GRT_ERROR_CUDA;
+    }
+    g_noAllocAddress[device] = p;
+    *out = p;
+    return GRT_SUCCESS;
+}
+
 }  // namespace grt
 
 using namespace grt;
 
 extern "C" {
+
+grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays,
+                                uint32_t rayCount, grtHit* hits, grtFuncTable table, const grtTraceOptions* options,
+                                void* stream) {
+    if (!ctx) return GRT_ERROR_INVALID_PARAMETER;
+    if (rayCount && (!rays || !hits || ((uintptr_t)rays & 15))) return GRT_ERROR_INVALID_PARAMETER;
+    Context* c = asContext(ctx);
+    int device = -1;
+    GRT_CUDA(cudaGetDevice(&device));
+    if (device != deviceOf(c)) return GRT_ERROR_INVALID_PARAMETER;
+    TraceParams P{};
+    bool isScene = false;
+    int bs = 128;
+    grtError e = prepareTrace(c, scene, geom, table, options, P, &isScene, &bs);
+    if (e != GRT_SUCCESS || rayCount == 0) return e;
+    // the grid keeps at least one block per SM (fewer only when there are fewer rays)
+    const size_t capacity = kNoAllocScratchBytes - kNoAllocStackOffset;
+    const size_t perBlock = (size_t)bs * P.globalDepth * sizeof(uint32_t);
+    const size_t minBlocks = std::min<size_t>((size_t)smCount(c), ceilDiv(rayCount, bs));
+    if (perBlock * minBlocks > capacity) {
+        logf(GRT_LOG_ERROR,
+             "grtTraceClosestNoAlloc: %zu blocks of %d threads with globalStackDepth %u need %zu bytes of global "
+             "stack, more than the %zu-byte static scratch",
+             minBlocks, bs, P.globalDepth, perBlock * minBlocks, capacity);
+        return GRT_ERROR_INVALID_PARAMETER;
+    }
+    void* base = nullptr;
+    e = noAllocScratchAddress(device, &base);
+    if (e != GRT_SUCCESS) return e;
+    const bool count = options && (options->flags & GRT_TRACE_FLAG_COUNT);
+    P.rays = (const float4*)rays;
+    P.hits = (uint32_t*)hits;
+    P.count = rayCount;
+    void (*kernel)(TraceParams) = nullptr;
+    if (count)
+        traceKernelFor<false, true>(isScene, &kernel);
+    else
+        traceKernelFor<false, false>(isScene, &kernel);
+    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    LaunchShape L = persistentShape(c, kernel, bs, smem);
+    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(rayCount, bs));
+    L.blocks = std::max(1, std::min<int>(L.blocks, (int)(capacity / perBlock)));  // the grid shrinks to fit
+    P.counter = reinterpret_cast<unsigned long long*>(base);
+    P.globalStack = reinterpret_cast<uint32_t*>(static_cast<char*>(base) + kNoAllocStackOffset);
+    P.globalStride = (uint32_t)(L.blocks * bs);
+    cudaStream_t s = (cudaStream_t)stream;
+    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));  // the work counter starts at zero
+    kernel<<<L.blocks, bs, smem, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
 
 grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* options, size_t* sizeBytes) {
     if (!ctx || !sizeBytes) return GRT_ERROR_INVALID_PARAMETER;
