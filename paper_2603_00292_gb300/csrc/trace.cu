@@ -9,28 +9,70 @@
 
 namespace grt {
 
-// Persistent kernel: warps take 32 rays at a time from a global counter until the
-// batch is exhausted.
+// Persistent refill loop shared by the query kernels (warp-level ray compaction):
+// each lane owns one work item and advances its ray one traversal step per iteration;
+// when the warp's live lanes drop to P.refillBelow or fewer, the idle lanes take fresh
+// items from the global queue with one atomic per warp, so short rays do not leave
+// lanes idle while long ones finish. Src supplies the items:
+//   count()             number of items (may be read from device memory)
+//   begin(i, P, st, s)  set up item i's ray in s; false if the item has no ray
+//   finish(i, s)        consume item i's result s.best
+template <bool ANY, bool SCENE, bool COUNT, class Src>
+__device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src& src) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t ltMask = (1u << lane) - 1u;
+    const unsigned long long total = src.count();
+    RayState s;
+    Visits v;
+    uint32_t item = kNone;
+    bool exhausted = false;
+    for (;;) {
+        uint32_t live = __ballot_sync(0xffffffffu, item != kNone);
+        while (!exhausted && (uint32_t)__popc(live) <= P.refillBelow) {
+            const uint32_t idle = ~live;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)__popc(idle));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + __popc(idle) >= total) exhausted = true;
+            if (item == kNone) {
+                const unsigned long long mine = base + __popc(idle & ltMask);
+                if (mine < total && src.begin((uint32_t)mine, P, st, s)) {
+                    item = (uint32_t)mine;
+                    if (COUNT) v = Visits{};
+                }
+            }
+            live = __ballot_sync(0xffffffffu, item != kNone);
+        }
+        if (live == 0) break;
+        if (item != kNone && stepRay<ANY, SCENE, COUNT>(P, st, s, &v)) {
+            src.finish(item, s);
+            if (COUNT) flushVisits(P.stats, v);
+            item = kNone;
+        }
+    }
+}
+
+// Items = rays of a ray buffer; results = hit records.
+template <bool SCENE>
+struct RayBufferSource {
+    uint32_t n;
+    __device__ unsigned long long count() const { return n; }
+    __device__ bool begin(uint32_t i, const TraceParams& P, Stack& st, RayState& s) const {
+        const float4 a = P.rays[2 * (size_t)i], b = P.rays[2 * (size_t)i + 1];
+        beginRay<SCENE>(P, st, s, f3(a), f3(b), a.w, b.w);
+        return true;
+    }
+    const TraceParams* P;
+    __device__ void finish(uint32_t i, const RayState& s) const { storeHit(P->hits, i, s.best); }
+};
+
 template <bool ANY, bool SCENE, bool COUNT>
 __global__ void traceKernel(TraceParams P) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
-    const uint32_t lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(P.counter, 32ull);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= P.count) break;
-        const uint32_t r = (uint32_t)base + lane;
-        if (r < P.count) {
-            const float4 a = P.rays[2 * (size_t)r], b = P.rays[2 * (size_t)r + 1];
-            Visits v;
-            const Hit h = traceRay<ANY, SCENE, COUNT>(P, st, f3(a), f3(b), a.w, b.w, &v);
-            storeHit(P.hits, r, h);
-            if (COUNT) flushVisits(P.stats, v);
-        }
-    }
+    RayBufferSource<SCENE> src{P.count, &P};
+    refillLoop<ANY, SCENE, COUNT>(P, st, src);
 }
 
 // ---------------------------------------------------------------- ambient occlusion (Sec. 4)
@@ -54,35 +96,63 @@ __global__ void aoRayKernel(const InstanceRecord* sceneLeaves, const uint32_t* s
     }
 }
 
-// Fused AO: one thread per pixel, the pixel's samples traced in turn as any-hit
-// queries; no ray buffer is stored.
+// Fused ambient occlusion in three launches, with no ray buffer:
+//  1. aoCompactKernel: pixels with a primary hit are appended to a list (one atomic
+//     per warp); every pixel's occlusion count starts at 0 (kept in ao's words);
+//  2. aoTraceKernel: the refill loop over the list's (pixel, sample) items; each
+//     item's ray is generated in registers and traced as an any-hit query, and an
+//     occluded sample adds 1 to its pixel's count;
+//  3. aoFinishKernel: ao = count / samplesPerPixel for the listed pixels.
+__global__ void aoCompactKernel(const uint32_t* __restrict__ hits, uint32_t pixels, uint32_t* __restrict__ list,
+                                uint32_t* __restrict__ listCount, uint32_t* __restrict__ counts) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool hit = p < pixels && hits[5 * (size_t)p + 1] != kInvalid;
+    if (p < pixels) counts[p] = 0u;
+    const uint32_t mask = __ballot_sync(0xffffffffu, hit);
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == 0 && mask) base = atomicAdd(listCount, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (hit) list[base + __popc(mask & ((1u << lane) - 1u))] = p;
+}
+
+struct AoSource {
+    const TraceParams* P;
+    const uint32_t* list;
+    const uint32_t* listCount;
+    uint32_t* counts;
+    __device__ unsigned long long count() const { return (unsigned long long)*listCount * P->spp; }
+    __device__ bool begin(uint32_t i, const TraceParams& Pm, Stack& st, RayState& s) const {
+        const uint32_t slot = i / Pm.spp, smp = i - slot * Pm.spp;
+        const uint32_t p = list[slot];
+        AoFrame F;
+        if (!aoFrame(Pm.sceneLeaves, Pm.scenePrimToLeaf, Pm.fwd32, Pm.primaryRays + 2 * (size_t)p,
+                     Pm.primaryHits + 5 * (size_t)p, F))
+            return false;
+        beginRay<true>(Pm, st, s, F.org, aoDirection(F, Pm.seed, p, smp), 0.0f, Pm.aoLength);
+        return true;
+    }
+    __device__ void finish(uint32_t i, const RayState& s) const {
+        if (s.best.prim != kInvalid) atomicAdd(&counts[list[i / P->spp]], 1u);
+    }
+};
+
 template <bool COUNT>
-__global__ void aoTraceKernel(TraceParams P) {
+__global__ void aoTraceKernel(TraceParams P, const uint32_t* list, const uint32_t* listCount, uint32_t* counts) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
-    const uint32_t lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(P.counter, 32ull);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= P.count) break;
-        const uint32_t p = (uint32_t)base + lane;
-        if (p < P.count) {
-            AoFrame F;
-            uint32_t occluded = 0;
-            if (aoFrame(P.sceneLeaves, P.scenePrimToLeaf, P.fwd32, P.primaryRays + 2 * (size_t)p,
-                        P.primaryHits + 5 * (size_t)p, F)) {
-                for (uint32_t s = 0; s < P.spp; ++s) {
-                    const float3 dir = aoDirection(F, P.seed, p, s);
-                    Visits v;
-                    const Hit h = traceRay<true, true, COUNT>(P, st, F.org, dir, 0.0f, P.aoLength, &v);
-                    occluded += (h.prim != kInvalid) ? 1u : 0u;
-                    if (COUNT) flushVisits(P.stats, v);
-                }
-            }
-            P.ao[p] = (float)occluded / (float)P.spp;
-        }
+    AoSource src{&P, list, listCount, counts};
+    refillLoop<true, true, COUNT>(P, st, src);
+}
+
+__global__ void aoFinishKernel(const uint32_t* __restrict__ list, const uint32_t* __restrict__ listCount,
+                               uint32_t spp, float* ao) {
+    const uint32_t n = *listCount;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t p = list[i];
+        const uint32_t k = __float_as_uint(ao[p]);  // the occlusion count
+        ao[p] = (float)k / (float)spp;
     }
 }
 
@@ -155,6 +225,8 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     P.target.geomType = o->geomType;
     P.target.empty = o->primCount == 0;
     P.maxSteps = 1u << 26;  // far above any legitimate walk; stops a corrupted (cyclic) hierarchy
+    const float compact = (opt && opt->compactThreshold > 0.f) ? fminf(opt->compactThreshold, 1.f) : 0.5f;
+    P.refillBelow = (uint32_t)(compact * 32.f);
     P.inv64 = o->inv64;
     if (table) {
         FuncTableObject* t = findFuncTable(table);
@@ -174,17 +246,24 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     return GRT_SUCCESS;
 }
 
-static grtError bindGlobalStack(Context* c, const grtTraceOptions* opt, int threads, TraceParams& P) {
-    const size_t need = (size_t)threads * P.globalDepth * sizeof(uint32_t);
+// Global stack for `threads` threads (the caller's buffer or the context's scratch),
+// plus optionally `extraBytes` more of context scratch returned in *extra.
+static grtError bindGlobalStack(Context* c, const grtTraceOptions* opt, int threads, TraceParams& P,
+                                size_t extraBytes = 0, void** extra = nullptr) {
+    const size_t need = alignUp((size_t)threads * P.globalDepth * sizeof(uint32_t), 256);
     P.globalStride = (uint32_t)threads;
+    void* p = nullptr;
     if (opt && opt->globalStack) {
         if (opt->globalStackBytes < need) return GRT_ERROR_INVALID_PARAMETER;
         P.globalStack = (uint32_t*)opt->globalStack;
-        return GRT_SUCCESS;
+        if (!extraBytes) return GRT_SUCCESS;
+        grtError e = contextScratch(c, extraBytes, &p);
+        *extra = p;
+        return e;
     }
-    void* p = nullptr;
-    grtError e = contextScratch(c, std::max<size_t>(need, 256), &p);
+    grtError e = contextScratch(c, std::max<size_t>(need + extraBytes, 256), &p);
     P.globalStack = (uint32_t*)p;
+    if (extraBytes) *extra = static_cast<char*>(p) + need;
     return e;
 }
 
@@ -405,19 +484,29 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
     P.seed = seed;
     P.aoLength = length;
     P.ao = ao;
+    if ((size_t)pixelCount * samplesPerPixel > 0xFFFFFFFEull) return GRT_ERROR_INVALID_PARAMETER;
     const bool count = options && (options->flags & GRT_TRACE_FLAG_COUNT);
-    void (*kernel)(TraceParams) = count ? aoTraceKernel<true> : aoTraceKernel<false>;
+    void (*kernel)(TraceParams, const uint32_t*, const uint32_t*, uint32_t*) =
+        count ? aoTraceKernel<true> : aoTraceKernel<false>;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
-    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(pixelCount, bs));
-    e = bindGlobalStack(c, options, L.blocks * bs, P);
+    // scratch after the global stack: the hit count (256 B) and the list of hit pixels
+    void* extra = nullptr;
+    e = bindGlobalStack(c, options, L.blocks * bs, P, 256 + 4 * (size_t)pixelCount, &extra);
     if (e != GRT_SUCCESS) return e;
+    uint32_t* listCount = static_cast<uint32_t*>(extra);
+    uint32_t* list = reinterpret_cast<uint32_t*>(static_cast<char*>(extra) + 256);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(ao);
     P.counter = nextCounter(c);
     GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
-    kernel<<<L.blocks, bs, smem, s>>>(P);
+    GRT_CUDA(cudaMemsetAsync(listCount, 0, sizeof(uint32_t), s));
+    aoCompactKernel<<<ceilDiv(pixelCount, 256), 256, 0, s>>>((const uint32_t*)primaryHits, pixelCount, list, listCount,
+                                                            counts);
+    kernel<<<L.blocks, bs, smem, s>>>(P, list, listCount, counts);
+    aoFinishKernel<<<smCount(c) * 4, 256, 0, s>>>(list, listCount, samplesPerPixel, ao);
     GRT_LAUNCH_CHECK();
-    noteLaunches(1);
+    noteLaunches(3);
     return GRT_SUCCESS;
 }
 

@@ -31,9 +31,10 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr float kEps = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of float32
 // 1 + 2*gamma(3) rounded up, gamma(n) = n*eps/(1 - n*eps)
 constexpr float kFarScale = 1.0000005f;
-// coefficient of the rounding terms of the triangle / sphere error bounds (about 4x
-// the worst-case count of roundings in each expression)
-constexpr float kBound = 32.0f * kEps;
+// coefficients of the rounding terms of the triangle and sphere error bounds (see
+// triangleTest and sphereTest)
+constexpr float kBound = 8.0f * kEps;
+constexpr float kSphereBound = 24.0f * kEps;
 
 struct TraceTarget {
     const float4* nodes;  // top-level nodes (scene) or the geometry's nodes
@@ -58,6 +59,7 @@ struct TraceParams {
     unsigned long long* counter;
     uint32_t* error;
     uint32_t maxSteps;
+    uint32_t refillBelow;           // refill a warp when at most this many lanes hold a ray
     const InstanceFrames64* inv64;  // scene: FP64 inverse frames by instance ID
     unsigned long long* stats;      // counting variants: grtTraceStatistics sums
     // fused ambient occlusion
@@ -101,12 +103,14 @@ __device__ __forceinline__ D3 crossd(D3 a, D3 b) {
     return D3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
-// Ray state at the current level.
+// Ray state at the current level. The level's origin o sits at world parameter tOff,
+// so a local parameter t' on this level is the world parameter tOff + t'.
 struct Level {
     float3 o, d, id;  // float32 ray and reciprocal direction
     float3 on, of;    // origins for the near and far slab planes (box widening applied)
     float dO, dD;     // bounds on the error of each origin / direction component
     float dl1;        // |d|_1
+    float tOff;       // world parameter of o
 };
 
 __device__ __forceinline__ void exactLevel(Level& L, float3 o, float3 d) {
@@ -118,6 +122,16 @@ __device__ __forceinline__ void exactLevel(Level& L, float3 o, float3 d) {
     L.dO = 0.f;
     L.dD = 0.f;
     L.dl1 = norm1(d);
+    L.tOff = 0.f;
+}
+
+// World parameter range [a, b] as a local range on level L, widened by the rounding of
+// the subtraction.
+__device__ __forceinline__ float localLo(const Level& L, float a) {
+    return L.tOff == 0.f ? a : (a - L.tOff) - kEps * (fabsf(a) + fabsf(L.tOff));
+}
+__device__ __forceinline__ float localHi(const Level& L, float b) {
+    return L.tOff == 0.f ? b : (b - L.tOff) + kEps * (fabsf(b) + fabsf(L.tOff));
 }
 
 // Slab test of both children of a node.
@@ -139,7 +153,10 @@ __device__ __forceinline__ void slab2(const float4& nx, const float4& ny, const 
 }
 
 // Float32 Moller-Trumbore with certified bounds on the three edge values.
-// Returns 0 = miss, 1 = hit with t in range (t, u, v set), 2 = undecided in float32.
+// Returns 0 = miss, 1 = hit with world t in [tmin, tmax] (t, u, v set), 2 = undecided
+// in float32. Rounding bound: T, e2 and the cross product each contribute at most u
+// times their magnitude and the dot product 3u, so |U - U*| <= 7u * sum|T_i|(|d_j||e2_k|
+// + |d_k||e2_j|) <= 7u * |T|_1 |d|_1 |e2|_1 (likewise for V and det); kBound = 8u.
 __device__ __forceinline__ int triangleTest(const Level& L, float3 v0, float3 v1, float3 v2, float e1n, float e2n,
                                            float tmin, float tmax, bool strict, float& t, float& u, float& v) {
     const float3 e1 = v1 - v0, e2 = v2 - v0;
@@ -162,14 +179,14 @@ __device__ __forceinline__ int triangleTest(const Level& L, float3 v0, float3 v1
     const float EW = Edet + EU + EV + 4.f * kEps * (ad + fabsf(U) + fabsf(V));
     if (W < -EW) return 0;
     if (U <= EU || V <= EV || W <= EW) return 2;
-    t = dot3(e2, Q) / det;
+    t = dot3(e2, Q) / det + L.tOff;
     u = U / ad;
     v = V / ad;
     return (t >= tmin && (strict ? t < tmax : t <= tmax)) ? 1 : 0;
 }
 
 // FP64 Moller-Trumbore with the same acceptance rules (u in [0,1], v >= 0, u+v <= 1).
-__device__ __noinline__ bool triangleTest64(D3 o, D3 d, float3 v0f, float3 v1f, float3 v2f, double tmin, double tmax,
+__device__ __forceinline__ bool triangleTest64(D3 o, D3 d, float3 v0f, float3 v1f, float3 v2f, double tmin, double tmax,
                                             bool strict, double& t, double& u, double& v) {
     const D3 v0 = d3(v0f), e1 = d3(v1f) - v0, e2 = d3(v2f) - v0;
     const D3 P = crossd(d, e2);
@@ -187,7 +204,7 @@ __device__ __noinline__ bool triangleTest64(D3 o, D3 d, float3 v0f, float3 v1f, 
 }
 
 // FP64 barycentrics and distance of a known hit (no acceptance test).
-__device__ __noinline__ bool triangleRefine64(D3 o, D3 d, float3 v0f, float3 v1f, float3 v2f, double& t, double& u,
+__device__ __forceinline__ bool triangleRefine64(D3 o, D3 d, float3 v0f, float3 v1f, float3 v2f, double& t, double& u,
                                               double& v) {
     const D3 v0 = d3(v0f), e1 = d3(v1f) - v0, e2 = d3(v2f) - v0;
     const D3 P = crossd(d, e2);
@@ -202,7 +219,7 @@ __device__ __noinline__ bool triangleRefine64(D3 o, D3 d, float3 v0f, float3 v1f
     return true;
 }
 
-// Float32 sphere test. Returns 0 = miss, 1 = hit (t set), 2 = undecided.
+// Float32 sphere test. Returns 0 = miss, 1 = hit (world t set), 2 = undecided.
 __device__ __forceinline__ int sphereTest(const Level& L, const float4& s, float tmin, float tmax, bool strict, float& t) {
     const float3 f = L.o - make_float3(s.x, s.y, s.z);
     const float a = dot3(L.d, L.d);
@@ -215,13 +232,13 @@ __device__ __forceinline__ int sphereTest(const Level& L, const float4& s, float
     const float fn = dot3(f, f);
     // position error at the closest approach, then its effect on r^2 - |l|^2
     const float ep = 1.7320508f * (L.dO + fabsf(tca) * L.dD);
-    const float E = kBound * (fn + r2) + 4.f * sqrtf(fn) * ep + ep * ep;
+    const float E = kSphereBound * (fn + r2) + 4.f * sqrtf(fn) * ep + ep * ep;
     if (D < -E) return 0;
     if (D <= E) return 2;
     const float c = fn - r2;
     const float q = -b - copysignf(sqrtf(a * D), b);
-    float t0 = (q != 0.0f) ? c / q : 0.0f;
-    float t1 = q / a;
+    float t0 = ((q != 0.0f) ? c / q : 0.0f) + L.tOff;
+    float t1 = q / a + L.tOff;
     if (t0 > t1) {
         const float x = t0;
         t0 = t1;
@@ -242,7 +259,7 @@ __device__ __forceinline__ int sphereTest(const Level& L, const float4& s, float
 }
 
 // FP64 sphere: smallest root of |o + t d - c|^2 = r^2 in range.
-__device__ __noinline__ bool sphereTest64(D3 o, D3 d, float4 s, double tmin, double tmax, bool strict, double& t) {
+__device__ __forceinline__ bool sphereTest64(D3 o, D3 d, float4 s, double tmin, double tmax, bool strict, double& t) {
     const D3 f = o - D3{(double)s.x, (double)s.y, (double)s.z};
     const double a = dotd(d, d);
     const double b = dotd(f, d);
@@ -283,35 +300,95 @@ __device__ __forceinline__ void ray64(const InstanceFrames64* inv64, bool inInst
     d = D3{r[3], r[4], r[5]};
 }
 
-// Enter an instance: float32 object-space ray with bounds on its error (matrix
-// entries rounded from FP64 plus three rounded FMAs per component), and boxes
-// widened by the worst position error over the instance's parameter range.
-__device__ __forceinline__ void instanceLevel(Level& L, const InstanceRecord* R, float3 wo, float3 wd, float3 wid,
-                                              float tmin, float lim) {
+// FP64 decision of a primitive test that float32 could not take, kept out of line
+// (and value-in, value-out) so that it weighs neither on the traversal loop's
+// registers nor on its memory. Returns (t, u, v, 1) for a hit, w = 0 for a miss.
+__device__ __noinline__ float4 decide64(const InstanceFrames64* inv64, bool inInstance, uint32_t inst, float3 wo,
+                                        float3 wd, const float4* rec, bool sphere, float tmin, float tmax,
+                                        bool strict) {
+    D3 o, d;
+    ray64(inv64, inInstance, inst, wo, wd, o, d);
+    if (sphere) {
+        double t64;
+        if (!sphereTest64(o, d, __ldg(rec), tmin, tmax, strict, t64)) return make_float4(0.f, 0.f, 0.f, 0.f);
+        return make_float4((float)t64, 0.f, 0.f, 1.f);
+    }
+    double t64, u64, v64;
+    if (!triangleTest64(o, d, f3(__ldg(rec)), f3(__ldg(rec + 1)), f3(__ldg(rec + 2)), tmin, tmax, strict, t64, u64,
+                        v64))
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    return make_float4((float)t64, (float)u64, (float)v64, 1.f);
+}
+
+// The closest hit's distance and barycentrics recomputed in FP64: (t, u, v, 1), or
+// w = 0 when FP64 cannot evaluate them (the float32 values then stand).
+__device__ __noinline__ float4 refine64(const InstanceFrames64* inv64, bool inInstance, uint32_t inst, float3 wo,
+                                        float3 wd, const float4* rec, bool sphere, float tmin, float tmax) {
+    D3 o, d;
+    ray64(inv64, inInstance, inst, wo, wd, o, d);
+    if (sphere) {
+        double t64;
+        if (sphereTest64(o, d, __ldg(rec), (double)tmin, (double)tmax, false, t64))
+            return make_float4((float)t64, 0.f, 0.f, 1.f);
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    double t64, u64, v64;
+    if (triangleRefine64(o, d, f3(__ldg(rec)), f3(__ldg(rec + 1)), f3(__ldg(rec + 2)), t64, u64, v64))
+        return make_float4((float)t64, (float)u64, (float)v64, 1.f);
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Object-space point of the world ray at world parameter te, in FP64 from the
+// instance's FP64 inverse frame, rounded to float32.
+__device__ __noinline__ float3 instanceOrigin64(const InstanceFrames64* inv64, uint32_t inst, float3 wo, float3 wd,
+                                                float te) {
+    const InstanceFrames64& G = inv64[inst];
+    const double tE = (double)te;
+    const double w[3] = {(double)wo.x + tE * (double)wd.x, (double)wo.y + tE * (double)wd.y,
+                         (double)wo.z + tE * (double)wd.z};
+    float o[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = (float)(G.inv[k][0] * w[0] + G.inv[k][1] * w[1] + G.inv[k][2] * w[2] + G.inv[k][3]);
+    return make_float3(o[0], o[1], o[2]);
+}
+
+// Enter an instance. The object-space origin is placed where the world ray enters the
+// instance's world box (world parameter tOff) and computed in FP64 from the FP64
+// inverse frame, so that it is small and correctly rounded: float32 differences to
+// nearby vertices then lose little. The direction is transformed in float32 with a
+// bound on its error (matrix entries rounded from FP64 plus three rounded FMAs per
+// component). Boxes are widened by the worst position error over the instance's
+// parameter range.
+__device__ __forceinline__ void instanceLevel(Level& L, const InstanceRecord* R, const InstanceFrames64* inv64,
+                                              float3 wo, float3 wd, float3 wid, float tmin, float lim) {
     const float4 m[3] = {R->inv[0], R->inv[1], R->inv[2]};
     const float4 blo = R->worldLo, bhi = R->worldHi;
-    float o[3], d[3], so = 0.f, sd = 0.f;
+    // entry and exit parameters of the world box (exact world ray, conservative)
+    const bool px = wid.x >= 0.f, py = wid.y >= 0.f, pz = wid.z >= 0.f;
+    const float nx = ((px ? blo.x : bhi.x) - wo.x) * wid.x, fx = ((px ? bhi.x : blo.x) - wo.x) * wid.x;
+    const float ny = ((py ? blo.y : bhi.y) - wo.y) * wid.y, fy = ((py ? bhi.y : blo.y) - wo.y) * wid.y;
+    const float nz = ((pz ? blo.z : bhi.z) - wo.z) * wid.z, fz = ((pz ? bhi.z : blo.z) - wo.z) * wid.z;
+    const float tentry = fmaxf(fmaxf(nx, ny), fmaxf(nz, tmin));
+    const float texit = fminf(fminf(fx, fy), fminf(fz, lim)) * kFarScale;
+    const float te = (tentry < texit && tentry < INFINITY) ? tentry : tmin;  // any finite shift is exact enough
+    const float3 og = instanceOrigin64(inv64, R->instanceID, wo, wd, te);
+    const float o[3] = {og.x, og.y, og.z};
+    float d[3], sd = 0.f, so = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        o[k] = fmaf(m[k].x, wo.x, fmaf(m[k].y, wo.y, fmaf(m[k].z, wo.z, m[k].w)));
         d[k] = fmaf(m[k].x, wd.x, fmaf(m[k].y, wd.y, m[k].z * wd.z));
-        so = fmaxf(so, fabsf(m[k].x * wo.x) + fabsf(m[k].y * wo.y) + fabsf(m[k].z * wo.z) + fabsf(m[k].w));
         sd = fmaxf(sd, fabsf(m[k].x * wd.x) + fabsf(m[k].y * wd.y) + fabsf(m[k].z * wd.z));
+        so = fmaxf(so, fabsf(o[k]));
     }
     L.o = make_float3(o[0], o[1], o[2]);
     L.d = make_float3(d[0], d[1], d[2]);
     L.id = make_float3(__frcp_rn(d[0]), __frcp_rn(d[1]), __frcp_rn(d[2]));
     L.dl1 = norm1(L.d);
-    L.dO = 6.f * kEps * so;
+    L.tOff = te;
+    L.dO = 1.01f * kEps * so + 1e-30f;  // rounding of the FP64 origin (its own error is ~1e-16)
     L.dD = 6.f * kEps * sd;
-    // exit parameter of the instance's world box (exact world ray, conservative)
-    const bool px = wid.x >= 0.f, py = wid.y >= 0.f, pz = wid.z >= 0.f;
-    const float fx = ((px ? bhi.x : blo.x) - wo.x) * wid.x;
-    const float fy = ((py ? bhi.y : blo.y) - wo.y) * wid.y;
-    const float fz = ((pz ? bhi.z : blo.z) - wo.z) * wid.z;
-    const float texit = fminf(fminf(fx, fy), fminf(fz, lim)) * kFarScale;
-    const float slack = L.dO + fmaxf(texit, tmin) * L.dD +
-                        2.f * kEps * fmaxf(fmaxf(fabsf(o[0]), fabsf(o[1])), fabsf(o[2]));
+    const float span = fmaxf(fabsf(texit - te), fabsf(tmin - te)) * (1.f + 4.f * kEps);
+    const float slack = L.dO + span * L.dD + 2.f * kEps * so;
     const float3 sg = make_float3(copysignf(slack, L.id.x), copysignf(slack, L.id.y), copysignf(slack, L.id.z));
     L.on = L.o + sg;
     L.of = L.o - sg;
@@ -352,160 +429,181 @@ __device__ __forceinline__ void flushVisits(unsigned long long* stats, const Vis
     atomicAdd(&stats[5], (unsigned long long)v.fp64);
 }
 
-// One ray through the target. Returns the hit (prim == kInvalid on a miss).
-template <bool ANY, bool SCENE, bool COUNT = false>
-__device__ Hit traceRay(const TraceParams& P, Stack& st, float3 wo, float3 wd, float tmin, float tmax,
-                        Visits* vis = nullptr) {
-    Hit best{kInvalid, kInvalid, INFINITY, 0.f, 0.f};
-    if (P.target.empty) return best;
-    Level L;
-    exactLevel(L, wo, wd);
-    const float3 wid = L.id;
-    const float4* nodes = P.target.nodes;
-    const void* leaves = P.target.leaves;
-    uint32_t primType = P.target.primType, geomType = P.target.geomType, instId = 0;
-    bool inBlas = !SCENE;
-    bool found = false;
-    const float4* bestRec = nullptr;  // closest hit's leaf record (triangle) or sphere data
-    bool bestSphere = false;
-    uint32_t steps = 0;
-    uint32_t next = 0;
+// Traversal state of one ray, kept in registers between steps.
+struct RayState {
+    float3 wo, wd, wid;  // world ray and its reciprocal direction
+    float tmin, tmax;
+    Level L;             // ray at the current level
+    const float4* nodes;
+    const void* leaves;
+    const float4* bestRec;  // closest hit's leaf record (triangle) or sphere data
+    Hit best;
+    uint32_t primType, geomType, instId;
+    uint32_t steps, next;
+    bool inBlas, found, bestSphere;
+};
+
+template <bool SCENE>
+__device__ __forceinline__ void beginRay(const TraceParams& P, Stack& st, RayState& s, float3 wo, float3 wd,
+                                         float tmin, float tmax) {
+    s.best = Hit{kInvalid, kInvalid, INFINITY, 0.f, 0.f};
+    s.wo = wo;
+    s.wd = wd;
+    s.tmin = tmin;
+    s.tmax = tmax;
+    exactLevel(s.L, wo, wd);
+    s.wid = s.L.id;
+    s.nodes = P.target.nodes;
+    s.leaves = P.target.leaves;
+    s.primType = P.target.primType;
+    s.geomType = P.target.geomType;
+    s.instId = 0;
+    s.inBlas = !SCENE;
+    s.found = false;
+    s.bestRec = nullptr;
+    s.bestSphere = false;
+    s.steps = 0;
+    s.next = P.target.empty ? kNone : 0u;
     st.sp = 0;
-    for (;;) {
-        if (next == kNone) {
-            if (st.sp == 0) break;
-            next = st.pop();
-            if (SCENE && next == kSentinel) {  // back to the top level
-                exactLevel(L, wo, wd);
-                nodes = P.target.nodes;
-                inBlas = false;
-                next = kNone;
-                continue;
+}
+
+// One traversal step: a node visit (with its leaf tests), an instance entry or an
+// instance exit. Returns true once the ray is finished (s.best is then final).
+template <bool ANY, bool SCENE, bool COUNT>
+__device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayState& s, Visits* vis) {
+    if (s.next == kNone) {
+        if (st.sp == 0) {
+            if (!ANY && s.found && s.bestRec) {
+                const float4 r = refine64(P.inv64, SCENE, s.best.inst, s.wo, s.wd, s.bestRec, s.bestSphere, s.tmin,
+                                          s.tmax);
+                if (r.w != 0.f) s.best.t = r.x, s.best.u = r.y, s.best.v = r.z;
             }
+            return true;
         }
-        if (SCENE && !inBlas && (next & kLeafBit)) {  // enter an instance
-            const InstanceRecord* R = reinterpret_cast<const InstanceRecord*>(P.target.leaves) + (next & ~kLeafBit);
-            const uint32_t bits = R->typeBits;
-            next = kNone;
-            if (bits & kInstEmpty) continue;
-            if (!st.push(kSentinel)) {
-                latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
-                continue;
-            }
-            if (COUNT) ++vis->insts;
-            instanceLevel(L, R, wo, wd, wid, tmin, (ANY || !found) ? tmax : best.t);
-            nodes = R->nodes;
-            leaves = R->leaves;
-            primType = instPrimType(bits);
-            geomType = instGeomType(bits);
-            instId = R->instanceID;
-            inBlas = true;
-            next = 0;
-            continue;
+        s.next = st.pop();
+        if (SCENE && s.next == kSentinel) {  // back to the top level
+            exactLevel(s.L, s.wo, s.wd);
+            s.nodes = P.target.nodes;
+            s.inBlas = false;
+            s.next = kNone;
+            return false;
         }
-        if (++steps > P.maxSteps) {
-            latchError(P.error, GRT_ERROR_STEP_LIMIT);
-            break;
+    }
+    if (SCENE && !s.inBlas && (s.next & kLeafBit)) {  // enter an instance
+        const InstanceRecord* R = reinterpret_cast<const InstanceRecord*>(P.target.leaves) + (s.next & ~kLeafBit);
+        const uint32_t bits = R->typeBits;
+        s.next = kNone;
+        if (bits & kInstEmpty) return false;
+        if (!st.push(kSentinel)) {
+            latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+            return false;
         }
-        if (COUNT) ++vis->nodes;
-        const float4* N = nodes + 4 * (size_t)next;
-        const float4 nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2), nc = __ldg(N + 3);
-        bool h0, h1;
-        float tn0, tn1;
-        slab2(nx, ny, nz, L, tmin, (ANY || !found) ? tmax : best.t, h0, h1, tn0, tn1);
-        const uint32_t c0 = __float_as_uint(nc.x), c1 = __float_as_uint(nc.y);
-        if (c1 == c0) h1 = false;  // a one-primitive level stores its leaf twice
-        next = kNone;
-        if (inBlas) {
+        if (COUNT) ++vis->insts;
+        instanceLevel(s.L, R, P.inv64, s.wo, s.wd, s.wid, s.tmin, (ANY || !s.found) ? s.tmax : s.best.t);
+        s.nodes = R->nodes;
+        s.leaves = R->leaves;
+        s.primType = instPrimType(bits);
+        s.geomType = instGeomType(bits);
+        s.instId = R->instanceID;
+        s.inBlas = true;
+        s.next = 0;
+        return false;
+    }
+    if (++s.steps > P.maxSteps) {
+        latchError(P.error, GRT_ERROR_STEP_LIMIT);
+        return true;
+    }
+    if (COUNT) ++vis->nodes;
+    const float4* N = s.nodes + 4 * (size_t)s.next;
+    const float4 nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2), nc = __ldg(N + 3);
+    bool h0, h1;
+    float tn0, tn1;
+    slab2(nx, ny, nz, s.L, localLo(s.L, s.tmin), localHi(s.L, (ANY || !s.found) ? s.tmax : s.best.t), h0, h1, tn0,
+          tn1);
+    const uint32_t c0 = __float_as_uint(nc.x), c1 = __float_as_uint(nc.y);
+    if (c1 == c0) h1 = false;  // a one-primitive level stores its leaf twice
+    s.next = kNone;
+    if (s.inBlas) {
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const bool h = side ? h1 : h0;
-                const uint32_t c = side ? c1 : c0;
-                if (!h || !(c & kLeafBit)) continue;
-                const uint32_t k = c & ~kLeafBit;
-                const bool strict = found && !ANY;
-                const float cur = (ANY || !found) ? tmax : best.t;
-                float t = 0.f, u = 0.f, v = 0.f;
-                uint32_t prim;
-                int res = 0;
-                const float4* rec;
-                bool sphere = false;
-                if (primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
-                    rec = reinterpret_cast<const float4*>(leaves) + 3 * (size_t)k;
-                    const float4 a = __ldg(rec), b = __ldg(rec + 1), e = __ldg(rec + 2);
-                    prim = __float_as_uint(a.w);
-                    res = triangleTest(L, f3(a), f3(b), f3(e), b.w, e.w, tmin, cur, strict, t, u, v);
-                    if (COUNT) ++vis->tris;
-                    if (res == 2) {
-                        if (COUNT) ++vis->fp64;
-                        D3 o64, d64;
-                        ray64(P.inv64, SCENE, instId, wo, wd, o64, d64);
-                        double t64, u64, v64;
-                        res = triangleTest64(o64, d64, f3(a), f3(b), f3(e), tmin, cur, strict, t64, u64, v64) ? 1 : 0;
-                        t = (float)t64, u = (float)u64, v = (float)v64;
-                    }
-                } else {
-                    prim = __ldg(reinterpret_cast<const uint32_t*>(leaves) + k);
-                    rec = nullptr;
-                    if (P.table && geomType < P.numGeomTypes) {
-                        const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + geomType];
-                        if (fe.func == GRT_INTERSECT_SPHERE) {
-                            rec = reinterpret_cast<const float4*>(fe.data) + prim;
-                            sphere = true;
-                            const float4 s = __ldg(rec);
-                            res = sphereTest(L, s, tmin, cur, strict, t);
-                            if (COUNT) ++vis->customs;
-                            if (res == 2) {
-                                if (COUNT) ++vis->fp64;
-                                D3 o64, d64;
-                                ray64(P.inv64, SCENE, instId, wo, wd, o64, d64);
-                                double t64;
-                                res = sphereTest64(o64, d64, s, tmin, cur, strict, t64) ? 1 : 0;
-                                t = (float)t64;
-                            }
+        for (int side = 0; side < 2; ++side) {
+            const bool h = side ? h1 : h0;
+            const uint32_t c = side ? c1 : c0;
+            if (!h || !(c & kLeafBit)) continue;
+            const uint32_t k = c & ~kLeafBit;
+            const bool strict = s.found && !ANY;
+            const float cur = (ANY || !s.found) ? s.tmax : s.best.t;
+            float t = 0.f, u = 0.f, v = 0.f;
+            uint32_t prim;
+            int res = 0;
+            const float4* rec;
+            bool sphere = false;
+            if (s.primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
+                rec = reinterpret_cast<const float4*>(s.leaves) + 3 * (size_t)k;
+                const float4 a = __ldg(rec), b = __ldg(rec + 1), e = __ldg(rec + 2);
+                prim = __float_as_uint(a.w);
+                res = triangleTest(s.L, f3(a), f3(b), f3(e), b.w, e.w, s.tmin, cur, strict, t, u, v);
+                if (COUNT) ++vis->tris;
+                if (res == 2) {
+                    if (COUNT) ++vis->fp64;
+                    const float4 r = decide64(P.inv64, SCENE, s.instId, s.wo, s.wd, rec, false, s.tmin, cur, strict);
+                    res = r.w != 0.f ? 1 : 0;
+                    t = r.x, u = r.y, v = r.z;
+                }
+            } else {
+                prim = __ldg(reinterpret_cast<const uint32_t*>(s.leaves) + k);
+                rec = nullptr;
+                if (P.table && s.geomType < P.numGeomTypes) {
+                    const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + s.geomType];
+                    if (fe.func == GRT_INTERSECT_SPHERE) {
+                        rec = reinterpret_cast<const float4*>(fe.data) + prim;
+                        sphere = true;
+                        const float4 sp = __ldg(rec);
+                        res = sphereTest(s.L, sp, s.tmin, cur, strict, t);
+                        if (COUNT) ++vis->customs;
+                        if (res == 2) {
+                            if (COUNT) ++vis->fp64;
+                            const float4 r =
+                                decide64(P.inv64, SCENE, s.instId, s.wo, s.wd, rec, true, s.tmin, cur, strict);
+                            res = r.w != 0.f ? 1 : 0;
+                            t = r.x, u = r.y, v = r.z;
                         }
                     }
                 }
-                if (res == 1) {
-                    best = Hit{instId, prim, t, u, v};
-                    bestRec = rec;
-                    bestSphere = sphere;
-                    found = true;
-                    if (ANY) return best;
-                }
             }
-            if (c0 & kLeafBit) h0 = false;
-            if (c1 & kLeafBit) h1 = false;
-        }
-        if (h0 && h1) {
-            const bool swap = tn1 < tn0;
-            const uint32_t nearC = swap ? c1 : c0, farC = swap ? c0 : c1;
-            if (!st.push(farC)) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
-            next = nearC;
-        } else if (h0) {
-            next = c0;
-        } else if (h1) {
-            next = c1;
-        }
-    }
-    if (!ANY && found && bestRec) {
-        // the reported distance and barycentrics, recomputed in FP64
-        D3 o64, d64;
-        ray64(P.inv64, SCENE, best.inst, wo, wd, o64, d64);
-        if (bestSphere) {
-            double t64;
-            if (sphereTest64(o64, d64, __ldg(bestRec), (double)tmin, (double)tmax, false, t64)) best.t = (float)t64;
-        } else {
-            double t64, u64, v64;
-            if (triangleRefine64(o64, d64, f3(__ldg(bestRec)), f3(__ldg(bestRec + 1)), f3(__ldg(bestRec + 2)), t64,
-                                 u64, v64)) {
-                best.t = (float)t64;
-                best.u = (float)u64;
-                best.v = (float)v64;
+            if (res == 1) {
+                s.best = Hit{s.instId, prim, t, u, v};
+                s.bestRec = rec;
+                s.bestSphere = sphere;
+                s.found = true;
+                if (ANY) return true;
             }
         }
+        if (c0 & kLeafBit) h0 = false;
+        if (c1 & kLeafBit) h1 = false;
     }
-    return best;
+    if (h0 && h1) {
+        const bool swap = tn1 < tn0;
+        const uint32_t nearC = swap ? c1 : c0, farC = swap ? c0 : c1;
+        if (!st.push(farC)) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+        s.next = nearC;
+    } else if (h0) {
+        s.next = c0;
+    } else if (h1) {
+        s.next = c1;
+    }
+    return false;
+}
+
+// One ray through the target, all steps in a row. Returns the hit (prim == kInvalid
+// on a miss).
+template <bool ANY, bool SCENE, bool COUNT = false>
+__device__ Hit traceRay(const TraceParams& P, Stack& st, float3 wo, float3 wd, float tmin, float tmax,
+                        Visits* vis = nullptr) {
+    RayState s;
+    beginRay<SCENE>(P, st, s, wo, wd, tmin, tmax);
+    while (!stepRay<ANY, SCENE, COUNT>(P, st, s, vis)) {
+    }
+    return s.best;
 }
 
 __device__ __forceinline__ void storeHit(uint32_t* hits, uint32_t r, const Hit& h) {
