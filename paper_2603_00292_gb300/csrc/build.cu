@@ -507,7 +507,7 @@ struct InstanceInput {
     float4* boxes;             // 2 float4 per instance: world lo, hi
     InstanceRecord* records;   // unsorted
     InstanceFrames64* inv64;   // per instance ID
-    float4* fwd32;             // 3 rows per instance ID
+    float4* fwd32;             // kFrameRows rows per instance ID
     float4* centroids;
     uint32_t* bounds;
 };
@@ -544,7 +544,12 @@ __global__ void __launch_bounds__(128) instanceSetupKernel(InstanceInput I) {
         for (int r = 0; r < 3; ++r) {
             rec.inv[r] = make_float4(__double2float_rn(G[r][0]), __double2float_rn(G[r][1]),
                                      __double2float_rn(G[r][2]), __double2float_rn(G[r][3]));
-            I.fwd32[3 * (size_t)i + r] = make_float4(__double2float_rn(F[r][0]), __double2float_rn(F[r][1]),
+            I.fwd32[kFrameRows * (size_t)i + 3 + r] =
+                make_float4(__double2float_rn(G[r][0] - (double)rec.inv[r].x),
+                            __double2float_rn(G[r][1] - (double)rec.inv[r].y),
+                            __double2float_rn(G[r][2] - (double)rec.inv[r].z),
+                            __double2float_rn(G[r][3] - (double)rec.inv[r].w));
+            I.fwd32[kFrameRows * (size_t)i + r] = make_float4(__double2float_rn(F[r][0]), __double2float_rn(F[r][1]),
                                                      __double2float_rn(F[r][2]), __double2float_rn(F[r][3]));
             for (int q = 0; q < 4; ++q) I.inv64[i].inv[r][q] = G[r][q];
         }
@@ -637,7 +642,7 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     if (e == cudaSuccess && count) e = cudaMalloc(&o->parents, (size_t)(2 * count - 1) * 4);
     if (e == cudaSuccess && count && primType != GRT_PRIMITIVE_AABB_LIST) e = cudaMalloc(&o->primToLeaf, (size_t)count * 4);
     if (e == cudaSuccess && count && primType == kPrimScene) e = cudaMalloc(&o->inv64, (size_t)count * sizeof(InstanceFrames64));
-    if (e == cudaSuccess && count && primType == kPrimScene) e = cudaMalloc(&o->fwd32, (size_t)count * 3 * sizeof(float4));
+    if (e == cudaSuccess && count && primType == kPrimScene) e = cudaMalloc(&o->fwd32, (size_t)count * kFrameRows * sizeof(float4));
     BvhHeader h{};
     for (int a = 0; a < 3; ++a) h.rootLo[a] = INFINITY, h.rootHi[a] = -INFINITY;
     h.primCount = count;

@@ -48,6 +48,7 @@ struct InstanceFrames64 {
     double inv[3][4];  // object = inv * world, FP64 from the SRT frame
 };
 constexpr uint32_t kInstEmpty = 0x80000000u;
+constexpr int kFrameRows = 6;  // float4 rows per instance in BvhObject::fwd32
 __host__ __device__ inline uint32_t instGeomType(uint32_t bits) { return bits & 0xFFFFFFu; }
 __host__ __device__ inline uint32_t instPrimType(uint32_t bits) { return (bits >> 24) & 0x7Fu; }
 static_assert(sizeof(InstanceRecord) == 128, "instance record size");
@@ -108,7 +109,8 @@ struct BvhObject {
     int32_t* parents;
     uint32_t* primToLeaf;  // primitive (instance) ID -> sorted position (triangles, scenes)
     InstanceFrames64* inv64;  // scenes: FP64 inverse frame per instance ID
-    float4* fwd32;            // scenes: 3 float4 rows of the forward frame per instance ID
+    float4* fwd32;            // scenes: per instance ID kFrameRows float4: forward frame rows 0-2, then
+                              // the low parts of the inverse frame (FP64 minus the record's float32 rows)
     uint32_t primCount;
     uint32_t nodeCount;
     uint32_t primType;

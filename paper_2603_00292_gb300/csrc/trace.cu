@@ -75,6 +75,51 @@ __global__ void traceKernel(TraceParams P) {
     refillLoop<ANY, SCENE, COUNT>(P, st, src);
 }
 
+// The closest hits' t, u, v recomputed in FP64, one thread per ray after traversal so
+// that every lane of a warp takes part (FP64 is far slower than FP32 on this GPU).
+__global__ void __launch_bounds__(256) refineKernel(TraceParams P) {
+    const bool scene = P.target.primType == kPrimScene;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < P.count; r += gridDim.x * blockDim.x) {
+        uint32_t* h = P.hits + 5 * (size_t)r;
+        const uint32_t inst = h[0], prim = h[1];
+        if (prim == kInvalid) continue;
+        uint32_t primType, geomType;
+        const void* leaves;
+        const uint32_t* toLeaf;
+        if (scene) {
+            const InstanceRecord* R = P.sceneLeaves + P.scenePrimToLeaf[inst];
+            primType = instPrimType(R->typeBits);
+            geomType = instGeomType(R->typeBits);
+            leaves = R->leaves;
+            toLeaf = R->geometry->primToLeaf;
+        } else {
+            primType = P.target.primType;
+            geomType = P.target.geomType;
+            leaves = P.target.leaves;
+            toLeaf = P.targetPrimToLeaf;
+        }
+        const float4* rec = nullptr;
+        bool sphere = false;
+        if (primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
+            rec = reinterpret_cast<const float4*>(leaves) + 3 * (size_t)toLeaf[prim];
+        } else if (P.table && geomType < P.numGeomTypes) {
+            const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + geomType];
+            if (fe.func == GRT_INTERSECT_SPHERE) {
+                rec = reinterpret_cast<const float4*>(fe.data) + prim;
+                sphere = true;
+            }
+        }
+        if (!rec) continue;
+        const float4 a = P.rays[2 * (size_t)r], b = P.rays[2 * (size_t)r + 1];
+        const float4 res = refine64(P.inv64, scene, inst, f3(a), f3(b), rec, sphere, a.w, b.w);
+        if (res.w != 0.f) {
+            h[2] = __float_as_uint(res.x);
+            h[3] = __float_as_uint(res.y);
+            h[4] = __float_as_uint(res.z);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- ambient occlusion (Sec. 4)
 __global__ void aoRayKernel(const InstanceRecord* sceneLeaves, const uint32_t* scenePrimToLeaf, const float4* fwd32,
                             const float4* rays, const uint32_t* hits, uint32_t pixels, uint32_t spp,
@@ -228,6 +273,13 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     const float compact = (opt && opt->compactThreshold > 0.f) ? fminf(opt->compactThreshold, 1.f) : 0.5f;
     P.refillBelow = (uint32_t)(compact * 32.f);
     P.inv64 = o->inv64;
+    P.fwd32 = (const float4*)o->fwd32;
+    if (scene) {
+        P.sceneLeaves = (const InstanceRecord*)o->leaves;
+        P.scenePrimToLeaf = o->primToLeaf;
+    } else {
+        P.targetPrimToLeaf = o->primToLeaf;
+    }
     if (table) {
         FuncTableObject* t = findFuncTable(table);
         if (!t) return GRT_ERROR_INVALID_PARAMETER;
@@ -301,8 +353,9 @@ static grtError launchTrace(grtContext ctx, grtScene scene, grtGeometry geom, co
     P.counter = nextCounter(c);
     GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
     kernel<<<L.blocks, bs, smem, s>>>(P);
+    if (!ANY) refineKernel<<<smCount(c) * 4, 256, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
-    noteLaunches(1);
+    noteLaunches(ANY ? 1 : 2);
     return GRT_SUCCESS;
 }
 
@@ -390,8 +443,9 @@ grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom
     cudaStream_t s = (cudaStream_t)stream;
     GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));  // the work counter starts at zero
     kernel<<<L.blocks, bs, smem, s>>>(P);
+    refineKernel<<<smCount(c) * 4, 256, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
-    noteLaunches(1);
+    noteLaunches(2);
     return GRT_SUCCESS;
 }
 

@@ -67,6 +67,7 @@ struct TraceParams {
     const uint32_t* primaryHits;
     const InstanceRecord* sceneLeaves;
     const uint32_t* scenePrimToLeaf;
+    const uint32_t* targetPrimToLeaf;  // a triangle geometry traced directly: primitive ID -> leaf
     const float4* fwd32;
     uint32_t spp;
     unsigned long long seed;
@@ -338,29 +339,59 @@ __device__ __noinline__ float4 refine64(const InstanceFrames64* inv64, bool inIn
     return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Object-space point of the world ray at world parameter te, in FP64 from the
-// instance's FP64 inverse frame, rounded to float32.
-__device__ __noinline__ float3 instanceOrigin64(const InstanceFrames64* inv64, uint32_t inst, float3 wo, float3 wd,
-                                                float te) {
-    const InstanceFrames64& G = inv64[inst];
-    const double tE = (double)te;
-    const double w[3] = {(double)wo.x + tE * (double)wd.x, (double)wo.y + tE * (double)wd.y,
-                         (double)wo.z + tE * (double)wd.z};
+// Error-free transformations (Dekker; Knuth): a*b = p + e and a + b = s + e exactly.
+__device__ __forceinline__ float2 twoProd(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return make_float2(p, fmaf(a, b, -p));
+}
+__device__ __forceinline__ float2 twoSum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+// Object-space point of the world ray at world parameter te, from the inverse frame
+// held as float32 rows plus low parts (hi + lo = the FP64 frame to 2^-48), evaluated
+// in float-float arithmetic (about 48 significant bits) and rounded to float32. This
+// stays on the float32 pipes: FP64 is far slower on this GPU.
+__device__ __forceinline__ float3 instanceOriginFF(const float4* hi, const float4* lo, float3 wo, float3 wd, float te) {
+    const float wo3[3] = {wo.x, wo.y, wo.z}, wd3[3] = {wd.x, wd.y, wd.z};
+    float wh[3], wl[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // w = wo + te * wd as hi + lo
+        const float2 p = twoProd(te, wd3[j]);
+        const float2 q = twoSum(wo3[j], p.x);
+        wh[j] = q.x;
+        wl[j] = __fadd_rn(q.y, p.y);
+    }
     float o[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) o[k] = (float)(G.inv[k][0] * w[0] + G.inv[k][1] * w[1] + G.inv[k][2] * w[2] + G.inv[k][3]);
+    for (int k = 0; k < 3; ++k) {
+        const float4 H = __ldg(hi + k), Lw = __ldg(lo + k);
+        const float gh[3] = {H.x, H.y, H.z}, gl[3] = {Lw.x, Lw.y, Lw.z};
+        float ah = H.w, al = Lw.w;  // translation part
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float2 p = twoProd(gh[j], wh[j]);
+            const float pl = fmaf(gh[j], wl[j], fmaf(gl[j], wh[j], p.y));
+            const float2 q = twoSum(ah, p.x);
+            ah = q.x;
+            al = __fadd_rn(al, __fadd_rn(q.y, pl));
+        }
+        o[k] = __fadd_rn(ah, al);
+    }
     return make_float3(o[0], o[1], o[2]);
 }
 
 // Enter an instance. The object-space origin is placed where the world ray enters the
-// instance's world box (world parameter tOff) and computed in FP64 from the FP64
-// inverse frame, so that it is small and correctly rounded: float32 differences to
+// instance's world box (world parameter tOff) and computed to near-FP64 accuracy (see
+// instanceOriginFF), so that it is small and correctly rounded: float32 differences to
 // nearby vertices then lose little. The direction is transformed in float32 with a
 // bound on its error (matrix entries rounded from FP64 plus three rounded FMAs per
 // component). Boxes are widened by the worst position error over the instance's
 // parameter range.
-__device__ __forceinline__ void instanceLevel(Level& L, const InstanceRecord* R, const InstanceFrames64* inv64,
-                                              float3 wo, float3 wd, float3 wid, float tmin, float lim) {
+__device__ __forceinline__ void instanceLevel(Level& L, const InstanceRecord* R, const float4* frames32, float3 wo,
+                                              float3 wd, float3 wid, float tmin, float lim) {
     const float4 m[3] = {R->inv[0], R->inv[1], R->inv[2]};
     const float4 blo = R->worldLo, bhi = R->worldHi;
     // entry and exit parameters of the world box (exact world ray, conservative)
@@ -371,7 +402,7 @@ __device__ __forceinline__ void instanceLevel(Level& L, const InstanceRecord* R,
     const float tentry = fmaxf(fmaxf(nx, ny), fmaxf(nz, tmin));
     const float texit = fminf(fminf(fx, fy), fminf(fz, lim)) * kFarScale;
     const float te = (tentry < texit && tentry < INFINITY) ? tentry : tmin;  // any finite shift is exact enough
-    const float3 og = instanceOrigin64(inv64, R->instanceID, wo, wd, te);
+    const float3 og = instanceOriginFF(R->inv, frames32 + kFrameRows * (size_t)R->instanceID + 3, wo, wd, te);
     const float o[3] = {og.x, og.y, og.z};
     float d[3], sd = 0.f, so = 0.f;
 #pragma unroll
@@ -385,7 +416,10 @@ __device__ __forceinline__ void instanceLevel(Level& L, const InstanceRecord* R,
     L.id = make_float3(__frcp_rn(d[0]), __frcp_rn(d[1]), __frcp_rn(d[2]));
     L.dl1 = norm1(L.d);
     L.tOff = te;
-    L.dO = 1.01f * kEps * so + 1e-30f;  // rounding of the FP64 origin (its own error is ~1e-16)
+    // final rounding (u) plus the float-float evaluation's own error (tens of u^2
+    // relative to the largest term, which is at most about 2^10 times |o| here)
+    L.dO = 1.01f * kEps * so + 64.f * kEps * kEps * (so + fabsf(m[0].w) + fabsf(m[1].w) + fabsf(m[2].w) +
+                                                  fabsf(te) * L.dl1 + norm1(wo) * 4.f) + 1e-30f;
     L.dD = 6.f * kEps * sd;
     const float span = fmaxf(fabsf(texit - te), fabsf(tmin - te)) * (1.f + 4.f * kEps);
     const float slack = L.dO + span * L.dD + 2.f * kEps * so;
@@ -436,11 +470,10 @@ struct RayState {
     Level L;             // ray at the current level
     const float4* nodes;
     const void* leaves;
-    const float4* bestRec;  // closest hit's leaf record (triangle) or sphere data
     Hit best;
     uint32_t primType, geomType, instId;
     uint32_t steps, next;
-    bool inBlas, found, bestSphere;
+    bool inBlas, found;
 };
 
 template <bool SCENE>
@@ -460,8 +493,6 @@ __device__ __forceinline__ void beginRay(const TraceParams& P, Stack& st, RaySta
     s.instId = 0;
     s.inBlas = !SCENE;
     s.found = false;
-    s.bestRec = nullptr;
-    s.bestSphere = false;
     s.steps = 0;
     s.next = P.target.empty ? kNone : 0u;
     st.sp = 0;
@@ -472,14 +503,7 @@ __device__ __forceinline__ void beginRay(const TraceParams& P, Stack& st, RaySta
 template <bool ANY, bool SCENE, bool COUNT>
 __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayState& s, Visits* vis) {
     if (s.next == kNone) {
-        if (st.sp == 0) {
-            if (!ANY && s.found && s.bestRec) {
-                const float4 r = refine64(P.inv64, SCENE, s.best.inst, s.wo, s.wd, s.bestRec, s.bestSphere, s.tmin,
-                                          s.tmax);
-                if (r.w != 0.f) s.best.t = r.x, s.best.u = r.y, s.best.v = r.z;
-            }
-            return true;
-        }
+        if (st.sp == 0) return true;  // closest hits are refined in FP64 afterwards (refineKernel)
         s.next = st.pop();
         if (SCENE && s.next == kSentinel) {  // back to the top level
             exactLevel(s.L, s.wo, s.wd);
@@ -499,7 +523,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
             return false;
         }
         if (COUNT) ++vis->insts;
-        instanceLevel(s.L, R, P.inv64, s.wo, s.wd, s.wid, s.tmin, (ANY || !s.found) ? s.tmax : s.best.t);
+        instanceLevel(s.L, R, P.fwd32, s.wo, s.wd, s.wid, s.tmin, (ANY || !s.found) ? s.tmax : s.best.t);
         s.nodes = R->nodes;
         s.leaves = R->leaves;
         s.primType = instPrimType(bits);
@@ -572,8 +596,6 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
             }
             if (res == 1) {
                 s.best = Hit{s.instId, prim, t, u, v};
-                s.bestRec = rec;
-                s.bestSphere = sphere;
                 s.found = true;
                 if (ANY) return true;
             }
@@ -643,7 +665,8 @@ __device__ __forceinline__ bool aoFrame(const InstanceRecord* sceneLeaves, const
     if (instPrimType(R->typeBits) != GRT_PRIMITIVE_TRIANGLE_MESH) return false;
     const BvhHeader* g = R->geometry;
     const float4* rec = reinterpret_cast<const float4*>(g->leaves) + 3 * (size_t)g->primToLeaf[prim];
-    const float4 m0 = fwd32[3 * (size_t)inst], m1 = fwd32[3 * (size_t)inst + 1], m2 = fwd32[3 * (size_t)inst + 2];
+    const float4* fr = fwd32 + kFrameRows * (size_t)inst;
+    const float4 m0 = fr[0], m1 = fr[1], m2 = fr[2];
     // world edges = linear part of the frame applied to object-space edges (no
     // cancellation against the translation)
     const float3 v0 = f3(rec[0]), a1 = f3(rec[1]) - v0, a2 = f3(rec[2]) - v0;
