@@ -23,7 +23,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["build_ref.cpp", "trace_ref.cpp", "shade_ref.cpp"]
+_SRCS = ["build_ref.cpp", "trace_ref.cpp", "shade_ref.cpp", "lambert_ref.cpp"]
 _LIB_PATH = os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -85,6 +85,10 @@ def lib() -> ctypes.CDLL:
             L.oracle_camera_rays.argtypes = [P, i64, i64, P]
             L.oracle_sample_hemisphere.argtypes = [ctypes.c_double, ctypes.c_double, P]
             L.oracle_ao_rays.argtypes = [P, P, P, P, i64, ctypes.c_int, ctypes.c_uint64, ctypes.c_float, P]
+            L.oracle_lambert_forward.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, P, P]
+            L.oracle_lambert_gradient.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, P]
+            L.oracle_lambert_gradient.restype = ctypes.c_double
+            L.oracle_lambert_fd.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, i64, ctypes.c_double, P, P, P]
             _lib = L
     return _lib
 
@@ -338,3 +342,62 @@ def ao_rays(scene: Scene, primary_rays, hits: Hits, spp: int, seed: int, length:
     lib().oracle_ao_rays(_p(r), _p(tri), _p(_c(hits.prim, np.uint32)), _p(_c(hits.t, np.float64)), n, spp,
                          ctypes.c_uint64(seed), ctypes.c_float(length), _p(out))
     return out
+
+
+# ----------------------------------------------------------------------------------
+# Lambertian shading and its gradient (FP64, brute-force visibility)
+# ----------------------------------------------------------------------------------
+class LambertResult:
+    def __init__(self, n: int):
+        self.image = np.zeros((n, 3))
+        self.prim = np.full(n, -1, np.int32)
+        self.vis = np.zeros(n, np.int8)
+        self.sign = np.zeros(n, np.int8)
+        self.tuv = np.zeros((n, 3))
+
+
+def lambert_forward(vertices, indices, colours, light, rays) -> LambertResult:
+    """Image I = V * max(0, n_f . l) * c(u,v) per pixel (see lambert_ref.cpp)."""
+    v = _c(vertices, np.float64)
+    i = _c(indices, np.uint32)
+    c = _c(colours, np.float64)
+    l = _c(light, np.float64).reshape(3)
+    r = _c(rays, np.float32).reshape(-1, 8)
+    R = LambertResult(r.shape[0])
+    lib().oracle_lambert_forward(_p(v), v.shape[0], _p(i), i.shape[0], _p(c), _p(l), _p(r), r.shape[0], _p(R.image),
+                                 _p(R.prim), _p(R.vis), _p(R.sign), _p(R.tuv))
+    return R
+
+
+def lambert_gradient(vertices, indices, colours, light, rays, target):
+    """(loss, dL/dcolours (V,3), dL/dlight (3,), dL/dpositions (V,3)) of L = sum (I - I*)^2."""
+    v = _c(vertices, np.float64)
+    i = _c(indices, np.uint32)
+    c = _c(colours, np.float64)
+    l = _c(light, np.float64).reshape(3)
+    r = _c(rays, np.float32).reshape(-1, 8)
+    t = _c(target, np.float64).reshape(-1, 3)
+    dc = np.zeros_like(c)
+    dl = np.zeros(3)
+    dp = np.zeros_like(v)
+    loss = lib().oracle_lambert_gradient(_p(v), v.shape[0], _p(i), i.shape[0], _p(c), _p(l), _p(r), r.shape[0], _p(t),
+                                         _p(dc), _p(dl), _p(dp))
+    return float(loss), dc, dl, dp
+
+
+def lambert_fd(vertices, indices, colours, light, rays, target, params, h: float = 1e-4):
+    """Central differences (masked loss) for parameter ids: [0,3V) colours, [3V,3V+3) light,
+    [3V+3, 6V+3) positions. Returns (fd, analytic gradient of the masked pixels, masked counts)."""
+    v = _c(vertices, np.float64)
+    i = _c(indices, np.uint32)
+    c = _c(colours, np.float64)
+    l = _c(light, np.float64).reshape(3)
+    r = _c(rays, np.float32).reshape(-1, 8)
+    t = _c(target, np.float64).reshape(-1, 3)
+    q = _c(params, np.int64)
+    fd = np.zeros(q.shape[0])
+    ma = np.zeros(q.shape[0])
+    mc = np.zeros(q.shape[0], np.int64)
+    lib().oracle_lambert_fd(_p(v), v.shape[0], _p(i), i.shape[0], _p(c), _p(l), _p(r), r.shape[0], _p(t), _p(q),
+                            q.shape[0], h, _p(fd), _p(ma), _p(mc))
+    return fd, ma, mc

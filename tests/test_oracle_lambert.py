@@ -1,0 +1,90 @@
+"""Pins for the oracle's Lambertian shading and its gradient (CPU only): FP64 central
+differences against the analytic gradient on a small render, Euler's identity for the
+light (the image is homogeneous of degree 1 in an unnormalised light where lit), and
+a closed form for the colour gradient of a one-triangle scene."""
+import math
+
+import numpy as np
+
+import oracle
+import scenegen
+
+
+def _setup(level=1, W=48, H=36, seed=3):
+    mesh = scenegen.icosphere(level)
+    rng = np.random.default_rng(seed)
+    cols = rng.uniform(0, 1, (mesh.vertices.shape[0], 3))
+    light = np.array([1.0, 1.0, 1.0]) / math.sqrt(3)
+    cam = scenegen.look_down_z_camera([0, 0, 3], W, H)
+    rays = oracle.camera_rays(cam.packed(), W, H)
+    verts = mesh.vertices.astype(np.float64)
+    # target: perturbed colours and a light rotated by a few degrees
+    tcols = cols + rng.uniform(-0.1, 0.1, cols.shape)
+    axis = np.cross(light, [0, 1.0, 0])
+    axis /= np.linalg.norm(axis)
+    ang = math.radians(4.0)
+    tlight = light * math.cos(ang) + np.cross(axis, light) * math.sin(ang)
+    target = oracle.lambert_forward(verts, mesh.indices, tcols, tlight, rays).image
+    return mesh, verts, cols, light, rays, target
+
+
+def test_forward_is_shaded_hits_only():
+    mesh, verts, cols, light, rays, target = _setup()
+    R = oracle.lambert_forward(verts, mesh.indices, cols, light, rays)
+    miss = R.prim < 0
+    assert miss.any() and (~miss).any()
+    assert np.all(R.image[miss] == 0)
+    # a convex sphere never shadows a lit point
+    lit = (R.prim >= 0) & (R.sign > 0)
+    assert np.all(R.vis[lit] == 1)
+    assert np.all(R.image[(R.prim >= 0) & (R.sign <= 0)] == 0)
+    assert np.all(R.image >= 0) and np.all(R.image <= 1)
+
+
+def test_gradient_matches_central_differences():
+    mesh, verts, cols, light, rays, target = _setup()
+    loss, dc, dl, dp = oracle.lambert_gradient(verts, mesh.indices, cols, light, rays, target)
+    nv = verts.shape[0]
+    analytic = np.concatenate([dc.ravel(), dl, dp.ravel()])
+    params = np.nonzero(analytic != 0)[0]
+    assert params.size > 60
+    fd, masked, count = oracle.lambert_fd(verts, mesh.indices, cols, light, rays, target, params, 1e-4)
+    g = analytic[params] - masked
+    scale = max(np.abs(fd).max(), 1e-30)
+    err = np.abs(g - fd)
+    ok = err <= 1e-3 * np.maximum(np.abs(fd), 1e-6 * scale)
+    assert ok.mean() == 1.0, (params[~ok][:5], g[~ok][:5], fd[~ok][:5])
+    # the three kinds of parameters are all exercised
+    assert (params < 3 * nv).any() and ((params >= 3 * nv) & (params < 3 * nv + 3)).any() and (params >= 3 * nv + 3).any()
+
+
+def test_light_gradient_euler_identity():
+    mesh, verts, cols, light, rays, target = _setup(level=2, seed=5)
+    loss, dc, dl, dp = oracle.lambert_gradient(verts, mesh.indices, cols, light, rays, target)
+    R = oracle.lambert_forward(verts, mesh.indices, cols, light, rays)
+    # I is homogeneous of degree 1 in l (max(0, n.l) with l unnormalised), so
+    # l . dL/dl = sum 2 (I - I*) . I
+    lhs = float(np.dot(light, dl))
+    rhs = float(np.sum(2 * (R.image - target) * R.image))
+    assert abs(lhs - rhs) <= 1e-9 * max(1.0, abs(rhs))
+
+
+def test_colour_gradient_closed_form_one_triangle():
+    v = np.array([[-1.0, -0.8, 0.0], [1.2, -0.6, 0.0], [0.1, 1.1, 0.0]])
+    idx = np.array([[0, 1, 2]], np.uint32)
+    cols = np.array([[0.2, 0.5, 0.9], [0.7, 0.1, 0.4], [0.3, 0.8, 0.6]])
+    tcols = cols + np.array([[0.05, -0.02, 0.03], [-0.04, 0.06, 0.01], [0.02, 0.02, -0.05]])
+    light = np.array([0.3, 0.2, 0.9])
+    cam = scenegen.look_down_z_camera([0, 0, 3], 40, 30)
+    rays = oracle.camera_rays(cam.packed(), 40, 30)
+    target = oracle.lambert_forward(v, idx, tcols, light, rays).image
+    loss, dc, dl, dp = oracle.lambert_gradient(v, idx, cols, light, rays, target)
+    R = oracle.lambert_forward(v, idx, cols, light, rays)
+    # the triangle faces +z toward the camera: s = n . l = l_z everywhere it is hit
+    hit = R.prim >= 0
+    u, w = R.tuv[hit, 1], R.tuv[hit, 2]
+    B = np.stack([1 - u - w, u, w], axis=1)           # barycentric weights per pixel
+    s = light[2]
+    G = (s * s) * (B.T @ B)                             # sum_p s^2 w w^T
+    expect = 2 * G @ (cols - tcols)                    # I - I* = s W (c - c*)
+    assert np.allclose(dc, expect, rtol=1e-10, atol=1e-12)
