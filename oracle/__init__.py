@@ -88,7 +88,7 @@ def lib() -> ctypes.CDLL:
             L.oracle_lambert_forward.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, P, P]
             L.oracle_lambert_gradient.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, P]
             L.oracle_lambert_gradient.restype = ctypes.c_double
-            L.oracle_lambert_fd.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, i64, ctypes.c_double, P, P, P]
+            L.oracle_lambert_fd.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, i64, ctypes.c_double, P, P, P, P, P]
             _lib = L
     return _lib
 
@@ -385,9 +385,12 @@ def lambert_gradient(vertices, indices, colours, light, rays, target):
     return float(loss), dc, dl, dp
 
 
-def lambert_fd(vertices, indices, colours, light, rays, target, params, h: float = 1e-4):
+def lambert_fd(vertices, indices, colours, light, rays, target, params, h: float = 1e-4, exclude=None,
+               return_unstable: bool = False):
     """Central differences (masked loss) for parameter ids: [0,3V) colours, [3V,3V+3) light,
-    [3V+3, 6V+3) positions. Returns (fd, analytic gradient of the masked pixels, masked counts)."""
+    [3V+3, 6V+3) positions. Returns (fd, analytic gradient of the masked pixels, masked counts)
+    and, with return_unstable, the per-pixel mask of pixels unstable for some parameter.
+    exclude (bool per pixel) removes pixels from every parameter's loss."""
     v = _c(vertices, np.float64)
     i = _c(indices, np.uint32)
     c = _c(colours, np.float64)
@@ -398,6 +401,10 @@ def lambert_fd(vertices, indices, colours, light, rays, target, params, h: float
     fd = np.zeros(q.shape[0])
     ma = np.zeros(q.shape[0])
     mc = np.zeros(q.shape[0], np.int64)
+    ex = None if exclude is None else _c(exclude, np.uint8)
+    un = np.zeros(r.shape[0], np.uint8)
     lib().oracle_lambert_fd(_p(v), v.shape[0], _p(i), i.shape[0], _p(c), _p(l), _p(r), r.shape[0], _p(t), _p(q),
-                            q.shape[0], h, _p(fd), _p(ma), _p(mc))
+                            q.shape[0], h, _p(fd), _p(ma), _p(mc), None if ex is None else _p(ex), _p(un))
+    if return_unstable:
+        return fd, ma, mc, un.astype(bool)
     return fd, ma, mc

@@ -241,11 +241,13 @@ double oracle_lambert_gradient(const double* verts, int64_t nv, const uint32_t* 
 // in the renders at q-h, q and q+h. Only pixels that can change are re-rendered:
 // colours touch the pixels whose hit triangle uses the vertex; the light touches every
 // hit pixel; a position touches the pixels whose primary or shadow ray meets the box
-// of the vertex's triangles widened by 4h.
+// of the vertex's triangles widened by 4h. exclude (n bytes, may be NULL) removes
+// pixels from every parameter's loss; unstable (n bytes, may be NULL) receives 1 for
+// each pixel found unstable for some parameter.
 void oracle_lambert_fd(const double* verts, int64_t nv, const uint32_t* idx, int64_t nt, const double* col,
                        const double* light, const float* rays, int64_t n, const double* target,
                        const int64_t* params, int64_t nparams, double h, double* fd, double* masked_analytic,
-                       int64_t* masked_count) {
+                       int64_t* masked_count, const uint8_t* exclude, uint8_t* unstable) {
     const Mesh M0{verts, idx, nt};
     const V3 l0 = v3(light[0], light[1], light[2]);
     std::vector<PixelState> S0((size_t)n);
@@ -342,6 +344,8 @@ void oracle_lambert_fd(const double* verts, int64_t nv, const uint32_t* idx, int
             const PixelState &s0 = S0[(size_t)p], &sp = Sp[j], &sm = Sm[j];
             const bool stable = s0.prim == sp.prim && s0.prim == sm.prim && s0.vis == sp.vis && s0.vis == sm.vis &&
                                 s0.sign == sp.sign && s0.sign == sm.sign;
+            if (!stable && unstable) unstable[p] = 1;
+            if (exclude && exclude[p]) continue;  // left out of every parameter's loss
             if (stable) {
                 Lp += pixelLoss(Mp, cp.data(), lp, p, sp);
                 Lm += pixelLoss(Mm, cm.data(), lm, p, sm);
