@@ -19,6 +19,11 @@ timed region.
 
 `--impl reference` times the CPU oracle (FP64, oracle/) on a bounded sample of the
 same workload on the host cores.
+
+`--workload lambert-adjoint-1080p` prints a second kind of line instead: differentiable
+Lambert shading of a 642-vertex icosphere at 1920x1080 (closest hit, shading with one
+shadow any-hit ray per lit pixel), forward alone against forward + adjoint backward,
+with the hit records stored (21 bytes per pixel) or recomputed by the backward pass.
 """
 from __future__ import annotations
 
@@ -54,6 +59,8 @@ def parse():
     p.add_argument("--impl", default="grt", choices=["grt", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--workload", default=WORKLOAD["workload"], choices=[WORKLOAD["workload"], "lambert-adjoint-1080p"],
+                   help="the ambient-occlusion throughput workload (default) or the differentiable-shading one")
     return p.parse_args()
 
 
@@ -381,11 +388,197 @@ def run_reference(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- adjoint workload
+ADJOINT = dict(workload="lambert-adjoint-1080p", mesh="icosphere level 3 (642 vertices, 1280 triangles)",
+               width=1920, height=1080, camera="(0,0,3) looking down -z, 60 degree fov", shadow_rays=1,
+               seed=20260301)
+
+
+def adjoint_problem():
+    import oracle
+    import scenegen
+
+    P = scenegen.shading_problem(ADJOINT["width"], ADJOINT["height"], ADJOINT["seed"])
+    rays = oracle.camera_rays(P.camera.packed(), ADJOINT["width"], ADJOINT["height"])
+    return P, rays
+
+
+def run_adjoint(args, rank, world, local):
+    """Differentiable Lambert shading at 1920x1080: forward (closest hit + shading with
+    one shadow any-hit ray per lit pixel) against forward + adjoint backward, with the
+    hit records stored or recomputed in the backward pass."""
+    import torch
+
+    import paper_2603_00292_gb300 as grt
+    from paper_2603_00292_gb300 import build as grt_build
+    from paper_2603_00292_gb300.objects import Context, Geometry, device_tensor, new_hits
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+    if rank == 0:
+        grt_build.build()
+    if dist:
+        dist.barrier()
+    P, rays_np = adjoint_problem()
+    W, H = ADJOINT["width"], ADJOINT["height"]
+    n = W * H
+    ctx = Context(local)
+    pos, idx = device_tensor(P.mesh.vertices), device_tensor(P.mesh.indices)
+    col, light = device_tensor(P.colours), device_tensor(P.light)
+    rays = device_tensor(rays_np)
+    geom = Geometry(ctx, vertices=pos, indices=idx).build()
+    target = torch.rand((n, 3), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    hits = new_hits(n)
+    img = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    vis = torch.empty(n, dtype=torch.uint8, device="cuda")
+    gimg = torch.empty_like(img)
+    gc, gl, gp = torch.zeros_like(col), torch.zeros_like(light), torch.zeros_like(pos)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def forward(store: bool):
+        grt.grtTraceClosest(ctx.handle, None, geom.handle, rays, n, hits, None, None, sh)
+        grt.grtShadeLambert(ctx.handle, geom.handle, rays, hits, n, idx, pos, col, light, img,
+                            vis if store else None, None, sh)
+
+    def backward(store: bool, mark: bool):
+        torch.sub(img, target, out=gimg).mul_(2.0)
+        gc.zero_(), gl.zero_(), gp.zero_()
+        if mark:
+            ev[2].record(stream)
+        grt.grtShadeLambertBackward(ctx.handle, geom.handle, rays, hits if store else None, vis if store else None,
+                                    n, idx, pos, col, light, gimg, gc, gl, gp, None, sh)
+        if mark:
+            ev[3].record(stream)
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(mode: str):
+        for _ in range(args.warmup):
+            forward(mode != "recompute")
+            if mode != "forward":
+                backward(mode == "store", False)
+        torch.cuda.synchronize()
+        step, bwd = [], []
+        l0 = grt.grtGetLaunchCount()
+        for _ in range(args.steps):
+            flush.zero_()
+            ev[0].record(stream)
+            forward(mode != "recompute")
+            if mode != "forward":
+                backward(mode == "store", True)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            step.append(ev[0].elapsed_time(ev[1]))
+            if mode != "forward":
+                bwd.append(ev[2].elapsed_time(ev[3]))
+        launches[mode] = grt.grtGetLaunchCount() - l0
+        return statistics.mean(step), (statistics.mean(bwd) if bwd else None)
+
+    clocks = ClockSampler(local)
+    launches = {}
+    if dist:
+        dist.barrier()
+    clocks.start()
+    fwd_ms, _ = timed("forward")
+    store_ms, bwd_store_ms = timed("store")
+    rec_ms, bwd_rec_ms = timed("recompute")
+    clk = clocks.stop()
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+    nhit = int((hits[:, 1].view(torch.int32) != -1).sum().item())
+    if dist:
+        t = torch.tensor([fwd_ms, store_ms, rec_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        fwd_ms, store_ms, rec_ms = (float(x) for x in t.tolist())
+
+    # backward (stored hits): per pixel the ray, hit record, visibility byte and dL/dI in;
+    # the mesh tables (indices, positions, colours) and the gradients are a few tens of KB
+    tables = P.mesh.indices.nbytes + P.mesh.vertices.nbytes + P.colours.nbytes
+    nbytes = n * (RAY_BYTES + HIT_BYTES + 1 + 12) + 3 * tables
+    peaks, how = measured_peaks()
+    achieved = nbytes / (bwd_store_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "shadeBackwardKernel<false>", "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "peak_source": how, "traffic": ncu_traffic("shadeBackwardKernel<false>"),
+                "algorithmic_bytes_per_launch": int(nbytes), "launch_ms": round(bwd_store_ms, 4)}
+
+    # end to end: parameters up from pinned host memory, image and gradients back
+    ch = torch.from_numpy(P.colours).pin_memory()
+    lh = torch.from_numpy(P.light).pin_memory()
+    ph = torch.from_numpy(P.mesh.vertices).pin_memory()
+    outs = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (img, gc, gl, gp)]
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        ev[0].record(stream)
+        col.copy_(ch, non_blocking=True), light.copy_(lh, non_blocking=True), pos.copy_(ph, non_blocking=True)
+        forward(True)
+        backward(True, False)
+        for o, t in zip(outs, (img, gc, gl, gp)):
+            o.copy_(t, non_blocking=True)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        if k >= args.warmup:
+            e2e.append(ev[0].elapsed_time(ev[1]))
+    h2d = ch.numel() * 4 + lh.numel() * 4 + ph.numel() * 4
+    d2h = sum(o.numel() * 4 for o in outs)
+    line = {"metric": "adjoint fwd+bwd ms vs plain fwd ms, same GPU", "value": round(store_ms, 4), "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(store_ms, 4),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(ADJOINT, primary_hits=nhit, l2="flushed between steps", parallelism=f"replicas{world}"),
+            "plain_forward_ms": round(fwd_ms, 4), "fwd_bwd_over_fwd": round(store_ms / fwd_ms, 3),
+            "recompute_ms": round(rec_ms, 4), "backward_ms": {"stored": round(bwd_store_ms, 4),
+                                                              "recompute": round(bwd_rec_ms, 4)},
+            "stored_bytes_per_pixel": HIT_BYTES + 1, "roofline": roofline,
+            "e2e": {"value": round(statistics.mean(e2e), 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches["store"]), "gpu_launches_by_mode": launches, "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_adjoint(P, rays_np, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_adjoint(P, rays, target_s: float):
+    """The FP64 oracle's forward + analytic gradient on every k-th pixel, scaled to the
+    whole image (the gradient is a sum over pixels)."""
+    import oracle
+
+    v = P.mesh.vertices.astype(np.float64)
+    c, l = P.colours.astype(np.float64), P.light.astype(np.float64)
+
+    def run(stride):
+        r = rays[::stride]
+        tgt = np.zeros((r.shape[0], 3))
+        t0 = time.perf_counter()
+        oracle.lambert_forward(v, P.mesh.indices, c, l, r)
+        oracle.lambert_gradient(v, P.mesh.indices, c, l, r, tgt)
+        return time.perf_counter() - t0
+
+    dt = run(2003)
+    stride = max(1, int(2003 * dt / max(target_s, 1e-3)))
+    dt = run(stride)
+    return {"value": round(1e3 * dt * stride, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"every {stride}th pixel of the 1920x1080 image, FP64 forward + analytic gradient "
+                      f"({dt:.1f} s), scaled by {stride}"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world, local)
+    elif args.workload == ADJOINT["workload"]:
+        run_adjoint(args, rank, world, local)
     else:
         run_grt(args, rank, world, local)
 

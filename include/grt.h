@@ -313,6 +313,35 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
                                   uint64_t seed, float length, float* ao, const grtTraceOptions* options,
                                   void* stream);
 
+/* ---------------------------------------------------------------- differentiable Lambertian shading */
+/* Shading of the primary hits on a triangle geometry (the cosine law of Sec. 4.1 with
+ * the Lambert BRDF c/pi of Sec. 5.2, the constant pi folded into the caller's loss
+ * scale). For pixel p with hit (prim, t, u, v) from grtTraceClosest on `geom`:
+ *   n_f = normalize((v1-v0) x (v2-v0)) turned to face the ray, s = max(0, n_f . l)
+ *   with l = light[0..2] used as given (not normalised), V = 0 if the shadow ray from
+ *   o + t d + 1e-4 n_f along l (t in [0, inf)) hits `geom` (any hit), else 1,
+ *   c(u,v) = (1-u-v) c[i0] + u c[i1] + v c[i2] from per-vertex colours,
+ *   image[p] = V s c(u,v) (3 float32); 0 for a miss or an unlit pixel.
+ * indices (3 uint32 per triangle), positions and colours (3 float32 per vertex) are the
+ * mesh the geometry was built from; light is 3 float32; all device pointers.
+ * visibility (pixelCount bytes, may be NULL) receives V for the backward pass. */
+grtError grtShadeLambert(grtContext ctx, grtGeometry geom, const grtRay* rays, const grtHit* hits, uint32_t pixelCount,
+                         const uint32_t* indices, const float* positions, const float* colours, const float* light,
+                         float* image, uint8_t* visibility, const grtTraceOptions* options, void* stream);
+
+/* Adjoint of grtShadeLambert: given gradImage = dL/dimage (3 float32 per pixel), ADDS
+ * dL/dcolours (3 per vertex), dL/dlight (3) and dL/dpositions (3 per vertex) into the
+ * caller's buffers. Positions are differentiated through the face normal and through
+ * the hit's barycentrics on the fixed primary ray (interior hits: visibility and the
+ * hit triangle are piecewise constant and contribute nothing). hits and visibility as
+ * stored by the forward pass; hits = NULL recomputes the primary hits (refined in FP64)
+ * and the visibility by tracing again, trading time for 21 bytes per pixel. */
+grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay* rays, const grtHit* hits,
+                                 const uint8_t* visibility, uint32_t pixelCount, const uint32_t* indices,
+                                 const float* positions, const float* colours, const float* light,
+                                 const float* gradImage, float* gradColours, float* gradLight, float* gradPositions,
+                                 const grtTraceOptions* options, void* stream);
+
 /* ---------------------------------------------------------------- introspection and building blocks */
 /* Device-side layout of a built geometry or scene, for tests and tools. */
 typedef struct grtBvhInfo {

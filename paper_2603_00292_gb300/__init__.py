@@ -135,6 +135,9 @@ _SIGS = {
     "grtGetBvhInfo": [_P, _P, _P, ctypes.POINTER(grtBvhInfo)],
     "grtGetBuildTemporaryLayout": [_U32, _U32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                    ctypes.POINTER(ctypes.c_size_t)],
+    "grtShadeLambert": [_P, _P, _P, _P, _U32, _P, _P, _P, _P, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
+    "grtShadeLambertBackward": [_P, _P, _P, _P, _P, _U32, _P, _P, _P, _P, _P, _P, _P, _P,
+                                ctypes.POINTER(grtTraceOptions), _P],
     "grtGetLaunchCount": [ctypes.POINTER(ctypes.c_uint64)],
     "grtGetTraceStatistics": [_P, _P, ctypes.c_void_p],
     "grtSortTemporaryBufferSize": [_U32, _U32, ctypes.POINTER(ctypes.c_size_t)],
@@ -342,6 +345,22 @@ def grtTraceAmbientOcclusion(ctx, scene, primary_rays, primary_hits, pixels, spp
     check(lib().grtTraceAmbientOcclusion(ctx, scene, _ptr(primary_rays), _ptr(primary_hits), pixels, spp, seed, length,
                                          _ptr(ao), ctypes.byref(opts) if opts else None, _stream(stream)),
           "grtTraceAmbientOcclusion")
+
+
+def grtShadeLambert(ctx, geom, rays, hits, count, indices, positions, colours, light, image, visibility=None,
+                    opts=None, stream=None):
+    check(lib().grtShadeLambert(ctx, geom, _ptr(rays), _ptr(hits), count, _ptr(indices), _ptr(positions),
+                                _ptr(colours), _ptr(light), _ptr(image), _ptr(visibility),
+                                ctypes.byref(opts) if opts else None, _stream(stream)), "grtShadeLambert")
+
+
+def grtShadeLambertBackward(ctx, geom, rays, hits, visibility, count, indices, positions, colours, light, grad_image,
+                            grad_colours, grad_light, grad_positions, opts=None, stream=None):
+    check(lib().grtShadeLambertBackward(ctx, geom, _ptr(rays), _ptr(hits), _ptr(visibility), count, _ptr(indices),
+                                        _ptr(positions), _ptr(colours), _ptr(light), _ptr(grad_image),
+                                        _ptr(grad_colours), _ptr(grad_light), _ptr(grad_positions),
+                                        ctypes.byref(opts) if opts else None, _stream(stream)),
+          "grtShadeLambertBackward")
 
 
 def grtGetBvhInfo(ctx, geom=None, scene=None) -> grtBvhInfo:

@@ -201,6 +201,189 @@ __global__ void aoFinishKernel(const uint32_t* __restrict__ list, const uint32_t
     }
 }
 
+// ---------------------------------------------------------------- Lambertian shading and its adjoint
+// Per pixel with a primary hit on a triangle geometry: n_f = the face normal turned
+// toward the viewer; s = max(0, n_f . l) with l used as given (the cosine law of Sec.
+// 4.1; the Lambert BRDF c/pi of Sec. 5.2 with pi folded into the loss scale); V = 1
+// unless the shadow ray from p + 1e-4 n_f along l (any hit, t in [0, inf)) is blocked;
+// c(u,v) interpolates per-vertex colours; I = V s c(u,v), 0 for a miss.
+struct ShadeParams {
+    const float4* rays;
+    const uint32_t* hits;  // 5 words per pixel
+    uint32_t n;
+    const uint32_t* idx;   // 3 per triangle
+    const float* pos;      // 3 per vertex
+    const float* col;      // 3 per vertex
+    const float* light;    // 3
+    float* image;          // 3 per pixel
+    uint8_t* vis;          // per pixel, or null
+    const float* gimg;     // adjoint: dL/dI, 3 per pixel
+    float* gcol;
+    float* glight;
+    float* gpos;
+};
+
+struct ShadeHit {
+    float3 v0, v1, v2, o, d, nf;
+    float nl, u, v, t;
+    uint32_t i0, i1, i2;
+};
+
+__device__ __forceinline__ float3 ld3(const float* p, uint32_t k) { return make_float3(p[3 * k], p[3 * k + 1], p[3 * k + 2]); }
+
+__device__ __forceinline__ ShadeHit shadeSetup(const ShadeParams& S, float4 ra, float4 rb, uint32_t prim, float t,
+                                               float u, float v, float3 l) {
+    ShadeHit H;
+    H.i0 = S.idx[3 * (size_t)prim], H.i1 = S.idx[3 * (size_t)prim + 1], H.i2 = S.idx[3 * (size_t)prim + 2];
+    H.v0 = ld3(S.pos, H.i0), H.v1 = ld3(S.pos, H.i1), H.v2 = ld3(S.pos, H.i2);
+    H.o = f3(ra), H.d = f3(rb);
+    float3 n = normalize3(cross3(H.v1 - H.v0, H.v2 - H.v0));
+    if (dot3(n, H.d) > 0.0f) n = n * -1.0f;
+    H.nf = n;
+    H.nl = dot3(n, l);
+    H.t = t, H.u = u, H.v = v;
+    return H;
+}
+
+__device__ __forceinline__ float3 shadeColour(const ShadeParams& S, const ShadeHit& H) {
+    const float w0 = 1.0f - H.u - H.v;
+    const float3 c0 = ld3(S.col, H.i0), c1 = ld3(S.col, H.i1), c2 = ld3(S.col, H.i2);
+    return make_float3(w0 * c0.x + H.u * c1.x + H.v * c2.x, w0 * c0.y + H.u * c1.y + H.v * c2.y,
+                       w0 * c0.z + H.u * c1.z + H.v * c2.z);
+}
+
+// Items = pixels; a lit hit pixel traces its shadow ray, everything else is written at once.
+struct ShadowSource {
+    const ShadeParams* S;
+    __device__ unsigned long long count() const { return S->n; }
+    __device__ bool begin(uint32_t i, const TraceParams& P, Stack& st, RayState& s) const {
+        const uint32_t* h = S->hits + 5 * (size_t)i;
+        const uint32_t prim = h[1];
+        if (prim != kInvalid) {
+            const float3 l = make_float3(S->light[0], S->light[1], S->light[2]);
+            const ShadeHit H = shadeSetup(*S, S->rays[2 * (size_t)i], S->rays[2 * (size_t)i + 1], prim,
+                                          __uint_as_float(h[2]), __uint_as_float(h[3]), __uint_as_float(h[4]), l);
+            if (H.nl > 0.0f) {
+                beginRay<false>(P, st, s, (H.o + H.d * H.t) + H.nf * 1e-4f, l, 0.0f, INFINITY);
+                return true;
+            }
+        }
+        S->image[3 * (size_t)i] = 0.f, S->image[3 * (size_t)i + 1] = 0.f, S->image[3 * (size_t)i + 2] = 0.f;
+        if (S->vis) S->vis[i] = 1;
+        return false;
+    }
+    __device__ void finish(uint32_t i, const RayState& s) const {
+        const uint32_t* h = S->hits + 5 * (size_t)i;
+        const float3 l = make_float3(S->light[0], S->light[1], S->light[2]);
+        const ShadeHit H = shadeSetup(*S, S->rays[2 * (size_t)i], S->rays[2 * (size_t)i + 1], h[1],
+                                      __uint_as_float(h[2]), __uint_as_float(h[3]), __uint_as_float(h[4]), l);
+        const float V = s.best.prim == kInvalid ? 1.0f : 0.0f;
+        const float3 c = shadeColour(*S, H);
+        const float k = V * H.nl;
+        S->image[3 * (size_t)i] = k * c.x, S->image[3 * (size_t)i + 1] = k * c.y, S->image[3 * (size_t)i + 2] = k * c.z;
+        if (S->vis) S->vis[i] = (uint8_t)V;
+    }
+};
+
+__global__ void shadeForwardKernel(TraceParams P, ShadeParams S) {
+    extern __shared__ uint32_t sstack[];
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
+    ShadowSource src{&S};
+    refillLoop<true, false, false>(P, st, src);
+}
+
+// Adjoint: one thread per pixel. With RECOMPUTE the primary hit (refined in FP64) and
+// the visibility are traced again instead of read.
+template <bool RECOMPUTE>
+__global__ void shadeBackwardKernel(TraceParams P, ShadeParams S) {
+    extern __shared__ uint32_t sstack[];
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
+    const float3 l = make_float3(S.light[0], S.light[1], S.light[2]);
+    float3 gl = make_float3(0.f, 0.f, 0.f);
+    for (uint32_t i = gtid; i < S.n; i += gridDim.x * blockDim.x) {
+        const float4 ra = S.rays[2 * (size_t)i], rb = S.rays[2 * (size_t)i + 1];
+        uint32_t prim;
+        float t, u, v, V;
+        if (RECOMPUTE) {
+            Hit h = traceRay<false, false>(P, st, f3(ra), f3(rb), ra.w, rb.w);
+            prim = h.prim;
+            if (prim == kInvalid) continue;
+            const float4* rec = reinterpret_cast<const float4*>(P.target.leaves) + 3 * (size_t)P.targetPrimToLeaf[prim];
+            const float4 r = refine64(P.inv64, false, 0, f3(ra), f3(rb), rec, false, ra.w, rb.w);
+            if (r.w != 0.f) h.t = r.x, h.u = r.y, h.v = r.z;
+            t = h.t, u = h.u, v = h.v;
+        } else {
+            const uint32_t* h = S.hits + 5 * (size_t)i;
+            prim = h[1];
+            if (prim == kInvalid) continue;
+            t = __uint_as_float(h[2]), u = __uint_as_float(h[3]), v = __uint_as_float(h[4]);
+        }
+        const ShadeHit H = shadeSetup(S, ra, rb, prim, t, u, v, l);
+        if (!(H.nl > 0.0f)) continue;  // unlit: I = 0 and no gradient
+        if (RECOMPUTE) {
+            const Hit sh = traceRay<true, false>(P, st, (H.o + H.d * H.t) + H.nf * 1e-4f, l, 0.0f, INFINITY);
+            V = sh.prim == kInvalid ? 1.0f : 0.0f;
+        } else {
+            V = S.vis ? (float)S.vis[i] : 1.0f;
+        }
+        if (V == 0.0f) continue;
+        const float3 g = make_float3(S.gimg[3 * (size_t)i], S.gimg[3 * (size_t)i + 1], S.gimg[3 * (size_t)i + 2]);
+        const float w[3] = {1.0f - u - v, u, v};
+        const uint32_t vk[3] = {H.i0, H.i1, H.i2};
+        const float s = H.nl;
+        // colours: dI/dc_k = s w_k per channel
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(&S.gcol[3 * (size_t)vk[k]], g.x * s * w[k]);
+            atomicAdd(&S.gcol[3 * (size_t)vk[k] + 1], g.y * s * w[k]);
+            atomicAdd(&S.gcol[3 * (size_t)vk[k] + 2], g.z * s * w[k]);
+        }
+        const float3 c = shadeColour(S, H);
+        const float gs = dot3(g, c);
+        gl = gl + H.nf * gs;  // light, where lit
+        // positions through the face normal: m = e1 x e2, n = m / |m|, n_f = sigma n
+        const float3 e1 = H.v1 - H.v0, e2 = H.v2 - H.v0;
+        const float3 m = cross3(e1, e2);
+        const float ml = sqrtf(dot3(m, m));
+        const float3 n = m * (1.0f / ml);
+        const float sigma = dot3(H.nf, n) > 0.f ? 1.f : -1.f;
+        const float3 gm = (l - n * dot3(n, l)) * (gs * sigma / ml);
+        float3 dv0 = cross3(e1 - e2, gm), dv1 = cross3(e2, gm), dv2 = cross3(gm, e1);
+        // positions through the barycentrics on the fixed ray: d(t,u,v)/dv_k = -w_k A^-1, A = [-d | e1 | e2]
+        const float3 c0 = ld3(S.col, H.i0), c1 = ld3(S.col, H.i1), c2 = ld3(S.col, H.i2);
+        const float gu = s * dot3(g, c1 - c0), gv = s * dot3(g, c2 - c0);
+        const float3 nd = H.d * -1.0f;
+        const float det = dot3(nd, cross3(e1, e2));
+        if (det != 0.0f) {
+            const float3 y = (cross3(e2, nd) * gu + cross3(nd, e1) * gv) * (1.0f / det);
+            dv0 = dv0 - y * w[0];
+            dv1 = dv1 - y * w[1];
+            dv2 = dv2 - y * w[2];
+        }
+        const float3 dv[3] = {dv0, dv1, dv2};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(&S.gpos[3 * (size_t)vk[k]], dv[k].x);
+            atomicAdd(&S.gpos[3 * (size_t)vk[k] + 1], dv[k].y);
+            atomicAdd(&S.gpos[3 * (size_t)vk[k] + 2], dv[k].z);
+        }
+    }
+    // light gradient: warp sum, one atomic per warp and axis
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gl.x += __shfl_xor_sync(0xffffffffu, gl.x, o);
+        gl.y += __shfl_xor_sync(0xffffffffu, gl.y, o);
+        gl.z += __shfl_xor_sync(0xffffffffu, gl.z, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&S.glight[0], gl.x);
+        atomicAdd(&S.glight[1], gl.y);
+        atomicAdd(&S.glight[2], gl.z);
+    }
+}
+
 // ---------------------------------------------------------------- camera rays (Sec. 3.2)
 __global__ void cameraRayKernel(grtCamera cam, uint32_t W, uint32_t H, float4* out) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -561,6 +744,85 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
     aoFinishKernel<<<smCount(c) * 4, 256, 0, s>>>(list, listCount, samplesPerPixel, ao);
     GRT_LAUNCH_CHECK();
     noteLaunches(3);
+    return GRT_SUCCESS;
+}
+
+static grtError prepareShade(grtContext ctx, grtGeometry geom, const grtRay* rays, uint32_t n, const uint32_t* indices,
+                             const float* positions, const float* colours, const float* light,
+                             const grtTraceOptions* options, TraceParams& P, ShadeParams& S, int* bs) {
+    if (!ctx || !geom) return GRT_ERROR_INVALID_PARAMETER;
+    BvhObject* o = findBvh(geom);
+    if (!o || o->primType != GRT_PRIMITIVE_TRIANGLE_MESH) return GRT_ERROR_INVALID_PARAMETER;
+    bool isScene = false;
+    grtError e = prepareTrace(asContext(ctx), nullptr, geom, nullptr, options, P, &isScene, bs);
+    if (e != GRT_SUCCESS) return e;
+    if (n && (!rays || !indices || !positions || !colours || !light || ((uintptr_t)rays & 15)))
+        return GRT_ERROR_INVALID_PARAMETER;
+    S.rays = (const float4*)rays;
+    S.n = n;
+    S.idx = indices;
+    S.pos = positions;
+    S.col = colours;
+    S.light = light;
+    return GRT_SUCCESS;
+}
+
+grtError grtShadeLambert(grtContext ctx, grtGeometry geom, const grtRay* rays, const grtHit* hits, uint32_t pixelCount,
+                         const uint32_t* indices, const float* positions, const float* colours, const float* light,
+                         float* image, uint8_t* visibility, const grtTraceOptions* options, void* stream) {
+    TraceParams P{};
+    ShadeParams S{};
+    int bs = 128;
+    grtError e = prepareShade(ctx, geom, rays, pixelCount, indices, positions, colours, light, options, P, S, &bs);
+    if (e != GRT_SUCCESS || pixelCount == 0) return e;
+    if (!hits || !image) return GRT_ERROR_INVALID_PARAMETER;
+    S.hits = (const uint32_t*)hits;
+    S.image = image;
+    S.vis = visibility;
+    Context* c = asContext(ctx);
+    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    LaunchShape L = persistentShape(c, shadeForwardKernel, bs, smem);
+    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(pixelCount, bs));
+    e = bindGlobalStack(c, options, L.blocks * bs, P);
+    if (e != GRT_SUCCESS) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    P.counter = nextCounter(c);
+    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
+    shadeForwardKernel<<<L.blocks, bs, smem, s>>>(P, S);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay* rays, const grtHit* hits,
+                                 const uint8_t* visibility, uint32_t pixelCount, const uint32_t* indices,
+                                 const float* positions, const float* colours, const float* light,
+                                 const float* gradImage, float* gradColours, float* gradLight, float* gradPositions,
+                                 const grtTraceOptions* options, void* stream) {
+    TraceParams P{};
+    ShadeParams S{};
+    int bs = 128;
+    grtError e = prepareShade(ctx, geom, rays, pixelCount, indices, positions, colours, light, options, P, S, &bs);
+    if (e != GRT_SUCCESS || pixelCount == 0) return e;
+    if (!gradImage || !gradColours || !gradLight || !gradPositions) return GRT_ERROR_INVALID_PARAMETER;
+    const bool recompute = hits == nullptr;
+    S.hits = (const uint32_t*)hits;
+    S.vis = const_cast<uint8_t*>(visibility);
+    S.gimg = gradImage;
+    S.gcol = gradColours;
+    S.glight = gradLight;
+    S.gpos = gradPositions;
+    Context* c = asContext(ctx);
+    void (*kernel)(TraceParams, ShadeParams) = recompute ? shadeBackwardKernel<true> : shadeBackwardKernel<false>;
+    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    LaunchShape L = persistentShape(c, kernel, bs, smem);
+    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(pixelCount, bs));
+    e = bindGlobalStack(c, options, L.blocks * bs, P);
+    if (e != GRT_SUCCESS) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    kernel<<<L.blocks, bs, smem, s>>>(P, S);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
     return GRT_SUCCESS;
 }
 

@@ -357,6 +357,36 @@ def overview_camera(scene: InstancedScene, width: int, height: int) -> Camera:
 
 
 @dataclass
+class ShadingProblem:
+    mesh: Mesh
+    camera: Camera
+    colours: np.ndarray         # float32 (V,3), uniform in [0,1]
+    light: np.ndarray           # float32 (3,), normalize(1,1,1)
+    target_colours: np.ndarray  # colours + U[-0.1, 0.1], unclamped
+    target_light: np.ndarray    # light rotated by U[0,5] degrees about a random perpendicular axis
+
+
+def shading_problem(width: int = 1920, height: int = 1080, seed: int = MASTER_SEED, config: int = 4,
+                    level: int = 3) -> ShadingProblem:
+    """The differentiable-shading workload: the icosphere seen by the (0,0,3) camera with
+    per-vertex colours and one directional light, plus the perturbed target parameters."""
+    mesh = icosphere(level)
+    key = stream_key(seed, config, 0x5AD)
+    nv = mesh.vertices.shape[0]
+    cols = uniform(stream_key(key, 1), 3 * nv).reshape(nv, 3)
+    tcols = cols + (-0.1 + 0.2 * uniform(stream_key(key, 2), 3 * nv).reshape(nv, 3))
+    light = np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0)
+    u = unit_vectors(stream_key(key, 3), 1)[0]
+    axis = np.cross(light, u)
+    axis /= np.linalg.norm(axis)
+    ang = math.radians(5.0 * float(uniform(stream_key(key, 4), 1)[0]))
+    tlight = light * math.cos(ang) + np.cross(axis, light) * math.sin(ang)
+    cam = look_down_z_camera([0, 0, 3], width, height)
+    return ShadingProblem(mesh, cam, cols.astype(np.float32), light.astype(np.float32), tcols.astype(np.float32),
+                          tlight.astype(np.float32))
+
+
+@dataclass
 class Soup:
     mesh: Mesh
     num_rays: int
