@@ -497,15 +497,16 @@ def run_adjoint(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         fwd_ms, store_ms, rec_ms = (float(x) for x in t.tolist())
 
-    # backward (stored hits): per pixel the ray, hit record, visibility byte and dL/dI in;
-    # the mesh tables (indices, positions, colours) and the gradients are a few tens of KB
+    # backward (stored hits): the hit record of every pixel; the ray, visibility byte and
+    # dL/dI of each hit pixel; the mesh tables (indices, positions, colours) read and the
+    # colour and position gradients written once (a few tens of KB)
     tables = P.mesh.indices.nbytes + P.mesh.vertices.nbytes + P.colours.nbytes
-    nbytes = n * (RAY_BYTES + HIT_BYTES + 1 + 12) + 3 * tables
+    nbytes = n * HIT_BYTES + nhit * (RAY_BYTES + 1 + 12) + tables + 2 * P.mesh.vertices.nbytes
     peaks, how = measured_peaks()
     achieved = nbytes / (bwd_store_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "shadeBackwardKernel<false>", "achieved": round(achieved, 1),
+    roofline = {"bound": "hbm", "kernel": "shadeBackwardKernel<false, true>", "achieved": round(achieved, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "peak_source": how, "traffic": ncu_traffic("shadeBackwardKernel<false>"),
+                "peak_source": how, "traffic": ncu_traffic("shadeBackwardKernel<false, true>"),
                 "algorithmic_bytes_per_launch": int(nbytes), "launch_ms": round(bwd_store_ms, 4)}
 
     # end to end: parameters up from pinned host memory, image and gradients back

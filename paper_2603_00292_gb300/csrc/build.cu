@@ -770,6 +770,7 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
     Context* c = asContext(ctx);
     cudaStream_t s = (cudaStream_t)stream;
     o->geomType = input->geomType;
+    if (input->type == GRT_PRIMITIVE_TRIANGLE_MESH) o->vertexCount = input->triangleMesh.vertexCount;
     if (n == 0) {
         o->built = true;
         return GRT_SUCCESS;

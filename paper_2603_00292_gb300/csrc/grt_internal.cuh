@@ -116,6 +116,7 @@ struct BvhObject {
     uint32_t primType;
     uint32_t geomType;
     uint32_t mortonBits;
+    uint32_t vertexCount;  // triangle meshes: the vertex count of the last build input
     bool built;
 };
 BvhObject* findBvh(const void* handle);

@@ -293,81 +293,167 @@ __global__ void shadeForwardKernel(TraceParams P, ShadeParams S) {
     refillLoop<true, false, false>(P, st, src);
 }
 
-// Adjoint: one thread per pixel. With RECOMPUTE the primary hit (refined in FP64) and
-// the visibility are traced again instead of read.
+// One pixel's share of the adjoint: dL/dc_k and dL/dv_k for the hit triangle's three
+// vertices, and its term of dL/dl. live = false for a miss, an unlit or a shadowed pixel.
+struct PixelAdjoint {
+    bool live;
+    uint32_t prim;
+    uint32_t vk[3];
+    float3 dc[3], dv[3];
+    float3 dl;
+};
+
 template <bool RECOMPUTE>
-__global__ void shadeBackwardKernel(TraceParams P, ShadeParams S) {
+__device__ __forceinline__ PixelAdjoint pixelAdjoint(const TraceParams& P, const ShadeParams& S, Stack& st,
+                                                     uint32_t i, float3 l) {
+    PixelAdjoint A;
+    A.live = false;
+    uint32_t prim;
+    float t, u, v, V;
+    float4 ra, rb;
+    if (RECOMPUTE) {
+        ra = S.rays[2 * (size_t)i], rb = S.rays[2 * (size_t)i + 1];
+        Hit h = traceRay<false, false>(P, st, f3(ra), f3(rb), ra.w, rb.w);
+        prim = h.prim;
+        if (prim == kInvalid) return A;
+        const float4* rec = reinterpret_cast<const float4*>(P.target.leaves) + 3 * (size_t)P.targetPrimToLeaf[prim];
+        const float4 r = refine64(P.inv64, false, 0, f3(ra), f3(rb), rec, false, ra.w, rb.w);
+        if (r.w != 0.f) h.t = r.x, h.u = r.y, h.v = r.z;
+        t = h.t, u = h.u, v = h.v;
+    } else {
+        const uint32_t* h = S.hits + 5 * (size_t)i;
+        prim = h[1];
+        if (prim == kInvalid) return A;  // a miss reads nothing else
+        t = __uint_as_float(h[2]), u = __uint_as_float(h[3]), v = __uint_as_float(h[4]);
+        ra = S.rays[2 * (size_t)i], rb = S.rays[2 * (size_t)i + 1];
+    }
+    const ShadeHit H = shadeSetup(S, ra, rb, prim, t, u, v, l);
+    if (!(H.nl > 0.0f)) return A;  // unlit: I = 0 and no gradient
+    if (RECOMPUTE) {
+        const Hit sh = traceRay<true, false>(P, st, (H.o + H.d * H.t) + H.nf * 1e-4f, l, 0.0f, INFINITY);
+        V = sh.prim == kInvalid ? 1.0f : 0.0f;
+    } else {
+        V = S.vis ? (float)S.vis[i] : 1.0f;
+    }
+    if (V == 0.0f) return A;
+    const float3 g = make_float3(S.gimg[3 * (size_t)i], S.gimg[3 * (size_t)i + 1], S.gimg[3 * (size_t)i + 2]);
+    const float w[3] = {1.0f - u - v, u, v};
+    const float s = H.nl;
+    A.live = true;
+    A.prim = prim;
+    A.vk[0] = H.i0, A.vk[1] = H.i1, A.vk[2] = H.i2;
+    // colours: dI/dc_k = s w_k per channel
+#pragma unroll
+    for (int k = 0; k < 3; ++k) A.dc[k] = g * (s * w[k]);
+    const float3 c0 = ld3(S.col, H.i0), c1 = ld3(S.col, H.i1), c2 = ld3(S.col, H.i2);
+    const float3 c = make_float3(w[0] * c0.x + u * c1.x + v * c2.x, w[0] * c0.y + u * c1.y + v * c2.y,
+                                 w[0] * c0.z + u * c1.z + v * c2.z);
+    const float gs = dot3(g, c);
+    A.dl = H.nf * gs;  // light, where lit
+    // positions through the face normal: m = e1 x e2, n = m / |m|, n_f = sigma n
+    const float3 e1 = H.v1 - H.v0, e2 = H.v2 - H.v0;
+    const float3 m = cross3(e1, e2);
+    const float ml = sqrtf(dot3(m, m));
+    const float3 n = m * (1.0f / ml);
+    const float sigma = dot3(H.nf, n) > 0.f ? 1.f : -1.f;
+    const float3 gm = (l - n * dot3(n, l)) * (gs * sigma / ml);
+    A.dv[0] = cross3(e1 - e2, gm), A.dv[1] = cross3(e2, gm), A.dv[2] = cross3(gm, e1);
+    // positions through the barycentrics on the fixed ray: d(t,u,v)/dv_k = -w_k A^-1, A = [-d | e1 | e2]
+    const float gu = s * dot3(g, c1 - c0), gv = s * dot3(g, c2 - c0);
+    const float3 nd = H.d * -1.0f;
+    const float det = dot3(nd, m);
+    if (det != 0.0f) {
+        const float3 y = (cross3(e2, nd) * gu + cross3(nd, e1) * gv) * (1.0f / det);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) A.dv[k] = A.dv[k] - y * w[k];
+    }
+    return A;
+}
+
+// Sum of x over lanes [lane, end] of a run of consecutive lanes (end = the run's last lane).
+__device__ __forceinline__ float runSum(float x, uint32_t lane, uint32_t end) {
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_down_sync(0xffffffffu, x, o);
+        if (lane + o <= end) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ float3 runSum3(float3 x, uint32_t lane, uint32_t end) {
+    return make_float3(runSum(x.x, lane, end), runSum(x.y, lane, end), runSum(x.z, lane, end));
+}
+
+// Adds one vertex's 3-vector into a block-private shared copy when there is one and the
+// vertex is inside it, else into the output in global memory.
+template <bool PRIV>
+__device__ __forceinline__ void addVertex3(float* priv, float* out, uint32_t nv, uint32_t k, float3 g) {
+    if (PRIV && k < nv) {
+        atomicAdd(priv + 3 * k, g.x), atomicAdd(priv + 3 * k + 1, g.y), atomicAdd(priv + 3 * k + 2, g.z);
+    } else {
+        atomicAdd(out + 3 * (size_t)k, g.x), atomicAdd(out + 3 * (size_t)k + 1, g.y),
+            atomicAdd(out + 3 * (size_t)k + 2, g.z);
+    }
+}
+
+// Warp-wide scatter of the vertex gradients (all 32 lanes call it). Neighbouring pixels
+// mostly hit the same triangle: each run of consecutive lanes with the same triangle is
+// summed by shuffles and its first lane adds the sums (18 atomics per run, not per pixel).
+template <bool PRIV>
+__device__ __forceinline__ void scatterAdjoint(const PixelAdjoint& A, float* priv, const ShadeParams& S, uint32_t nv) {
+    const unsigned full = 0xffffffffu;
+    if (!__any_sync(full, A.live)) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t key = A.live ? A.prim : kInvalid;
+    const uint32_t next = __shfl_down_sync(full, key, 1), prev = __shfl_up_sync(full, key, 1);
+    const unsigned ends = __ballot_sync(full, lane == 31u || next != key);
+    const uint32_t end = (uint32_t)__ffs(ends & (full << lane)) - 1u;
+    const bool head = lane == 0u || prev != key;
+    float3 dc[3], dv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dc[k] = runSum3(A.live ? A.dc[k] : make_float3(0.f, 0.f, 0.f), lane, end);
+        dv[k] = runSum3(A.live ? A.dv[k] : make_float3(0.f, 0.f, 0.f), lane, end);
+    }
+    if (head && A.live) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            addVertex3<PRIV>(priv, S.gcol, nv, A.vk[k], dc[k]);
+            addVertex3<PRIV>(priv + 3 * nv, S.gpos, nv, A.vk[k], dv[k]);
+        }
+    }
+}
+
+// Adjoint: blocks take tiles of consecutive pixels (image rows) from a work counter;
+// one thread per pixel. With PRIV the colour and position gradients of every vertex (6
+// floats each) are summed in shared memory and each block adds its nonzero entries to
+// the output once at the end: a small mesh's gradients sit in a few hundred cache lines,
+// and per-pixel global atomics on them queue in a few L2 slices. With RECOMPUTE the
+// primary hit (refined in FP64) and the visibility are traced again instead of read.
+template <bool RECOMPUTE, bool PRIV>
+__global__ void shadeBackwardKernel(TraceParams P, ShadeParams S, uint32_t nv) {
     extern __shared__ uint32_t sstack[];
+    __shared__ unsigned long long tile;
+    float* priv = reinterpret_cast<float*>(sstack + (RECOMPUTE ? blockDim.x * P.sharedDepth : 0));
+    if (PRIV)
+        for (uint32_t j = threadIdx.x; j < 6 * nv; j += blockDim.x) priv[j] = 0.0f;
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
     const float3 l = make_float3(S.light[0], S.light[1], S.light[2]);
     float3 gl = make_float3(0.f, 0.f, 0.f);
-    for (uint32_t i = gtid; i < S.n; i += gridDim.x * blockDim.x) {
-        const float4 ra = S.rays[2 * (size_t)i], rb = S.rays[2 * (size_t)i + 1];
-        uint32_t prim;
-        float t, u, v, V;
-        if (RECOMPUTE) {
-            Hit h = traceRay<false, false>(P, st, f3(ra), f3(rb), ra.w, rb.w);
-            prim = h.prim;
-            if (prim == kInvalid) continue;
-            const float4* rec = reinterpret_cast<const float4*>(P.target.leaves) + 3 * (size_t)P.targetPrimToLeaf[prim];
-            const float4 r = refine64(P.inv64, false, 0, f3(ra), f3(rb), rec, false, ra.w, rb.w);
-            if (r.w != 0.f) h.t = r.x, h.u = r.y, h.v = r.z;
-            t = h.t, u = h.u, v = h.v;
-        } else {
-            const uint32_t* h = S.hits + 5 * (size_t)i;
-            prim = h[1];
-            if (prim == kInvalid) continue;
-            t = __uint_as_float(h[2]), u = __uint_as_float(h[3]), v = __uint_as_float(h[4]);
-        }
-        const ShadeHit H = shadeSetup(S, ra, rb, prim, t, u, v, l);
-        if (!(H.nl > 0.0f)) continue;  // unlit: I = 0 and no gradient
-        if (RECOMPUTE) {
-            const Hit sh = traceRay<true, false>(P, st, (H.o + H.d * H.t) + H.nf * 1e-4f, l, 0.0f, INFINITY);
-            V = sh.prim == kInvalid ? 1.0f : 0.0f;
-        } else {
-            V = S.vis ? (float)S.vis[i] : 1.0f;
-        }
-        if (V == 0.0f) continue;
-        const float3 g = make_float3(S.gimg[3 * (size_t)i], S.gimg[3 * (size_t)i + 1], S.gimg[3 * (size_t)i + 2]);
-        const float w[3] = {1.0f - u - v, u, v};
-        const uint32_t vk[3] = {H.i0, H.i1, H.i2};
-        const float s = H.nl;
-        // colours: dI/dc_k = s w_k per channel
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            atomicAdd(&S.gcol[3 * (size_t)vk[k]], g.x * s * w[k]);
-            atomicAdd(&S.gcol[3 * (size_t)vk[k] + 1], g.y * s * w[k]);
-            atomicAdd(&S.gcol[3 * (size_t)vk[k] + 2], g.z * s * w[k]);
-        }
-        const float3 c = shadeColour(S, H);
-        const float gs = dot3(g, c);
-        gl = gl + H.nf * gs;  // light, where lit
-        // positions through the face normal: m = e1 x e2, n = m / |m|, n_f = sigma n
-        const float3 e1 = H.v1 - H.v0, e2 = H.v2 - H.v0;
-        const float3 m = cross3(e1, e2);
-        const float ml = sqrtf(dot3(m, m));
-        const float3 n = m * (1.0f / ml);
-        const float sigma = dot3(H.nf, n) > 0.f ? 1.f : -1.f;
-        const float3 gm = (l - n * dot3(n, l)) * (gs * sigma / ml);
-        float3 dv0 = cross3(e1 - e2, gm), dv1 = cross3(e2, gm), dv2 = cross3(gm, e1);
-        // positions through the barycentrics on the fixed ray: d(t,u,v)/dv_k = -w_k A^-1, A = [-d | e1 | e2]
-        const float3 c0 = ld3(S.col, H.i0), c1 = ld3(S.col, H.i1), c2 = ld3(S.col, H.i2);
-        const float gu = s * dot3(g, c1 - c0), gv = s * dot3(g, c2 - c0);
-        const float3 nd = H.d * -1.0f;
-        const float det = dot3(nd, cross3(e1, e2));
-        if (det != 0.0f) {
-            const float3 y = (cross3(e2, nd) * gu + cross3(nd, e1) * gv) * (1.0f / det);
-            dv0 = dv0 - y * w[0];
-            dv1 = dv1 - y * w[1];
-            dv2 = dv2 - y * w[2];
-        }
-        const float3 dv[3] = {dv0, dv1, dv2};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            atomicAdd(&S.gpos[3 * (size_t)vk[k]], dv[k].x);
-            atomicAdd(&S.gpos[3 * (size_t)vk[k] + 1], dv[k].y);
-            atomicAdd(&S.gpos[3 * (size_t)vk[k] + 2], dv[k].z);
+    const uint32_t perTile = blockDim.x * (RECOMPUTE ? 2u : 8u);
+    for (;;) {
+        if (threadIdx.x == 0) tile = atomicAdd(P.counter, 1ull);
+        __syncthreads();  // also orders the zeroing of priv before the first adds
+        const unsigned long long first = tile * perTile;
+        __syncthreads();  // every thread has read tile before thread 0 takes the next one
+        if (first >= S.n) break;
+        for (uint32_t k = threadIdx.x; k < perTile; k += blockDim.x) {  // same trip count in every lane
+            PixelAdjoint A;
+            A.live = false;
+            if (first + k < S.n) A = pixelAdjoint<RECOMPUTE>(P, S, st, (uint32_t)(first + k), l);
+            if (A.live) gl = gl + A.dl;
+            scatterAdjoint<PRIV>(A, priv, S, nv);
         }
     }
     // light gradient: warp sum, one atomic per warp and axis
@@ -381,6 +467,14 @@ __global__ void shadeBackwardKernel(TraceParams P, ShadeParams S) {
         atomicAdd(&S.glight[0], gl.x);
         atomicAdd(&S.glight[1], gl.y);
         atomicAdd(&S.glight[2], gl.z);
+    }
+    if (PRIV) {
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < 3 * nv; j += blockDim.x) {
+            const float a = priv[j], b = priv[3 * nv + j];
+            if (a != 0.0f) atomicAdd(&S.gcol[j], a);
+            if (b != 0.0f) atomicAdd(&S.gpos[j], b);
+        }
     }
 }
 
@@ -747,6 +841,9 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
     return GRT_SUCCESS;
 }
 
+// Shared-memory budget of the adjoint's block-private gradient copy (4,096 vertices).
+static constexpr size_t kShadePrivateBytes = 96 * 1024;
+
 static grtError prepareShade(grtContext ctx, grtGeometry geom, const grtRay* rays, uint32_t n, const uint32_t* indices,
                              const float* positions, const float* colours, const float* light,
                              const grtTraceOptions* options, TraceParams& P, ShadeParams& S, int* bs) {
@@ -813,14 +910,26 @@ grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay*
     S.glight = gradLight;
     S.gpos = gradPositions;
     Context* c = asContext(ctx);
-    void (*kernel)(TraceParams, ShadeParams) = recompute ? shadeBackwardKernel<true> : shadeBackwardKernel<false>;
-    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    // block-private gradient copy when the mesh's vertex count is known and its 24 bytes
+    // per vertex fit the budget
+    const uint32_t nv = findBvh(geom)->vertexCount;
+    const bool priv = nv > 0 && (size_t)nv * 24 <= kShadePrivateBytes;
+    void (*kernel)(TraceParams, ShadeParams, uint32_t) =
+        recompute ? (priv ? shadeBackwardKernel<true, true> : shadeBackwardKernel<true, false>)
+                  : (priv ? shadeBackwardKernel<false, true> : shadeBackwardKernel<false, false>);
+    const size_t smem = (recompute ? (size_t)bs * P.sharedDepth * sizeof(uint32_t) : 0) + (priv ? (size_t)nv * 24 : 0);
+    if (smem > 48 * 1024) GRT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LaunchShape L = persistentShape(c, kernel, bs, smem);
+    // replaying stored hits traces nothing: 8 blocks per SM keep each block's share of
+    // pixels large next to its pass over the private copy
+    if (!recompute) L.blocks = std::min(L.blocks, 8 * smCount(c));
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(pixelCount, bs));
     e = bindGlobalStack(c, options, L.blocks * bs, P);
     if (e != GRT_SUCCESS) return e;
     cudaStream_t s = (cudaStream_t)stream;
-    kernel<<<L.blocks, bs, smem, s>>>(P, S);
+    P.counter = nextCounter(c);
+    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
+    kernel<<<L.blocks, bs, smem, s>>>(P, S, priv ? nv : 0u);
     GRT_LAUNCH_CHECK();
     noteLaunches(1);
     return GRT_SUCCESS;

@@ -50,14 +50,14 @@ class Geometry:
     """A bottom-level BVH over an indexed triangle mesh or an AABB list."""
 
     def __init__(self, ctx: Context, *, vertices=None, indices=None, boxes=None, geom_type: int = 0,
-                 morton_bits: int = 0, temp: torch.Tensor | None = None):
+                 morton_bits: int = 0, temp: torch.Tensor | None = None, vertex_count: int | None = None):
         self.ctx = ctx
         if boxes is not None:
             self.boxes = boxes
             self.input = aabb_list_input(boxes, geom_type=geom_type)
         else:
             self.vertices, self.indices = vertices, indices
-            self.input = triangle_mesh_input(indices, vertices, geom_type=geom_type)
+            self.input = triangle_mesh_input(indices, vertices, vertex_count=vertex_count, geom_type=geom_type)
         self.options = build_options(morton_bits)
         self.temp_bytes = grtGetGeometryBuildTemporaryBufferSize(ctx.handle, self.input, self.options)
         self.temp = temp if temp is not None and temp.numel() >= self.temp_bytes else empty_bytes(self.temp_bytes)

@@ -84,6 +84,34 @@ def test_backward_matches_oracle_gradient(gpu, recompute):
     assert _rel_ok(gp, dp).mean() > 0.995, np.abs(gp - dp).max()
 
 
+@pytest.mark.parametrize("layout", ["global", "mixed"])
+def test_backward_accumulation_paths_agree(gpu, layout):
+    """The adjoint sums vertex gradients in a block-private shared-memory copy when the
+    geometry's vertex count fits it, else in global memory; a vertex index at or beyond
+    the declared count goes to global memory. All three give the same gradients."""
+    W, H = 320, 180
+    P, rays, verts64, target, d, g = _problem(gpu, W, H)
+    n = W * H
+    hits, img, vis = _gpu_forward(gpu, d, g, n)
+    gimg = 2.0 * (img - device_tensor(target.astype(np.float32)))
+    ref = _gpu_backward(gpu, d, g, n, hits, vis, gimg)
+    nv = P.mesh.vertices.shape[0]
+    if layout == "global":  # 5,000 unused vertices appended: above the shared-memory budget
+        extra = np.zeros((5000, 3), np.float32)
+        d2 = dict(d, pos=device_tensor(np.concatenate([P.mesh.vertices, extra])),
+                  col=device_tensor(np.concatenate([P.colours, extra])))
+        g2 = Geometry(gpu, vertices=d2["pos"], indices=d2["idx"]).build()
+    else:  # declared vertex count 100: indices 100..641 take the global path
+        d2 = d
+        g2 = Geometry(gpu, vertices=d["pos"], indices=d["idx"], vertex_count=100).build()
+    got = _gpu_backward(gpu, d2, g2, n, hits, vis, gimg)
+    for a, b in zip(got, ref):
+        a = a.reshape(-1, 3)[:nv] if a.size > 3 else a
+        assert np.allclose(a, b, rtol=1e-4, atol=1e-4 * np.abs(b).max())
+    if layout == "global":
+        assert not got[0][nv:].any() and not got[2][nv:].any()
+
+
 def test_autograd_function(gpu):
     W, H = 160, 90
     P, rays, verts64, target, d, g = _problem(gpu, W, H)
