@@ -342,6 +342,68 @@ grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay*
                                  const float* gradImage, float* gradColours, float* gradLight, float* gradPositions,
                                  const grtTraceOptions* options, void* stream);
 
+/* ---------------------------------------------------------------- batched build + trace */
+/* Many independent triangle geometries, each with its own ray batch, built and traced
+ * (closest hit) in one persistent launch that takes work items from a device queue.
+ * The paper builds and traces one geometry per call (Sec. 7.2-7.6) and has no batched
+ * form; each geometry ends up exactly as grtBuildGeometry(BUILD) would leave it and each
+ * hit record exactly as grtTraceClosest would write it. */
+typedef struct grtBatch_t* grtBatch;
+
+typedef struct grtBatchScene {
+    grtGeometry geometry;         /* from grtCreateGeometry on `input` (triangle mesh) */
+    grtGeometryBuildInput input;  /* the mesh (device pointers), read during every launch */
+    const grtRay* rays;           /* rayCount rays, 16-byte aligned (device) */
+    uint32_t rayCount;
+    grtHit* hits;                 /* rayCount closest-hit records (device) */
+} grtBatchScene;
+
+enum {
+    GRT_BATCH_FLAG_GRAPH = 1 /* capture the launch sequence once into a CUDA graph and replay it */
+};
+
+/* Tuning knobs (0 selects the default in brackets). */
+typedef struct grtBatchOptions {
+    uint32_t blockSize;         /* threads per block: 64, 128 or 256 [128] */
+    uint32_t sharedStackDepth;  /* traversal stack entries in shared memory, <= 32 [16] */
+    uint32_t globalStackDepth;  /* spill entries per thread, <= 4096 [64] */
+    float compactThreshold;     /* refill a warp when <= this fraction of lanes hold a ray [0.5] */
+    uint32_t smallScenePrims;   /* scenes up to this many triangles are built by one block [8192] */
+    uint32_t sortChunkTiles;    /* radix tiles (blockSize x 8 keys) per sort work item [8] */
+    uint32_t buildChunk;        /* primitives per prep / emission / fit work item [16384] */
+    uint32_t traceChunk;        /* rays per trace work item [16384] */
+    uint32_t flags;             /* GRT_BATCH_FLAG_* */
+} grtBatchOptions;
+
+typedef struct grtBatchInfo {
+    uint32_t sceneCount;
+    uint32_t itemCount;   /* work items per launch */
+    uint32_t smallScenes; /* scenes built by a single block */
+    uint32_t blocks;      /* persistent grid */
+    uint32_t blockSize;
+    uint32_t pad;
+    size_t deviceBytes;   /* library-owned device memory of the batch (scratch, queue, stacks) */
+} grtBatchInfo;
+
+/* Plans the work items and allocates the batch's device memory (scratch for every
+ * scene's build, the queue and the traversal stacks), so that a launch allocates
+ * nothing. Every geometry must be a triangle-mesh geometry created from its input's
+ * triangle count; the scenes' buffers must stay valid while the batch is used.
+ * Errors: GRT_ERROR_INVALID_PARAMETER (bad option, input, geometry or buffer),
+ * GRT_ERROR_OUT_OF_MEMORY. */
+grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sceneCount,
+                        const grtBatchOptions* options, grtBatch* batch);
+
+/* Builds every geometry and traces every scene's rays on `stream`: a small reset kernel
+ * and the persistent kernel, or their CUDA graph with GRT_BATCH_FLAG_GRAPH (captured on
+ * the first call). Work items wait for the items they depend on with bounded waits; an
+ * expired wait latches GRT_ERROR_TIMEOUT (read with grtGetLastDeviceError). Launches of
+ * one batch must not overlap. */
+grtError grtBatchBuildTrace(grtContext ctx, grtBatch batch, void* stream);
+
+grtError grtGetBatchInfo(grtContext ctx, grtBatch batch, grtBatchInfo* info);
+grtError grtDestroyBatch(grtContext ctx, grtBatch batch);
+
 /* ---------------------------------------------------------------- introspection and building blocks */
 /* Device-side layout of a built geometry or scene, for tests and tools. */
 typedef struct grtBvhInfo {

@@ -99,6 +99,26 @@ class grtBvhInfo(ctypes.Structure):
                 ("mortonBits", ctypes.c_uint32)]
 
 
+class grtBatchScene(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_void_p), ("input", grtGeometryBuildInput), ("rays", ctypes.c_void_p),
+                ("rayCount", ctypes.c_uint32), ("hits", ctypes.c_void_p)]
+
+
+class grtBatchOptions(ctypes.Structure):
+    _fields_ = [("blockSize", ctypes.c_uint32), ("sharedStackDepth", ctypes.c_uint32),
+                ("globalStackDepth", ctypes.c_uint32), ("compactThreshold", ctypes.c_float),
+                ("smallScenePrims", ctypes.c_uint32), ("sortChunkTiles", ctypes.c_uint32),
+                ("buildChunk", ctypes.c_uint32), ("traceChunk", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class grtBatchInfo(ctypes.Structure):
+    _fields_ = [("sceneCount", ctypes.c_uint32), ("itemCount", ctypes.c_uint32), ("smallScenes", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32), ("blockSize", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("deviceBytes", ctypes.c_size_t)]
+
+
+GRT_BATCH_FLAG_GRAPH = 1
+
 # ------------------------------------------------------------------ loading
 _lib = None
 
@@ -142,6 +162,10 @@ _SIGS = {
     "grtGetTraceStatistics": [_P, _P, ctypes.c_void_p],
     "grtSortTemporaryBufferSize": [_U32, _U32, ctypes.POINTER(ctypes.c_size_t)],
     "grtSortPairs": [_P, _P, _P, _U32, _U32, _U32, _P, _P],
+    "grtCreateBatch": [_P, ctypes.POINTER(grtBatchScene), _U32, ctypes.POINTER(grtBatchOptions), ctypes.POINTER(_P)],
+    "grtBatchBuildTrace": [_P, _P, _P],
+    "grtGetBatchInfo": [_P, _P, ctypes.POINTER(grtBatchInfo)],
+    "grtDestroyBatch": [_P, _P],
 }
 
 
@@ -406,3 +430,35 @@ def grtSortTemporaryBufferSize(count: int, key_bits: int) -> int:
 def grtSortPairs(ctx, keys, values, count, key_bits, significant_bits, temp, stream=None):
     check(lib().grtSortPairs(ctx, _ptr(keys), _ptr(values), count, key_bits, significant_bits, _ptr(temp),
                              _stream(stream)), "grtSortPairs")
+
+
+def batch_options(block_size=0, shared_depth=0, global_depth=0, compact=0.0, small_scene_prims=0,
+                  sort_chunk_tiles=0, build_chunk=0, trace_chunk=0, graph=False) -> grtBatchOptions:
+    return grtBatchOptions(block_size, shared_depth, global_depth, compact, small_scene_prims, sort_chunk_tiles,
+                           build_chunk, trace_chunk, GRT_BATCH_FLAG_GRAPH if graph else 0)
+
+
+def batch_scene(geometry: int, inp: grtGeometryBuildInput, rays, ray_count: int, hits) -> grtBatchScene:
+    return grtBatchScene(geometry, inp, _ptr(rays), ray_count, _ptr(hits))
+
+
+def grtCreateBatch(ctx, scenes, opts=None) -> int:
+    arr = (grtBatchScene * max(1, len(scenes)))(*scenes)
+    out = _P()
+    check(lib().grtCreateBatch(ctx, arr, len(scenes), ctypes.byref(opts) if opts is not None else None,
+                               ctypes.byref(out)), "grtCreateBatch")
+    return out.value
+
+
+def grtBatchBuildTrace(ctx, batch, stream=None):
+    check(lib().grtBatchBuildTrace(ctx, batch, _stream(stream)), "grtBatchBuildTrace")
+
+
+def grtGetBatchInfo(ctx, batch) -> grtBatchInfo:
+    info = grtBatchInfo()
+    check(lib().grtGetBatchInfo(ctx, batch, ctypes.byref(info)), "grtGetBatchInfo")
+    return info
+
+
+def grtDestroyBatch(ctx, batch):
+    check(lib().grtDestroyBatch(ctx, batch), "grtDestroyBatch")

@@ -1,0 +1,776 @@
+// Batched build and trace: many independent triangle geometries, each with its own
+// ray batch, built (LBVH) and traced (closest hit) in one persistent launch that takes
+// work items from a device queue.
+//
+// The paper builds and traces one geometry or scene per call (Sec. 7.2-7.6); this
+// scheduler has no counterpart there. Every item runs the same per-element work as the
+// per-geometry path (lbvh.cuh, traverse.cuh), so each geometry ends up bit-identical to
+// a grtBuildGeometry of the same input and each hit record identical to grtTraceClosest.
+//
+// Items. A scene of more than smallScenePrims primitives is split into phases, each a
+// set of chunk items:
+//   0            prep: centroids, centroid bounds (atomics), zeroed fit counters
+//   1 + 3p       radix pass p, digit histograms per chunk (pass 0 also writes the
+//                Morton codes)
+//   2 + 3p       radix pass p, exclusive scan of the histograms (one item)
+//   3 + 3p       radix pass p, stable scatter per chunk
+//   1 + 3P       Karras emission over internal-node chunks
+//   2 + 3P       bottom-up fit over leaf chunks
+//   3 + 3P       closest-hit trace over ray chunks (refill loop), then FP64 refinement
+// A smaller scene is built entirely by one block (phase 0) and traced in phase 1.
+// An item of phase k waits until every item of phase k-1 of its scene has finished
+// (per-scene completion counters). The host orders the queue so that an item only
+// ever waits for items taken from the queue before it, so a waiting block never
+// blocks the progress it waits for; every wait is bounded in time all the same and
+// latches GRT_ERROR_TIMEOUT if it expires.
+//
+// Memory. Data written earlier in the launch by another block (centroids, keys,
+// histograms, parents, boxes) is read with L1-bypassing loads. Node and leaf records,
+// which traversal reads through the read-only path, are never read through L1 before
+// their scene's fit has finished.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "lbvh.cuh"
+#include "traverse.cuh"
+
+namespace grt {
+
+constexpr uint32_t kBatchPhases = 32;
+constexpr int kBatchRadix = 256;
+constexpr int kBatchSortItems = 8;  // keys per thread in a sort tile
+constexpr int kBatchScanItems = 8;
+constexpr unsigned long long kBatchWaitNs = 2000000000ull;  // 2 s per wait
+constexpr uint32_t kBatchWaitSpins = 1u << 25;                // and at most this many polls
+
+struct BatchSceneDev {
+    PrimSource src;
+    uint32_t n;
+    uint32_t rays;
+    uint32_t bits;        // Morton bits (30 or 63)
+    uint32_t small;       // built by one item
+    uint32_t sortChunks;  // chunk items of a radix pass
+    uint32_t passes;      // radix passes
+    uint32_t tracePhase;
+    uint32_t pad;
+    const float4* rayBuf;
+    uint32_t* hitBuf;
+    float4* nodes;
+    void* leaves;
+    uint32_t* parents;
+    uint32_t* primToLeaf;
+    BvhHeader* header;
+    uint32_t* bounds;  // 6 ordered-int words
+    float4* centroids;
+    void* keys[2];
+    uint32_t* vals[2];
+    uint32_t* counts;  // kBatchRadix x sortChunks
+    uint32_t* flags;   // fit visit counters
+    uint32_t* error;   // the context's device error word
+};
+
+struct BatchItemDev {
+    uint32_t scene;
+    uint32_t phase;
+    uint32_t chunk;
+    uint32_t waitCount;  // items of phase-1 of the scene
+};
+
+struct BatchParams {
+    const BatchSceneDev* scenes;
+    const BatchItemDev* items;
+    uint32_t itemCount;
+    uint32_t sceneCount;
+    uint32_t* done;  // sceneCount x kBatchPhases completion counters
+    unsigned long long* head;
+    unsigned long long* traceCounters;  // per item
+    uint32_t* error;
+    uint32_t* abort;  // set when a wait expired: later items skip their work
+    uint32_t* globalStack;
+    uint32_t globalDepth;
+    uint32_t globalStride;
+    uint32_t sharedDepth;
+    uint32_t refillBelow;
+    uint32_t buildChunk;
+    uint32_t sortChunkKeys;
+    uint32_t traceChunk;
+};
+
+__device__ __forceinline__ unsigned long long globalTimerNs() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Thread 0 only: returns once `need` items of (scene, phase) are done or the launch is
+// aborted. A wait that runs out latches GRT_ERROR_TIMEOUT and aborts the launch.
+__device__ void waitPhase(const BatchParams& B, uint32_t scene, uint32_t phase, uint32_t need) {
+    volatile uint32_t* d = B.done + (size_t)scene * kBatchPhases + phase;
+    volatile uint32_t* abort = B.abort;
+    if (*d < need) {
+        const unsigned long long t0 = globalTimerNs();
+        for (uint32_t k = 0; *d < need; ++k) {
+            if (*abort != 0u) break;
+            if (k >= kBatchWaitSpins || ((k & 63u) == 0u && globalTimerNs() - t0 > kBatchWaitNs)) {
+                latchError(B.error, GRT_ERROR_TIMEOUT);
+                atomicExch(B.abort, 1u);
+                break;
+            }
+            __nanosleep(200);
+        }
+    }
+    __threadfence();
+}
+
+// ------------------------------------------------------------------ build phases
+__device__ __forceinline__ void loadBounds(const BatchSceneDev& S, uint32_t b[6]) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) b[a] = __ldcg(S.bounds + a);
+}
+
+// Centroids of primitives [begin, end), their bounds, and zeroed fit counters.
+__device__ __noinline__ void prepRange(const BatchSceneDev& S, uint32_t begin, uint32_t end) {
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        float3 v[3];
+        const float3 c = boxCentroid(primBox(S.src, i, v));
+        S.centroids[i] = make_float4(c.x, c.y, c.z, 0.f);
+        mn[0] = fminf(mn[0], c.x), mn[1] = fminf(mn[1], c.y), mn[2] = fminf(mn[2], c.z);
+        mx[0] = fmaxf(mx[0], c.x), mx[1] = fmaxf(mx[1], c.y), mx[2] = fmaxf(mx[2], c.z);
+        if (i + 1 < S.n) S.flags[i] = 0u;
+    }
+    reduceBoxBounds(mn, mx, S.bounds);
+}
+
+// Digit histogram of chunk `chunk` of radix pass `pass` into counts[d * chunks + chunk].
+// Pass 0 computes the Morton codes (and identity values) from the centroids first.
+template <typename K, int BITS>
+__device__ __noinline__ void sortUpsweepChunk(const BatchSceneDev& S, uint32_t chunk, uint32_t pass, uint32_t chunkKeys,
+                                 uint32_t* smem) {
+    const uint32_t warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    for (uint32_t d = threadIdx.x; d < warps * kBatchRadix; d += blockDim.x) smem[d] = 0u;
+    __syncthreads();
+    const int shift = 8 * (int)pass;
+    const size_t begin = (size_t)chunk * chunkKeys;
+    const size_t end = min((size_t)S.n, begin + chunkKeys);
+    const K* kin = static_cast<const K*>(S.keys[pass & 1u]);
+    uint32_t b[6];
+    if (pass == 0) loadBounds(S, b);
+    for (size_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        K k;
+        if (pass == 0) {
+            k = mortonCode<K, BITS>(__ldcg(S.centroids + i), b);
+            static_cast<K*>(S.keys[0])[i] = k;
+            S.vals[0][i] = (uint32_t)i;
+        } else {
+            k = __ldcg(kin + i);
+        }
+        atomicAdd(&smem[warp * kBatchRadix + ((uint32_t)(k >> shift) & (kBatchRadix - 1))], 1u);
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < kBatchRadix; d += blockDim.x) {
+        uint32_t sum = 0;
+        for (uint32_t w = 0; w < warps; ++w) sum += smem[w * kBatchRadix + d];
+        S.counts[(size_t)d * S.sortChunks + chunk] = sum;
+    }
+}
+
+// Exclusive prefix sum in place over the scene's kBatchRadix x sortChunks histogram
+// (digit-major, so each (digit, chunk) gets its first output position).
+__device__ __noinline__ void sortScanScene(const BatchSceneDev& S, uint32_t* smem) {
+    uint32_t* warpSums = smem;        // 32
+    uint32_t* carry = smem + 32;      // 1
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    const uint32_t total = kBatchRadix * S.sortChunks;
+    if (threadIdx.x == 0) *carry = 0u;
+    __syncthreads();
+    for (uint32_t base = 0; base < total; base += blockDim.x * kBatchScanItems) {
+        uint32_t v[kBatchScanItems];
+        uint32_t sum = 0;
+        const uint32_t my = base + threadIdx.x * kBatchScanItems;
+#pragma unroll
+        for (int i = 0; i < kBatchScanItems; ++i) {
+            v[i] = (my + i < total) ? __ldcg(S.counts + my + i) : 0u;
+            sum += v[i];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        if (lane == 31u) warpSums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = lane < warps ? warpSums[lane] : 0u;
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= (uint32_t)o) wi += t;
+            }
+            if (lane < warps) warpSums[lane] = wi - w;
+        }
+        __syncthreads();
+        uint32_t run = *carry + warpSums[warp] + (incl - sum);
+#pragma unroll
+        for (int i = 0; i < kBatchScanItems; ++i) {
+            if (my + i < total) S.counts[my + i] = run;
+            run += v[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) *carry = run;
+        __syncthreads();
+    }
+}
+
+// Stable scatter of chunk `chunk` of radix pass `pass`: tiles of blockDim x 16 keys in
+// order; within a tile each warp ranks its 512 keys (match_any per digit) after the
+// warps before it.
+template <typename K>
+__device__ __noinline__ void sortDownsweepChunk(const BatchSceneDev& S, uint32_t chunk, uint32_t pass, uint32_t chunkKeys,
+                                   uint32_t* smem) {
+    const uint32_t warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    uint32_t* warpHist = smem;                        // warps x kBatchRadix
+    uint32_t* digitBase = smem + warps * kBatchRadix;  // kBatchRadix
+    uint32_t* tileTotal = digitBase + kBatchRadix;     // kBatchRadix
+    const uint32_t ltMask = (1u << lane) - 1u;
+    const int shift = 8 * (int)pass;
+    const K* kin = static_cast<const K*>(S.keys[pass & 1u]);
+    const uint32_t* vin = S.vals[pass & 1u];
+    K* kout = static_cast<K*>(S.keys[(pass + 1) & 1u]);
+    uint32_t* vout = S.vals[(pass + 1) & 1u];
+    for (uint32_t d = threadIdx.x; d < kBatchRadix; d += blockDim.x) {
+        digitBase[d] = __ldcg(S.counts + (size_t)d * S.sortChunks + chunk);
+        for (uint32_t w = 0; w < warps; ++w) warpHist[w * kBatchRadix + d] = 0u;
+    }
+    __syncthreads();
+    const size_t begin = (size_t)chunk * chunkKeys;
+    const size_t end = min((size_t)S.n, begin + chunkKeys);
+    const size_t tileKeys = (size_t)blockDim.x * kBatchSortItems;
+    for (size_t tile = begin; tile < end; tile += tileKeys) {
+        const size_t base = tile + (size_t)warp * 32 * kBatchSortItems;
+        K k[kBatchSortItems];
+        uint32_t v[kBatchSortItems], dg[kBatchSortItems], rank[kBatchSortItems];
+#pragma unroll
+        for (int i = 0; i < kBatchSortItems; ++i) {
+            const size_t idx = base + (size_t)i * 32 + lane;
+            const bool ok = idx < end;
+            k[i] = ok ? __ldcg(kin + idx) : (K)0;
+            v[i] = ok ? __ldcg(vin + idx) : 0u;
+            dg[i] = ok ? ((uint32_t)(k[i] >> shift) & (kBatchRadix - 1)) : (uint32_t)kBatchRadix;
+        }
+#pragma unroll
+        for (int i = 0; i < kBatchSortItems; ++i) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg[i]);
+            const int leader = __ffs(peers) - 1;
+            const bool ok = dg[i] < (uint32_t)kBatchRadix;
+            const uint32_t b = ok ? warpHist[warp * kBatchRadix + dg[i]] : 0u;
+            __syncwarp();
+            if (ok && lane == (uint32_t)leader) warpHist[warp * kBatchRadix + dg[i]] = b + __popc(peers);
+            __syncwarp();
+            rank[i] = b + __popc(peers & ltMask);
+        }
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d < kBatchRadix; d += blockDim.x) {
+            uint32_t run = 0;
+            for (uint32_t w = 0; w < warps; ++w) {
+                const uint32_t t = warpHist[w * kBatchRadix + d];
+                warpHist[w * kBatchRadix + d] = run;
+                run += t;
+            }
+            tileTotal[d] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kBatchSortItems; ++i) {
+            if (dg[i] < (uint32_t)kBatchRadix) {
+                const uint32_t pos = digitBase[dg[i]] + warpHist[warp * kBatchRadix + dg[i]] + rank[i];
+                if (pos < S.n) {  // always, given consistent histograms
+                    kout[pos] = k[i];
+                    vout[pos] = v[i];
+                } else {
+                    latchError(S.error, GRT_ERROR_INTERNAL);
+                }
+            }
+        }
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d < kBatchRadix; d += blockDim.x) {
+            digitBase[d] += tileTotal[d];
+            for (uint32_t w = 0; w < warps; ++w) warpHist[w * kBatchRadix + d] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename K>
+__device__ __noinline__ void karrasRange(const BatchSceneDev& S, uint32_t begin, uint32_t end) {
+    const K* keys = static_cast<const K*>(S.keys[S.passes & 1u]);
+    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x)
+        karrasNode<true>(keys, (int)S.n, (int)i, S.nodes, S.parents);
+}
+
+__device__ __noinline__ void fitRange(const BatchSceneDev& S, uint32_t begin, uint32_t end) {
+    FitParams P{};
+    P.src = S.src;
+    P.n = S.n;
+    P.sortedPrims = S.vals[S.passes & 1u];
+    P.nodes = S.nodes;
+    P.leaves = S.leaves;
+    P.primToLeaf = S.primToLeaf;
+    P.parents = S.parents;
+    P.flags = S.flags;
+    P.header = S.header;
+    for (uint32_t k = begin + threadIdx.x; k < end; k += blockDim.x) fitLeaf<0>(P, k);
+}
+
+// The whole build of a small scene by one block, phase after phase.
+template <typename K, int BITS>
+__device__ __noinline__ void buildWhole(const BatchSceneDev& S, uint32_t chunkKeys, uint32_t* smem) {
+    if (S.n == 0) return;
+    prepRange(S, 0, S.n);
+    __threadfence();
+    __syncthreads();
+    for (uint32_t p = 0; p < S.passes; ++p) {
+        for (uint32_t c = 0; c < S.sortChunks; ++c) {
+            sortUpsweepChunk<K, BITS>(S, c, p, chunkKeys, smem);
+            __syncthreads();
+        }
+        __threadfence();
+        __syncthreads();
+        sortScanScene(S, smem);
+        __threadfence();
+        __syncthreads();
+        for (uint32_t c = 0; c < S.sortChunks; ++c) {
+            sortDownsweepChunk<K>(S, c, p, chunkKeys, smem);
+            __syncthreads();
+        }
+        __threadfence();
+        __syncthreads();
+    }
+    if (S.n >= 2) karrasRange<K>(S, 0, S.n - 1);
+    __threadfence();
+    __syncthreads();
+    fitRange(S, 0, S.n);
+}
+
+// ------------------------------------------------------------------ trace phase
+// Items = the rays of one chunk of a scene's ray batch.
+struct ChunkRaySource {
+    const TraceParams* P;
+    uint32_t base, n;
+    __device__ unsigned long long count() const { return n; }
+    __device__ bool begin(uint32_t i, const TraceParams& Q, Stack& st, RayState& s) const {
+        const size_t r = (size_t)base + i;
+        const float4 a = Q.rays[2 * r], b = Q.rays[2 * r + 1];
+        beginRay<false>(Q, st, s, f3(a), f3(b), a.w, b.w);
+        return true;
+    }
+    __device__ void finish(uint32_t i, const RayState& s) const { storeHit(P->hits, base + i, s.best); }
+};
+
+__device__ __noinline__ void traceChunk(const BatchParams& B, const BatchSceneDev& S, uint32_t chunk, unsigned long long item,
+                           uint32_t* smem) {
+    TraceParams P{};
+    P.target.nodes = S.nodes;
+    P.target.leaves = S.leaves;
+    P.target.primType = GRT_PRIMITIVE_TRIANGLE_MESH;
+    P.target.geomType = 0;
+    P.target.empty = S.n == 0;
+    P.rays = S.rayBuf;
+    P.hits = S.hitBuf;
+    P.count = S.rays;
+    P.sharedDepth = B.sharedDepth;
+    P.globalDepth = B.globalDepth;
+    P.globalStack = B.globalStack;
+    P.globalStride = B.globalStride;
+    P.counter = B.traceCounters + item;
+    P.error = B.error;
+    P.maxSteps = 1u << 26;
+    P.refillBelow = B.refillBelow;
+    P.targetPrimToLeaf = S.primToLeaf;
+    const uint32_t base = chunk * B.traceChunk;
+    const uint32_t n = min(B.traceChunk, S.rays - base);
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    Stack st{smem + threadIdx.x, B.globalStack + gtid, B.sharedDepth, B.globalDepth, B.globalStride, 0};
+    ChunkRaySource src{&P, base, n};
+    refillLoop<false, false, false>(P, st, src);
+    __syncthreads();  // hit records of the chunk complete
+    for (uint32_t r = base + threadIdx.x; r < base + n; r += blockDim.x) refineHit(P, r);
+}
+
+// ------------------------------------------------------------------ the persistent kernel
+__global__ void batchInitKernel(BatchParams B) {
+    const size_t doneWords = (size_t)B.sceneCount * kBatchPhases;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < max(doneWords, (size_t)B.itemCount);
+         i += (size_t)gridDim.x * blockDim.x) {
+        if (i < doneWords) B.done[i] = 0u;
+        if (i < B.itemCount) B.traceCounters[i] = 0ull;
+        if (i < B.sceneCount) {
+            uint32_t* b = B.scenes[i].bounds;
+            b[0] = b[1] = b[2] = 0xFFFFFFFFu;  // running minima start at the top
+            b[3] = b[4] = b[5] = 0u;           // running maxima at the bottom
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *B.head = 0ull, *B.abort = 0u;
+}
+
+__global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
+    extern __shared__ uint32_t smem[];
+    __shared__ unsigned long long itemS;
+    __shared__ uint32_t skipS;
+    for (;;) {
+        if (threadIdx.x == 0) itemS = atomicAdd(B.head, 1ull);
+        __syncthreads();
+        const unsigned long long item = itemS;
+        if (item >= B.itemCount) break;
+        const BatchItemDev it = B.items[item];
+        const BatchSceneDev& S = B.scenes[it.scene];
+        if (threadIdx.x == 0) {
+            if (it.phase > 0) waitPhase(B, it.scene, it.phase - 1, it.waitCount);
+            skipS = *(volatile uint32_t*)B.abort;
+        }
+        __syncthreads();
+        const bool wide = S.bits != 30;
+        if (skipS) {
+            // aborted launch: the item only counts as done
+        } else if (S.small) {
+            if (it.phase == 0) {
+                if (wide)
+                    buildWhole<unsigned long long, 21>(S, B.sortChunkKeys, smem);
+                else
+                    buildWhole<uint32_t, 10>(S, B.sortChunkKeys, smem);
+            } else {
+                traceChunk(B, S, it.chunk, item, smem);
+            }
+        } else if (it.phase == 0) {
+            const uint32_t b0 = it.chunk * B.buildChunk;
+            prepRange(S, b0, min(S.n, b0 + B.buildChunk));
+        } else if (it.phase <= 3 * S.passes) {
+            const uint32_t p = (it.phase - 1) / 3, step = (it.phase - 1) % 3;
+            if (step == 0) {
+                if (wide)
+                    sortUpsweepChunk<unsigned long long, 21>(S, it.chunk, p, B.sortChunkKeys, smem);
+                else
+                    sortUpsweepChunk<uint32_t, 10>(S, it.chunk, p, B.sortChunkKeys, smem);
+            } else if (step == 1) {
+                sortScanScene(S, smem);
+            } else if (wide) {
+                sortDownsweepChunk<unsigned long long>(S, it.chunk, p, B.sortChunkKeys, smem);
+            } else {
+                sortDownsweepChunk<uint32_t>(S, it.chunk, p, B.sortChunkKeys, smem);
+            }
+        } else if (it.phase == 3 * S.passes + 1) {
+            const uint32_t b0 = it.chunk * B.buildChunk;
+            if (wide)
+                karrasRange<unsigned long long>(S, b0, min(S.n - 1, b0 + B.buildChunk));
+            else
+                karrasRange<uint32_t>(S, b0, min(S.n - 1, b0 + B.buildChunk));
+        } else if (it.phase == 3 * S.passes + 2) {
+            const uint32_t b0 = it.chunk * B.buildChunk;
+            fitRange(S, b0, min(S.n, b0 + B.buildChunk));
+        } else {
+            traceChunk(B, S, it.chunk, item, smem);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(B.done + (size_t)it.scene * kBatchPhases + it.phase, 1u);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+struct BatchObject {
+    int device = 0;
+    uint32_t sceneCount = 0, itemCount = 0;
+    uint32_t blockSize = 128, blocks = 0;
+    size_t smem = 0;
+    std::vector<grtGeometry> geometries;
+    std::vector<uint32_t> vertexCounts;
+    void* deviceMem = nullptr;  // descriptors, items, counters, scratch, global stack
+    size_t deviceBytes = 0;
+    BatchParams params{};
+    grtBatchInfo info{};
+    bool useGraph = false;
+    cudaGraphExec_t graph = nullptr;
+};
+
+static std::mutex g_batchMutex;
+static std::vector<BatchObject*> g_batches;
+
+static BatchObject* findBatch(grtBatch b) {
+    std::lock_guard<std::mutex> g(g_batchMutex);
+    for (BatchObject* o : g_batches)
+        if (reinterpret_cast<grtBatch>(o) == b) return o;
+    return nullptr;
+}
+
+static grtError resolveBatchOptions(const grtBatchOptions* o, grtBatchOptions* r) {
+    grtBatchOptions d{};
+    if (o) d = *o;
+    if (!d.blockSize) d.blockSize = 128;
+    if (!d.sharedStackDepth) d.sharedStackDepth = 16;
+    if (!d.globalStackDepth) d.globalStackDepth = 64;
+    if (!(d.compactThreshold > 0.f)) d.compactThreshold = 0.5f;
+    if (!d.smallScenePrims) d.smallScenePrims = 8192;
+    if (!d.sortChunkTiles) d.sortChunkTiles = 8;
+    if (!d.buildChunk) d.buildChunk = 16384;
+    if (!d.traceChunk) d.traceChunk = 16384;
+    if (d.blockSize != 64 && d.blockSize != 128 && d.blockSize != 256) return GRT_ERROR_INVALID_PARAMETER;
+    if (d.sharedStackDepth > 32 || d.globalStackDepth > 4096) return GRT_ERROR_INVALID_PARAMETER;
+    if (d.compactThreshold > 1.f || d.sortChunkTiles > 4096) return GRT_ERROR_INVALID_PARAMETER;
+    if (d.buildChunk > (1u << 24) || d.traceChunk > (1u << 24)) return GRT_ERROR_INVALID_PARAMETER;
+    if (d.flags & ~(uint32_t)GRT_BATCH_FLAG_GRAPH) return GRT_ERROR_INVALID_PARAMETER;
+    *r = d;
+    return GRT_SUCCESS;
+}
+
+static void destroyBatchObject(BatchObject* o) {
+    if (o->graph) cudaGraphExecDestroy(o->graph);
+    if (o->deviceMem) cudaFree(o->deviceMem);
+    delete o;
+}
+
+}  // namespace grt
+
+using namespace grt;
+
+extern "C" {
+
+grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sceneCount,
+                        const grtBatchOptions* options, grtBatch* out) {
+    if (!ctx || !out || (sceneCount && !scenes)) return GRT_ERROR_INVALID_PARAMETER;
+    grtBatchOptions opt;
+    grtError e = resolveBatchOptions(options, &opt);
+    if (e != GRT_SUCCESS) return e;
+    Context* c = asContext(ctx);
+    const uint32_t bs = opt.blockSize;
+    const uint32_t warps = bs / 32;
+    const uint32_t chunkKeys = opt.sortChunkTiles * bs * kBatchSortItems;
+
+    // scene descriptors (pointers into the scratch region are filled in below)
+    std::vector<BatchSceneDev> S(sceneCount);
+    std::vector<size_t> scratchOff(sceneCount);
+    size_t scratch = 0;
+    for (uint32_t i = 0; i < sceneCount; ++i) {
+        const grtBatchScene& in = scenes[i];
+        uint32_t n = 0;
+        e = validateGeometryInput(&in.input, &n);
+        if (e != GRT_SUCCESS) return e;
+        BvhObject* o = findBvh(in.geometry);
+        if (!o || o->primType != GRT_PRIMITIVE_TRIANGLE_MESH || in.input.type != GRT_PRIMITIVE_TRIANGLE_MESH ||
+            o->primCount != n)
+            return GRT_ERROR_INVALID_PARAMETER;
+        if (in.rayCount && (!in.rays || !in.hits || ((uintptr_t)in.rays & 15) || ((uintptr_t)in.hits & 3)))
+            return GRT_ERROR_INVALID_PARAMETER;
+        BatchSceneDev& d = S[i];
+        d.src = primSource(&in.input, n);
+        d.n = n;
+        d.rays = in.rayCount;
+        d.bits = o->mortonBits;
+        d.small = n <= opt.smallScenePrims;
+        d.sortChunks = std::max(1u, ceilDiv(n, chunkKeys));
+        d.passes = (d.bits + 7) / 8;
+        d.tracePhase = d.small ? 1u : 3u * d.passes + 3u;
+        d.rayBuf = (const float4*)in.rays;
+        d.hitBuf = (uint32_t*)in.hits;
+        d.nodes = (float4*)o->nodes;
+        d.leaves = o->leaves;
+        d.parents = (uint32_t*)o->parents;
+        d.primToLeaf = o->primToLeaf;
+        d.header = o->dHeader;
+        d.error = &workspace(c)->error;
+        const size_t kb = d.bits == 30 ? 4 : 8, nn = std::max(n, 1u);
+        scratchOff[i] = scratch;
+        scratch += 256 + alignUp(16 * nn, 256) + 2 * alignUp(kb * nn, 256) + 2 * alignUp(4 * nn, 256) +
+                   alignUp(4 * (size_t)kBatchRadix * d.sortChunks, 256) + alignUp(4 * nn, 256);
+    }
+
+    // work items: rounds of phases, the larger scenes first within a round; trace
+    // items last, the scenes whose builds end soonest first
+    std::vector<BatchItemDev> items;
+    std::vector<uint32_t> order(sceneCount);
+    for (uint32_t i = 0; i < sceneCount; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return S[a].n > S[b].n; });
+    auto phaseItems = [&](const BatchSceneDev& d, uint32_t ph) -> uint32_t {
+        if (ph == d.tracePhase) return ceilDiv(d.rays, opt.traceChunk);
+        if (d.small) return ph == 0 ? 1u : 0u;
+        if (ph == 0) return ceilDiv(d.n, opt.buildChunk);
+        if (ph <= 3 * d.passes) return (ph - 1) % 3 == 1 ? 1u : d.sortChunks;
+        if (ph == 3 * d.passes + 1) return ceilDiv(d.n - 1, opt.buildChunk);
+        if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);
+        return 0u;
+    };
+    for (uint32_t r = 0; r < kBatchPhases; ++r)
+        for (uint32_t i : order) {
+            const BatchSceneDev& d = S[i];
+            if (r >= d.tracePhase) continue;
+            const uint32_t cnt = phaseItems(d, r), wait = r ? phaseItems(d, r - 1) : 0u;
+            for (uint32_t k = 0; k < cnt; ++k) items.push_back(BatchItemDev{i, r, k, wait});
+        }
+    std::vector<uint32_t> traceOrder(order.rbegin(), order.rend());
+    std::stable_sort(traceOrder.begin(), traceOrder.end(),
+                     [&](uint32_t a, uint32_t b) { return S[a].tracePhase < S[b].tracePhase; });
+    for (uint32_t i : traceOrder) {
+        const BatchSceneDev& d = S[i];
+        const uint32_t cnt = phaseItems(d, d.tracePhase), wait = phaseItems(d, d.tracePhase - 1);
+        for (uint32_t k = 0; k < cnt; ++k) items.push_back(BatchItemDev{i, d.tracePhase, k, wait});
+    }
+    // the queue takes a phase's items only after every item of the phase before it
+    // (waits point backwards), which the round order guarantees; the trace items come
+    // after every build item
+
+    // launch shape and the device allocation
+    BatchObject* b = new BatchObject();
+    b->device = deviceOf(c);
+    b->sceneCount = sceneCount;
+    b->itemCount = (uint32_t)items.size();
+    b->blockSize = bs;
+    const size_t stackSmem = (size_t)bs * opt.sharedStackDepth * 4;
+    const size_t sortSmem = ((size_t)warps * kBatchRadix + 2 * kBatchRadix) * 4;
+    b->smem = std::max<size_t>(std::max(stackSmem, sortSmem), 33 * 4);
+    int perSm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSm, batchKernel, (int)bs, b->smem) != cudaSuccess ||
+        perSm < 1)
+        perSm = 1;
+    b->blocks = (uint32_t)perSm * (uint32_t)smCount(c);
+    const size_t threads = (size_t)b->blocks * bs;
+    const size_t offScenes = 0;
+    const size_t offItems = alignUp(sizeof(BatchSceneDev) * std::max(sceneCount, 1u), 256);
+    const size_t offDone = offItems + alignUp(sizeof(BatchItemDev) * std::max<size_t>(items.size(), 1), 256);
+    const size_t offHead = offDone + alignUp(4 * (size_t)std::max(sceneCount, 1u) * kBatchPhases, 256);
+    const size_t offTrace = offHead + 256;  // head (8 bytes) and abort flag (4 bytes at +64)
+    const size_t offStack = offTrace + alignUp(8 * std::max<size_t>(items.size(), 1), 256);
+    const size_t offScratch = offStack + alignUp(threads * opt.globalStackDepth * 4, 256);
+    b->deviceBytes = offScratch + scratch;
+    if (cudaMalloc(&b->deviceMem, b->deviceBytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return GRT_ERROR_OUT_OF_MEMORY;
+    }
+    char* base = static_cast<char*>(b->deviceMem);
+    for (uint32_t i = 0; i < sceneCount; ++i) {
+        BatchSceneDev& d = S[i];
+        const size_t kb = d.bits == 30 ? 4 : 8, nn = std::max(d.n, 1u);
+        char* p = base + offScratch + scratchOff[i];
+        d.bounds = (uint32_t*)p, p += 256;
+        d.centroids = (float4*)p, p += alignUp(16 * nn, 256);
+        d.keys[0] = p, p += alignUp(kb * nn, 256);
+        d.keys[1] = p, p += alignUp(kb * nn, 256);
+        d.vals[0] = (uint32_t*)p, p += alignUp(4 * nn, 256);
+        d.vals[1] = (uint32_t*)p, p += alignUp(4 * nn, 256);
+        d.counts = (uint32_t*)p, p += alignUp(4 * (size_t)kBatchRadix * d.sortChunks, 256);
+        d.flags = (uint32_t*)p;
+    }
+    cudaError_t ce = cudaSuccess;
+    if (sceneCount)
+        ce = cudaMemcpy(base + offScenes, S.data(), sizeof(BatchSceneDev) * sceneCount, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && !items.empty())
+        ce = cudaMemcpy(base + offItems, items.data(), sizeof(BatchItemDev) * items.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        destroyBatchObject(b);
+        return GRT_ERROR_CUDA;
+    }
+    BatchParams& P = b->params;
+    P.scenes = (const BatchSceneDev*)(base + offScenes);
+    P.items = (const BatchItemDev*)(base + offItems);
+    P.itemCount = (uint32_t)items.size();
+    P.sceneCount = sceneCount;
+    P.done = (uint32_t*)(base + offDone);
+    P.head = (unsigned long long*)(base + offHead);
+    P.abort = (uint32_t*)(base + offHead + 64);
+    P.traceCounters = (unsigned long long*)(base + offTrace);
+    P.error = &workspace(c)->error;
+    P.globalStack = (uint32_t*)(base + offStack);
+    P.globalDepth = opt.globalStackDepth;
+    P.globalStride = (uint32_t)threads;
+    P.sharedDepth = opt.sharedStackDepth;
+    P.refillBelow = (uint32_t)(opt.compactThreshold * 32.f);
+    P.buildChunk = opt.buildChunk;
+    P.sortChunkKeys = chunkKeys;
+    P.traceChunk = opt.traceChunk;
+    b->useGraph = (opt.flags & GRT_BATCH_FLAG_GRAPH) != 0;
+    for (uint32_t i = 0; i < sceneCount; ++i) {
+        b->geometries.push_back(scenes[i].geometry);
+        b->vertexCounts.push_back(scenes[i].input.triangleMesh.vertexCount);
+    }
+    grtBatchInfo& I = b->info;
+    I.sceneCount = sceneCount;
+    I.itemCount = (uint32_t)items.size();
+    I.blocks = b->blocks;
+    I.blockSize = bs;
+    I.deviceBytes = b->deviceBytes;
+    I.smallScenes = 0;
+    for (const BatchSceneDev& d : S) I.smallScenes += d.small;
+    {
+        std::lock_guard<std::mutex> g(g_batchMutex);
+        g_batches.push_back(b);
+    }
+    *out = reinterpret_cast<grtBatch>(b);
+    return GRT_SUCCESS;
+}
+
+static grtError enqueueBatch(BatchObject* b, cudaStream_t s) {
+    batchInitKernel<<<64, 256, 0, s>>>(b->params);
+    if (b->params.itemCount) batchKernel<<<b->blocks, b->blockSize, b->smem, s>>>(b->params);
+    GRT_LAUNCH_CHECK();
+    return GRT_SUCCESS;
+}
+
+grtError grtBatchBuildTrace(grtContext ctx, grtBatch batch, void* stream) {
+    BatchObject* b = findBatch(batch);
+    if (!ctx || !b) return GRT_ERROR_INVALID_PARAMETER;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->useGraph) {
+        if (!b->graph) {
+            // capture once on a private stream, then replay on the caller's
+            cudaStream_t cap;
+            GRT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            grtError e = GRT_SUCCESS;
+            if (ce == cudaSuccess) {
+                e = enqueueBatch(b, cap);
+                ce = cudaStreamEndCapture(cap, &g);
+            }
+            if (ce == cudaSuccess && e == GRT_SUCCESS) ce = cudaGraphInstantiate(&b->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cap);
+            if (e != GRT_SUCCESS) return e;
+            GRT_CUDA(ce);
+        }
+        GRT_CUDA(cudaGraphLaunch(b->graph, s));
+    } else {
+        grtError e = enqueueBatch(b, s);
+        if (e != GRT_SUCCESS) return e;
+    }
+    noteLaunches(b->params.itemCount ? 2 : 1);
+    for (size_t i = 0; i < b->geometries.size(); ++i) {
+        BvhObject* o = findBvh(b->geometries[i]);
+        if (o) {
+            o->built = true;
+            o->vertexCount = b->vertexCounts[i];
+        }
+    }
+    return GRT_SUCCESS;
+}
+
+grtError grtGetBatchInfo(grtContext ctx, grtBatch batch, grtBatchInfo* info) {
+    BatchObject* b = findBatch(batch);
+    if (!ctx || !b || !info) return GRT_ERROR_INVALID_PARAMETER;
+    *info = b->info;
+    return GRT_SUCCESS;
+}
+
+grtError grtDestroyBatch(grtContext ctx, grtBatch batch) {
+    BatchObject* b = findBatch(batch);
+    if (!ctx || !b) return GRT_ERROR_INVALID_PARAMETER;
+    {
+        std::lock_guard<std::mutex> g(g_batchMutex);
+        g_batches.erase(std::find(g_batches.begin(), g_batches.end(), b));
+    }
+    destroyBatchObject(b);
+    return GRT_SUCCESS;
+}
+
+}  // extern "C"

@@ -10,7 +10,7 @@
 // the second child to arrive at a node computing its box.
 #include <algorithm>
 
-#include "grt_internal.cuh"
+#include "lbvh.cuh"
 
 namespace grt {
 
@@ -219,90 +219,7 @@ grtError radixSort(Context* ctx, void* keys0, void* keys1, uint32_t* vals0, uint
                                           significantBits, hist, s, finalBuf);
 }
 
-// ======================================================================= primitive boxes (A1) and bounds (A2)
-struct Box3 {
-    float3 lo, hi;
-};
-
-__device__ __forceinline__ float3 load3(const char* base, size_t byteOffset) {
-    const float* p = reinterpret_cast<const float*>(base + byteOffset);
-    return make_float3(p[0], p[1], p[2]);
-}
-
-__device__ __forceinline__ Box3 triangleBox(float3 a, float3 b, float3 c) {
-    Box3 r;
-    r.lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y), fminf(fminf(a.z, b.z), c.z));
-    r.hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y), fmaxf(fmaxf(a.z, b.z), c.z));
-    return r;
-}
-
-__device__ __forceinline__ float3 boxCentroid(const Box3& b) {
-    return make_float3(__fmul_rn(0.5f, __fadd_rn(b.lo.x, b.hi.x)), __fmul_rn(0.5f, __fadd_rn(b.lo.y, b.hi.y)),
-                       __fmul_rn(0.5f, __fadd_rn(b.lo.z, b.hi.z)));
-}
-
-struct PrimSource {
-    uint32_t kind;  // 0 triangles, 1 boxes at stride
-    uint32_t count;
-    const char* idx;
-    uint32_t idxStride;
-    const char* verts;
-    uint32_t vertStride;
-    const char* boxes;
-    uint32_t boxStride;
-};
-
-__device__ __forceinline__ Box3 primBox(const PrimSource& S, uint32_t i, float3* v) {
-    if (S.kind == 0) {
-        const uint32_t* t = reinterpret_cast<const uint32_t*>(S.idx + (size_t)i * S.idxStride);
-        v[0] = load3(S.verts, (size_t)t[0] * S.vertStride);
-        v[1] = load3(S.verts, (size_t)t[1] * S.vertStride);
-        v[2] = load3(S.verts, (size_t)t[2] * S.vertStride);
-        return triangleBox(v[0], v[1], v[2]);
-    }
-    const float* b = reinterpret_cast<const float*>(S.boxes + (size_t)i * S.boxStride);
-    Box3 r;
-    r.lo = make_float3(b[0], b[1], b[2]);
-    r.hi = make_float3(b[3], b[4], b[5]);
-    return r;
-}
-
-// Block-wide min/max reduction of centroids folded into 6 ordered-int atomics.
-__device__ __forceinline__ void reduceBounds(float3 c, bool valid, uint32_t* bounds) {
-    float mn[3] = {valid ? c.x : INFINITY, valid ? c.y : INFINITY, valid ? c.z : INFINITY};
-    float mx[3] = {valid ? c.x : -INFINITY, valid ? c.y : -INFINITY, valid ? c.z : -INFINITY};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
-        }
-    __shared__ float sm[32][6];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0)
-        for (int a = 0; a < 3; ++a) sm[warp][a] = mn[a], sm[warp][3 + a] = mx[a];
-    __syncthreads();
-    if (warp == 0) {
-        for (int a = 0; a < 3; ++a) {
-            mn[a] = lane < nw ? sm[lane][a] : INFINITY;
-            mx[a] = lane < nw ? sm[lane][3 + a] : -INFINITY;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-                mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
-            }
-        if (lane == 0)
-            for (int a = 0; a < 3; ++a) {
-                atomicMin(&bounds[a], floatToOrdered(mn[a]));
-                atomicMax(&bounds[3 + a], floatToOrdered(mx[a]));
-            }
-    }
-}
-
+// ======================================================================= element kernels (A1-A7)
 __global__ void __launch_bounds__(256) primCentroidKernel(PrimSource S, float4* __restrict__ centroids,
                                                           uint32_t* __restrict__ bounds) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -316,187 +233,28 @@ __global__ void __launch_bounds__(256) primCentroidKernel(PrimSource S, float4* 
     reduceBounds(c, valid, bounds);
 }
 
-// ======================================================================= Morton codes (A3)
-__device__ __forceinline__ uint32_t expand10(uint32_t x) {
-    x &= 0x3FFu;
-    x = (x | (x << 16)) & 0x030000FFu;
-    x = (x | (x << 8)) & 0x0300F00Fu;
-    x = (x | (x << 4)) & 0x030C30C3u;
-    x = (x | (x << 2)) & 0x09249249u;
-    return x;
-}
-
-__device__ __forceinline__ unsigned long long expand21(uint32_t v) {
-    unsigned long long x = v & 0x1FFFFFull;
-    x = (x | (x << 32)) & 0x001F00000000FFFFull;
-    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
-    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
-    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
-    return x;
-}
-
-// q = clamp(floor(((c - lo) / (hi - lo)) * 2^bits), 0, 2^bits - 1), each step rounded
-// to nearest in float32; a zero extent gives 0.
-template <int BITS>
-__device__ __forceinline__ uint32_t quantise(float c, float lo, float hi) {
-    const float ext = __fsub_rn(hi, lo);
-    const float x = (ext == 0.0f) ? 0.0f : __fdiv_rn(__fsub_rn(c, lo), ext);
-    const float s = __fmul_rn(x, (float)(1u << BITS));
-    const float f = floorf(s);
-    const float top = (float)((1u << BITS) - 1u);
-    if (!(f >= 0.0f)) return 0u;
-    return (uint32_t)(f > top ? top : f);
-}
-
 template <typename K, int BITS>
 __global__ void __launch_bounds__(256) mortonKernel(const float4* __restrict__ centroids, uint32_t n,
                                                     const uint32_t* __restrict__ bounds, K* __restrict__ keys,
                                                     uint32_t* __restrict__ vals) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float4 c = centroids[i];
-    const float lx = orderedToFloat(bounds[0]), ly = orderedToFloat(bounds[1]), lz = orderedToFloat(bounds[2]);
-    const float hx = orderedToFloat(bounds[3]), hy = orderedToFloat(bounds[4]), hz = orderedToFloat(bounds[5]);
-    const uint32_t qx = quantise<BITS>(c.x, lx, hx), qy = quantise<BITS>(c.y, ly, hy), qz = quantise<BITS>(c.z, lz, hz);
-    K code;
-    if constexpr (BITS == 10)
-        code = (K)((expand10(qx) << 2) | (expand10(qy) << 1) | expand10(qz));
-    else
-        code = (K)((expand21(qx) << 2) | (expand21(qy) << 1) | expand21(qz));
-    keys[i] = code;
+    keys[i] = mortonCode<K, BITS>(centroids[i], bounds);
     vals[i] = i;
 }
 
-// ======================================================================= Karras emission (A5)
-template <typename K>
-__device__ __forceinline__ int commonPrefix(const K* __restrict__ keys, int n, int i, int j) {
-    if (j < 0 || j >= n) return -1;
-    const K a = keys[i], b = keys[j];
-    constexpr int KB = (int)sizeof(K) * 8;
-    if (a != b) {
-        if (sizeof(K) == 4) return __clz((uint32_t)(a ^ b));
-        return __clzll((long long)(a ^ b));
-    }
-    return KB + __clz((uint32_t)i ^ (uint32_t)j);
-}
-
-// One thread per internal node i in [0, n-2]: direction, range end, split; writes
-// the node's child indices (word 3 of the node) and each child's parent entry
-// (parent << 1 | side).
+// One thread per internal node i in [0, n-2].
 template <typename K>
 __global__ void __launch_bounds__(256) karrasKernel(const K* __restrict__ keys, int n, float4* __restrict__ nodes,
                                                     uint32_t* __restrict__ parents) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    const int d = (commonPrefix(keys, n, i, i + 1) - commonPrefix(keys, n, i, i - 1)) >= 0 ? 1 : -1;
-    const int dmin = commonPrefix(keys, n, i, i - d);
-    int lmax = 2;
-    while (commonPrefix(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
-    int l = 0;
-    for (int t = lmax >> 1; t >= 1; t >>= 1)
-        if (commonPrefix(keys, n, i, i + (l + t) * d) > dmin) l += t;
-    const int j = i + l * d;
-    const int dnode = commonPrefix(keys, n, i, j);
-    int s = 0;
-    int t = l;
-    do {
-        t = (t + 1) >> 1;
-        if (commonPrefix(keys, n, i, i + (s + t) * d) > dnode) s += t;
-    } while (t > 1);
-    const int gamma = i + s * d + min(d, 0);
-    const int lo = min(i, j), hi = max(i, j);
-    const uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
-    const uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
-    nodes[4 * (size_t)i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.f, 0.f);
-    const uint32_t leafBase = (uint32_t)n - 1u;
-    parents[(left & kLeafBit) ? leafBase + (left & ~kLeafBit) : left] = ((uint32_t)i << 1) | 0u;
-    parents[(right & kLeafBit) ? leafBase + (right & ~kLeafBit) : right] = ((uint32_t)i << 1) | 1u;
-    if (i == 0) parents[0] = kInvalid;
-}
-
-// ======================================================================= bottom-up fit (A6) + leaf layout (A7)
-struct FitParams {
-    PrimSource src;
-    uint32_t n;
-    const uint32_t* sortedPrims;  // nullptr for a refit (IDs read back from the leaves)
-    float4* nodes;
-    void* leaves;
-    uint32_t* primToLeaf;
-    const uint32_t* parents;
-    uint32_t* flags;
-    BvhHeader* header;
-    const float4* instBoxes;              // scene: world boxes (2 float4 per instance)
-    const InstanceRecord* instRecords;    // scene: unsorted records
-};
-
-__device__ __forceinline__ void writeChildBox(float4* nodes, uint32_t p, uint32_t side, const Box3& b) {
-    float2* n2 = reinterpret_cast<float2*>(nodes + 4 * (size_t)p);
-    n2[0 * 2 + side] = make_float2(b.lo.x, b.hi.x);
-    n2[1 * 2 + side] = make_float2(b.lo.y, b.hi.y);
-    n2[2 * 2 + side] = make_float2(b.lo.z, b.hi.z);
+    if (i < n - 1) karrasNode<false>(keys, n, i, nodes, parents);
 }
 
 template <int KIND>  // 0 triangles, 1 AABB list, 2 instances
 __global__ void __launch_bounds__(256) fitKernel(FitParams P) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.n) return;
-    Box3 b;
-    if (KIND == 0) {
-        float4* rec = reinterpret_cast<float4*>(P.leaves) + 3 * (size_t)k;
-        const uint32_t prim = P.sortedPrims ? P.sortedPrims[k] : __float_as_uint(rec[0].w);
-        float3 v[3];
-        b = primBox(P.src, prim, v);
-        rec[0] = make_float4(v[0].x, v[0].y, v[0].z, __uint_as_float(prim));
-        // w slots: L1 norms of the edges v1-v0 and v2-v0 (scale of the traversal's error bounds)
-        const float e1 = fabsf(v[1].x - v[0].x) + fabsf(v[1].y - v[0].y) + fabsf(v[1].z - v[0].z);
-        const float e2 = fabsf(v[2].x - v[0].x) + fabsf(v[2].y - v[0].y) + fabsf(v[2].z - v[0].z);
-        rec[1] = make_float4(v[1].x, v[1].y, v[1].z, e1);
-        rec[2] = make_float4(v[2].x, v[2].y, v[2].z, e2);
-        P.primToLeaf[prim] = k;
-    } else if (KIND == 1) {
-        uint32_t* ids = reinterpret_cast<uint32_t*>(P.leaves);
-        const uint32_t prim = P.sortedPrims ? P.sortedPrims[k] : ids[k];
-        float3 v[3];
-        b = primBox(P.src, prim, v);
-        ids[k] = prim;
-    } else {
-        const uint32_t prim = P.sortedPrims[k];
-        const float4 lo = P.instBoxes[2 * (size_t)prim], hi = P.instBoxes[2 * (size_t)prim + 1];
-        b.lo = make_float3(lo.x, lo.y, lo.z);
-        b.hi = make_float3(hi.x, hi.y, hi.z);
-        reinterpret_cast<InstanceRecord*>(P.leaves)[k] = P.instRecords[prim];
-        P.primToLeaf[prim] = k;
-    }
-    if (P.n == 1) {
-        // a single primitive: node 0 holds it as both children
-        writeChildBox(P.nodes, 0, 0, b);
-        writeChildBox(P.nodes, 0, 1, b);
-        P.nodes[3] = make_float4(__uint_as_float(kLeafBit), __uint_as_float(kLeafBit), 0.f, 0.f);
-        P.header->rootLo[0] = b.lo.x, P.header->rootLo[1] = b.lo.y, P.header->rootLo[2] = b.lo.z;
-        P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
-        return;
-    }
-    uint32_t pe = P.parents[P.n - 1 + k];
-    for (;;) {
-        const uint32_t p = pe >> 1, side = pe & 1u;
-        writeChildBox(P.nodes, p, side, b);
-        __threadfence();
-        const uint32_t prev = atomicAdd(&P.flags[p], 1u);
-        if (prev == 0) return;  // the sibling is still on its way up
-        __threadfence();
-        const float4 x = __ldcg(&P.nodes[4 * (size_t)p + 0]);
-        const float4 y = __ldcg(&P.nodes[4 * (size_t)p + 1]);
-        const float4 z = __ldcg(&P.nodes[4 * (size_t)p + 2]);
-        b.lo = make_float3(fminf(x.x, x.z), fminf(y.x, y.z), fminf(z.x, z.z));
-        b.hi = make_float3(fmaxf(x.y, x.w), fmaxf(y.y, y.w), fmaxf(z.y, z.w));
-        if (p == 0) {
-            P.header->rootLo[0] = b.lo.x, P.header->rootLo[1] = b.lo.y, P.header->rootLo[2] = b.lo.z;
-            P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
-            return;
-        }
-        pe = __ldcg(&P.parents[p]);
-    }
+    if (k < P.n) fitLeaf<KIND>(P, k);
 }
 
 // ======================================================================= instances (A8)
@@ -588,7 +346,7 @@ __global__ void __launch_bounds__(128) instanceSetupKernel(InstanceInput I) {
 }
 
 // ======================================================================= host drivers
-static grtError validateGeometryInput(const grtGeometryBuildInput* in, uint32_t* count) {
+grtError validateGeometryInput(const grtGeometryBuildInput* in, uint32_t* count) {
     if (!in) return GRT_ERROR_INVALID_PARAMETER;
     if (in->type == GRT_PRIMITIVE_TRIANGLE_MESH) {
         const grtTriangleMeshPrimitive& m = in->triangleMesh;
@@ -609,7 +367,7 @@ static grtError validateGeometryInput(const grtGeometryBuildInput* in, uint32_t*
     return GRT_ERROR_INVALID_PARAMETER;
 }
 
-static PrimSource primSource(const grtGeometryBuildInput* in, uint32_t count) {
+PrimSource primSource(const grtGeometryBuildInput* in, uint32_t count) {
     PrimSource S{};
     S.count = count;
     if (in->type == GRT_PRIMITIVE_TRIANGLE_MESH) {

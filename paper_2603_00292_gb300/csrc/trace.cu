@@ -9,63 +9,6 @@
 
 namespace grt {
 
-// Persistent refill loop shared by the query kernels (warp-level ray compaction):
-// each lane owns one work item and advances its ray one traversal step per iteration;
-// when the warp's live lanes drop to P.refillBelow or fewer, the idle lanes take fresh
-// items from the global queue with one atomic per warp, so short rays do not leave
-// lanes idle while long ones finish. Src supplies the items:
-//   count()             number of items (may be read from device memory)
-//   begin(i, P, st, s)  set up item i's ray in s; false if the item has no ray
-//   finish(i, s)        consume item i's result s.best
-template <bool ANY, bool SCENE, bool COUNT, class Src>
-__device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src& src) {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t ltMask = (1u << lane) - 1u;
-    const unsigned long long total = src.count();
-    RayState s;
-    Visits v;
-    uint32_t item = kNone;
-    bool exhausted = false;
-    for (;;) {
-        uint32_t live = __ballot_sync(0xffffffffu, item != kNone);
-        while (!exhausted && (uint32_t)__popc(live) <= P.refillBelow) {
-            const uint32_t idle = ~live;
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)__popc(idle));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base + __popc(idle) >= total) exhausted = true;
-            if (item == kNone) {
-                const unsigned long long mine = base + __popc(idle & ltMask);
-                if (mine < total && src.begin((uint32_t)mine, P, st, s)) {
-                    item = (uint32_t)mine;
-                    if (COUNT) v = Visits{};
-                }
-            }
-            live = __ballot_sync(0xffffffffu, item != kNone);
-        }
-        if (live == 0) break;
-        if (item != kNone && stepRay<ANY, SCENE, COUNT>(P, st, s, &v)) {
-            src.finish(item, s);
-            if (COUNT) flushVisits(P.stats, v);
-            item = kNone;
-        }
-    }
-}
-
-// Items = rays of a ray buffer; results = hit records.
-template <bool SCENE>
-struct RayBufferSource {
-    uint32_t n;
-    __device__ unsigned long long count() const { return n; }
-    __device__ bool begin(uint32_t i, const TraceParams& P, Stack& st, RayState& s) const {
-        const float4 a = P.rays[2 * (size_t)i], b = P.rays[2 * (size_t)i + 1];
-        beginRay<SCENE>(P, st, s, f3(a), f3(b), a.w, b.w);
-        return true;
-    }
-    const TraceParams* P;
-    __device__ void finish(uint32_t i, const RayState& s) const { storeHit(P->hits, i, s.best); }
-};
-
 template <bool ANY, bool SCENE, bool COUNT>
 __global__ void traceKernel(TraceParams P) {
     extern __shared__ uint32_t sstack[];
@@ -78,46 +21,7 @@ __global__ void traceKernel(TraceParams P) {
 // The closest hits' t, u, v recomputed in FP64, one thread per ray after traversal so
 // that every lane of a warp takes part (FP64 is far slower than FP32 on this GPU).
 __global__ void __launch_bounds__(256) refineKernel(TraceParams P) {
-    const bool scene = P.target.primType == kPrimScene;
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < P.count; r += gridDim.x * blockDim.x) {
-        uint32_t* h = P.hits + 5 * (size_t)r;
-        const uint32_t inst = h[0], prim = h[1];
-        if (prim == kInvalid) continue;
-        uint32_t primType, geomType;
-        const void* leaves;
-        const uint32_t* toLeaf;
-        if (scene) {
-            const InstanceRecord* R = P.sceneLeaves + P.scenePrimToLeaf[inst];
-            primType = instPrimType(R->typeBits);
-            geomType = instGeomType(R->typeBits);
-            leaves = R->leaves;
-            toLeaf = R->geometry->primToLeaf;
-        } else {
-            primType = P.target.primType;
-            geomType = P.target.geomType;
-            leaves = P.target.leaves;
-            toLeaf = P.targetPrimToLeaf;
-        }
-        const float4* rec = nullptr;
-        bool sphere = false;
-        if (primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
-            rec = reinterpret_cast<const float4*>(leaves) + 3 * (size_t)toLeaf[prim];
-        } else if (P.table && geomType < P.numGeomTypes) {
-            const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + geomType];
-            if (fe.func == GRT_INTERSECT_SPHERE) {
-                rec = reinterpret_cast<const float4*>(fe.data) + prim;
-                sphere = true;
-            }
-        }
-        if (!rec) continue;
-        const float4 a = P.rays[2 * (size_t)r], b = P.rays[2 * (size_t)r + 1];
-        const float4 res = refine64(P.inv64, scene, inst, f3(a), f3(b), rec, sphere, a.w, b.w);
-        if (res.w != 0.f) {
-            h[2] = __float_as_uint(res.x);
-            h[3] = __float_as_uint(res.y);
-            h[4] = __float_as_uint(res.z);
-        }
-    }
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < P.count; r += gridDim.x * blockDim.x) refineHit(P, r);
 }
 
 // ---------------------------------------------------------------- ambient occlusion (Sec. 4)

@@ -304,7 +304,7 @@ __device__ __forceinline__ void ray64(const InstanceFrames64* inv64, bool inInst
 // FP64 decision of a primitive test that float32 could not take, kept out of line
 // (and value-in, value-out) so that it weighs neither on the traversal loop's
 // registers nor on its memory. Returns (t, u, v, 1) for a hit, w = 0 for a miss.
-__device__ __noinline__ float4 decide64(const InstanceFrames64* inv64, bool inInstance, uint32_t inst, float3 wo,
+static __device__ __noinline__ float4 decide64(const InstanceFrames64* inv64, bool inInstance, uint32_t inst, float3 wo,
                                         float3 wd, const float4* rec, bool sphere, float tmin, float tmax,
                                         bool strict) {
     D3 o, d;
@@ -323,7 +323,7 @@ __device__ __noinline__ float4 decide64(const InstanceFrames64* inv64, bool inIn
 
 // The closest hit's distance and barycentrics recomputed in FP64: (t, u, v, 1), or
 // w = 0 when FP64 cannot evaluate them (the float32 values then stand).
-__device__ __noinline__ float4 refine64(const InstanceFrames64* inv64, bool inInstance, uint32_t inst, float3 wo,
+static __device__ __noinline__ float4 refine64(const InstanceFrames64* inv64, bool inInstance, uint32_t inst, float3 wo,
                                         float3 wd, const float4* rec, bool sphere, float tmin, float tmax) {
     D3 o, d;
     ray64(inv64, inInstance, inst, wo, wd, o, d);
@@ -693,6 +693,105 @@ __device__ __forceinline__ float3 aoDirection(const AoFrame& F, uint64_t seed, u
     const float r = sqrtf(xi1);
     const float x = cs * r, z = sn * r, y = sqrtf(fmaxf(1.0f - r * r, 0.0f));
     return F.tg * x + F.bt * z + F.n * y;
+}
+
+// Persistent refill loop shared by the query kernels (warp-level ray compaction):
+// each lane owns one work item and advances its ray one traversal step per iteration;
+// when the warp's live lanes drop to P.refillBelow or fewer, the idle lanes take fresh
+// items from the global queue with one atomic per warp, so short rays do not leave
+// lanes idle while long ones finish. Src supplies the items:
+//   count()             number of items (may be read from device memory)
+//   begin(i, P, st, s)  set up item i's ray in s; false if the item has no ray
+//   finish(i, s)        consume item i's result s.best
+template <bool ANY, bool SCENE, bool COUNT, class Src>
+__device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src& src) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t ltMask = (1u << lane) - 1u;
+    const unsigned long long total = src.count();
+    RayState s;
+    Visits v;
+    uint32_t item = kNone;
+    bool exhausted = false;
+    for (;;) {
+        uint32_t live = __ballot_sync(0xffffffffu, item != kNone);
+        while (!exhausted && (uint32_t)__popc(live) <= P.refillBelow) {
+            const uint32_t idle = ~live;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)__popc(idle));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + __popc(idle) >= total) exhausted = true;
+            if (item == kNone) {
+                const unsigned long long mine = base + __popc(idle & ltMask);
+                if (mine < total && src.begin((uint32_t)mine, P, st, s)) {
+                    item = (uint32_t)mine;
+                    if (COUNT) v = Visits{};
+                }
+            }
+            live = __ballot_sync(0xffffffffu, item != kNone);
+        }
+        if (live == 0) break;
+        if (item != kNone && stepRay<ANY, SCENE, COUNT>(P, st, s, &v)) {
+            src.finish(item, s);
+            if (COUNT) flushVisits(P.stats, v);
+            item = kNone;
+        }
+    }
+}
+
+// Items = rays of a ray buffer; results = hit records.
+template <bool SCENE>
+struct RayBufferSource {
+    uint32_t n;
+    __device__ unsigned long long count() const { return n; }
+    __device__ bool begin(uint32_t i, const TraceParams& P, Stack& st, RayState& s) const {
+        const float4 a = P.rays[2 * (size_t)i], b = P.rays[2 * (size_t)i + 1];
+        beginRay<SCENE>(P, st, s, f3(a), f3(b), a.w, b.w);
+        return true;
+    }
+    const TraceParams* P;
+    __device__ void finish(uint32_t i, const RayState& s) const { storeHit(P->hits, i, s.best); }
+};
+
+// Ray r's closest hit: t, u, v recomputed in FP64 (the hit record is updated in place).
+__device__ __forceinline__ void refineHit(const TraceParams& P, uint32_t r) {
+    const bool scene = P.target.primType == kPrimScene;
+    uint32_t* h = P.hits + 5 * (size_t)r;
+    const uint32_t inst = h[0], prim = h[1];
+    if (prim == kInvalid) return;
+    uint32_t primType, geomType;
+    const void* leaves;
+    const uint32_t* toLeaf;
+    if (scene) {
+        const InstanceRecord* R = P.sceneLeaves + P.scenePrimToLeaf[inst];
+        primType = instPrimType(R->typeBits);
+        geomType = instGeomType(R->typeBits);
+        leaves = R->leaves;
+        toLeaf = R->geometry->primToLeaf;
+    } else {
+        primType = P.target.primType;
+        geomType = P.target.geomType;
+        leaves = P.target.leaves;
+        toLeaf = P.targetPrimToLeaf;
+    }
+    const float4* rec = nullptr;
+    bool sphere = false;
+    if (primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
+        rec = reinterpret_cast<const float4*>(leaves) + 3 * (size_t)toLeaf[prim];
+    } else if (P.table && geomType < P.numGeomTypes) {
+        const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + geomType];
+        if (fe.func == GRT_INTERSECT_SPHERE) {
+            rec = reinterpret_cast<const float4*>(fe.data) + prim;
+            sphere = true;
+        }
+    }
+    if (!rec) return;
+    const float4 a = P.rays[2 * (size_t)r], b = P.rays[2 * (size_t)r + 1];
+    const float4 res = refine64(P.inv64, scene, inst, f3(a), f3(b), rec, sphere, a.w, b.w);
+    if (res.w != 0.f) {
+        h[2] = __float_as_uint(res.x);
+        h[3] = __float_as_uint(res.y);
+        h[4] = __float_as_uint(res.z);
+    }
 }
 
 }  // namespace grt

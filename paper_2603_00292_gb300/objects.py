@@ -6,9 +6,10 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (GRT_BUILD_OPERATION_BUILD, GRT_INSTANCE_GEOMETRY, aabb_list_input, build_options, grtBuildGeometry,
-               grtBuildScene, grtCreateContext, grtCreateFuncTable, grtCreateGeometry, grtCreateScene,
-               grtDestroyContext, grtDestroyFuncTable, grtDestroyGeometry, grtDestroyScene, grtGetBvhInfo,
+from . import (GRT_BUILD_OPERATION_BUILD, GRT_INSTANCE_GEOMETRY, aabb_list_input, batch_scene, build_options,
+               grtBatchBuildTrace, grtBuildGeometry, grtBuildScene, grtCreateBatch, grtCreateContext,
+               grtCreateFuncTable, grtCreateGeometry, grtCreateScene, grtDestroyBatch, grtDestroyContext,
+               grtDestroyFuncTable, grtDestroyGeometry, grtDestroyScene, grtGetBatchInfo, grtGetBvhInfo,
                grtGetGeometryBuildTemporaryBufferSize, grtGetSceneBuildTemporaryBufferSize, grtSetFuncTable,
                scene_input, triangle_mesh_input)
 
@@ -109,6 +110,31 @@ class Scene:
     def close(self):
         if self.handle:
             grtDestroyScene(self.ctx.handle, self.handle)
+            self.handle = None
+
+
+class Batch:
+    """Many triangle geometries, each with its own rays, built and traced (closest hit)
+    in one persistent launch. `scenes` is a list of (Geometry, rays (R,8), hits (R,5));
+    the tensors are kept alive with the batch."""
+
+    def __init__(self, ctx: Context, scenes, options=None):
+        self.ctx = ctx
+        self.scenes = list(scenes)
+        recs = [batch_scene(g.handle, g.input, rays, int(rays.shape[0]), hits) for g, rays, hits in self.scenes]
+        self.options = options
+        self.handle = grtCreateBatch(ctx.handle, recs, options)
+
+    def run(self, stream=None):
+        grtBatchBuildTrace(self.ctx.handle, self.handle, stream)
+        return self
+
+    def info(self):
+        return grtGetBatchInfo(self.ctx.handle, self.handle)
+
+    def close(self):
+        if self.handle:
+            grtDestroyBatch(self.ctx.handle, self.handle)
             self.handle = None
 
 

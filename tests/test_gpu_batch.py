@@ -1,0 +1,132 @@
+"""Batched build + trace of many uneven triangle soups in one persistent launch.
+
+Every geometry the batch builds must be bit-identical to grtBuildGeometry on the same
+input (nodes, leaves, parents: the same Morton codes, stable sort and Karras topology),
+every hit record identical to grtTraceClosest, and the hits must match the FP64 oracle
+within the stated tolerances on sampled scenes.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2603_00292_gb300 as grt
+import scenegen
+from paper_2603_00292_gb300.objects import Batch, Geometry, device_tensor, hits_to_numpy, new_hits, read_device
+from parity import compare_closest
+
+pytestmark = pytest.mark.gpu
+
+
+def _soup_rays(s):
+    cam = s.camera
+    cam_rays = oracle.camera_rays(cam.packed(), cam.width, cam.height)
+    return np.concatenate([cam_rays, s.random_rays]).astype(np.float32)
+
+
+def _workload(count, nmax, rmax, seed=scenegen.MASTER_SEED):
+    out = []
+    for i in range(count):
+        s = scenegen.soup_scene(i, seed=seed, nmin=100, nmax=nmax, rmin=256, rmax=rmax)
+        out.append((s, _soup_rays(s)))
+    return out
+
+
+def _bvh_arrays(g):
+    info = g.info()
+    n = info.primCount
+    nodes = read_device(info.nodes, 64 * info.nodeCount, np.uint32)
+    leaves = read_device(info.leaves, 48 * n, np.uint32)
+    # a one-primitive hierarchy has no parent links (its leaf sits in node 0)
+    parents = read_device(info.parents, 4 * (2 * n - 1), np.uint32) if n >= 2 else np.zeros(0, np.uint32)
+    return nodes, leaves, parents
+
+
+def _run(gpu, work, opts, morton_bits=None):
+    """The batch over `work`, and the same scenes built and traced one by one."""
+    batched, single = [], []
+    for k, (s, rays) in enumerate(work):
+        bits = 0 if morton_bits is None else morton_bits(k)
+        v, i = device_tensor(s.mesh.vertices), device_tensor(s.mesh.indices)
+        r = device_tensor(rays)
+        batched.append((Geometry(gpu, vertices=v, indices=i, morton_bits=bits), r, new_hits(rays.shape[0])))
+        g = Geometry(gpu, vertices=v, indices=i, morton_bits=bits).build()
+        h = new_hits(rays.shape[0])
+        grt.grtTraceClosest(gpu.handle, None, g.handle, r, rays.shape[0], h)
+        single.append((g, h))
+    B = Batch(gpu, batched, opts)
+    B.run()
+    torch.cuda.synchronize()
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+    return B, batched, single
+
+
+def _assert_identical(batched, single):
+    for (gb, _, hb), (gs, hs) in zip(batched, single):
+        for a, b in zip(_bvh_arrays(gb), _bvh_arrays(gs)):
+            assert np.array_equal(a, b)
+        assert torch.equal(hb, hs)
+
+
+def test_batch_matches_per_scene_builds_and_traces(gpu):
+    """Small scenes (one block), 30-bit and forced 63-bit multi-item scenes."""
+    work = _workload(24, nmax=120_000, rmax=30_000)
+    B, batched, single = _run(gpu, work, grt.batch_options(), morton_bits=lambda k: 63 if k % 5 == 3 else 0)
+    info = B.info()
+    assert info.sceneCount == 24 and 0 < info.smallScenes < 24
+    _assert_identical(batched, single)
+
+
+@pytest.mark.parametrize("opts", [
+    dict(block_size=64, shared_depth=8, compact=0.25, small_scene_prims=2000, sort_chunk_tiles=1, build_chunk=1024,
+         trace_chunk=512),
+    dict(block_size=256, shared_depth=32, compact=0.75, small_scene_prims=50_000, sort_chunk_tiles=32,
+         build_chunk=100_000, trace_chunk=100_000, graph=True),
+])
+def test_batch_options_do_not_change_results(gpu, opts):
+    work = _workload(10, nmax=60_000, rmax=8_000)
+    B, batched, single = _run(gpu, work, grt.batch_options(**opts))
+    _assert_identical(batched, single)
+    if opts.get("graph"):  # a replay of the captured graph gives the same records
+        before = [h.clone() for _, _, h in batched]
+        for _, _, h in batched:
+            h.fill_(-1)
+        B.run()
+        torch.cuda.synchronize()
+        assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+        for a, (_, _, h) in zip(before, batched):
+            assert torch.equal(a, h)
+
+
+def test_batch_hits_match_oracle_on_sampled_scenes(gpu):
+    work = _workload(6, nmax=40_000, rmax=6_000, seed=scenegen.MASTER_SEED + 7)
+    B, batched, _ = _run(gpu, work, grt.batch_options(graph=True))
+    for (s, rays), (g, r, h) in zip(work, batched):
+        S = oracle.Scene()
+        S.add_instance(S.add_mesh(s.mesh.vertices, s.mesh.indices))
+        S.build()
+        take = np.arange(0, rays.shape[0], max(1, rays.shape[0] // 1500))
+        ref = S.trace(rays[take])
+        got = tuple(a[take] for a in hits_to_numpy(h))
+        extent = float(np.max(s.hi - s.lo))
+        compare_closest(got, ref, S, rays[take], extent=extent).check()
+        assert (got[1] != 0xFFFFFFFF).sum() > 0
+
+
+def test_batch_edge_cases(gpu):
+    """A one-triangle scene, a scene with no rays, and a scene whose rays all miss."""
+    tri = scenegen.Mesh(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32), np.array([[0, 1, 2]], np.uint32))
+    s = scenegen.soup_scene(0, nmin=3000, nmax=3000, rmin=600, rmax=600)
+    away = np.tile(np.array([[0, 0, 5, 0, 0, 0, 1, np.inf]], np.float32), (100, 1))
+    cases = [(tri, scenegen.random_rays(64, np.array([-1.0] * 3), np.array([1.0] * 3), 3, 1)),
+             (s.mesh, np.zeros((0, 8), np.float32)), (s.mesh, away)]
+    work = []
+    for mesh, rays in cases:
+        class _S:
+            pass
+        x = _S()
+        x.mesh = mesh
+        work.append((x, rays.astype(np.float32)))
+    B, batched, single = _run(gpu, work, grt.batch_options())
+    _assert_identical(batched, single)
+    assert (hits_to_numpy(batched[2][2])[1] == 0xFFFFFFFF).all()
