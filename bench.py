@@ -20,6 +20,10 @@ timed region.
 `--impl reference` times the CPU oracle (FP64, oracle/) on a bounded sample of the
 same workload on the host cores.
 
+`--workload batched-soups-256` times 256 uneven triangle soups (1e3 to 2e6 triangles,
+4,096 to 2^20 rays each): all builds and closest-hit traces in one persistent launch
+(CUDA graph, autotuned options) against 256 sequential per-scene build + trace calls.
+
 `--workload lambert-adjoint-1080p` prints a second kind of line instead: differentiable
 Lambert shading of a 642-vertex icosphere at 1920x1080 (closest hit, shading with one
 shadow any-hit ray per lit pixel), forward alone against forward + adjoint backward,
@@ -59,8 +63,11 @@ def parse():
     p.add_argument("--impl", default="grt", choices=["grt", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
-    p.add_argument("--workload", default=WORKLOAD["workload"], choices=[WORKLOAD["workload"], "lambert-adjoint-1080p"],
-                   help="the ambient-occlusion throughput workload (default) or the differentiable-shading one")
+    p.add_argument("--workload", default=WORKLOAD["workload"],
+                   choices=[WORKLOAD["workload"], "lambert-adjoint-1080p", "batched-soups-256"],
+                   help="the ambient-occlusion throughput workload (default), the differentiable-shading one, "
+                        "or the batched many-scenes one")
+    p.add_argument("--no-autotune", action="store_true", help="batched workload: default launch options")
     return p.parse_args()
 
 
@@ -573,6 +580,234 @@ def cpu_adjoint(P, rays, target_s: float):
                       f"({dt:.1f} s), scaled by {stride}"}
 
 
+# ----------------------------------------------------------------------------- batched workload
+BATCHED = dict(workload="batched-soups-256", scenes=256, prims="log-U[1e3, 2e6] per scene",
+               rays="log-U[4096, 2^20] per scene, half camera, half uniform random",
+               clusters="8 Gaussian", edges="log-U[1e-3, 1e-1]", seed=20260301)
+
+
+def _soup_worker(i: int):
+    """One soup of the batched workload (host arrays), for a spawn-started pool."""
+    import scenegen
+
+    s = scenegen.soup_scene(i, seed=BATCHED["seed"])
+    return (s.mesh.vertices, s.mesh.indices, s.camera.packed(), s.camera.width, s.camera.height, s.random_rays,
+            float(np.max(s.hi - s.lo)))
+
+
+def batched_soups(count: int):
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_soup_worker, range(count), chunksize=1)
+
+
+def build_bytes_per_prim(bits: int) -> int:
+    """Algorithmic DRAM bytes of building one triangle (LBVH): prep reads the indices
+    and vertices (48) and writes a centroid and a fit counter (20); radix pass 0 reads
+    the centroid and writes key and value, every pass reads the keys once for its
+    histogram and reads and writes keys and values in its scatter; emission reads a key
+    and writes a node word and two parent links (28 or 32); the fit reads the value,
+    indices and vertices (52), writes the leaf record and its slot (52) and, per
+    internal node, two parent links, two box writes and one box read (~80)."""
+    kb, passes = (4, 4) if bits == 30 else (8, 8)
+    sort = (16 + kb + 4) + (passes - 1) * kb + passes * 2 * (kb + 4)
+    return 68 + sort + (kb + 24) + 52 + 52 + 80
+
+
+def run_batched(args, rank, world, local):
+    """256 uneven triangle soups, each with its own rays: every BVH build and closest-hit
+    trace in one persistent launch (CUDA graph, autotuned options) against the same
+    work as 256 sequential per-scene build + trace calls."""
+    soups = batched_soups(BATCHED["scenes"])  # before the first GPU call (spawned pool)
+    import torch
+
+    import paper_2603_00292_gb300 as grt
+    from paper_2603_00292_gb300 import autotune
+    from paper_2603_00292_gb300 import build as grt_build
+    from paper_2603_00292_gb300.objects import Batch, Context, Geometry, device_tensor, empty_bytes, new_hits
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        grt_build.build()
+    if dist:
+        dist.barrier()
+    ctx = Context(local)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    meshes, rays, hits_b, hits_s, geo_b, geo_s = [], [], [], [], [], []
+    host = []
+    total_prims = total_rays = 0
+    # one build temporary for every geometry, sized for the largest
+    big = max(range(len(soups)), key=lambda k: soups[k][1].shape[0])
+    nbig = soups[big][1].shape[0]  # the size query reads only the counts (the addresses stand in)
+    temp = empty_bytes(grt.grtGetGeometryBuildTemporaryBufferSize(
+        ctx.handle, grt.triangle_mesh_input(256, 256, triangle_count=nbig, vertex_count=3 * nbig),
+        grt.build_options()))
+    for v, i, cam, W, H, rr, extent in soups:
+        dv, di = device_tensor(v), device_tensor(i)
+        R = W * H + rr.shape[0]
+        r = torch.empty((R, 8), dtype=torch.float32, device="cuda")
+        grt.grtGenerateCameraRays(ctx.handle, grt.camera(cam[0:3], cam[3:6], cam[6:9]), W, H, r, sh)
+        r[W * H:].copy_(torch.from_numpy(rr))
+        meshes.append((dv, di))
+        rays.append(r)
+        hits_b.append(new_hits(R))
+        hits_s.append(new_hits(R))
+        geo_b.append(Geometry(ctx, vertices=dv, indices=di, temp=temp))
+        geo_s.append(Geometry(ctx, vertices=dv, indices=di, temp=temp))
+        host.append((v, i, rr, W * H))
+        total_prims += i.shape[0]
+        total_rays += R
+    scenes = list(zip(geo_b, rays, hits_b))
+    torch.cuda.synchronize()
+
+    tune_report = None
+    if args.no_autotune:
+        opts = dict(autotune.DEFAULTS)
+    else:
+        opts, tune_report = autotune.tune(ctx, scenes)
+    B = Batch(ctx, scenes, grt.batch_options(graph=True, **opts))
+    info = B.info()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def sequential():
+        for g, r, h in zip(geo_s, rays, hits_s):
+            g.build(sh)
+            grt.grtTraceClosest(ctx.handle, None, g.handle, r, r.shape[0], h, None, None, sh)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        out = []
+        l0 = grt.grtGetLaunchCount()
+        for _ in range(args.steps):
+            flush.zero_()
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            ev[1].synchronize()
+            out.append(ev[0].elapsed_time(ev[1]))
+        return out, grt.grtGetLaunchCount() - l0
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    clocks.start()
+    b_ms, b_launches = timed(lambda: B.run(sh))
+    s_ms, s_launches = timed(sequential)
+    clk = clocks.stop()
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+    identical = all(torch.equal(a, b) for a, b in zip(hits_b, hits_s))
+    batched_ms, seq_ms = statistics.mean(b_ms), statistics.mean(s_ms)
+    if dist:
+        t = torch.tensor([batched_ms, seq_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        batched_ms, seq_ms = (float(x) for x in t.tolist())
+
+    # algorithmic bytes of one launch: the builds by formula, the traces from a
+    # counting pass (nodes and triangles visited per ray) on the per-scene path
+    cnt = grt.trace_options(flags=grt.GRT_TRACE_FLAG_COUNT)
+    grt.grtGetTraceStatistics(ctx.handle, sh)
+    for g, r, h in zip(geo_s, rays, hits_s):
+        grt.grtTraceClosest(ctx.handle, None, g.handle, r, r.shape[0], h, None, cnt, sh)
+    st = grt.grtGetTraceStatistics(ctx.handle, sh)
+    trace_bytes = total_rays * (RAY_BYTES + HIT_BYTES) + NODE_BYTES * st["nodesVisited"] + TRI_BYTES * st["trianglesTested"]
+    bits = [grt.grtGetBvhInfo(ctx.handle, geom=g.handle).mortonBits for g in geo_s]
+    build_bytes = sum(build_bytes_per_prim(b) * m[1].shape[0] for b, m in zip(bits, meshes))
+    nbytes = trace_bytes + build_bytes
+    peaks, how = measured_peaks()
+    achieved = nbytes / (batched_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "batchKernel", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": how,
+                "traffic": ncu_traffic("batchKernel"), "algorithmic_bytes_per_launch": int(nbytes),
+                "build_bytes": int(build_bytes), "trace_bytes": int(trace_bytes), "launch_ms": round(batched_ms, 4),
+                "per_ray": {"nodes": round(st["nodesVisited"] / max(1, st["rays"]), 2),
+                            "triangles": round(st["trianglesTested"] / max(1, st["rays"]), 2)}}
+
+    # end to end: meshes and rays up from pinned host memory, hit records back
+    pin = [(torch.from_numpy(v).pin_memory(), torch.from_numpy(i.view(np.int32)).pin_memory(), r.cpu().pin_memory())
+           for (v, i, _, _), r in zip(host, rays)]
+    hits_h = [torch.empty(h.shape, dtype=h.dtype).pin_memory() for h in hits_b]
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        ev[0].record(stream)
+        for (dv, di), r, (pv, pi, pr) in zip(meshes, rays, pin):
+            dv.copy_(pv, non_blocking=True)
+            di.copy_(pi, non_blocking=True)
+            r.copy_(pr, non_blocking=True)
+        B.run(sh)
+        for hh, h in zip(hits_h, hits_b):
+            hh.copy_(h, non_blocking=True)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        if k >= args.warmup:
+            e2e.append(ev[0].elapsed_time(ev[1]))
+    h2d = sum(pv.numel() * 4 + pi.numel() * 4 + pr.numel() * 4 for pv, pi, pr in pin)
+    d2h = sum(h.numel() * 4 for h in hits_h)
+    line = {"metric": "batched build+trace of 256 uneven scenes: ms per launch vs 256 sequential per-scene build+trace",
+            "value": round(batched_ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(batched_ms, 3), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": dict(BATCHED, total_prims=total_prims, total_rays=total_rays, l2="flushed between steps",
+                           parallelism=f"replicas{world}"),
+            "sequential_ms": round(seq_ms, 3), "speedup_vs_sequential": round(seq_ms / batched_ms, 3),
+            "mrays_per_s": round(total_rays / (batched_ms / 1e3) / 1e6, 1),
+            "mprims_per_s": round(total_prims / (batched_ms / 1e3) / 1e6, 1),
+            "sequential_mrays_per_s": round(total_rays / (seq_ms / 1e3) / 1e6, 1),
+            "identical_to_sequential": bool(identical), "options": opts,
+            "batch": {"items": info.itemCount, "small_scenes": info.smallScenes, "blocks": info.blocks,
+                      "block_size": info.blockSize, "device_bytes": int(info.deviceBytes)},
+            "autotune": None if tune_report is None else {k: tune_report[k] for k in tune_report if k != "tried"},
+            "roofline": roofline,
+            "e2e": {"value": round(statistics.mean(e2e), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(b_launches), "sequential_gpu_launches": int(s_launches), "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_batched(host, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    B.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_batched(host, target_s: float):
+    """The FP64 oracle (its own BVH build + closest-hit trace) over the smallest scenes
+    of the workload until about target_s seconds are spent."""
+    import oracle
+
+    order = sorted(range(len(host)), key=lambda k: host[k][1].shape[0])
+    prims = rays = 0
+    t0 = time.perf_counter()
+    used = 0
+    for k in order:
+        v, i, rr, _ = host[k]
+        S = oracle.Scene()
+        S.add_instance(S.add_mesh(v, i))
+        S.build()
+        S.trace(rr)
+        prims += i.shape[0]
+        rays += rr.shape[0]
+        used += 1
+        if time.perf_counter() - t0 > target_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(rays / dt / 1e6, 4), "unit": "Mrays/s (build+trace)", "cores": os.cpu_count(),
+            "kind": "oracle", "mprims_per_s": round(prims / dt / 1e6, 4),
+            "sample": f"the {used} smallest scenes: FP64 BVH build + closest hit of their random rays "
+                      f"({prims} triangles, {rays} rays, {dt:.1f} s)"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -580,6 +815,8 @@ def main():
         run_reference(args, rank, world, local)
     elif args.workload == ADJOINT["workload"]:
         run_adjoint(args, rank, world, local)
+    elif args.workload == BATCHED["workload"]:
+        run_batched(args, rank, world, local)
     else:
         run_grt(args, rank, world, local)
 

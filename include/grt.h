@@ -359,7 +359,8 @@ typedef struct grtBatchScene {
 } grtBatchScene;
 
 enum {
-    GRT_BATCH_FLAG_GRAPH = 1 /* capture the launch sequence once into a CUDA graph and replay it */
+    GRT_BATCH_FLAG_GRAPH = 1,  /* capture the launch sequence once into a CUDA graph and replay it */
+    GRT_BATCH_FLAG_PROFILE = 2 /* record when each work item started, was ready and ended */
 };
 
 /* Tuning knobs (0 selects the default in brackets). */
@@ -372,6 +373,8 @@ typedef struct grtBatchOptions {
     uint32_t sortChunkTiles;    /* radix tiles (blockSize x 8 keys) per sort work item [8] */
     uint32_t buildChunk;        /* primitives per prep / emission / fit work item [16384] */
     uint32_t traceChunk;        /* rays per trace work item [16384] */
+    uint32_t sceneGroup;        /* scenes per scheduling group, largest first: a group's builds, then its
+                                   traces [32] */
     uint32_t flags;             /* GRT_BATCH_FLAG_* */
 } grtBatchOptions;
 
@@ -402,6 +405,25 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
 grtError grtBatchBuildTrace(grtContext ctx, grtBatch batch, void* stream);
 
 grtError grtGetBatchInfo(grtContext ctx, grtBatch batch, grtBatchInfo* info);
+
+/* One work item of the last launch of a batch created with GRT_BATCH_FLAG_PROFILE:
+ * scene, phase and chunk, the SM that ran it, and the device clock (ns) when its block
+ * took it, when its dependencies were met, and when it finished. */
+typedef struct grtBatchItemRecord {
+    uint32_t scene;
+    uint32_t phase;
+    uint32_t chunk;
+    uint32_t sm;
+    uint64_t startNs;
+    uint64_t readyNs;
+    uint64_t endNs;
+} grtBatchItemRecord;
+
+/* Copies up to `capacity` item records of the last launch (queue order) into `records`
+ * (host memory) and sets *count to the batch's item count (0 without profiling).
+ * Synchronous: call after the launch has finished. */
+grtError grtGetBatchProfile(grtContext ctx, grtBatch batch, grtBatchItemRecord* records, uint32_t capacity,
+                            uint32_t* count);
 grtError grtDestroyBatch(grtContext ctx, grtBatch batch);
 
 /* ---------------------------------------------------------------- introspection and building blocks */

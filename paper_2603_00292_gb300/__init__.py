@@ -108,7 +108,8 @@ class grtBatchOptions(ctypes.Structure):
     _fields_ = [("blockSize", ctypes.c_uint32), ("sharedStackDepth", ctypes.c_uint32),
                 ("globalStackDepth", ctypes.c_uint32), ("compactThreshold", ctypes.c_float),
                 ("smallScenePrims", ctypes.c_uint32), ("sortChunkTiles", ctypes.c_uint32),
-                ("buildChunk", ctypes.c_uint32), ("traceChunk", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("buildChunk", ctypes.c_uint32), ("traceChunk", ctypes.c_uint32), ("sceneGroup", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
 
 
 class grtBatchInfo(ctypes.Structure):
@@ -118,6 +119,13 @@ class grtBatchInfo(ctypes.Structure):
 
 
 GRT_BATCH_FLAG_GRAPH = 1
+GRT_BATCH_FLAG_PROFILE = 2
+
+
+class grtBatchItemRecord(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_uint32), ("phase", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("sm", ctypes.c_uint32), ("startNs", ctypes.c_uint64), ("readyNs", ctypes.c_uint64),
+                ("endNs", ctypes.c_uint64)]
 
 # ------------------------------------------------------------------ loading
 _lib = None
@@ -165,6 +173,7 @@ _SIGS = {
     "grtCreateBatch": [_P, ctypes.POINTER(grtBatchScene), _U32, ctypes.POINTER(grtBatchOptions), ctypes.POINTER(_P)],
     "grtBatchBuildTrace": [_P, _P, _P],
     "grtGetBatchInfo": [_P, _P, ctypes.POINTER(grtBatchInfo)],
+    "grtGetBatchProfile": [_P, _P, ctypes.c_void_p, _U32, ctypes.POINTER(_U32)],
     "grtDestroyBatch": [_P, _P],
 }
 
@@ -433,9 +442,11 @@ def grtSortPairs(ctx, keys, values, count, key_bits, significant_bits, temp, str
 
 
 def batch_options(block_size=0, shared_depth=0, global_depth=0, compact=0.0, small_scene_prims=0,
-                  sort_chunk_tiles=0, build_chunk=0, trace_chunk=0, graph=False) -> grtBatchOptions:
+                  sort_chunk_tiles=0, build_chunk=0, trace_chunk=0, scene_group=0, graph=False,
+                  profile=False) -> grtBatchOptions:
+    flags = (GRT_BATCH_FLAG_GRAPH if graph else 0) | (GRT_BATCH_FLAG_PROFILE if profile else 0)
     return grtBatchOptions(block_size, shared_depth, global_depth, compact, small_scene_prims, sort_chunk_tiles,
-                           build_chunk, trace_chunk, GRT_BATCH_FLAG_GRAPH if graph else 0)
+                           build_chunk, trace_chunk, scene_group, flags)
 
 
 def batch_scene(geometry: int, inp: grtGeometryBuildInput, rays, ray_count: int, hits) -> grtBatchScene:
@@ -462,3 +473,17 @@ def grtGetBatchInfo(ctx, batch) -> grtBatchInfo:
 
 def grtDestroyBatch(ctx, batch):
     check(lib().grtDestroyBatch(ctx, batch), "grtDestroyBatch")
+
+
+def grtGetBatchProfile(ctx, batch):
+    """Item records of the batch's last launch as a numpy structured array (empty
+    without GRT_BATCH_FLAG_PROFILE)."""
+    import numpy as np
+
+    count = _U32()
+    check(lib().grtGetBatchProfile(ctx, batch, None, 0, ctypes.byref(count)), "grtGetBatchProfile")
+    recs = (grtBatchItemRecord * max(1, count.value))()
+    check(lib().grtGetBatchProfile(ctx, batch, recs, count.value, ctypes.byref(count)), "grtGetBatchProfile")
+    dt = np.dtype([("scene", "<u4"), ("phase", "<u4"), ("chunk", "<u4"), ("sm", "<u4"), ("startNs", "<u8"),
+                   ("readyNs", "<u8"), ("endNs", "<u8")])
+    return np.frombuffer(bytes(recs), dtype=dt, count=count.value).copy()

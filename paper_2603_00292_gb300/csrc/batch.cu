@@ -22,7 +22,8 @@
 // (per-scene completion counters). The host orders the queue so that an item only
 // ever waits for items taken from the queue before it, so a waiting block never
 // blocks the progress it waits for; every wait is bounded in time all the same and
-// latches GRT_ERROR_TIMEOUT if it expires.
+// latches GRT_ERROR_TIMEOUT if it expires. Scenes are queued in groups, largest
+// first, each group's builds followed by its traces (see grtCreateBatch).
 //
 // Memory. Data written earlier in the launch by another block (centroids, keys,
 // histograms, parents, boxes) is read with L1-bypassing loads. Node and leaf records,
@@ -87,6 +88,7 @@ struct BatchParams {
     unsigned long long* traceCounters;  // per item
     uint32_t* error;
     uint32_t* abort;  // set when a wait expired: later items skip their work
+    unsigned long long* profile;  // with GRT_BATCH_FLAG_PROFILE: 4 words per item, else null
     uint32_t* globalStack;
     uint32_t globalDepth;
     uint32_t globalStride;
@@ -427,9 +429,12 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
         if (item >= B.itemCount) break;
         const BatchItemDev it = B.items[item];
         const BatchSceneDev& S = B.scenes[it.scene];
+        unsigned long long t0 = 0, t1 = 0;
         if (threadIdx.x == 0) {
+            if (B.profile) t0 = globalTimerNs();
             if (it.phase > 0) waitPhase(B, it.scene, it.phase - 1, it.waitCount);
             skipS = *(volatile uint32_t*)B.abort;
+            if (B.profile) t1 = globalTimerNs();
         }
         __syncthreads();
         const bool wide = S.bits != 30;
@@ -475,7 +480,15 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
         }
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(B.done + (size_t)it.scene * kBatchPhases + it.phase, 1u);
+        if (threadIdx.x == 0) {
+            atomicAdd(B.done + (size_t)it.scene * kBatchPhases + it.phase, 1u);
+            if (B.profile) {
+                unsigned smid;
+                asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+                unsigned long long* pr = B.profile + 4 * item;
+                pr[0] = t0, pr[1] = t1, pr[2] = globalTimerNs(), pr[3] = ((unsigned long long)smid << 32) | blockIdx.x;
+            }
+        }
     }
 }
 
@@ -516,11 +529,12 @@ static grtError resolveBatchOptions(const grtBatchOptions* o, grtBatchOptions* r
     if (!d.sortChunkTiles) d.sortChunkTiles = 8;
     if (!d.buildChunk) d.buildChunk = 16384;
     if (!d.traceChunk) d.traceChunk = 16384;
+    if (!d.sceneGroup) d.sceneGroup = 32;
     if (d.blockSize != 64 && d.blockSize != 128 && d.blockSize != 256) return GRT_ERROR_INVALID_PARAMETER;
     if (d.sharedStackDepth > 32 || d.globalStackDepth > 4096) return GRT_ERROR_INVALID_PARAMETER;
     if (d.compactThreshold > 1.f || d.sortChunkTiles > 4096) return GRT_ERROR_INVALID_PARAMETER;
     if (d.buildChunk > (1u << 24) || d.traceChunk > (1u << 24)) return GRT_ERROR_INVALID_PARAMETER;
-    if (d.flags & ~(uint32_t)GRT_BATCH_FLAG_GRAPH) return GRT_ERROR_INVALID_PARAMETER;
+    if (d.flags & ~(uint32_t)(GRT_BATCH_FLAG_GRAPH | GRT_BATCH_FLAG_PROFILE)) return GRT_ERROR_INVALID_PARAMETER;
     *r = d;
     return GRT_SUCCESS;
 }
@@ -586,8 +600,11 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
                    alignUp(4 * (size_t)kBatchRadix * d.sortChunks, 256) + alignUp(4 * nn, 256);
     }
 
-    // work items: rounds of phases, the larger scenes first within a round; trace
-    // items last, the scenes whose builds end soonest first
+    // work items. Scenes go in groups of opt.sceneGroup, largest first: a group's build
+    // phases in rounds (every scene's phase r before any scene's phase r+1), then the
+    // group's trace items, largest scene first. The largest scenes, whose rays are the
+    // longest, are thus built first and their traces overlap the later groups' builds.
+    // Every wait points to a phase of the same scene placed earlier in the queue.
     std::vector<BatchItemDev> items;
     std::vector<uint32_t> order(sceneCount);
     for (uint32_t i = 0; i < sceneCount; ++i) order[i] = i;
@@ -601,24 +618,23 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);
         return 0u;
     };
-    for (uint32_t r = 0; r < kBatchPhases; ++r)
-        for (uint32_t i : order) {
+    for (uint32_t g0 = 0; g0 < sceneCount; g0 += opt.sceneGroup) {
+        const uint32_t g1 = std::min(sceneCount, g0 + opt.sceneGroup);
+        for (uint32_t r = 0; r < kBatchPhases; ++r)
+            for (uint32_t k = g0; k < g1; ++k) {
+                const uint32_t i = order[k];
+                const BatchSceneDev& d = S[i];
+                if (r >= d.tracePhase) continue;
+                const uint32_t cnt = phaseItems(d, r), wait = r ? phaseItems(d, r - 1) : 0u;
+                for (uint32_t c = 0; c < cnt; ++c) items.push_back(BatchItemDev{i, r, c, wait});
+            }
+        for (uint32_t k = g0; k < g1; ++k) {
+            const uint32_t i = order[k];
             const BatchSceneDev& d = S[i];
-            if (r >= d.tracePhase) continue;
-            const uint32_t cnt = phaseItems(d, r), wait = r ? phaseItems(d, r - 1) : 0u;
-            for (uint32_t k = 0; k < cnt; ++k) items.push_back(BatchItemDev{i, r, k, wait});
+            const uint32_t cnt = phaseItems(d, d.tracePhase), wait = phaseItems(d, d.tracePhase - 1);
+            for (uint32_t c = 0; c < cnt; ++c) items.push_back(BatchItemDev{i, d.tracePhase, c, wait});
         }
-    std::vector<uint32_t> traceOrder(order.rbegin(), order.rend());
-    std::stable_sort(traceOrder.begin(), traceOrder.end(),
-                     [&](uint32_t a, uint32_t b) { return S[a].tracePhase < S[b].tracePhase; });
-    for (uint32_t i : traceOrder) {
-        const BatchSceneDev& d = S[i];
-        const uint32_t cnt = phaseItems(d, d.tracePhase), wait = phaseItems(d, d.tracePhase - 1);
-        for (uint32_t k = 0; k < cnt; ++k) items.push_back(BatchItemDev{i, d.tracePhase, k, wait});
     }
-    // the queue takes a phase's items only after every item of the phase before it
-    // (waits point backwards), which the round order guarantees; the trace items come
-    // after every build item
 
     // launch shape and the device allocation
     BatchObject* b = new BatchObject();
@@ -641,7 +657,9 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
     const size_t offHead = offDone + alignUp(4 * (size_t)std::max(sceneCount, 1u) * kBatchPhases, 256);
     const size_t offTrace = offHead + 256;  // head (8 bytes) and abort flag (4 bytes at +64)
     const size_t offStack = offTrace + alignUp(8 * std::max<size_t>(items.size(), 1), 256);
-    const size_t offScratch = offStack + alignUp(threads * opt.globalStackDepth * 4, 256);
+    const size_t offProfile = offStack + alignUp(threads * opt.globalStackDepth * 4, 256);
+    const bool profile = (opt.flags & GRT_BATCH_FLAG_PROFILE) != 0;
+    const size_t offScratch = offProfile + (profile ? alignUp(32 * std::max<size_t>(items.size(), 1), 256) : 0);
     b->deviceBytes = offScratch + scratch;
     if (cudaMalloc(&b->deviceMem, b->deviceBytes) != cudaSuccess) {
         cudaGetLastError();
@@ -679,6 +697,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
     P.done = (uint32_t*)(base + offDone);
     P.head = (unsigned long long*)(base + offHead);
     P.abort = (uint32_t*)(base + offHead + 64);
+    P.profile = profile ? (unsigned long long*)(base + offProfile) : nullptr;
     P.traceCounters = (unsigned long long*)(base + offTrace);
     P.error = &workspace(c)->error;
     P.globalStack = (uint32_t*)(base + offStack);
@@ -751,6 +770,30 @@ grtError grtBatchBuildTrace(grtContext ctx, grtBatch batch, void* stream) {
             o->built = true;
             o->vertexCount = b->vertexCounts[i];
         }
+    }
+    return GRT_SUCCESS;
+}
+
+grtError grtGetBatchProfile(grtContext ctx, grtBatch batch, grtBatchItemRecord* records, uint32_t capacity,
+                            uint32_t* count) {
+    BatchObject* b = findBatch(batch);
+    if (!ctx || !b || !count || (capacity && !records)) return GRT_ERROR_INVALID_PARAMETER;
+    *count = b->params.profile ? b->itemCount : 0u;
+    if (!b->params.profile || capacity == 0) return GRT_SUCCESS;
+    const uint32_t n = std::min(capacity, b->itemCount);
+    std::vector<unsigned long long> raw(4 * (size_t)n);
+    std::vector<BatchItemDev> items(n);
+    GRT_CUDA(cudaMemcpy(raw.data(), b->params.profile, raw.size() * 8, cudaMemcpyDeviceToHost));
+    GRT_CUDA(cudaMemcpy(items.data(), b->params.items, items.size() * sizeof(BatchItemDev), cudaMemcpyDeviceToHost));
+    for (uint32_t i = 0; i < n; ++i) {
+        grtBatchItemRecord& r = records[i];
+        r.scene = items[i].scene;
+        r.phase = items[i].phase;
+        r.chunk = items[i].chunk;
+        r.sm = (uint32_t)(raw[4 * i + 3] >> 32);
+        r.startNs = raw[4 * i];
+        r.readyNs = raw[4 * i + 1];
+        r.endNs = raw[4 * i + 2];
     }
     return GRT_SUCCESS;
 }
