@@ -691,7 +691,9 @@ __device__ __forceinline__ float3 aoDirection(const AoFrame& F, uint64_t seed, u
     float sn, cs;
     sincospif(2.0f * xi0, &sn, &cs);
     const float r = sqrtf(xi1);
-    const float x = cs * r, z = sn * r, y = sqrtf(fmaxf(1.0f - r * r, 0.0f));
+    // y = sqrt(1 - r^2) = sqrt(1 - xi1): xi1 is a multiple of 2^-24 in [0, 1), so 1 - xi1
+    // is exact in float32, where 1 - r*r would cancel for grazing samples (xi1 near 1)
+    const float x = cs * r, z = sn * r, y = sqrtf(1.0f - xi1);
     return F.tg * x + F.bt * z + F.n * y;
 }
 

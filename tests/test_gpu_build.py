@@ -58,20 +58,16 @@ def _oracle_for(case):
     return lo, hi, c
 
 
-@pytest.mark.parametrize("name", ["icosphere", "terrain", "flat", "spheres", "dupes", "n1", "n2", "n3", "n17",
-                                  "n4097"])
-@pytest.mark.parametrize("bits", [30, 63])
-def test_build_matches_oracle_bit_exact(gpu, name, bits):
-    case = _case(name)
-    dev = {k: device_tensor(v) for k, v in case.items()}
-    g = Geometry(gpu, morton_bits=bits, **dev).build()
+def check_bit_exact(g, case, bits):
+    """The built geometry `g` of `case` equals the oracle's LBVH bit for bit: sorted
+    Morton codes and order (from the build temporary), topology, child boxes, parent
+    links and leaf records."""
     torch.cuda.synchronize()
     info = g.info()
     n = info.primCount
     lo, hi, cen = _oracle_for(case)
     ref = oracle.lbvh(lo, hi, cen, 10 if bits == 30 else 21)
     assert info.mortonBits == bits
-    # sorted keys and order from the temporary buffer
     koff, voff, boff = grt.grtGetBuildTemporaryLayout(n, bits)
     kdt = np.uint32 if bits == 30 else np.uint64
     keys = _tensor_bytes(g.temp, koff, n * (4 if bits == 30 else 8), kdt)
@@ -104,10 +100,11 @@ def test_build_matches_oracle_bit_exact(gpu, name, bits):
     # parent links: (parent << 1 | side), root marked invalid
     par = _read(info.parents, (2 * n - 1) * 4, np.uint32)
     assert par[0] == 0xFFFFFFFF
-    for k in range(n - 1):
-        for side, c in enumerate((cl[k], cr[k])):
-            slot = (n - 1 + (c & 0x7FFFFFFF)) if c & LEAF else c
-            assert par[slot] == (k << 1 | side)
+    k = np.arange(n - 1, dtype=np.uint64)
+    for side, c in enumerate((cl, cr)):
+        c = c.astype(np.uint64)
+        slot = np.where(c & LEAF, n - 1 + (c & 0x7FFFFFFF), c).astype(np.int64)
+        assert np.array_equal(par[slot].astype(np.uint64), (k << 1) | side), "parent links"
     # leaves
     if "indices" in case:
         rec = _read(info.leaves, n * 48, np.float32).reshape(n, 12)
@@ -119,6 +116,16 @@ def test_build_matches_oracle_bit_exact(gpu, name, bits):
     else:
         ids = _read(info.leaves, n * 4, np.uint32)
         assert np.array_equal(ids, ref["order"])
+
+
+@pytest.mark.parametrize("name", ["icosphere", "terrain", "flat", "spheres", "dupes", "n1", "n2", "n3", "n17",
+                                  "n4097"])
+@pytest.mark.parametrize("bits", [30, 63])
+def test_build_matches_oracle_bit_exact(gpu, name, bits):
+    case = _case(name)
+    dev = {k: device_tensor(v) for k, v in case.items()}
+    g = Geometry(gpu, morton_bits=bits, **dev).build()
+    check_bit_exact(g, case, bits)
     g.close()
 
 
