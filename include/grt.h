@@ -230,7 +230,8 @@ typedef struct grtTraceOptions {
     uint32_t blockSize;        /* threads per block: 0 = default (128); 64, 128 or 256 */
     uint32_t sharedStackDepth; /* entries per thread in shared memory: 0 = default (16), 1..32 */
     uint32_t globalStackDepth; /* further entries per thread in global memory: 0 = default (64) */
-    float compactThreshold;    /* warp refill threshold (fraction of live lanes), 0 = default (0.5) */
+    float compactThreshold;    /* warp refill threshold (fraction of live lanes), 0 = default (0.75 for
+                                  grtTraceAmbientOcclusion, else 0.5) */
     uint32_t flags;            /* GRT_TRACE_FLAG_COUNT: accumulate grtTraceStatistics (slower) */
     void* globalStack;         /* optional caller-owned device buffer for the global entries; NULL = the
                                   context's own (then traces on one context must not overlap in time) */
@@ -368,7 +369,7 @@ typedef struct grtBatchOptions {
     uint32_t blockSize;         /* threads per block: 64, 128 or 256 [128] */
     uint32_t sharedStackDepth;  /* traversal stack entries in shared memory, <= 32 [16] */
     uint32_t globalStackDepth;  /* spill entries per thread, <= 4096 [64] */
-    float compactThreshold;     /* refill a warp when <= this fraction of lanes hold a ray [0.5] */
+    float compactThreshold;     /* refill a warp when <= this fraction of lanes hold a ray [0.75] */
     uint32_t smallScenePrims;   /* scenes up to this many triangles are built by one block [8192] */
     uint32_t sortChunkTiles;    /* radix tiles (blockSize x 8 keys) per sort work item [8] */
     uint32_t buildChunk;        /* primitives per prep / emission / fit work item [16384] */

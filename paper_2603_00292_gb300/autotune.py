@@ -25,7 +25,7 @@ from .objects import Batch
 GRID = dict(block_size=[64, 128, 256], shared_depth=[8, 16, 32], compact=[0.25, 0.5, 0.75])
 REFINE = dict(scene_group=[8, 16, 64, 256], trace_chunk=[4096, 16384, 65536], sort_chunk_tiles=[2, 8, 32],
               small_scene_prims=[2048, 8192, 32768])
-DEFAULTS = dict(block_size=128, shared_depth=16, compact=0.5, trace_chunk=16384, sort_chunk_tiles=8,
+DEFAULTS = dict(block_size=128, shared_depth=16, compact=0.75, trace_chunk=16384, sort_chunk_tiles=8,
                 small_scene_prims=8192, scene_group=32)
 
 

@@ -524,7 +524,7 @@ static grtError resolveBatchOptions(const grtBatchOptions* o, grtBatchOptions* r
     if (!d.blockSize) d.blockSize = 128;
     if (!d.sharedStackDepth) d.sharedStackDepth = 16;
     if (!d.globalStackDepth) d.globalStackDepth = 64;
-    if (!(d.compactThreshold > 0.f)) d.compactThreshold = 0.5f;
+    if (!(d.compactThreshold > 0.f)) d.compactThreshold = 0.75f;
     if (!d.smallScenePrims) d.smallScenePrims = 8192;
     if (!d.sortChunkTiles) d.sortChunkTiles = 8;
     if (!d.buildChunk) d.buildChunk = 16384;

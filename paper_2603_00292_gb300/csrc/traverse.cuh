@@ -447,6 +447,10 @@ struct Stack {
         --sp;
         return sp < shDepth ? sh[sp * blockDim.x] : gl[(size_t)(sp - shDepth) * stride];
     }
+    __device__ __forceinline__ uint32_t top() const {
+        const uint32_t i = sp - 1;
+        return i < shDepth ? sh[i * blockDim.x] : gl[(size_t)(i - shDepth) * stride];
+    }
 };
 
 // Per-ray work counts (only with COUNT): nodes, triangles, customs, instances, FP64 tests.
@@ -498,6 +502,82 @@ __device__ __forceinline__ void beginRay(const TraceParams& P, Stack& st, RaySta
     st.sp = 0;
 }
 
+// Moves the ray into instance R (a top-level leaf): the ray in R's object space, R's
+// bottom level as the current level, and a marker on the stack that brings the ray
+// back to the top level when R's traversal is done. False when nothing was entered.
+template <bool ANY, bool COUNT>
+__device__ __forceinline__ bool enterInstance(const TraceParams& P, Stack& st, RayState& s, const InstanceRecord* R,
+                                              Visits* vis) {
+    const uint32_t bits = R->typeBits;
+    if (bits & kInstEmpty) return false;
+    if (!st.push(kSentinel)) {
+        latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+        return false;
+    }
+    if (COUNT) ++vis->insts;
+    instanceLevel(s.L, R, P.fwd32, s.wo, s.wd, s.wid, s.tmin, (ANY || !s.found) ? s.tmax : s.best.t);
+    s.nodes = R->nodes;
+    s.leaves = R->leaves;
+    s.primType = instPrimType(bits);
+    s.geomType = instGeomType(bits);
+    s.instId = R->instanceID;
+    s.inBlas = true;
+    s.next = 0;
+    return true;
+}
+
+// Tests leaf k of the current level against the ray (closest hit: only nearer than
+// the best so far). Returns true when it is a hit; s.best then holds it.
+template <bool ANY, bool SCENE, bool COUNT>
+__device__ __forceinline__ bool testLeaf(const TraceParams& P, RayState& s, uint32_t k, Visits* vis) {
+    const bool strict = s.found && !ANY;
+    const float cur = (ANY || !s.found) ? s.tmax : s.best.t;
+    float t = 0.f, u = 0.f, v = 0.f;
+    uint32_t prim;
+    int res = 0;
+    const float4* rec;
+    bool sphere = false;
+    if (s.primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
+        rec = reinterpret_cast<const float4*>(s.leaves) + 3 * (size_t)k;
+        const float4 a = __ldg(rec), b = __ldg(rec + 1), e = __ldg(rec + 2);
+        prim = __float_as_uint(a.w);
+        res = triangleTest(s.L, f3(a), f3(b), f3(e), b.w, e.w, s.tmin, cur, strict, t, u, v);
+        if (COUNT) ++vis->tris;
+        if (res == 2) {
+            if (COUNT) ++vis->fp64;
+            const float4 r = decide64(P.inv64, SCENE, s.instId, s.wo, s.wd, rec, false, s.tmin, cur, strict);
+            res = r.w != 0.f ? 1 : 0;
+            t = r.x, u = r.y, v = r.z;
+        }
+    } else {
+        prim = __ldg(reinterpret_cast<const uint32_t*>(s.leaves) + k);
+        rec = nullptr;
+        if (P.table && s.geomType < P.numGeomTypes) {
+            const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + s.geomType];
+            if (fe.func == GRT_INTERSECT_SPHERE) {
+                rec = reinterpret_cast<const float4*>(fe.data) + prim;
+                sphere = true;
+                const float4 sp = __ldg(rec);
+                res = sphereTest(s.L, sp, s.tmin, cur, strict, t);
+                if (COUNT) ++vis->customs;
+                if (res == 2) {
+                    if (COUNT) ++vis->fp64;
+                    const float4 r =
+                        decide64(P.inv64, SCENE, s.instId, s.wo, s.wd, rec, true, s.tmin, cur, strict);
+                    res = r.w != 0.f ? 1 : 0;
+                    t = r.x, u = r.y, v = r.z;
+                }
+            }
+        }
+    }
+    if (res == 1) {
+        s.best = Hit{s.instId, prim, t, u, v};
+        s.found = true;
+        return true;
+    }
+    return false;
+}
+
 // One traversal step: a node visit (with its leaf tests), an instance entry or an
 // instance exit. Returns true once the ray is finished (s.best is then final).
 template <bool ANY, bool SCENE, bool COUNT>
@@ -514,23 +594,9 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
         }
     }
     if (SCENE && !s.inBlas && (s.next & kLeafBit)) {  // enter an instance
-        const InstanceRecord* R = reinterpret_cast<const InstanceRecord*>(P.target.leaves) + (s.next & ~kLeafBit);
-        const uint32_t bits = R->typeBits;
+        const uint32_t leaf = s.next & ~kLeafBit;
         s.next = kNone;
-        if (bits & kInstEmpty) return false;
-        if (!st.push(kSentinel)) {
-            latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
-            return false;
-        }
-        if (COUNT) ++vis->insts;
-        instanceLevel(s.L, R, P.fwd32, s.wo, s.wd, s.wid, s.tmin, (ANY || !s.found) ? s.tmax : s.best.t);
-        s.nodes = R->nodes;
-        s.leaves = R->leaves;
-        s.primType = instPrimType(bits);
-        s.geomType = instGeomType(bits);
-        s.instId = R->instanceID;
-        s.inBlas = true;
-        s.next = 0;
+        enterInstance<ANY, COUNT>(P, st, s, reinterpret_cast<const InstanceRecord*>(P.target.leaves) + leaf, vis);
         return false;
     }
     if (++s.steps > P.maxSteps) {
@@ -553,52 +619,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
             const bool h = side ? h1 : h0;
             const uint32_t c = side ? c1 : c0;
             if (!h || !(c & kLeafBit)) continue;
-            const uint32_t k = c & ~kLeafBit;
-            const bool strict = s.found && !ANY;
-            const float cur = (ANY || !s.found) ? s.tmax : s.best.t;
-            float t = 0.f, u = 0.f, v = 0.f;
-            uint32_t prim;
-            int res = 0;
-            const float4* rec;
-            bool sphere = false;
-            if (s.primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
-                rec = reinterpret_cast<const float4*>(s.leaves) + 3 * (size_t)k;
-                const float4 a = __ldg(rec), b = __ldg(rec + 1), e = __ldg(rec + 2);
-                prim = __float_as_uint(a.w);
-                res = triangleTest(s.L, f3(a), f3(b), f3(e), b.w, e.w, s.tmin, cur, strict, t, u, v);
-                if (COUNT) ++vis->tris;
-                if (res == 2) {
-                    if (COUNT) ++vis->fp64;
-                    const float4 r = decide64(P.inv64, SCENE, s.instId, s.wo, s.wd, rec, false, s.tmin, cur, strict);
-                    res = r.w != 0.f ? 1 : 0;
-                    t = r.x, u = r.y, v = r.z;
-                }
-            } else {
-                prim = __ldg(reinterpret_cast<const uint32_t*>(s.leaves) + k);
-                rec = nullptr;
-                if (P.table && s.geomType < P.numGeomTypes) {
-                    const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + s.geomType];
-                    if (fe.func == GRT_INTERSECT_SPHERE) {
-                        rec = reinterpret_cast<const float4*>(fe.data) + prim;
-                        sphere = true;
-                        const float4 sp = __ldg(rec);
-                        res = sphereTest(s.L, sp, s.tmin, cur, strict, t);
-                        if (COUNT) ++vis->customs;
-                        if (res == 2) {
-                            if (COUNT) ++vis->fp64;
-                            const float4 r =
-                                decide64(P.inv64, SCENE, s.instId, s.wo, s.wd, rec, true, s.tmin, cur, strict);
-                            res = r.w != 0.f ? 1 : 0;
-                            t = r.x, u = r.y, v = r.z;
-                        }
-                    }
-                }
-            }
-            if (res == 1) {
-                s.best = Hit{s.instId, prim, t, u, v};
-                s.found = true;
-                if (ANY) return true;
-            }
+            if (testLeaf<ANY, SCENE, COUNT>(P, s, c & ~kLeafBit, vis) && ANY) return true;
         }
         if (c0 & kLeafBit) h0 = false;
         if (c1 & kLeafBit) h1 = false;
@@ -697,16 +718,11 @@ __device__ __forceinline__ float3 aoDirection(const AoFrame& F, uint64_t seed, u
     return F.tg * x + F.bt * z + F.n * y;
 }
 
-// Persistent refill loop shared by the query kernels (warp-level ray compaction):
-// each lane owns one work item and advances its ray one traversal step per iteration;
-// when the warp's live lanes drop to P.refillBelow or fewer, the idle lanes take fresh
-// items from the global queue with one atomic per warp, so short rays do not leave
-// lanes idle while long ones finish. Src supplies the items:
-//   count()             number of items (may be read from device memory)
-//   begin(i, P, st, s)  set up item i's ray in s; false if the item has no ray
-//   finish(i, s)        consume item i's result s.best
+// Refill loop with one traversal step per lane per iteration (node visits test their
+// leaves at once). Used for any-hit queries on a single geometry (shadow rays), which
+// stop at their first hit and so gain nothing from queueing leaves.
 template <bool ANY, bool SCENE, bool COUNT, class Src>
-__device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src& src) {
+__device__ __forceinline__ void refillLoopPerRay(const TraceParams& P, Stack& st, Src& src) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t ltMask = (1u << lane) - 1u;
     const unsigned long long total = src.count();
@@ -733,6 +749,194 @@ __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src&
         }
         if (live == 0) break;
         if (item != kNone && stepRay<ANY, SCENE, COUNT>(P, st, s, &v)) {
+            src.finish(item, s);
+            if (COUNT) flushVisits(P.stats, v);
+            item = kNone;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- phased warp traversal
+// What a lane does next. NODE: visit s.next; ENTER: enter the instance at top-level
+// leaf s.next; FLUSH: test its pending leaves before anything else (its queue is too
+// full for another node visit, or its ray is about to leave the current instance or
+// to finish); DONE: the ray is finished.
+enum : uint32_t { kStNode = 0, kStEnter = 1, kStFlush = 2, kStDone = 3 };
+
+// Leaves of the current bottom level whose boxes the ray hit, waiting to be tested (at
+// most 4, held in registers).
+struct Pending {
+    uint32_t k0, k1, k2, k3, n;
+    __device__ __forceinline__ void add(uint32_t k) {
+        if (n == 0) k0 = k;
+        else if (n == 1) k1 = k;
+        else if (n == 2) k2 = k;
+        else k3 = k;
+        ++n;
+    }
+    __device__ __forceinline__ uint32_t at(uint32_t i) const { return i == 0 ? k0 : i == 1 ? k1 : i == 2 ? k2 : k3; }
+};
+
+// Node visit that queues hit leaf children instead of testing them (inner children
+// and top-level leaves go on as in stepRay). Requires q.n <= 2.
+template <bool ANY, bool SCENE, bool COUNT>
+__device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RayState& s, Pending& q, Visits* vis) {
+    if (++s.steps > P.maxSteps) {
+        latchError(P.error, GRT_ERROR_STEP_LIMIT);
+        s.next = kNone;
+        st.sp = 0;
+        q.n = 0;
+        return;
+    }
+    if (COUNT) ++vis->nodes;
+    const float4* N = s.nodes + 4 * (size_t)s.next;
+    const float4 nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2), nc = __ldg(N + 3);
+    bool h0, h1;
+    float tn0, tn1;
+    slab2(nx, ny, nz, s.L, localLo(s.L, s.tmin), localHi(s.L, (ANY || !s.found) ? s.tmax : s.best.t), h0, h1, tn0,
+          tn1);
+    const uint32_t c0 = __float_as_uint(nc.x), c1 = __float_as_uint(nc.y);
+    if (c1 == c0) h1 = false;  // a one-primitive level stores its leaf twice
+    s.next = kNone;
+    if (s.inBlas) {
+        if (h0 && (c0 & kLeafBit)) q.add(c0 & ~kLeafBit), h0 = false;
+        if (h1 && (c1 & kLeafBit)) q.add(c1 & ~kLeafBit), h1 = false;
+    }
+    if (h0 && h1) {
+        const bool swap = tn1 < tn0;
+        const uint32_t nearC = swap ? c1 : c0, farC = swap ? c0 : c1;
+        if (!st.push(farC)) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+        s.next = nearC;
+    } else if (h0) {
+        s.next = c0;
+    } else if (h1) {
+        s.next = c1;
+    }
+}
+
+// The lane's next action after its last one: pops the stack (leaving an instance
+// when its marker comes up) until there is a node to visit or an instance to enter,
+// but not past a marker or the end while leaves of the level are still pending.
+template <bool SCENE>
+__device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, RayState& s, const Pending& q) {
+    for (;;) {
+        if (s.next != kNone) {
+            if (SCENE && !s.inBlas && (s.next & kLeafBit)) return kStEnter;
+            return q.n > 2 ? kStFlush : kStNode;
+        }
+        if (st.sp == 0) return q.n ? kStFlush : kStDone;
+        if (SCENE && st.top() == kSentinel) {
+            if (q.n) return kStFlush;
+            st.pop();
+            exactLevel(s.L, s.wo, s.wd);  // back to the top level
+            s.nodes = P.target.nodes;
+            s.inBlas = false;
+            continue;
+        }
+        s.next = st.pop();
+    }
+}
+
+// Persistent refill loop shared by the query kernels: each lane owns one work item
+// (a ray). Every iteration the whole warp takes ONE kind of step, so that the node,
+// leaf and instance-entry code paths do not run one after another in a warp:
+//   LEAF  - lanes with pending leaves test them (when some lane must flush, or when at
+//           least half the working lanes have leaves queued);
+//   ENTER - lanes at a top-level leaf enter the instance (when at least a quarter of
+//           the working lanes wait to, or no lane has a node to visit);
+//   NODE  - lanes with a node to visit visit it, queueing the leaves they hit.
+// Once the queue is exhausted and at most two lanes still work, each finishes its ray
+// in a tight loop of single steps. (Speculative, leaf-deferring traversal after Aila
+// and Laine, "Understanding the Efficiency of Ray Traversal on GPUs", HPG 2009.) When
+// the warp's working lanes drop
+// to P.refillBelow or fewer, idle lanes take fresh items from the global queue with one
+// atomic per warp. Src supplies the items:
+//   count()             number of items (may be read from device memory)
+//   begin(i, P, st, s)  set up item i's ray in s; false if the item has no ray
+//   finish(i, s)        consume item i's result s.best
+template <bool ANY, bool SCENE, bool COUNT, class Src>
+__device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src& src) {
+    if constexpr (ANY && !SCENE) {
+        refillLoopPerRay<ANY, SCENE, COUNT>(P, st, src);
+        return;
+    }
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t ltMask = (1u << lane) - 1u;
+    const unsigned long long total = src.count();
+    RayState s;
+    Visits v;
+    Pending q;
+    q.n = 0;
+    uint32_t item = kNone, state = kStDone;
+    bool exhausted = false;
+    for (;;) {
+        uint32_t live = __ballot_sync(0xffffffffu, item != kNone);
+        while (!exhausted && (uint32_t)__popc(live) <= P.refillBelow) {
+            const uint32_t idle = ~live;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)__popc(idle));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + __popc(idle) >= total) exhausted = true;
+            if (item == kNone) {
+                const unsigned long long mine = base + __popc(idle & ltMask);
+                if (mine < total && src.begin((uint32_t)mine, P, st, s)) {
+                    item = (uint32_t)mine;
+                    if (COUNT) v = Visits{};
+                    q.n = 0;
+                    state = nextState<SCENE>(P, st, s, q);
+                    if (state == kStDone) {  // nothing to traverse (an empty target)
+                        src.finish(item, s);
+                        if (COUNT) flushVisits(P.stats, v);
+                        item = kNone;
+                    }
+                }
+            }
+            live = __ballot_sync(0xffffffffu, item != kNone);
+        }
+        if (live == 0) break;
+        const bool on = item != kNone;
+        const uint32_t flush = __ballot_sync(0xffffffffu, on && state == kStFlush);
+        const uint32_t queued = __ballot_sync(0xffffffffu, on && q.n > 0);
+        const uint32_t enter = __ballot_sync(0xffffffffu, on && state == kStEnter);
+        const uint32_t node = __ballot_sync(0xffffffffu, on && state == kStNode);
+        const uint32_t working = (uint32_t)__popc(live);
+        // the last rays of the warp (queue exhausted, at most two lanes working) run to
+        // their end without votes, testing their leaves as soon as they are found
+        const bool tail = exhausted && working <= 2u;
+        uint32_t phase;
+        if (flush || 2u * (uint32_t)__popc(queued) >= working)
+            phase = kStFlush;
+        else if (enter && (4u * (uint32_t)__popc(enter) >= working || !node))
+            phase = kStEnter;
+        else
+            phase = kStNode;
+        if (!on) continue;
+        do {
+        if (tail) phase = q.n ? kStFlush : state;
+        bool acted = false;
+        if (phase == kStFlush) {
+            if (q.n) {
+                acted = true;
+                const uint32_t n = q.n;
+                q.n = 0;
+                for (uint32_t i = 0; i < n; ++i)
+                    if (testLeaf<ANY, SCENE, COUNT>(P, s, q.at(i), &v) && ANY) break;
+            }
+        } else if (phase == kStEnter) {
+            if (state == kStEnter) {
+                acted = true;
+                const uint32_t leaf = s.next & ~kLeafBit;
+                s.next = kNone;
+                enterInstance<ANY, COUNT>(P, st, s, reinterpret_cast<const InstanceRecord*>(P.target.leaves) + leaf,
+                                          &v);
+            }
+        } else if (state == kStNode) {
+            acted = true;
+            visitNode<ANY, SCENE, COUNT>(P, st, s, q, &v);
+        }
+        if (acted) state = (ANY && s.found) ? kStDone : nextState<SCENE>(P, st, s, q);
+        } while (tail && state != kStDone);
+        if (state == kStDone) {
             src.finish(item, s);
             if (COUNT) flushVisits(P.stats, v);
             item = kNone;
