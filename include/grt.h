@@ -280,6 +280,33 @@ grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom
 grtError grtTraceAnyHit(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
                         grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream);
 
+/* ---------------------------------------------------------------- device-side queries (Sec. 7.6) */
+/* Everything a user CUDA kernel needs to trace rays itself through grt_device.cuh (the
+ * paper's device traversal object, Sec. 7.6): device pointers of the target's arrays,
+ * of a scene's instance frames and of the function table. Plain data: pass it to a
+ * kernel by value. Valid while the target, the table and the context live and the
+ * target is not rebuilt with a different primitive count. */
+typedef struct grtDeviceTarget {
+    const void* nodes;            /* the target's nodes */
+    const void* leaves;           /* triangle records / primitive IDs / instance records */
+    const uint32_t* primToLeaf;   /* primitive (instance) ID -> sorted leaf position */
+    const void* frames64;         /* scenes: FP64 inverse frame per instance ID, else NULL */
+    const void* frames32;         /* scenes: float32 frame rows per instance ID, else NULL */
+    const void* funcTable;        /* function-table entries (grtSetFuncTable), or NULL */
+    uint32_t* deviceError;        /* the context's device error word (grtGetLastDeviceError) */
+    uint32_t primType;            /* grtPrimitiveType of a geometry; 2 for a scene */
+    uint32_t geomType;
+    uint32_t primCount;
+    uint32_t numGeomTypes;        /* of the function table */
+    uint32_t rayType;             /* function-table row used by the queries */
+} grtDeviceTarget;
+
+/* Fills *out for exactly one of scene / geom (built), with an optional function table
+ * and the ray type selecting its row. Errors: GRT_ERROR_INVALID_PARAMETER,
+ * GRT_ERROR_NOT_BUILT. */
+grtError grtGetDeviceTarget(grtContext ctx, grtScene scene, grtGeometry geom, grtFuncTable table, uint32_t rayType,
+                            grtDeviceTarget* out);
+
 /* ---------------------------------------------------------------- ray generation (Sec. 3.2, 4) */
 /* Pinhole camera (Sec. 3.2): lens at origin, film at distance 1 along
  * normalize(up x right), spanning +-right and +-up. */

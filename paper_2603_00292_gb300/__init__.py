@@ -99,6 +99,13 @@ class grtBvhInfo(ctypes.Structure):
                 ("mortonBits", ctypes.c_uint32)]
 
 
+class grtDeviceTarget(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("primToLeaf", ctypes.c_void_p),
+                ("frames64", ctypes.c_void_p), ("frames32", ctypes.c_void_p), ("funcTable", ctypes.c_void_p),
+                ("deviceError", ctypes.c_void_p), ("primType", ctypes.c_uint32), ("geomType", ctypes.c_uint32),
+                ("primCount", ctypes.c_uint32), ("numGeomTypes", ctypes.c_uint32), ("rayType", ctypes.c_uint32)]
+
+
 class grtBatchScene(ctypes.Structure):
     _fields_ = [("geometry", ctypes.c_void_p), ("input", grtGeometryBuildInput), ("rays", ctypes.c_void_p),
                 ("rayCount", ctypes.c_uint32), ("hits", ctypes.c_void_p)]
@@ -170,6 +177,7 @@ _SIGS = {
     "grtGetTraceStatistics": [_P, _P, ctypes.c_void_p],
     "grtSortTemporaryBufferSize": [_U32, _U32, ctypes.POINTER(ctypes.c_size_t)],
     "grtSortPairs": [_P, _P, _P, _U32, _U32, _U32, _P, _P],
+    "grtGetDeviceTarget": [_P, _P, _P, _P, _U32, ctypes.POINTER(grtDeviceTarget)],
     "grtCreateBatch": [_P, ctypes.POINTER(grtBatchScene), _U32, ctypes.POINTER(grtBatchOptions), ctypes.POINTER(_P)],
     "grtBatchBuildTrace": [_P, _P, _P],
     "grtGetBatchInfo": [_P, _P, ctypes.POINTER(grtBatchInfo)],
@@ -487,3 +495,11 @@ def grtGetBatchProfile(ctx, batch):
     dt = np.dtype([("scene", "<u4"), ("phase", "<u4"), ("chunk", "<u4"), ("sm", "<u4"), ("startNs", "<u8"),
                    ("readyNs", "<u8"), ("endNs", "<u8")])
     return np.frombuffer(bytes(recs), dtype=dt, count=count.value).copy()
+
+
+def grtGetDeviceTarget(ctx, scene=None, geom=None, table=None, ray_type: int = 0) -> grtDeviceTarget:
+    """The plain-data description of a built scene or geometry that user kernels pass to
+    grt_device.cuh's traceClosest / traceAnyHit."""
+    out = grtDeviceTarget()
+    check(lib().grtGetDeviceTarget(ctx, scene, geom, table, ray_type, ctypes.byref(out)), "grtGetDeviceTarget")
+    return out

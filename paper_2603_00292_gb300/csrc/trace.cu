@@ -672,6 +672,33 @@ grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* optio
     return GRT_SUCCESS;
 }
 
+grtError grtGetDeviceTarget(grtContext ctx, grtScene scene, grtGeometry geom, grtFuncTable table, uint32_t rayType,
+                            grtDeviceTarget* out) {
+    if (!ctx || !out || (scene != nullptr) == (geom != nullptr)) return GRT_ERROR_INVALID_PARAMETER;
+    BvhObject* o = findBvh(scene ? (const void*)scene : (const void*)geom);
+    if (!o || (scene != nullptr) != (o->primType == kPrimScene)) return GRT_ERROR_INVALID_PARAMETER;
+    if (!o->built) return GRT_ERROR_NOT_BUILT;
+    grtDeviceTarget t{};
+    t.nodes = o->nodes;
+    t.leaves = o->leaves;
+    t.primToLeaf = o->primToLeaf;
+    t.frames64 = o->inv64;
+    t.frames32 = o->fwd32;
+    t.deviceError = &workspace(asContext(ctx))->error;
+    t.primType = o->primType;
+    t.geomType = o->geomType;
+    t.primCount = o->primCount;
+    t.rayType = rayType;
+    if (table) {
+        FuncTableObject* f = findFuncTable(table);
+        if (!f || rayType >= f->numRayTypes) return GRT_ERROR_INVALID_PARAMETER;
+        t.funcTable = f->dEntries;
+        t.numGeomTypes = f->numGeomTypes;
+    }
+    *out = t;
+    return GRT_SUCCESS;
+}
+
 grtError grtTraceClosest(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
                          grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream) {
     return launchTrace<false>(ctx, scene, geom, rays, rayCount, hits, table, options, stream);

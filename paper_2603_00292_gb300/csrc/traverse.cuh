@@ -477,6 +477,7 @@ struct RayState {
     Hit best;
     uint32_t primType, geomType, instId;
     uint32_t steps, next;
+    float lo, hi;  // [tmin, limit] on the current level (limit = tmax, or the best t so far)
     bool inBlas, found;
 };
 
@@ -499,6 +500,8 @@ __device__ __forceinline__ void beginRay(const TraceParams& P, Stack& st, RaySta
     s.found = false;
     s.steps = 0;
     s.next = P.target.empty ? kNone : 0u;
+    s.lo = tmin;  // the world level: local = world parameters
+    s.hi = tmax;
     st.sp = 0;
 }
 
@@ -515,7 +518,10 @@ __device__ __forceinline__ bool enterInstance(const TraceParams& P, Stack& st, R
         return false;
     }
     if (COUNT) ++vis->insts;
-    instanceLevel(s.L, R, P.fwd32, s.wo, s.wd, s.wid, s.tmin, (ANY || !s.found) ? s.tmax : s.best.t);
+    const float lim = (ANY || !s.found) ? s.tmax : s.best.t;
+    instanceLevel(s.L, R, P.fwd32, s.wo, s.wd, s.wid, s.tmin, lim);
+    s.lo = localLo(s.L, s.tmin);
+    s.hi = localHi(s.L, lim);
     s.nodes = R->nodes;
     s.leaves = R->leaves;
     s.primType = instPrimType(bits);
@@ -573,6 +579,7 @@ __device__ __forceinline__ bool testLeaf(const TraceParams& P, RayState& s, uint
     if (res == 1) {
         s.best = Hit{s.instId, prim, t, u, v};
         s.found = true;
+        if (!ANY) s.hi = localHi(s.L, t);
         return true;
     }
     return false;
@@ -587,6 +594,8 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
         s.next = st.pop();
         if (SCENE && s.next == kSentinel) {  // back to the top level
             exactLevel(s.L, s.wo, s.wd);
+            s.lo = s.tmin;
+            s.hi = (ANY || !s.found) ? s.tmax : s.best.t;
             s.nodes = P.target.nodes;
             s.inBlas = false;
             s.next = kNone;
@@ -608,8 +617,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
     const float4 nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2), nc = __ldg(N + 3);
     bool h0, h1;
     float tn0, tn1;
-    slab2(nx, ny, nz, s.L, localLo(s.L, s.tmin), localHi(s.L, (ANY || !s.found) ? s.tmax : s.best.t), h0, h1, tn0,
-          tn1);
+    slab2(nx, ny, nz, s.L, s.lo, s.hi, h0, h1, tn0, tn1);
     const uint32_t c0 = __float_as_uint(nc.x), c1 = __float_as_uint(nc.y);
     if (c1 == c0) h1 = false;  // a one-primitive level stores its leaf twice
     s.next = kNone;
@@ -793,8 +801,7 @@ __device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RaySt
     const float4 nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2), nc = __ldg(N + 3);
     bool h0, h1;
     float tn0, tn1;
-    slab2(nx, ny, nz, s.L, localLo(s.L, s.tmin), localHi(s.L, (ANY || !s.found) ? s.tmax : s.best.t), h0, h1, tn0,
-          tn1);
+    slab2(nx, ny, nz, s.L, s.lo, s.hi, h0, h1, tn0, tn1);
     const uint32_t c0 = __float_as_uint(nc.x), c1 = __float_as_uint(nc.y);
     if (c1 == c0) h1 = false;  // a one-primitive level stores its leaf twice
     s.next = kNone;
@@ -817,7 +824,7 @@ __device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RaySt
 // The lane's next action after its last one: pops the stack (leaving an instance
 // when its marker comes up) until there is a node to visit or an instance to enter,
 // but not past a marker or the end while leaves of the level are still pending.
-template <bool SCENE>
+template <bool ANY, bool SCENE>
 __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, RayState& s, const Pending& q) {
     for (;;) {
         if (s.next != kNone) {
@@ -829,6 +836,8 @@ __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, R
             if (q.n) return kStFlush;
             st.pop();
             exactLevel(s.L, s.wo, s.wd);  // back to the top level
+            s.lo = s.tmin;
+            s.hi = (ANY || !s.found) ? s.tmax : s.best.t;
             s.nodes = P.target.nodes;
             s.inBlas = false;
             continue;
@@ -883,7 +892,7 @@ __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src&
                     item = (uint32_t)mine;
                     if (COUNT) v = Visits{};
                     q.n = 0;
-                    state = nextState<SCENE>(P, st, s, q);
+                    state = nextState<ANY, SCENE>(P, st, s, q);
                     if (state == kStDone) {  // nothing to traverse (an empty target)
                         src.finish(item, s);
                         if (COUNT) flushVisits(P.stats, v);
@@ -895,10 +904,10 @@ __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src&
         }
         if (live == 0) break;
         const bool on = item != kNone;
-        const uint32_t flush = __ballot_sync(0xffffffffu, on && state == kStFlush);
+        const uint32_t b0 = __ballot_sync(0xffffffffu, on && (state & 1u));  // enter (working lanes)
+        const uint32_t b1 = __ballot_sync(0xffffffffu, on && (state & 2u));  // flush
         const uint32_t queued = __ballot_sync(0xffffffffu, on && q.n > 0);
-        const uint32_t enter = __ballot_sync(0xffffffffu, on && state == kStEnter);
-        const uint32_t node = __ballot_sync(0xffffffffu, on && state == kStNode);
+        const uint32_t flush = b1, enter = b0, node = live & ~(b0 | b1);
         const uint32_t working = (uint32_t)__popc(live);
         // the last rays of the warp (queue exhausted, at most two lanes working) run to
         // their end without votes, testing their leaves as soon as they are found
@@ -934,7 +943,7 @@ __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src&
             acted = true;
             visitNode<ANY, SCENE, COUNT>(P, st, s, q, &v);
         }
-        if (acted) state = (ANY && s.found) ? kStDone : nextState<SCENE>(P, st, s, q);
+        if (acted) state = (ANY && s.found) ? kStDone : nextState<ANY, SCENE>(P, st, s, q);
         } while (tail && state != kStDone);
         if (state == kStDone) {
             src.finish(item, s);
@@ -958,17 +967,16 @@ struct RayBufferSource {
     __device__ void finish(uint32_t i, const RayState& s) const { storeHit(P->hits, i, s.best); }
 };
 
-// Ray r's closest hit: t, u, v recomputed in FP64 (the hit record is updated in place).
-__device__ __forceinline__ void refineHit(const TraceParams& P, uint32_t r) {
+// Hit h of the ray (wo, wd, [tmin, tmax]): its t, u, v recomputed in FP64 (kept when
+// the FP64 test does not confirm the hit).
+__device__ __forceinline__ void refineOne(const TraceParams& P, float3 wo, float3 wd, float tmin, float tmax, Hit& h) {
+    if (h.prim == kInvalid) return;
     const bool scene = P.target.primType == kPrimScene;
-    uint32_t* h = P.hits + 5 * (size_t)r;
-    const uint32_t inst = h[0], prim = h[1];
-    if (prim == kInvalid) return;
     uint32_t primType, geomType;
     const void* leaves;
     const uint32_t* toLeaf;
     if (scene) {
-        const InstanceRecord* R = P.sceneLeaves + P.scenePrimToLeaf[inst];
+        const InstanceRecord* R = P.sceneLeaves + P.scenePrimToLeaf[h.inst];
         primType = instPrimType(R->typeBits);
         geomType = instGeomType(R->typeBits);
         leaves = R->leaves;
@@ -982,22 +990,29 @@ __device__ __forceinline__ void refineHit(const TraceParams& P, uint32_t r) {
     const float4* rec = nullptr;
     bool sphere = false;
     if (primType == GRT_PRIMITIVE_TRIANGLE_MESH) {
-        rec = reinterpret_cast<const float4*>(leaves) + 3 * (size_t)toLeaf[prim];
+        rec = reinterpret_cast<const float4*>(leaves) + 3 * (size_t)toLeaf[h.prim];
     } else if (P.table && geomType < P.numGeomTypes) {
         const FuncEntry fe = P.table[(size_t)P.rayType * P.numGeomTypes + geomType];
         if (fe.func == GRT_INTERSECT_SPHERE) {
-            rec = reinterpret_cast<const float4*>(fe.data) + prim;
+            rec = reinterpret_cast<const float4*>(fe.data) + h.prim;
             sphere = true;
         }
     }
     if (!rec) return;
+    const float4 res = refine64(P.inv64, scene, h.inst, wo, wd, rec, sphere, tmin, tmax);
+    if (res.w != 0.f) h.t = res.x, h.u = res.y, h.v = res.z;
+}
+
+// Ray r's closest hit: t, u, v recomputed in FP64 (the hit record is updated in place).
+__device__ __forceinline__ void refineHit(const TraceParams& P, uint32_t r) {
+    uint32_t* p = P.hits + 5 * (size_t)r;
+    Hit h{p[0], p[1], __uint_as_float(p[2]), __uint_as_float(p[3]), __uint_as_float(p[4])};
+    if (h.prim == kInvalid) return;
     const float4 a = P.rays[2 * (size_t)r], b = P.rays[2 * (size_t)r + 1];
-    const float4 res = refine64(P.inv64, scene, inst, f3(a), f3(b), rec, sphere, a.w, b.w);
-    if (res.w != 0.f) {
-        h[2] = __float_as_uint(res.x);
-        h[3] = __float_as_uint(res.y);
-        h[4] = __float_as_uint(res.z);
-    }
+    refineOne(P, f3(a), f3(b), a.w, b.w, h);
+    p[2] = __float_as_uint(h.t);
+    p[3] = __float_as_uint(h.u);
+    p[4] = __float_as_uint(h.v);
 }
 
 }  // namespace grt

@@ -116,6 +116,18 @@ def test_million_spheres_closest_and_any_hit(gpu):
     rep.check()
     assert rep.matched > 100_000
     compare_any(hits_to_numpy(ha)[1], ref, S, rays, extent=100.0, has_spheres=True).check()
+    # with tmax = +inf nearly every ray is occluded (mean free path ~2.9 in a box of
+    # 100); at tmax = 2.9 about 70% are, so occlusion parity is not trivially met
+    short = rays.copy()
+    short[:, 7] = 2.9
+    hs = new_hits(n)
+    grt.grtTraceAnyHit(gpu.handle, None, g.handle, device_tensor(short), n, hs, table.handle)
+    torch.cuda.synchronize()
+    _no_device_error(gpu)
+    ref_short = S.trace(short, any_hit=True)
+    occluded = (ref_short.prim != NONE).mean()
+    assert 0.3 < occluded < 0.85, occluded
+    compare_any(hits_to_numpy(hs)[1], ref_short, S, short, extent=100.0, has_spheres=True).check()
 
 
 def _soup_worker(i):
@@ -128,7 +140,8 @@ def _soup_worker(i):
 def test_batched_soups_full_size(gpu):
     """The 256-soup batch (67.8 M triangles, 51.7 M rays) in one graph-captured launch:
     hit records identical to 256 per-scene build+trace calls, BVHs of the smallest and
-    the largest scene bit-exact, and the oracle on sampled rays of four scenes."""
+    the largest scene bit-exact, and the oracle on every scene (all rays of 16 seeded
+    scenes, sampled rays elsewhere)."""
     import multiprocessing as mp
 
     with mp.get_context("spawn").Pool(16) as pool:
@@ -167,13 +180,23 @@ def test_batched_soups_full_size(gpu):
         assert np.array_equal(read_device(a.nodes, 64 * a.nodeCount, np.uint32),
                               read_device(b.nodes, 64 * b.nodeCount, np.uint32))
         assert np.array_equal(read_device(a.leaves, 48 * n, np.uint32), read_device(b.leaves, 48 * n, np.uint32))
+    # the oracle: every ray of 16 seeded scenes (plus the four picked above, their rays
+    # sampled when above 100,000) and 1,024 sampled rays of every other scene
     rng = np.random.default_rng(SEED)
-    for k in picks:
+    full = set(int(k) for k in rng.choice(256, size=16, replace=False))
+    checked = 0
+    for k in range(256):
         v, i, r, extent = soups[k]
-        take = np.sort(rng.choice(r.shape[0], size=min(r.shape[0], 4000), replace=False))
+        if k in full or k in picks:
+            cap = r.shape[0] if k in full and r.shape[0] <= 100_000 else 100_000
+        else:
+            cap = 1024
+        take = np.arange(r.shape[0]) if cap >= r.shape[0] else np.sort(rng.choice(r.shape[0], cap, replace=False))
         S = oracle.Scene()
         S.add_instance(S.add_mesh(v, i))
         S.build()
         ref = S.trace(r[take])
         got = tuple(a[take] for a in hits_to_numpy(scenes[k][2]))
         compare_closest(got, ref, S, r[take], extent=extent).check()
+        checked += take.size
+    assert checked > 500_000
