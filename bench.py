@@ -81,6 +81,26 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(values, dist=None, device: str = "cuda"):
+    """Element-wise maximum of per-rank timings over all ranks (each rank runs its own
+    replica; the job takes as long as its slowest rank). Without a process group the
+    values are returned as they are."""
+    values = [float(v) for v in values]
+    if dist is None:
+        return values
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units per second of the whole job: every rank processed units_per_rank (weak
+    scaling) in at most `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def workload():
     import scenegen
 
@@ -254,11 +274,8 @@ def run_grt(args, rank, world, local):
     clk = clocks.stop()
     launches = grt.grtGetLaunchCount() - launches0
     total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * rays_per_step * args.steps / total_s / 1e6
+    (total_s,) = max_over_ranks([total_s], dist)
+    value = job_throughput(rays_per_step * args.steps, world, total_s) / 1e6
 
     # --------------------------------------------------- traversal work per ray (counting pass)
     cnt = grt.trace_options(flags=grt.GRT_TRACE_FLAG_COUNT)
@@ -308,13 +325,10 @@ def run_grt(args, rank, world, local):
         if k >= args.warmup:
             e2e_ms.append(ev["s0"].elapsed_time(ev["s1"]))
     e2e_s = sum(e2e_ms) / 1e3
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    (e2e_s,) = max_over_ranks([e2e_s], dist)
     h2d = vh.numel() * 4 + ih.numel() * 4 + fh.numel() * 4
     d2h = ao_h.numel() * 4 + hits_h.numel() * 4
-    e2e = {"value": round(world * rays_per_step * args.steps / e2e_s / 1e6, 2), "unit": UNIT,
+    e2e = {"value": round(job_throughput(rays_per_step * args.steps, world, e2e_s) / 1e6, 2), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -502,10 +516,7 @@ def run_adjoint(args, rank, world, local):
     clk = clocks.stop()
     assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
     nhit = int((hits[:, 1].view(torch.int32) != -1).sum().item())
-    if dist:
-        t = torch.tensor([fwd_ms, store_ms, rec_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        fwd_ms, store_ms, rec_ms = (float(x) for x in t.tolist())
+    fwd_ms, store_ms, rec_ms = max_over_ranks([fwd_ms, store_ms, rec_ms], dist)
 
     # backward (stored hits): the hit record of every pixel; the ray, visibility byte and
     # dL/dI of each hit pixel; the mesh tables (indices, positions, colours) read and the
@@ -716,10 +727,7 @@ def run_batched(args, rank, world, local):
     assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
     identical = all(torch.equal(a, b) for a, b in zip(hits_b, hits_s))
     batched_ms, seq_ms = statistics.mean(b_ms), statistics.mean(s_ms)
-    if dist:
-        t = torch.tensor([batched_ms, seq_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        batched_ms, seq_ms = (float(x) for x in t.tolist())
+    batched_ms, seq_ms = max_over_ranks([batched_ms, seq_ms], dist)
 
     # algorithmic bytes of one launch: the builds by formula, the traces from a
     # counting pass (nodes and triangles visited per ray) on the per-scene path
