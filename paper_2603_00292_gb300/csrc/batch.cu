@@ -33,42 +33,23 @@
 #include <mutex>
 #include <vector>
 
-#include "lbvh.cuh"
+#include "lbvh_block.cuh"
 #include "traverse.cuh"
 
 namespace grt {
 
 constexpr uint32_t kBatchPhases = 32;
-constexpr int kBatchRadix = 256;
-constexpr int kBatchSortItems = 8;  // keys per thread in a sort tile
-constexpr int kBatchScanItems = 8;
 constexpr unsigned long long kBatchWaitNs = 2000000000ull;  // 2 s per wait
 constexpr uint32_t kBatchWaitSpins = 1u << 25;                // and at most this many polls
 
-struct BatchSceneDev {
-    PrimSource src;
-    uint32_t n;
+// A scene of the batch: its build (BlockBuild) plus its rays and the trace phase.
+struct BatchSceneDev : BlockBuild {
     uint32_t rays;
-    uint32_t bits;        // Morton bits (30 or 63)
     uint32_t small;       // built by one item
-    uint32_t sortChunks;  // chunk items of a radix pass
-    uint32_t passes;      // radix passes
     uint32_t tracePhase;
     uint32_t pad;
     const float4* rayBuf;
     uint32_t* hitBuf;
-    float4* nodes;
-    void* leaves;
-    uint32_t* parents;
-    uint32_t* primToLeaf;
-    BvhHeader* header;
-    uint32_t* bounds;  // 6 ordered-int words
-    float4* centroids;
-    void* keys[2];
-    uint32_t* vals[2];
-    uint32_t* counts;  // kBatchRadix x sortChunks
-    uint32_t* flags;   // fit visit counters
-    uint32_t* error;   // the context's device error word
 };
 
 struct BatchItemDev {
@@ -123,238 +104,6 @@ __device__ void waitPhase(const BatchParams& B, uint32_t scene, uint32_t phase, 
         }
     }
     __threadfence();
-}
-
-// ------------------------------------------------------------------ build phases
-__device__ __forceinline__ void loadBounds(const BatchSceneDev& S, uint32_t b[6]) {
-#pragma unroll
-    for (int a = 0; a < 6; ++a) b[a] = __ldcg(S.bounds + a);
-}
-
-// Centroids of primitives [begin, end), their bounds, and zeroed fit counters.
-__device__ __noinline__ void prepRange(const BatchSceneDev& S, uint32_t begin, uint32_t end) {
-    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
-        float3 v[3];
-        const float3 c = boxCentroid(primBox(S.src, i, v));
-        S.centroids[i] = make_float4(c.x, c.y, c.z, 0.f);
-        mn[0] = fminf(mn[0], c.x), mn[1] = fminf(mn[1], c.y), mn[2] = fminf(mn[2], c.z);
-        mx[0] = fmaxf(mx[0], c.x), mx[1] = fmaxf(mx[1], c.y), mx[2] = fmaxf(mx[2], c.z);
-        if (i + 1 < S.n) S.flags[i] = 0u;
-    }
-    reduceBoxBounds(mn, mx, S.bounds);
-}
-
-// Digit histogram of chunk `chunk` of radix pass `pass` into counts[d * chunks + chunk].
-// Pass 0 computes the Morton codes (and identity values) from the centroids first.
-template <typename K, int BITS>
-__device__ __noinline__ void sortUpsweepChunk(const BatchSceneDev& S, uint32_t chunk, uint32_t pass, uint32_t chunkKeys,
-                                 uint32_t* smem) {
-    const uint32_t warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
-    for (uint32_t d = threadIdx.x; d < warps * kBatchRadix; d += blockDim.x) smem[d] = 0u;
-    __syncthreads();
-    const int shift = 8 * (int)pass;
-    const size_t begin = (size_t)chunk * chunkKeys;
-    const size_t end = min((size_t)S.n, begin + chunkKeys);
-    const K* kin = static_cast<const K*>(S.keys[pass & 1u]);
-    uint32_t b[6];
-    if (pass == 0) loadBounds(S, b);
-    for (size_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
-        K k;
-        if (pass == 0) {
-            k = mortonCode<K, BITS>(__ldcg(S.centroids + i), b);
-            static_cast<K*>(S.keys[0])[i] = k;
-            S.vals[0][i] = (uint32_t)i;
-        } else {
-            k = __ldcg(kin + i);
-        }
-        atomicAdd(&smem[warp * kBatchRadix + ((uint32_t)(k >> shift) & (kBatchRadix - 1))], 1u);
-    }
-    __syncthreads();
-    for (uint32_t d = threadIdx.x; d < kBatchRadix; d += blockDim.x) {
-        uint32_t sum = 0;
-        for (uint32_t w = 0; w < warps; ++w) sum += smem[w * kBatchRadix + d];
-        S.counts[(size_t)d * S.sortChunks + chunk] = sum;
-    }
-}
-
-// Exclusive prefix sum in place over the scene's kBatchRadix x sortChunks histogram
-// (digit-major, so each (digit, chunk) gets its first output position).
-__device__ __noinline__ void sortScanScene(const BatchSceneDev& S, uint32_t* smem) {
-    uint32_t* warpSums = smem;        // 32
-    uint32_t* carry = smem + 32;      // 1
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-    const uint32_t total = kBatchRadix * S.sortChunks;
-    if (threadIdx.x == 0) *carry = 0u;
-    __syncthreads();
-    for (uint32_t base = 0; base < total; base += blockDim.x * kBatchScanItems) {
-        uint32_t v[kBatchScanItems];
-        uint32_t sum = 0;
-        const uint32_t my = base + threadIdx.x * kBatchScanItems;
-#pragma unroll
-        for (int i = 0; i < kBatchScanItems; ++i) {
-            v[i] = (my + i < total) ? __ldcg(S.counts + my + i) : 0u;
-            sum += v[i];
-        }
-        uint32_t incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= (uint32_t)o) incl += t;
-        }
-        if (lane == 31u) warpSums[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t w = lane < warps ? warpSums[lane] : 0u;
-            uint32_t wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= (uint32_t)o) wi += t;
-            }
-            if (lane < warps) warpSums[lane] = wi - w;
-        }
-        __syncthreads();
-        uint32_t run = *carry + warpSums[warp] + (incl - sum);
-#pragma unroll
-        for (int i = 0; i < kBatchScanItems; ++i) {
-            if (my + i < total) S.counts[my + i] = run;
-            run += v[i];
-        }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) *carry = run;
-        __syncthreads();
-    }
-}
-
-// Stable scatter of chunk `chunk` of radix pass `pass`: tiles of blockDim x 16 keys in
-// order; within a tile each warp ranks its 512 keys (match_any per digit) after the
-// warps before it.
-template <typename K>
-__device__ __noinline__ void sortDownsweepChunk(const BatchSceneDev& S, uint32_t chunk, uint32_t pass, uint32_t chunkKeys,
-                                   uint32_t* smem) {
-    const uint32_t warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    uint32_t* warpHist = smem;                        // warps x kBatchRadix
-    uint32_t* digitBase = smem + warps * kBatchRadix;  // kBatchRadix
-    uint32_t* tileTotal = digitBase + kBatchRadix;     // kBatchRadix
-    const uint32_t ltMask = (1u << lane) - 1u;
-    const int shift = 8 * (int)pass;
-    const K* kin = static_cast<const K*>(S.keys[pass & 1u]);
-    const uint32_t* vin = S.vals[pass & 1u];
-    K* kout = static_cast<K*>(S.keys[(pass + 1) & 1u]);
-    uint32_t* vout = S.vals[(pass + 1) & 1u];
-    for (uint32_t d = threadIdx.x; d < kBatchRadix; d += blockDim.x) {
-        digitBase[d] = __ldcg(S.counts + (size_t)d * S.sortChunks + chunk);
-        for (uint32_t w = 0; w < warps; ++w) warpHist[w * kBatchRadix + d] = 0u;
-    }
-    __syncthreads();
-    const size_t begin = (size_t)chunk * chunkKeys;
-    const size_t end = min((size_t)S.n, begin + chunkKeys);
-    const size_t tileKeys = (size_t)blockDim.x * kBatchSortItems;
-    for (size_t tile = begin; tile < end; tile += tileKeys) {
-        const size_t base = tile + (size_t)warp * 32 * kBatchSortItems;
-        K k[kBatchSortItems];
-        uint32_t v[kBatchSortItems], dg[kBatchSortItems], rank[kBatchSortItems];
-#pragma unroll
-        for (int i = 0; i < kBatchSortItems; ++i) {
-            const size_t idx = base + (size_t)i * 32 + lane;
-            const bool ok = idx < end;
-            k[i] = ok ? __ldcg(kin + idx) : (K)0;
-            v[i] = ok ? __ldcg(vin + idx) : 0u;
-            dg[i] = ok ? ((uint32_t)(k[i] >> shift) & (kBatchRadix - 1)) : (uint32_t)kBatchRadix;
-        }
-#pragma unroll
-        for (int i = 0; i < kBatchSortItems; ++i) {
-            const uint32_t peers = __match_any_sync(0xffffffffu, dg[i]);
-            const int leader = __ffs(peers) - 1;
-            const bool ok = dg[i] < (uint32_t)kBatchRadix;
-            const uint32_t b = ok ? warpHist[warp * kBatchRadix + dg[i]] : 0u;
-            __syncwarp();
-            if (ok && lane == (uint32_t)leader) warpHist[warp * kBatchRadix + dg[i]] = b + __popc(peers);
-            __syncwarp();
-            rank[i] = b + __popc(peers & ltMask);
-        }
-        __syncthreads();
-        for (uint32_t d = threadIdx.x; d < kBatchRadix; d += blockDim.x) {
-            uint32_t run = 0;
-            for (uint32_t w = 0; w < warps; ++w) {
-                const uint32_t t = warpHist[w * kBatchRadix + d];
-                warpHist[w * kBatchRadix + d] = run;
-                run += t;
-            }
-            tileTotal[d] = run;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < kBatchSortItems; ++i) {
-            if (dg[i] < (uint32_t)kBatchRadix) {
-                const uint32_t pos = digitBase[dg[i]] + warpHist[warp * kBatchRadix + dg[i]] + rank[i];
-                if (pos < S.n) {  // always, given consistent histograms
-                    kout[pos] = k[i];
-                    vout[pos] = v[i];
-                } else {
-                    latchError(S.error, GRT_ERROR_INTERNAL);
-                }
-            }
-        }
-        __syncthreads();
-        for (uint32_t d = threadIdx.x; d < kBatchRadix; d += blockDim.x) {
-            digitBase[d] += tileTotal[d];
-            for (uint32_t w = 0; w < warps; ++w) warpHist[w * kBatchRadix + d] = 0u;
-        }
-        __syncthreads();
-    }
-}
-
-template <typename K>
-__device__ __noinline__ void karrasRange(const BatchSceneDev& S, uint32_t begin, uint32_t end) {
-    const K* keys = static_cast<const K*>(S.keys[S.passes & 1u]);
-    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x)
-        karrasNode<true>(keys, (int)S.n, (int)i, S.nodes, S.parents);
-}
-
-__device__ __noinline__ void fitRange(const BatchSceneDev& S, uint32_t begin, uint32_t end) {
-    FitParams P{};
-    P.src = S.src;
-    P.n = S.n;
-    P.sortedPrims = S.vals[S.passes & 1u];
-    P.nodes = S.nodes;
-    P.leaves = S.leaves;
-    P.primToLeaf = S.primToLeaf;
-    P.parents = S.parents;
-    P.flags = S.flags;
-    P.header = S.header;
-    for (uint32_t k = begin + threadIdx.x; k < end; k += blockDim.x) fitLeaf<0>(P, k);
-}
-
-// The whole build of a small scene by one block, phase after phase.
-template <typename K, int BITS>
-__device__ __noinline__ void buildWhole(const BatchSceneDev& S, uint32_t chunkKeys, uint32_t* smem) {
-    if (S.n == 0) return;
-    prepRange(S, 0, S.n);
-    __threadfence();
-    __syncthreads();
-    for (uint32_t p = 0; p < S.passes; ++p) {
-        for (uint32_t c = 0; c < S.sortChunks; ++c) {
-            sortUpsweepChunk<K, BITS>(S, c, p, chunkKeys, smem);
-            __syncthreads();
-        }
-        __threadfence();
-        __syncthreads();
-        sortScanScene(S, smem);
-        __threadfence();
-        __syncthreads();
-        for (uint32_t c = 0; c < S.sortChunks; ++c) {
-            sortDownsweepChunk<K>(S, c, p, chunkKeys, smem);
-            __syncthreads();
-        }
-        __threadfence();
-        __syncthreads();
-    }
-    if (S.n >= 2) karrasRange<K>(S, 0, S.n - 1);
-    __threadfence();
-    __syncthreads();
-    fitRange(S, 0, S.n);
 }
 
 // ------------------------------------------------------------------ trace phase
@@ -560,7 +309,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
     Context* c = asContext(ctx);
     const uint32_t bs = opt.blockSize;
     const uint32_t warps = bs / 32;
-    const uint32_t chunkKeys = opt.sortChunkTiles * bs * kBatchSortItems;
+    const uint32_t chunkKeys = opt.sortChunkTiles * bs * kBlockSortItems;
 
     // scene descriptors (pointers into the scratch region are filled in below)
     std::vector<BatchSceneDev> S(sceneCount);
@@ -579,6 +328,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
             return GRT_ERROR_INVALID_PARAMETER;
         BatchSceneDev& d = S[i];
         d.src = primSource(&in.input, n);
+        d.kind = 0;  // triangles
         d.n = n;
         d.rays = in.rayCount;
         d.bits = o->mortonBits;
@@ -597,7 +347,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         const size_t kb = d.bits == 30 ? 4 : 8, nn = std::max(n, 1u);
         scratchOff[i] = scratch;
         scratch += 256 + alignUp(16 * nn, 256) + 2 * alignUp(kb * nn, 256) + 2 * alignUp(4 * nn, 256) +
-                   alignUp(4 * (size_t)kBatchRadix * d.sortChunks, 256) + alignUp(4 * nn, 256);
+                   alignUp(4 * (size_t)kBlockRadix * d.sortChunks, 256) + alignUp(4 * nn, 256);
     }
 
     // work items. Scenes go in groups of opt.sceneGroup, largest first: a group's build
@@ -643,7 +393,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
     b->itemCount = (uint32_t)items.size();
     b->blockSize = bs;
     const size_t stackSmem = (size_t)bs * opt.sharedStackDepth * 4;
-    const size_t sortSmem = ((size_t)warps * kBatchRadix + 2 * kBatchRadix) * 4;
+    const size_t sortSmem = ((size_t)warps * kBlockRadix + 2 * kBlockRadix) * 4;
     b->smem = std::max<size_t>(std::max(stackSmem, sortSmem), 33 * 4);
     int perSm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSm, batchKernel, (int)bs, b->smem) != cudaSuccess ||
@@ -677,7 +427,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         d.keys[1] = p, p += alignUp(kb * nn, 256);
         d.vals[0] = (uint32_t*)p, p += alignUp(4 * nn, 256);
         d.vals[1] = (uint32_t*)p, p += alignUp(4 * nn, 256);
-        d.counts = (uint32_t*)p, p += alignUp(4 * (size_t)kBatchRadix * d.sortChunks, 256);
+        d.counts = (uint32_t*)p, p += alignUp(4 * (size_t)kBlockRadix * d.sortChunks, 256);
         d.flags = (uint32_t*)p;
     }
     cudaError_t ce = cudaSuccess;
