@@ -322,76 +322,101 @@ struct InstanceInput {
 // Per instance: frame M = T R S and its inverse S^-1 R^T (x - T) in FP64 (rounded to
 // float32), the world box of the bottom level's root box (8 corners through M,
 // rounded outward), and the centroid of that box.
+__device__ __forceinline__ float3 setupInstance(const InstanceInput& I, uint32_t i) {
+    float3 c;
+    const grtInstance in = I.instances[i];
+    const grtFrameSRT f = I.frames[i];
+    const BvhHeader* g = reinterpret_cast<const BvhHeader*>(in.geometry);
+    double qx = f.rotation[0], qy = f.rotation[1], qz = f.rotation[2], qw = f.rotation[3];
+    const double qn = sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
+    qx /= qn, qy /= qn, qz /= qn, qw /= qn;
+    const double R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qz * qw), 2 * (qx * qz + qy * qw)},
+                            {2 * (qx * qy + qz * qw), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qx * qw)},
+                            {2 * (qx * qz - qy * qw), 2 * (qy * qz + qx * qw), 1 - 2 * (qx * qx + qy * qy)}};
+    const double S[3] = {f.scale[0], f.scale[1], f.scale[2]};
+    const double T[3] = {f.translation[0], f.translation[1], f.translation[2]};
+    double F[3][4], G[3][4];
+    for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q) {
+            F[r][q] = R[r][q] * S[q];
+            G[r][q] = R[q][r] / S[r];
+        }
+        F[r][3] = T[r];
+        G[r][3] = -(G[r][0] * T[0] + G[r][1] * T[1] + G[r][2] * T[2]);
+    }
+    InstanceRecord rec;
+    for (int r = 0; r < 3; ++r) {
+        rec.inv[r] = make_float4(__double2float_rn(G[r][0]), __double2float_rn(G[r][1]),
+                                 __double2float_rn(G[r][2]), __double2float_rn(G[r][3]));
+        I.fwd32[kFrameRows * (size_t)i + 3 + r] =
+            make_float4(__double2float_rn(G[r][0] - (double)rec.inv[r].x),
+                        __double2float_rn(G[r][1] - (double)rec.inv[r].y),
+                        __double2float_rn(G[r][2] - (double)rec.inv[r].z),
+                        __double2float_rn(G[r][3] - (double)rec.inv[r].w));
+        I.fwd32[kFrameRows * (size_t)i + r] = make_float4(__double2float_rn(F[r][0]), __double2float_rn(F[r][1]),
+                                                 __double2float_rn(F[r][2]), __double2float_rn(F[r][3]));
+        for (int q = 0; q < 4; ++q) I.inv64[i].inv[r][q] = G[r][q];
+    }
+    rec.nodes = g->nodes;
+    rec.leaves = g->leaves;
+    rec.instanceID = i;
+    rec.typeBits = (g->geomType & 0xFFFFFFu) | (g->primType << 24) | (g->primCount == 0 ? kInstEmpty : 0u);
+    rec.geometry = g;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (g->primCount > 0) {
+        for (int cnr = 0; cnr < 8; ++cnr) {
+            const double p[3] = {(cnr & 1) ? g->rootHi[0] : g->rootLo[0], (cnr & 2) ? g->rootHi[1] : g->rootLo[1],
+                                 (cnr & 4) ? g->rootHi[2] : g->rootLo[2]};
+            for (int r = 0; r < 3; ++r) {
+                const double w = F[r][0] * p[0] + F[r][1] * p[1] + F[r][2] * p[2] + F[r][3];
+                lo[r] = fmin(lo[r], w);
+                hi[r] = fmax(hi[r], w);
+            }
+        }
+    } else {
+        for (int r = 0; r < 3; ++r) lo[r] = hi[r] = T[r];  // empty: a point box, skipped by traversal
+    }
+    Box3 b;
+    b.lo = make_float3(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]));
+    b.hi = make_float3(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]));
+    I.boxes[2 * (size_t)i] = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f);
+    I.boxes[2 * (size_t)i + 1] = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
+    rec.worldLo = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f);
+    rec.worldHi = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
+    rec.reserved = make_float4(0.f, 0.f, 0.f, 0.f);
+    I.records[i] = rec;
+    c = boxCentroid(b);
+    I.centroids[i] = make_float4(c.x, c.y, c.z, 0.f);
+    return c;
+}
+
 __global__ void __launch_bounds__(128) instanceSetupKernel(InstanceInput I) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < I.count;
-    float3 c = make_float3(0.f, 0.f, 0.f);
-    if (valid) {
-        const grtInstance in = I.instances[i];
-        const grtFrameSRT f = I.frames[i];
-        const BvhHeader* g = reinterpret_cast<const BvhHeader*>(in.geometry);
-        double qx = f.rotation[0], qy = f.rotation[1], qz = f.rotation[2], qw = f.rotation[3];
-        const double qn = sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
-        qx /= qn, qy /= qn, qz /= qn, qw /= qn;
-        const double R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qz * qw), 2 * (qx * qz + qy * qw)},
-                                {2 * (qx * qy + qz * qw), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qx * qw)},
-                                {2 * (qx * qz - qy * qw), 2 * (qy * qz + qx * qw), 1 - 2 * (qx * qx + qy * qy)}};
-        const double S[3] = {f.scale[0], f.scale[1], f.scale[2]};
-        const double T[3] = {f.translation[0], f.translation[1], f.translation[2]};
-        double F[3][4], G[3][4];
-        for (int r = 0; r < 3; ++r) {
-            for (int q = 0; q < 3; ++q) {
-                F[r][q] = R[r][q] * S[q];
-                G[r][q] = R[q][r] / S[r];
-            }
-            F[r][3] = T[r];
-            G[r][3] = -(G[r][0] * T[0] + G[r][1] * T[1] + G[r][2] * T[2]);
-        }
-        InstanceRecord rec;
-        for (int r = 0; r < 3; ++r) {
-            rec.inv[r] = make_float4(__double2float_rn(G[r][0]), __double2float_rn(G[r][1]),
-                                     __double2float_rn(G[r][2]), __double2float_rn(G[r][3]));
-            I.fwd32[kFrameRows * (size_t)i + 3 + r] =
-                make_float4(__double2float_rn(G[r][0] - (double)rec.inv[r].x),
-                            __double2float_rn(G[r][1] - (double)rec.inv[r].y),
-                            __double2float_rn(G[r][2] - (double)rec.inv[r].z),
-                            __double2float_rn(G[r][3] - (double)rec.inv[r].w));
-            I.fwd32[kFrameRows * (size_t)i + r] = make_float4(__double2float_rn(F[r][0]), __double2float_rn(F[r][1]),
-                                                     __double2float_rn(F[r][2]), __double2float_rn(F[r][3]));
-            for (int q = 0; q < 4; ++q) I.inv64[i].inv[r][q] = G[r][q];
-        }
-        rec.nodes = g->nodes;
-        rec.leaves = g->leaves;
-        rec.instanceID = i;
-        rec.typeBits = (g->geomType & 0xFFFFFFu) | (g->primType << 24) | (g->primCount == 0 ? kInstEmpty : 0u);
-        rec.geometry = g;
-        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        if (g->primCount > 0) {
-            for (int cnr = 0; cnr < 8; ++cnr) {
-                const double p[3] = {(cnr & 1) ? g->rootHi[0] : g->rootLo[0], (cnr & 2) ? g->rootHi[1] : g->rootLo[1],
-                                     (cnr & 4) ? g->rootHi[2] : g->rootLo[2]};
-                for (int r = 0; r < 3; ++r) {
-                    const double w = F[r][0] * p[0] + F[r][1] * p[1] + F[r][2] * p[2] + F[r][3];
-                    lo[r] = fmin(lo[r], w);
-                    hi[r] = fmax(hi[r], w);
-                }
-            }
-        } else {
-            for (int r = 0; r < 3; ++r) lo[r] = hi[r] = T[r];  // empty: a point box, skipped by traversal
-        }
-        Box3 b;
-        b.lo = make_float3(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]));
-        b.hi = make_float3(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]));
-        I.boxes[2 * (size_t)i] = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f);
-        I.boxes[2 * (size_t)i + 1] = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
-        rec.worldLo = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f);
-        rec.worldHi = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
-        rec.reserved = make_float4(0.f, 0.f, 0.f, 0.f);
-        I.records[i] = rec;
-        c = boxCentroid(b);
-        I.centroids[i] = make_float4(c.x, c.y, c.z, 0.f);
-    }
+    const float3 c = valid ? setupInstance(I, i) : make_float3(0.f, 0.f, 0.f);
     reduceBounds(c, valid, I.bounds);
+}
+
+// A top level of at most kSmallBuild instances in one block and one launch: the bounds
+// and fit counters initialised, the instance setup, then every LBVH step.
+template <typename K, int BITS>
+__global__ void __launch_bounds__(kSmallBuildThreads) smallSceneKernel(BlockBuild B, InstanceInput I) {
+    extern __shared__ uint32_t smem[];
+    if (threadIdx.x == 0) {
+        B.bounds[0] = B.bounds[1] = B.bounds[2] = 0xFFFFFFFFu;
+        B.bounds[3] = B.bounds[4] = B.bounds[5] = 0u;
+    }
+    for (uint32_t i = threadIdx.x; i + 1 < B.n; i += blockDim.x) B.flags[i] = 0u;
+    __syncthreads();
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (uint32_t i = threadIdx.x; i < I.count; i += blockDim.x) {
+        const float3 c = setupInstance(I, i);
+        mn[0] = fminf(mn[0], c.x), mn[1] = fminf(mn[1], c.y), mn[2] = fminf(mn[2], c.z);
+        mx[0] = fmaxf(mx[0], c.x), mx[1] = fmaxf(mx[1], c.y), mx[2] = fmaxf(mx[2], c.z);
+    }
+    reduceBoxBounds(mn, mx, B.bounds);
+    __syncthreads();
+    buildWhole<K, BITS>(B, B.n, smem);
 }
 
 // ======================================================================= host drivers
@@ -584,10 +609,8 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
     }
     const BuildLayout L = buildLayout(n, o->mortonBits, false);
     char* t = (char*)temp;
-    e = resetBuildScratch(L, t, n, s);
-    if (e != GRT_SUCCESS) return e;
     const PrimSource S = primSource(input, n);
-    if (op == GRT_BUILD_OPERATION_BUILD && n <= kSmallBuild) {
+    if (op == GRT_BUILD_OPERATION_BUILD && n <= kSmallBuild) {  // initialises its own scratch
         BlockBuild B = blockBuildOf(c, o, L, t, input->type == GRT_PRIMITIVE_TRIANGLE_MESH ? 0u : 1u);
         B.src = S;
         e = launchSmallBuild(B, s);
@@ -595,6 +618,8 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
         o->built = true;
         return GRT_SUCCESS;
     }
+    e = resetBuildScratch(L, t, n, s);
+    if (e != GRT_SUCCESS) return e;
     const uint32_t* sorted = nullptr;
     if (op == GRT_BUILD_OPERATION_BUILD) {
         primCentroidKernel<<<ceilDiv(n, 256), 256, 0, s>>>(S, (float4*)(t + L.centroids), (uint32_t*)(t + L.bounds));
@@ -679,8 +704,6 @@ grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* in
     // An update of a scene rebuilds its (small) top level: instance frames may move freely.
     const BuildLayout L = buildLayout(n, o->mortonBits, true);
     char* t = (char*)temp;
-    e = resetBuildScratch(L, t, n, s);
-    if (e != GRT_SUCCESS) return e;
     InstanceInput I{};
     I.instances = input->instances;
     I.frames = input->instanceFrames;
@@ -691,18 +714,25 @@ grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* in
     I.bounds = (uint32_t*)(t + L.bounds);
     I.inv64 = o->inv64;
     I.fwd32 = o->fwd32;
-    instanceSetupKernel<<<ceilDiv(n, 128), 128, 0, s>>>(I);
-    GRT_LAUNCH_CHECK();
-    noteLaunches(1);
     if (n <= kSmallBuild) {
         BlockBuild B = blockBuildOf(c, o, L, t, 2u);
         B.instBoxes = I.boxes;
         B.instRecords = I.records;
-        e = launchSmallBuild(B, s);
-        if (e != GRT_SUCCESS) return e;
+        const size_t smem = blockBuildSmemWords(kSmallBuildThreads) * sizeof(uint32_t);
+        if (B.bits == 30)
+            smallSceneKernel<uint32_t, 10><<<1, kSmallBuildThreads, smem, s>>>(B, I);
+        else
+            smallSceneKernel<unsigned long long, 21><<<1, kSmallBuildThreads, smem, s>>>(B, I);
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
         o->built = true;
         return GRT_SUCCESS;
     }
+    e = resetBuildScratch(L, t, n, s);
+    if (e != GRT_SUCCESS) return e;
+    instanceSetupKernel<<<ceilDiv(n, 128), 128, 0, s>>>(I);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
     const uint32_t* sorted = nullptr;
     e = sortAndEmit(c, o, L, t, s, &sorted);
     if (e != GRT_SUCCESS) return e;

@@ -264,10 +264,11 @@ __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
     for (;;) {
         const uint32_t p = pe >> 1, side = pe & 1u;
         writeChildBox(P.nodes, p, side, b);
-        __threadfence();
-        const uint32_t prev = atomicAdd(&P.flags[p], 1u);
+        // acquire-release at GPU scope: releases this box to the sibling's thread if it
+        // comes second, and acquires the sibling's box if this thread comes second
+        uint32_t prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(P.flags + p) : "memory");
         if (prev == 0) return;  // the sibling is still on its way up
-        __threadfence();
         const float4 x = __ldcg(&P.nodes[4 * (size_t)p + 0]);
         const float4 y = __ldcg(&P.nodes[4 * (size_t)p + 1]);
         const float4 z = __ldcg(&P.nodes[4 * (size_t)p + 2]);

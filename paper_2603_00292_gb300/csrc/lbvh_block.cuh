@@ -257,30 +257,34 @@ static __device__ __noinline__ void fitRange(const BlockBuild& S, uint32_t begin
 
 // The whole build of a small scene by one block, phase after phase.
 template <typename K, int BITS>
+// Every step's global writes are read by other threads of the same block after a
+// block barrier, which orders them at block scope; no wider fence is needed here. Triangle
+// and box builds start from uninitialised bounds and fit counters; an instance build
+// expects both prepared with the centroids (its setup runs first).
 __device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys, uint32_t* smem) {
     if (S.n == 0) return;
-    if (S.kind != 2) prepRange(S, 0, S.n);  // instances: centroids and bounds come with their setup
-    __threadfence();
+    if (S.kind != 2) {
+        if (threadIdx.x == 0) {
+            S.bounds[0] = S.bounds[1] = S.bounds[2] = 0xFFFFFFFFu;  // running minima start at the top
+            S.bounds[3] = S.bounds[4] = S.bounds[5] = 0u;           // running maxima at the bottom
+        }
+        __syncthreads();
+        prepRange(S, 0, S.n);
+    }
     __syncthreads();
     for (uint32_t p = 0; p < S.passes; ++p) {
         for (uint32_t c = 0; c < S.sortChunks; ++c) {
             sortUpsweepChunk<K, BITS>(S, c, p, chunkKeys, smem);
             __syncthreads();
         }
-        __threadfence();
-        __syncthreads();
         sortScanScene(S, smem);
-        __threadfence();
         __syncthreads();
         for (uint32_t c = 0; c < S.sortChunks; ++c) {
             sortDownsweepChunk<K>(S, c, p, chunkKeys, smem);
             __syncthreads();
         }
-        __threadfence();
-        __syncthreads();
     }
     if (S.n >= 2) karrasRange<K>(S, 0, S.n - 1);
-    __threadfence();
     __syncthreads();
     fitRange(S, 0, S.n);
 }
