@@ -230,7 +230,7 @@ typedef struct grtTraceOptions {
     uint32_t blockSize;        /* threads per block: 0 = default (128); 64, 128 or 256 */
     uint32_t sharedStackDepth; /* entries per thread in shared memory: 0 = default (16), 1..32 */
     uint32_t globalStackDepth; /* further entries per thread in global memory: 0 = default (64) */
-    float compactThreshold;    /* warp refill threshold (fraction of live lanes), 0 = default (0.75 for
+    float compactThreshold;    /* warp refill threshold (fraction of live lanes), 0 = default (0.6 for
                                   grtTraceAmbientOcclusion, else 0.5) */
     uint32_t flags;            /* GRT_TRACE_FLAG_COUNT: accumulate grtTraceStatistics (slower) */
     void* globalStack;         /* optional caller-owned device buffer for the global entries; NULL = the

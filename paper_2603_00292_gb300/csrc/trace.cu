@@ -456,7 +456,7 @@ static grtError resolveOptions(const grtTraceOptions* opt, int* blockSize, uint3
 
 // Everything a launch needs except the kernel-specific fields.
 // defaultCompact: the refill threshold when the options leave it 0 (measured best per
-// query kind: 0.5 for closest / any hit and shading, 0.75 for fused ambient occlusion).
+// query kind: 0.5 for closest / any hit and shading, 0.6 for fused ambient occlusion).
 static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFuncTable table,
                              const grtTraceOptions* opt, TraceParams& P, bool* isScene, int* blockSize,
                              float defaultCompact = 0.5f) {
@@ -754,7 +754,7 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
     TraceParams P{};
     bool isScene = false;
     int bs = 128;
-    grtError e = prepareTrace(c, scene, nullptr, nullptr, options, P, &isScene, &bs, 0.75f);
+    grtError e = prepareTrace(c, scene, nullptr, nullptr, options, P, &isScene, &bs, 0.6f);
     if (e != GRT_SUCCESS || pixelCount == 0) return e;
     if (!primaryRays || !primaryHits || !ao) return GRT_ERROR_INVALID_PARAMETER;
     BvhObject* o = findBvh(scene);
