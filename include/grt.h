@@ -388,7 +388,11 @@ typedef struct grtBatchScene {
 
 enum {
     GRT_BATCH_FLAG_GRAPH = 1,  /* capture the launch sequence once into a CUDA graph and replay it */
-    GRT_BATCH_FLAG_PROFILE = 2 /* record when each work item started, was ready and ended */
+    GRT_BATCH_FLAG_PROFILE = 2, /* record when each work item started, was ready and ended */
+    /* Test of the bounded waits: one work item is planned to wait for one completion more
+     * than can ever happen, so its wait expires after waitLimitMs, GRT_ERROR_TIMEOUT is
+     * latched and the launch aborts (the other items skip their work and end). */
+    GRT_BATCH_FLAG_TEST_EXPIRE_WAIT = 4
 };
 
 /* Tuning knobs (0 selects the default in brackets). */
@@ -403,6 +407,7 @@ typedef struct grtBatchOptions {
     uint32_t traceChunk;        /* rays per trace work item [16384] */
     uint32_t sceneGroup;        /* scenes per scheduling group, largest first: a group's builds, then its
                                    traces [32] */
+    uint32_t waitLimitMs;       /* a work item's wait for another expires after this long [2000] */
     uint32_t flags;             /* GRT_BATCH_FLAG_* */
 } grtBatchOptions;
 

@@ -116,7 +116,7 @@ class grtBatchOptions(ctypes.Structure):
                 ("globalStackDepth", ctypes.c_uint32), ("compactThreshold", ctypes.c_float),
                 ("smallScenePrims", ctypes.c_uint32), ("sortChunkTiles", ctypes.c_uint32),
                 ("buildChunk", ctypes.c_uint32), ("traceChunk", ctypes.c_uint32), ("sceneGroup", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("waitLimitMs", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class grtBatchInfo(ctypes.Structure):
@@ -127,6 +127,7 @@ class grtBatchInfo(ctypes.Structure):
 
 GRT_BATCH_FLAG_GRAPH = 1
 GRT_BATCH_FLAG_PROFILE = 2
+GRT_BATCH_FLAG_TEST_EXPIRE_WAIT = 4
 
 
 class grtBatchItemRecord(ctypes.Structure):
@@ -450,11 +451,12 @@ def grtSortPairs(ctx, keys, values, count, key_bits, significant_bits, temp, str
 
 
 def batch_options(block_size=0, shared_depth=0, global_depth=0, compact=0.0, small_scene_prims=0,
-                  sort_chunk_tiles=0, build_chunk=0, trace_chunk=0, scene_group=0, graph=False,
-                  profile=False) -> grtBatchOptions:
-    flags = (GRT_BATCH_FLAG_GRAPH if graph else 0) | (GRT_BATCH_FLAG_PROFILE if profile else 0)
+                  sort_chunk_tiles=0, build_chunk=0, trace_chunk=0, scene_group=0, wait_limit_ms=0, graph=False,
+                  profile=False, test_expire_wait=False) -> grtBatchOptions:
+    flags = ((GRT_BATCH_FLAG_GRAPH if graph else 0) | (GRT_BATCH_FLAG_PROFILE if profile else 0) |
+             (GRT_BATCH_FLAG_TEST_EXPIRE_WAIT if test_expire_wait else 0))
     return grtBatchOptions(block_size, shared_depth, global_depth, compact, small_scene_prims, sort_chunk_tiles,
-                           build_chunk, trace_chunk, scene_group, flags)
+                           build_chunk, trace_chunk, scene_group, wait_limit_ms, flags)
 
 
 def batch_scene(geometry: int, inp: grtGeometryBuildInput, rays, ray_count: int, hits) -> grtBatchScene:

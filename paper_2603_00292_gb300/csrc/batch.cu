@@ -21,8 +21,8 @@
 // An item of phase k waits until every item of phase k-1 of its scene has finished
 // (per-scene completion counters). The host orders the queue so that an item only
 // ever waits for items taken from the queue before it, so a waiting block never
-// blocks the progress it waits for; every wait is bounded in time all the same and
-// latches GRT_ERROR_TIMEOUT if it expires. Scenes are queued in groups, largest
+// blocks the progress it waits for; every wait is bounded in time all the same
+// (waitLimitMs) and latches GRT_ERROR_TIMEOUT if it expires. Scenes are queued in groups, largest
 // first, each group's builds followed by its traces (see grtCreateBatch).
 //
 // Memory. Data written earlier in the launch by another block (centroids, keys,
@@ -39,8 +39,7 @@
 namespace grt {
 
 constexpr uint32_t kBatchPhases = 32;
-constexpr unsigned long long kBatchWaitNs = 2000000000ull;  // 2 s per wait
-constexpr uint32_t kBatchWaitSpins = 1u << 25;                // and at most this many polls
+constexpr uint32_t kBatchWaitSpins = 1u << 25;  // a wait polls at most this many times
 
 // A scene of the batch: its build (BlockBuild) plus its rays and the trace phase.
 struct BatchSceneDev : BlockBuild {
@@ -78,6 +77,7 @@ struct BatchParams {
     uint32_t buildChunk;
     uint32_t sortChunkKeys;
     uint32_t traceChunk;
+    unsigned long long waitNs;  // time limit of one wait
 };
 
 __device__ __forceinline__ unsigned long long globalTimerNs() {
@@ -95,7 +95,7 @@ __device__ void waitPhase(const BatchParams& B, uint32_t scene, uint32_t phase, 
         const unsigned long long t0 = globalTimerNs();
         for (uint32_t k = 0; *d < need; ++k) {
             if (*abort != 0u) break;
-            if (k >= kBatchWaitSpins || ((k & 63u) == 0u && globalTimerNs() - t0 > kBatchWaitNs)) {
+            if (k >= kBatchWaitSpins || ((k & 63u) == 0u && globalTimerNs() - t0 > B.waitNs)) {
                 latchError(B.error, GRT_ERROR_TIMEOUT);
                 atomicExch(B.abort, 1u);
                 break;
@@ -279,11 +279,14 @@ static grtError resolveBatchOptions(const grtBatchOptions* o, grtBatchOptions* r
     if (!d.buildChunk) d.buildChunk = 16384;
     if (!d.traceChunk) d.traceChunk = 16384;
     if (!d.sceneGroup) d.sceneGroup = 32;
+    if (!d.waitLimitMs) d.waitLimitMs = 2000;
     if (d.blockSize != 64 && d.blockSize != 128 && d.blockSize != 256) return GRT_ERROR_INVALID_PARAMETER;
     if (d.sharedStackDepth > 32 || d.globalStackDepth > 4096) return GRT_ERROR_INVALID_PARAMETER;
     if (d.compactThreshold > 1.f || d.sortChunkTiles > 4096) return GRT_ERROR_INVALID_PARAMETER;
     if (d.buildChunk > (1u << 24) || d.traceChunk > (1u << 24)) return GRT_ERROR_INVALID_PARAMETER;
-    if (d.flags & ~(uint32_t)(GRT_BATCH_FLAG_GRAPH | GRT_BATCH_FLAG_PROFILE)) return GRT_ERROR_INVALID_PARAMETER;
+    if (d.flags & ~(uint32_t)(GRT_BATCH_FLAG_GRAPH | GRT_BATCH_FLAG_PROFILE | GRT_BATCH_FLAG_TEST_EXPIRE_WAIT))
+        return GRT_ERROR_INVALID_PARAMETER;
+    if (d.waitLimitMs > 600000) return GRT_ERROR_INVALID_PARAMETER;
     *r = d;
     return GRT_SUCCESS;
 }
@@ -386,6 +389,14 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         }
     }
 
+    if (opt.flags & GRT_BATCH_FLAG_TEST_EXPIRE_WAIT) {
+        for (BatchItemDev& it : items)
+            if (it.phase > 0) {  // one completion more than the phase before it has items
+                ++it.waitCount;
+                break;
+            }
+    }
+
     // launch shape and the device allocation
     BatchObject* b = new BatchObject();
     b->device = deviceOf(c);
@@ -458,6 +469,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
     P.buildChunk = opt.buildChunk;
     P.sortChunkKeys = chunkKeys;
     P.traceChunk = opt.traceChunk;
+    P.waitNs = (unsigned long long)opt.waitLimitMs * 1000000ull;
     b->useGraph = (opt.flags & GRT_BATCH_FLAG_GRAPH) != 0;
     for (uint32_t i = 0; i < sceneCount; ++i) {
         b->geometries.push_back(scenes[i].geometry);

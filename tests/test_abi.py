@@ -51,7 +51,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(grt.grtTraceOptions) == 40
     assert grt.RAY_BYTES == 32 and grt.HIT_BYTES == 20
     assert ctypes.sizeof(grt.grtBatchScene) == 8 + 56 + 8 + 8 + 8
-    assert ctypes.sizeof(grt.grtBatchOptions) == 40
+    assert ctypes.sizeof(grt.grtBatchOptions) == 44
     assert ctypes.sizeof(grt.grtBatchInfo) == 32
     assert ctypes.sizeof(grt.grtBatchItemRecord) == 40
     assert ctypes.sizeof(grt.grtDeviceTarget) == 7 * 8 + 5 * 4 + 4

@@ -130,3 +130,27 @@ def test_batch_edge_cases(gpu):
     B, batched, single = _run(gpu, work, grt.batch_options())
     _assert_identical(batched, single)
     assert (hits_to_numpy(batched[2][2])[1] == 0xFFFFFFFF).all()
+
+
+def test_expired_wait_latches_timeout_and_the_context_stays_usable(gpu):
+    """A work item planned to wait for a completion that never comes: its wait runs out
+    after wait_limit_ms, the launch latches GRT_ERROR_TIMEOUT and drains (every later item
+    skips its work), and the same context then runs a normal batch correctly."""
+    work = _workload(6, nmax=40_000, rmax=4_000)
+    scenes = []
+    for s, rays in work:
+        v, i = device_tensor(s.mesh.vertices), device_tensor(s.mesh.indices)
+        scenes.append((Geometry(gpu, vertices=v, indices=i), device_tensor(rays), new_hits(rays.shape[0])))
+    stalled = Batch(gpu, scenes, grt.batch_options(wait_limit_ms=100, test_expire_wait=True))
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    stalled.run()
+    t1.record()
+    t1.synchronize()
+    assert 90.0 <= t0.elapsed_time(t1) < 5000.0  # the wait ran out, and the launch ended
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_ERROR_TIMEOUT
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS  # read and cleared
+    stalled.close()
+    B, batched, single = _run(gpu, work, grt.batch_options())
+    _assert_identical(batched, single)
