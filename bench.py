@@ -52,7 +52,7 @@ UNIT = "Mrays/s"
 WORKLOAD = dict(workload="terrain64-ao-1080p", instances=64, terrain_cells=256, triangles_per_instance=131072,
                 width=1920, height=1080, ao_samples=8, ao_length="0.05*extent", seed=20260301)
 RAY_BYTES, HIT_BYTES = 32, 20
-NODE_BYTES, TRI_BYTES, INST_BYTES = 64, 48, 128
+NODE_BYTES, TRI_BYTES, INST_BYTES = 112, 48, 128  # a 4-wide node visit reads 7 of its 8 float4
 
 
 def parse():
@@ -634,10 +634,11 @@ def build_bytes_per_prim(bits: int) -> int:
     histogram and reads and writes keys and values in its scatter; emission reads a key
     and writes a node word and two parent links (28 or 32); the fit reads the value,
     indices and vertices (52), writes the leaf record and its slot (52) and, per
-    internal node, two parent links, two box writes and one box read (~80)."""
+    internal node, two parent links, two box writes and one box read (~80), plus the
+    4-wide nodes: 128 bytes per internal node, written slot by slot."""
     kb, passes = (4, 4) if bits == 30 else (8, 8)
     sort = (16 + kb + 4) + (passes - 1) * kb + passes * 2 * (kb + 4)
-    return 68 + sort + (kb + 24) + 52 + 52 + 80
+    return 68 + sort + (kb + 24) + 52 + 52 + 80 + 128
 
 
 def run_batched(args, rank, world, local):

@@ -287,7 +287,7 @@ grtError grtTraceAnyHit(grtContext ctx, grtScene scene, grtGeometry geom, const 
  * kernel by value. Valid while the target, the table and the context live and the
  * target is not rebuilt with a different primitive count. */
 typedef struct grtDeviceTarget {
-    const void* nodes;            /* the target's nodes */
+    const void* nodes;            /* the target's 4-wide nodes (grtBvhInfo.wideNodes) */
     const void* leaves;           /* triangle records / primitive IDs / instance records */
     const uint32_t* primToLeaf;   /* primitive (instance) ID -> sorted leaf position */
     const void* frames64;         /* scenes: FP64 inverse frame per instance ID, else NULL */
@@ -470,6 +470,7 @@ typedef struct grtBvhInfo {
     uint32_t primCount;
     uint32_t primType;   /* grtPrimitiveType; 2 for a scene */
     uint32_t mortonBits; /* key width used by the last build */
+    const void* wideNodes; /* nodeCount x 128-byte 4-wide nodes, the ones traversal reads (layout below) */
 } grtBvhInfo;
 /*
  * Node (64 bytes, 4 x float4): children c0 and c1 of internal node k
@@ -479,6 +480,15 @@ typedef struct grtBvhInfo {
  *   [3] = (uint32) c0 index, c1 index, 0, 0 ; bit 31 set = leaf, low bits = sorted position
  * Node 0 is the root. Triangle leaf k (48 bytes): {v0.xyz, primID}, {v1.xyz, 0}, {v2.xyz, 0}.
  * A single-primitive geometry has one node whose second child is empty.
+ *
+ * Wide node k (128 bytes, 8 x float4): binary node k with each internal child replaced
+ * by that child's two children, so up to four slots j = 0..3; slots 2s and 2s+1 come
+ * from child s (its two children, or the leaf itself and an empty slot):
+ *   [0] = lo.x of slots 0-3   [1] = hi.x   [2] = lo.y   [3] = hi.y   [4] = lo.z   [5] = hi.z
+ *   [6] = (uint32) slot indices as in binary nodes; 0xFFFFFFFF = empty (box lo = +inf, hi = -inf)
+ *   [7] = unused
+ * Traversal starts at wide node 0 and follows slot indices, so it visits the wide nodes
+ * of binary nodes at even depth; the rest are written but not read.
  */
 grtError grtGetBvhInfo(grtContext ctx, grtGeometry geom, grtScene scene, grtBvhInfo* info);
 
@@ -496,7 +506,7 @@ grtError grtGetLaunchCount(uint64_t* count);
 #define GRT_TRACE_FLAG_COUNT 1u
 typedef struct grtTraceStatistics {
     uint64_t rays;            /* rays traced */
-    uint64_t nodesVisited;    /* 64-byte internal nodes fetched */
+    uint64_t nodesVisited;    /* 4-wide nodes fetched (112 bytes each: boxes and children) */
     uint64_t trianglesTested; /* 48-byte triangle records tested */
     uint64_t customTested;    /* custom primitives tested */
     uint64_t instancesEntered;/* 128-byte instance records read on entry */

@@ -29,6 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 NONE = 0xFFFFFFFF
+LEAF_BIT = 0x80000000
 
 
 def build(force: bool = False) -> str:
@@ -197,6 +198,39 @@ def lbvh(leaf_lo, leaf_hi, centroids, bits_per_axis: int):
     return dict(centroid_lo=clo, centroid_hi=chi, codes=codes, sorted_codes=sk, order=order, childL=cl,
                 childR=cr, parent_internal=pi, parent_leaf=pl, node_lo=nlo, node_hi=nhi, leaf_lo=slo,
                 leaf_hi=shi)
+
+
+def wide_nodes(ref):
+    """4-wide nodes from a binary LBVH (the dict of lbvh()), by definition: wide node k has
+    binary node k's two children, each internal child replaced by its own two children.
+    Slots 2s and 2s+1 come from child s: its two children, or the leaf itself and an
+    empty slot (index 0xFFFFFFFF, box lo = +inf, hi = -inf). Returns lo, hi (m, 4, 3)
+    float32 and child (m, 4) uint32, m = max(n - 1, 1). Child words use the binary
+    format: bit 31 set = leaf, low bits = sorted position."""
+    n = ref["leaf_lo"].shape[0]
+    m = max(n - 1, 1)
+    lo = np.full((m, 4, 3), np.inf, np.float32)
+    hi = np.full((m, 4, 3), -np.inf, np.float32)
+    child = np.full((m, 4), NONE, np.uint32)
+    if n == 1:  # a single primitive: one node, the leaf in slot 0
+        lo[0, 0], hi[0, 0], child[0, 0] = ref["leaf_lo"][0], ref["leaf_hi"][0], LEAF_BIT
+        return lo, hi, child
+    cl = ref["childL"].view(np.uint32)
+    cr = ref["childR"].view(np.uint32)
+    all_lo = np.concatenate([ref["node_lo"], ref["leaf_lo"]])  # internal nodes, then leaves
+    all_hi = np.concatenate([ref["node_hi"], ref["leaf_hi"]])
+    for s_, c in enumerate((cl, cr)):
+        leaf = (c & LEAF_BIT) != 0
+        inner = np.where(leaf, 0, c & 0x7FFFFFFF)
+        first = np.where(leaf, c, cl[inner])  # the leaf itself, or the child's two children
+        second = np.where(leaf, np.uint32(NONE), cr[inner])
+        for j, g in enumerate((first, second)):
+            used = g != NONE
+            row = np.where(g & LEAF_BIT, n - 1 + (g & 0x7FFFFFFF), g).astype(np.int64)
+            lo[used, 2 * s_ + j] = all_lo[row[used]]
+            hi[used, 2 * s_ + j] = all_hi[row[used]]
+            child[:, 2 * s_ + j] = g
+    return lo, hi, child
 
 
 # ----------------------------------------------------------------------------------

@@ -96,7 +96,7 @@ class grtCamera(ctypes.Structure):
 class grtBvhInfo(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("parents", ctypes.c_void_p),
                 ("nodeCount", ctypes.c_uint32), ("primCount", ctypes.c_uint32), ("primType", ctypes.c_uint32),
-                ("mortonBits", ctypes.c_uint32)]
+                ("mortonBits", ctypes.c_uint32), ("wideNodes", ctypes.c_void_p)]
 
 
 class grtDeviceTarget(ctypes.Structure):

@@ -124,7 +124,7 @@ struct ChunkRaySource {
 __device__ __noinline__ void traceChunk(const BatchParams& B, const BatchSceneDev& S, uint32_t chunk, unsigned long long item,
                            uint32_t* smem) {
     TraceParams P{};
-    P.target.nodes = S.nodes;
+    P.target.nodes = S.wide;
     P.target.leaves = S.leaves;
     P.target.primType = GRT_PRIMITIVE_TRIANGLE_MESH;
     P.target.geomType = 0;
@@ -342,6 +342,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         d.rayBuf = (const float4*)in.rays;
         d.hitBuf = (uint32_t*)in.hits;
         d.nodes = (float4*)o->nodes;
+        d.wide = (float4*)o->wide;
         d.leaves = o->leaves;
         d.parents = (uint32_t*)o->parents;
         d.primToLeaf = o->primToLeaf;
@@ -403,7 +404,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
     b->sceneCount = sceneCount;
     b->itemCount = (uint32_t)items.size();
     b->blockSize = bs;
-    const size_t stackSmem = (size_t)bs * opt.sharedStackDepth * 4;
+    const size_t stackSmem = (size_t)bs * traceSmemWords(opt.sharedStackDepth) * 4;
     const size_t sortSmem = ((size_t)warps * kBlockRadix + 2 * kBlockRadix) * 4;
     b->smem = std::max<size_t>(std::max(stackSmem, sortSmem), 33 * 4);
     int perSm = 0;

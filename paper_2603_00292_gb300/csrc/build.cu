@@ -279,6 +279,7 @@ static BlockBuild blockBuildOf(Context* c, BvhObject* o, const BuildLayout& L, c
     B.passes = (o->mortonBits + 7) / 8;
     B.kind = kind;
     B.nodes = (float4*)o->nodes;
+    B.wide = (float4*)o->wide;
     B.leaves = o->leaves;
     B.parents = (uint32_t*)o->parents;
     B.primToLeaf = o->primToLeaf;
@@ -470,6 +471,7 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     size_t leafBytes = primType == GRT_PRIMITIVE_TRIANGLE_MESH ? 48 : (primType == kPrimScene ? 128 : 4);
     cudaError_t e = cudaMalloc(&o->dHeader, sizeof(BvhHeader));
     if (e == cudaSuccess && count) e = cudaMalloc(&o->nodes, (size_t)o->nodeCount * 64);
+    if (e == cudaSuccess && count) e = cudaMalloc(&o->wide, (size_t)o->nodeCount * kWideWords * sizeof(float4));
     if (e == cudaSuccess && count) e = cudaMalloc(&o->leaves, (size_t)count * leafBytes);
     if (e == cudaSuccess && count) e = cudaMalloc(&o->parents, (size_t)(2 * count - 1) * 4);
     if (e == cudaSuccess && count && primType != GRT_PRIMITIVE_AABB_LIST) e = cudaMalloc(&o->primToLeaf, (size_t)count * 4);
@@ -479,7 +481,7 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     for (int a = 0; a < 3; ++a) h.rootLo[a] = INFINITY, h.rootHi[a] = -INFINITY;
     h.primCount = count;
     h.primType = primType;
-    h.nodes = (const float4*)o->nodes;
+    h.nodes = (const float4*)o->wide;
     h.leaves = o->leaves;
     h.nodeCount = o->nodeCount;
     h.geomType = geomType;
@@ -488,6 +490,7 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     if (e != cudaSuccess) {
         cudaFree(o->dHeader);
         cudaFree(o->nodes);
+        cudaFree(o->wide);
         cudaFree(o->leaves);
         cudaFree(o->parents);
         cudaFree(o->primToLeaf);
@@ -506,6 +509,7 @@ static void destroyBvhObject(BvhObject* o) {
     unregisterBvh(o->dHeader);
     cudaFree(o->dHeader);
     cudaFree(o->nodes);
+    cudaFree(o->wide);
     cudaFree(o->leaves);
     cudaFree(o->parents);
     cudaFree(o->primToLeaf);
@@ -633,6 +637,7 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
     P.n = n;
     P.sortedPrims = sorted;  // null for UPDATE: IDs come from the leaves
     P.nodes = (float4*)o->nodes;
+    P.wide = (float4*)o->wide;
     P.leaves = o->leaves;
     P.primToLeaf = o->primToLeaf;
     P.parents = (const uint32_t*)o->parents;
@@ -740,6 +745,7 @@ grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* in
     P.n = n;
     P.sortedPrims = sorted;
     P.nodes = (float4*)o->nodes;
+    P.wide = (float4*)o->wide;
     P.leaves = o->leaves;
     P.parents = (const uint32_t*)o->parents;
     P.flags = (uint32_t*)(t + L.flags);

@@ -246,6 +246,7 @@ grtError grtGetBvhInfo(grtContext ctx, grtGeometry geom, grtScene scene, grtBvhI
     BvhObject* o = findBvh(geom ? (const void*)geom : (const void*)scene);
     if (!o) return GRT_ERROR_INVALID_PARAMETER;
     info->nodes = o->nodes;
+    info->wideNodes = o->wide;
     info->leaves = o->leaves;
     info->parents = o->parents;
     info->nodeCount = o->nodeCount;

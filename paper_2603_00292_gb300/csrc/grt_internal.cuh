@@ -13,6 +13,7 @@ namespace grt {
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 constexpr uint32_t kPrimScene = 2;  // primType of a scene header
+constexpr int kWideWords = 8;       // float4 per 4-wide node (128 B)
 
 // Device-resident header that a grtGeometry / grtScene handle points to (64 B).
 struct alignas(16) BvhHeader {
@@ -20,7 +21,7 @@ struct alignas(16) BvhHeader {
     uint32_t primCount;
     float rootHi[3];
     uint32_t primType;    // grtPrimitiveType, or kPrimScene
-    const float4* nodes;  // nodeCount x 4 float4
+    const float4* nodes;  // nodeCount 4-wide nodes (kWideWords float4 each), read by traversal
     const void* leaves;   // triangle records / prim IDs / instance records
     uint32_t nodeCount;
     uint32_t geomType;
@@ -33,7 +34,7 @@ static_assert(sizeof(BvhHeader) == 64, "header size");
 // (bounds the parameter range inside it), and the geometry header.
 struct alignas(16) InstanceRecord {
     float4 inv[3];          // object = inv * world (rows; w = translation), rounded from FP64
-    const float4* nodes;    // bottom-level nodes
+    const float4* nodes;    // bottom-level 4-wide nodes
     const void* leaves;     // bottom-level leaves
     uint32_t instanceID;
     uint32_t typeBits;      // geomType (bits 0-23) | primType << 24 | kInstEmpty
@@ -104,7 +105,8 @@ int deviceOf(Context* c);
 // Host-side records of library-owned objects, looked up by handle.
 struct BvhObject {
     BvhHeader* dHeader;  // == handle
-    void* nodes;
+    void* nodes;  // binary nodes (64 B each)
+    void* wide;   // 4-wide nodes (128 B each), one per binary node
     void* leaves;
     int32_t* parents;
     uint32_t* primToLeaf;  // primitive (instance) ID -> sorted position (triangles, scenes)

@@ -204,6 +204,7 @@ struct FitParams {
     uint32_t n;
     const uint32_t* sortedPrims;  // nullptr for a refit (IDs read back from the leaves)
     float4* nodes;
+    float4* wide;  // 4-wide nodes, one per binary internal node (kWideWords float4 each)
     void* leaves;
     uint32_t* primToLeaf;
     const uint32_t* parents;
@@ -220,8 +221,36 @@ __device__ __forceinline__ void writeChildBox(float4* nodes, uint32_t p, uint32_
     n2[2 * 2 + side] = make_float2(b.lo.z, b.hi.z);
 }
 
+// Slot j of 4-wide node w: a child's box and index (kNone with an empty box for an
+// empty slot). Layout of a wide node (kWideWords float4): lo.x of slots 0-3, hi.x,
+// lo.y, hi.y, lo.z, hi.z, the four child words, then one unused float4.
+__device__ __forceinline__ void writeWideSlot(float4* wide, uint32_t w, uint32_t j, const Box3& b, uint32_t child) {
+    float* f = reinterpret_cast<float*>(wide + kWideWords * (size_t)w);
+    f[0 + j] = b.lo.x;
+    f[4 + j] = b.hi.x;
+    f[8 + j] = b.lo.y;
+    f[12 + j] = b.hi.y;
+    f[16 + j] = b.lo.z;
+    f[20 + j] = b.hi.z;
+    reinterpret_cast<uint32_t*>(f)[24 + j] = child;
+}
+__device__ __forceinline__ void writeWideEmpty(float4* wide, uint32_t w, uint32_t j) {
+    Box3 e;
+    e.lo = make_float3(INFINITY, INFINITY, INFINITY);
+    e.hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+    writeWideSlot(wide, w, j, e, kInvalid);
+}
+
 // Leaf k of the sorted order: writes the leaf record and walks up while this thread is
 // the second to reach a node, writing each box into its parent.
+//
+// The same walk writes the 4-wide nodes. Wide node w has the children of binary node w,
+// each internal child replaced by its own two children: slots 2s and 2s+1 hold child
+// s's two children, or child s itself (a leaf) and an empty slot. So the box of a node
+// x whose parent is p (side s) and grandparent g (side s') goes to slot 2s'+s of wide
+// node g, and a leaf's box also to slot 2s of wide node p. Traversal starts at wide node
+// 0 and only reaches the wide nodes of binary nodes at even depth; the others are
+// written all the same.
 template <int KIND>  // 0 triangles, 1 AABB list, 2 instances
 __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
     Box3 b;
@@ -256,30 +285,43 @@ __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
         writeChildBox(P.nodes, 0, 0, b);
         writeChildBox(P.nodes, 0, 1, b);
         P.nodes[3] = make_float4(__uint_as_float(kLeafBit), __uint_as_float(kLeafBit), 0.f, 0.f);
+        writeWideSlot(P.wide, 0, 0, b, kLeafBit);
+        writeWideEmpty(P.wide, 0, 1);
+        writeWideEmpty(P.wide, 0, 2);
+        writeWideEmpty(P.wide, 0, 3);
         P.header->rootLo[0] = b.lo.x, P.header->rootLo[1] = b.lo.y, P.header->rootLo[2] = b.lo.z;
         P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
         return;
     }
     uint32_t pe = __ldcg(P.parents + P.n - 1 + k);
+    uint32_t x = kLeafBit | k;  // the node whose box b is
+    {
+        const uint32_t p = pe >> 1, side = pe & 1u;
+        writeWideSlot(P.wide, p, 2 * side, b, x);
+        writeWideEmpty(P.wide, p, 2 * side + 1);
+    }
     for (;;) {
         const uint32_t p = pe >> 1, side = pe & 1u;
         writeChildBox(P.nodes, p, side, b);
+        const uint32_t ge = p == 0 ? kInvalid : __ldcg(&P.parents[p]);
+        if (ge != kInvalid) writeWideSlot(P.wide, ge >> 1, 2 * (ge & 1u) + side, b, x);
         // acquire-release at GPU scope: releases this box to the sibling's thread if it
         // comes second, and acquires the sibling's box if this thread comes second
         uint32_t prev;
         asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(P.flags + p) : "memory");
         if (prev == 0) return;  // the sibling is still on its way up
-        const float4 x = __ldcg(&P.nodes[4 * (size_t)p + 0]);
-        const float4 y = __ldcg(&P.nodes[4 * (size_t)p + 1]);
-        const float4 z = __ldcg(&P.nodes[4 * (size_t)p + 2]);
-        b.lo = make_float3(fminf(x.x, x.z), fminf(y.x, y.z), fminf(z.x, z.z));
-        b.hi = make_float3(fmaxf(x.y, x.w), fmaxf(y.y, y.w), fmaxf(z.y, z.w));
+        const float4 bx = __ldcg(&P.nodes[4 * (size_t)p + 0]);
+        const float4 by = __ldcg(&P.nodes[4 * (size_t)p + 1]);
+        const float4 bz = __ldcg(&P.nodes[4 * (size_t)p + 2]);
+        b.lo = make_float3(fminf(bx.x, bx.z), fminf(by.x, by.z), fminf(bz.x, bz.z));
+        b.hi = make_float3(fmaxf(bx.y, bx.w), fmaxf(by.y, by.w), fmaxf(bz.y, bz.w));
         if (p == 0) {
             P.header->rootLo[0] = b.lo.x, P.header->rootLo[1] = b.lo.y, P.header->rootLo[2] = b.lo.z;
             P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
             return;
         }
-        pe = __ldcg(&P.parents[p]);
+        x = p;
+        pe = ge;
     }
 }
 

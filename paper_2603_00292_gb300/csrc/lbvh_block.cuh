@@ -24,6 +24,7 @@ struct BlockBuild {
     uint32_t kind;        // 0 triangles, 1 AABB list, 2 instances
     uint32_t pad0;
     float4* nodes;
+    float4* wide;
     void* leaves;
     uint32_t* parents;
     uint32_t* primToLeaf;
@@ -238,6 +239,7 @@ static __device__ __noinline__ void fitRange(const BlockBuild& S, uint32_t begin
     P.n = S.n;
     P.sortedPrims = S.vals[S.passes & 1u];
     P.nodes = S.nodes;
+    P.wide = S.wide;
     P.leaves = S.leaves;
     P.primToLeaf = S.primToLeaf;
     P.parents = S.parents;

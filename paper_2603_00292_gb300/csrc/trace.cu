@@ -357,7 +357,7 @@ template <bool RECOMPUTE, bool PRIV>
 __global__ void shadeBackwardKernel(TraceParams P, ShadeParams S, uint32_t nv) {
     extern __shared__ uint32_t sstack[];
     __shared__ unsigned long long tile;
-    float* priv = reinterpret_cast<float*>(sstack + (RECOMPUTE ? blockDim.x * P.sharedDepth : 0));
+    float* priv = reinterpret_cast<float*>(sstack + (RECOMPUTE ? blockDim.x * traceSmemWords(P.sharedDepth) : 0));
     if (PRIV)
         for (uint32_t j = threadIdx.x; j < 6 * nv; j += blockDim.x) priv[j] = 0.0f;
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -467,7 +467,7 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     if (geom && o->primType == kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
     if (!o->built) return GRT_ERROR_NOT_BUILT;
     *isScene = scene != nullptr;
-    P.target.nodes = (const float4*)o->nodes;
+    P.target.nodes = (const float4*)o->wide;
     P.target.leaves = o->leaves;
     P.target.primType = o->primType;
     P.target.geomType = o->geomType;
@@ -548,7 +548,7 @@ static grtError launchTrace(grtContext ctx, grtScene scene, grtGeometry geom, co
     else
         traceKernelFor<ANY, false>(isScene, &kernel);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(n, bs));
     e = bindGlobalStack(c, opt, L.blocks * bs, P);
@@ -636,7 +636,7 @@ grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom
         traceKernelFor<false, true>(isScene, &kernel);
     else
         traceKernelFor<false, false>(isScene, &kernel);
-    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(rayCount, bs));
     L.blocks = std::max(1, std::min<int>(L.blocks, (int)(capacity / perBlock)));  // the grid shrinks to fit
@@ -659,7 +659,7 @@ grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* optio
     grtError e = resolveOptions(options, &bs, &sh, &gl);
     if (e != GRT_SUCCESS) return e;
     Context* c = asContext(ctx);
-    const size_t smem = (size_t)bs * sh * sizeof(uint32_t);
+    const size_t smem = (size_t)bs * traceSmemWords(sh) * sizeof(uint32_t);
     int threads = 0;
     void (*kernels[])(TraceParams) = {traceKernel<false, false, false>, traceKernel<false, true, false>,
                                       traceKernel<true, false, false>,  traceKernel<true, true, false>,
@@ -679,7 +679,7 @@ grtError grtGetDeviceTarget(grtContext ctx, grtScene scene, grtGeometry geom, gr
     if (!o || (scene != nullptr) != (o->primType == kPrimScene)) return GRT_ERROR_INVALID_PARAMETER;
     if (!o->built) return GRT_ERROR_NOT_BUILT;
     grtDeviceTarget t{};
-    t.nodes = o->nodes;
+    t.nodes = o->wide;
     t.leaves = o->leaves;
     t.primToLeaf = o->primToLeaf;
     t.frames64 = o->inv64;
@@ -773,7 +773,7 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
     void (*kernel)(TraceParams, const uint32_t*, const uint32_t*, uint32_t*, const float4*) =
         count ? aoTraceKernel<true> : aoTraceKernel<false>;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     // scratch after the global stack: the hit count (256 B), the list of hit pixels and
     // their AO frames (48 B each)
@@ -832,7 +832,7 @@ grtError grtShadeLambert(grtContext ctx, grtGeometry geom, const grtRay* rays, c
     S.image = image;
     S.vis = visibility;
     Context* c = asContext(ctx);
-    const size_t smem = (size_t)bs * P.sharedDepth * sizeof(uint32_t);
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, shadeForwardKernel, bs, smem);
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(pixelCount, bs));
     e = bindGlobalStack(c, options, L.blocks * bs, P);
@@ -872,7 +872,7 @@ grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay*
     void (*kernel)(TraceParams, ShadeParams, uint32_t) =
         recompute ? (priv ? shadeBackwardKernel<true, true> : shadeBackwardKernel<true, false>)
                   : (priv ? shadeBackwardKernel<false, true> : shadeBackwardKernel<false, false>);
-    const size_t smem = (recompute ? (size_t)bs * P.sharedDepth * sizeof(uint32_t) : 0) + (priv ? (size_t)nv * 24 : 0);
+    const size_t smem = (recompute ? (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t) : 0) + (priv ? (size_t)nv * 24 : 0);
     if (smem > 48 * 1024) GRT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     // replaying stored hits traces nothing: 8 blocks per SM keep each block's share of

@@ -28,6 +28,10 @@ namespace grt {
 
 constexpr uint32_t kSentinel = 0xFFFFFFFEu;  // stack marker: leave the current instance
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kPendingCap = 8;  // queued leaves per lane (phased traversal)
+// Shared memory per thread of a kernel that runs refillLoop, in words: its stack slice
+// of `depth` entries and its queue of pending leaves.
+__host__ __device__ constexpr uint32_t traceSmemWords(uint32_t depth) { return depth + kPendingCap; }
 constexpr float kEps = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of float32
 // 1 + 2*gamma(3) rounded up, gamma(n) = n*eps/(1 - n*eps)
 constexpr float kFarScale = 1.0000005f;
@@ -135,22 +139,39 @@ __device__ __forceinline__ float localHi(const Level& L, float b) {
     return L.tOff == 0.f ? b : (b - L.tOff) + kEps * (fabsf(b) + fabsf(L.tOff));
 }
 
-// Slab test of both children of a node.
-__device__ __forceinline__ void slab2(const float4& nx, const float4& ny, const float4& nz, const Level& L,
-                                      float tmin, float tmax, bool& h0, bool& h1, float& tn0, float& tn1) {
-    const bool px = L.id.x >= 0.f, py = L.id.y >= 0.f, pz = L.id.z >= 0.f;
-    const float n0x = ((px ? nx.x : nx.y) - L.on.x) * L.id.x, f0x = ((px ? nx.y : nx.x) - L.of.x) * L.id.x;
-    const float n0y = ((py ? ny.x : ny.y) - L.on.y) * L.id.y, f0y = ((py ? ny.y : ny.x) - L.of.y) * L.id.y;
-    const float n0z = ((pz ? nz.x : nz.y) - L.on.z) * L.id.z, f0z = ((pz ? nz.y : nz.x) - L.of.z) * L.id.z;
-    const float n1x = ((px ? nx.z : nx.w) - L.on.x) * L.id.x, f1x = ((px ? nx.w : nx.z) - L.of.x) * L.id.x;
-    const float n1y = ((py ? ny.z : ny.w) - L.on.y) * L.id.y, f1y = ((py ? ny.w : ny.z) - L.of.y) * L.id.y;
-    const float n1z = ((pz ? nz.z : nz.w) - L.on.z) * L.id.z, f1z = ((pz ? nz.w : nz.z) - L.of.z) * L.id.z;
-    tn0 = fmaxf(fmaxf(n0x, n0y), fmaxf(n0z, tmin));
-    tn1 = fmaxf(fmaxf(n1x, n1y), fmaxf(n1z, tmin));
-    const float tf0 = fminf(fminf(f0x, f0y), fminf(f0z, tmax));
-    const float tf1 = fminf(fminf(f1x, f1y), fminf(f1z, tmax));
-    h0 = tn0 <= tf0 * kFarScale;
-    h1 = tn1 <= tf1 * kFarScale;
+// Slab test of the four slots of wide node w. Per axis the near plane is the slot's lo
+// for a non-negative direction (else hi) and its distance (p - on) * id; the far plane
+// likewise with of. A slot is hit when the largest near distance (and tmin) is at most
+// the smallest far distance (and tmax) times Ize's far factor. Returns the mask of
+// slots hit; tn gets each slot's entry distance and c its child word. Empty slots
+// (child kNone) never count as hit.
+__device__ __forceinline__ uint32_t slab4(const float4* nodes, uint32_t w, const Level& L, float tmin, float tmax,
+                                          float tn[4], uint32_t c[4]) {
+    const float4* W = nodes + kWideWords * (size_t)w;
+    // near and far planes of each axis: lo for a non-negative direction, else hi
+    const uint32_t sx = L.id.x >= 0.f ? 0u : 1u, sy = L.id.y >= 0.f ? 0u : 1u, sz = L.id.z >= 0.f ? 0u : 1u;
+    const float4 nx = __ldg(W + sx), fx = __ldg(W + (1u - sx));
+    const float4 ny = __ldg(W + 2 + sy), fy = __ldg(W + 2 + (1u - sy));
+    const float4 nz = __ldg(W + 4 + sz), fz = __ldg(W + 4 + (1u - sz));
+    const float4 cw = __ldg(W + 6);
+    const float px[4] = {nx.x, nx.y, nx.z, nx.w}, qx[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float py[4] = {ny.x, ny.y, ny.z, ny.w}, qy[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float pz[4] = {nz.x, nz.y, nz.z, nz.w}, qz[4] = {fz.x, fz.y, fz.z, fz.w};
+    c[0] = __float_as_uint(cw.x), c[1] = __float_as_uint(cw.y), c[2] = __float_as_uint(cw.z), c[3] = __float_as_uint(cw.w);
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        tn[j] = fmaxf(fmaxf((px[j] - L.on.x) * L.id.x, (py[j] - L.on.y) * L.id.y),
+                      fmaxf((pz[j] - L.on.z) * L.id.z, tmin));
+        const float tf = fminf(fminf((qx[j] - L.of.x) * L.id.x, (qy[j] - L.of.y) * L.id.y),
+                               fminf((qz[j] - L.of.z) * L.id.z, tmax));
+        if (tn[j] <= tf * kFarScale && c[j] != kInvalid) m |= 1u << j;
+    }
+    return m;
+}
+
+__device__ __forceinline__ uint32_t pick4(const uint32_t c[4], uint32_t j) {
+    return j == 0 ? c[0] : j == 1 ? c[1] : j == 2 ? c[2] : c[3];
 }
 
 // Float32 Moller-Trumbore with certified bounds on the three edge values.
@@ -585,6 +606,38 @@ __device__ __forceinline__ bool testLeaf(const TraceParams& P, RayState& s, uint
     return false;
 }
 
+__device__ __forceinline__ void sort2(uint32_t& a, uint32_t& b) {
+    const uint32_t x = min(a, b);
+    b = max(a, b);
+    a = x;
+}
+
+// The slots in mask m go on: the nearest (smallest entry distance) becomes s.next and
+// the others are pushed, farthest first, so that they come off the stack near to far.
+// Keys are the entry distance as an ordered integer with the slot in its two low bits.
+__device__ __forceinline__ void orderChildren(const TraceParams& P, Stack& st, RayState& s, uint32_t m,
+                                              const float tn[4], const uint32_t c[4]) {
+    if (m == 0) return;
+    if ((m & (m - 1u)) == 0) {
+        s.next = pick4(c, (uint32_t)__ffs(m) - 1u);
+        return;
+    }
+    uint32_t k[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[j] = ((m >> j) & 1u) ? ((floatToOrdered(tn[j]) & ~3u) | (uint32_t)j) : kInvalid;
+    sort2(k[0], k[1]);
+    sort2(k[2], k[3]);
+    sort2(k[0], k[2]);
+    sort2(k[1], k[3]);
+    sort2(k[1], k[2]);
+    bool ok = true;
+    if (k[3] != kInvalid) ok &= st.push(pick4(c, k[3] & 3u));
+    if (k[2] != kInvalid) ok &= st.push(pick4(c, k[2] & 3u));
+    ok &= st.push(pick4(c, k[1] & 3u));
+    if (!ok) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+    s.next = pick4(c, k[0] & 3u);
+}
+
 // One traversal step: a node visit (with its leaf tests), an instance entry or an
 // instance exit. Returns true once the ray is finished (s.best is then final).
 template <bool ANY, bool SCENE, bool COUNT>
@@ -613,35 +666,19 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
         return true;
     }
     if (COUNT) ++vis->nodes;
-    const float4* N = s.nodes + 4 * (size_t)s.next;
-    const float4 nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2), nc = __ldg(N + 3);
-    bool h0, h1;
-    float tn0, tn1;
-    slab2(nx, ny, nz, s.L, s.lo, s.hi, h0, h1, tn0, tn1);
-    const uint32_t c0 = __float_as_uint(nc.x), c1 = __float_as_uint(nc.y);
-    if (c1 == c0) h1 = false;  // a one-primitive level stores its leaf twice
+    float tn[4];
+    uint32_t c[4];
+    uint32_t m = slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
     s.next = kNone;
     if (s.inBlas) {
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const bool h = side ? h1 : h0;
-            const uint32_t c = side ? c1 : c0;
-            if (!h || !(c & kLeafBit)) continue;
-            if (testLeaf<ANY, SCENE, COUNT>(P, s, c & ~kLeafBit, vis) && ANY) return true;
+        for (int j = 0; j < 4; ++j) {
+            if (!((m >> j) & 1u) || !(c[j] & kLeafBit)) continue;
+            m &= ~(1u << j);
+            if (testLeaf<ANY, SCENE, COUNT>(P, s, c[j] & ~kLeafBit, vis) && ANY) return true;
         }
-        if (c0 & kLeafBit) h0 = false;
-        if (c1 & kLeafBit) h1 = false;
     }
-    if (h0 && h1) {
-        const bool swap = tn1 < tn0;
-        const uint32_t nearC = swap ? c1 : c0, farC = swap ? c0 : c1;
-        if (!st.push(farC)) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
-        s.next = nearC;
-    } else if (h0) {
-        s.next = c0;
-    } else if (h1) {
-        s.next = c1;
-    }
+    orderChildren(P, st, s, m, tn, c);
     return false;
 }
 
@@ -771,22 +808,22 @@ __device__ __forceinline__ void refillLoopPerRay(const TraceParams& P, Stack& st
 // to finish); DONE: the ray is finished.
 enum : uint32_t { kStNode = 0, kStEnter = 1, kStFlush = 2, kStDone = 3 };
 
-// Leaves of the current bottom level whose boxes the ray hit, waiting to be tested (at
-// most 4, held in registers).
+// Leaves of the current bottom level whose boxes the ray hit, waiting to be tested:
+// at most kPendingCap, in shared memory after the lane's stack slice (entry i at
+// buf[i * blockDim.x]). Kernels running refillLoop reserve traceSmemWords(depth)
+// words of shared memory per thread.
 struct Pending {
-    uint32_t k0, k1, k2, k3, n;
+    uint32_t* buf;
+    uint32_t n;
     __device__ __forceinline__ void add(uint32_t k) {
-        if (n == 0) k0 = k;
-        else if (n == 1) k1 = k;
-        else if (n == 2) k2 = k;
-        else k3 = k;
+        buf[n * blockDim.x] = k;
         ++n;
     }
-    __device__ __forceinline__ uint32_t at(uint32_t i) const { return i == 0 ? k0 : i == 1 ? k1 : i == 2 ? k2 : k3; }
+    __device__ __forceinline__ uint32_t at(uint32_t i) const { return buf[i * blockDim.x]; }
 };
 
 // Node visit that queues hit leaf children instead of testing them (inner children
-// and top-level leaves go on as in stepRay). Requires q.n <= 2.
+// and top-level leaves go on as in stepRay). Requires q.n <= kPendingCap - 4.
 template <bool ANY, bool SCENE, bool COUNT>
 __device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RayState& s, Pending& q, Visits* vis) {
     if (++s.steps > P.maxSteps) {
@@ -797,28 +834,16 @@ __device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RaySt
         return;
     }
     if (COUNT) ++vis->nodes;
-    const float4* N = s.nodes + 4 * (size_t)s.next;
-    const float4 nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2), nc = __ldg(N + 3);
-    bool h0, h1;
-    float tn0, tn1;
-    slab2(nx, ny, nz, s.L, s.lo, s.hi, h0, h1, tn0, tn1);
-    const uint32_t c0 = __float_as_uint(nc.x), c1 = __float_as_uint(nc.y);
-    if (c1 == c0) h1 = false;  // a one-primitive level stores its leaf twice
+    float tn[4];
+    uint32_t c[4];
+    uint32_t m = slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
     s.next = kNone;
     if (s.inBlas) {
-        if (h0 && (c0 & kLeafBit)) q.add(c0 & ~kLeafBit), h0 = false;
-        if (h1 && (c1 & kLeafBit)) q.add(c1 & ~kLeafBit), h1 = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (((m >> j) & 1u) && (c[j] & kLeafBit)) q.add(c[j] & ~kLeafBit), m &= ~(1u << j);
     }
-    if (h0 && h1) {
-        const bool swap = tn1 < tn0;
-        const uint32_t nearC = swap ? c1 : c0, farC = swap ? c0 : c1;
-        if (!st.push(farC)) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
-        s.next = nearC;
-    } else if (h0) {
-        s.next = c0;
-    } else if (h1) {
-        s.next = c1;
-    }
+    orderChildren(P, st, s, m, tn, c);
 }
 
 // The lane's next action after its last one: pops the stack (leaving an instance
@@ -829,7 +854,7 @@ __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, R
     for (;;) {
         if (s.next != kNone) {
             if (SCENE && !s.inBlas && (s.next & kLeafBit)) return kStEnter;
-            return q.n > 2 ? kStFlush : kStNode;
+            return q.n > kPendingCap - 4 ? kStFlush : kStNode;
         }
         if (st.sp == 0) return q.n ? kStFlush : kStDone;
         if (SCENE && st.top() == kSentinel) {
@@ -874,8 +899,7 @@ __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src&
     const unsigned long long total = src.count();
     RayState s;
     Visits v;
-    Pending q;
-    q.n = 0;
+    Pending q{st.sh + st.shDepth * blockDim.x, 0};
     uint32_t item = kNone, state = kStDone;
     bool exhausted = false;
     for (;;) {

@@ -39,7 +39,9 @@ def _bvh_arrays(g):
     leaves = read_device(info.leaves, 48 * n, np.uint32)
     # a one-primitive hierarchy has no parent links (its leaf sits in node 0)
     parents = read_device(info.parents, 4 * (2 * n - 1), np.uint32) if n >= 2 else np.zeros(0, np.uint32)
-    return nodes, leaves, parents
+    m = info.nodeCount  # 4-wide nodes without their unused last float4
+    wide = read_device(info.wideNodes, 128 * m, np.uint32).reshape(m, 32)[:, :28]
+    return nodes, leaves, parents, wide
 
 
 def _run(gpu, work, opts, morton_bits=None):

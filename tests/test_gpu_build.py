@@ -58,6 +58,18 @@ def _oracle_for(case):
     return lo, hi, c
 
 
+def check_wide(info, ref):
+    """The 4-wide nodes the traversal reads equal the oracle's collapse of its own binary
+    LBVH (oracle.wide_nodes), bit for bit: slot boxes and child words."""
+    lo, hi, child = oracle.wide_nodes(ref)
+    m = info.nodeCount
+    assert lo.shape[0] == m
+    w = _read(info.wideNodes, m * 128, np.float32).reshape(m, 32)
+    assert np.array_equal(w[:, 24:28].view(np.uint32), child), "wide children"
+    assert np.array_equal(np.stack([w[:, 0:4], w[:, 8:12], w[:, 16:20]], axis=2), lo), "wide lo"
+    assert np.array_equal(np.stack([w[:, 4:8], w[:, 12:16], w[:, 20:24]], axis=2), hi), "wide hi"
+
+
 def check_bit_exact(g, case, bits):
     """The built geometry `g` of `case` equals the oracle's LBVH bit for bit: sorted
     Morton codes and order (from the build temporary), topology, child boxes, parent
@@ -76,6 +88,7 @@ def check_bit_exact(g, case, bits):
     assert np.array_equal(order, ref["order"]), "stable sort order"
     nodes = _read(info.nodes, info.nodeCount * 64, np.float32).reshape(-1, 16)
     children = nodes.view(np.uint32)[:, 12:14]
+    check_wide(info, ref)
     if n == 1:
         assert children.tolist() == [[LEAF, LEAF]]
         assert np.array_equal(nodes[0, [0, 4, 8]], lo[0]) and np.array_equal(nodes[0, [1, 5, 9]], hi[0])

@@ -180,6 +180,9 @@ def test_batched_soups_full_size(gpu):
         assert np.array_equal(read_device(a.nodes, 64 * a.nodeCount, np.uint32),
                               read_device(b.nodes, 64 * b.nodeCount, np.uint32))
         assert np.array_equal(read_device(a.leaves, 48 * n, np.uint32), read_device(b.leaves, 48 * n, np.uint32))
+        m = a.nodeCount  # 4-wide nodes: all but the unused last float4 of each
+        assert np.array_equal(read_device(a.wideNodes, 128 * m, np.uint32).reshape(m, 32)[:, :28],
+                              read_device(b.wideNodes, 128 * m, np.uint32).reshape(m, 32)[:, :28])
     # the oracle: every ray of 16 seeded scenes (plus the four picked above, their rays
     # sampled when above 100,000) and 1,024 sampled rays of every other scene
     rng = np.random.default_rng(SEED)

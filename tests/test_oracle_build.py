@@ -205,3 +205,82 @@ def test_triangle_aabbs_and_centroids():
 def test_sah_cost_of_two_unit_boxes():
     # root [0,2]x[0,1]x[0,1] area 10; two unit children are leaves: cost = 10/10 = 1
     assert oracle.sah_cost(np.array([[0, 0, 0]], np.float32), np.array([[2, 1, 1]], np.float32)) == 1.0
+
+
+# ---------------------------------------------------------------- 4-wide nodes
+def _tree_dict(cl, cr, leaf_lo, leaf_hi):
+    nlo, nhi = oracle.fit(cl, cr, leaf_lo, leaf_hi)
+    return dict(childL=cl, childR=cr, node_lo=nlo, node_hi=nhi, leaf_lo=leaf_lo, leaf_hi=leaf_hi)
+
+
+def test_wide_nodes_hand_derived():
+    # five equal keys: node 0 = (node 3, leaf 4), node 3 = (node 1, node 2),
+    # node 1 = (leaf 0, leaf 1), node 2 = (leaf 2, leaf 3) (see the duplicate-key test)
+    cl, cr, _, _ = oracle.topology(np.zeros(5, np.uint64), 32)
+    leaf_lo = np.array([[i, 0, 0] for i in range(5)], np.float32)
+    leaf_hi = leaf_lo + np.float32(0.5)
+    lo, hi, child = oracle.wide_nodes(_tree_dict(cl, cr, leaf_lo, leaf_hi))
+    L = 0x80000000
+    E = 0xFFFFFFFF
+    assert child.tolist() == [[1, 2, L | 4, E], [L | 0, E, L | 1, E], [L | 2, E, L | 3, E],
+                              [L | 0, L | 1, L | 2, L | 3]]
+    # node 0: slot 0 = node 1 = leaves 0-1, slot 1 = node 2 = leaves 2-3, slot 2 = leaf 4
+    assert lo[0, 0].tolist() == [0, 0, 0] and hi[0, 0].tolist() == [1.5, 0.5, 0.5]
+    assert lo[0, 1].tolist() == [2, 0, 0] and hi[0, 1].tolist() == [3.5, 0.5, 0.5]
+    assert lo[0, 2].tolist() == [4, 0, 0] and hi[0, 2].tolist() == [4.5, 0.5, 0.5]
+    assert np.all(lo[0, 3] == np.inf) and np.all(hi[0, 3] == -np.inf)
+    assert lo[3, 3].tolist() == [3, 0, 0] and hi[3, 3].tolist() == [3.5, 0.5, 0.5]
+
+
+def test_wide_nodes_single_primitive():
+    d = dict(leaf_lo=np.array([[1, 2, 3]], np.float32), leaf_hi=np.array([[4, 5, 6]], np.float32))
+    lo, hi, child = oracle.wide_nodes(d)
+    assert child.tolist() == [[0x80000000, 0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF]]
+    assert lo[0, 0].tolist() == [1, 2, 3] and hi[0, 0].tolist() == [4, 5, 6]
+    assert np.all(lo[0, 1:] == np.inf) and np.all(hi[0, 1:] == -np.inf)
+
+
+@pytest.mark.parametrize("level", [1, 3])
+def test_wide_nodes_invariants(level):
+    mesh = scenegen.icosphere(level)
+    tlo, thi, c = oracle.triangle_aabbs(mesh.vertices, mesh.indices)
+    r = oracle.lbvh(tlo, thi, c, 10)
+    n = tlo.shape[0]
+    lo, hi, child = oracle.wide_nodes(r)
+    assert child.shape == (n - 1, 4)
+    for k in range(n - 1):
+        used = child[k] != 0xFFFFFFFF
+        # the slots cover exactly the binary node's box
+        assert np.array_equal(lo[k][used].min(axis=0), r["node_lo"][k])
+        assert np.array_equal(hi[k][used].max(axis=0), r["node_hi"][k])
+        # an empty slot is always the second of a pair whose first is a leaf
+        for j in (1, 3):
+            if not used[j]:
+                assert child[k, j - 1] & 0x80000000
+        assert used[0] and used[2]
+    # a walk from wide node 0 reaches every leaf exactly once, through the wide nodes of
+    # binary nodes at even depth only
+    seen = np.zeros(n, int)
+    visited = []
+    stack = [0]
+    while stack:
+        k = stack.pop()
+        visited.append(k)
+        for cc in child[k]:
+            if cc == 0xFFFFFFFF:
+                continue
+            if cc & 0x80000000:
+                seen[cc & 0x7FFFFFFF] += 1
+            else:
+                stack.append(int(cc))
+    assert (seen == 1).all()
+    parent = np.full(n - 1, -1)
+    for k in range(n - 1):
+        for cc in (r["childL"][k], r["childR"][k]):
+            if cc >= 0:
+                parent[cc] = k
+    for k in visited:  # even depth: the number of binary edges up to the root
+        d, x = 0, k
+        while parent[x] >= 0:
+            x, d = parent[x], d + 1
+        assert d % 2 == 0
