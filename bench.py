@@ -117,18 +117,36 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def source_hash() -> str:
-    h = hashlib.sha256()
+# The translation unit that holds each kernel whose DRAM traffic bench.py reports.
+KERNEL_UNITS = {"aoTraceKernel": "trace.cu", "traceKernel<closest, scene>": "trace.cu",
+                "shadeBackwardKernel<false, true>": "trace.cu", "batchKernel": "batch.cu"}
+
+
+def source_hash(unit: str) -> str:
+    """Hash of a translation unit of the library as compiled: the .cu file, every header it
+    includes (transitively, by #include "..."), and the build script with its flags."""
     csrc = os.path.join(ROOT, "paper_2603_00292_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    seen, todo = [], [os.path.join(csrc, unit)]
+    while todo:
+        f = os.path.normpath(todo.pop())
+        if f in seen:
+            continue
+        seen.append(f)
+        with open(f) as fh:
+            for line in fh:
+                line = line.strip()
+                if line.startswith('#include "'):
+                    todo.append(os.path.join(os.path.dirname(f), line.split('"')[1]))
+    h = hashlib.sha256()
+    for f in sorted(seen) + [os.path.join(ROOT, "paper_2603_00292_gb300", "build.py")]:
+        with open(f, "rb") as fh:
+            h.update(os.path.relpath(f, ROOT).encode() + fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken from the current sources (else None)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
+    from the kernel's current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -136,7 +154,7 @@ def ncu_traffic(kernel: str):
     except Exception:
         return None
     e = d.get(kernel)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(KERNEL_UNITS[kernel]):
         return None
     return e.get("dram_bytes_per_launch")
 

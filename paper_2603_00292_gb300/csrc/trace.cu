@@ -20,6 +20,11 @@ __global__ void traceKernel(TraceParams P) {
 
 // The closest hits' t, u, v recomputed in FP64, one thread per ray after traversal so
 // that every lane of a warp takes part (FP64 is far slower than FP32 on this GPU).
+// One thread per ray: the hit records are read with every load in flight at once, and
+// the FP64 work of the hits (a few percent of the rays on a camera view) stays dense in
+// the warps that have them.
+static unsigned refineBlocks(uint32_t rays) { return std::max(1u, ceilDiv(rays, 256)); }
+
 __global__ void __launch_bounds__(256) refineKernel(TraceParams P) {
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < P.count; r += gridDim.x * blockDim.x) refineHit(P, r);
 }
@@ -556,7 +561,7 @@ static grtError launchTrace(grtContext ctx, grtScene scene, grtGeometry geom, co
     P.counter = nextCounter(c);
     GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
     kernel<<<L.blocks, bs, smem, s>>>(P);
-    if (!ANY) refineKernel<<<smCount(c) * 4, 256, 0, s>>>(P);
+    if (!ANY) refineKernel<<<refineBlocks(n), 256, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
     noteLaunches(ANY ? 1 : 2);
     return GRT_SUCCESS;
@@ -646,7 +651,7 @@ grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom
     cudaStream_t s = (cudaStream_t)stream;
     GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));  // the work counter starts at zero
     kernel<<<L.blocks, bs, smem, s>>>(P);
-    refineKernel<<<smCount(c) * 4, 256, 0, s>>>(P);
+    refineKernel<<<refineBlocks(rayCount), 256, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
     noteLaunches(2);
     return GRT_SUCCESS;
