@@ -221,24 +221,20 @@ __device__ __forceinline__ void writeChildBox(float4* nodes, uint32_t p, uint32_
     n2[2 * 2 + side] = make_float2(b.lo.z, b.hi.z);
 }
 
-// Slot j of 4-wide node w: a child's box and index (kNone with an empty box for an
-// empty slot). Layout of a wide node (kWideWords float4): lo.x of slots 0-3, hi.x,
-// lo.y, hi.y, lo.z, hi.z, the four child words, then one unused float4.
-__device__ __forceinline__ void writeWideSlot(float4* wide, uint32_t w, uint32_t j, const Box3& b, uint32_t child) {
-    float* f = reinterpret_cast<float*>(wide + kWideWords * (size_t)w);
-    f[0 + j] = b.lo.x;
-    f[4 + j] = b.hi.x;
-    f[8 + j] = b.lo.y;
-    f[12 + j] = b.hi.y;
-    f[16 + j] = b.lo.z;
-    f[20 + j] = b.hi.z;
-    reinterpret_cast<uint32_t*>(f)[24 + j] = child;
-}
-__device__ __forceinline__ void writeWideEmpty(float4* wide, uint32_t w, uint32_t j) {
-    Box3 e;
-    e.lo = make_float3(INFINITY, INFINITY, INFINITY);
-    e.hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
-    writeWideSlot(wide, w, j, e, kInvalid);
+// Slots 2t and 2t+1 of 4-wide node w: two boxes (a, b) and their child words (kNone
+// with an empty box for an empty slot). Layout of a wide node (kWideWords float4): lo.x
+// of slots 0-3, hi.x, lo.y, hi.y, lo.z, hi.z, the four child words, then one unused
+// float4; a slot pair is one 8-byte store per row.
+__device__ __forceinline__ void writeWidePair(float4* wide, uint32_t w, uint32_t t, float3 alo, float3 ahi, uint32_t ca,
+                                              float3 blo, float3 bhi, uint32_t cb) {
+    float2* f = reinterpret_cast<float2*>(wide + kWideWords * (size_t)w) + t;
+    f[0] = make_float2(alo.x, blo.x);
+    f[2] = make_float2(ahi.x, bhi.x);
+    f[4] = make_float2(alo.y, blo.y);
+    f[6] = make_float2(ahi.y, bhi.y);
+    f[8] = make_float2(alo.z, blo.z);
+    f[10] = make_float2(ahi.z, bhi.z);
+    reinterpret_cast<uint2*>(f)[12] = make_uint2(ca, cb);
 }
 
 // Leaf k of the sorted order: writes the leaf record and walks up while this thread is
@@ -246,11 +242,13 @@ __device__ __forceinline__ void writeWideEmpty(float4* wide, uint32_t w, uint32_
 //
 // The same walk writes the 4-wide nodes. Wide node w has the children of binary node w,
 // each internal child replaced by its own two children: slots 2s and 2s+1 hold child
-// s's two children, or child s itself (a leaf) and an empty slot. So the box of a node
-// x whose parent is p (side s) and grandparent g (side s') goes to slot 2s'+s of wide
-// node g, and a leaf's box also to slot 2s of wide node p. Traversal starts at wide node
-// 0 and only reaches the wide nodes of binary nodes at even depth; the others are
-// written all the same.
+// s's two children, or child s itself (a leaf) and an empty slot. The thread that
+// completes binary node p (the second to arrive) reads its two child boxes and writes
+// them as slots 2s'+0/1 of wide node g, p's parent (p being g's child s'), and each
+// leaf child s of p as slot pair 2s of wide node p. These stores come after the atomic,
+// so its release orders only the binary box the sibling's thread reads. Traversal starts
+// at wide node 0 and only reaches the wide nodes of binary nodes at even depth; the
+// others are written all the same.
 template <int KIND>  // 0 triangles, 1 AABB list, 2 instances
 __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
     Box3 b;
@@ -285,26 +283,17 @@ __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
         writeChildBox(P.nodes, 0, 0, b);
         writeChildBox(P.nodes, 0, 1, b);
         P.nodes[3] = make_float4(__uint_as_float(kLeafBit), __uint_as_float(kLeafBit), 0.f, 0.f);
-        writeWideSlot(P.wide, 0, 0, b, kLeafBit);
-        writeWideEmpty(P.wide, 0, 1);
-        writeWideEmpty(P.wide, 0, 2);
-        writeWideEmpty(P.wide, 0, 3);
+        const float3 elo = make_float3(INFINITY, INFINITY, INFINITY), ehi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+        writeWidePair(P.wide, 0, 0, b.lo, b.hi, kLeafBit, elo, ehi, kInvalid);
+        writeWidePair(P.wide, 0, 1, elo, ehi, kInvalid, elo, ehi, kInvalid);
         P.header->rootLo[0] = b.lo.x, P.header->rootLo[1] = b.lo.y, P.header->rootLo[2] = b.lo.z;
         P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
         return;
     }
     uint32_t pe = __ldcg(P.parents + P.n - 1 + k);
-    uint32_t x = kLeafBit | k;  // the node whose box b is
-    {
-        const uint32_t p = pe >> 1, side = pe & 1u;
-        writeWideSlot(P.wide, p, 2 * side, b, x);
-        writeWideEmpty(P.wide, p, 2 * side + 1);
-    }
     for (;;) {
         const uint32_t p = pe >> 1, side = pe & 1u;
         writeChildBox(P.nodes, p, side, b);
-        const uint32_t ge = p == 0 ? kInvalid : __ldcg(&P.parents[p]);
-        if (ge != kInvalid) writeWideSlot(P.wide, ge >> 1, 2 * (ge & 1u) + side, b, x);
         // acquire-release at GPU scope: releases this box to the sibling's thread if it
         // comes second, and acquires the sibling's box if this thread comes second
         uint32_t prev;
@@ -313,6 +302,15 @@ __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
         const float4 bx = __ldcg(&P.nodes[4 * (size_t)p + 0]);
         const float4 by = __ldcg(&P.nodes[4 * (size_t)p + 1]);
         const float4 bz = __ldcg(&P.nodes[4 * (size_t)p + 2]);
+        const float4 bc = __ldcg(&P.nodes[4 * (size_t)p + 3]);
+        const uint32_t ge = p == 0 ? kInvalid : __ldcg(&P.parents[p]);
+        const uint32_t c0 = __float_as_uint(bc.x), c1 = __float_as_uint(bc.y);
+        const float3 lo0 = make_float3(bx.x, by.x, bz.x), hi0 = make_float3(bx.y, by.y, bz.y);
+        const float3 lo1 = make_float3(bx.z, by.z, bz.z), hi1 = make_float3(bx.w, by.w, bz.w);
+        const float3 elo = make_float3(INFINITY, INFINITY, INFINITY), ehi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+        if (c0 & kLeafBit) writeWidePair(P.wide, p, 0, lo0, hi0, c0, elo, ehi, kInvalid);
+        if (c1 & kLeafBit) writeWidePair(P.wide, p, 1, lo1, hi1, c1, elo, ehi, kInvalid);
+        if (ge != kInvalid) writeWidePair(P.wide, ge >> 1, ge & 1u, lo0, hi0, c0, lo1, hi1, c1);
         b.lo = make_float3(fminf(bx.x, bx.z), fminf(by.x, by.z), fminf(bz.x, bz.z));
         b.hi = make_float3(fmaxf(bx.y, bx.w), fmaxf(by.y, by.w), fmaxf(bz.y, bz.w));
         if (p == 0) {
@@ -320,7 +318,6 @@ __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
             P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
             return;
         }
-        x = p;
         pe = ge;
     }
 }
