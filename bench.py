@@ -214,7 +214,7 @@ def run_grt(args, rank, world, local):
 
     import paper_2603_00292_gb300 as grt
     from paper_2603_00292_gb300 import build as grt_build
-    from paper_2603_00292_gb300.objects import Context, Geometry, Scene, device_tensor, new_hits, new_rays
+    from paper_2603_00292_gb300.objects import Context, FuncTable, Geometry, Scene, device_tensor, new_hits, new_rays
 
     torch.cuda.set_device(local)
     dist = None
@@ -295,6 +295,56 @@ def run_grt(args, rank, world, local):
     (total_s,) = max_over_ranks([total_s], dist)
     value = job_throughput(rays_per_step * args.steps, world, total_s) / 1e6
 
+    # --------------------------------------------------- the traversal features on the same scene
+    # (device-resident, L2 flushed before each timed launch, CUDA events, median of 10):
+    # instance masks (alternate instances carry mask 1 or 2; the rays carry mask 1),
+    # a primitive-mask intersection filter that rejects every other triangle, and every
+    # hit of each primary ray (up to 4 stored per ray).
+    def timed(fn, reps=10):
+        out = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            fn()
+        for _ in range(reps):
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    masked = Scene(ctx, [geom.handle] * WORKLOAD["instances"], frames,
+                   masks=[1 + (k & 1) for k in range(WORKLOAD["instances"])]).build(sh)
+    mopt = grt.trace_options(ray_mask=1)
+    mhits = new_hits(npix)
+
+    def masked_step():
+        grt.grtTraceClosest(ctx.handle, masked.handle, None, rays, npix, mhits, None, mopt, sh)
+        grt.grtTraceAmbientOcclusion(ctx.handle, masked.handle, rays, mhits, npix, spp, seed, length, ao, mopt, sh)
+
+    keep = torch.full(((mesh.indices.shape[0] + 31) // 32,), 0x55555555, dtype=torch.int32, device="cuda")
+    table = FuncTable(ctx)  # triangles 0, 2, 4, ... stand
+    table.set(0, 0, grt.GRT_INTERSECT_NONE, None, grt.GRT_FILTER_PRIMITIVE_MASK, keep)
+    fhits = new_hits(npix)
+    kmax = 4
+    ahits = new_hits(npix * kmax)
+    acount = torch.empty(npix, dtype=torch.int32, device="cuda")
+    ms_mask = timed(masked_step)
+    ms_filter = timed(lambda: grt.grtTraceClosest(ctx.handle, scene.handle, None, rays, npix, fhits, table.handle,
+                                                  None, sh))
+    ms_all = timed(lambda: grt.grtTraceAllHits(ctx.handle, scene.handle, None, rays, npix, ahits, kmax, acount,
+                                               None, None, sh))
+    torch.cuda.synchronize()
+    mhit = int((mhits[:, 1].view(torch.int32) != -1).sum().item())
+    all_found = int(acount.sum().item())
+    features = {"instance_mask_half": {"closest_plus_ao_ms": round(ms_mask, 4), "primary_hits": mhit,
+                                       "mrays_per_s": round((npix + spp * mhit) / ms_mask / 1e3, 1)},
+                "filter_half_closest_ms": round(ms_filter, 4),
+                "all_hits_primary": {"ms": round(ms_all, 4), "hits_found": all_found,
+                                     "mrays_per_s": round(npix / ms_all / 1e3, 1)}}
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+
     # --------------------------------------------------- traversal work per ray (counting pass)
     cnt = grt.trace_options(flags=grt.GRT_TRACE_FLAG_COUNT)
     grt.grtGetTraceStatistics(ctx.handle, sh)
@@ -366,7 +416,8 @@ def run_grt(args, rank, world, local):
             "config": dict(WORKLOAD, rays_per_step=rays_per_step, primary_hits=nhit, l2="flushed between steps",
                            parallelism=f"replicas{world}"),
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "kernel_ms": {"closest": round(statistics.mean(closest_ms), 4), "ao": round(statistics.mean(ao_ms), 4)}}
+            "kernel_ms": {"closest": round(statistics.mean(closest_ms), 4), "ao": round(statistics.mean(ao_ms), 4)},
+            "features": features}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle(sc, cam, length, seed, args.cpu_seconds)
     if rank == 0:

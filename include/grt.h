@@ -6,7 +6,7 @@
  * triangle mesh or from a list of AABBs of custom primitives (Sec. 7.2); a two-level
  * scene built from instances of geometries with SRT frames (Sec. 7.3); a function
  * table that maps (geometry type, ray type) to a custom intersection (Sec. 7.4); and
- * closest-hit / any-hit queries that write hit records (Sec. 7.6).
+ * closest-hit / any-hit queries that write hit records (Sec. 7.5).
  *
  * Conventions for every call:
  *  - Every function returns grtError. GRT_SUCCESS is 0.
@@ -151,7 +151,8 @@ typedef enum grtInstanceType { GRT_INSTANCE_GEOMETRY = 0 } grtInstanceType;
 
 typedef struct grtInstance { /* 16 bytes */
     uint32_t type;           /* grtInstanceType */
-    uint32_t mask;           /* reserved, 0 */
+    uint32_t mask;           /* visibility mask (Sec. 7.5): a ray sees the instance only when
+                                mask & the ray mask != 0; 0 = all bits set */
     grtGeometry geometry;
 } grtInstance;
 
@@ -186,10 +187,20 @@ typedef enum grtIntersectFunc {
     GRT_INTERSECT_SPHERE = 1 /* built-in: data = float4 {centre.xyz, radius} per primitive */
 } grtIntersectFunc;
 
+/* Intersection filters (Sec. 7.6): called on every hit the intersector (or the
+ * built-in triangle test) accepts, for triangles and custom primitives alike; a hit the
+ * filter rejects is skipped and traversal goes on, as for alpha masking. */
+typedef enum grtFilterFunc {
+    GRT_FILTER_NONE = 0,          /* every hit stands */
+    GRT_FILTER_PRIMITIVE_MASK = 1 /* built-in: data = uint32 bit array over primitive IDs; a hit on
+                                     primitive p stands only when bit p (word p / 32, bit p % 32) is set */
+} grtFilterFunc;
+
 typedef struct grtFuncDataSet {
     uint32_t intersectFunc;        /* grtIntersectFunc */
-    uint32_t reserved;
+    uint32_t filterFunc;           /* grtFilterFunc */
     const void* intersectFuncData; /* device pointer handed to the intersector */
+    const void* filterFuncData;    /* device pointer handed to the filter */
 } grtFuncDataSet;
 
 /* A numRayTypes x numGeomTypes table, row-major (row = ray type), as the paper's
@@ -236,6 +247,7 @@ typedef struct grtTraceOptions {
     void* globalStack;         /* optional caller-owned device buffer for the global entries; NULL = the
                                   context's own (then traces on one context must not overlap in time) */
     size_t globalStackBytes;   /* size of globalStack; must be >= grtGetTraceGlobalStackSize */
+    uint32_t rayMask;          /* ray mask (Sec. 7.5), ANDed with each instance's mask; 0 = all bits set */
 } grtTraceOptions;
 
 /* Bytes of global stack a trace with `options` (NULL = defaults) needs. */
@@ -247,6 +259,18 @@ grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* optio
  * NULL (defaults). */
 grtError grtTraceClosest(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
                          grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream);
+/* Every hit of each ray (Sec. 7.5: all intersections, as repeated getNextHit() calls on
+ * the any-hit traversal object return them): each (instance, primitive) whose exact
+ * intersection lies in [minT, maxT], once. Ray r's first maxHitsPerRay hits, in
+ * traversal order (not sorted by t) with t, u, v recomputed in FP64, go to
+ * hits[r * maxHitsPerRay ...]; its remaining slots are set to misses; hitCounts[r]
+ * (device, rayCount uint32) gets the number of hits found, which may exceed
+ * maxHitsPerRay. Instance masks, the ray mask and intersection filters apply as for
+ * the other queries. One thread per ray with a 96-entry local stack (a deeper walk
+ * latches GRT_ERROR_STACK_OVERFLOW); maxHitsPerRay = 0 is GRT_ERROR_INVALID_PARAMETER. */
+grtError grtTraceAllHits(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
+                         grtHit* hits, uint32_t maxHitsPerRay, uint32_t* hitCounts, grtFuncTable table,
+                         const grtTraceOptions* options, void* stream);
 /* The same closest-hit query as grtTraceClosest for callers that must not allocate
  * device memory: code running while a stream is being captured into a CUDA graph
  * (where cudaMalloc is not allowed), code whose memory is fully owned by another
@@ -280,9 +304,9 @@ grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom
 grtError grtTraceAnyHit(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
                         grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream);
 
-/* ---------------------------------------------------------------- device-side queries (Sec. 7.6) */
+/* ---------------------------------------------------------------- device-side queries (Sec. 7.5) */
 /* Everything a user CUDA kernel needs to trace rays itself through grt_device.cuh (the
- * paper's device traversal object, Sec. 7.6): device pointers of the target's arrays,
+ * paper's device traversal object, Sec. 7.5): device pointers of the target's arrays,
  * of a scene's instance frames and of the function table. Plain data: pass it to a
  * kernel by value. Valid while the target, the table and the context live and the
  * target is not rebuilt with a different primitive count. */
@@ -373,7 +397,7 @@ grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay*
 /* ---------------------------------------------------------------- batched build + trace */
 /* Many independent triangle geometries, each with its own ray batch, built and traced
  * (closest hit) in one persistent launch that takes work items from a device queue.
- * The paper builds and traces one geometry per call (Sec. 7.2-7.6) and has no batched
+ * The paper builds and traces one geometry per call (Sec. 7.2-7.5) and has no batched
  * form; each geometry ends up exactly as grtBuildGeometry(BUILD) would leave it and each
  * hit record exactly as grtTraceClosest would write it. */
 typedef struct grtBatch_t* grtBatch;

@@ -62,7 +62,12 @@ def lib() -> ctypes.CDLL:
             L.oracle_scene_add_spheres.argtypes = [P, P, i64]
             L.oracle_scene_add_instance.argtypes = [P, ctypes.c_int, P]
             L.oracle_scene_build.argtypes = [P]
-            L.oracle_trace.argtypes = [P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+            L.oracle_trace.argtypes = [P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, P, P, P,
+                                       P, P]
+            L.oracle_scene_set_instance_mask.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32]
+            L.oracle_scene_set_prim_filter.argtypes = [P, ctypes.c_int, P]
+            L.oracle_all_hits.argtypes = [P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, i64, P, P, P, P, P,
+                                          P]
             L.oracle_intersect_prim.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
             L.oracle_min_edge_margin.argtypes = [P, P]
             L.oracle_min_edge_margin.restype = ctypes.c_double
@@ -282,15 +287,44 @@ class Scene:
             f = _c(frame, np.float32).reshape(10)
             self._L.oracle_scene_add_instance(self._h, geom, _p(f))
 
+    def set_prim_filter(self, geom: int, bits):
+        """Intersection filter (Sec. 7.6) of geometry `geom` as a primitive mask: hits on
+        primitive i stand only when bit i of `bits` (uint32 words, word i // 32) is set."""
+        b = _c(bits, np.uint32)
+        self._keep.append(b)
+        self._L.oracle_scene_set_prim_filter(self._h, geom, _p(b))
+
+    def set_instance_mask(self, inst: int, mask: int):
+        """Instance `inst`'s 32-bit visibility mask (Sec. 7.5; default all bits set): a ray
+        sees the instance only when the mask ANDed with the ray's mask is nonzero."""
+        self._L.oracle_scene_set_instance_mask(self._h, inst, mask & 0xFFFFFFFF)
+
     def build(self):
         self._L.oracle_scene_build(self._h)
 
-    def trace(self, rays, any_hit: bool = False, bvh: bool = True, threads: int = 0) -> Hits:
+    def trace(self, rays, any_hit: bool = False, bvh: bool = True, threads: int = 0,
+              ray_mask: int = 0xFFFFFFFF) -> Hits:
         r = _c(rays, np.float32).reshape(-1, 8)
         h = Hits(r.shape[0])
-        self._L.oracle_trace(self._h, _p(r), r.shape[0], int(any_hit), int(bvh), threads, _p(h.inst), _p(h.prim),
-                             _p(h.t), _p(h.u), _p(h.v))
+        self._L.oracle_trace(self._h, _p(r), r.shape[0], int(any_hit), int(bvh), threads, ray_mask & 0xFFFFFFFF,
+                             _p(h.inst), _p(h.prim), _p(h.t), _p(h.u), _p(h.v))
         return h
+
+    def all_hits(self, rays, max_hits: int, bvh: bool = True, threads: int = 0, ray_mask: int = 0xFFFFFFFF):
+        """Every hit of each ray (Sec. 7.5), sorted by (t, instance, primitive): arrays
+        inst, prim, t, u, v of shape (n, max_hits) (misses after the last hit) and the
+        number of hits per ray (n,), which may exceed max_hits."""
+        r = _c(rays, np.float32).reshape(-1, 8)
+        n = r.shape[0]
+        inst = np.empty((n, max_hits), np.uint32)
+        prim = np.empty((n, max_hits), np.uint32)
+        t = np.empty((n, max_hits))
+        u = np.empty((n, max_hits))
+        v = np.empty((n, max_hits))
+        cnt = np.empty(n, np.int64)
+        self._L.oracle_all_hits(self._h, _p(r), n, int(bvh), threads, ray_mask & 0xFFFFFFFF, max_hits, _p(inst),
+                                _p(prim), _p(t), _p(u), _p(v), _p(cnt))
+        return inst, prim, t, u, v, cnt
 
     def intersect_prim(self, ray, inst: int, prim: int):
         """(hit, t, u, v) of one (instance, primitive) in FP64."""

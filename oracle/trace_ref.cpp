@@ -2,7 +2,7 @@
 // any-hit queries in FP64.
 //
 // Definitions followed:
-//  * ray R(t) = o + t d with t in [minT, maxT] (paper Eq. 1 and Sec. 7.6's ray
+//  * ray R(t) = o + t d with t in [minT, maxT] (paper Eq. 1 and Sec. 7.5's ray
 //    fields); both ends inclusive;
 //  * triangles are double-sided with inclusive edges (Sec. 3.1 rejects only a
 //    negative edge function and tests no orientation). Two formulas are provided:
@@ -164,7 +164,12 @@ struct Geom {
         }
         return bx;
     }
+    // Intersection filter (Sec. 7.6) as a primitive mask: bit i of keep (word i / 32)
+    // says whether hits on primitive i stand; empty = every hit stands.
+    std::vector<uint32_t> keep;
+    bool accepts(size_t i) const { return keep.empty() || ((keep[i >> 5] >> (i & 31)) & 1u); }
     bool intersect(const RayD& r, size_t i, double& t, double& u, double& v) const {
+        if (!accepts(i)) return false;
         if (kind == 0) return mt(r, a[i], b[i], c[i], t, u, v);
         u = v = 0.0;
         return sphere(r, centre[i], radius[i], t);
@@ -231,6 +236,7 @@ struct Instance {
     int geom = 0;
     Affine fwd, inv;
     Box world;
+    uint32_t mask = 0xFFFFFFFFu;  // visibility mask (Sec. 7.5): tested against the ray mask with AND
 };
 
 struct Scene {
@@ -304,14 +310,57 @@ void trace_geom(const Geom& g, const RayD& r, bool any, bool use_bvh, uint32_t i
     }
 }
 
-void trace_one(const Scene& S, const RayD& wr, bool any, bool use_bvh, HitD& best) {
+void trace_one(const Scene& S, const RayD& wr, bool any, bool use_bvh, uint32_t ray_mask, HitD& best) {
     for (size_t i = 0; i < S.inst.size(); ++i) {
         const Instance& I = S.inst[i];
+        if ((I.mask & ray_mask) == 0) continue;  // the instance is invisible to this ray
         if (use_bvh && !box_hit(I.world, wr, any ? wr.tmax : std::min(wr.tmax, best.t))) continue;
         RayD r{I.inv.point(wr.o), I.inv.vector(wr.d), wr.tmin, wr.tmax};
         trace_geom(S.geoms[(size_t)I.geom], r, any, use_bvh, (uint32_t)i, best);
         if (any && best.prim != NONE) return;
     }
+}
+
+// Every valid intersection of one world ray: (instance, primitive, t, u, v) for each
+// primitive of each visible instance whose exact intersection lies in [tmin, tmax].
+struct HitRec {
+    double t, u, v;
+    uint32_t inst, prim;
+};
+void all_hits_one(const Scene& S, const RayD& wr, bool use_bvh, uint32_t ray_mask, std::vector<HitRec>& out) {
+    for (size_t i = 0; i < S.inst.size(); ++i) {
+        const Instance& I = S.inst[i];
+        if ((I.mask & ray_mask) == 0) continue;
+        if (use_bvh && !box_hit(I.world, wr, wr.tmax)) continue;
+        const RayD r{I.inv.point(wr.o), I.inv.vector(wr.d), wr.tmin, wr.tmax};
+        const Geom& g = S.geoms[(size_t)I.geom];
+        auto consider = [&](uint32_t p) {
+            double t, u, v;
+            if (g.intersect(r, p, t, u, v)) out.push_back(HitRec{t, u, v, (uint32_t)i, p});
+        };
+        if (!use_bvh) {
+            for (size_t p = 0; p < g.count(); ++p) consider((uint32_t)p);
+            continue;
+        }
+        if (g.nodes.empty()) continue;
+        std::vector<int32_t> st{0};
+        while (!st.empty()) {
+            const auto& nd = g.nodes[(size_t)st.back()];
+            st.pop_back();
+            if (!box_hit(nd.box, r, r.tmax)) continue;
+            if (nd.left < 0) {
+                for (uint32_t k = nd.first; k < nd.first + nd.count; ++k) consider(g.prims[k]);
+            } else {
+                st.push_back(nd.left);
+                st.push_back(nd.right);
+            }
+        }
+    }
+    std::sort(out.begin(), out.end(), [](const HitRec& a, const HitRec& b) {
+        if (a.t != b.t) return a.t < b.t;
+        if (a.inst != b.inst) return a.inst < b.inst;
+        return a.prim < b.prim;
+    });
 }
 
 template <class F>
@@ -391,6 +440,20 @@ void oracle_scene_add_instance(void* s, int geom, const float* frame) {
     S->built = false;
 }
 
+// Gives geometry `geom` a primitive-mask filter: hits on primitive i stand only when bit
+// i of `bits` (word i / 32, bit i % 32) is set.
+void oracle_scene_set_prim_filter(void* s, int geom, const uint32_t* bits) {
+    Scene* S = (Scene*)s;
+    Geom& g = S->geoms[(size_t)geom];
+    g.keep.assign(bits, bits + (g.count() + 31) / 32);
+}
+
+// Sets instance `inst`'s 32-bit visibility mask (default: all bits set).
+void oracle_scene_set_instance_mask(void* s, uint32_t inst, uint32_t mask) {
+    Scene* S = (Scene*)s;
+    if (inst < S->inst.size()) S->inst[inst].mask = mask;
+}
+
 void oracle_scene_build(void* s) {
     Scene* S = (Scene*)s;
     for (auto& g : S->geoms) g.build();
@@ -408,20 +471,45 @@ void oracle_scene_build(void* s) {
     S->built = true;
 }
 
-// rays: n x 8 float32 {o.xyz, minT, d.xyz, maxT}. Outputs per ray: instance ID, prim
-// ID (NONE on a miss), t (+inf on a miss), u, v.
-void oracle_trace(void* s, const float* rays, int64_t n, int any, int use_bvh, int threads, uint32_t* inst_out,
-                  uint32_t* prim_out, double* t_out, double* u_out, double* v_out) {
+// rays: n x 8 float32 {o.xyz, minT, d.xyz, maxT}. Only instances whose mask ANDed
+// with ray_mask is nonzero take part. Outputs per ray: instance ID, prim ID (NONE on a
+// miss), t (+inf on a miss), u, v.
+void oracle_trace(void* s, const float* rays, int64_t n, int any, int use_bvh, int threads, uint32_t ray_mask,
+                  uint32_t* inst_out, uint32_t* prim_out, double* t_out, double* u_out, double* v_out) {
     Scene* S = (Scene*)s;
     if (use_bvh && !S->built) oracle_scene_build(s);
     parallel_for(n, threads, [&](int64_t i) {
         HitD h;
-        trace_one(*S, load_ray(rays + 8 * i), any != 0, use_bvh != 0, h);
+        trace_one(*S, load_ray(rays + 8 * i), any != 0, use_bvh != 0, ray_mask, h);
         inst_out[i] = h.inst;
         prim_out[i] = h.prim;
         t_out[i] = h.t;
         u_out[i] = h.u;
         v_out[i] = h.v;
+    });
+}
+
+// All hits of each ray (Sec. 7.5), sorted by (t, instance, primitive): the first
+// max_hits of ray i go to rows [i * max_hits, ...) of the outputs (misses after them),
+// count_out[i] gets how many there are.
+void oracle_all_hits(void* s, const float* rays, int64_t n, int use_bvh, int threads, uint32_t ray_mask,
+                     int64_t max_hits, uint32_t* inst_out, uint32_t* prim_out, double* t_out, double* u_out,
+                     double* v_out, int64_t* count_out) {
+    Scene* S = (Scene*)s;
+    if (use_bvh && !S->built) oracle_scene_build(s);
+    parallel_for(n, threads, [&](int64_t i) {
+        std::vector<HitRec> h;
+        all_hits_one(*S, load_ray(rays + 8 * i), use_bvh != 0, ray_mask, h);
+        count_out[i] = (int64_t)h.size();
+        for (int64_t j = 0; j < max_hits; ++j) {
+            const int64_t o = i * max_hits + j;
+            const bool ok = j < (int64_t)h.size();
+            inst_out[o] = ok ? h[(size_t)j].inst : NONE;
+            prim_out[o] = ok ? h[(size_t)j].prim : NONE;
+            t_out[o] = ok ? h[(size_t)j].t : INFINITY;
+            u_out[o] = ok ? h[(size_t)j].u : 0.0;
+            v_out[o] = ok ? h[(size_t)j].v : 0.0;
+        }
     });
 }
 

@@ -35,6 +35,8 @@ GRT_BUILD_OPERATION_UPDATE = 1
 GRT_INSTANCE_GEOMETRY = 0
 GRT_INTERSECT_NONE = 0
 GRT_INTERSECT_SPHERE = 1
+GRT_FILTER_NONE = 0
+GRT_FILTER_PRIMITIVE_MASK = 1
 GRT_INVALID_ID = 0xFFFFFFFF
 GRT_LOG_NONE, GRT_LOG_ERROR, GRT_LOG_WARN, GRT_LOG_INFO = 0, 1, 2, 4
 
@@ -78,15 +80,16 @@ class grtSceneBuildInput(ctypes.Structure):
 
 
 class grtFuncDataSet(ctypes.Structure):
-    _fields_ = [("intersectFunc", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("intersectFuncData", ctypes.c_void_p)]
+    _fields_ = [("intersectFunc", ctypes.c_uint32), ("filterFunc", ctypes.c_uint32),
+                ("intersectFuncData", ctypes.c_void_p), ("filterFuncData", ctypes.c_void_p)]
 
 
 class grtTraceOptions(ctypes.Structure):
     _fields_ = [("rayType", ctypes.c_uint32), ("blockSize", ctypes.c_uint32),
                 ("sharedStackDepth", ctypes.c_uint32), ("globalStackDepth", ctypes.c_uint32),
                 ("compactThreshold", ctypes.c_float), ("flags", ctypes.c_uint32),
-                ("globalStack", ctypes.c_void_p), ("globalStackBytes", ctypes.c_size_t)]
+                ("globalStack", ctypes.c_void_p), ("globalStackBytes", ctypes.c_size_t),
+                ("rayMask", ctypes.c_uint32)]
 
 
 class grtCamera(ctypes.Structure):
@@ -164,6 +167,7 @@ _SIGS = {
     "grtTraceClosest": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
     "grtTraceAnyHit": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
     "grtTraceClosestNoAlloc": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
+    "grtTraceAllHits": [_P, _P, _P, _P, _U32, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
     "grtGenerateCameraRays": [_P, ctypes.POINTER(grtCamera), _U32, _U32, _P, _P],
     "grtGenerateAORays": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P, _P],
     "grtTraceAmbientOcclusion": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P,
@@ -327,8 +331,10 @@ def grtCreateFuncTable(ctx, num_geom_types: int, num_ray_types: int) -> int:
     return out.value
 
 
-def grtSetFuncTable(ctx, table, geom_type: int, ray_type: int, func: int, data):
-    check(lib().grtSetFuncTable(ctx, table, geom_type, ray_type, grtFuncDataSet(func, 0, _ptr(data))),
+def grtSetFuncTable(ctx, table, geom_type: int, ray_type: int, func: int, data, filter_func: int = 0,
+                    filter_data=None):
+    check(lib().grtSetFuncTable(ctx, table, geom_type, ray_type,
+                                grtFuncDataSet(func, filter_func, _ptr(data), _ptr(filter_data))),
           "grtSetFuncTable")
 
 
@@ -337,9 +343,9 @@ def grtDestroyFuncTable(ctx, table):
 
 
 def trace_options(ray_type=0, block_size=0, shared_depth=0, global_depth=0, compact=0.0, global_stack=None,
-                  global_stack_bytes=0, flags=0) -> grtTraceOptions:
+                  global_stack_bytes=0, flags=0, ray_mask=0) -> grtTraceOptions:
     return grtTraceOptions(ray_type, block_size, shared_depth, global_depth, compact, flags, _ptr(global_stack),
-                           global_stack_bytes)
+                           global_stack_bytes, ray_mask)
 
 
 def grtGetTraceGlobalStackSize(ctx, opts=None) -> int:
@@ -357,6 +363,12 @@ def grtTraceClosest(ctx, scene, geom, rays, count, hits, table=None, opts=None, 
 def grtTraceAnyHit(ctx, scene, geom, rays, count, hits, table=None, opts=None, stream=None):
     check(lib().grtTraceAnyHit(ctx, scene, geom, _ptr(rays), count, _ptr(hits), table,
                                ctypes.byref(opts) if opts else None, _stream(stream)), "grtTraceAnyHit")
+
+
+def grtTraceAllHits(ctx, scene, geom, rays, count, hits, max_hits, counts, table=None, opts=None, stream=None):
+    """hits: (count * max_hits, 5) records; counts: uint32 device tensor of count entries."""
+    check(lib().grtTraceAllHits(ctx, scene, geom, _ptr(rays), count, _ptr(hits), max_hits, _ptr(counts), table,
+                                ctypes.byref(opts) if opts else None, _stream(stream)), "grtTraceAllHits")
 
 
 def grtTraceClosestNoAlloc(ctx, scene, geom, rays, count, hits, table=None, opts=None, stream=None):

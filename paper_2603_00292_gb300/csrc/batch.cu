@@ -2,7 +2,7 @@
 // ray batch, built (LBVH) and traced (closest hit) in one persistent launch that takes
 // work items from a device queue.
 //
-// The paper builds and traces one geometry or scene per call (Sec. 7.2-7.6); this
+// The paper builds and traces one geometry or scene per call (Sec. 7.2-7.5); this
 // scheduler has no counterpart there. Every item runs the same per-element work as the
 // per-geometry path (lbvh.cuh, traverse.cuh), so each geometry ends up bit-identical to
 // a grtBuildGeometry of the same input and each hit record identical to grtTraceClosest.
@@ -140,6 +140,7 @@ __device__ __noinline__ void traceChunk(const BatchParams& B, const BatchSceneDe
     P.error = B.error;
     P.maxSteps = 1u << 26;
     P.refillBelow = B.refillBelow;
+    P.rayMask = 0xFFFFFFFFu;
     P.targetPrimToLeaf = S.primToLeaf;
     const uint32_t base = chunk * B.traceChunk;
     const uint32_t n = min(B.traceChunk, S.rays - base);

@@ -384,7 +384,8 @@ __device__ __forceinline__ float3 setupInstance(const InstanceInput& I, uint32_t
     I.boxes[2 * (size_t)i + 1] = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
     rec.worldLo = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f);
     rec.worldHi = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
-    rec.reserved = make_float4(0.f, 0.f, 0.f, 0.f);
+    rec.mask = in.mask ? in.mask : 0xFFFFFFFFu;
+    rec.pad[0] = rec.pad[1] = rec.pad[2] = 0u;
     I.records[i] = rec;
     c = boxCentroid(b);
     I.centroids[i] = make_float4(c.x, c.y, c.z, 0.f);

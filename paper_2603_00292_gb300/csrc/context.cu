@@ -221,8 +221,10 @@ grtError grtCreateFuncTable(grtContext ctx, uint32_t numGeomTypes, uint32_t numR
 grtError grtSetFuncTable(grtContext ctx, grtFuncTable table, uint32_t geomType, uint32_t rayType, grtFuncDataSet set) {
     FuncTableObject* t = findFuncTable(table);
     if (!ctx || !t || geomType >= t->numGeomTypes || rayType >= t->numRayTypes) return GRT_ERROR_INVALID_PARAMETER;
-    if (set.intersectFunc > GRT_INTERSECT_SPHERE) return GRT_ERROR_INVALID_PARAMETER;
-    FuncEntry e{set.intersectFunc, 0u, set.intersectFuncData};
+    if (set.intersectFunc > GRT_INTERSECT_SPHERE || set.filterFunc > GRT_FILTER_PRIMITIVE_MASK)
+        return GRT_ERROR_INVALID_PARAMETER;
+    if (set.filterFunc != GRT_FILTER_NONE && !set.filterFuncData) return GRT_ERROR_INVALID_PARAMETER;
+    FuncEntry e{set.intersectFunc, set.filterFunc, set.intersectFuncData, set.filterFuncData};
     // Synchronous copy: the table may be used by work enqueued afterwards on any stream.
     GRT_CUDA(cudaMemcpy(t->dEntries + (size_t)rayType * t->numGeomTypes + geomType, &e, sizeof(e),
                         cudaMemcpyHostToDevice));

@@ -41,7 +41,8 @@ struct alignas(16) InstanceRecord {
     const BvhHeader* geometry;
     float4 worldLo;         // xyz: world box (rounded outward)
     float4 worldHi;
-    float4 reserved;
+    uint32_t mask;          // visibility mask, ANDed with the ray mask
+    uint32_t pad[3];
 };
 
 // Per-instance frames of a scene, indexed by instance ID.
@@ -128,8 +129,9 @@ void unregisterBvh(const void* handle);
 // Function-table record in device memory: one per (rayType, geomType).
 struct FuncEntry {
     uint32_t func;
-    uint32_t pad;
+    uint32_t filter;
     const void* data;
+    const void* filterData;
 };
 struct FuncTableObject {
     FuncEntry* dEntries;

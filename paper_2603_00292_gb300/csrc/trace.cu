@@ -29,6 +29,30 @@ __global__ void __launch_bounds__(256) refineKernel(TraceParams P) {
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < P.count; r += gridDim.x * blockDim.x) refineHit(P, r);
 }
 
+// Every hit of each ray (Sec. 7.5): one thread per ray walks it on a local stack of
+// kAllHitsDepth entries and stores its first maxHits hits (traversal order, FP64-refined)
+// in hits[r * maxHits ...], the rest of the ray's slots as misses, and the number of
+// hits found in counts[r].
+constexpr int kAllHitsDepth = 96;
+
+__global__ void __launch_bounds__(128) allHitsKernel(TraceParams P, uint32_t maxHits, uint32_t* counts) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= P.count) return;
+    const float4 a = P.rays[2 * (size_t)r], b = P.rays[2 * (size_t)r + 1];
+    AllHitsWalk<kAllHitsDepth> w;
+    w.begin(P, f3(a), f3(b), a.w, b.w);
+    uint32_t k = 0;
+    uint32_t* out = P.hits + 5 * (size_t)r * maxHits;
+    for (;;) {
+        const Hit h = w.next(P);
+        if (h.prim == kInvalid) break;
+        if (k < maxHits) storeHit(out, k, h);
+        ++k;
+    }
+    for (uint32_t j = k; j < maxHits; ++j) storeHit(out, j, Hit{kInvalid, kInvalid, INFINITY, 0.f, 0.f});
+    counts[r] = k;
+}
+
 // ---------------------------------------------------------------- ambient occlusion (Sec. 4)
 __global__ void aoRayKernel(const InstanceRecord* sceneLeaves, const uint32_t* scenePrimToLeaf, const float4* fwd32,
                             const float4* rays, const uint32_t* hits, uint32_t pixels, uint32_t spp,
@@ -478,6 +502,7 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     P.target.geomType = o->geomType;
     P.target.empty = o->primCount == 0;
     P.maxSteps = 1u << 26;  // far above any legitimate walk; stops a corrupted (cyclic) hierarchy
+    P.rayMask = (opt && opt->rayMask) ? opt->rayMask : 0xFFFFFFFFu;
     const float compact = (opt && opt->compactThreshold > 0.f) ? fminf(opt->compactThreshold, 1.f) : defaultCompact;
     P.refillBelow = (uint32_t)(compact * 32.f);
     P.inv64 = o->inv64;
@@ -712,6 +737,26 @@ grtError grtTraceClosest(grtContext ctx, grtScene scene, grtGeometry geom, const
 grtError grtTraceAnyHit(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
                         grtHit* hits, grtFuncTable table, const grtTraceOptions* options, void* stream) {
     return launchTrace<true>(ctx, scene, geom, rays, rayCount, hits, table, options, stream);
+}
+
+grtError grtTraceAllHits(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
+                         grtHit* hits, uint32_t maxHitsPerRay, uint32_t* hitCounts, grtFuncTable table,
+                         const grtTraceOptions* options, void* stream) {
+    if (!ctx || maxHitsPerRay == 0) return GRT_ERROR_INVALID_PARAMETER;
+    if (rayCount && (!rays || !hits || !hitCounts || ((uintptr_t)rays & 15))) return GRT_ERROR_INVALID_PARAMETER;
+    Context* c = asContext(ctx);
+    TraceParams P{};
+    bool isScene = false;
+    int bs = 128;
+    grtError e = prepareTrace(c, scene, geom, table, options, P, &isScene, &bs);
+    if (e != GRT_SUCCESS || rayCount == 0) return e;
+    P.rays = (const float4*)rays;
+    P.hits = (uint32_t*)hits;
+    P.count = rayCount;
+    allHitsKernel<<<ceilDiv(rayCount, 128), 128, 0, (cudaStream_t)stream>>>(P, maxHitsPerRay, hitCounts);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
 }
 
 grtError grtGenerateCameraRays(grtContext ctx, const grtCamera* camera, uint32_t width, uint32_t height, grtRay* rays,

@@ -5,7 +5,7 @@
 // two-level hierarchy whose instance leaves take the ray to object space with the
 // inverse frame (Sec. 6.2 "Two-Level Hierarchy and Instancing"); the stack keeps its
 // first entries in shared memory and spills to a global buffer (Sec. 7.5); closest-
-// hit and any-hit queries (Sec. 7.6; any-hit may stop at the first valid hit, Sec.
+// hit and any-hit queries (Sec. 7.5; any-hit may stop at the first valid hit, Sec.
 // 4.2); custom primitives through a (ray type x geometry type) function table (Sec.
 // 7.4). Triangles: Moller-Trumbore (1997), double-sided with inclusive edges as the
 // paper's test (Sec. 3.1). Spheres: centre-relative discriminant of Haines et al.,
@@ -64,6 +64,7 @@ struct TraceParams {
     uint32_t* error;
     uint32_t maxSteps;
     uint32_t refillBelow;           // refill a warp when at most this many lanes hold a ray
+    uint32_t rayMask;               // instances whose mask shares no bit with it are skipped
     const InstanceFrames64* inv64;  // scene: FP64 inverse frames by instance ID
     unsigned long long* stats;      // counting variants: grtTraceStatistics sums
     // fused ambient occlusion
@@ -533,7 +534,7 @@ template <bool ANY, bool COUNT>
 __device__ __forceinline__ bool enterInstance(const TraceParams& P, Stack& st, RayState& s, const InstanceRecord* R,
                                               Visits* vis) {
     const uint32_t bits = R->typeBits;
-    if (bits & kInstEmpty) return false;
+    if ((bits & kInstEmpty) || !(R->mask & P.rayMask)) return false;
     if (!st.push(kSentinel)) {
         latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
         return false;
@@ -595,6 +596,13 @@ __device__ __forceinline__ bool testLeaf(const TraceParams& P, RayState& s, uint
                     t = r.x, u = r.y, v = r.z;
                 }
             }
+        }
+    }
+    if (res == 1 && P.table && s.geomType < P.numGeomTypes) {  // intersection filter (Sec. 7.6)
+        const FuncEntry* fe = P.table + (size_t)P.rayType * P.numGeomTypes + s.geomType;
+        if (fe->filter == GRT_FILTER_PRIMITIVE_MASK) {
+            const uint32_t* bits = static_cast<const uint32_t*>(fe->filterData);
+            if (!((__ldg(bits + (prim >> 5)) >> (prim & 31u)) & 1u)) res = 0;
         }
     }
     if (res == 1) {
@@ -680,6 +688,55 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
     }
     orderChildren(P, st, s, m, tn, c);
     return false;
+}
+
+// One step of an all-hits walk (Sec. 7.5: every intersection, found by asking the
+// any-hit traversal for its next hit until it is done): a node visit that tests every
+// leaf it reaches against the whole range [tmin, tmax] and appends each hit to `found`
+// (at most four per visit), or an instance entry or exit. Returns the number of hits
+// appended, or -1 once the walk is over. Each primitive of each instance sits in one
+// leaf, so each (instance, primitive) is reported at most once.
+template <bool SCENE>
+__device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState& s, Hit* found) {
+    if (s.next == kNone) {
+        if (st.sp == 0) return -1;
+        s.next = st.pop();
+        if (SCENE && s.next == kSentinel) {  // back to the top level
+            exactLevel(s.L, s.wo, s.wd);
+            s.lo = s.tmin;
+            s.hi = s.tmax;
+            s.nodes = P.target.nodes;
+            s.inBlas = false;
+            s.next = kNone;
+            return 0;
+        }
+    }
+    if (SCENE && !s.inBlas && (s.next & kLeafBit)) {  // enter an instance
+        const uint32_t leaf = s.next & ~kLeafBit;
+        s.next = kNone;
+        s.found = false;
+        enterInstance<true, false>(P, st, s, reinterpret_cast<const InstanceRecord*>(P.target.leaves) + leaf, nullptr);
+        return 0;
+    }
+    if (++s.steps > P.maxSteps) {
+        latchError(P.error, GRT_ERROR_STEP_LIMIT);
+        return -1;
+    }
+    float tn[4];
+    uint32_t c[4];
+    uint32_t m = slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+    s.next = kNone;
+    int added = 0;
+    if (s.inBlas) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!((m >> j) & 1u) || !(c[j] & kLeafBit)) continue;
+            m &= ~(1u << j);
+            if (testLeaf<true, SCENE, false>(P, s, c[j] & ~kLeafBit, nullptr)) found[added++] = s.best;
+        }
+    }
+    orderChildren(P, st, s, m, tn, c);
+    return added;
 }
 
 // One ray through the target, all steps in a row. Returns the hit (prim == kInvalid
@@ -1026,6 +1083,48 @@ __device__ __forceinline__ void refineOne(const TraceParams& P, float3 wo, float
     const float4 res = refine64(P.inv64, scene, h.inst, wo, wd, rec, sphere, tmin, tmax);
     if (res.w != 0.f) h.t = res.x, h.u = res.y, h.v = res.z;
 }
+
+// The state of an all-hits walk of one ray on a per-thread stack of DEPTH entries: next()
+// returns the ray's hits one at a time, in traversal order, each with t, u, v recomputed
+// in FP64, then a record with prim == kInvalid. The stack points into the object, so
+// an AllHitsWalk is used where it was begun and never copied.
+template <int DEPTH>
+struct AllHitsWalk {
+    RayState s;
+    uint32_t entries[DEPTH];
+    Stack st;
+    Hit buf[4];
+    int n, i;
+    bool scene, finished;
+    float3 o, d;
+    float tmin, tmax;
+
+    __device__ void begin(const TraceParams& P, float3 o_, float3 d_, float tmin_, float tmax_) {
+        o = o_, d = d_, tmin = tmin_, tmax = tmax_;
+        st = Stack{nullptr, entries, 0u, (uint32_t)DEPTH, 1u, 0u};
+        scene = P.target.primType == kPrimScene;
+        if (scene)
+            beginRay<true>(P, st, s, o, d, tmin, tmax);
+        else
+            beginRay<false>(P, st, s, o, d, tmin, tmax);
+        n = i = 0;
+        finished = false;
+    }
+    __device__ Hit next(const TraceParams& P) {
+        while (i == n && !finished) {
+            const int r = scene ? stepAll<true>(P, st, s, buf) : stepAll<false>(P, st, s, buf);
+            if (r < 0)
+                finished = true;
+            else
+                n = r, i = 0;
+        }
+        if (i == n) return Hit{kInvalid, kInvalid, INFINITY, 0.f, 0.f};
+        Hit h = buf[i++];
+        refineOne(P, o, d, tmin, tmax, h);
+        return h;
+    }
+    __device__ bool done() const { return finished && i == n; }
+};
 
 // Ray r's closest hit: t, u, v recomputed in FP64 (the hit record is updated in place).
 __device__ __forceinline__ void refineHit(const TraceParams& P, uint32_t r) {

@@ -77,11 +77,14 @@ class Geometry:
             self.handle = None
 
 
-def instance_records(geometry_handles) -> np.ndarray:
-    """16-byte grtInstance records {type, mask, geometry} as raw bytes."""
+def instance_records(geometry_handles, masks=None) -> np.ndarray:
+    """16-byte grtInstance records {type, mask, geometry} as raw bytes (masks: one 32-bit
+    visibility mask per instance, 0 = all bits; default all bits)."""
     n = len(geometry_handles)
     rec = np.zeros(n, dtype=np.dtype([("type", "<u4"), ("mask", "<u4"), ("geometry", "<u8")]))
     rec["type"] = GRT_INSTANCE_GEOMETRY
+    if masks is not None:
+        rec["mask"] = np.asarray(masks, dtype=np.uint32)
     rec["geometry"] = np.asarray(geometry_handles, dtype=np.uint64)
     return rec.view(np.uint8)
 
@@ -90,9 +93,9 @@ class Scene:
     """A top-level BVH over instances of geometries with SRT frames (float32 (I,10):
     quaternion xyzw, scale xyz, translation xyz)."""
 
-    def __init__(self, ctx: Context, geometry_handles, frames: torch.Tensor, morton_bits: int = 0):
+    def __init__(self, ctx: Context, geometry_handles, frames: torch.Tensor, morton_bits: int = 0, masks=None):
         self.ctx = ctx
-        self.instances = device_tensor(instance_records(geometry_handles))
+        self.instances = device_tensor(instance_records(geometry_handles, masks))
         self.frames = frames
         self.input = scene_input(self.instances, self.frames, count=len(geometry_handles))
         self.options = build_options(morton_bits)
@@ -144,9 +147,9 @@ class FuncTable:
         self.handle = grtCreateFuncTable(ctx.handle, num_geom_types, num_ray_types)
         self._keep = []
 
-    def set(self, geom_type: int, ray_type: int, func: int, data):
-        self._keep.append(data)
-        grtSetFuncTable(self.ctx.handle, self.handle, geom_type, ray_type, func, data)
+    def set(self, geom_type: int, ray_type: int, func: int, data, filter_func: int = 0, filter_data=None):
+        self._keep += [data, filter_data]
+        grtSetFuncTable(self.ctx.handle, self.handle, geom_type, ray_type, func, data, filter_func, filter_data)
 
     def close(self):
         if self.handle:

@@ -46,9 +46,9 @@ def test_struct_layouts():
     assert ctypes.sizeof(grt.grtAABBListPrimitive) == 16
     assert ctypes.sizeof(grt.grtGeometryBuildInput) == 8 + 32 + 16
     assert ctypes.sizeof(grt.grtSceneBuildInput) == 24
-    assert ctypes.sizeof(grt.grtFuncDataSet) == 16
+    assert ctypes.sizeof(grt.grtFuncDataSet) == 24
     assert ctypes.sizeof(grt.grtCamera) == 36
-    assert ctypes.sizeof(grt.grtTraceOptions) == 40
+    assert ctypes.sizeof(grt.grtTraceOptions) == 48
     assert grt.RAY_BYTES == 32 and grt.HIT_BYTES == 20
     assert ctypes.sizeof(grt.grtBatchScene) == 8 + 56 + 8 + 8 + 8
     assert ctypes.sizeof(grt.grtBatchOptions) == 44

@@ -39,6 +39,12 @@ def user_lib(gpu, tmp_path_factory):
     L.userTraceLaunch.argtypes = [ctypes.POINTER(grt.grtDeviceTarget), ctypes.c_void_p, ctypes.c_uint32,
                                   ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     L.userTraceLaunch.restype = ctypes.c_int
+    L.userTraceMaskedLaunch.argtypes = [ctypes.POINTER(grt.grtDeviceTarget), ctypes.c_void_p, ctypes.c_uint32,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p]
+    L.userTraceMaskedLaunch.restype = ctypes.c_int
+    L.userAllHitsLaunch.argtypes = [ctypes.POINTER(grt.grtDeviceTarget), ctypes.c_void_p, ctypes.c_uint32,
+                                    ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]
+    L.userAllHitsLaunch.restype = ctypes.c_int
     return L
 
 
@@ -122,3 +128,55 @@ def test_user_kernel_with_custom_spheres(gpu, user_lib):
     assert (a[1] != NONE).sum() > 1000
     assert np.array_equal(_user(user_lib, T, rays, True)[1] != NONE,
                           _library(gpu, rays, True, geom=g.handle, table=table.handle)[1] != NONE)
+
+
+def test_user_kernel_with_a_ray_mask(gpu, user_lib):
+    m = scenegen.terrain(cells=32, amplitude=0.2)
+    fr = scenegen.random_frames(10, seed=6)
+    g = Geometry(gpu, vertices=device_tensor(m.vertices), indices=device_tensor(m.indices)).build()
+    masks = [1 << (k % 4) for k in range(10)]
+    sc = Scene(gpu, [g.handle] * 10, device_tensor(fr.packed()), masks=masks).build()
+    lo, hi = scenegen.world_bounds([m], np.zeros(10, np.int32), fr)
+    rays_np = scenegen.random_rays(40_000, lo, hi, config=75)
+    rays = device_tensor(rays_np)
+    T = grt.grtGetDeviceTarget(gpu.handle, scene=sc.handle)
+    for ray_mask in (0x1, 0x6):
+        for any_hit in (False, True):
+            h = new_hits(rays.shape[0])
+            assert user_lib.userTraceMaskedLaunch(ctypes.byref(T), rays.data_ptr(), rays.shape[0], h.data_ptr(),
+                                                  int(any_hit), ray_mask,
+                                                  torch.cuda.current_stream().cuda_stream) == 0
+            torch.cuda.synchronize()
+            a = hits_to_numpy(h)
+            hl = new_hits(rays.shape[0])
+            fn = grt.grtTraceAnyHit if any_hit else grt.grtTraceClosest
+            fn(gpu.handle, sc.handle, None, rays, rays.shape[0], hl, None, grt.trace_options(ray_mask=ray_mask))
+            torch.cuda.synchronize()
+            b = hits_to_numpy(hl)
+            assert np.array_equal(a[1] != NONE, b[1] != NONE)
+            hit = a[1] != NONE
+            assert all(masks[k] & ray_mask for k in np.unique(a[0][hit]).tolist())
+            assert hit.sum() > 500
+
+
+def test_user_kernel_all_hits(gpu, user_lib):
+    """grt_device::AllHits in a user kernel returns exactly what grtTraceAllHits stores
+    (the same walk), and reports the walk as done after its last hit."""
+    m = scenegen.terrain(cells=32, amplitude=0.3)
+    fr = scenegen.random_frames(8, seed=7)
+    g = Geometry(gpu, vertices=device_tensor(m.vertices), indices=device_tensor(m.indices)).build()
+    sc = Scene(gpu, [g.handle] * 8, device_tensor(fr.packed())).build()
+    lo, hi = scenegen.world_bounds([m], np.zeros(8, np.int32), fr)
+    rays_np = scenegen.random_rays(30_000, lo, hi, config=76)
+    rays = device_tensor(rays_np)
+    n, k = rays.shape[0], 8
+    T = grt.grtGetDeviceTarget(gpu.handle, scene=sc.handle)
+    hu, cu = new_hits(n * k), torch.empty(n, dtype=torch.int32, device="cuda")
+    assert user_lib.userAllHitsLaunch(ctypes.byref(T), rays.data_ptr(), n, hu.data_ptr(), k, cu.data_ptr(),
+                                      torch.cuda.current_stream().cuda_stream) == 0
+    hl, cl = new_hits(n * k), torch.empty(n, dtype=torch.int32, device="cuda")
+    grt.grtTraceAllHits(gpu.handle, sc.handle, None, rays, n, hl, k, cl)
+    torch.cuda.synchronize()
+    assert torch.equal(cu, cl) and torch.equal(hu, hl)
+    assert (cl >= 2).sum().item() > 100
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS

@@ -294,3 +294,243 @@ def test_ambient_occlusion_rays_and_occlusion(gpu):
     assert np.array_equal(ao_img.cpu().numpy(), expect.astype(np.float32))
     assert 0.0 < expect[gh[1] != NONE].mean() < 1.0
     _no_device_error(gpu)
+
+
+# ------------------------------------------------------------------ instance and ray masks
+def test_instance_and_ray_masks(gpu):
+    """Sec. 7.5: an instance takes part only when its mask ANDed with the ray mask is
+    nonzero (0 in either place means all bits). Closest and any hit against the oracle
+    with the same effective masks, the fused AO kernel against any-hit on its own rays
+    under the same mask, and the device-side entry point honouring the mask."""
+    count = 12
+    mesh = scenegen.terrain(cells=32, amplitude=0.2)
+    fr = scenegen.random_frames(count, config=89)
+    g = Geometry(gpu, vertices=device_tensor(mesh.vertices), indices=device_tensor(mesh.indices)).build()
+    masks = [0, 1, 2, 3, 4, 6, 8, 1, 2, 0x10, 0x80000000, 5]
+    sc = Scene(gpu, [g.handle] * count, device_tensor(fr.packed()), masks=masks).build()
+    S = oracle.Scene()
+    gi = S.add_mesh(mesh.vertices, mesh.indices)
+    for k in range(count):
+        S.add_instance(gi, fr.packed()[k])
+        S.set_instance_mask(k, masks[k] if masks[k] else 0xFFFFFFFF)
+    S.build()
+    targets = fr.translation.astype(np.float64)
+    rays = _aimed(40_000, targets, 93)
+    rays[::4, 7] = 6.0
+    for ray_mask in (0, 0x1, 0x6, 0x80000010, 0x40000000):
+        effective = ray_mask if ray_mask else 0xFFFFFFFF
+        opts = grt.trace_options(ray_mask=ray_mask)
+        ref = S.trace(rays, ray_mask=effective)
+        got = _trace(gpu, rays, scene=sc.handle, opts=opts)
+        compare_closest(got, ref, S, rays, extent=25.0).check()
+        anyg = _trace(gpu, rays, scene=sc.handle, any_hit=True, opts=opts)
+        compare_any(anyg[1], ref, S, rays, extent=25.0).check()
+        visible = {k for k in range(count) if (masks[k] if masks[k] else 0xFFFFFFFF) & effective}
+        hit = got[1] != NONE
+        assert set(np.unique(got[0][hit]).tolist()) <= visible
+        if ray_mask == 0x40000000:  # only instance 0 (mask 0 = all bits) is visible
+            assert visible == {0}
+    _no_device_error(gpu)
+
+
+def test_ambient_occlusion_with_a_ray_mask(gpu):
+    sc, S, fr, table, keep = _instanced(gpu, cells=32, count=16)
+    W, H, spp, seed = 160, 96, 8, 79
+    from scenegen import InstancedScene
+    mesh = scenegen.terrain(cells=32, amplitude=0.2)
+    g = np.zeros(16, np.int32)
+    blo, bhi = scenegen.world_bounds([mesh], g, fr)
+    scn = InstancedScene([mesh], g, fr, blo, bhi)
+    cam = scenegen.overview_camera(scn, W, H)
+    masks = [1 << (k % 3) for k in range(16)]
+    gm = Geometry(gpu, vertices=device_tensor(mesh.vertices), indices=device_tensor(mesh.indices)).build()
+    scm = Scene(gpu, [gm.handle] * 16, device_tensor(fr.packed()), masks=masks).build()
+    rays_d = device_tensor(oracle.camera_rays(cam.packed(), W, H))
+    hits_d = new_hits(W * H)
+    grt.grtTraceClosest(gpu.handle, scm.handle, None, rays_d, W * H, hits_d)
+    length = float(np.float32(0.05 * scn.extent))
+    ao_d = new_rays(W * H * spp)
+    grt.grtGenerateAORays(gpu.handle, scm.handle, rays_d, hits_d, W * H, spp, seed, length, ao_d)
+    opts = grt.trace_options(ray_mask=0x2)
+    img = torch.empty(W * H, dtype=torch.float32, device="cuda")
+    grt.grtTraceAmbientOcclusion(gpu.handle, scm.handle, rays_d, hits_d, W * H, spp, seed, length, img, opts)
+    occ = _trace(gpu, ao_d.cpu().numpy(), scene=scm.handle, any_hit=True, opts=opts)
+    expect = (occ[1] != NONE).reshape(W * H, spp).sum(axis=1) / spp
+    assert np.array_equal(img.cpu().numpy(), expect.astype(np.float32))
+    full = torch.empty_like(img)
+    grt.grtTraceAmbientOcclusion(gpu.handle, scm.handle, rays_d, hits_d, W * H, spp, seed, length, full)
+    assert (img <= full).all() and (img < full).any()  # fewer occluders under the mask
+    _no_device_error(gpu)
+
+
+# ------------------------------------------------------------------ intersection filters
+def _bits(keep):
+    w = np.zeros((keep.size + 31) // 32, np.uint32)
+    idx = np.nonzero(keep)[0]
+    np.bitwise_or.at(w, idx >> 5, (np.uint32(1) << (idx & 31).astype(np.uint32)))
+    return w
+
+
+@pytest.mark.parametrize("two_level", [False, True])
+def test_primitive_mask_filter(gpu, two_level):
+    """Sec. 7.6: a filter rejects hits, for triangles and custom primitives alike; traversal
+    goes on past them. The built-in primitive-mask filter against the oracle with the
+    same filter; under another ray type (table row without a filter) nothing is rejected."""
+    rng = np.random.default_rng(61)
+    mesh = scenegen.terrain(cells=48, amplitude=0.2)
+    sph = scenegen.spheres(2000, half=1.0, rmin=0.01, rmax=0.15, config=62)
+    keep_t = rng.random(mesh.indices.shape[0]) < 0.55
+    keep_s = rng.random(sph.shape[0]) < 0.5
+    gt = Geometry(gpu, vertices=device_tensor(mesh.vertices), indices=device_tensor(mesh.indices), geom_type=0).build()
+    gs = Geometry(gpu, boxes=device_tensor(scenegen.sphere_aabbs(sph)), geom_type=1).build()
+    table = FuncTable(gpu, num_geom_types=2, num_ray_types=2)
+    table.set(0, 0, grt.GRT_INTERSECT_NONE, None, grt.GRT_FILTER_PRIMITIVE_MASK, device_tensor(_bits(keep_t)))
+    table.set(1, 0, grt.GRT_INTERSECT_SPHERE, device_tensor(sph), grt.GRT_FILTER_PRIMITIVE_MASK,
+              device_tensor(_bits(keep_s)))
+    table.set(1, 1, grt.GRT_INTERSECT_SPHERE, device_tensor(sph))  # ray type 1: no filter
+    S = oracle.Scene()
+    ot = S.add_mesh(mesh.vertices, mesh.indices)
+    os_ = S.add_spheres(sph)
+    U = oracle.Scene()  # unfiltered, for ray type 1
+    ut = U.add_mesh(mesh.vertices, mesh.indices)
+    us = U.add_spheres(sph)
+    S.set_prim_filter(ot, _bits(keep_t))
+    S.set_prim_filter(os_, _bits(keep_s))
+    frame = np.array([0, 0, 0, 1, 1, 1, 1, 0, 0.4, 0], np.float32)
+    rays = _aimed(50_000, np.array([[0.0, 0.0, 0.0], [0.0, 0.4, 0.0]]), 63, spread=0.6)
+    rays[::3, 7] = 2.0
+    if two_level:
+        sc = Scene(gpu, [gt.handle, gs.handle], device_tensor(np.stack([np.array([0, 0, 0, 1, 1, 1, 1, 0, 0, 0],
+                                                                                  np.float32), frame])))
+        sc.build()
+        for X, a, b in ((S, ot, os_), (U, ut, us)):
+            X.add_instance(a)
+            X.add_instance(b, frame)
+        target = dict(scene=sc.handle)
+    else:
+        S.add_instance(ot)
+        U.add_instance(ut)
+        target = dict(geom=gt.handle)
+    S.build()
+    U.build()
+    for ray_type, ref_scene in ((0, S), (1, U)):
+        opts = grt.trace_options(ray_type=ray_type)
+        ref = ref_scene.trace(rays)
+        got = _trace(gpu, rays, table=table.handle, opts=opts, **target)
+        compare_closest(got, ref, ref_scene, rays, extent=3.0, has_spheres=two_level).check()
+        anyg = _trace(gpu, rays, any_hit=True, table=table.handle, opts=opts, **target)
+        compare_any(anyg[1], ref, ref_scene, rays, extent=3.0, has_spheres=two_level).check()
+        hit = got[1] != NONE
+        assert hit.mean() > 0.05
+        if ray_type == 0:  # no rejected primitive is ever reported
+            tri = hit & (got[0] == 0)
+            assert keep_t[got[1][tri]].all()
+            if two_level:
+                sp = hit & (got[0] == 1)
+                assert sp.any() and keep_s[got[1][sp]].all()
+    _no_device_error(gpu)
+
+
+# ------------------------------------------------------------------ all hits (Sec. 7.5)
+def _all_hits(gpu, rays_np, k, **kw):
+    n = rays_np.shape[0]
+    hits = new_hits(n * k)
+    counts = torch.empty(n, dtype=torch.int32, device="cuda")
+    grt.grtTraceAllHits(gpu.handle, kw.get("scene"), kw.get("geom"), device_tensor(rays_np), n, hits, k, counts,
+                        kw.get("table"), kw.get("opts"))
+    torch.cuda.synchronize()
+    h = hits_to_numpy(hits)
+    return tuple(a.reshape(n, k) for a in h), counts.cpu().numpy().astype(np.int64)
+
+
+def _check_all_hits(got, cnt, ref, S, rays, k, extent):
+    """Per ray the set of (instance, primitive) equals the oracle's; matched t within
+    1e-5 relative, u, v within 1e-5. A ray may differ only where it grazes an edge
+    (margin below 1e-6), and such rays must stay below 1e-4 of all (at least 3 allowed)."""
+    gi, gp, gt, gu, gv = got
+    ri, rp, rt, ru, rv, rc = ref
+    bad = 0
+    for r in range(rays.shape[0]):
+        m = min(cnt[r], k)
+        a = sorted(zip(gi[r, :m].tolist(), gp[r, :m].tolist()))
+        b = sorted(zip(ri[r, :min(rc[r], k)].tolist(), rp[r, :min(rc[r], k)].tolist()))
+        if cnt[r] != rc[r] or (cnt[r] <= k and a != b):
+            assert S.min_edge_margin(rays[r]) < 1e-6, (r, a, b)
+            bad += 1
+            continue
+        if cnt[r] > k:  # truncated: the test keeps k above the largest count
+            continue
+        ref_t = {(i, p): (t, uu, vv) for i, p, t, uu, vv in zip(ri[r, :m], rp[r, :m], rt[r, :m], ru[r, :m], rv[r, :m])}
+        for j in range(m):
+            t, uu, vv = ref_t[(gi[r, j], gp[r, j])]
+            assert abs(gt[r, j] - t) <= 1e-5 * max(abs(t), 1e-3 * extent), (r, gt[r, j], t)
+            assert abs(gu[r, j] - uu) <= 1e-5 and abs(gv[r, j] - vv) <= 1e-5
+    assert bad <= max(3, 1e-4 * rays.shape[0]), bad
+
+
+def test_all_hits_two_level_scene(gpu):
+    sc, S, fr, table, keep = _instanced(gpu, cells=32, count=12)
+    rays = _aimed(20_000, fr.translation.astype(np.float64), 88)
+    rays[::2, 7] = 8.0
+    k = 12
+    got, cnt = _all_hits(gpu, rays, k, scene=sc.handle)
+    ref = S.all_hits(rays, k)
+    assert (ref[5] >= 2).sum() > 200 and ref[5].max() <= k
+    _check_all_hits(got, cnt, ref, S, rays, k, extent=25.0)
+    # counts agree with any-hit, and the nearest stored hit is the closest hit
+    anyg = _trace(gpu, rays, scene=sc.handle, any_hit=True)
+    assert np.array_equal(cnt > 0, anyg[1] != NONE)
+    close = _trace(gpu, rays, scene=sc.handle)
+    hit = cnt > 0
+    tmin = np.where(np.arange(k)[None, :] < cnt[:, None], got[2], np.inf).min(axis=1)
+    assert np.array_equal(tmin[hit], close[2][hit])
+    # truncation: two slots per ray, the count still complete
+    got2, cnt2 = _all_hits(gpu, rays, 2, scene=sc.handle)
+    assert np.array_equal(cnt2, cnt)
+    assert np.array_equal(got2[1], got[1][:, :2]) and np.array_equal(got2[2].view(np.uint32), got[2][:, :2].view(np.uint32))
+    _no_device_error(gpu)
+
+
+def test_all_hits_with_masks_filters_and_spheres(gpu):
+    rng = np.random.default_rng(64)
+    mesh = scenegen.terrain(cells=32, amplitude=0.3)
+    sph = scenegen.spheres(1500, half=1.0, rmin=0.01, rmax=0.15, config=65)
+    keep_s = rng.random(sph.shape[0]) < 0.6
+    gt = Geometry(gpu, vertices=device_tensor(mesh.vertices), indices=device_tensor(mesh.indices), geom_type=0).build()
+    gs = Geometry(gpu, boxes=device_tensor(scenegen.sphere_aabbs(sph)), geom_type=1).build()
+    table = FuncTable(gpu, num_geom_types=2, num_ray_types=1)
+    table.set(1, 0, grt.GRT_INTERSECT_SPHERE, device_tensor(sph), grt.GRT_FILTER_PRIMITIVE_MASK,
+              device_tensor(_bits(keep_s)))
+    frames = np.array([[0, 0, 0, 1, 1, 1, 1, 0, 0, 0], [0, 0, 0, 1, 1, 1, 1, 0, 0.3, 0],
+                       [0, 0.3826834, 0, 0.9238795, 1, 1, 1, 0, -0.2, 0]], np.float32)
+    masks = [1, 2, 4]
+    sc = Scene(gpu, [gt.handle, gs.handle, gt.handle], device_tensor(frames), masks=masks).build()
+    S = oracle.Scene()
+    ot, os_ = S.add_mesh(mesh.vertices, mesh.indices), S.add_spheres(sph)
+    S.set_prim_filter(os_, _bits(keep_s))
+    for i, (g_, f) in enumerate(zip((ot, os_, ot), frames)):
+        S.add_instance(g_, f)
+        S.set_instance_mask(i, masks[i])
+    S.build()
+    rays = _aimed(15_000, np.array([[0.0, 0.0, 0.0], [0.0, 0.3, 0.0]]), 66, spread=0.5)
+    k = 16
+    for ray_mask in (0x3, 0x6, 0x7):
+        got, cnt = _all_hits(gpu, rays, k, scene=sc.handle, table=table.handle,
+                             opts=grt.trace_options(ray_mask=ray_mask))
+        ref = S.all_hits(rays, k, ray_mask=ray_mask)
+        _check_all_hits(got, cnt, ref, S, rays, k, extent=3.0)
+        assert (cnt >= 2).sum() > 100
+    _no_device_error(gpu)
+
+
+def test_all_hits_edge_cases(gpu):
+    empty = Geometry(gpu, vertices=device_tensor(np.zeros((3, 3), np.float32)),
+                     indices=device_tensor(np.zeros((0, 3), np.uint32))).build()
+    rays = _aimed(100, np.zeros((1, 3)), 87)
+    got, cnt = _all_hits(gpu, rays, 3, geom=empty.handle)
+    assert (cnt == 0).all() and (got[1] == NONE).all()
+    with pytest.raises(grt.GrtError):
+        grt.grtTraceAllHits(gpu.handle, None, empty.handle, device_tensor(rays), 100, new_hits(100), 0,
+                            torch.empty(100, dtype=torch.int32, device="cuda"))
+    grt.grtTraceAllHits(gpu.handle, None, empty.handle, None, 0, None, 4, None)  # no rays: nothing to do
+    _no_device_error(gpu)

@@ -210,6 +210,84 @@ def test_bvh_equals_brute_force(any_hit):
         assert np.array_equal(a.t, b.t)
 
 
+@pytest.mark.parametrize("bvh", [False, True])
+def test_instance_masks_equal_a_scene_of_the_visible_instances(bvh):
+    """Sec. 7.5: an instance takes part only when its mask ANDed with the ray mask is
+    nonzero. So a masked trace equals a trace of a scene that holds only the visible
+    instances (instance IDs mapped back), and a ray mask that no instance shares hits
+    nothing."""
+    S, mesh, fr = _small_instanced_scene()
+    masks = [0x1, 0x2, 0x3, 0x4, 0x5, 0x8]
+    for k, m in enumerate(masks):
+        S.set_instance_mask(k, m)
+    S.build()
+    rays = _aimed_rays(5000, fr.translation.astype(np.float64), 95)
+    for ray_mask in (0x1, 0x6, 0xFFFFFFFF):
+        visible = [k for k, m in enumerate(masks) if m & ray_mask]
+        V = oracle.Scene()
+        g = V.add_mesh(mesh.vertices, mesh.indices)
+        for k in visible:
+            V.add_instance(g, fr.packed()[k])
+        V.build()
+        for any_hit in (False, True):
+            a = S.trace(rays, any_hit=any_hit, bvh=bvh, ray_mask=ray_mask)
+            b = V.trace(rays, any_hit=any_hit, bvh=bvh)
+            assert np.array_equal(a.prim != NONE, b.prim != NONE)
+            if not any_hit:
+                hit = b.prim != NONE
+                assert np.array_equal(a.inst[hit], np.asarray(visible, np.uint32)[b.inst[hit]])
+                assert np.array_equal(a.prim, b.prim) and np.array_equal(a.t, b.t)
+        assert (a.prim != NONE).mean() > 0.02
+    none = S.trace(rays, bvh=bvh, ray_mask=0x10)
+    assert (none.prim == NONE).all()
+
+
+@pytest.mark.parametrize("bvh", [False, True])
+def test_primitive_filter_equals_removing_the_rejected_primitives(bvh):
+    """Sec. 7.6's intersection filter, as a primitive mask: tracing with hits on the
+    masked-out primitives rejected equals tracing a geometry without those primitives
+    (IDs mapped back), for triangles and for spheres."""
+    rng = np.random.default_rng(94)
+    mesh = scenegen.terrain(cells=24, amplitude=0.2)
+    sph = scenegen.spheres(400, half=1.0, rmin=0.02, rmax=0.2, config=93)
+    keep_t = rng.random(mesh.indices.shape[0]) < 0.6
+    keep_s = rng.random(sph.shape[0]) < 0.5
+
+    def bits(keep):
+        w = np.zeros((keep.size + 31) // 32, np.uint32)
+        for i in np.nonzero(keep)[0]:
+            w[i >> 5] |= np.uint32(1) << np.uint32(i & 31)
+        return w
+
+    S = oracle.Scene()
+    gt = S.add_mesh(mesh.vertices, mesh.indices)
+    gs = S.add_spheres(sph)
+    S.set_prim_filter(gt, bits(keep_t))
+    S.set_prim_filter(gs, bits(keep_s))
+    S.add_instance(gt)
+    S.add_instance(gs, np.array([0, 0, 0, 1, 1, 1, 1, 0, 0.5, 0], np.float32))
+    S.build()
+    R = oracle.Scene()
+    R.add_instance(R.add_mesh(mesh.vertices, mesh.indices[keep_t]))
+    R.add_instance(R.add_spheres(sph[keep_s]), np.array([0, 0, 0, 1, 1, 1, 1, 0, 0.5, 0], np.float32))
+    R.build()
+    rays = _aimed_rays(5000, np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.0]]), 92)
+    ids = [np.nonzero(keep_t)[0], np.nonzero(keep_s)[0]]
+    for any_hit in (False, True):
+        a = S.trace(rays, any_hit=any_hit, bvh=bvh)
+        b = R.trace(rays, any_hit=any_hit, bvh=bvh)
+        assert np.array_equal(a.prim != NONE, b.prim != NONE)
+        if not any_hit:
+            hit = b.prim != NONE
+            mapped = np.array([ids[i][p] for i, p in zip(b.inst[hit], b.prim[hit])], np.uint32)
+            assert np.array_equal(a.inst, b.inst) and np.array_equal(a.prim[hit], mapped)
+            assert np.array_equal(a.t, b.t)
+            assert hit.mean() > 0.05
+    # a filtered primitive is no hit for the single-primitive query either
+    rej = int(np.nonzero(~keep_t)[0][0])
+    assert not S.intersect_prim(rays[0], 0, rej)[0]
+
+
 def test_any_hit_equals_closest_within_max_t():
     S, mesh, fr = _small_instanced_scene()
     S.build()
@@ -334,3 +412,53 @@ def test_ao_rays_on_the_flat_plane():
     h = S.trace(prim)
     ao = oracle.ao_rays(S, prim, h, 4, 1234, 0.25)
     assert np.allclose(ao[:, 1], -1e-4, atol=1e-7) and np.all(ao[:, 5] <= 0)
+
+
+# ---------------------------------------------------------------- all hits (Sec. 7.5)
+@pytest.mark.parametrize("bvh", [False, True])
+def test_all_hits_agree_with_closest_and_any_hit(bvh):
+    S, mesh, fr = _small_instanced_scene()
+    S.build()
+    rays = _aimed_rays(3000, fr.translation.astype(np.float64), 91)
+    rays[1::2, 7] = 9.0
+    inst, prim, t, u, v, cnt = S.all_hits(rays, 16, bvh=bvh)
+    c = S.trace(rays)
+    a = S.trace(rays, any_hit=True)
+    assert np.array_equal(cnt > 0, a.prim != NONE)
+    hit = cnt > 0
+    # the first hit in (t, instance, primitive) order is the closest hit (same tie rule)
+    assert np.array_equal(inst[hit, 0], c.inst[hit]) and np.array_equal(prim[hit, 0], c.prim[hit])
+    assert np.array_equal(t[hit, 0], c.t[hit])
+    # sorted, within [minT, maxT], misses after the last hit
+    k = np.minimum(cnt, 16)
+    col = np.arange(16)[None, :]
+    valid = col < k[:, None]
+    assert np.all(np.diff(np.where(valid, t, 1e300), axis=1) >= 0)
+    assert np.all(t[valid] <= np.repeat(rays[:, 7:8], 16, axis=1)[valid])
+    assert np.all(prim[~valid] == NONE)
+    assert (cnt >= 2).mean() > 0.01 and cnt.max() >= 3  # some rays cross several surfaces
+    if bvh:
+        b = S.all_hits(rays, 16, bvh=False)
+        assert np.array_equal(b[5], cnt) and np.array_equal(b[1], prim) and np.array_equal(b[2], t)
+
+
+def test_all_hits_through_a_closed_sphere_mesh():
+    """A ray from outside through the centre of a closed convex mesh crosses it exactly
+    twice (away from edges and vertices), once on each side of the centre."""
+    mesh = scenegen.icosphere(3)
+    S = oracle.Scene()
+    S.add_instance(S.add_mesh(mesh.vertices, mesh.indices))
+    S.build()
+    rng = np.random.default_rng(90)
+    d = rng.normal(size=(2000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = -5.0 * d
+    rays = _rays(o, d)
+    inst, prim, t, u, v, cnt = S.all_hits(rays, 8)
+    clean = np.array([S.min_edge_margin(r) > 1e-6 for r in rays])
+    assert clean.mean() > 0.9
+    assert np.all(cnt[clean] == 2)
+    assert np.all(t[clean, 0] < 5.0) and np.all(t[clean, 1] > 5.0)
+    # the two crossings are at distance between the inradius and 1 from the centre
+    assert np.all(np.abs(t[clean, :2] - 5.0) <= 1.0 + 1e-9)
+    assert np.all(np.abs(t[clean, :2] - 5.0) >= 0.98)
