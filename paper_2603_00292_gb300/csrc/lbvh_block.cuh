@@ -257,6 +257,49 @@ static __device__ __noinline__ void fitRange(const BlockBuild& S, uint32_t begin
     }
 }
 
+// Up to this many primitives, a single-block build sorts by rank in shared memory.
+constexpr uint32_t kRankSortMax = 512;
+
+// Stable sort of a small build's Morton codes in shared memory: key i goes to position
+// #{j : k_j < k_i, or k_j = k_i and j < i}. A stable sort's output is unique, so this is
+// the permutation the radix passes produce. The sorted keys and values go to the final
+// ping-pong buffers (keys[passes & 1], vals[passes & 1]) as after the radix passes, and
+// the sorted keys stay in shared memory (the first n keys of smem) for emission. Needs
+// n * (sizeof(K) + 4) bytes of smem: codes, then ranks.
+template <typename K, int BITS>
+__device__ __noinline__ void rankSortShared(const BlockBuild& S, uint32_t* smem) {
+    const uint32_t n = S.n;
+    K* keys = reinterpret_cast<K*>(smem);
+    uint32_t* rank = reinterpret_cast<uint32_t*>(keys + n);
+    uint32_t b[6];
+    loadBounds(S, b);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) keys[i] = mortonCode<K, BITS>(__ldcg(S.centroids + i), b);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const K k = keys[i];
+        uint32_t r = 0;
+        for (uint32_t j = 0; j < n; ++j) {
+            const K kj = keys[j];
+            r += (kj < k || (kj == k && j < i)) ? 1u : 0u;
+        }
+        rank[i] = r;
+    }
+    __syncthreads();
+    K* kout = static_cast<K*>(S.keys[S.passes & 1u]);
+    uint32_t* vout = S.vals[S.passes & 1u];
+    K k[kRankSortMax / 64];  // this thread's keys, read before any is overwritten
+    uint32_t c = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) k[c++] = keys[i];
+    __syncthreads();
+    c = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x, ++c) {
+        const uint32_t r = rank[i];
+        keys[r] = k[c];
+        kout[r] = k[c];
+        vout[r] = i;
+    }
+}
+
 // The whole build of a small scene by one block, phase after phase.
 template <typename K, int BITS>
 // Every step's global writes are read by other threads of the same block after a
@@ -274,19 +317,29 @@ __device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys,
         prepRange(S, 0, S.n);
     }
     __syncthreads();
-    for (uint32_t p = 0; p < S.passes; ++p) {
-        for (uint32_t c = 0; c < S.sortChunks; ++c) {
-            sortUpsweepChunk<K, BITS>(S, c, p, chunkKeys, smem);
-            __syncthreads();
-        }
-        sortScanScene(S, smem);
+    const bool ranked = S.n <= kRankSortMax && blockDim.x >= 64 &&
+                        (size_t)S.n * (sizeof(K) + 4) <= blockBuildSmemWords(blockDim.x) * sizeof(uint32_t);
+    if (ranked) {
+        rankSortShared<K, BITS>(S, smem);
         __syncthreads();
-        for (uint32_t c = 0; c < S.sortChunks; ++c) {
-            sortDownsweepChunk<K>(S, c, p, chunkKeys, smem);
+        const K* sorted = reinterpret_cast<const K*>(smem);
+        for (uint32_t i = threadIdx.x; i + 1 < S.n; i += blockDim.x)
+            karrasNode<false>(sorted, (int)S.n, (int)i, S.nodes, S.parents);
+    } else {
+        for (uint32_t p = 0; p < S.passes; ++p) {
+            for (uint32_t c = 0; c < S.sortChunks; ++c) {
+                sortUpsweepChunk<K, BITS>(S, c, p, chunkKeys, smem);
+                __syncthreads();
+            }
+            sortScanScene(S, smem);
             __syncthreads();
+            for (uint32_t c = 0; c < S.sortChunks; ++c) {
+                sortDownsweepChunk<K>(S, c, p, chunkKeys, smem);
+                __syncthreads();
+            }
         }
+        if (S.n >= 2) karrasRange<K>(S, 0, S.n - 1);
     }
-    if (S.n >= 2) karrasRange<K>(S, 0, S.n - 1);
     __syncthreads();
     fitRange(S, 0, S.n);
 }
