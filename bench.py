@@ -330,6 +330,26 @@ def run_grt(args, rank, world, local):
     kmax = 4
     ahits = new_hits(npix * kmax)
     acount = torch.empty(npix, dtype=torch.int32, device="cuda")
+    # path tracing with next event estimation (Sec. 5): the 64 terrain instances plus an
+    # emitting 4x4 quad above the scene's centre; per-triangle albedo 0.7, sky (0.3, 0.4, 0.6);
+    # three path vertices, one sample per pixel from the camera rays
+    quad_v = device_tensor(np.array([[-1, 0, -1], [1, 0, -1], [1, 0, 1], [-1, 0, 1]], np.float32))
+    quad_i = device_tensor(np.array([[0, 1, 2], [0, 2, 3]], np.uint32))
+    quad = Geometry(ctx, vertices=quad_v, indices=quad_i).build(sh)
+    ctr = 0.5 * (sc.lo + sc.hi)
+    light_frame = np.array([0, 0, 0, 1, 2, 1, 2, ctr[0], sc.hi[1] + 0.5 * sc.extent, ctr[2]], np.float32)
+    pt_frames = device_tensor(np.concatenate([sc.frames.packed(), light_frame[None, :]]))
+    pt_scene = Scene(ctx, [geom.handle] * WORKLOAD["instances"] + [quad.handle], pt_frames).build(sh)
+    ntri = mesh.indices.shape[0]
+    pt_alb = device_tensor(np.concatenate([np.full((ntri, 3), 0.7), np.zeros((2, 3))]).astype(np.float32))
+    pt_emi = device_tensor(np.concatenate([np.zeros((ntri, 3)), np.full((2, 3), 20.0)]).astype(np.float32))
+    pt_off = device_tensor(np.array([0] * WORKLOAD["instances"] + [ntri], np.uint32))
+    pt_lights = device_tensor(np.array([[WORKLOAD["instances"], 0], [WORKLOAD["instances"], 1]], np.uint32))
+    pt_in = grt.path_trace_input(pt_alb, pt_emi, pt_off, pt_lights, 2, 3, 1, seed, (0.3, 0.4, 0.6))
+    pt_ws = torch.empty(grt.grtGetPathTraceWorkspaceSize(npix), dtype=torch.uint8, device="cuda")
+    pt_out = torch.empty((npix, 3), dtype=torch.float32, device="cuda")
+    ms_pt = timed(lambda: grt.grtPathTrace(ctx.handle, pt_scene.handle, rays, npix, pt_in, pt_ws, pt_out, None, sh),
+                  reps=5)
     ms_mask = timed(masked_step)
     ms_filter = timed(lambda: grt.grtTraceClosest(ctx.handle, scene.handle, None, rays, npix, fhits, table.handle,
                                                   None, sh))
@@ -342,7 +362,10 @@ def run_grt(args, rank, world, local):
                                        "mrays_per_s": round((npix + spp * mhit) / ms_mask / 1e3, 1)},
                 "filter_half_closest_ms": round(ms_filter, 4),
                 "all_hits_primary": {"ms": round(ms_all, 4), "hits_found": all_found,
-                                     "mrays_per_s": round(npix / ms_all / 1e3, 1)}}
+                                     "mrays_per_s": round(npix / ms_all / 1e3, 1)},
+                "path_trace_nee": {"ms": round(ms_pt, 4), "max_depth": 3, "spp": 1,
+                                   "mpaths_per_s": round(npix / ms_pt / 1e3, 1),
+                                   "mean_radiance": round(float(pt_out.mean().item()), 5)}}
     assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
 
     # --------------------------------------------------- traversal work per ray (counting pass)

@@ -271,6 +271,47 @@ grtError grtTraceClosest(grtContext ctx, grtScene scene, grtGeometry geom, const
 grtError grtTraceAllHits(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t rayCount,
                          grtHit* hits, uint32_t maxHitsPerRay, uint32_t* hitCounts, grtFuncTable table,
                          const grtTraceOptions* options, void* stream);
+/* ---------------------------------------------------------------- path tracing (Sec. 5) */
+/* Materials and lights of a path trace. Primitive p of instance i uses material entry
+ * materialOffset[i] + p of albedo and emission (3 floats each, device); an entry with
+ * nonzero emission marks an emitting triangle. lights lists the emitting triangles for
+ * next event estimation as lightCount (instanceID, primID) pairs (device). */
+typedef struct grtPathTraceInput {
+    const float* albedo;
+    const float* emission;
+    const uint32_t* materialOffset;
+    const uint32_t* lights;
+    uint32_t lightCount;
+    uint32_t maxDepth;        /* path vertices per sample, >= 1 */
+    uint32_t samplesPerPixel; /* >= 1 */
+    uint32_t reserved;
+    uint64_t seed;            /* stream of the splitmix64 random numbers */
+    float sky[3];             /* radiance of rays that leave the scene */
+    float reserved2;
+} grtPathTraceInput;
+
+/* Bytes of device workspace grtPathTrace needs for rayCount rays (path and shadow rays
+ * and hits, throughput, radiance, pending light samples: about 152 B per ray). */
+grtError grtGetPathTraceWorkspaceSize(uint32_t rayCount, size_t* sizeBytes);
+
+/* Path tracing with next event estimation (Sec. 5) over a two-level scene of triangle
+ * meshes, one path per (ray, sample) from the given rays (e.g. camera rays from
+ * grtGenerateCameraRays). Per path vertex: a miss adds throughput * sky; a hit on an
+ * emitting triangle adds throughput * emission at the first vertex only (later ones
+ * count lights through next event estimation) and ends the path; otherwise one light
+ * triangle and a uniform point on it are sampled, its contribution
+ * T (albedo / pi) cos_s |cos_l| / dist^2 emission_l / pdf (pdf = 1 / (lightCount area_l))
+ * counts when an any-hit shadow ray from p + 1e-4 n over (1 - 1e-4) dist finds nothing,
+ * and the path continues along a cosine-weighted direction with T *= albedo. n is the
+ * face normal turned toward the incoming ray. radiance (device, 3 floats per ray) gets
+ * the mean over samplesPerPixel. workspace: device, 256-byte aligned, at least
+ * grtGetPathTraceWorkspaceSize bytes. options apply to every trace of the walk
+ * (ray mask, stack sizes). Runs as a wavefront of the library's closest-hit and any-hit
+ * queries with a shading pass per vertex, all on `stream`. */
+grtError grtPathTrace(grtContext ctx, grtScene scene, const grtRay* rays, uint32_t rayCount,
+                      const grtPathTraceInput* input, void* workspace, float* radiance,
+                      const grtTraceOptions* options, void* stream);
+
 /* The same closest-hit query as grtTraceClosest for callers that must not allocate
  * device memory: code running while a stream is being captured into a CUDA graph
  * (where cudaMalloc is not allowed), code whose memory is fully owned by another

@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
                                        P, P]
             L.oracle_scene_set_instance_mask.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32]
             L.oracle_scene_set_prim_filter.argtypes = [P, ctypes.c_int, P]
+            L.oracle_path_trace.argtypes = [P, P, i64, P, P, P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                            P, ctypes.c_int, P]
             L.oracle_all_hits.argtypes = [P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, i64, P, P, P, P, P,
                                           P]
             L.oracle_intersect_prim.argtypes = [P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
@@ -325,6 +327,24 @@ class Scene:
         self._L.oracle_all_hits(self._h, _p(r), n, int(bvh), threads, ray_mask & 0xFFFFFFFF, max_hits, _p(inst),
                                 _p(prim), _p(t), _p(u), _p(v), _p(cnt))
         return inst, prim, t, u, v, cnt
+
+    def path_trace(self, rays, albedo, emission, mat_offset, lights, max_depth: int, spp: int, seed: int, sky,
+                   threads: int = 0) -> np.ndarray:
+        """Path tracing with next event estimation (Sec. 5) from the given float32 rays:
+        the mean radiance over `spp` samples, (n, 3) FP64. albedo / emission: (M, 3)
+        per material entry, entry mat_offset[instance] + primitive; lights: (K, 2)
+        (instance, primitive) pairs of emitting triangles; sky: radiance of escaping
+        rays. The steps are listed at oracle_path_trace (trace_ref.cpp)."""
+        r = _c(rays, np.float32).reshape(-1, 8)
+        a = _c(albedo, np.float32).reshape(-1, 3)
+        e = _c(emission, np.float32).reshape(-1, 3)
+        mo = _c(mat_offset, np.uint32)
+        li = _c(lights, np.uint32).reshape(-1, 2)
+        sk = _c(sky, np.float32).reshape(3)
+        out = np.empty((r.shape[0], 3))
+        self._L.oracle_path_trace(self._h, _p(r), r.shape[0], _p(a), _p(e), _p(mo), _p(li), li.shape[0], max_depth,
+                                  spp, seed, _p(sk), threads, _p(out))
+        return out
 
     def intersect_prim(self, ray, inst: int, prim: int):
         """(hit, t, u, v) of one (instance, primitive) in FP64."""

@@ -38,6 +38,7 @@
 using namespace oracle;
 
 namespace {
+const double PI = 3.14159265358979323846;
 
 const uint32_t NONE = 0xFFFFFFFFu;
 
@@ -510,6 +511,108 @@ void oracle_all_hits(void* s, const float* rays, int64_t n, int use_bvh, int thr
             u_out[o] = ok ? h[(size_t)j].u : 0.0;
             v_out[o] = ok ? h[(size_t)j].v : 0.0;
         }
+    });
+}
+
+double oracle_xi(uint64_t seed, uint64_t pixel, uint32_t sample, uint32_t dim);
+void oracle_sample_hemisphere(double xi0, double xi1, double* out3);
+
+// Path tracing with next event estimation (Sec. 5), in FP64, one path per (ray,
+// sample) starting from the given float32 ray. Per path vertex (depth 0 .. max_depth-1):
+//  * closest hit; a miss adds T * sky and ends the path;
+//  * a hit on an emitting triangle (emission != 0) adds T * emission only at depth 0
+//    (later vertices count emitters through next event estimation) and ends the path;
+//  * otherwise, with n the face normal turned toward the ray, tangent normalize(v1-v0),
+//    p' = p + 1e-4 n: one light triangle l = floor(xi_a * L) (in integers on the 24-bit
+//    xi), a uniform point q on it (s = sqrt(xi_b): (1-s) a + s(1-xi_c) b + s xi_c c); if
+//    cos_s = n.w > 0 and cos_l = |n_l.w| > 0 with w = (q - p') / dist, and an any-hit
+//    ray from p' along w over [0, dist (1 - 1e-4)] finds nothing, add
+//    T * (albedo / pi) * cos_s cos_l / dist^2 * emission_l * L * area_l;
+//  * the next ray leaves p' along a cosine-weighted direction (xi_d, xi_e) around n
+//    (tangent frame as for ambient occlusion), and T *= albedo.
+// Random numbers: xi(seed, ray, j, dim) with j = (sample * max_depth + depth) * 3 + k:
+// (k, dim) = (0,0) a, (0,1) b, (1,0) c, (1,1) d, (2,0) e. Materials: entry
+// mat_offset[instance] + primitive of albedo / emission (3 floats each). lights: (instance,
+// primitive) pairs. out: the mean over samples, 3 doubles per ray.
+void oracle_path_trace(void* s, const float* rays, int64_t n, const float* albedo, const float* emission,
+                       const uint32_t* mat_offset, const uint32_t* lights, int64_t light_count, int max_depth,
+                       int spp, uint64_t seed, const float* sky, int threads, double* out) {
+    Scene* S = (Scene*)s;
+    if (!S->built) oracle_scene_build(s);
+    auto world_tri = [&](uint32_t inst, uint32_t prim, V3& a, V3& b, V3& c) {
+        const Instance& I = S->inst[inst];
+        const Geom& g = S->geoms[(size_t)I.geom];
+        a = I.fwd.point(g.a[prim]);
+        b = I.fwd.point(g.b[prim]);
+        c = I.fwd.point(g.c[prim]);
+    };
+    auto col = [](const float* f, size_t m) { return v3(f[3 * m], f[3 * m + 1], f[3 * m + 2]); };
+    const V3 skyL = v3(sky[0], sky[1], sky[2]);
+    parallel_for(n, threads, [&](int64_t p) {
+        V3 acc = v3(0, 0, 0);
+        for (int smp = 0; smp < spp; ++smp) {
+            RayD ray = load_ray(rays + 8 * p);
+            V3 T = v3(1, 1, 1), L = v3(0, 0, 0);
+            for (int depth = 0; depth < max_depth; ++depth) {
+                HitD h;
+                trace_one(*S, ray, false, true, 0xFFFFFFFFu, h);
+                if (h.prim == NONE) {
+                    L = L + v3(T.x * skyL.x, T.y * skyL.y, T.z * skyL.z);
+                    break;
+                }
+                const size_t m = (size_t)mat_offset[h.inst] + h.prim;
+                const V3 Le = col(emission, m);
+                if (Le.x != 0.0 || Le.y != 0.0 || Le.z != 0.0) {
+                    if (depth == 0) L = L + v3(T.x * Le.x, T.y * Le.y, T.z * Le.z);
+                    break;
+                }
+                V3 v0, v1, v2;
+                world_tri(h.inst, h.prim, v0, v1, v2);
+                V3 nrm = normalize(cross(v1 - v0, v2 - v0));
+                if (dot(nrm, ray.d) > 0.0) nrm = -nrm;
+                const V3 tg = normalize(v1 - v0);
+                const V3 bt = cross(nrm, tg);
+                const V3 org = (ray.o + ray.d * h.t) + nrm * 1e-4;
+                const uint32_t j = (uint32_t)((smp * max_depth + depth) * 3);
+                const V3 rho = col(albedo, m);
+                if (light_count > 0) {
+                    const uint64_t ka = (uint64_t)(oracle_xi(seed, (uint64_t)p, j, 0) * 16777216.0);
+                    const int64_t li = (int64_t)((ka * (uint64_t)light_count) >> 24);
+                    const uint32_t linst = lights[2 * li], lprim = lights[2 * li + 1];
+                    V3 a, b, c;
+                    world_tri(linst, lprim, a, b, c);
+                    const V3 cr = cross(b - a, c - a);
+                    const double area = 0.5 * length(cr);
+                    const V3 nl = normalize(cr);
+                    const double su = std::sqrt(oracle_xi(seed, (uint64_t)p, j, 1));
+                    const double xc = oracle_xi(seed, (uint64_t)p, j + 1, 0);
+                    const V3 q = a * (1.0 - su) + b * (su * (1.0 - xc)) + c * (su * xc);
+                    V3 w = q - org;
+                    const double dist = length(w);
+                    w = w * (1.0 / dist);
+                    const double cs = dot(nrm, w), cl = std::fabs(dot(nl, w));
+                    if (cs > 0.0 && cl > 0.0) {
+                        HitD sh;
+                        trace_one(*S, RayD{org, w, 0.0, dist * (1.0 - 1e-4)}, true, true, 0xFFFFFFFFu, sh);
+                        if (sh.prim == NONE) {
+                            const V3 El = col(emission, (size_t)mat_offset[linst] + lprim);
+                            const double k = cs * cl / (dist * dist) * (double)light_count * area / PI;
+                            L = L + v3(T.x * rho.x * El.x * k, T.y * rho.y * El.y * k, T.z * rho.z * El.z * k);
+                        }
+                    }
+                }
+                double hs[3];
+                oracle_sample_hemisphere(oracle_xi(seed, (uint64_t)p, j + 1, 1), oracle_xi(seed, (uint64_t)p, j + 2, 0),
+                                         hs);
+                const V3 dir = tg * hs[0] + bt * hs[2] + nrm * hs[1];
+                T = v3(T.x * rho.x, T.y * rho.y, T.z * rho.z);
+                ray = RayD{org, dir, 0.0, INFINITY};
+            }
+            acc = acc + L;
+        }
+        out[3 * p] = acc.x / spp;
+        out[3 * p + 1] = acc.y / spp;
+        out[3 * p + 2] = acc.z / spp;
     });
 }
 

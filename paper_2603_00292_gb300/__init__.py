@@ -102,6 +102,13 @@ class grtBvhInfo(ctypes.Structure):
                 ("mortonBits", ctypes.c_uint32), ("wideNodes", ctypes.c_void_p)]
 
 
+class grtPathTraceInput(ctypes.Structure):
+    _fields_ = [("albedo", ctypes.c_void_p), ("emission", ctypes.c_void_p), ("materialOffset", ctypes.c_void_p),
+                ("lights", ctypes.c_void_p), ("lightCount", ctypes.c_uint32), ("maxDepth", ctypes.c_uint32),
+                ("samplesPerPixel", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("sky", ctypes.c_float * 3), ("reserved2", ctypes.c_float)]
+
+
 class grtDeviceTarget(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("primToLeaf", ctypes.c_void_p),
                 ("frames64", ctypes.c_void_p), ("frames32", ctypes.c_void_p), ("funcTable", ctypes.c_void_p),
@@ -168,6 +175,9 @@ _SIGS = {
     "grtTraceAnyHit": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
     "grtTraceClosestNoAlloc": [_P, _P, _P, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
     "grtTraceAllHits": [_P, _P, _P, _P, _U32, _P, _U32, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
+    "grtGetPathTraceWorkspaceSize": [_U32, ctypes.POINTER(ctypes.c_size_t)],
+    "grtPathTrace": [_P, _P, _P, _U32, ctypes.POINTER(grtPathTraceInput), _P, _P, ctypes.POINTER(grtTraceOptions),
+                     _P],
     "grtGenerateCameraRays": [_P, ctypes.POINTER(grtCamera), _U32, _U32, _P, _P],
     "grtGenerateAORays": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P, _P],
     "grtTraceAmbientOcclusion": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P,
@@ -369,6 +379,25 @@ def grtTraceAllHits(ctx, scene, geom, rays, count, hits, max_hits, counts, table
     """hits: (count * max_hits, 5) records; counts: uint32 device tensor of count entries."""
     check(lib().grtTraceAllHits(ctx, scene, geom, _ptr(rays), count, _ptr(hits), max_hits, _ptr(counts), table,
                                 ctypes.byref(opts) if opts else None, _stream(stream)), "grtTraceAllHits")
+
+
+def path_trace_input(albedo, emission, material_offset, lights, light_count, max_depth, spp, seed,
+                     sky) -> grtPathTraceInput:
+    """albedo / emission: device float32 (M, 3); material_offset: device uint32 per instance;
+    lights: device uint32 (K, 2) (instance, primitive) pairs."""
+    return grtPathTraceInput(_ptr(albedo), _ptr(emission), _ptr(material_offset), _ptr(lights), light_count,
+                             max_depth, spp, 0, seed, (ctypes.c_float * 3)(*[float(x) for x in sky]), 0.0)
+
+
+def grtGetPathTraceWorkspaceSize(count: int) -> int:
+    sz = ctypes.c_size_t()
+    check(lib().grtGetPathTraceWorkspaceSize(count, ctypes.byref(sz)), "grtGetPathTraceWorkspaceSize")
+    return sz.value
+
+
+def grtPathTrace(ctx, scene, rays, count, inp, workspace, radiance, opts=None, stream=None):
+    check(lib().grtPathTrace(ctx, scene, _ptr(rays), count, ctypes.byref(inp), _ptr(workspace), _ptr(radiance),
+                             ctypes.byref(opts) if opts else None, _stream(stream)), "grtPathTrace")
 
 
 def grtTraceClosestNoAlloc(ctx, scene, geom, rays, count, hits, table=None, opts=None, stream=None):

@@ -846,6 +846,250 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
     return GRT_SUCCESS;
 }
 
+// ---------------------------------------------------------------- path tracing (Sec. 5)
+// Path tracing with next event estimation as a wavefront over the library's own queries:
+// per path vertex, closest hit of every live path ray, one shading pass, then any hit of
+// the shadow rays that pass wrote. The shading pass (ptShadeKernel) first credits the
+// previous vertex's light sample when its shadow ray found nothing, then:
+//  * a miss adds T * sky and ends the path; a hit on an emitting triangle adds
+//    T * emission at the first vertex only and ends the path;
+//  * otherwise, in the hit's AO frame (face normal toward the ray, tangent v1 - v0,
+//    origin p + 1e-4 n): one light triangle l = (xi_a * L) >> 24 in integers, a uniform
+//    point q on it (s = sqrt(xi_b): (1-s) a + s (1-xi_c) b + s xi_c c), and if
+//    cos_s > 0 and |cos_l| > 0 a shadow ray over [0, dist (1 - 1e-4)] with the pending
+//    contribution T * (albedo / pi) * cos_s |cos_l| / dist^2 * emission_l * L * area_l;
+//    the next ray leaves along a cosine-weighted direction (xi_d, xi_e); T *= albedo.
+// Random numbers: xi(seed, ray, (sample * maxDepth + depth) * 3 + k, dim) with
+// (k, dim) = (0,0) a, (0,1) b, (1,0) c, (1,1) d, (2,0) e.
+struct PathParams {
+    float4* pathRays;
+    uint32_t* pathHits;
+    float4* shadowRays;
+    uint32_t* shadowHits;
+    float4* T;        // throughput (xyz)
+    float4* L;        // radiance of the current sample (xyz)
+    float4* pending;  // light sample waiting for its shadow ray (xyz)
+    const float* albedo;
+    const float* emission;
+    const uint32_t* materialOffset;
+    const uint32_t* lights;
+    uint32_t lightCount;
+    uint32_t maxDepth;
+    uint32_t n;
+    uint32_t sample;
+    uint32_t spp;
+    uint64_t seed;
+    float3 sky;
+};
+
+__device__ __forceinline__ uint32_t sampleBits24(uint64_t seed, uint64_t pixel, uint32_t sample, uint32_t dim) {
+    const uint64_t c = (pixel << 32) | ((uint64_t)sample << 1) | dim;
+    return (uint32_t)(mix64(seed + (c + 1ull) * 0x9E3779B97F4A7C15ull) >> 40);
+}
+
+__device__ __forceinline__ float3 loadColour(const float* f, size_t m) {
+    return make_float3(__ldg(f + 3 * m), __ldg(f + 3 * m + 1), __ldg(f + 3 * m + 2));
+}
+
+// World-space vertices of primitive `prim` of instance `inst` (float32 forward frame).
+__device__ __forceinline__ void worldTriangle(const TraceParams& P, uint32_t inst, uint32_t prim, float3 v[3]) {
+    const InstanceRecord* R = P.sceneLeaves + P.scenePrimToLeaf[inst];
+    const BvhHeader* g = R->geometry;
+    const float4* rec = reinterpret_cast<const float4*>(g->leaves) + 3 * (size_t)g->primToLeaf[prim];
+    const float4* fr = P.fwd32 + kFrameRows * (size_t)inst;
+    const float4 m0 = fr[0], m1 = fr[1], m2 = fr[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float3 o = f3(rec[k]);
+        v[k] = make_float3(m0.x * o.x + m0.y * o.y + m0.z * o.z + m0.w, m1.x * o.x + m1.y * o.y + m1.z * o.z + m1.w,
+                           m2.x * o.x + m2.y * o.y + m2.z * o.z + m2.w);
+    }
+}
+
+__global__ void __launch_bounds__(256) ptInitKernel(PathParams Q, const float4* rays) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Q.n) return;
+    Q.pathRays[2 * (size_t)i] = rays[2 * (size_t)i];
+    Q.pathRays[2 * (size_t)i + 1] = rays[2 * (size_t)i + 1];
+    Q.T[i] = make_float4(1.f, 1.f, 1.f, 0.f);
+    Q.L[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void creditPending(const PathParams& Q, uint32_t i) {
+    if (Q.shadowRays[2 * (size_t)i + 1].w >= 0.f && Q.shadowHits[5 * (size_t)i + 1] == kInvalid) {
+        const float4 c = Q.pending[i], l = Q.L[i];
+        Q.L[i] = make_float4(l.x + c.x, l.y + c.y, l.z + c.z, 0.f);
+    }
+}
+
+__device__ __forceinline__ void endPath(const PathParams& Q, uint32_t i) {
+    Q.pathRays[2 * (size_t)i + 1].w = -1.f;
+    Q.shadowRays[2 * (size_t)i + 1] = make_float4(0.f, 0.f, 0.f, -1.f);
+}
+
+__global__ void __launch_bounds__(256) ptShadeKernel(TraceParams P, PathParams Q, uint32_t depth) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Q.n) return;
+    if (depth > 0) creditPending(Q, i);
+    const float4* ray = Q.pathRays + 2 * (size_t)i;
+    if (ray[1].w < 0.f) {  // the path has ended
+        Q.shadowRays[2 * (size_t)i + 1] = make_float4(0.f, 0.f, 0.f, -1.f);
+        return;
+    }
+    const uint32_t* hit = Q.pathHits + 5 * (size_t)i;
+    const float4 T = Q.T[i];
+    float4 L = Q.L[i];
+    if (hit[1] == kInvalid) {
+        Q.L[i] = make_float4(L.x + T.x * Q.sky.x, L.y + T.y * Q.sky.y, L.z + T.z * Q.sky.z, 0.f);
+        endPath(Q, i);
+        return;
+    }
+    const size_t m = (size_t)Q.materialOffset[hit[0]] + hit[1];
+    const float3 Le = loadColour(Q.emission, m);
+    if (Le.x != 0.f || Le.y != 0.f || Le.z != 0.f) {
+        if (depth == 0) Q.L[i] = make_float4(L.x + T.x * Le.x, L.y + T.y * Le.y, L.z + T.z * Le.z, 0.f);
+        endPath(Q, i);
+        return;
+    }
+    AoFrame F;
+    aoFrame(P.sceneLeaves, P.scenePrimToLeaf, P.fwd32, ray, hit, F);
+    const float3 rho = loadColour(Q.albedo, m);
+    const uint32_t j = (Q.sample * Q.maxDepth + depth) * 3u;
+    float4 sray1 = make_float4(0.f, 0.f, 0.f, -1.f);
+    if (Q.lightCount > 0) {
+        const uint32_t ka = sampleBits24(Q.seed, i, j, 0);
+        const uint32_t li = (uint32_t)(((uint64_t)ka * Q.lightCount) >> 24);
+        const uint32_t linst = Q.lights[2 * (size_t)li], lprim = Q.lights[2 * (size_t)li + 1];
+        float3 v[3];
+        worldTriangle(P, linst, lprim, v);
+        const float3 cr = cross3(v[1] - v[0], v[2] - v[0]);
+        const float area2 = sqrtf(dot3(cr, cr));  // twice the area
+        const float3 nl = cr * (1.0f / area2);
+        const float su = sqrtf(sampleXi(Q.seed, i, j, 1)), xc = sampleXi(Q.seed, i, j + 1, 0);
+        const float3 q = v[0] * (1.f - su) + v[1] * (su * (1.f - xc)) + v[2] * (su * xc);
+        float3 w = q - F.org;
+        const float dist = sqrtf(dot3(w, w));
+        w = w * (1.0f / dist);
+        const float cs = dot3(F.n, w), cl = fabsf(dot3(nl, w));
+        if (cs > 0.f && cl > 0.f) {
+            const float3 El = loadColour(Q.emission, (size_t)Q.materialOffset[linst] + lprim);
+            const float k = cs * cl / (dist * dist) * (float)Q.lightCount * (0.5f * area2) * (1.0f / 3.14159265358979f);
+            Q.pending[i] = make_float4(T.x * rho.x * El.x * k, T.y * rho.y * El.y * k, T.z * rho.z * El.z * k, 0.f);
+            Q.shadowRays[2 * (size_t)i] = make_float4(F.org.x, F.org.y, F.org.z, 0.f);
+            sray1 = make_float4(w.x, w.y, w.z, dist * (1.f - 1e-4f));
+        }
+    }
+    Q.shadowRays[2 * (size_t)i + 1] = sray1;
+    // next direction: cosine-weighted about n, the AO frame's sample form
+    const float xd = sampleXi(Q.seed, i, j + 1, 1), xe = sampleXi(Q.seed, i, j + 2, 0);
+    float sn, cs2;
+    sincospif(2.0f * xd, &sn, &cs2);
+    const float r = sqrtf(xe);
+    const float3 dir = F.tg * (cs2 * r) + F.bt * (sn * r) + F.n * sqrtf(1.0f - xe);
+    Q.T[i] = make_float4(T.x * rho.x, T.y * rho.y, T.z * rho.z, 0.f);
+    Q.pathRays[2 * (size_t)i] = make_float4(F.org.x, F.org.y, F.org.z, 0.f);
+    Q.pathRays[2 * (size_t)i + 1] = make_float4(dir.x, dir.y, dir.z, INFINITY);
+}
+
+__global__ void __launch_bounds__(256) ptFinishKernel(PathParams Q, float* radiance) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Q.n) return;
+    creditPending(Q, i);
+    const float4 l = Q.L[i];
+    const float inv = 1.0f / (float)Q.spp;
+    float* out = radiance + 3 * (size_t)i;
+    if (Q.sample == 0) {
+        out[0] = l.x * inv, out[1] = l.y * inv, out[2] = l.z * inv;
+    } else {
+        out[0] += l.x * inv, out[1] += l.y * inv, out[2] += l.z * inv;
+    }
+}
+
+// Workspace of a path trace of n rays: path rays, path hits, shadow rays, shadow hits,
+// throughput, radiance, pending light samples.
+static size_t pathWorkspace(uint32_t n, size_t off[7]) {
+    const size_t sizes[7] = {32 * (size_t)n, 20 * (size_t)n, 32 * (size_t)n, 20 * (size_t)n,
+                             16 * (size_t)n, 16 * (size_t)n, 16 * (size_t)n};
+    size_t at = 0;
+    for (int k = 0; k < 7; ++k) {
+        off[k] = at;
+        at = alignUp(at + sizes[k], 256);
+    }
+    return at;
+}
+
+grtError grtGetPathTraceWorkspaceSize(uint32_t rayCount, size_t* sizeBytes) {
+    if (!sizeBytes) return GRT_ERROR_INVALID_PARAMETER;
+    size_t off[7];
+    *sizeBytes = pathWorkspace(rayCount, off);
+    return GRT_SUCCESS;
+}
+
+grtError grtPathTrace(grtContext ctx, grtScene scene, const grtRay* rays, uint32_t rayCount,
+                      const grtPathTraceInput* input, void* workspace, float* radiance,
+                      const grtTraceOptions* options, void* stream) {
+    if (!ctx || !input || input->maxDepth == 0 || input->samplesPerPixel == 0) return GRT_ERROR_INVALID_PARAMETER;
+    Context* c = asContext(ctx);
+    TraceParams P{};
+    bool isScene = false;
+    int bs = 128;
+    grtError e = prepareTrace(c, scene, nullptr, nullptr, options, P, &isScene, &bs);
+    if (e != GRT_SUCCESS || rayCount == 0) return e;
+    if (!rays || !radiance || !workspace || ((uintptr_t)rays & 15) || ((uintptr_t)workspace & 255))
+        return GRT_ERROR_INVALID_PARAMETER;
+    if (!input->albedo || !input->emission || !input->materialOffset || (input->lightCount && !input->lights))
+        return GRT_ERROR_INVALID_PARAMETER;
+    if ((uint64_t)input->samplesPerPixel * input->maxDepth * 3 >= 0x80000000ull) return GRT_ERROR_INVALID_PARAMETER;
+    BvhObject* o = findBvh(scene);
+    P.sceneLeaves = (const InstanceRecord*)o->leaves;
+    P.scenePrimToLeaf = o->primToLeaf;
+    P.fwd32 = (const float4*)o->fwd32;
+    size_t off[7];
+    pathWorkspace(rayCount, off);
+    char* w = static_cast<char*>(workspace);
+    PathParams Q{};
+    Q.pathRays = reinterpret_cast<float4*>(w + off[0]);
+    Q.pathHits = reinterpret_cast<uint32_t*>(w + off[1]);
+    Q.shadowRays = reinterpret_cast<float4*>(w + off[2]);
+    Q.shadowHits = reinterpret_cast<uint32_t*>(w + off[3]);
+    Q.T = reinterpret_cast<float4*>(w + off[4]);
+    Q.L = reinterpret_cast<float4*>(w + off[5]);
+    Q.pending = reinterpret_cast<float4*>(w + off[6]);
+    Q.albedo = input->albedo;
+    Q.emission = input->emission;
+    Q.materialOffset = input->materialOffset;
+    Q.lights = input->lights;
+    Q.lightCount = input->lightCount;
+    Q.maxDepth = input->maxDepth;
+    Q.n = rayCount;
+    Q.spp = input->samplesPerPixel;
+    Q.seed = input->seed;
+    Q.sky = make_float3(input->sky[0], input->sky[1], input->sky[2]);
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned blocks = ceilDiv(rayCount, 256);
+    for (uint32_t smp = 0; smp < Q.spp; ++smp) {
+        Q.sample = smp;
+        ptInitKernel<<<blocks, 256, 0, s>>>(Q, (const float4*)rays);
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
+        for (uint32_t depth = 0; depth < Q.maxDepth; ++depth) {
+            e = launchTrace<false>(ctx, scene, nullptr, (const grtRay*)Q.pathRays, rayCount, (grtHit*)Q.pathHits,
+                                   nullptr, options, stream);
+            if (e != GRT_SUCCESS) return e;
+            ptShadeKernel<<<blocks, 256, 0, s>>>(P, Q, depth);
+            GRT_LAUNCH_CHECK();
+            noteLaunches(1);
+            e = launchTrace<true>(ctx, scene, nullptr, (const grtRay*)Q.shadowRays, rayCount, (grtHit*)Q.shadowHits,
+                                  nullptr, options, stream);
+            if (e != GRT_SUCCESS) return e;
+        }
+        ptFinishKernel<<<blocks, 256, 0, s>>>(Q, radiance);
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
+    }
+    return GRT_SUCCESS;
+}
+
 // Shared-memory budget of the adjoint's block-private gradient copy (4,096 vertices).
 static constexpr size_t kShadePrivateBytes = 96 * 1024;
 

@@ -56,6 +56,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(grt.grtBatchItemRecord) == 40
     assert ctypes.sizeof(grt.grtDeviceTarget) == 7 * 8 + 5 * 4 + 4
     assert ctypes.sizeof(grt.grtBvhInfo) == 3 * 8 + 4 * 4 + 8
+    assert ctypes.sizeof(grt.grtPathTraceInput) == 4 * 8 + 4 * 4 + 8 + 4 * 4
 
 
 def test_host_only_queries_without_a_device(lib):

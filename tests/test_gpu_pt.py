@@ -1,0 +1,109 @@
+"""Path tracing with next event estimation (Sec. 5) on the GPU against the FP64 oracle
+path tracer: the same float32 camera rays, materials, lights, random-number stream and
+path rules. Pixels agree to rounding except where a path meets a tie or grazes an edge
+at some vertex (different hit or shadow decision): those must stay below half a percent."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2603_00292_gb300 as grt
+import scenegen
+from paper_2603_00292_gb300.objects import Geometry, Scene, device_tensor
+
+pytestmark = pytest.mark.gpu
+
+
+def _scene(gpu, count=8):
+    mesh = scenegen.terrain(cells=40, amplitude=0.25)
+    fr = scenegen.random_frames(count, config=41)
+    quad_v = np.array([[-1, 0, -1], [1, 0, -1], [1, 0, 1], [-1, 0, 1]], np.float32)
+    quad_i = np.array([[0, 1, 2], [0, 2, 3]], np.uint32)
+    g = Geometry(gpu, vertices=device_tensor(mesh.vertices), indices=device_tensor(mesh.indices)).build()
+    q = Geometry(gpu, vertices=device_tensor(quad_v), indices=device_tensor(quad_i)).build()
+    lo, hi = scenegen.world_bounds([mesh], np.zeros(count, np.int32), fr)
+    c = 0.5 * (lo + hi)
+    light = np.array([0, 0, 0, 1, 2.0, 1, 2.0, c[0], hi[1] + 3.0, c[2]], np.float32)  # a 4x4 quad above
+    frames = np.concatenate([fr.packed(), light[None, :]])
+    sc = Scene(gpu, [g.handle] * count + [q.handle], device_tensor(frames)).build()
+    S = oracle.Scene()
+    gi, qi = S.add_mesh(mesh.vertices, mesh.indices), S.add_mesh(quad_v, quad_i)
+    for k in range(count):
+        S.add_instance(gi, fr.packed()[k])
+    S.add_instance(qi, light)
+    S.build()
+    nt = mesh.indices.shape[0]
+    rng = np.random.default_rng(42)
+    albedo = np.concatenate([rng.uniform(0.2, 0.8, (nt, 3)), np.zeros((2, 3))]).astype(np.float32)
+    emission = np.concatenate([np.zeros((nt, 3)), np.tile([6.0, 5.0, 4.0], (2, 1))]).astype(np.float32)
+    offsets = np.array([0] * count + [nt], np.uint32)
+    lights = np.array([[count, 0], [count, 1]], np.uint32)
+    scn = scenegen.InstancedScene([mesh], np.zeros(count, np.int32), fr, lo, hi)
+    keep = [g, q, sc]
+    return sc, S, scn, albedo, emission, offsets, lights, keep
+
+
+def _gpu_pt(gpu, sc, rays, albedo, emission, offsets, lights, depth, spp, seed, sky):
+    n = rays.shape[0]
+    ws = torch.empty(grt.grtGetPathTraceWorkspaceSize(n), dtype=torch.uint8, device="cuda")
+    out = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    # the input struct holds raw pointers: the tensors stay alive (named) until the sync
+    a, e, o, li = (device_tensor(x) for x in (albedo, emission, offsets, lights))
+    inp = grt.path_trace_input(a, e, o, li if lights.shape[0] else None, lights.shape[0], depth, spp, seed, sky)
+    grt.grtPathTrace(gpu.handle, sc.handle, device_tensor(rays), n, inp, ws, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _compare(got, ref, frac=0.995):
+    scale = max(float(np.abs(ref).max()), 1e-6)
+    close = np.all(np.abs(got - ref) <= 1e-3 * np.abs(ref) + 1e-4 * scale, axis=1)
+    assert close.mean() >= frac, (close.mean(), np.argwhere(~close)[:5].ravel())
+    assert abs(got.mean() - ref.mean()) <= 2e-3 * abs(ref.mean()) + 1e-6
+    return close
+
+
+@pytest.mark.parametrize("depth,spp,with_lights", [(3, 2, True), (1, 1, True), (4, 1, False)])
+def test_path_trace_matches_the_oracle(gpu, depth, spp, with_lights):
+    sc, S, scn, albedo, emission, offsets, lights, keep = _scene(gpu)
+    W, H = 160, 96
+    cam = scenegen.overview_camera(scn, W, H)
+    rays = oracle.camera_rays(cam.packed(), W, H)
+    sky = np.array([0.3, 0.4, 0.6], np.float32)
+    L = lights if with_lights else np.zeros((0, 2), np.uint32)
+    got = _gpu_pt(gpu, sc, rays, albedo, emission, offsets, L, depth, spp, 1234, sky)
+    ref = S.path_trace(rays, albedo, emission, offsets, L, depth, spp, 1234, sky)
+    _compare(got, ref)
+    lit = ref.sum(axis=1) > 0
+    assert lit.mean() > 0.2
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+
+
+def test_path_trace_direct_light_seen_from_below(gpu):
+    """Rays straight up at the light quad see its emission at the first vertex; rays that
+    miss everything see the sky; both exactly."""
+    sc, S, scn, albedo, emission, offsets, lights, keep = _scene(gpu, count=2)
+    c = 0.5 * (scn.lo + scn.hi)
+    o = np.array([[c[0] + 0.3, scn.hi[1] + 1.0, c[2] - 0.2], [c[0], scn.hi[1] + 1.0, c[2]],
+                  [c[0] + 50.0, scn.hi[1] + 1.0, c[2]]], np.float32)
+    rays = np.zeros((3, 8), np.float32)
+    rays[:, 0:3] = o
+    rays[:, 4:7] = [0, 1, 0]
+    rays[:, 7] = np.inf
+    sky = np.array([0.25, 0.5, 1.0], np.float32)
+    got = _gpu_pt(gpu, sc, rays, albedo, emission, offsets, lights, 3, 4, 5, sky)
+    assert np.allclose(got[0], [6, 5, 4]) and np.allclose(got[1], [6, 5, 4]) and np.allclose(got[2], sky)
+
+
+def test_path_trace_bad_input(gpu):
+    sc, S, scn, albedo, emission, offsets, lights, keep = _scene(gpu, count=1)
+    rays = np.zeros((4, 8), np.float32)
+    ws = torch.empty(grt.grtGetPathTraceWorkspaceSize(4), dtype=torch.uint8, device="cuda")
+    out = torch.empty((4, 3), dtype=torch.float32, device="cuda")
+    a, e, o = (device_tensor(x) for x in (albedo, emission, offsets))
+    bad = grt.path_trace_input(a, e, o, None, 2, 3, 1, 0, (0, 0, 0))  # lights missing
+    with pytest.raises(grt.GrtError):
+        grt.grtPathTrace(gpu.handle, sc.handle, device_tensor(rays), 4, bad, ws, out)
+    zero = grt.path_trace_input(a, e, o, None, 0, 0, 1, 0, (0, 0, 0))  # maxDepth 0
+    with pytest.raises(grt.GrtError):
+        grt.grtPathTrace(gpu.handle, sc.handle, device_tensor(rays), 4, zero, ws, out)
