@@ -622,12 +622,23 @@ __device__ __forceinline__ void sort2(uint32_t& a, uint32_t& b) {
 
 // The slots in mask m go on: the nearest (smallest entry distance) becomes s.next and
 // the others are pushed, farthest first, so that they come off the stack near to far.
-// Keys are the entry distance as an ordered integer with the slot in its two low bits.
+// Two slots take one comparison; three or four go through a sorting network on keys
+// made of the entry distance as an ordered integer with the slot in its two low bits.
 __device__ __forceinline__ void orderChildren(const TraceParams& P, Stack& st, RayState& s, uint32_t m,
                                               const float tn[4], const uint32_t c[4]) {
     if (m == 0) return;
     if ((m & (m - 1u)) == 0) {
         s.next = pick4(c, (uint32_t)__ffs(m) - 1u);
+        return;
+    }
+    if (__popc(m) == 2) {  // the most frequent case after a single hit: one comparison
+        const uint32_t a = (uint32_t)__ffs(m) - 1u, b = 31u - (uint32_t)__clz(m);
+        const float ta = a == 0 ? tn[0] : a == 1 ? tn[1] : tn[2];
+        const float tb = b == 1 ? tn[1] : b == 2 ? tn[2] : tn[3];
+        const uint32_t ca = pick4(c, a), cb = pick4(c, b);
+        const bool swap = tb < ta;
+        if (!st.push(swap ? ca : cb)) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+        s.next = swap ? cb : ca;
         return;
     }
     uint32_t k[4];
