@@ -9,6 +9,9 @@
 // range and split from the sorted codes alone, and leaves walk up to the root,
 // the second child to arrive at a node computing its box.
 #include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "lbvh_block.cuh"
 
@@ -561,6 +564,129 @@ static grtError resetBuildScratch(const BuildLayout& L, char* temp, uint32_t n, 
     return GRT_SUCCESS;
 }
 
+// The launch sequence of a geometry BUILD (above kSmallBuild) or UPDATE on stream s:
+// scratch reset, centroids and bounds, Morton codes, the radix passes, emission, the fit.
+static grtError issueGeometryBuild(Context* c, BvhObject* o, uint32_t op, const grtGeometryBuildInput* input,
+                                   const BuildLayout& L, char* t, const PrimSource& S, cudaStream_t s) {
+    const uint32_t n = o->primCount;
+    grtError e = resetBuildScratch(L, t, n, s);
+    if (e != GRT_SUCCESS) return e;
+    const uint32_t* sorted = nullptr;
+    if (op == GRT_BUILD_OPERATION_BUILD) {
+        primCentroidKernel<<<ceilDiv(n, 256), 256, 0, s>>>(S, (float4*)(t + L.centroids), (uint32_t*)(t + L.bounds));
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
+        e = sortAndEmit(c, o, L, t, s, &sorted);
+        if (e != GRT_SUCCESS) return e;
+    }
+    FitParams P{};
+    P.src = S;
+    P.n = n;
+    P.sortedPrims = sorted;  // null for UPDATE: IDs come from the leaves
+    P.nodes = (float4*)o->nodes;
+    P.wide = (float4*)o->wide;
+    P.leaves = o->leaves;
+    P.primToLeaf = o->primToLeaf;
+    P.parents = (const uint32_t*)o->parents;
+    P.flags = (uint32_t*)(t + L.flags);
+    P.header = o->dHeader;
+    if (input->type == GRT_PRIMITIVE_TRIANGLE_MESH)
+        fitKernel<0><<<ceilDiv(n, 256), 256, 0, s>>>(P);
+    else
+        fitKernel<1><<<ceilDiv(n, 256), 256, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+// Repeated BUILDs of a geometry from the same buffers replay a CUDA graph of the launch
+// sequence. Every kernel argument is a function of the build input (addresses, strides,
+// counts), the temporary buffer, the object's own arrays and the device, so a graph
+// captured once serves every later build with the same description: new vertex data in
+// the same buffers is read by the replay. The graph is captured on a private stream and
+// launched on the caller's; a different description captures again, and a caller's
+// stream that is itself being captured gets the launches directly.
+struct BuildKey {
+    grtGeometryBuildInput input;
+    const void* temp;
+    int device;
+    bool operator==(const BuildKey& k) const { return std::memcmp(this, &k, sizeof(*this)) == 0; }
+};
+struct BuildGraph {
+    BuildKey key;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;
+};
+static std::mutex g_buildGraphLock;
+static std::unordered_map<const BvhObject*, BuildGraph> g_buildGraphs;
+unsigned long long launchCountNow();  // context.cu
+
+static void dropBuildGraph(const BvhObject* o) {
+    std::lock_guard<std::mutex> g(g_buildGraphLock);
+    auto it = g_buildGraphs.find(o);
+    if (it == g_buildGraphs.end()) return;
+    cudaGraphExecDestroy(it->second.exec);
+    g_buildGraphs.erase(it);
+}
+
+static grtError replayOrCaptureBuild(Context* c, BvhObject* o, const grtGeometryBuildInput* input,
+                                     const BuildLayout& L, char* t, const PrimSource& S, cudaStream_t s) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (s && cudaStreamIsCapturing(s, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+    if (cap != cudaStreamCaptureStatusNone) {  // the caller is capturing: issue directly
+        grtError e = issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, s);
+        if (e == GRT_SUCCESS) o->built = true;
+        return e;
+    }
+    BuildKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.input.type = input->type;  // only the fields the launches read
+    if (input->type == GRT_PRIMITIVE_TRIANGLE_MESH)
+        key.input.triangleMesh = input->triangleMesh;
+    else
+        key.input.aabbList = input->aabbList;
+    key.temp = t;
+    key.device = deviceOf(c);
+    std::lock_guard<std::mutex> g(g_buildGraphLock);
+    auto it = g_buildGraphs.find(o);
+    if (it != g_buildGraphs.end() && !(it->second.key == key)) {
+        cudaGraphExecDestroy(it->second.exec);
+        g_buildGraphs.erase(it);
+        it = g_buildGraphs.end();
+    }
+    if (it == g_buildGraphs.end()) {
+        cudaStream_t cs = nullptr;
+        GRT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        const unsigned long long before = launchCountNow();
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        grtError e = ce == cudaSuccess ? issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, cs)
+                                       : GRT_ERROR_CUDA;
+        if (ce == cudaSuccess) ce = cudaStreamEndCapture(cs, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (e == GRT_SUCCESS && ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (e != GRT_SUCCESS || ce != cudaSuccess) {  // no graph: the launches go straight to s
+            cudaGetLastError();
+            if (exec) cudaGraphExecDestroy(exec);
+            e = issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, s);
+            if (e == GRT_SUCCESS) o->built = true;
+            return e;
+        }
+        BuildGraph bg;
+        bg.key = key;
+        bg.exec = exec;
+        bg.launches = launchCountNow() - before;  // counted once at capture, for this first replay
+        it = g_buildGraphs.emplace(o, bg).first;
+    } else {
+        noteLaunches((unsigned)it->second.launches);
+    }
+    GRT_CUDA(cudaGraphLaunch(it->second.exec, s));
+    o->built = true;
+    return GRT_SUCCESS;
+}
+
 }  // namespace grt
 
 using namespace grt;
@@ -623,33 +749,9 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
         o->built = true;
         return GRT_SUCCESS;
     }
-    e = resetBuildScratch(L, t, n, s);
+    if (op == GRT_BUILD_OPERATION_BUILD) return replayOrCaptureBuild(c, o, input, L, t, S, s);
+    e = issueGeometryBuild(c, o, op, input, L, t, S, s);
     if (e != GRT_SUCCESS) return e;
-    const uint32_t* sorted = nullptr;
-    if (op == GRT_BUILD_OPERATION_BUILD) {
-        primCentroidKernel<<<ceilDiv(n, 256), 256, 0, s>>>(S, (float4*)(t + L.centroids), (uint32_t*)(t + L.bounds));
-        GRT_LAUNCH_CHECK();
-        noteLaunches(1);
-        e = sortAndEmit(c, o, L, t, s, &sorted);
-        if (e != GRT_SUCCESS) return e;
-    }
-    FitParams P{};
-    P.src = S;
-    P.n = n;
-    P.sortedPrims = sorted;  // null for UPDATE: IDs come from the leaves
-    P.nodes = (float4*)o->nodes;
-    P.wide = (float4*)o->wide;
-    P.leaves = o->leaves;
-    P.primToLeaf = o->primToLeaf;
-    P.parents = (const uint32_t*)o->parents;
-    P.flags = (uint32_t*)(t + L.flags);
-    P.header = o->dHeader;
-    if (input->type == GRT_PRIMITIVE_TRIANGLE_MESH)
-        fitKernel<0><<<ceilDiv(n, 256), 256, 0, s>>>(P);
-    else
-        fitKernel<1><<<ceilDiv(n, 256), 256, 0, s>>>(P);
-    GRT_LAUNCH_CHECK();
-    noteLaunches(1);
     o->built = true;
     return GRT_SUCCESS;
 }
@@ -657,6 +759,7 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
 grtError grtDestroyGeometry(grtContext ctx, grtGeometry geom) {
     BvhObject* o = findBvh(geom);
     if (!ctx || !o || o->primType == kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
+    dropBuildGraph(o);
     destroyBvhObject(o);
     return GRT_SUCCESS;
 }

@@ -51,6 +51,7 @@ static std::atomic<unsigned long long> g_launches{0};
 
 int logLevel() { return g_logLevel; }
 void noteLaunches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launchCountNow() { return g_launches.load(); }
 
 void logf(int level, const char* fmt, ...) {
     if (!(g_logLevel & level)) return;
