@@ -275,7 +275,10 @@ grtError grtTraceAllHits(grtContext ctx, grtScene scene, grtGeometry geom, const
 /* Materials and lights of a path trace. Primitive p of instance i uses material entry
  * materialOffset[i] + p of albedo and emission (3 floats each, device); an entry with
  * nonzero emission marks an emitting triangle. lights lists the emitting triangles for
- * next event estimation as lightCount (instanceID, primID) pairs (device). */
+ * next event estimation as lightCount (instanceID, primID) pairs (device). The caller
+ * keeps every material index within albedo and emission (the device does not know their
+ * length). A light entry naming no triangle of the scene is skipped and latches
+ * GRT_ERROR_INVALID_PARAMETER (grtGetLastDeviceError). */
 typedef struct grtPathTraceInput {
     const float* albedo;
     const float* emission;

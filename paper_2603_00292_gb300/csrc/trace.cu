@@ -874,6 +874,7 @@ struct PathParams {
     const uint32_t* materialOffset;
     const uint32_t* lights;
     uint32_t lightCount;
+    uint32_t instanceCount;  // of the scene: light entries naming another instance are rejected
     uint32_t maxDepth;
     uint32_t n;
     uint32_t sample;
@@ -960,23 +961,33 @@ __global__ void __launch_bounds__(256) ptShadeKernel(TraceParams P, PathParams Q
         const uint32_t ka = sampleBits24(Q.seed, i, j, 0);
         const uint32_t li = (uint32_t)(((uint64_t)ka * Q.lightCount) >> 24);
         const uint32_t linst = Q.lights[2 * (size_t)li], lprim = Q.lights[2 * (size_t)li + 1];
-        float3 v[3];
-        worldTriangle(P, linst, lprim, v);
-        const float3 cr = cross3(v[1] - v[0], v[2] - v[0]);
-        const float area2 = sqrtf(dot3(cr, cr));  // twice the area
-        const float3 nl = cr * (1.0f / area2);
-        const float su = sqrtf(sampleXi(Q.seed, i, j, 1)), xc = sampleXi(Q.seed, i, j + 1, 0);
-        const float3 q = v[0] * (1.f - su) + v[1] * (su * (1.f - xc)) + v[2] * (su * xc);
-        float3 w = q - F.org;
-        const float dist = sqrtf(dot3(w, w));
-        w = w * (1.0f / dist);
-        const float cs = dot3(F.n, w), cl = fabsf(dot3(nl, w));
-        if (cs > 0.f && cl > 0.f) {
-            const float3 El = loadColour(Q.emission, (size_t)Q.materialOffset[linst] + lprim);
-            const float k = cs * cl / (dist * dist) * (float)Q.lightCount * (0.5f * area2) * (1.0f / 3.14159265358979f);
-            Q.pending[i] = make_float4(T.x * rho.x * El.x * k, T.y * rho.y * El.y * k, T.z * rho.z * El.z * k, 0.f);
-            Q.shadowRays[2 * (size_t)i] = make_float4(F.org.x, F.org.y, F.org.z, 0.f);
-            sray1 = make_float4(w.x, w.y, w.z, dist * (1.f - 1e-4f));
+        bool lightOk = linst < Q.instanceCount;
+        if (lightOk) {
+            const InstanceRecord* R = P.sceneLeaves + P.scenePrimToLeaf[linst];
+            lightOk = instPrimType(R->typeBits) == GRT_PRIMITIVE_TRIANGLE_MESH && lprim < R->geometry->primCount;
+        }
+        if (!lightOk) {
+            latchError(P.error, GRT_ERROR_INVALID_PARAMETER);  // no light sample from a bad entry
+        } else {
+            float3 v[3];
+            worldTriangle(P, linst, lprim, v);
+            const float3 cr = cross3(v[1] - v[0], v[2] - v[0]);
+            const float area2 = sqrtf(dot3(cr, cr));  // twice the area
+            const float3 nl = cr * (1.0f / area2);
+            const float su = sqrtf(sampleXi(Q.seed, i, j, 1)), xc = sampleXi(Q.seed, i, j + 1, 0);
+            const float3 q = v[0] * (1.f - su) + v[1] * (su * (1.f - xc)) + v[2] * (su * xc);
+            float3 w = q - F.org;
+            const float dist = sqrtf(dot3(w, w));
+            w = w * (1.0f / dist);
+            const float cs = dot3(F.n, w), cl = fabsf(dot3(nl, w));
+            if (cs > 0.f && cl > 0.f) {
+                const float3 El = loadColour(Q.emission, (size_t)Q.materialOffset[linst] + lprim);
+                const float k =
+                    cs * cl / (dist * dist) * (float)Q.lightCount * (0.5f * area2) * (1.0f / 3.14159265358979f);
+                Q.pending[i] = make_float4(T.x * rho.x * El.x * k, T.y * rho.y * El.y * k, T.z * rho.z * El.z * k, 0.f);
+                Q.shadowRays[2 * (size_t)i] = make_float4(F.org.x, F.org.y, F.org.z, 0.f);
+                sray1 = make_float4(w.x, w.y, w.z, dist * (1.f - 1e-4f));
+            }
         }
     }
     Q.shadowRays[2 * (size_t)i + 1] = sray1;
@@ -1060,6 +1071,7 @@ grtError grtPathTrace(grtContext ctx, grtScene scene, const grtRay* rays, uint32
     Q.materialOffset = input->materialOffset;
     Q.lights = input->lights;
     Q.lightCount = input->lightCount;
+    Q.instanceCount = o->primCount;
     Q.maxDepth = input->maxDepth;
     Q.n = rayCount;
     Q.spp = input->samplesPerPixel;

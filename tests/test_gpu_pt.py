@@ -107,3 +107,19 @@ def test_path_trace_bad_input(gpu):
     zero = grt.path_trace_input(a, e, o, None, 0, 0, 1, 0, (0, 0, 0))  # maxDepth 0
     with pytest.raises(grt.GrtError):
         grt.grtPathTrace(gpu.handle, sc.handle, device_tensor(rays), 4, zero, ws, out)
+
+
+def test_path_trace_rejects_a_light_entry_outside_the_scene(gpu):
+    """A light entry naming no triangle of the scene gives no light sample and latches
+    GRT_ERROR_INVALID_PARAMETER; the rest of the path (sky, emitters, bounces) stands."""
+    sc, S, scn, albedo, emission, offsets, lights, keep = _scene(gpu, count=2)
+    W, H = 64, 48
+    rays = oracle.camera_rays(scenegen.overview_camera(scn, W, H).packed(), W, H)
+    sky = np.array([0.3, 0.4, 0.6], np.float32)
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+    bad = np.array([[99, 0]], np.uint32)  # instance 99 does not exist
+    got = _gpu_pt(gpu, sc, rays, albedo, emission, offsets, bad, 2, 1, 9, sky)
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_ERROR_INVALID_PARAMETER
+    ref = S.path_trace(rays, albedo, emission, offsets, np.zeros((0, 2), np.uint32), 2, 1, 9, sky)
+    _compare(got, ref)  # as without lights
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
