@@ -355,6 +355,41 @@ def run_grt(args, rank, world, local):
                                                   None, sh))
     ms_all = timed(lambda: grt.grtTraceAllHits(ctx.handle, scene.handle, None, rays, npix, ahits, kmax, acount,
                                                None, None, sh))
+    # the three build options of the terrain geometry (linear BVH, clustering with search
+    # radius 8 and 32): build time, surface-area cost of the tree (sum of internal node
+    # box areas over the root's), the closest + AO traces and the whole step over it
+    from paper_2603_00292_gb300.objects import read_device
+    builds = {}
+    for name, flags in (("fast_lbvh", grt.GRT_BUILD_PREFER_FAST), ("balanced_ploc8", grt.GRT_BUILD_PREFER_BALANCED),
+                        ("high_quality_ploc32", grt.GRT_BUILD_PREFER_HIGH_QUALITY)):
+        gq = Geometry(ctx, vertices=verts, indices=idx, build_flags=flags).build(sh)
+        sq = Scene(ctx, [gq.handle] * WORKLOAD["instances"], frames).build(sh)
+        qhits = new_hits(npix)
+
+        def q_trace(sq=sq, qhits=qhits):
+            grt.grtTraceClosest(ctx.handle, sq.handle, None, rays, npix, qhits, None, None, sh)
+            grt.grtTraceAmbientOcclusion(ctx.handle, sq.handle, rays, qhits, npix, spp, seed, length, ao, None, sh)
+
+        def q_step(gq=gq, sq=sq, q_trace=q_trace):
+            gq.build(sh)
+            sq.build(sh)
+            grt.grtGenerateCameraRays(ctx.handle, gcam, W, H, rays, sh)
+            q_trace()
+
+        ms_b = timed(lambda gq=gq: gq.build(sh))
+        ms_t = timed(q_trace)
+        ms_s = timed(q_step)
+        torch.cuda.synchronize()
+        inf = gq.info()
+        nd = read_device(inf.nodes, inf.nodeCount * 64, np.float32).reshape(-1, 16).astype(np.float64)
+        ext = np.maximum(nd[:, [1, 5, 9]], nd[:, [3, 7, 11]]) - np.minimum(nd[:, [0, 4, 8]], nd[:, [2, 6, 10]])
+        area = ext[:, 0] * ext[:, 1] + ext[:, 1] * ext[:, 2] + ext[:, 2] * ext[:, 0]
+        qhit = int((qhits[:, 1].view(torch.int32) != -1).sum().item())
+        builds[name] = {"blas_build_ms": round(ms_b, 4), "sah_cost": round(float(area.sum() / area[0]), 3),
+                        "closest_plus_ao_ms": round(ms_t, 4), "step_ms": round(ms_s, 4),
+                        "primary_hits": qhit}
+        sq.close()
+        gq.close()
     torch.cuda.synchronize()
     mhit = int((mhits[:, 1].view(torch.int32) != -1).sum().item())
     all_found = int(acount.sum().item())
@@ -365,7 +400,8 @@ def run_grt(args, rank, world, local):
                                      "mrays_per_s": round(npix / ms_all / 1e3, 1)},
                 "path_trace_nee": {"ms": round(ms_pt, 4), "max_depth": 3, "spp": 1,
                                    "mpaths_per_s": round(npix / ms_pt / 1e3, 1),
-                                   "mean_radiance": round(float(pt_out.mean().item()), 5)}}
+                                   "mean_radiance": round(float(pt_out.mean().item()), 5)},
+                "build_options": builds}
     assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
 
     # --------------------------------------------------- traversal work per ray (counting pass)

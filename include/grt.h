@@ -114,8 +114,19 @@ typedef struct grtGeometryBuildInput {
     grtAABBListPrimitive aabbList;
 } grtGeometryBuildInput;
 
-/* The paper's fast / balanced / high-quality flags (Sec. 7.2) are accepted; every
- * flag builds the same linear BVH (LBVH). */
+/* The paper's fast / balanced / high-quality flags (Sec. 7.2) choose the build of a
+ * geometry (Sec. 6.2 "BVH Construction": top-down splitting or bottom-up clustering):
+ *   FAST         linear BVH: Morton codes, radix sort, Karras emission, bottom-up fit;
+ *   BALANCED     bottom-up clustering (PLOC, Meister and Bittner 2018) over the same
+ *                Morton order, nearest neighbours searched 8 positions either side;
+ *   HIGH_QUALITY the same clustering with a 32-position search (the spatial-split
+ *                builder the paper names for this flag is not provided).
+ * All three give binary nodes, 4-wide nodes and leaves of the same layout, and all
+ * support GRT_BUILD_OPERATION_UPDATE. A geometry's flag is fixed by grtCreateGeometry;
+ * grtGetGeometryBuildTemporaryBufferSize and grtBuildGeometry must be given the same
+ * flag (the clustering builds need 68 more bytes of temporary memory per primitive).
+ * Scene (top-level) builds always use the linear BVH. Other values are rejected with
+ * GRT_ERROR_INVALID_PARAMETER; so are clustering builds of 2^30 or more primitives. */
 typedef enum grtBuildFlags {
     GRT_BUILD_PREFER_FAST = 0,
     GRT_BUILD_PREFER_BALANCED = 1,
@@ -139,9 +150,13 @@ grtError grtGetGeometryBuildTemporaryBufferSize(grtContext ctx, const grtGeometr
 /* Allocates the library-owned node and leaf arrays for `input`'s primitive count. */
 grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, const grtBuildOptions* options,
                            grtGeometry* out);
-/* Enqueues the LBVH build (or, for UPDATE, the refit) on `stream`. `temp` is a
- * device buffer of at least the queried size, 16-byte aligned. The primitive count
- * must equal the one given to grtCreateGeometry. */
+/* Enqueues the build chosen by the geometry's flag (or, for UPDATE, the refit) on
+ * `stream`. `temp` is a device buffer of at least the size queried with the same
+ * options, 16-byte aligned. The primitive count must equal the one given to
+ * grtCreateGeometry. A clustering build is one persistent launch whose blocks wait on
+ * one another at grid barriers; each wait is bounded (2 s), and one that runs out (the
+ * blocks could not all be resident, e.g. beside other work on the device) latches
+ * GRT_ERROR_TIMEOUT for grtGetLastDeviceError and leaves an unusable tree. */
 grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInput* input,
                           const grtBuildOptions* options, void* temp, void* stream, grtGeometry geom);
 grtError grtDestroyGeometry(grtContext ctx, grtGeometry geom);

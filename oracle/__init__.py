@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             L.oracle_stable_sort.argtypes = [P, i64, P, P]
             L.oracle_topology.argtypes = [P, i64, ctypes.c_int, P, P, P, P]
             L.oracle_fit.argtypes = [P, P, i64, P, P, P, P]
+            L.oracle_ploc.argtypes = [P, P, i64, ctypes.c_int, P, P, P, P, P]
             L.oracle_sah_cost.argtypes = [P, P, i64]
             L.oracle_sah_cost.restype = ctypes.c_double
             L.oracle_xi.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
@@ -205,6 +206,39 @@ def lbvh(leaf_lo, leaf_hi, centroids, bits_per_axis: int):
     return dict(centroid_lo=clo, centroid_hi=chi, codes=codes, sorted_codes=sk, order=order, childL=cl,
                 childR=cr, parent_internal=pi, parent_leaf=pl, node_lo=nlo, node_hi=nhi, leaf_lo=slo,
                 leaf_hi=shi)
+
+
+def ploc_topology(leaf_lo, leaf_hi, radius: int):
+    """Clustering hierarchy over leaves in sorted order: (childL, childR, parent_internal,
+    parent_leaf, iterations), in the format of topology()."""
+    lo = _c(leaf_lo, np.float32)
+    hi = _c(leaf_hi, np.float32)
+    n = lo.shape[0]
+    m = max(n - 1, 0)
+    cl = np.full(m, -1, np.int32)
+    cr = np.full(m, -1, np.int32)
+    pi = np.full(m, -1, np.int32)
+    pl = np.full(n, -1, np.int32)
+    it = np.zeros(1, np.int64)
+    if n >= 2:
+        lib().oracle_ploc(_p(lo), _p(hi), n, int(radius), _p(cl), _p(cr), _p(pi), _p(pl), _p(it))
+    return cl, cr, pi, pl, int(it[0])
+
+
+def ploc(leaf_lo, leaf_hi, centroids, bits_per_axis: int, radius: int):
+    """The whole clustering-build reference: the LBVH's Morton order (bounds, codes,
+    stable sort), then clustering with the given search radius, then the fit. Returns a
+    dict with the keys of lbvh() plus 'iterations'."""
+    clo, chi = centroid_bounds(centroids)
+    codes = morton(centroids, clo, chi, bits_per_axis)
+    sk, order = stable_sort(codes)
+    slo = np.ascontiguousarray(np.asarray(leaf_lo)[order])
+    shi = np.ascontiguousarray(np.asarray(leaf_hi)[order])
+    cl, cr, pi, pl, iters = ploc_topology(slo, shi, radius)
+    nlo, nhi = fit(cl, cr, slo, shi)
+    return dict(centroid_lo=clo, centroid_hi=chi, codes=codes, sorted_codes=sk, order=order, childL=cl,
+                childR=cr, parent_internal=pi, parent_leaf=pl, node_lo=nlo, node_hi=nhi, leaf_lo=slo,
+                leaf_hi=shi, iterations=iters)
 
 
 def wide_nodes(ref):

@@ -15,7 +15,10 @@
 //    with Karras's numbering: root 0, an internal left child is numbered by the
 //    last leaf of its range, an internal right child by the first;
 //  * the fit: each internal box is the union of its children's boxes (the bottom-up
-//    refit from child volumes of the paper's Sec. 6.2 "BVH Construction").
+//    refit from child volumes of the paper's Sec. 6.2 "BVH Construction");
+//  * the clustering build (bottom-up, Sec. 6.2; PLOC of Meister and Bittner, "Parallel
+//    Locally-Ordered Clustering for Bounding Volume Hierarchy Construction", TVCG 2018),
+//    one iteration at a time over a plain array of clusters.
 //
 // Compile with -ffp-contract=off so no multiply-add is fused.
 #include <algorithm>
@@ -64,6 +67,26 @@ uint32_t quantise(float c, float lo, float hi, int bits) {
     if (!(f >= 0.0)) f = 0.0;  // also maps NaN to 0
     if (f > top) f = top;
     return (uint32_t)f;
+}
+
+// Half the surface area of the union of boxes a and b, float32, in the order
+// (dx*dy + dy*dz) + dz*dx, plus +0 so a zero area is +0.
+float union_area(const float* alo, const float* ahi, const float* blo, const float* bhi) {
+    float d[3];
+    for (int k = 0; k < 3; ++k) d[k] = std::fmax(ahi[k], bhi[k]) - std::fmin(alo[k], blo[k]);
+    float a = d[0] * d[1] + d[1] * d[2];
+    a = a + d[2] * d[0];
+    return a + 0.0f;
+}
+
+// MurmurHash3's 32-bit finaliser (fmix32, Appleby).
+uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
 }
 
 }  // namespace
@@ -213,6 +236,85 @@ void oracle_fit(const int32_t* childL, const int32_t* childR, int64_t n, const f
         }
         st.pop_back();
     }
+}
+
+// Clustering build over n >= 2 leaves in sorted order (boxes leaf_lo/hi, 3*n float32).
+// Clusters start as the leaves. One iteration:
+//   1. nearest neighbour of each cluster i among positions i-radius..i+radius (not i):
+//      smallest union area; equal areas by the pair hash fmix32(fmix32(a) + b) of the
+//      two positions a < b; then the lower position;
+//   2. each pair that are each other's nearest neighbour merges; the new internal node
+//      has the lower position's cluster as left child and takes that position;
+//   3. the remaining clusters close ranks in their order.
+// The m-th merge of the build (iterations in order, merges within one by position)
+// is internal node n-2-m, so the last one is the root, 0. Output in the format of
+// oracle_topology; *iterations = number of iterations run.
+void oracle_ploc(const float* leaf_lo, const float* leaf_hi, int64_t n, int radius, int32_t* childL,
+                 int32_t* childR, int32_t* parent_internal, int32_t* parent_leaf, int64_t* iterations) {
+    *iterations = 0;
+    if (n < 2) return;
+    struct Cluster {
+        float lo[3], hi[3];
+        int32_t id;  // leaf: LEAF | sorted position; internal: node index
+    };
+    std::vector<Cluster> cur((size_t)n);
+    for (int64_t k = 0; k < n; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            cur[(size_t)k].lo[a] = leaf_lo[3 * k + a];
+            cur[(size_t)k].hi[a] = leaf_hi[3 * k + a];
+        }
+        cur[(size_t)k].id = LEAF | (int32_t)k;
+    }
+    auto link = [&](int32_t child, int32_t parent) {
+        if (child & LEAF)
+            parent_leaf[child & 0x7fffffff] = parent;
+        else
+            parent_internal[child] = parent;
+    };
+    int64_t merges = 0;
+    while (cur.size() > 1) {
+        const int64_t m = (int64_t)cur.size();
+        std::vector<int64_t> nearest((size_t)m);
+        for (int64_t i = 0; i < m; ++i) {
+            uint64_t best_key = ~0ull;
+            int64_t best = -1;
+            for (int64_t j = std::max<int64_t>(0, i - radius); j <= std::min<int64_t>(m - 1, i + radius); ++j) {
+                if (j == i) continue;
+                const Cluster &a = cur[(size_t)i], &b = cur[(size_t)j];
+                const float area = union_area(a.lo, a.hi, b.lo, b.hi);
+                uint32_t bits;
+                std::memcpy(&bits, &area, 4);
+                const uint32_t lo = (uint32_t)std::min(i, j), hi = (uint32_t)std::max(i, j);
+                const uint64_t key = ((uint64_t)bits << 32) | fmix32(fmix32(lo) + hi);
+                if (key < best_key) best_key = key, best = j;  // j ascends: ties keep the lower j
+            }
+            nearest[(size_t)i] = best;
+        }
+        std::vector<Cluster> next;
+        for (int64_t i = 0; i < m; ++i) {
+            const int64_t j = nearest[(size_t)i];
+            const bool mutual = nearest[(size_t)j] == i;
+            if (mutual && j < i) continue;  // merged into the cluster at j
+            if (!mutual) {
+                next.push_back(cur[(size_t)i]);
+                continue;
+            }
+            const int32_t q = (int32_t)(n - 2 - merges);
+            ++merges;
+            const Cluster &a = cur[(size_t)i], &b = cur[(size_t)j];
+            childL[q] = a.id;
+            childR[q] = b.id;
+            link(a.id, q);
+            link(b.id, q);
+            Cluster u;
+            for (int k = 0; k < 3; ++k) u.lo[k] = std::fmin(a.lo[k], b.lo[k]), u.hi[k] = std::fmax(a.hi[k], b.hi[k]);
+            u.id = q;
+            next.push_back(u);
+        }
+        cur.swap(next);
+        ++*iterations;
+    }
+    parent_internal[0] = -1;
 }
 
 // Surface-area cost of a binary BVH: sum over internal nodes of box area, divided by

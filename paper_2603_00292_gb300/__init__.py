@@ -32,6 +32,9 @@ GRT_PRIMITIVE_TRIANGLE_MESH = 0
 GRT_PRIMITIVE_AABB_LIST = 1
 GRT_BUILD_OPERATION_BUILD = 0
 GRT_BUILD_OPERATION_UPDATE = 1
+GRT_BUILD_PREFER_FAST = 0          # linear BVH (Morton order, Karras emission)
+GRT_BUILD_PREFER_BALANCED = 1      # PLOC clustering, search radius 8
+GRT_BUILD_PREFER_HIGH_QUALITY = 2  # PLOC clustering, search radius 32
 GRT_INSTANCE_GEOMETRY = 0
 GRT_INTERSECT_NONE = 0
 GRT_INTERSECT_SPHERE = 1
@@ -281,7 +284,7 @@ def aabb_list_input(boxes, count=None, stride=24, geom_type=0) -> grtGeometryBui
                                  grtAABBListPrimitive(n, stride, _ptr(boxes)))
 
 
-def build_options(morton_bits: int = 0, flags: int = 1) -> grtBuildOptions:
+def build_options(morton_bits: int = 0, flags: int = GRT_BUILD_PREFER_FAST) -> grtBuildOptions:
     return grtBuildOptions(flags, morton_bits)
 
 

@@ -14,6 +14,7 @@
 #include <unordered_map>
 
 #include "lbvh_block.cuh"
+#include "ploc.cuh"
 
 namespace grt {
 
@@ -524,7 +525,7 @@ static void destroyBvhObject(BvhObject* o) {
 
 // Morton + sort + Karras over the centroids already in temp (count >= 1).
 static grtError sortAndEmit(Context* ctx, BvhObject* o, const BuildLayout& L, char* temp, cudaStream_t s,
-                            const uint32_t** sortedOut) {
+                            const uint32_t** sortedOut, bool emit = true) {
     const uint32_t n = o->primCount;
     const float4* cen = (const float4*)(temp + L.centroids);
     const uint32_t* bounds = (const uint32_t*)(temp + L.bounds);
@@ -543,7 +544,7 @@ static grtError sortAndEmit(Context* ctx, BvhObject* o, const BuildLayout& L, ch
                              s, &fb);
     if (err != GRT_SUCCESS) return err;
     const void* sk = temp + L.keys[fb];
-    if (n >= 2) {
+    if (n >= 2 && emit) {
         if (o->mortonBits == 30)
             karrasKernel<uint32_t><<<ceilDiv(n - 1, 256), 256, 0, s>>>((const uint32_t*)sk, (int)n,
                                                                         (float4*)o->nodes, (uint32_t*)o->parents);
@@ -564,10 +565,73 @@ static grtError resetBuildScratch(const BuildLayout& L, char* temp, uint32_t n, 
     return GRT_SUCCESS;
 }
 
+// ======================================================================= clustering builds
+// A geometry's build method is fixed when it is created: 0 = LBVH (GRT_BUILD_PREFER_FAST),
+// else PLOC with this search radius (ploc.cuh).
+static uint32_t clusterRadius(const grtBuildOptions* opt) {
+    if (!opt || opt->buildFlags == GRT_BUILD_PREFER_FAST) return 0;
+    return opt->buildFlags == GRT_BUILD_PREFER_BALANCED ? 8u : 32u;
+}
+static bool validBuildFlags(const grtBuildOptions* opt) { return !opt || opt->buildFlags <= 2u; }
+
+static std::mutex g_methodLock;
+static std::unordered_map<const BvhObject*, uint32_t> g_clusterRadius;  // objects with a PLOC build
+
+static uint32_t radiusOf(const BvhObject* o) {
+    std::lock_guard<std::mutex> g(g_methodLock);
+    auto it = g_clusterRadius.find(o);
+    return it == g_clusterRadius.end() ? 0u : it->second;
+}
+
+// PLOC scratch after the LBVH layout: two cluster arrays (32 B per cluster), the
+// per-position neighbour words, per-block counts and the barrier words.
+struct PlocLayout {
+    size_t clusters, pick, counts, sync, total;
+};
+static PlocLayout plocLayout(const BuildLayout& L, uint32_t n) {
+    PlocLayout P{};
+    const size_t m = n ? n : 1;
+    P.clusters = alignUp(L.total, 256);
+    P.pick = P.clusters + alignUp(2 * 32 * m, 256);
+    P.counts = P.pick + alignUp(4 * m, 256);
+    P.sync = P.counts + alignUp(8 * (size_t)ceilDiv(m, kPlocThreads), 256);
+    P.total = P.sync + 256;
+    return P;
+}
+
+// The clustering kernel over the sorted leaves: writes child words and parent links.
+static grtError launchPloc(Context* c, BvhObject* o, const BuildLayout& L, char* t, const PrimSource& S,
+                           const uint32_t* sorted, uint32_t radius, cudaStream_t s) {
+    const uint32_t n = o->primCount;
+    const PlocLayout Q = plocLayout(L, n);
+    PlocParams P{};
+    P.src = S;
+    P.n = n;
+    P.radius = radius;
+    P.sortedPrims = sorted;
+    P.clusters[0] = (float4*)(t + Q.clusters);
+    P.clusters[1] = P.clusters[0] + 2 * (size_t)n;
+    P.pick = (uint32_t*)(t + Q.pick);
+    P.blockCounts = (uint2*)(t + Q.counts);
+    P.sync = (uint32_t*)(t + Q.sync);
+    P.nodes = (float4*)o->nodes;
+    P.parents = (uint32_t*)o->parents;
+    P.error = &workspace(c)->error;
+    P.waitNs = 2000000000ull;
+    const uint32_t blocks = std::min<uint32_t>(ceilDiv(n, kPlocThreads), 2u * (uint32_t)std::max(smCount(c), 1));
+    GRT_CUDA(cudaMemsetAsync(P.sync, 0, 16, s));
+    plocKernel<<<blocks, kPlocThreads, plocSmemBytes(radius), s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
 // The launch sequence of a geometry BUILD (above kSmallBuild) or UPDATE on stream s:
-// scratch reset, centroids and bounds, Morton codes, the radix passes, emission, the fit.
+// scratch reset, centroids and bounds, Morton codes, the radix passes, the hierarchy
+// (Karras emission, or PLOC clustering when radius > 0), the fit.
 static grtError issueGeometryBuild(Context* c, BvhObject* o, uint32_t op, const grtGeometryBuildInput* input,
-                                   const BuildLayout& L, char* t, const PrimSource& S, cudaStream_t s) {
+                                   const BuildLayout& L, char* t, const PrimSource& S, cudaStream_t s,
+                                   uint32_t radius = 0) {
     const uint32_t n = o->primCount;
     grtError e = resetBuildScratch(L, t, n, s);
     if (e != GRT_SUCCESS) return e;
@@ -576,8 +640,12 @@ static grtError issueGeometryBuild(Context* c, BvhObject* o, uint32_t op, const 
         primCentroidKernel<<<ceilDiv(n, 256), 256, 0, s>>>(S, (float4*)(t + L.centroids), (uint32_t*)(t + L.bounds));
         GRT_LAUNCH_CHECK();
         noteLaunches(1);
-        e = sortAndEmit(c, o, L, t, s, &sorted);
+        e = sortAndEmit(c, o, L, t, s, &sorted, radius == 0);
         if (e != GRT_SUCCESS) return e;
+        if (radius != 0 && n >= 2) {
+            e = launchPloc(c, o, L, t, S, sorted, radius, s);
+            if (e != GRT_SUCCESS) return e;
+        }
     }
     FitParams P{};
     P.src = S;
@@ -610,6 +678,7 @@ struct BuildKey {
     grtGeometryBuildInput input;
     const void* temp;
     int device;
+    uint32_t radius;
     bool operator==(const BuildKey& k) const { return std::memcmp(this, &k, sizeof(*this)) == 0; }
 };
 struct BuildGraph {
@@ -630,11 +699,12 @@ static void dropBuildGraph(const BvhObject* o) {
 }
 
 static grtError replayOrCaptureBuild(Context* c, BvhObject* o, const grtGeometryBuildInput* input,
-                                     const BuildLayout& L, char* t, const PrimSource& S, cudaStream_t s) {
+                                     const BuildLayout& L, char* t, const PrimSource& S, cudaStream_t s,
+                                     uint32_t radius) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (s && cudaStreamIsCapturing(s, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
     if (cap != cudaStreamCaptureStatusNone) {  // the caller is capturing: issue directly
-        grtError e = issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, s);
+        grtError e = issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, s, radius);
         if (e == GRT_SUCCESS) o->built = true;
         return e;
     }
@@ -647,6 +717,7 @@ static grtError replayOrCaptureBuild(Context* c, BvhObject* o, const grtGeometry
         key.input.aabbList = input->aabbList;
     key.temp = t;
     key.device = deviceOf(c);
+    key.radius = radius;
     std::lock_guard<std::mutex> g(g_buildGraphLock);
     auto it = g_buildGraphs.find(o);
     if (it != g_buildGraphs.end() && !(it->second.key == key)) {
@@ -660,8 +731,9 @@ static grtError replayOrCaptureBuild(Context* c, BvhObject* o, const grtGeometry
         const unsigned long long before = launchCountNow();
         cudaGraph_t graph = nullptr;
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        grtError e = ce == cudaSuccess ? issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, cs)
-                                       : GRT_ERROR_CUDA;
+        grtError e = ce == cudaSuccess
+                         ? issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, cs, radius)
+                         : GRT_ERROR_CUDA;
         if (ce == cudaSuccess) ce = cudaStreamEndCapture(cs, &graph);
         cudaGraphExec_t exec = nullptr;
         if (e == GRT_SUCCESS && ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -670,7 +742,7 @@ static grtError replayOrCaptureBuild(Context* c, BvhObject* o, const grtGeometry
         if (e != GRT_SUCCESS || ce != cudaSuccess) {  // no graph: the launches go straight to s
             cudaGetLastError();
             if (exec) cudaGraphExecDestroy(exec);
-            e = issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, s);
+            e = issueGeometryBuild(c, o, GRT_BUILD_OPERATION_BUILD, input, L, t, S, s, radius);
             if (e == GRT_SUCCESS) o->built = true;
             return e;
         }
@@ -699,7 +771,9 @@ grtError grtGetGeometryBuildTemporaryBufferSize(grtContext ctx, const grtGeometr
     if (!ctx || !sizeBytes) return GRT_ERROR_INVALID_PARAMETER;
     grtError e = validateGeometryInput(input, &n);
     if (e != GRT_SUCCESS) return e;
-    *sizeBytes = buildLayout(n, resolveMortonBits(n, options), false).total;
+    if (!validBuildFlags(options)) return GRT_ERROR_INVALID_PARAMETER;
+    const BuildLayout L = buildLayout(n, resolveMortonBits(n, options), false);
+    *sizeBytes = clusterRadius(options) ? plocLayout(L, n).total : L.total;
     return GRT_SUCCESS;
 }
 
@@ -709,9 +783,14 @@ grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, c
     if (!ctx || !out) return GRT_ERROR_INVALID_PARAMETER;
     grtError e = validateGeometryInput(input, &n);
     if (e != GRT_SUCCESS) return e;
+    if (!validBuildFlags(options) || (clusterRadius(options) && n > kPlocIndex)) return GRT_ERROR_INVALID_PARAMETER;
     BvhObject* o = nullptr;
     e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(n, options), &o);
     if (e != GRT_SUCCESS) return e;
+    if (clusterRadius(options)) {
+        std::lock_guard<std::mutex> g(g_methodLock);
+        g_clusterRadius[o] = clusterRadius(options);
+    }
     *out = reinterpret_cast<grtGeometry>(o->dHeader);
     return GRT_SUCCESS;
 }
@@ -730,6 +809,8 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
     if (n > 0 && (!temp || ((uintptr_t)temp & 15))) return GRT_ERROR_INVALID_PARAMETER;
     if (options && options->mortonBits && resolveMortonBits(n, options) != o->mortonBits)
         return GRT_ERROR_INVALID_PARAMETER;
+    const uint32_t radius = radiusOf(o);
+    if (!validBuildFlags(options) || (options && clusterRadius(options) != radius)) return GRT_ERROR_INVALID_PARAMETER;
     Context* c = asContext(ctx);
     cudaStream_t s = (cudaStream_t)stream;
     o->geomType = input->geomType;
@@ -741,7 +822,7 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
     const BuildLayout L = buildLayout(n, o->mortonBits, false);
     char* t = (char*)temp;
     const PrimSource S = primSource(input, n);
-    if (op == GRT_BUILD_OPERATION_BUILD && n <= kSmallBuild) {  // initialises its own scratch
+    if (op == GRT_BUILD_OPERATION_BUILD && n <= kSmallBuild && radius == 0) {  // initialises its own scratch
         BlockBuild B = blockBuildOf(c, o, L, t, input->type == GRT_PRIMITIVE_TRIANGLE_MESH ? 0u : 1u);
         B.src = S;
         e = launchSmallBuild(B, s);
@@ -749,7 +830,7 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
         o->built = true;
         return GRT_SUCCESS;
     }
-    if (op == GRT_BUILD_OPERATION_BUILD) return replayOrCaptureBuild(c, o, input, L, t, S, s);
+    if (op == GRT_BUILD_OPERATION_BUILD) return replayOrCaptureBuild(c, o, input, L, t, S, s, radius);
     e = issueGeometryBuild(c, o, op, input, L, t, S, s);
     if (e != GRT_SUCCESS) return e;
     o->built = true;
@@ -760,6 +841,10 @@ grtError grtDestroyGeometry(grtContext ctx, grtGeometry geom) {
     BvhObject* o = findBvh(geom);
     if (!ctx || !o || o->primType == kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
     dropBuildGraph(o);
+    {
+        std::lock_guard<std::mutex> g(g_methodLock);
+        g_clusterRadius.erase(o);
+    }
     destroyBvhObject(o);
     return GRT_SUCCESS;
 }

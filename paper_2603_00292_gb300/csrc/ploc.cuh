@@ -1,0 +1,324 @@
+// Bottom-up clustering build: Parallel Locally-Ordered Clustering (PLOC; Meister and
+// Bittner, "Parallel Locally-Ordered Clustering for Bounding Volume Hierarchy
+// Construction", IEEE TVCG 2018), the clustering family behind the paper's "balanced"
+// build (Sec. 6.2 "BVH Construction" describes bottom-up clustering; Sec. 8 names
+// H-PLOC as that option).
+//
+// The clusters start as the leaves in Morton order. Each iteration:
+//   1. every cluster i finds its nearest neighbour among the clusters i-r..i+r: the one
+//      whose union with i has the smallest surface area (ties: see below);
+//   2. every mutual pair (i, j), i < j, merges into a new internal node left = i,
+//      right = j, which takes position i; position j is dropped;
+//   3. the survivors are compacted in order.
+// until one cluster is left. The surface area is the float32 sum dx*dy + dy*dz + dz*dx
+// of the union box, each operation rounded to nearest, with a +0 added so that a zero
+// area has one sign. Candidates are ordered by (area, pair hash, position): the pair
+// hash is MurmurHash3's 32-bit finaliser (fmix32) applied to fmix32(lo) + hi of the
+// pair's two positions lo < hi, so equal areas (a regular grid, stacked copies) are
+// split pseudo-randomly instead of all in favour of the leftmost candidate, which would
+// let a run of equal boxes merge one pair per iteration. The order is the same from
+// either end of a pair, so the smallest pair overall is always mutual and every
+// iteration merges at least once.
+//
+// Node numbering: the m-th merge of the whole build (merges counted in iteration order,
+// then by position) creates internal node n-2-m, so the last merge is the root, node 0,
+// and every internal child has a larger index than its parent. Leaves keep their sorted
+// positions. The kernel writes what Karras emission writes (the child words of each
+// internal node, word 3 of the binary node, and the parent links); the bottom-up fit
+// then computes boxes, leaf records and 4-wide nodes exactly as for an LBVH.
+//
+// Execution: one persistent launch of at most 2 blocks per SM. A block owns a contiguous
+// range of whole 256-cluster tiles; phase A (nearest neighbours, with the r-wide halo
+// recomputed on both sides so the mutual test needs no other block) and phase B (offsets
+// from the per-block counts, scatter of survivors and merges) are separated by grid
+// barriers. Blocks whose range has become empty leave for good. Every barrier wait is
+// bounded in time; one that runs out latches GRT_ERROR_TIMEOUT and every block leaves.
+// Indices read from memory are range-checked before use, so a launch that is cut short
+// leaves a wrong tree (and an error) but touches nothing outside its buffers.
+#pragma once
+
+#include "lbvh.cuh"
+
+namespace grt {
+
+constexpr int kPlocThreads = 256;           // threads per block = clusters per tile
+constexpr uint32_t kPlocMaxRadius = 64;
+constexpr uint32_t kPlocWaitSpins = 1u << 25;
+constexpr uint32_t kPlocKeep = 1u << 30, kPlocMerge = 1u << 31, kPlocIndex = (1u << 30) - 1u;
+
+struct PlocParams {
+    PrimSource src;
+    uint32_t n;
+    uint32_t radius;
+    const uint32_t* sortedPrims;  // primitive at each sorted position
+    float4* clusters[2];          // ping-pong, 2 float4 per cluster: {lo.xyz, id}, {hi.xyz, 0}
+    uint32_t* pick;               // per position: neighbour | kPlocKeep | kPlocMerge
+    uint2* blockCounts;           // per block: (survivors, merges) of the current iteration
+    uint32_t* sync;               // [0] arrivals, [1] generation, [2] abort (zeroed before the launch)
+    float4* nodes;                // binary nodes: word 3 = child words
+    uint32_t* parents;            // parent << 1 | side; internal node k at [k], leaf k at [n-1+k]
+    uint32_t* error;
+    unsigned long long waitNs;    // time limit of one barrier wait
+};
+
+__device__ __forceinline__ unsigned long long plocTimerNs() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier among `participants` blocks (every thread of each calls it). Returns false
+// once the launch has been aborted (a wait ran out here or elsewhere).
+__device__ bool plocBarrier(const PlocParams& P, uint32_t participants, uint32_t& gen) {
+    __shared__ uint32_t ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t* vsync = P.sync;
+        uint32_t good = 1u;
+        const uint32_t target = gen + 1u;
+        __threadfence();
+        const uint32_t prev = atomicAdd(P.sync + 0, 1u);
+        if (prev == participants - 1u) {
+            atomicExch(P.sync + 0, 0u);
+            __threadfence();
+            atomicExch(P.sync + 1, target);
+        } else {
+            const unsigned long long t0 = plocTimerNs();
+            for (uint32_t k = 0; vsync[1] != target; ++k) {
+                if (vsync[2] != 0u) break;
+                if (k >= kPlocWaitSpins || ((k & 63u) == 0u && plocTimerNs() - t0 > P.waitNs)) {
+                    latchError(P.error, GRT_ERROR_TIMEOUT);
+                    atomicExch(P.sync + 2, 1u);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (vsync[2] != 0u) good = 0u;
+        ok = good;
+    }
+    __syncthreads();
+    gen += 1u;
+    return ok != 0u;
+}
+
+// Surface area (halved) of the union of two cluster boxes, float32 in a fixed order.
+__device__ __forceinline__ float plocUnionArea(float4 alo, float4 ahi, float4 blo, float4 bhi) {
+    const float dx = __fsub_rn(fmaxf(ahi.x, bhi.x), fminf(alo.x, blo.x));
+    const float dy = __fsub_rn(fmaxf(ahi.y, bhi.y), fminf(alo.y, blo.y));
+    const float dz = __fsub_rn(fmaxf(ahi.z, bhi.z), fminf(alo.z, blo.z));
+    const float a = __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx));
+    return __fadd_rn(a, 0.0f);
+}
+
+// Block-wide exclusive ranks of two flags and their block totals (kPlocThreads threads).
+__device__ __forceinline__ void plocRanks(bool a, bool b, uint32_t& ra, uint32_t& rb, uint32_t& ta, uint32_t& tb) {
+    __shared__ uint32_t wa[kPlocThreads / 32], wb[kPlocThreads / 32];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t ma = __ballot_sync(0xffffffffu, a), mb = __ballot_sync(0xffffffffu, b);
+    const uint32_t below = (1u << lane) - 1u;
+    if (lane == 0) wa[warp] = __popc(ma), wb[warp] = __popc(mb);
+    __syncthreads();
+    uint32_t pa = 0, pb = 0;
+    ta = tb = 0;
+    for (uint32_t w = 0; w < kPlocThreads / 32; ++w) {
+        if (w < warp) pa += wa[w], pb += wb[w];
+        ta += wa[w], tb += wb[w];
+    }
+    ra = pa + __popc(ma & below);
+    rb = pb + __popc(mb & below);
+    __syncthreads();
+}
+
+// Block-wide sums of (x, y) pairs over blockCounts[0..count), and over [0..upTo).
+__device__ __forceinline__ void plocCountSums(const uint2* counts, uint32_t count, uint32_t upTo, uint2& below,
+                                              uint2& total) {
+    __shared__ uint32_t part[4][kPlocThreads / 32];
+    uint32_t bx = 0, by = 0, tx = 0, ty = 0;
+    for (uint32_t t = threadIdx.x; t < count; t += kPlocThreads) {
+        const uint2 v = __ldcg(counts + t);
+        tx += v.x, ty += v.y;
+        if (t < upTo) bx += v.x, by += v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bx += __shfl_xor_sync(0xffffffffu, bx, o);
+        by += __shfl_xor_sync(0xffffffffu, by, o);
+        tx += __shfl_xor_sync(0xffffffffu, tx, o);
+        ty += __shfl_xor_sync(0xffffffffu, ty, o);
+    }
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (lane == 0) part[0][warp] = bx, part[1][warp] = by, part[2][warp] = tx, part[3][warp] = ty;
+    __syncthreads();
+    below = make_uint2(0, 0);
+    total = make_uint2(0, 0);
+    for (uint32_t w = 0; w < kPlocThreads / 32; ++w) {
+        below.x += part[0][w], below.y += part[1][w];
+        total.x += part[2][w], total.y += part[3][w];
+    }
+    __syncthreads();
+}
+
+// fmix32, the 32-bit finaliser of MurmurHash3 (Appleby).
+__device__ __forceinline__ uint32_t plocMix(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Tie-break of the pair of positions a < b.
+__device__ __forceinline__ uint32_t plocPairHash(uint32_t a, uint32_t b) { return plocMix(plocMix(a) + b); }
+
+// Parent-link slot of a child word: internal node k at k, leaf k at n-1+k.
+__device__ __forceinline__ uint32_t plocSlot(uint32_t id, uint32_t n) {
+    return (id & kLeafBit) ? n - 1u + (id & ~kLeafBit) : id;
+}
+
+// Dynamic shared memory: (kPlocThreads + 4r) cluster boxes (2 float4 each), then
+// (kPlocThreads + 2r) neighbour words.
+__host__ __device__ inline size_t plocSmemBytes(uint32_t radius) {
+    return (size_t)(kPlocThreads + 4 * radius) * 2 * sizeof(float4) + (size_t)(kPlocThreads + 2 * radius) * 4;
+}
+
+__global__ void __launch_bounds__(kPlocThreads) plocKernel(PlocParams P) {
+    extern __shared__ float4 plocSmem[];
+    const int r = (int)P.radius;
+    float4* box = plocSmem;                                                  // window of cluster boxes
+    uint32_t* nbr = reinterpret_cast<uint32_t*>(plocSmem + 2 * (kPlocThreads + 4 * r));  // neighbours
+    const uint32_t n = P.n;
+    const uint32_t G = gridDim.x;
+    uint32_t gen = 0;
+
+    // the leaves in sorted order
+    for (uint32_t k = blockIdx.x * kPlocThreads + threadIdx.x; k < n; k += G * kPlocThreads) {
+        const uint32_t prim = __ldcg(P.sortedPrims + k);
+        float3 v[3];
+        const Box3 b = primBox(P.src, prim < P.src.count ? prim : 0u, v);
+        P.clusters[0][2 * (size_t)k] = make_float4(b.lo.x, b.lo.y, b.lo.z, __uint_as_float(kLeafBit | k));
+        P.clusters[0][2 * (size_t)k + 1] = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
+    }
+    if (!plocBarrier(P, G, gen)) return;
+
+    uint32_t c = n, created = 0, src = 0;
+    for (uint32_t iter = 0; c > 1u; ++iter) {
+        const uint32_t tiles = (c + kPlocThreads - 1) / kPlocThreads;
+        const uint32_t A = min(G, tiles);
+        if (blockIdx.x >= A) return;  // no range from now on: the count only shrinks
+        const uint32_t per = (tiles + A - 1) / A;
+        const uint32_t begin = min(blockIdx.x * per * kPlocThreads, c);
+        const uint32_t end = min(begin + per * kPlocThreads, c);
+        const float4* cur = P.clusters[src];
+        float4* nxt = P.clusters[src ^ 1u];
+
+        // ---- phase A: nearest neighbours of [begin - r, end + r), mutual test on [begin, end)
+        uint32_t keepCount = 0, mergeCount = 0;
+        for (uint32_t s = begin; s < end; s += kPlocThreads) {
+            const int w0 = (int)s - 2 * r;
+            for (int t = threadIdx.x; t < kPlocThreads + 4 * r; t += kPlocThreads) {
+                const int g = w0 + t;
+                if (g >= 0 && g < (int)c) {
+                    box[2 * t] = __ldcg(cur + 2 * (size_t)g);
+                    box[2 * t + 1] = __ldcg(cur + 2 * (size_t)g + 1);
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < kPlocThreads + 2 * r; e += kPlocThreads) {
+                const int i = (int)s - r + e;
+                uint32_t best = kInvalid;
+                if (i >= 0 && i < (int)c) {
+                    const float4 alo = box[2 * (i - w0)], ahi = box[2 * (i - w0) + 1];
+                    unsigned long long key = ~0ull;
+                    for (int o = -r; o <= r; ++o) {
+                        const int j = i + o;
+                        if (o == 0 || j < 0 || j >= (int)c) continue;
+                        const float area = plocUnionArea(alo, ahi, box[2 * (j - w0)], box[2 * (j - w0) + 1]);
+                        const uint32_t h =
+                            o < 0 ? plocPairHash((uint32_t)j, (uint32_t)i) : plocPairHash((uint32_t)i, (uint32_t)j);
+                        const unsigned long long kj = ((unsigned long long)__float_as_uint(area) << 32) | h;
+                        if (kj < key) key = kj, best = (uint32_t)j;  // j ascends: equal keys keep the lower j
+                    }
+                }
+                nbr[e] = best;
+            }
+            __syncthreads();
+            const uint32_t i = s + threadIdx.x;
+            if (i < end) {
+                const uint32_t j = nbr[threadIdx.x + r];  // in [i - r, i + r]
+                const int ej = (int)j - ((int)s - r);
+                const bool mutual = ej >= 0 && ej < kPlocThreads + 2 * r && nbr[ej] == i;
+                const bool keep = !mutual || i < j, merge = mutual && i < j;
+                keepCount += keep, mergeCount += merge;
+                P.pick[i] = (j & kPlocIndex) | (keep ? kPlocKeep : 0u) | (merge ? kPlocMerge : 0u);
+            }
+            __syncthreads();
+        }
+        {
+            __shared__ uint32_t red[2][kPlocThreads / 32];
+            for (int o = 16; o > 0; o >>= 1) {
+                keepCount += __shfl_xor_sync(0xffffffffu, keepCount, o);
+                mergeCount += __shfl_xor_sync(0xffffffffu, mergeCount, o);
+            }
+            if ((threadIdx.x & 31u) == 0) red[0][threadIdx.x >> 5] = keepCount, red[1][threadIdx.x >> 5] = mergeCount;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint2 v = make_uint2(0, 0);
+                for (int w = 0; w < kPlocThreads / 32; ++w) v.x += red[0][w], v.y += red[1][w];
+                P.blockCounts[blockIdx.x] = v;
+            }
+        }
+        if (!plocBarrier(P, A, gen)) return;
+
+        // ---- phase B: offsets, then survivors and new nodes written in order
+        uint2 below, total;
+        plocCountSums(P.blockCounts, A, blockIdx.x, below, total);
+        uint32_t keepBase = below.x, mergeBase = below.y;
+        for (uint32_t s = begin; s < end; s += kPlocThreads) {
+            const uint32_t i = s + threadIdx.x;
+            const uint32_t pk = i < end ? P.pick[i] : 0u;
+            const bool keep = (pk & kPlocKeep) != 0u, merge = (pk & kPlocMerge) != 0u;
+            uint32_t rk, rm, tk, tm;
+            plocRanks(keep, merge, rk, rm, tk, tm);
+            if (keep) {
+                const uint32_t pos = keepBase + rk;
+                float4 lo = __ldcg(cur + 2 * (size_t)i), hi = __ldcg(cur + 2 * (size_t)i + 1);
+                if (merge) {
+                    const uint32_t j = pk & kPlocIndex;
+                    const uint32_t m = created + mergeBase + rm;
+                    if (j < c && m + 2u <= n) {
+                        const uint32_t q = n - 2u - m;
+                        const float4 jlo = __ldcg(cur + 2 * (size_t)j), jhi = __ldcg(cur + 2 * (size_t)j + 1);
+                        const uint32_t a = __float_as_uint(lo.w), b = __float_as_uint(jlo.w);
+                        const uint32_t sa = plocSlot(a, n), sb = plocSlot(b, n);
+                        P.nodes[4 * (size_t)q + 3] = make_float4(__uint_as_float(a), __uint_as_float(b), 0.f, 0.f);
+                        if (sa < 2u * n - 1u) P.parents[sa] = q << 1;
+                        if (sb < 2u * n - 1u) P.parents[sb] = (q << 1) | 1u;
+                        lo = make_float4(fminf(lo.x, jlo.x), fminf(lo.y, jlo.y), fminf(lo.z, jlo.z),
+                                         __uint_as_float(q));
+                        hi = make_float4(fmaxf(hi.x, jhi.x), fmaxf(hi.y, jhi.y), fmaxf(hi.z, jhi.z), 0.f);
+                    } else {
+                        latchError(P.error, GRT_ERROR_INTERNAL);
+                    }
+                }
+                if (pos < n) {
+                    nxt[2 * (size_t)pos] = lo;
+                    nxt[2 * (size_t)pos + 1] = hi;
+                }
+            }
+            keepBase += tk, mergeBase += tm;
+        }
+        if (total.y == 0u || total.x >= c) {  // no merge: cannot happen with consistent keys
+            if (threadIdx.x == 0) latchError(P.error, GRT_ERROR_INTERNAL);
+            return;
+        }
+        created += total.y;
+        c = total.x;
+        src ^= 1u;
+        if (!plocBarrier(P, A, gen)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.parents[0] = kInvalid;
+}
+
+}  // namespace grt

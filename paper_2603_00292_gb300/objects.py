@@ -48,10 +48,12 @@ class Context:
 
 
 class Geometry:
-    """A bottom-level BVH over an indexed triangle mesh or an AABB list."""
+    """A bottom-level BVH over an indexed triangle mesh or an AABB list. build_flags:
+    GRT_BUILD_PREFER_FAST (linear BVH), _BALANCED or _HIGH_QUALITY (PLOC clustering)."""
 
     def __init__(self, ctx: Context, *, vertices=None, indices=None, boxes=None, geom_type: int = 0,
-                 morton_bits: int = 0, temp: torch.Tensor | None = None, vertex_count: int | None = None):
+                 morton_bits: int = 0, temp: torch.Tensor | None = None, vertex_count: int | None = None,
+                 build_flags: int = 0):
         self.ctx = ctx
         if boxes is not None:
             self.boxes = boxes
@@ -59,7 +61,7 @@ class Geometry:
         else:
             self.vertices, self.indices = vertices, indices
             self.input = triangle_mesh_input(indices, vertices, vertex_count=vertex_count, geom_type=geom_type)
-        self.options = build_options(morton_bits)
+        self.options = build_options(morton_bits, build_flags)
         self.temp_bytes = grtGetGeometryBuildTemporaryBufferSize(ctx.handle, self.input, self.options)
         self.temp = temp if temp is not None and temp.numel() >= self.temp_bytes else empty_bytes(self.temp_bytes)
         self.handle = grtCreateGeometry(ctx.handle, self.input, self.options)

@@ -70,15 +70,19 @@ def check_wide(info, ref):
     assert np.array_equal(np.stack([w[:, 4:8], w[:, 12:16], w[:, 20:24]], axis=2), hi), "wide hi"
 
 
-def check_bit_exact(g, case, bits):
-    """The built geometry `g` of `case` equals the oracle's LBVH bit for bit: sorted
-    Morton codes and order (from the build temporary), topology, child boxes, parent
-    links and leaf records."""
+def check_bit_exact(g, case, bits, radius: int = 0):
+    """The built geometry `g` of `case` equals the oracle's build bit for bit (the LBVH,
+    or with radius > 0 the clustering build of that search radius): sorted Morton codes
+    and order (from the build temporary), topology, child boxes, parent links and leaf
+    records."""
     torch.cuda.synchronize()
     info = g.info()
     n = info.primCount
     lo, hi, cen = _oracle_for(case)
-    ref = oracle.lbvh(lo, hi, cen, 10 if bits == 30 else 21)
+    if radius:
+        ref = oracle.ploc(lo, hi, cen, 10 if bits == 30 else 21, radius)
+    else:
+        ref = oracle.lbvh(lo, hi, cen, 10 if bits == 30 else 21)
     assert info.mortonBits == bits
     koff, voff, boff = grt.grtGetBuildTemporaryLayout(n, bits)
     kdt = np.uint32 if bits == 30 else np.uint64
