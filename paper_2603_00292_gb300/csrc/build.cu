@@ -618,11 +618,16 @@ static grtError launchPloc(Context* c, BvhObject* o, const BuildLayout& L, char*
     P.parents = (uint32_t*)o->parents;
     P.error = &workspace(c)->error;
     P.waitNs = 2000000000ull;
+    // below this many clusters one block is faster than the grid: its neighbour search
+    // costs about 2r area tests per cluster and thread, a grid iteration about 10 us
+    P.finishAt = std::min<uint32_t>(kPlocFinishMax, 24576u / radius);
     const uint32_t blocks = std::min<uint32_t>(ceilDiv(n, kPlocThreads), 2u * (uint32_t)std::max(smCount(c), 1));
-    GRT_CUDA(cudaMemsetAsync(P.sync, 0, 16, s));
+    GRT_CUDA(cudaMemsetAsync(P.sync, 0, 32, s));
     plocKernel<<<blocks, kPlocThreads, plocSmemBytes(radius), s>>>(P);
     GRT_LAUNCH_CHECK();
-    noteLaunches(1);
+    plocFinishKernel<<<1, kPlocFinishThreads, plocFinishSmemBytes(), s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(2);
     return GRT_SUCCESS;
 }
 
@@ -788,6 +793,15 @@ grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, c
     e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(n, options), &o);
     if (e != GRT_SUCCESS) return e;
     if (clusterRadius(options)) {
+        // the finishing block's shared memory is above the default limit
+        cudaError_t ce = cudaFuncSetAttribute(plocFinishKernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)plocFinishSmemBytes());
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            destroyBvhObject(o);
+            logf(GRT_LOG_ERROR, "clustering build: %s", cudaGetErrorString(ce));
+            return GRT_ERROR_CUDA;
+        }
         std::lock_guard<std::mutex> g(g_methodLock);
         g_clusterRadius[o] = clusterRadius(options);
     }

@@ -27,12 +27,15 @@
 // internal node, word 3 of the binary node, and the parent links); the bottom-up fit
 // then computes boxes, leaf records and 4-wide nodes exactly as for an LBVH.
 //
-// Execution: one persistent launch of at most 2 blocks per SM. A block owns a contiguous
-// range of whole 256-cluster tiles; phase A (nearest neighbours, with the r-wide halo
-// recomputed on both sides so the mutual test needs no other block) and phase B (offsets
-// from the per-block counts, scatter of survivors and merges) are separated by grid
-// barriers. Blocks whose range has become empty leave for good. Every barrier wait is
-// bounded in time; one that runs out latches GRT_ERROR_TIMEOUT and every block leaves.
+// Execution: one persistent launch of at most 2 blocks per SM runs the iterations while
+// many clusters are left. A block owns a contiguous range of whole 256-cluster tiles;
+// phase A (nearest neighbours, with the r-wide halo recomputed on both sides so the
+// mutual test needs no other block) and phase B (offsets from the per-block counts,
+// scatter of survivors and merges) are separated by grid barriers. Blocks whose range has
+// become empty leave for good. Every barrier wait is bounded in time; one that runs out
+// latches GRT_ERROR_TIMEOUT and every block leaves. Once at most finishAt clusters are
+// left, a second launch of one block finishes in shared memory, where an iteration costs
+// a few block barriers instead of two grid barriers and a dozen round trips to L2.
 // Indices read from memory are range-checked before use, so a launch that is cut short
 // leaves a wrong tree (and an error) but touches nothing outside its buffers.
 #pragma once
@@ -54,11 +57,13 @@ struct PlocParams {
     float4* clusters[2];          // ping-pong, 2 float4 per cluster: {lo.xyz, id}, {hi.xyz, 0}
     uint32_t* pick;               // per position: neighbour | kPlocKeep | kPlocMerge
     uint2* blockCounts;           // per block: (survivors, merges) of the current iteration
-    uint32_t* sync;               // [0] arrivals, [1] generation, [2] abort (zeroed before the launch)
+    uint32_t* sync;               // [0] arrivals, [1] generation, [2] abort, [3..5] hand-over state
+                                  // (clusters left, merges so far, current array); zeroed before the launch
     float4* nodes;                // binary nodes: word 3 = child words
     uint32_t* parents;            // parent << 1 | side; internal node k at [k], leaf k at [n-1+k]
     uint32_t* error;
     unsigned long long waitNs;    // time limit of one barrier wait
+    uint32_t finishAt;            // the grid launch hands over to one block at this many clusters
 };
 
 __device__ __forceinline__ unsigned long long plocTimerNs() {
@@ -177,6 +182,39 @@ __device__ __forceinline__ uint32_t plocSlot(uint32_t id, uint32_t n) {
     return (id & kLeafBit) ? n - 1u + (id & ~kLeafBit) : id;
 }
 
+// Running choice of cluster i's nearest neighbour; candidates j must come in ascending
+// order. Order: smallest (area bits, pair hash), equal keys to the lower position; the
+// hash is only evaluated between candidates of equal area.
+struct PlocBest {
+    uint32_t bits, hash, j;
+    bool hashed;
+};
+__device__ __forceinline__ void plocConsider(PlocBest& b, uint32_t i, uint32_t j, uint32_t bits) {
+    if (b.j == kInvalid || bits < b.bits) {
+        b.bits = bits, b.j = j, b.hashed = false;
+    } else if (bits == b.bits) {
+        if (!b.hashed) {
+            b.hash = b.j < i ? plocPairHash(b.j, i) : plocPairHash(i, b.j);
+            b.hashed = true;
+        }
+        const uint32_t h = j < i ? plocPairHash(j, i) : plocPairHash(i, j);
+        if (h < b.hash) b.hash = h, b.j = j;
+    }
+}
+
+// Nearest neighbour of cluster i among the positions [lo, hi] (i excluded), boxes in
+// shared memory at box[2 * (position - base)] (two float4: lo.xyz, hi.xyz).
+__device__ __forceinline__ uint32_t plocNearest(const float4* box, int base, int i, int lo, int hi) {
+    const float4 alo = box[2 * (i - base)], ahi = box[2 * (i - base) + 1];
+    PlocBest b{0u, 0u, kInvalid, false};
+    for (int j = lo; j <= hi; ++j) {
+        if (j == i) continue;
+        const float area = plocUnionArea(alo, ahi, box[2 * (j - base)], box[2 * (j - base) + 1]);
+        plocConsider(b, (uint32_t)i, (uint32_t)j, __float_as_uint(area));
+    }
+    return b.j;
+}
+
 // Dynamic shared memory: (kPlocThreads + 4r) cluster boxes (2 float4 each), then
 // (kPlocThreads + 2r) neighbour words.
 __host__ __device__ inline size_t plocSmemBytes(uint32_t radius) {
@@ -204,6 +242,14 @@ __global__ void __launch_bounds__(kPlocThreads) plocKernel(PlocParams P) {
 
     uint32_t c = n, created = 0, src = 0;
     for (uint32_t iter = 0; c > 1u; ++iter) {
+        if (c <= P.finishAt) {  // the rest in one block's shared memory (plocFinishKernel)
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                P.sync[3] = c;
+                P.sync[4] = created;
+                P.sync[5] = src;
+            }
+            return;
+        }
         const uint32_t tiles = (c + kPlocThreads - 1) / kPlocThreads;
         const uint32_t A = min(G, tiles);
         if (blockIdx.x >= A) return;  // no range from now on: the count only shrinks
@@ -228,19 +274,7 @@ __global__ void __launch_bounds__(kPlocThreads) plocKernel(PlocParams P) {
             for (int e = threadIdx.x; e < kPlocThreads + 2 * r; e += kPlocThreads) {
                 const int i = (int)s - r + e;
                 uint32_t best = kInvalid;
-                if (i >= 0 && i < (int)c) {
-                    const float4 alo = box[2 * (i - w0)], ahi = box[2 * (i - w0) + 1];
-                    unsigned long long key = ~0ull;
-                    for (int o = -r; o <= r; ++o) {
-                        const int j = i + o;
-                        if (o == 0 || j < 0 || j >= (int)c) continue;
-                        const float area = plocUnionArea(alo, ahi, box[2 * (j - w0)], box[2 * (j - w0) + 1]);
-                        const uint32_t h =
-                            o < 0 ? plocPairHash((uint32_t)j, (uint32_t)i) : plocPairHash((uint32_t)i, (uint32_t)j);
-                        const unsigned long long kj = ((unsigned long long)__float_as_uint(area) << 32) | h;
-                        if (kj < key) key = kj, best = (uint32_t)j;  // j ascends: equal keys keep the lower j
-                    }
-                }
+                if (i >= 0 && i < (int)c) best = plocNearest(box, w0, i, max(i - r, 0), min(i + r, (int)c - 1));
                 nbr[e] = best;
             }
             __syncthreads();
@@ -318,7 +352,119 @@ __global__ void __launch_bounds__(kPlocThreads) plocKernel(PlocParams P) {
         src ^= 1u;
         if (!plocBarrier(P, A, gen)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.parents[0] = kInvalid;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // n <= 1 never gets here; finishAt >= 1
+        P.sync[3] = c;
+        P.sync[4] = created;
+        P.sync[5] = src;
+    }
+}
+
+// ======================================================================= the last iterations
+// One block of kPlocFinishThreads threads takes the clusters left by plocKernel (at most
+// finishAt <= kPlocFinishMax) into shared memory and runs the same iterations there.
+// Neighbour searches are spread one cluster per thread (the loop is latency-bound: each
+// thread runs a chain of 2r area tests, so more threads beat fewer, longer chains); for
+// the numbering, thread t owns a contiguous run of positions, so one block-wide scan of
+// its survivor and merge counts numbers the survivors and the new nodes in position order.
+constexpr int kPlocFinishThreads = 1024;
+constexpr uint32_t kPlocFinishMax = 3072;
+
+__host__ __device__ inline size_t plocFinishSmemBytes() {
+    return (size_t)kPlocFinishMax * (4 * sizeof(float4) + sizeof(uint32_t));
+}
+
+// Block-wide exclusive scan of one word per thread (kPlocFinishThreads threads); the
+// block total in *total.
+__device__ __forceinline__ uint32_t plocBlockScan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t warpSum[kPlocFinishThreads / 32];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    if (lane == 31) warpSum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (uint32_t w = 0; w < kPlocFinishThreads / 32; ++w) {
+        if (w < warp) before += warpSum[w];
+        all += warpSum[w];
+    }
+    __syncthreads();
+    *total = all;
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kPlocFinishThreads) plocFinishKernel(PlocParams P) {
+    extern __shared__ float4 finSmem[];
+    float4* A = finSmem;                       // clusters, 2 float4 each: {lo.xyz, id}, {hi.xyz, 0}
+    float4* B = finSmem + 2 * kPlocFinishMax;  // the next iteration's
+    uint32_t* nb = reinterpret_cast<uint32_t*>(finSmem + 4 * kPlocFinishMax);
+    const uint32_t n = P.n;
+    const int r = (int)P.radius;
+    uint32_t c = __ldcg(P.sync + 3), created = __ldcg(P.sync + 4);
+    const uint32_t src = __ldcg(P.sync + 5) & 1u;
+    if (n < 2 || __ldcg(P.sync + 2) != 0u) return;  // nothing to do, or the grid launch gave up
+    if (c == 0u || c > kPlocFinishMax || c > n || created + c != n) {
+        if (threadIdx.x == 0) latchError(P.error, GRT_ERROR_INTERNAL);
+        return;
+    }
+    for (uint32_t k = threadIdx.x; k < 2 * c; k += kPlocFinishThreads) A[k] = __ldcg(P.clusters[src] + k);
+    __syncthreads();
+    while (c > 1u) {
+        for (uint32_t i = threadIdx.x; i < c; i += kPlocFinishThreads)
+            nb[i] = plocNearest(A, 0, (int)i, max((int)i - r, 0), min((int)i + r, (int)c - 1));
+        __syncthreads();
+        const uint32_t per = (c + kPlocFinishThreads - 1) / kPlocFinishThreads;
+        const uint32_t b0 = min(threadIdx.x * per, c), b1 = min(b0 + per, c);
+        uint32_t keeps = 0, merges = 0;
+        for (uint32_t i = b0; i < b1; ++i) {
+            const uint32_t j = nb[i];
+            const bool mutual = j < c && nb[j] == i;
+            keeps += !mutual || i < j;
+            merges += mutual && i < j;
+        }
+        uint32_t total;
+        const uint32_t off = plocBlockScan(keeps | (merges << 16), &total);
+        uint32_t pos = off & 0xFFFFu, m = created + (off >> 16);
+        for (uint32_t i = b0; i < b1; ++i) {
+            const uint32_t j = nb[i];
+            const bool mutual = j < c && nb[j] == i;
+            if (mutual && j < i) continue;
+            float4 lo = A[2 * i], hi = A[2 * i + 1];
+            if (mutual) {
+                if (m + 2u <= n) {
+                    const uint32_t q = n - 2u - m;
+                    const float4 jlo = A[2 * j], jhi = A[2 * j + 1];
+                    const uint32_t a = __float_as_uint(lo.w), b = __float_as_uint(jlo.w);
+                    const uint32_t sa = plocSlot(a, n), sb = plocSlot(b, n);
+                    P.nodes[4 * (size_t)q + 3] = make_float4(__uint_as_float(a), __uint_as_float(b), 0.f, 0.f);
+                    if (sa < 2u * n - 1u) P.parents[sa] = q << 1;
+                    if (sb < 2u * n - 1u) P.parents[sb] = (q << 1) | 1u;
+                    lo = make_float4(fminf(lo.x, jlo.x), fminf(lo.y, jlo.y), fminf(lo.z, jlo.z),
+                                     __uint_as_float(q));
+                    hi = make_float4(fmaxf(hi.x, jhi.x), fmaxf(hi.y, jhi.y), fmaxf(hi.z, jhi.z), 0.f);
+                } else {
+                    latchError(P.error, GRT_ERROR_INTERNAL);
+                }
+                ++m;
+            }
+            if (pos < kPlocFinishMax) B[2 * pos] = lo, B[2 * pos + 1] = hi;
+            ++pos;
+        }
+        __syncthreads();
+        const uint32_t kept = total & 0xFFFFu, merged = total >> 16;
+        if (merged == 0u || kept >= c) {
+            if (threadIdx.x == 0) latchError(P.error, GRT_ERROR_INTERNAL);
+            return;
+        }
+        created += merged;
+        c = kept;
+        float4* t = A;
+        A = B;
+        B = t;
+    }
+    if (threadIdx.x == 0) P.parents[0] = kInvalid;
 }
 
 }  // namespace grt
