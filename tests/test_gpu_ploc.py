@@ -1,8 +1,8 @@
 """GPU clustering build (PLOC: GRT_BUILD_PREFER_BALANCED, search radius 8, and
 GRT_BUILD_PREFER_HIGH_QUALITY, radius 32) vs the oracle's sequential clustering:
 topology, node numbering, parent links, boxes, 4-wide nodes and leaves bit-exact; traces
-over the resulting trees vs the oracle's hits; refit; repeated (graph-replayed) builds;
-flag validation."""
+over the resulting trees (one level and instanced) vs the oracle's hits; refit; repeated
+(graph-replayed) builds; flag validation."""
 import numpy as np
 import pytest
 import torch
@@ -118,7 +118,8 @@ def test_trace_spheres_over_clustering_tree(gpu):
     from paper_2603_00292_gb300.objects import FuncTable
 
     s = scenegen.spheres(20_000, half=10.0, rmin=0.01, rmax=0.5, config=85)
-    g = Geometry(gpu, boxes=device_tensor(scenegen.sphere_aabbs(s)), build_flags=grt.GRT_BUILD_PREFER_BALANCED).build()
+    g = Geometry(gpu, boxes=device_tensor(scenegen.sphere_aabbs(s)),
+                 build_flags=grt.GRT_BUILD_PREFER_BALANCED).build()
     table = FuncTable(gpu)
     table.set(0, 0, grt.GRT_INTERSECT_SPHERE, device_tensor(s))
     S = oracle.Scene()
@@ -193,3 +194,41 @@ def test_flag_validation(gpu):
     bal = grt.grtGetGeometryBuildTemporaryBufferSize(gpu.handle, g.input, grt.build_options(0, 1))
     assert bal >= fast + 68 * m.indices.shape[0]
     g.close()
+
+
+def test_two_level_scene_over_clustering_trees(gpu):
+    """Instances of two clustered bottom levels (radius 8 and 32) under random SRT frames
+    (the top level stays a linear BVH): closest and any hit against the oracle."""
+    from paper_2603_00292_gb300.objects import Scene
+    from test_gpu_trace import _aimed
+
+    mesh = scenegen.terrain(cells=40, amplitude=0.2)
+    dev = dict(vertices=device_tensor(mesh.vertices), indices=device_tensor(mesh.indices))
+    g8 = Geometry(gpu, build_flags=grt.GRT_BUILD_PREFER_BALANCED, **dev).build()
+    g32 = Geometry(gpu, build_flags=grt.GRT_BUILD_PREFER_HIGH_QUALITY, **dev).build()
+    count = 10
+    fr = scenegen.random_frames(count, config=89)
+    handles = [g8.handle if k % 2 == 0 else g32.handle for k in range(count)]
+    sc = Scene(gpu, handles, device_tensor(fr.packed())).build()
+    S = oracle.Scene()
+    gi = S.add_mesh(mesh.vertices, mesh.indices)
+    for k in range(count):
+        S.add_instance(gi, fr.packed()[k])
+    S.build()
+    rays = _aimed(40_000, fr.translation.astype(np.float64), 93)
+    rays[::3, 7] = 6.0
+    ref = S.trace(rays)
+    n = rays.shape[0]
+    hits = new_hits(n)
+    grt.grtTraceClosest(gpu.handle, sc.handle, None, device_tensor(rays), n, hits)
+    torch.cuda.synchronize()
+    rep = compare_closest(hits_to_numpy(hits), ref, S, rays, extent=25.0)
+    rep.check()
+    assert rep.matched > 10_000
+    anyh = new_hits(n)
+    grt.grtTraceAnyHit(gpu.handle, sc.handle, None, device_tensor(rays), n, anyh)
+    torch.cuda.synchronize()
+    compare_any(hits_to_numpy(anyh)[1], ref, S, rays, extent=25.0).check()
+    _no_device_error(gpu)
+    for obj in (sc, g8, g32):
+        obj.close()

@@ -1,5 +1,6 @@
 """Differentiable Lambertian shading on the GPU vs the FP64 oracle: forward image,
-adjoint gradient, recompute mode, the autograd.Function, and the full 1920x1080 check
+adjoint gradient, recompute mode, the autograd.Function, a scene where visibility matters
+(a sphere shadowing the ground), and the full 1920x1080 check
 against FP64 central differences (h = 1e-4) on 1,000 parameters."""
 import numpy as np
 import pytest
@@ -212,3 +213,52 @@ def test_full_size_gradient_against_central_differences(gpu):
     ok = _rel_ok(grad, ref)
     assert ok[plain].all(), failures(ok | ~plain, ref)
     assert ok[~plain].all(), failures(ok | plain, ref)
+
+
+def test_shadowed_scene_forward_and_gradient(gpu):
+    """The icosphere above a ground quad, lit from above and in front, so the sphere casts a
+    shadow the camera sees: visibility decides thousands of lit pixels (V = 0, I = 0).
+    Forward image and visibility, and the adjoint gradients, against the FP64 oracle."""
+    W, H = 320, 180
+    ico = scenegen.icosphere(3)
+    ground = np.array([[-4, -1.2, -4], [4, -1.2, -4], [4, -1.2, 4], [-4, -1.2, 4]], np.float32)
+    verts = np.concatenate([ico.vertices, ground]).astype(np.float32)
+    nv = ico.vertices.shape[0]
+    idx = np.concatenate([ico.indices, np.array([[0, 2, 1], [0, 3, 2]], np.uint32) + nv]).astype(np.uint32)
+    rng = np.random.default_rng(11)
+    cols = rng.uniform(0.2, 1.0, verts.shape).astype(np.float32)
+    tcols = (cols + rng.uniform(-0.05, 0.05, cols.shape)).astype(np.float32)
+    light = np.array([0.2, 1.0, -0.6], np.float64)  # toward the light: the shadow falls toward the camera
+    light = (light / np.linalg.norm(light)).astype(np.float32)
+    cam = scenegen.look_down_z_camera([0, 0.4, 3.5], W, H)
+    rays = oracle.camera_rays(cam.packed(), W, H)
+    v64 = verts.astype(np.float64)
+    target = oracle.lambert_forward(v64, idx, tcols.astype(np.float64), light.astype(np.float64), rays).image
+    R = oracle.lambert_forward(v64, idx, cols.astype(np.float64), light.astype(np.float64), rays)
+    n = W * H
+    d = dict(pos=device_tensor(verts), idx=device_tensor(idx), col=device_tensor(cols), light=device_tensor(light),
+             rays=device_tensor(rays))
+    g = Geometry(gpu, vertices=d["pos"], indices=d["idx"]).build()
+    hits, img, vis = _gpu_forward(gpu, d, g, n)
+    gprim = hits_to_numpy(hits)[1].astype(np.int64)
+    oprim = np.where(R.prim < 0, 0xFFFFFFFF, R.prim.astype(np.int64))
+    lit = (gprim == oprim) & (R.prim >= 0) & (R.sign > 0)
+    gv = vis.cpu().numpy()
+    shadowed = lit & (R.vis == 0)
+    assert shadowed.sum() > 1500, shadowed.sum()  # the sphere's shadow on the ground (2,145 pixels)
+    agree = gv[lit] == R.vis[lit].astype(np.uint8)
+    assert (~agree).sum() <= max(3, 1e-3 * lit.sum())  # shadow-edge rays only
+    same = lit & (gv == R.vis.astype(np.uint8))
+    gi = img.cpu().numpy()
+    assert np.all(gi[shadowed & same] == 0)
+    assert np.abs(gi[same] - R.image[same]).max() < 2e-5
+    # adjoint against the oracle's analytic gradient of the same loss
+    loss, dc, dl, dp = oracle.lambert_gradient(v64, idx, cols.astype(np.float64), light.astype(np.float64), rays,
+                                               target)
+    gimg = device_tensor((2.0 * (R.image - target)).astype(np.float32))
+    gc, gl, gp = _gpu_backward(gpu, d, g, n, hits, vis, gimg)
+    assert _rel_ok(gc, dc).mean() > 0.995, np.abs(gc - dc).max()
+    assert np.allclose(gl, dl, rtol=2e-3, atol=1e-3 * np.abs(dl).max()), (gl, dl)
+    assert _rel_ok(gp, dp).mean() > 0.99, np.abs(gp - dp).max()
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+    g.close()

@@ -88,3 +88,35 @@ def test_colour_gradient_closed_form_one_triangle():
     G = (s * s) * (B.T @ B)                             # sum_p s^2 w w^T
     expect = 2 * G @ (cols - tcols)                    # I - I* = s W (c - c*)
     assert np.allclose(dc, expect, rtol=1e-10, atol=1e-12)
+
+
+def test_shadow_closed_form_occluder_above_ground():
+    """A ground quad in the plane y = 0 (facing +y) and a small square occluder in the
+    plane y = 1 over x, z in [-0.5, 0.5], light straight up (0, 1, 0), camera rays straight
+    down. Under the occluder the shadow ray meets it (V = 0, I = 0); elsewhere on the
+    ground I = (n . l) c = c exactly, with c the barycentric blend of the ground colours;
+    the occluder itself is lit from above but is seen from above, facing the ray: V = 1."""
+    g = [[-3, 0, -3], [3, 0, -3], [3, 0, 3], [-3, 0, 3]]
+    o = [[-0.5, 1, -0.5], [0.5, 1, -0.5], [0.5, 1, 0.5], [-0.5, 1, 0.5]]
+    v = np.array(g + o, np.float64)
+    idx = np.array([[0, 2, 1], [0, 3, 2], [4, 6, 5], [4, 7, 6]], np.uint32)
+    cols = np.tile(np.array([[0.25, 0.5, 0.75]]), (8, 1))  # uniform: c(u, v) is exact
+    light = np.array([0.0, 1.0, 0.0])
+    xs = np.array([-2.0, -0.8, -0.3, 0.0, 0.2, 0.45, 0.7, 1.9])
+    rays = np.zeros((xs.size * xs.size, 8), np.float32)
+    X, Z = np.meshgrid(xs, xs)
+    rays[:, 0], rays[:, 1], rays[:, 2] = X.ravel(), 5.0, Z.ravel()
+    rays[:, 5] = -1.0
+    rays[:, 7] = np.inf
+    R = oracle.lambert_forward(v, idx, cols, light, rays)
+    under = (np.abs(X.ravel()) < 0.5) & (np.abs(Z.ravel()) < 0.5)
+    assert np.all(R.prim[under] >= 2)  # the camera ray meets the occluder first
+    assert np.all(R.vis[under] == 1) and np.allclose(R.image[under], cols[0], rtol=0, atol=1e-15)
+    # move the occluder out of the camera's way (camera rays start below it) but keep it
+    # between the ground and the light
+    rays2 = rays.copy()
+    rays2[:, 1] = 0.5
+    R2 = oracle.lambert_forward(v, idx, cols, light, rays2)
+    assert np.all(R2.prim <= 1)  # only the ground is hit
+    assert np.all(R2.vis[under] == 0) and np.all(R2.image[under] == 0)
+    assert np.all(R2.vis[~under] == 1) and np.allclose(R2.image[~under], cols[0], rtol=0, atol=1e-15)
