@@ -618,9 +618,10 @@ static grtError launchPloc(Context* c, BvhObject* o, const BuildLayout& L, char*
     P.parents = (uint32_t*)o->parents;
     P.error = &workspace(c)->error;
     P.waitNs = 2000000000ull;
-    // below this many clusters one block is faster than the grid: its neighbour search
-    // costs about 2r area tests per cluster and thread, a grid iteration about 10 us
-    P.finishAt = std::min<uint32_t>(kPlocFinishMax, 24576u / radius);
+    // below this many clusters one block is faster than the grid: a grid iteration costs
+    // about 12 us (r = 8) to 24 us (r = 32) of round trips and barriers, the block's
+    // neighbour search about 2r area tests per cluster on one SM
+    P.finishAt = std::min<uint32_t>(kPlocFinishMax, 49152u / radius);
     const uint32_t blocks = std::min<uint32_t>(ceilDiv(n, kPlocThreads), 2u * (uint32_t)std::max(smCount(c), 1));
     GRT_CUDA(cudaMemsetAsync(P.sync, 0, 32, s));
     plocKernel<<<blocks, kPlocThreads, plocSmemBytes(radius), s>>>(P);
