@@ -67,3 +67,35 @@ def test_host_only_queries_without_a_device(lib):
     with pytest.raises(grt.GrtError) as e:
         grt.grtSortTemporaryBufferSize(10, 16)
     assert e.value.code == grt.GRT_ERROR_INVALID_PARAMETER
+
+
+def test_constants_match_the_header():
+    """Every enumerator and numeric #define of include/grt.h that the binding exports has
+    the header's value (the build flags, errors, primitive types, trace and batch flags)."""
+    txt = open(os.path.join(ROOT, "include", "grt.h")).read()
+    code = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    values = {}
+    for body in re.findall(r"typedef\s+enum\s+\w*\s*\{(.*?)\}", code, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            if "=" in item:
+                name, val = (x.strip() for x in item.split("=", 1))
+                nxt = int(val, 0)
+            else:
+                name = item
+            values[name] = nxt
+            nxt += 1
+    for name, val in re.findall(r"^#define\s+(GRT_\w+)\s+\(?([0-9xXa-fA-Fu<> ]+)\)?\s*$", code, flags=re.M):
+        try:
+            values[name] = int(eval(val.replace("u", "")))  # literals such as 1u or (1u << 3)
+        except Exception:
+            pass
+    exported = {k: v for k, v in values.items() if hasattr(grt, k)}
+    assert len(exported) >= 20, sorted(exported)
+    wrong = {k: (getattr(grt, k), v) for k, v in exported.items() if getattr(grt, k) != v}
+    assert not wrong, wrong
+    for k in ("GRT_BUILD_PREFER_FAST", "GRT_BUILD_PREFER_BALANCED", "GRT_BUILD_PREFER_HIGH_QUALITY"):
+        assert k in exported
