@@ -359,6 +359,8 @@ def run_grt(args, rank, world, local):
     # radius 8 and 32): build time, surface-area cost of the tree (sum of internal node
     # box areas over the root's), the closest + AO traces and the whole step over it
     from paper_2603_00292_gb300.objects import read_device
+    torch.cuda.synchronize()
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS  # the features above
     builds = {}
     for name, flags in (("fast_lbvh", grt.GRT_BUILD_PREFER_FAST), ("balanced_ploc8", grt.GRT_BUILD_PREFER_BALANCED),
                         ("high_quality_ploc32", grt.GRT_BUILD_PREFER_HIGH_QUALITY)):
@@ -391,6 +393,11 @@ def run_grt(args, rank, world, local):
         sq.close()
         gq.close()
     torch.cuda.synchronize()
+    # a clustering build that could not keep its blocks co-resident reports a timeout
+    # instead of a tree: record it here rather than fail the line
+    build_err = grt.grtGetLastDeviceError(ctx.handle, sh)
+    if build_err != grt.GRT_SUCCESS:
+        builds["device_error"] = int(build_err)
     mhit = int((mhits[:, 1].view(torch.int32) != -1).sum().item())
     all_found = int(acount.sum().item())
     features = {"instance_mask_half": {"closest_plus_ao_ms": round(ms_mask, 4), "primary_hits": mhit,
