@@ -36,6 +36,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -122,9 +123,37 @@ KERNEL_UNITS = {"aoTraceKernel": "trace.cu", "traceKernel<closest, scene>": "tra
                 "shadeBackwardKernel<false, true>": "trace.cu", "batchKernel": "batch.cu"}
 
 
+def code_only(src: str) -> str:
+    """C/C++ source without its comments and without blank space (runs of spaces and tabs
+    collapsed, lines trimmed, empty lines dropped); string and character literals kept."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    lines = (re.sub(r"[ \t]+", " ", line).strip() for line in "".join(out).split("\n"))
+    return "\n".join(line for line in lines if line)
+
+
 def source_hash(unit: str) -> str:
-    """Hash of a translation unit of the library as compiled: the .cu file, every header it
-    includes (transitively, by #include "..."), and the build script with its flags."""
+    """Hash of a translation unit of the library as compiled: the code (comments and blank
+    space removed) of the .cu file and of every header it includes (transitively, by
+    #include "..."), and the build script with its flags. A change to comments alone leaves
+    the hash, and the DRAM traffic recorded under it, as they were."""
     csrc = os.path.join(ROOT, "paper_2603_00292_gb300", "csrc")
     seen, todo = [], [os.path.join(csrc, unit)]
     while todo:
@@ -138,9 +167,11 @@ def source_hash(unit: str) -> str:
                 if line.startswith('#include "'):
                     todo.append(os.path.join(os.path.dirname(f), line.split('"')[1]))
     h = hashlib.sha256()
-    for f in sorted(seen) + [os.path.join(ROOT, "paper_2603_00292_gb300", "build.py")]:
-        with open(f, "rb") as fh:
-            h.update(os.path.relpath(f, ROOT).encode() + fh.read())
+    for f in sorted(seen):
+        with open(f) as fh:
+            h.update(os.path.relpath(f, ROOT).encode() + code_only(fh.read()).encode())
+    with open(os.path.join(ROOT, "paper_2603_00292_gb300", "build.py"), "rb") as fh:
+        h.update(b"paper_2603_00292_gb300/build.py" + fh.read())
     return h.hexdigest()[:16]
 
 

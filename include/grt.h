@@ -72,6 +72,8 @@ typedef enum grtLogLevel {
  * (else GRT_ERROR_INVALID_API_VERSION). Allocates the context's small device
  * workspace (error word, work counters). */
 grtError grtCreateContext(uint32_t apiVersion, const grtContextCreationInput* input, grtContext* out);
+/* Frees the context and its device workspace (Sec. 7.1). Objects created from it must be
+ * destroyed first and no work of it may be in flight. */
 grtError grtDestroyContext(grtContext ctx);
 /* Bit set of grtLogLevel values printed to stderr (Sec. 7.1's log level). */
 grtError grtSetLogLevel(uint32_t levels);
@@ -159,6 +161,9 @@ grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, c
  * GRT_ERROR_TIMEOUT for grtGetLastDeviceError and leaves an unusable tree. */
 grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInput* input,
                           const grtBuildOptions* options, void* temp, void* stream, grtGeometry geom);
+/* Frees the geometry's node, leaf and link arrays and any captured build graph. No scene
+ * that instances it may be traced afterwards; no work using it may be in flight.
+ * GRT_ERROR_INVALID_PARAMETER for a handle that is not a live geometry. */
 grtError grtDestroyGeometry(grtContext ctx, grtGeometry geom);
 
 /* ---------------------------------------------------------------- scene (Sec. 7.3) */
@@ -186,14 +191,19 @@ typedef struct grtSceneBuildInput {
     const grtFrameSRT* instanceFrames; /* device pointer, frameCount entries */
 } grtSceneBuildInput;
 
+/* Size in bytes of the caller-allocated temporary buffer for building the top level of
+ * `input` (Sec. 7.3); instanceCount must equal frameCount (else GRT_ERROR_INVALID_PARAMETER). */
 grtError grtGetSceneBuildTemporaryBufferSize(grtContext ctx, const grtSceneBuildInput* input,
                                              const grtBuildOptions* options, size_t* sizeBytes);
+/* Allocates the library-owned top level for `input`'s instance count: nodes, instance
+ * records and the FP64 frames. The build flag is ignored (top levels are linear BVHs). */
 grtError grtCreateScene(grtContext ctx, const grtSceneBuildInput* input, const grtBuildOptions* options,
                         grtScene* out);
 /* Builds the top level over the instances' world boxes. The instances' geometries
  * must have been built earlier on the same stream (or be complete). */
 grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* input, const grtBuildOptions* options,
                        void* temp, void* stream, grtScene scene);
+/* Frees the top level (not the geometries it instances); no work using it may be in flight. */
 grtError grtDestroyScene(grtContext ctx, grtScene scene);
 
 /* ---------------------------------------------------------------- custom intersection (Sec. 7.4) */
@@ -221,8 +231,13 @@ typedef struct grtFuncDataSet {
 /* A numRayTypes x numGeomTypes table, row-major (row = ray type), as the paper's
  * flattened function layout. */
 grtError grtCreateFuncTable(grtContext ctx, uint32_t numGeomTypes, uint32_t numRayTypes, grtFuncTable* out);
+/* Sets entry (rayType, geomType) (Sec. 7.4's hiprtSetFuncTable): the intersector and filter
+ * IDs and their device data pointers, which stay owned by the caller and must outlive every
+ * trace that uses the table. Synchronous copy to the device. GRT_ERROR_INVALID_PARAMETER for
+ * an index out of range, an unknown intersector or filter ID, or a filter without data. */
 grtError grtSetFuncTable(grtContext ctx, grtFuncTable table, uint32_t geomType, uint32_t rayType,
                          grtFuncDataSet set);
+/* Frees the table; no trace using it may be in flight. */
 grtError grtDestroyFuncTable(grtContext ctx, grtFuncTable table);
 
 /* ---------------------------------------------------------------- traversal (Sec. 6.2, 7.5, 7.6) */
@@ -520,6 +535,8 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
  * one batch must not overlap. */
 grtError grtBatchBuildTrace(grtContext ctx, grtBatch batch, void* stream);
 
+/* The batch's plan (host memory out): scene and item counts, the persistent grid and the
+ * library-owned device bytes. */
 grtError grtGetBatchInfo(grtContext ctx, grtBatch batch, grtBatchInfo* info);
 
 /* One work item of the last launch of a batch created with GRT_BATCH_FLAG_PROFILE:
@@ -540,6 +557,8 @@ typedef struct grtBatchItemRecord {
  * Synchronous: call after the launch has finished. */
 grtError grtGetBatchProfile(grtContext ctx, grtBatch batch, grtBatchItemRecord* records, uint32_t capacity,
                             uint32_t* count);
+/* Frees the batch's device memory and captured graph (not the geometries, rays or hit
+ * buffers, which the caller owns); no launch of it may be in flight. */
 grtError grtDestroyBatch(grtContext ctx, grtBatch batch);
 
 /* ---------------------------------------------------------------- introspection and building blocks */

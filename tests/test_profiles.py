@@ -41,3 +41,16 @@ def test_traffic_entries_name_a_translation_unit():
         assert kernel in bench.KERNEL_UNITS, kernel
         assert set(entry) >= {"source_hash", "dram_bytes_per_launch", "note"}
         assert entry["dram_bytes_per_launch"] > 0
+
+
+def test_code_hash_ignores_comments_only():
+    import bench
+
+    a = 'int f(int x) { return x + 1; }  // one\n/* block\n comment */\nconst char* s = "/* kept */ // kept";\n'
+    b = '/* other words */ int f(int x)   { return x + 1; }\n\n\nconst char* s = "/* kept */ // kept"; // two\n'
+    c = 'int f(int x) { return x + 2; }\nconst char* s = "/* kept */ // kept";\n'
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)  # code changed
+    assert "/* kept */" in bench.code_only(a)
+    assert bench.code_only("char q = '\\''; // x") == "char q = '\\'';"  # an escaped quote
+    assert bench.code_only("char b = '\\\\'; // x") == "char b = '\\\\';"  # an escaped backslash
