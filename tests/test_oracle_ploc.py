@@ -197,3 +197,16 @@ def test_unclear_inputs_still_terminate():
     cl, cr, pi, pl, it = oracle.ploc_topology(lo, hi, 8)
     _check_tree(cl, cr, pi, pl, 2000)
     assert it < 80
+
+
+def test_sah_cost_hand_worked_four_boxes():
+    # Four unit cubes at x = 0, 2, 10, 12 (y, z in [0, 1]). The clustering pairs (0, 2) and
+    # (10, 12): node boxes [0,3]x[0,1]^2 and [10,13]x[0,1]^2, root [0,13]x[0,1]^2. Surface
+    # areas 2(3 + 1 + 3) = 14 twice and 2(13 + 1 + 13) = 54: cost (54 + 14 + 14) / 54.
+    lo = np.array([[0, 0, 0], [2, 0, 0], [10, 0, 0], [12, 0, 0]], np.float32)
+    hi = lo + 1
+    cl, cr, pi, pl, _ = oracle.ploc_topology(lo, hi, 8)
+    nlo, nhi = oracle.fit(cl, cr, lo, hi)
+    assert np.array_equal(nlo[0], [0, 0, 0]) and np.array_equal(nhi[0], [13, 1, 1])
+    assert sorted(map(tuple, nhi[1:].tolist())) == [(3, 1, 1), (13, 1, 1)]
+    assert oracle.sah_cost(nlo, nhi) == (54 + 14 + 14) / 54
