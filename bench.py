@@ -596,12 +596,9 @@ ADJOINT = dict(workload="lambert-adjoint-1080p", mesh="icosphere level 3 (642 ve
 
 
 def adjoint_problem():
-    import oracle
     import scenegen
 
-    P = scenegen.shading_problem(ADJOINT["width"], ADJOINT["height"], ADJOINT["seed"])
-    rays = oracle.camera_rays(P.camera.packed(), ADJOINT["width"], ADJOINT["height"])
-    return P, rays
+    return scenegen.shading_problem(ADJOINT["width"], ADJOINT["height"], ADJOINT["seed"])
 
 
 def run_adjoint(args, rank, world, local):
@@ -612,7 +609,7 @@ def run_adjoint(args, rank, world, local):
 
     import paper_2603_00292_gb300 as grt
     from paper_2603_00292_gb300 import build as grt_build
-    from paper_2603_00292_gb300.objects import Context, Geometry, device_tensor, new_hits
+    from paper_2603_00292_gb300.objects import Context, Geometry, device_tensor, new_hits, new_rays
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -625,13 +622,15 @@ def run_adjoint(args, rank, world, local):
         grt_build.build()
     if dist:
         dist.barrier()
-    P, rays_np = adjoint_problem()
+    P = adjoint_problem()
     W, H = ADJOINT["width"], ADJOINT["height"]
     n = W * H
     ctx = Context(local)
     pos, idx = device_tensor(P.mesh.vertices), device_tensor(P.mesh.indices)
     col, light = device_tensor(P.colours), device_tensor(P.light)
-    rays = device_tensor(rays_np)
+    rays = new_rays(n)
+    c = P.camera.packed()
+    grt.grtGenerateCameraRays(ctx.handle, grt.camera(c[0:3], c[3:6], c[6:9]), W, H, rays)
     geom = Geometry(ctx, vertices=pos, indices=idx).build()
     target = torch.rand((n, 3), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     hits = new_hits(n)
@@ -739,7 +738,7 @@ def run_adjoint(args, rank, world, local):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches["store"]), "gpu_launches_by_mode": launches, "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_adjoint(P, rays_np, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_adjoint(P, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -747,11 +746,12 @@ def run_adjoint(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def cpu_adjoint(P, rays, target_s: float):
+def cpu_adjoint(P, target_s: float):
     """The FP64 oracle's forward + analytic gradient on every k-th pixel, scaled to the
-    whole image (the gradient is a sum over pixels)."""
+    whole image (the gradient is a sum over pixels); camera rays from the oracle."""
     import oracle
 
+    rays = oracle.camera_rays(P.camera.packed(), ADJOINT["width"], ADJOINT["height"])
     v = P.mesh.vertices.astype(np.float64)
     c, l = P.colours.astype(np.float64), P.light.astype(np.float64)
 

@@ -368,7 +368,10 @@ grtError grtPathTrace(grtContext ctx, grtScene scene, const grtRay* rays, uint32
  * make that first call before any stream capture begins. Every call shares the one
  * array (the work counter is cleared on `stream` at the start of each call): calls
  * that overlap on the GPU race, so serialise them on one stream or order them with
- * events. The device current at the call must be the context's. */
+ * events. The device current at the call must be the context's. The cached address
+ * belongs to the device's primary context as it is when first looked up: after
+ * cudaDeviceReset (or anything else that tears that context down) it no longer names
+ * the array, so do not call this entry point again in that process. */
 grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays,
                                 uint32_t rayCount, grtHit* hits, grtFuncTable table, const grtTraceOptions* options,
                                 void* stream);

@@ -26,8 +26,6 @@ class LambertRenderer:
         self.n = rays.shape[0]
         self.store = store
         self.opts = opts
-        self.hits = None
-        self.vis = None
 
 
 class LambertShade(torch.autograd.Function):
@@ -43,8 +41,10 @@ class LambertShade(torch.autograd.Function):
         vis = torch.empty(R.n, dtype=torch.uint8, device=colours.device) if R.store else None
         grtShadeLambert(R.ctx.handle, R.geometry.handle, R.rays, hits, R.n, R.indices, positions, colours, light,
                         image, vis, R.opts, stream)
-        R.hits, R.vis = (hits, vis) if R.store else (None, None)
+        # the hit records and visibility of THIS forward stay with its autograd node, so
+        # several forwards through one renderer each get their own backward
         fctx.R = R
+        fctx.hits, fctx.vis = (hits, vis) if R.store else (None, None)
         fctx.save_for_backward(colours, light, positions)
         return image
 
@@ -55,7 +55,7 @@ class LambertShade(torch.autograd.Function):
         gc = torch.zeros_like(colours)
         gl = torch.zeros_like(light)
         gp = torch.zeros_like(positions)
-        grtShadeLambertBackward(R.ctx.handle, R.geometry.handle, R.rays, R.hits, R.vis, R.n, R.indices, positions,
+        grtShadeLambertBackward(R.ctx.handle, R.geometry.handle, R.rays, fctx.hits, fctx.vis, R.n, R.indices, positions,
                                 colours, light, grad_image.contiguous(), gc, gl, gp, R.opts,
                                 torch.cuda.current_stream().cuda_stream)
         return gc, gl, gp, None

@@ -90,39 +90,48 @@ def check_bit_exact(g, case, bits, radius: int = 0):
     order = _tensor_bytes(g.temp, voff, n * 4, np.uint32)
     assert np.array_equal(keys.astype(np.uint64), ref["sorted_codes"]), "Morton codes / sort"
     assert np.array_equal(order, ref["order"]), "stable sort order"
+    check_tree(info, ref, case)
+
+
+def check_tree(info, ref, case):
+    """The geometry's binary nodes (both child boxes and child words), parent links,
+    4-wide nodes and leaf records equal those of the oracle build `ref` of `case`, bit
+    for bit. Triangle leaves hold the sorted triangles' vertices, the primitive ID and
+    the L1 norms |v1 - v0|_1 and |v2 - v0|_1 (summed x, y, z in float32)."""
+    n = info.primCount
+    lo, hi = ref["leaf_lo"], ref["leaf_hi"]
     nodes = _read(info.nodes, info.nodeCount * 64, np.float32).reshape(-1, 16)
     children = nodes.view(np.uint32)[:, 12:14]
     check_wide(info, ref)
     if n == 1:
         assert children.tolist() == [[LEAF, LEAF]]
         assert np.array_equal(nodes[0, [0, 4, 8]], lo[0]) and np.array_equal(nodes[0, [1, 5, 9]], hi[0])
-        return
-    cl = ref["childL"].view(np.uint32)
-    cr = ref["childR"].view(np.uint32)
-    assert np.array_equal(children[:, 0], cl) and np.array_equal(children[:, 1], cr), "topology"
+    else:
+        cl = ref["childL"].view(np.uint32)
+        cr = ref["childR"].view(np.uint32)
+        assert np.array_equal(children[:, 0], cl) and np.array_equal(children[:, 1], cr), "topology"
 
-    def child_box(c):
-        c = np.asarray(c, np.uint32)
-        leaf = (c & LEAF) != 0
-        idx = (c & 0x7FFFFFFF).astype(np.int64)
-        blo = np.where(leaf[:, None], ref["leaf_lo"][np.minimum(idx, n - 1)], ref["node_lo"][np.minimum(idx, n - 2)])
-        bhi = np.where(leaf[:, None], ref["leaf_hi"][np.minimum(idx, n - 1)], ref["node_hi"][np.minimum(idx, n - 2)])
-        return blo, bhi
+        def child_box(c):
+            c = np.asarray(c, np.uint32)
+            leaf = (c & LEAF) != 0
+            idx = (c & 0x7FFFFFFF).astype(np.int64)
+            blo = np.where(leaf[:, None], lo[np.minimum(idx, n - 1)], ref["node_lo"][np.minimum(idx, n - 2)])
+            bhi = np.where(leaf[:, None], hi[np.minimum(idx, n - 1)], ref["node_hi"][np.minimum(idx, n - 2)])
+            return blo, bhi
 
-    l0, h0 = child_box(cl)
-    l1, h1 = child_box(cr)
-    # node rows: x = (c0.lo, c0.hi, c1.lo, c1.hi) at 0..3, y at 4..7, z at 8..11
-    assert np.array_equal(nodes[:, [0, 4, 8]], l0) and np.array_equal(nodes[:, [1, 5, 9]], h0), "left boxes"
-    assert np.array_equal(nodes[:, [2, 6, 10]], l1) and np.array_equal(nodes[:, [3, 7, 11]], h1), "right boxes"
-    # parent links: (parent << 1 | side), root marked invalid
-    par = _read(info.parents, (2 * n - 1) * 4, np.uint32)
-    assert par[0] == 0xFFFFFFFF
-    k = np.arange(n - 1, dtype=np.uint64)
-    for side, c in enumerate((cl, cr)):
-        c = c.astype(np.uint64)
-        slot = np.where(c & LEAF, n - 1 + (c & 0x7FFFFFFF), c).astype(np.int64)
-        assert np.array_equal(par[slot].astype(np.uint64), (k << 1) | side), "parent links"
-    # leaves
+        l0, h0 = child_box(cl)
+        l1, h1 = child_box(cr)
+        # node rows: x = (c0.lo, c0.hi, c1.lo, c1.hi) at 0..3, y at 4..7, z at 8..11
+        assert np.array_equal(nodes[:, [0, 4, 8]], l0) and np.array_equal(nodes[:, [1, 5, 9]], h0), "left boxes"
+        assert np.array_equal(nodes[:, [2, 6, 10]], l1) and np.array_equal(nodes[:, [3, 7, 11]], h1), "right boxes"
+        # parent links: (parent << 1 | side), root marked invalid
+        par = _read(info.parents, (2 * n - 1) * 4, np.uint32)
+        assert par[0] == 0xFFFFFFFF
+        k = np.arange(n - 1, dtype=np.uint64)
+        for side, c in enumerate((cl, cr)):
+            c = c.astype(np.uint64)
+            slot = np.where(c & LEAF, n - 1 + (c & 0x7FFFFFFF), c).astype(np.int64)
+            assert np.array_equal(par[slot].astype(np.uint64), (k << 1) | side), "parent links"
     if "indices" in case:
         rec = _read(info.leaves, n * 48, np.float32).reshape(n, 12)
         prim = rec[:, 3].view(np.uint32)
@@ -130,9 +139,50 @@ def check_bit_exact(g, case, bits, radius: int = 0):
         v = case["vertices"][case["indices"][ref["order"]]]  # (n,3,3)
         assert np.array_equal(rec[:, 0:3], v[:, 0]) and np.array_equal(rec[:, 4:7], v[:, 1])
         assert np.array_equal(rec[:, 8:11], v[:, 2])
+        for j, col in ((1, 7), (2, 11)):
+            d = np.abs(v[:, j] - v[:, 0])
+            assert np.array_equal(rec[:, col], (d[:, 0] + d[:, 1]) + d[:, 2]), "leaf edge norms"
     else:
         ids = _read(info.leaves, n * 4, np.uint32)
         assert np.array_equal(ids, ref["order"])
+
+
+def refit_reference(ref, case):
+    """The oracle build `ref` with its topology and order kept and every box fitted again
+    over the primitives of `case` (the moved vertices or boxes)."""
+    lo, hi, _ = _oracle_for(case)
+    slo = np.ascontiguousarray(lo[ref["order"]])
+    shi = np.ascontiguousarray(hi[ref["order"]])
+    nlo, nhi = oracle.fit(ref["childL"], ref["childR"], slo, shi)
+    return dict(ref, leaf_lo=slo, leaf_hi=shi, node_lo=nlo, node_hi=nhi)
+
+
+def check_refit_traces(gpu, g, case, seed):
+    """Closest hits traced through the refitted geometry equal the oracle's hits on the
+    moved primitives (rays from above the terrain's box, aimed down at it)."""
+    from paper_2603_00292_gb300.objects import hits_to_numpy, new_hits
+    from parity import compare_closest
+
+    v = case["vertices"]
+    lo, hi = v.min(axis=0).astype(np.float64), v.max(axis=0).astype(np.float64)
+    rng = np.random.default_rng(seed)
+    n = 20_000
+    org = np.stack([rng.uniform(lo[0], hi[0], n), np.full(n, hi[1] + 1.0), rng.uniform(lo[2], hi[2], n)], axis=1)
+    tgt = np.stack([rng.uniform(lo[0], hi[0], n), rng.uniform(lo[1], hi[1], n), rng.uniform(lo[2], hi[2], n)], axis=1)
+    d = tgt - org
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.zeros((n, 8), np.float32)
+    rays[:, 0:3], rays[:, 4:7], rays[:, 7] = org, d, np.inf
+    S = oracle.Scene()
+    S.add_instance(S.add_mesh(v, case["indices"]))
+    S.build()
+    ref = S.trace(rays)
+    hits = new_hits(n)
+    grt.grtTraceClosest(gpu.handle, None, g.handle, device_tensor(rays), n, hits)
+    torch.cuda.synchronize()
+    rep = compare_closest(hits_to_numpy(hits), ref, S, rays, extent=float(np.max(hi - lo)))
+    rep.check()
+    assert rep.matched > n // 2, rep.summary()
 
 
 @pytest.mark.parametrize("name", ["icosphere", "terrain", "flat", "spheres", "dupes", "n1", "n2", "n3", "n17",
@@ -158,8 +208,15 @@ def test_rebuild_is_deterministic(gpu):
     assert np.array_equal(a, c)
 
 
-def test_refit_after_moving_vertices(gpu):
-    m = scenegen.terrain(cells=32, amplitude=0.2)
+@pytest.mark.parametrize("cells", [32, 80])
+def test_refit_after_moving_vertices(gpu, cells):
+    """UPDATE keeps the topology and fits every box again from the moved vertices: both
+    child boxes of every binary node, the parent links, the triangle leaves (moved
+    vertices and edge norms) and the 4-wide nodes equal the oracle's fit of the kept
+    tree, bit for bit; closest hits traced afterwards equal the oracle's on the moved
+    mesh. 32 cells (2,048 triangles) stay under the one-block build size, 80 cells
+    (12,800) take the grid launches."""
+    m = scenegen.terrain(cells=cells, amplitude=0.2)
     v = device_tensor(m.vertices)
     g = Geometry(gpu, vertices=v, indices=device_tensor(m.indices), morton_bits=30).build()
     moved = m.vertices.copy()
@@ -168,22 +225,32 @@ def test_refit_after_moving_vertices(gpu):
     v.copy_(torch.from_numpy(moved))
     g.build(op=grt.GRT_BUILD_OPERATION_UPDATE)
     torch.cuda.synchronize()
-    info = g.info()
-    n = info.primCount
-    # topology kept, boxes refit from children: compare with the oracle fit on the same order
     lo, hi, cen = oracle.triangle_aabbs(m.vertices, m.indices)
+    ref = oracle.lbvh(lo, hi, cen, 10)  # the topology of the first build
+    case = dict(vertices=moved, indices=m.indices)
+    check_tree(g.info(), refit_reference(ref, case), case)
+    check_refit_traces(gpu, g, case, seed=cells)
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+    g.close()
+
+
+def test_refit_of_aabb_list(gpu):
+    """UPDATE of an AABB-list geometry after its boxes moved: node boxes and 4-wide nodes
+    against the oracle's fit of the kept tree."""
+    case = _case("n4097")
+    b = device_tensor(case["boxes"])
+    g = Geometry(gpu, boxes=b, morton_bits=30).build()
+    rng = np.random.default_rng(5)
+    moved = case["boxes"] + np.repeat(rng.uniform(-0.3, 0.3, (case["boxes"].shape[0], 3)), 2, axis=0).reshape(-1, 6)
+    moved = moved.astype(np.float32)
+    b.copy_(torch.from_numpy(moved))
+    g.build(op=grt.GRT_BUILD_OPERATION_UPDATE)
+    torch.cuda.synchronize()
+    lo, hi, cen = _oracle_for(case)
     ref = oracle.lbvh(lo, hi, cen, 10)
-    lo2, hi2, _ = oracle.triangle_aabbs(moved, m.indices)
-    nlo, nhi = oracle.fit(ref["childL"], ref["childR"], lo2[ref["order"]], hi2[ref["order"]])
-    nodes = _read(info.nodes, info.nodeCount * 64, np.float32).reshape(-1, 16)
-    assert np.array_equal(nodes.view(np.uint32)[:, 12], ref["childL"].view(np.uint32))
-    root_lo = np.minimum(nodes[0, [0, 4, 8]], nodes[0, [2, 6, 10]])
-    root_hi = np.maximum(nodes[0, [1, 5, 9]], nodes[0, [3, 7, 11]])
-    assert np.array_equal(root_lo, nlo[0]) and np.array_equal(root_hi, nhi[0])
-    internal = ref["childL"] >= 0
-    k = np.nonzero(internal)[0]
-    cidx = ref["childL"][k]
-    assert np.array_equal(nodes[k][:, [0, 4, 8]], nlo[cidx]) and np.array_equal(nodes[k][:, [1, 5, 9]], nhi[cidx])
+    moved_case = dict(boxes=moved)
+    check_tree(g.info(), refit_reference(ref, moved_case), moved_case)
+    g.close()
 
 
 @pytest.mark.parametrize("n", [0, 1, 5, 4096, 4097, 100_003, 1_000_003])

@@ -12,7 +12,7 @@ import paper_2603_00292_gb300 as grt
 import scenegen
 from paper_2603_00292_gb300.objects import Geometry, device_tensor, hits_to_numpy, new_hits
 from parity import check_any_hit_records, compare_any, compare_closest
-from test_gpu_build import _case, _oracle_for, _read, check_bit_exact
+from test_gpu_build import _case, _oracle_for, _read, check_bit_exact, check_refit_traces, check_tree, refit_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -136,6 +136,9 @@ def test_trace_spheres_over_clustering_tree(gpu):
 
 
 def test_refit_of_clustering_tree(gpu):
+    """UPDATE of a clustered tree keeps its topology: both child boxes of every node,
+    parent links, leaves and 4-wide nodes equal the oracle's fit of the kept clustering
+    over the moved vertices, and closest hits traced afterwards equal the oracle's."""
     m = scenegen.terrain(cells=48, amplitude=0.2)
     v = device_tensor(m.vertices)
     g = Geometry(gpu, vertices=v, indices=device_tensor(m.indices), morton_bits=30,
@@ -145,18 +148,13 @@ def test_refit_of_clustering_tree(gpu):
     v.copy_(torch.from_numpy(moved))
     g.build(op=grt.GRT_BUILD_OPERATION_UPDATE)
     torch.cuda.synchronize()
-    info = g.info()
     lo, hi, cen = oracle.triangle_aabbs(m.vertices, m.indices)
     ref = oracle.ploc(lo, hi, cen, 10, 8)  # topology of the first build
-    lo2, hi2, _ = oracle.triangle_aabbs(moved, m.indices)
-    nlo, nhi = oracle.fit(ref["childL"], ref["childR"], lo2[ref["order"]], hi2[ref["order"]])
-    nodes = _read(info.nodes, info.nodeCount * 64, np.float32).reshape(-1, 16)
-    assert np.array_equal(nodes.view(np.uint32)[:, 12], ref["childL"].view(np.uint32))
-    assert np.array_equal(nodes.view(np.uint32)[:, 13], ref["childR"].view(np.uint32))
-    k = np.nonzero(ref["childL"] >= 0)[0]
-    cidx = ref["childL"][k]
-    assert np.array_equal(nodes[k][:, [0, 4, 8]], nlo[cidx]) and np.array_equal(nodes[k][:, [1, 5, 9]], nhi[cidx])
+    case = dict(vertices=moved, indices=m.indices)
+    check_tree(g.info(), refit_reference(ref, case), case)
+    check_refit_traces(gpu, g, case, seed=48)
     _no_device_error(gpu)
+    g.close()
 
 
 def test_repeated_builds_replay_and_follow_new_vertices(gpu):

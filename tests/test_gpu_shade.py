@@ -69,20 +69,39 @@ def test_forward_matches_oracle(gpu):
     assert lit.sum() > 1000
 
 
+def _mismatched(hits, vis, R):
+    """Pixels where the GPU and the oracle disagree on the primary hit's triangle, or, on
+    a lit hit, on the shadow ray's visibility (edge-grazing and shadow-edge rays)."""
+    gprim = hits_to_numpy(hits)[1].astype(np.int64)
+    oprim = np.where(R.prim < 0, 0xFFFFFFFF, R.prim.astype(np.int64))
+    bad = gprim != oprim
+    lit = ~bad & (R.prim >= 0) & (R.sign > 0)
+    bad |= lit & (vis.cpu().numpy() != R.vis.astype(np.uint8))
+    return bad
+
+
 @pytest.mark.parametrize("recompute", [False, True])
 def test_backward_matches_oracle_gradient(gpu, recompute):
+    """Every colour, light and position gradient within 1e-3 relative of the oracle's
+    FP64 analytic gradient. Pixels whose primary hit (or visibility) differs between
+    the GPU and the oracle, at most 1e-4 of them, get dL/dI = 0 on the GPU side and are
+    left out of the oracle's loss."""
     W, H = 320, 180
     P, rays, verts64, target, d, g = _problem(gpu, W, H)
     n = W * H
     cols64, l64 = P.colours.astype(np.float64), P.light.astype(np.float64)
-    loss, dc, dl, dp = oracle.lambert_gradient(verts64, P.mesh.indices, cols64, l64, rays, target)
     R = oracle.lambert_forward(verts64, P.mesh.indices, cols64, l64, rays)
-    gimg = device_tensor((2.0 * (R.image - target)).astype(np.float32))
     hits, img, vis = _gpu_forward(gpu, d, g, n)
-    gc, gl, gp = _gpu_backward(gpu, d, g, n, None if recompute else hits, None if recompute else vis, gimg)
-    assert _rel_ok(gc, dc).mean() > 0.999, np.abs(gc - dc).max()
-    assert _rel_ok(gl, dl).all(), (gl, dl)
-    assert _rel_ok(gp, dp).mean() > 0.995, np.abs(gp - dp).max()
+    exclude = _mismatched(hits, vis, R)
+    assert exclude.sum() <= max(3, 1e-4 * n)
+    _, dc, dl, dp = oracle.lambert_gradient(verts64, P.mesh.indices, cols64, l64, rays[~exclude], target[~exclude])
+    gimg = 2.0 * (R.image - target)
+    gimg[exclude] = 0.0
+    gc, gl, gp = _gpu_backward(gpu, d, g, n, None if recompute else hits, None if recompute else vis,
+                               device_tensor(gimg.astype(np.float32)))
+    for got, ref in ((gc, dc), (gl, dl), (gp, dp)):
+        ok = _rel_ok(got, ref)
+        assert ok.all(), (np.nonzero(~ok), got[~ok][:5], ref[~ok][:5])
 
 
 @pytest.mark.parametrize("layout", ["global", "mixed"])
@@ -252,13 +271,56 @@ def test_shadowed_scene_forward_and_gradient(gpu):
     gi = img.cpu().numpy()
     assert np.all(gi[shadowed & same] == 0)
     assert np.abs(gi[same] - R.image[same]).max() < 2e-5
-    # adjoint against the oracle's analytic gradient of the same loss
-    loss, dc, dl, dp = oracle.lambert_gradient(v64, idx, cols.astype(np.float64), light.astype(np.float64), rays,
-                                               target)
-    gimg = device_tensor((2.0 * (R.image - target)).astype(np.float32))
-    gc, gl, gp = _gpu_backward(gpu, d, g, n, hits, vis, gimg)
-    assert _rel_ok(gc, dc).mean() > 0.995, np.abs(gc - dc).max()
-    assert np.allclose(gl, dl, rtol=2e-3, atol=1e-3 * np.abs(dl).max()), (gl, dl)
-    assert _rel_ok(gp, dp).mean() > 0.99, np.abs(gp - dp).max()
+    # adjoint against the oracle's analytic gradient of the same loss, over the pixels
+    # where the GPU and the oracle agree on the hit and the visibility: every gradient
+    # within 1e-3 relative
+    exclude = _mismatched(hits, vis, R)
+    assert exclude.sum() <= max(3, 1e-3 * lit.sum())
+    _, dc, dl, dp = oracle.lambert_gradient(v64, idx, cols.astype(np.float64), light.astype(np.float64),
+                                            rays[~exclude], target[~exclude])
+    gimg = 2.0 * (R.image - target)
+    gimg[exclude] = 0.0
+    gc, gl, gp = _gpu_backward(gpu, d, g, n, hits, vis, device_tensor(gimg.astype(np.float32)))
+    for got, ref in ((gc, dc), (gl, dl), (gp, dp)):
+        ok = _rel_ok(got, ref)
+        assert ok.all(), (np.nonzero(~ok), got[~ok][:5], ref[~ok][:5])
     assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+    g.close()
+
+
+def test_two_forwards_through_one_renderer(gpu):
+    """Two forwards through one LambertRenderer under two lights, then the first one's
+    backward: it uses its own visibility, not the second forward's. The scene is the
+    icosphere over a ground quad, so the two lights shadow different pixels."""
+    W, H = 160, 90
+    ico = scenegen.icosphere(3)
+    ground = np.array([[-4, -1.2, -4], [4, -1.2, -4], [4, -1.2, 4], [-4, -1.2, 4]], np.float32)
+    verts = np.concatenate([ico.vertices, ground]).astype(np.float32)
+    nv = ico.vertices.shape[0]
+    idx = np.concatenate([ico.indices, np.array([[0, 2, 1], [0, 3, 2]], np.uint32) + nv]).astype(np.uint32)
+    cols = np.random.default_rng(12).uniform(0.2, 1.0, verts.shape).astype(np.float32)
+    lights = [np.array(l, np.float64) / np.linalg.norm(l) for l in ([0.2, 1.0, -0.6], [-0.7, 1.0, 0.3])]
+    cam = scenegen.look_down_z_camera([0, 0.4, 3.5], W, H)
+    rays = device_tensor(oracle.camera_rays(cam.packed(), W, H))
+    pos, ind, col = device_tensor(verts), device_tensor(idx), device_tensor(cols)
+    g = Geometry(gpu, vertices=pos, indices=ind).build()
+    R = LambertRenderer(gpu, g, ind, rays, store=True)
+    tgt = torch.zeros((W * H, 3), dtype=torch.float32, device="cuda")
+    params, imgs = [], []
+    for l in lights:
+        p = (col.clone().requires_grad_(True), device_tensor(l.astype(np.float32)).requires_grad_(True),
+             pos.clone().requires_grad_(True))
+        params.append(p)
+        imgs.append(lambert_shade(*p, R))
+    ((imgs[0] - tgt) ** 2).sum().backward()
+    # the same gradient from direct calls with the first light
+    d = dict(pos=pos, idx=ind, col=col, light=device_tensor(lights[0].astype(np.float32)), rays=rays)
+    hits, img, vis = _gpu_forward(gpu, d, g, W * H)
+    hits2, img2, vis2 = _gpu_forward(gpu, dict(d, light=device_tensor(lights[1].astype(np.float32))), g, W * H)
+    assert (vis.cpu() != vis2.cpu()).sum() > 100  # the lights shadow different pixels
+    gc, gl, gp = _gpu_backward(gpu, d, g, W * H, hits, vis, 2.0 * (img - tgt))
+    c_, l_, p_ = (t.grad.cpu().numpy() for t in params[0])
+    assert np.allclose(c_, gc, rtol=1e-4, atol=1e-5)
+    assert np.allclose(l_, gl, rtol=1e-4, atol=1e-4)
+    assert np.allclose(p_, gp, rtol=1e-3, atol=1e-4)
     g.close()

@@ -249,6 +249,38 @@ def test_instance_frames_and_world_boxes(gpu):
         assert np.all(row[20:23] <= w.min(axis=0)) and np.all(row[24:27] >= w.max(axis=0))
 
 
+@pytest.mark.parametrize("count,cells", [(12, 32), (4500, 6)])
+def test_scene_update_after_frames_moved(gpu, count, cells):
+    """UPDATE of a scene after every instance frame changed in place: closest and any-hit
+    traces equal the oracle's over the new frames. 12 instances take the one-block top
+    level, 4,500 the grid launches."""
+    mesh = scenegen.terrain(cells=cells, amplitude=0.2)
+    g = Geometry(gpu, vertices=device_tensor(mesh.vertices), indices=device_tensor(mesh.indices)).build()
+    fr0 = scenegen.random_frames(count, config=89)
+    frames = device_tensor(fr0.packed())
+    sc = Scene(gpu, [g.handle] * count, frames).build()
+    fr1 = scenegen.random_frames(count, config=92)
+    frames.copy_(torch.from_numpy(fr1.packed()))
+    sc.build(op=grt.GRT_BUILD_OPERATION_UPDATE)
+    S = oracle.Scene()
+    gi = S.add_mesh(mesh.vertices, mesh.indices)
+    for k in range(count):
+        S.add_instance(gi, fr1.packed()[k])
+    S.build()
+    rays = _aimed(40_000, fr1.translation.astype(np.float64), 95)
+    rays[::3, 7] = 6.0
+    ref = S.trace(rays)
+    got = _trace(gpu, rays, scene=sc.handle)
+    rep = compare_closest(got, ref, S, rays, extent=25.0)
+    rep.check()
+    assert rep.matched > 10_000
+    anyg = _trace(gpu, rays, scene=sc.handle, any_hit=True)
+    compare_any(anyg[1], ref, S, rays, extent=25.0).check()
+    _no_device_error(gpu)
+    sc.close()
+    g.close()
+
+
 # ------------------------------------------------------------------ ambient occlusion
 def test_ambient_occlusion_rays_and_occlusion(gpu):
     sc, S, fr, table, keep = _instanced(gpu, cells=32, count=16)

@@ -462,3 +462,88 @@ def test_all_hits_through_a_closed_sphere_mesh():
     # the two crossings are at distance between the inradius and 1 from the centre
     assert np.all(np.abs(t[clean, :2] - 5.0) <= 1.0 + 1e-9)
     assert np.all(np.abs(t[clean, :2] - 5.0) >= 0.98)
+
+
+# ---------------------------------------------------------------- comparator helpers
+def _down_ray(x, y, z=1.0, tmax=np.inf):
+    r = np.zeros(8, np.float32)
+    r[0:3] = (x, y, z)
+    r[4:7] = (0, 0, -1)
+    r[7] = tmax
+    return r
+
+
+def test_min_edge_margin_closed_forms():
+    """The right triangle (0,0,0), (1,0,0), (0,1,0) hit straight down at (x, y): the
+    plane point's barycentrics are u = x, v = y, so the margin is |min(x, y, 1-x-y)|,
+    inside or outside the triangle; a plane crossing beyond maxT does not count; an
+    instance translation moves the triangle with it."""
+    tri = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    S = oracle.Scene()
+    g = S.add_mesh(tri, np.array([[0, 1, 2]], np.uint32))
+    S.add_instance(g)
+    assert S.min_edge_margin(_down_ray(0.25, 0.25)) == 0.25
+    assert S.min_edge_margin(_down_ray(0.125, 0.5)) == 0.125
+    assert S.min_edge_margin(_down_ray(0.5, 0.0)) == 0.0  # on the edge v = 0
+    assert S.min_edge_margin(_down_ray(0.5, 0.5)) == 0.0  # on the hypotenuse
+    assert S.min_edge_margin(_down_ray(0.0, 0.0)) == 0.0  # on a vertex
+    assert abs(S.min_edge_margin(_down_ray(0.75, 0.5)) - 0.25) < 1e-15  # outside: 1-u-v = -0.25
+    assert S.min_edge_margin(_down_ray(0.25, 0.25, tmax=0.5)) == np.inf  # plane at t = 1 > maxT
+    T = oracle.Scene()
+    T.add_instance(T.add_mesh(tri, np.array([[0, 1, 2]], np.uint32)), [0, 0, 0, 1, 1, 1, 1, 5, 0, 0])
+    assert T.min_edge_margin(_down_ray(5.25, 0.125)) == 0.125
+    assert T.min_edge_margin(_down_ray(5.5, 0.0)) == 0.0
+
+
+def test_min_sphere_margin_closed_forms():
+    """The unit sphere at the origin and a ray along +z at lateral offset b from (0, b, -5):
+    the closest approach is at t = 5, the line's distance to the centre is b, and the
+    margin is |1 - b^2| / (b^2 + 25 + 1). Tangent rays give 0; a sphere behind the origin
+    does not count; under a uniform scale 2 the tangent offset is 2."""
+    S = oracle.Scene()
+    S.add_instance(S.add_spheres(np.array([[0, 0, 0, 1]], np.float32)))
+
+    def ray(b, dz=1.0, scale=1.0):
+        r = np.zeros(8, np.float32)
+        r[0:3] = (0, b, -5 * scale)
+        r[4:7] = (0, 0, dz)
+        r[7] = np.inf
+        return r
+
+    assert S.min_sphere_margin(ray(1.0)) == 0.0
+    assert abs(S.min_sphere_margin(ray(0.0)) - 1 / 26) < 1e-15
+    assert abs(S.min_sphere_margin(ray(0.5)) - 0.75 / 26.25) < 1e-15
+    assert abs(S.min_sphere_margin(ray(2.0)) - 3 / 30) < 1e-15  # a miss still has a margin
+    assert S.min_sphere_margin(ray(0.0, dz=-1.0)) == np.inf  # the sphere lies behind
+    T = oracle.Scene()
+    T.add_instance(T.add_spheres(np.array([[0, 0, 0, 1]], np.float32)), [0, 0, 0, 1, 2, 2, 2, 0, 0, 0])
+    assert T.min_sphere_margin(ray(2.0, scale=2.0)) == 0.0
+    assert abs(T.min_sphere_margin(ray(0.0, scale=2.0)) - 1 / 26) < 1e-15
+
+
+def test_ao_frame_of_a_tilted_triangle():
+    """AO rays off the triangle v0 = (1,1,1), v1 = v0 + (3,0,4), v2 = v0 + (0,2,0), hit
+    from the side its normal (-0.8, 0, 0.6) faces: tangent = (v1 - v0)/5 = (0.6, 0, 0.8),
+    bitangent = n x tangent = (0, 1, 0), so a hemisphere sample (x, y, z) becomes the
+    direction (0.6x - 0.8y, z, 0.8x + 0.6y); the origin is the hit point + 1e-4 n."""
+    v0 = np.array([1, 1, 1], np.float64)
+    tri = np.array([v0, v0 + [3, 0, 4], v0 + [0, 2, 0]], np.float32)
+    S = oracle.Scene()
+    S.add_instance(S.add_mesh(tri, np.array([[0, 1, 2]], np.uint32)))
+    n = np.array([-0.8, 0.0, 0.6])
+    p = v0 + 0.25 * np.array([3, 0, 4]) + 0.25 * np.array([0, 2, 0])
+    prim = np.zeros((1, 8), np.float32)
+    prim[0, 0:3] = p + 2.0 * n
+    prim[0, 4:7] = -n
+    prim[0, 7] = np.inf
+    h = S.trace(prim, bvh=False)
+    assert h.prim[0] == 0 and abs(h.t[0] - 2.0) < 1e-6
+    spp, seed = 6, 99
+    ao = oracle.ao_rays(S, prim, h, spp, seed, 0.5)
+    hit = prim[0, 0:3].astype(np.float64) + h.t[0] * prim[0, 4:7].astype(np.float64)
+    for s in range(spp):
+        x, y, z = oracle.sample_hemisphere(oracle.xi(seed, 0, s, 0), oracle.xi(seed, 0, s, 1))
+        want = np.array([0.6 * x - 0.8 * y, z, 0.8 * x + 0.6 * y])
+        assert np.allclose(ao[s, 4:7], want, atol=1e-6), (s, ao[s, 4:7], want)
+        assert np.allclose(ao[s, 0:3], hit + 1e-4 * n, atol=1e-6)
+        assert ao[s, 3] == 0 and ao[s, 7] == np.float32(0.5)

@@ -73,3 +73,56 @@ def test_no_alloc_closest_hit_matches_the_allocating_entry_point(gpu):
         grt.grtTraceClosestNoAlloc(gpu.handle, sc.handle, None, rays, n, got2, table.handle,
                                    grt.trace_options(block_size=256, global_depth=4096))
     assert err.value.code == grt.GRT_ERROR_INVALID_PARAMETER
+
+
+def test_no_alloc_on_a_fresh_context_allocates_nothing(gpu):
+    """On a context that has never run an allocating trace, the entry point leaves the
+    device's free memory unchanged (one earlier call caches the scratch array's address
+    and loads the kernels), while grtTraceClosest on the same context then grows the
+    context's global-stack area by cudaMalloc: the measurement sees that allocation. A
+    call with no rays succeeds and leaves the hit buffer as it was; a call with another
+    device current is rejected (on machines with more than one device)."""
+    from paper_2603_00292_gb300.objects import Context
+
+    ctx = Context(0)
+    mesh = scenegen.terrain(cells=64, amplitude=0.2)
+    g = Geometry(ctx, vertices=device_tensor(mesh.vertices), indices=device_tensor(mesh.indices)).build()
+    n = 400_000
+    rng = np.random.default_rng(73)
+    r = np.zeros((n, 8), np.float32)
+    r[:, 0:3] = np.stack([rng.uniform(-1, 1, n), np.full(n, 1.5), rng.uniform(-1, 1, n)], axis=1)
+    d = np.stack([rng.normal(0, 0.3, n), -np.ones(n), rng.normal(0, 0.3, n)], axis=1)
+    r[:, 4:7] = d / np.linalg.norm(d, axis=1, keepdims=True)
+    r[:, 7] = np.inf
+    rays = device_tensor(r)
+    got = [new_hits(n) for _ in range(3)]
+    ref = new_hits(n)
+    grt.grtTraceClosestNoAlloc(ctx.handle, None, g.handle, rays, n, got[0])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for h in got[1:]:
+        grt.grtTraceClosestNoAlloc(ctx.handle, None, g.handle, rays, n, h)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, f"the allocation-free entry point changed free device memory by {free0 - free1} bytes"
+    grt.grtTraceClosest(ctx.handle, None, g.handle, rays, n, ref)
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free2 < free1, "the allocating entry point's global stack should show up as less free memory"
+    for h in got:
+        assert torch.equal(h, ref)
+    assert (hits_to_numpy(ref)[1] != grt.GRT_INVALID_ID).sum() > n // 2
+    # no rays: success, hit buffer untouched
+    untouched = new_hits(4)
+    untouched.fill_(-5)
+    grt.grtTraceClosestNoAlloc(ctx.handle, None, g.handle, rays, 0, untouched)
+    torch.cuda.synchronize()
+    assert bool((untouched == -5).all())
+    if torch.cuda.device_count() > 1:
+        with torch.cuda.device(1):
+            with pytest.raises(grt.GrtError) as err:
+                grt.grtTraceClosestNoAlloc(ctx.handle, None, g.handle, rays, n, got[1])
+        assert err.value.code == grt.GRT_ERROR_INVALID_PARAMETER
+    assert grt.grtGetLastDeviceError(ctx.handle) == grt.GRT_SUCCESS
+    g.close()
+    ctx.close()
