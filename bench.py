@@ -65,8 +65,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--workload", default=WORKLOAD["workload"],
-                   choices=[WORKLOAD["workload"], "lambert-adjoint-1080p", "batched-soups-256"],
-                   help="the ambient-occlusion throughput workload (default), the differentiable-shading one, "
+                   choices=[WORKLOAD["workload"], "icosphere-512", "spheres-1m", "lambert-adjoint-1080p",
+                            "batched-soups-256"],
+                   help="the two-level ambient-occlusion throughput workload (default), the single-icosphere "
+                        "primary-ray one, the million-sphere custom-primitive one, the differentiable-shading one, "
                         "or the batched many-scenes one")
     p.add_argument("--no-autotune", action="store_true", help="batched workload: default launch options")
     p.add_argument("--scenes", type=int, default=256, help="batched workload: the first N soups (a smaller case)")
@@ -120,6 +122,9 @@ def measured_peaks():
 
 # The translation unit that holds each kernel whose DRAM traffic bench.py reports.
 KERNEL_UNITS = {"aoTraceKernel": "trace.cu", "traceKernel<closest, scene>": "trace.cu",
+                "traceKernel<closest, geometry> icosphere-512": "trace.cu",
+                "traceKernel<closest, geometry> spheres-1m": "trace.cu",
+                "traceKernel<any, geometry> spheres-1m": "trace.cu",
                 "shadeBackwardKernel<false, true>": "trace.cu", "batchKernel": "batch.cu"}
 
 
@@ -277,11 +282,17 @@ def run_grt(args, rank, world, local):
     gcam = grt.camera(c[0:3], c[3:6], c[6:9])
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
-    ev = {k: torch.cuda.Event(enable_timing=True) for k in ("c0", "c1", "a0", "a1", "s0", "s1")}
+    ev = {k: torch.cuda.Event(enable_timing=True) for k in ("b0", "b1", "b2", "c0", "c1", "a0", "a1", "s0", "s1")}
 
     def step(timed_kernels: bool):
+        if timed_kernels:
+            ev["b0"].record(stream)
         geom.build(sh)
+        if timed_kernels:
+            ev["b1"].record(stream)
         scene.build(sh)
+        if timed_kernels:
+            ev["b2"].record(stream)
         grt.grtGenerateCameraRays(ctx.handle, gcam, W, H, rays, sh)
         if timed_kernels:
             ev["c0"].record(stream)
@@ -301,7 +312,7 @@ def run_grt(args, rank, world, local):
     rays_per_step = npix + spp * nhit
 
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    step_ms, closest_ms, ao_ms = [], [], []
+    step_ms, closest_ms, ao_ms, blas_ms, tlas_ms = [], [], [], [], []
     clocks = ClockSampler(local)
     launches0 = grt.grtGetLaunchCount()
     if dist:
@@ -317,6 +328,8 @@ def run_grt(args, rank, world, local):
         step_ms.append(ev["s0"].elapsed_time(ev["s1"]))
         closest_ms.append(ev["c0"].elapsed_time(ev["c1"]))
         ao_ms.append(ev["a0"].elapsed_time(ev["a1"]))
+        blas_ms.append(ev["b0"].elapsed_time(ev["b1"]))
+        tlas_ms.append(ev["b1"].elapsed_time(ev["b2"]))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -513,7 +526,14 @@ def run_grt(args, rank, world, local):
             "config": dict(WORKLOAD, rays_per_step=rays_per_step, primary_hits=nhit, l2="flushed between steps",
                            parallelism=f"replicas{world}"),
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "kernel_ms": {"closest": round(statistics.mean(closest_ms), 4), "ao": round(statistics.mean(ao_ms), 4)},
+            "kernel_ms": {"closest": round(statistics.mean(closest_ms), 4), "ao": round(statistics.mean(ao_ms), 4),
+                          "blas_build": round(statistics.mean(blas_ms), 4),
+                          "tlas_build": round(statistics.mean(tlas_ms), 4)},
+            "build": {"blas_prims": int(mesh.indices.shape[0]), "tlas_instances": WORKLOAD["instances"],
+                      "ms": round(statistics.mean(blas_ms) + statistics.mean(tlas_ms), 4),
+                      "mprims_per_s": round((mesh.indices.shape[0] + WORKLOAD["instances"]) /
+                                            (statistics.mean(blas_ms) + statistics.mean(tlas_ms)) / 1e3, 1),
+                      "blas_mprims_per_s": round(mesh.indices.shape[0] / statistics.mean(blas_ms) / 1e3, 1)},
             "features": features}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle(sc, cam, length, seed, args.cpu_seconds)
@@ -569,7 +589,7 @@ def run_reference(args, rank, world, local):
     length = float(np.float32(0.05 * sc.extent))
     seed = WORKLOAD["seed"]
     S = oracle_scene(sc)
-    budget = 120.0 / max(1, args.steps + args.warmup)  # seconds per step
+    budget = 10.0 * args.cpu_seconds / max(1, args.steps + args.warmup)  # seconds per step (2 min by default)
     n, dt = oracle_sample(S, sc, cam, length, seed, stride=4001)
     stride = max(1, int(4001 * dt / budget))
     times, count = [], 0
@@ -587,6 +607,373 @@ def run_reference(args, rank, world, local):
             "config": dict(WORKLOAD, parallelism="host cores"), "cpu_baseline": cb,
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- single-geometry workloads
+ICOSPHERE = dict(workload="icosphere-512", mesh="icosphere level 3 (642 vertices, 1280 triangles, radius 1)",
+                 width=512, height=512, camera="(0,0,3) looking down -z, 60 degree fov", query="closest hit")
+SPHERES = dict(workload="spheres-1m", spheres=1_000_000, centres="U[-50,50]^3", radii="log-U[0.01,1]",
+               rays=4_194_304, ray_origins="U[-50,50]^3", ray_directions="uniform on the sphere",
+               queries="closest hit + any hit (tmax = inf)", seed=20260301)
+
+
+def _setup_gpu(local, world):
+    import torch
+
+    from paper_2603_00292_gb300 import build as grt_build
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if int(os.environ.get("RANK", "0")) == 0:
+        grt_build.build()
+    if dist:
+        dist.barrier()
+    return dist
+
+
+class StepTimer:
+    """CUDA events around named parts of a step on one stream: mark(name) at the start
+    of a part, mark(None) at the end of the step; durations in ms per part."""
+
+    def __init__(self, stream, names):
+        import torch
+
+        self.stream = stream
+        self.names = list(names)
+        self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(self.names) + 1)]
+        self.k = 0
+        self.samples = {n: [] for n in self.names}
+
+    def mark(self):
+        self.ev[self.k].record(self.stream)
+        self.k += 1
+
+    def collect(self):
+        self.ev[-1].synchronize()
+        for i, n in enumerate(self.names):
+            self.samples[n].append(self.ev[i].elapsed_time(self.ev[i + 1]))
+        self.k = 0
+        return sum(self.ev[i].elapsed_time(self.ev[i + 1]) for i in range(len(self.names)))
+
+    def mean(self, name):
+        return statistics.mean(self.samples[name])
+
+
+def roofline_entry(kernel, nbytes, ms, bound, stats=None):
+    """The roofline object of one kernel: algorithmic bytes per launch over its measured
+    duration against the measured HBM copy peak; traffic = ncu DRAM bytes per launch of
+    the kernel's current sources (else null)."""
+    peaks, how = measured_peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
+    traffic = ncu_traffic(kernel)
+    out = {"bound": bound, "kernel": kernel, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+           "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": how, "traffic": traffic,
+           "algorithmic_bytes_per_launch": int(nbytes), "launch_ms": round(ms, 4)}
+    if traffic:
+        out["dram_share_of_algorithmic"] = round(traffic / nbytes, 4)
+    if stats:
+        out["per_ray"] = {k: round(v / max(1, stats["rays"]), 3) for k, v in stats.items() if k != "rays"}
+    return out
+
+
+def run_icosphere(args, rank, world, local):
+    """The smallest instance of the plain method: one 1,280-triangle icosphere, 512x512
+    primary rays from (0,0,3), closest hit. Step = LBVH build + camera rays + closest hit
+    (+ FP64 refinement). The CPU baseline is the FP64 oracle's brute force on one core."""
+    dist = _setup_gpu(local, world)
+    import torch
+
+    import paper_2603_00292_gb300 as grt
+    import scenegen
+    from paper_2603_00292_gb300.objects import Context, Geometry, device_tensor, new_hits, new_rays
+
+    W, H = ICOSPHERE["width"], ICOSPHERE["height"]
+    n = W * H
+    mesh = scenegen.icosphere(3)
+    cam = scenegen.look_down_z_camera([0, 0, 3], W, H)
+    c = cam.packed()
+    gcam = grt.camera(c[0:3], c[3:6], c[6:9])
+    ctx = Context(local)
+    verts, idx = device_tensor(mesh.vertices), device_tensor(mesh.indices)
+    geom = Geometry(ctx, vertices=verts, indices=idx)
+    rays, hits = new_rays(n), new_hits(n)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    T = StepTimer(stream, ["build", "raygen", "closest"])
+
+    def step(timer):
+        timer and timer.mark()
+        geom.build(sh)
+        timer and timer.mark()
+        grt.grtGenerateCameraRays(ctx.handle, gcam, W, H, rays, sh)
+        timer and timer.mark()
+        grt.grtTraceClosest(ctx.handle, None, geom.handle, rays, n, hits, None, None, sh)
+        timer and timer.mark()
+
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(local)
+    l0 = grt.grtGetLaunchCount()
+    if dist:
+        dist.barrier()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        step(T)
+        step_ms.append(T.collect())
+    clk = clocks.stop()
+    launches = grt.grtGetLaunchCount() - l0
+    (total_s,) = max_over_ranks([sum(step_ms) / 1e3], dist)
+    value = job_throughput(n * args.steps, world, total_s) / 1e6
+    nhit = int((hits[:, 1].view(torch.int32) != -1).sum().item())
+    cnt = grt.trace_options(flags=grt.GRT_TRACE_FLAG_COUNT)
+    grt.grtGetTraceStatistics(ctx.handle, sh)
+    grt.grtTraceClosest(ctx.handle, None, geom.handle, rays, n, new_hits(n), None, cnt, sh)
+    st = grt.grtGetTraceStatistics(ctx.handle, sh)
+    nbytes = n * (RAY_BYTES + HIT_BYTES) + NODE_BYTES * st["nodesVisited"] + TRI_BYTES * st["trianglesTested"]
+    # the 143 KB BVH stays in L1/L2: DRAM carries only the rays and the hit records
+    roofline = roofline_entry("traceKernel<closest, geometry> icosphere-512", nbytes, T.mean("closest"), "l1", st)
+
+    # end to end: the mesh up from pinned host memory, the hit records back
+    vh = torch.from_numpy(mesh.vertices).pin_memory()
+    ih = torch.from_numpy(mesh.indices.view(np.int32)).pin_memory()
+    hh = torch.empty((n, 5), dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        ev[0].record(stream)
+        verts.copy_(vh, non_blocking=True)
+        idx.copy_(ih, non_blocking=True)
+        step(None)
+        hh.copy_(hits, non_blocking=True)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(ev[0].elapsed_time(ev[1]))
+    (e2e_s,) = max_over_ranks([sum(e2e_ms) / 1e3], dist)
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(ICOSPHERE, rays_per_step=n, primary_hits=nhit, l2="flushed between steps",
+                           parallelism=f"replicas{world}"),
+            "trace_mrays_per_s": round(n / T.mean("closest") / 1e3, 1),
+            "build": {"ms": round(T.mean("build"), 4), "prims": int(mesh.indices.shape[0]),
+                      "mprims_per_s": round(mesh.indices.shape[0] / T.mean("build") / 1e3, 2)},
+            "kernel_ms": {k: round(T.mean(k), 4) for k in T.names},
+            "roofline": roofline,
+            "e2e": {"value": round(job_throughput(n * args.steps, world, e2e_s) / 1e6, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": int(vh.numel() * 4 + ih.numel() * 4),
+                    "d2h_bytes_per_step": int(hh.numel() * 4)},
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_icosphere(mesh, c, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    geom.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_icosphere(mesh, cam_packed, target_s: float):
+    """The FP64 oracle's brute force (every ray against all 1,280 triangles) on one host
+    core, over every k-th pixel of the 512x512 image."""
+    import oracle
+
+    W, H = ICOSPHERE["width"], ICOSPHERE["height"]
+    rays = oracle.camera_rays(cam_packed, W, H)
+    S = oracle.Scene()
+    S.add_instance(S.add_mesh(mesh.vertices, mesh.indices))
+
+    def run(stride):
+        r = rays[::stride]
+        t0 = time.perf_counter()
+        S.trace(r, bvh=False, threads=1)
+        return r.shape[0], time.perf_counter() - t0
+
+    m, dt = run(512)
+    stride = max(1, int(512 * dt / max(target_s, 1e-3)))
+    m, dt = run(stride)
+    return {"value": round(m / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"every {stride}th pixel of the 512x512 image ({m} rays), FP64 brute force over all 1,280 "
+                      f"triangles on one host core ({dt:.1f} s)"}
+
+
+def run_spheres(args, rank, world, local):
+    """Custom primitives through the function table: 1 M spheres as an AABB-list
+    geometry, 4,194,304 uniform random rays generated on the GPU, each traced as a
+    closest-hit and an any-hit query. Step = LBVH build over the boxes + ray generation +
+    closest hit (+ FP64 refinement) + any hit."""
+    dist = _setup_gpu(local, world)
+    import torch
+
+    import paper_2603_00292_gb300 as grt
+    import scenegen
+    from paper_2603_00292_gb300.objects import Context, FuncTable, Geometry, device_tensor, new_hits, new_rays
+
+    n, seed = SPHERES["rays"], SPHERES["seed"]
+    sph = scenegen.spheres(SPHERES["spheres"], half=50.0, rmin=0.01, rmax=1.0, seed=seed, config=3)
+    boxes = scenegen.sphere_aabbs(sph)
+    ctx = Context(local)
+    dsph, dbox = device_tensor(sph), device_tensor(boxes)
+    geom = Geometry(ctx, boxes=dbox)
+    table = FuncTable(ctx)
+    table.set(0, 0, grt.GRT_INTERSECT_SPHERE, dsph)
+    rays, hc, ha = new_rays(n), new_hits(n), new_hits(n)
+    lo, hi = [-50.0] * 3, [50.0] * 3
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    T = StepTimer(stream, ["build", "raygen", "closest", "any"])
+
+    def step(timer):
+        timer and timer.mark()
+        geom.build(sh)
+        timer and timer.mark()
+        grt.grtGenerateUniformRays(ctx.handle, lo, hi, seed, n, rays, 0.0, float("inf"), sh)
+        timer and timer.mark()
+        grt.grtTraceClosest(ctx.handle, None, geom.handle, rays, n, hc, table.handle, None, sh)
+        timer and timer.mark()
+        grt.grtTraceAnyHit(ctx.handle, None, geom.handle, rays, n, ha, table.handle, None, sh)
+        timer and timer.mark()
+
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(local)
+    l0 = grt.grtGetLaunchCount()
+    if dist:
+        dist.barrier()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        step(T)
+        step_ms.append(T.collect())
+    clk = clocks.stop()
+    launches = grt.grtGetLaunchCount() - l0
+    (total_s,) = max_over_ranks([sum(step_ms) / 1e3], dist)
+    value = job_throughput(2 * n * args.steps, world, total_s) / 1e6
+    hits_c = int((hc[:, 1].view(torch.int32) != -1).sum().item())
+    occl = int((ha[:, 1].view(torch.int32) != -1).sum().item())
+
+    # any hit at tmax = 2.9 (about 70% occluded): a non-trivial occlusion query
+    short = new_rays(n)
+    grt.grtGenerateUniformRays(ctx.handle, lo, hi, seed, n, short, 0.0, 2.9, sh)
+    hs = new_hits(n)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    short_ms = []
+    for k in range(3 + 5):
+        flush.zero_()
+        e0.record(stream)
+        grt.grtTraceAnyHit(ctx.handle, None, geom.handle, short, n, hs, table.handle, None, sh)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 3:
+            short_ms.append(e0.elapsed_time(e1))
+    occl_short = int((hs[:, 1].view(torch.int32) != -1).sum().item())
+
+    # algorithmic bytes per launch from counting passes: per ray the ray and the hit
+    # record, per 4-wide node visit 112 B, per sphere test its leaf's primitive ID (4 B)
+    # and its centre and radius (16 B)
+    cnt = grt.trace_options(flags=grt.GRT_TRACE_FLAG_COUNT)
+    grt.grtGetTraceStatistics(ctx.handle, sh)
+    grt.grtTraceClosest(ctx.handle, None, geom.handle, rays, n, new_hits(n), table.handle, cnt, sh)
+    st_c = grt.grtGetTraceStatistics(ctx.handle, sh)
+    grt.grtTraceAnyHit(ctx.handle, None, geom.handle, rays, n, new_hits(n), table.handle, cnt, sh)
+    st_a = grt.grtGetTraceStatistics(ctx.handle, sh)
+
+    def nbytes(st):
+        return n * (RAY_BYTES + HIT_BYTES) + NODE_BYTES * st["nodesVisited"] + 20 * st["customTested"]
+
+    kern = {"closest": ("traceKernel<closest, geometry> spheres-1m", st_c),
+            "any": ("traceKernel<any, geometry> spheres-1m", st_a)}
+    dom = max(kern, key=lambda k: T.mean(k))
+    # 64 MB of nodes and 16 MB of spheres fit the 126 MB L2 next to the streamed rays
+    roofline = roofline_entry(kern[dom][0], nbytes(kern[dom][1]), T.mean(dom), "l2", kern[dom][1])
+    prims = SPHERES["spheres"]
+
+    # end to end: spheres and boxes up from pinned host memory, both hit buffers back
+    sh_h = torch.from_numpy(sph).pin_memory()
+    bh = torch.from_numpy(boxes).pin_memory()
+    hch = torch.empty((n, 5), dtype=torch.int32).pin_memory()
+    hah = torch.empty((n, 5), dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0.record(stream)
+        dsph.copy_(sh_h, non_blocking=True)
+        dbox.copy_(bh, non_blocking=True)
+        step(None)
+        hch.copy_(hc, non_blocking=True)
+        hah.copy_(ha, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    (e2e_s,) = max_over_ranks([sum(e2e_ms) / 1e3], dist)
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(SPHERES, rays_per_step=2 * n, closest_hits=hits_c, occluded=occl,
+                           l2="flushed between steps", parallelism=f"replicas{world}"),
+            "trace_mrays_per_s": {"closest": round(n / T.mean("closest") / 1e3, 1),
+                                  "any": round(n / T.mean("any") / 1e3, 1),
+                                  "any_tmax_2.9": round(n / statistics.mean(short_ms) / 1e3, 1)},
+            "occluded_tmax_2.9": occl_short,
+            "build": {"ms": round(T.mean("build"), 4), "prims": prims,
+                      "mprims_per_s": round(prims / T.mean("build") / 1e3, 1)},
+            "kernel_ms": {k: round(T.mean(k), 4) for k in T.names},
+            "roofline": roofline,
+            "e2e": {"value": round(job_throughput(2 * n * args.steps, world, e2e_s) / 1e6, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": int(sh_h.numel() * 4 + bh.numel() * 4),
+                    "d2h_bytes_per_step": int(hch.numel() * 4 + hah.numel() * 4)},
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_spheres(sph, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    table.close()
+    geom.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_spheres(sph, target_s: float):
+    """The FP64 oracle (its own BVH over the spheres, closest + any hit) on the host
+    cores over the first k rays of the workload's generator."""
+    import oracle
+
+    t0 = time.perf_counter()
+    S = oracle.Scene()
+    S.add_instance(S.add_spheres(sph))
+    S.build()
+    build_s = time.perf_counter() - t0
+
+    def run(m):
+        r = oracle.uniform_rays([-50.0] * 3, [50.0] * 3, SPHERES["seed"], m)
+        t0 = time.perf_counter()
+        S.trace(r)
+        S.trace(r, any_hit=True)
+        return 2 * m, time.perf_counter() - t0
+
+    m, dt = run(20_000)
+    m, dt = run(min(SPHERES["rays"], max(20_000, int(20_000 * target_s / max(dt, 1e-3)))))
+    return {"value": round(m / dt / 1e6, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the first {m // 2} rays of the workload, closest + any hit ({m} queries), FP64 oracle BVH "
+                      f"on {os.cpu_count()} host threads ({dt:.1f} s; its BVH build over the 1 M spheres took "
+                      f"{build_s:.1f} s, not counted)"}
 
 
 # ----------------------------------------------------------------------------- adjoint workload
@@ -1005,15 +1392,41 @@ def cpu_batched(host, target_s: float):
                       f"({prims} triangles, {rays} rays, {dt:.1f} s)"}
 
 
+def launch_command(args_list, gpus: int, port: int) -> list:
+    """The torchrun command that runs this script as `gpus` ranks on this node (one
+    process per GPU, rendezvous on 127.0.0.1)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *args_list]
+
+
+def spawn_ranks(args) -> int:
+    """bench.py --gpus N (N > 1) started without torchrun: run itself under torchrun as N
+    ranks and return its exit status (rank 0 prints the JSON line)."""
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    return subprocess.call(launch_command(sys.argv[1:], args.gpus, port))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        sys.exit(spawn_ranks(args))
+    if world != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} but {world} ranks were launched")
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     elif args.workload == ADJOINT["workload"]:
         run_adjoint(args, rank, world, local)
     elif args.workload == BATCHED["workload"]:
         run_batched(args, rank, world, local)
+    elif args.workload == ICOSPHERE["workload"]:
+        run_icosphere(args, rank, world, local)
+    elif args.workload == SPHERES["workload"]:
+        run_spheres(args, rank, world, local)
     else:
         run_grt(args, rank, world, local)
 

@@ -422,6 +422,18 @@ typedef struct grtCamera {
 grtError grtGenerateCameraRays(grtContext ctx, const grtCamera* camera, uint32_t width, uint32_t height,
                                grtRay* rays, void* stream);
 
+/* count rays with origins uniform in the box [lo, hi] and directions uniform on the
+ * unit sphere, t in [minT, maxT]: the incoherent rays of a custom-primitive workload
+ * (the paper traces its rays from a generator kernel, Sec. 3.2-3.3; this is the
+ * uniform counterpart of its camera). Ray i takes the splitmix64 numbers xi(s, d) of
+ * stream `seed` at counter (i << 32) | (s << 1) | d, top 24 bits as a float in [0,1):
+ * origin = lo + (hi - lo) * (xi(0,0), xi(0,1), xi(1,0)); z = 1 - 2 xi(1,1), azimuth =
+ * 2 pi xi(2,0), direction = (sqrt(1 - z^2) cos, sqrt(1 - z^2) sin, z). lo, hi: host
+ * arrays of 3 floats (hi >= lo, finite); rays: device, 16-byte aligned, count entries.
+ * Errors: GRT_ERROR_INVALID_PARAMETER for a null or misaligned pointer or a bad box. */
+grtError grtGenerateUniformRays(grtContext ctx, const float lo[3], const float hi[3], uint64_t seed, uint32_t count,
+                                float minT, float maxT, grtRay* rays, void* stream);
+
 /* Ambient-occlusion rays (Sec. 4): for pixel p with a primary hit, samplesPerPixel
  * cosine-weighted directions about the world face normal turned toward the viewer
  * (tangent = world v1 - v0), origin = hit point + 1e-4 * normal, t in [0, length].

@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
             L.oracle_xi.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
             L.oracle_xi.restype = ctypes.c_double
             L.oracle_camera_rays.argtypes = [P, i64, i64, P]
+            L.oracle_uniform_rays.argtypes = [P, P, ctypes.c_uint64, i64, ctypes.c_float, ctypes.c_float, P]
             L.oracle_sample_hemisphere.argtypes = [ctypes.c_double, ctypes.c_double, P]
             L.oracle_ao_rays.argtypes = [P, P, P, P, i64, ctypes.c_int, ctypes.c_uint64, ctypes.c_float, P]
             L.oracle_lambert_forward.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, P, P]
@@ -440,6 +441,15 @@ def camera_rays(camera_packed, width: int, height: int) -> np.ndarray:
     cam = _c(camera_packed, np.float32).reshape(9)
     out = np.empty((width * height, 8), np.float32)
     lib().oracle_camera_rays(_p(cam), width, height, _p(out))
+    return out
+
+
+def uniform_rays(lo, hi, seed: int, count: int, tmin: float = 0.0, tmax: float = float("inf")) -> np.ndarray:
+    """count rays, origins uniform in the box [lo, hi], directions uniform on the unit
+    sphere (FP64, rounded to float32), from the splitmix64 stream `seed`."""
+    out = np.empty((count, 8), np.float32)
+    lib().oracle_uniform_rays(_p(_c(lo, np.float32).reshape(3)), _p(_c(hi, np.float32).reshape(3)),
+                              ctypes.c_uint64(seed), count, ctypes.c_float(tmin), ctypes.c_float(tmax), _p(out))
     return out
 
 

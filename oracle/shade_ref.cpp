@@ -54,6 +54,25 @@ void oracle_camera_rays(const float* cam, int64_t W, int64_t H, float* rays) {
         }
 }
 
+// Uniform random rays: origin uniform in the box [lo, hi] (lo + (hi - lo) * xi per
+// axis), direction uniform on the unit sphere by Archimedes' hat-box theorem (the
+// height z = 1 - 2 xi is uniform in [-1, 1], the azimuth 2 pi xi uniform, the radius
+// of the circle at height z is sqrt(1 - z^2)). Numbers: ray i's splitmix64 values at
+// (sample, dim) = (0,0), (0,1), (1,0) for the origin, (1,1) for z, (2,0) for the azimuth.
+void oracle_uniform_rays(const float* lo, const float* hi, uint64_t seed, int64_t n, float tmin, float tmax,
+                         float* rays) {
+    for (int64_t i = 0; i < n; ++i) {
+        const uint64_t p = (uint64_t)i;
+        const V3 o = v3(lo[0] + ((double)hi[0] - lo[0]) * oracle_xi(seed, p, 0, 0),
+                        lo[1] + ((double)hi[1] - lo[1]) * oracle_xi(seed, p, 0, 1),
+                        lo[2] + ((double)hi[2] - lo[2]) * oracle_xi(seed, p, 1, 0));
+        const double z = 1.0 - 2.0 * oracle_xi(seed, p, 1, 1);
+        const double phi = 2.0 * PI * oracle_xi(seed, p, 2, 0);
+        const double r = std::sqrt(std::fmax(1.0 - z * z, 0.0));
+        store_ray(rays + 8 * i, o, (double)tmin, v3(r * std::cos(phi), r * std::sin(phi), z), (double)tmax);
+    }
+}
+
 // Cosine-weighted hemisphere sample (Y up) for one (xi0, xi1).
 void oracle_sample_hemisphere(double xi0, double xi1, double* out3) {
     const double phi = xi0 * 2.0 * PI;

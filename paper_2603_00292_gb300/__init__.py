@@ -182,6 +182,8 @@ _SIGS = {
     "grtPathTrace": [_P, _P, _P, _U32, ctypes.POINTER(grtPathTraceInput), _P, _P, ctypes.POINTER(grtTraceOptions),
                      _P],
     "grtGenerateCameraRays": [_P, ctypes.POINTER(grtCamera), _U32, _U32, _P, _P],
+    "grtGenerateUniformRays": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_uint64,
+                               _U32, ctypes.c_float, ctypes.c_float, _P, _P],
     "grtGenerateAORays": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P, _P],
     "grtTraceAmbientOcclusion": [_P, _P, _P, _P, _U32, _U32, ctypes.c_uint64, ctypes.c_float, _P,
                                  ctypes.POINTER(grtTraceOptions), _P],
@@ -414,6 +416,14 @@ def grtTraceClosestNoAlloc(ctx, scene, geom, rays, count, hits, table=None, opts
 
 def camera(origin, right, up) -> grtCamera:
     return grtCamera((ctypes.c_float * 3)(*origin), (ctypes.c_float * 3)(*right), (ctypes.c_float * 3)(*up))
+
+
+def grtGenerateUniformRays(ctx, lo, hi, seed: int, count: int, rays, min_t: float = 0.0,
+                           max_t: float = float("inf"), stream=None):
+    f3 = ctypes.c_float * 3
+    check(lib().grtGenerateUniformRays(ctx, f3(*[float(x) for x in lo]), f3(*[float(x) for x in hi]),
+                                       ctypes.c_uint64(seed), count, ctypes.c_float(min_t), ctypes.c_float(max_t),
+                                       _ptr(rays), _stream(stream)), "grtGenerateUniformRays")
 
 
 def grtGenerateCameraRays(ctx, cam: grtCamera, width: int, height: int, rays, stream=None):

@@ -5,6 +5,8 @@
 #include <mutex>
 #include <unordered_map>
 
+#include <cmath>
+
 #include "traverse.cuh"
 
 namespace grt {
@@ -447,6 +449,25 @@ __global__ void cameraRayKernel(grtCamera cam, uint32_t W, uint32_t H, float4* o
     out[2 * (size_t)i + 1] = make_float4(d.x, d.y, d.z, INFINITY);
 }
 
+// Uniform random rays: origin uniform in the box [lo, hi], direction uniform on the unit
+// sphere (Archimedes: z uniform in [-1, 1], azimuth uniform), from the splitmix64
+// numbers of stream `seed` at ray i's counters (samples 0..2, dims 0..1). The radius
+// sqrt(1 - z^2) is evaluated as 2 sqrt(xi (1 - xi)), the same real number: 1 - xi is
+// exact for a multiple of 2^-24, where 1 - z*z cancels near the poles.
+__global__ void uniformRayKernel(float3 lo, float3 ext, uint64_t seed, uint32_t n, float tmin, float tmax,
+                                 float4* out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float ox = sampleXi(seed, i, 0, 0), oy = sampleXi(seed, i, 0, 1), oz = sampleXi(seed, i, 1, 0);
+    const float xz = sampleXi(seed, i, 1, 1), xp = sampleXi(seed, i, 2, 0);
+    const float z = 1.0f - 2.0f * xz;
+    const float r = 2.0f * sqrtf(xz * (1.0f - xz));
+    float sn, cs;
+    sincospif(2.0f * xp, &sn, &cs);
+    out[2 * (size_t)i] = make_float4(fmaf(ext.x, ox, lo.x), fmaf(ext.y, oy, lo.y), fmaf(ext.z, oz, lo.z), tmin);
+    out[2 * (size_t)i + 1] = make_float4(r * cs, r * sn, z, tmax);
+}
+
 // ---------------------------------------------------------------- host side
 struct LaunchShape {
     int blockSize;
@@ -766,6 +787,21 @@ grtError grtGenerateCameraRays(grtContext ctx, const grtCamera* camera, uint32_t
     if (n == 0) return GRT_SUCCESS;
     if (n > 0xFFFFFFFFull) return GRT_ERROR_INVALID_PARAMETER;
     cameraRayKernel<<<ceilDiv(n, 256), 256, 0, (cudaStream_t)stream>>>(*camera, width, height, (float4*)rays);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+grtError grtGenerateUniformRays(grtContext ctx, const float lo[3], const float hi[3], uint64_t seed, uint32_t count,
+                                float minT, float maxT, grtRay* rays, void* stream) {
+    if (!ctx || !lo || !hi || (count && !rays) || ((uintptr_t)rays & 15)) return GRT_ERROR_INVALID_PARAMETER;
+    for (int a = 0; a < 3; ++a)
+        if (!(hi[a] >= lo[a]) || !std::isfinite(lo[a]) || !std::isfinite(hi[a])) return GRT_ERROR_INVALID_PARAMETER;
+    if (count == 0) return GRT_SUCCESS;
+    const float3 l = make_float3(lo[0], lo[1], lo[2]);
+    const float3 e = make_float3(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]);
+    uniformRayKernel<<<ceilDiv(count, 256), 256, 0, (cudaStream_t)stream>>>(l, e, seed, count, minT, maxT,
+                                                                               (float4*)rays);
     GRT_LAUNCH_CHECK();
     noteLaunches(1);
     return GRT_SUCCESS;

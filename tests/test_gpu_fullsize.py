@@ -93,7 +93,8 @@ def test_terrain_ambient_occlusion_1080p(gpu):
 
 def test_million_spheres_closest_and_any_hit(gpu):
     """1 M spheres (centres in [-50,50]^3, radii log-U[0.01,1]) through the function
-    table, 4,194,304 random rays, closest hit and any hit, every ray checked."""
+    table, 4,194,304 uniform random rays generated on the GPU (checked against the
+    oracle's generator), closest hit and any hit, every ray checked."""
     s = scenegen.spheres(1_000_000, half=50.0, rmin=0.01, rmax=1.0, seed=SEED, config=3)
     boxes = scenegen.sphere_aabbs(s)
     g = Geometry(gpu, boxes=device_tensor(boxes)).build()
@@ -101,8 +102,15 @@ def test_million_spheres_closest_and_any_hit(gpu):
     table = FuncTable(gpu)
     table.set(0, 0, grt.GRT_INTERSECT_SPHERE, device_tensor(s))
     n = 4_194_304
-    rays = scenegen.random_rays(n, [-50.0] * 3, [50.0] * 3, SEED, config=3)
-    rd = device_tensor(rays)
+    # the rays come from the GPU generator as in bench.py; they equal the oracle's
+    # generator (FP64 from the same splitmix64 numbers) within float32 rounding
+    rd = new_rays(n)
+    grt.grtGenerateUniformRays(gpu.handle, [-50.0] * 3, [50.0] * 3, SEED, n, rd)
+    rays = rd.cpu().numpy()
+    want = oracle.uniform_rays([-50.0] * 3, [50.0] * 3, SEED, n)
+    assert np.abs(rays[:, 0:3] - want[:, 0:3]).max() <= 1e-5  # 50 x 2^-22: within two ulps of 50
+    assert np.abs(rays[:, 4:7] - want[:, 4:7]).max() <= 1e-6
+    assert np.array_equal(rays[:, [3, 7]], want[:, [3, 7]])
     hc, ha = new_hits(n), new_hits(n)
     grt.grtTraceClosest(gpu.handle, None, g.handle, rd, n, hc, table.handle)
     grt.grtTraceAnyHit(gpu.handle, None, g.handle, rd, n, ha, table.handle)

@@ -566,3 +566,26 @@ def test_all_hits_edge_cases(gpu):
                             torch.empty(100, dtype=torch.int32, device="cuda"))
     grt.grtTraceAllHits(gpu.handle, None, empty.handle, None, 0, None, 4, None)  # no rays: nothing to do
     _no_device_error(gpu)
+
+
+@pytest.mark.parametrize("count", [1, 255, 257, 100_003])
+def test_uniform_rays_match_oracle(gpu, count):
+    """grtGenerateUniformRays against the oracle's FP64 generator from the same
+    splitmix64 numbers: origins within float32 rounding of the box, directions within
+    1e-6, range ends exact; an off-centre, non-cubic box."""
+    lo, hi = [-3.0, 10.0, -0.5], [5.0, 11.0, 0.25]
+    rays = new_rays(count)
+    grt.grtGenerateUniformRays(gpu.handle, lo, hi, 1234567, count, rays, 0.125, 7.5)
+    torch.cuda.synchronize()
+    got = rays.cpu().numpy()
+    want = oracle.uniform_rays(lo, hi, 1234567, count, 0.125, 7.5)
+    assert np.abs(got[:, 0:3] - want[:, 0:3]).max() <= 2.5e-6  # two ulps of 11
+    assert np.abs(got[:, 4:7] - want[:, 4:7]).max() <= 1e-6
+    assert np.all(got[:, 3] == np.float32(0.125)) and np.all(got[:, 7] == np.float32(7.5))
+    assert np.all(got[:, 0:3] >= np.float32(lo)) and np.all(got[:, 0:3] <= np.float32(hi))
+    # rejected: a box with hi < lo, a misaligned ray buffer
+    with pytest.raises(grt.GrtError):
+        grt.grtGenerateUniformRays(gpu.handle, hi, lo, 1, count, rays)
+    flat = torch.empty(8 * count + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(grt.GrtError):
+        grt.grtGenerateUniformRays(gpu.handle, lo, hi, 1, count, flat[1:])

@@ -547,3 +547,30 @@ def test_ao_frame_of_a_tilted_triangle():
         assert np.allclose(ao[s, 4:7], want, atol=1e-6), (s, ao[s, 4:7], want)
         assert np.allclose(ao[s, 0:3], hit + 1e-4 * n, atol=1e-6)
         assert ao[s, 3] == 0 and ao[s, 7] == np.float32(0.5)
+
+
+def test_uniform_rays_distribution():
+    """The oracle's uniform rays: unit directions whose moments are those of the uniform
+    distribution on the sphere (mean 0, E[d_i^2] = 1/3, E[d_i d_j] = 0, z uniform in
+    [-1, 1] by Archimedes' theorem, every octant 1/8), origins uniform in the box (mean
+    the centre, variance (hi - lo)^2 / 12), all in range; different seeds differ, equal
+    seeds repeat."""
+    n = 200_000
+    lo, hi = np.array([-3.0, 10.0, -0.5]), np.array([5.0, 11.0, 0.25])
+    r = oracle.uniform_rays(lo, hi, 99, n, 0.0, 4.0).astype(np.float64)
+    d, o = r[:, 4:7], r[:, 0:3]
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-6)
+    assert np.abs(d.mean(axis=0)).max() < 0.01
+    assert np.abs((d ** 2).mean(axis=0) - 1 / 3).max() < 0.01
+    c = d.T @ d / n
+    assert abs(c[0, 1]) < 0.01 and abs(c[0, 2]) < 0.01 and abs(c[1, 2]) < 0.01
+    hist = np.histogram(d[:, 2], bins=10, range=(-1, 1))[0] / n
+    assert np.abs(hist - 0.1).max() < 0.005
+    octant = (d[:, 0] > 0) * 4 + (d[:, 1] > 0) * 2 + (d[:, 2] > 0)
+    assert np.abs(np.bincount(octant, minlength=8) / n - 0.125).max() < 0.005
+    assert np.all(o >= lo) and np.all(o <= hi)
+    assert np.abs(o.mean(axis=0) - 0.5 * (lo + hi)).max() < 0.01 * (hi - lo).max()
+    assert np.abs(o.var(axis=0) / ((hi - lo) ** 2 / 12) - 1).max() < 0.02
+    assert np.all(r[:, 3] == 0.0) and np.all(r[:, 7] == 4.0)
+    assert np.array_equal(r, oracle.uniform_rays(lo, hi, 99, n, 0.0, 4.0))
+    assert not np.array_equal(r[:100], oracle.uniform_rays(lo, hi, 100, 100, 0.0, 4.0))

@@ -60,3 +60,29 @@ def test_single_process_needs_no_group():
 
     assert bench.max_over_ranks([3, 1.5]) == [3.0, 1.5]
     assert bench.job_throughput(10.0, 1, 2.0) == 5.0
+
+
+def test_gpus_flag_spawns_its_own_ranks():
+    """bench.py --gpus 2 started as a plain process runs itself under torchrun as two
+    ranks: the reference arm (CPU only) prints one line, from rank 0, with n_gpus 2."""
+    import json
+    import subprocess
+
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.05"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
+def test_launch_command_names_torchrun_on_localhost():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    cmd = bench.launch_command(["--gpus", "4", "--steps", "3"], 4, 29555)
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and "--master-addr=127.0.0.1" in cmd and "--master-port=29555" in cmd
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "3"]
