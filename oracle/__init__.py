@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
             L.oracle_lambert_forward.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, P, P]
             L.oracle_lambert_gradient.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, P]
             L.oracle_lambert_gradient.restype = ctypes.c_double
+            L.oracle_lambert_gradient_l1.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, P, P]
             L.oracle_lambert_fd.argtypes = [P, i64, P, i64, P, P, P, i64, P, P, i64, ctypes.c_double, P, P, P, P, P]
             _lib = L
     return _lib
@@ -515,6 +516,24 @@ def lambert_gradient(vertices, indices, colours, light, rays, target):
     loss = lib().oracle_lambert_gradient(_p(v), v.shape[0], _p(i), i.shape[0], _p(c), _p(l), _p(r), r.shape[0], _p(t),
                                          _p(dc), _p(dl), _p(dp))
     return float(loss), dc, dl, dp
+
+
+def lambert_gradient_l1(vertices, indices, colours, light, rays, target):
+    """Per-parameter sums over pixels of |the pixel's term of the analytic gradient|:
+    (colours (V,3), light (3,), positions (V,3)). How much a gradient's terms cancel:
+    the accuracy a sum of rounded terms can reach is relative to these, not to the sum."""
+    v = _c(vertices, np.float64)
+    i = _c(indices, np.uint32)
+    c = _c(colours, np.float64)
+    l = _c(light, np.float64).reshape(3)
+    r = _c(rays, np.float32).reshape(-1, 8)
+    t = _c(target, np.float64).reshape(-1, 3)
+    ac = np.zeros_like(c)
+    al = np.zeros(3)
+    ap = np.zeros_like(v)
+    lib().oracle_lambert_gradient_l1(_p(v), v.shape[0], _p(i), i.shape[0], _p(c), _p(l), _p(r), r.shape[0], _p(t),
+                                     _p(ac), _p(al), _p(ap))
+    return ac, al, ap
 
 
 def lambert_fd(vertices, indices, colours, light, rays, target, params, h: float = 1e-4, exclude=None,

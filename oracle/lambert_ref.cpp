@@ -234,6 +234,34 @@ double oracle_lambert_gradient(const double* verts, int64_t nv, const uint32_t* 
     return loss;
 }
 
+// Per-parameter L1 norms of the per-pixel terms of the analytic gradient: for each
+// parameter the sum over hit pixels of |that pixel's term| (the terms
+// oracle_lambert_gradient adds up). It measures how much the gradient's terms cancel,
+// which sets the accuracy a sum of rounded terms can reach. Outputs as
+// oracle_lambert_gradient's (zeroed here).
+void oracle_lambert_gradient_l1(const double* verts, int64_t nv, const uint32_t* idx, int64_t nt, const double* col,
+                                const double* light, const float* rays, int64_t n, const double* target, double* acol,
+                                double* al, double* apos) {
+    const Mesh M{verts, idx, nt};
+    const V3 l = v3(light[0], light[1], light[2]);
+    std::vector<PixelState> S((size_t)n);
+    parallel_for(n, [&](int64_t p) { S[(size_t)p] = shadePixel(M, rays + 8 * p, l); });
+    std::fill(acol, acol + 3 * nv, 0.0);
+    std::fill(apos, apos + 3 * nv, 0.0);
+    al[0] = al[1] = al[2] = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+        const PixelState& s = S[(size_t)p];
+        if (s.prim < 0) continue;
+        const PixelGrad G = pixelGrad(M, col, l, rays + 8 * p, s, target + 3 * p);
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a) {
+                acol[3 * (int64_t)G.vk[k] + a] += std::fabs(G.dcol[k][a]);
+                apos[3 * (int64_t)G.vk[k] + a] += std::fabs(G.dpos[k][a]);
+            }
+        for (int a = 0; a < 3; ++a) al[a] += std::fabs(G.dl[a]);
+    }
+}
+
 // Central differences of the masked loss for a list of parameters, and the analytic
 // gradient of the pixels the mask removes. Parameter ids: [0, 3nv) colours
 // (3*vertex + channel), [3nv, 3nv+3) light, [3nv+3, 6nv+3) positions (3*vertex + axis).

@@ -262,16 +262,53 @@ __global__ void __launch_bounds__(256) fitKernel(FitParams P) {
 }
 
 // ======================================================================= small builds
-// Up to this many primitives (or instances) a build runs in one block of
+// Up to kSmallBuild primitives (kSmallScene instances) a build runs in one block of
 // kSmallBuildThreads threads, as one launch, instead of a dozen grid-wide launches whose
-// cost is their own latency at this size (a 64-instance top level: 0.11 ms).
-constexpr uint32_t kSmallBuild = 4096;
-constexpr int kSmallBuildThreads = 256;
+// cost is their own latency at this size. The thresholds are where the measured times
+// cross (one block against the graph of grid launches, 30-bit codes): a 1,280-triangle
+// icosphere 0.070 vs 0.080 ms, 2,048 triangles 0.093 vs 0.083 ms, 4,050 triangles 0.19
+// vs 0.095 ms; a top level of 4,000 instances 0.61 vs 0.15 ms (its FP64 instance setup
+// runs on one SM). Up to kSharedFitMax primitives the block keeps the whole build on
+// chip (bitonicSortShared, fitLeafShared).
+#ifndef GRT_SMALL_BUILD
+#define GRT_SMALL_BUILD 2048
+#endif
+constexpr uint32_t kSmallBuild = GRT_SMALL_BUILD;
+constexpr uint32_t kSmallScene = 1024;
+#ifndef GRT_SMALL_BUILD_THREADS
+#define GRT_SMALL_BUILD_THREADS 1024
+#endif
+constexpr int kSmallBuildThreads = GRT_SMALL_BUILD_THREADS;
+constexpr int kSmallSceneThreads = 512;  // its FP64 instance setup needs more than 64 registers
+
+// Dynamic shared memory of a single-block build: the radix routines' histograms, or
+// the on-chip path's sort pairs, boxes and counters for kSmallBuild primitives.
+template <typename K>
+constexpr size_t smallBuildSmemBytes() {
+    return std::max(blockBuildSmemWords(kSmallBuildThreads) * sizeof(uint32_t),
+                    std::max(sharedBuildBytes<K>(kSmallBuild), sharedBuildBytes<K>(kSmallScene)));
+}
 
 template <typename K, int BITS>
 __global__ void __launch_bounds__(kSmallBuildThreads) smallBuildKernel(BlockBuild B) {
     extern __shared__ uint32_t smem[];
-    buildWhole<K, BITS>(B, B.n > 0 ? B.n : 1u, smem);  // one sort chunk
+    buildWhole<K, BITS>(B, B.n > 0 ? B.n : 1u, smem, smallBuildSmemBytes<K>());  // one sort chunk
+}
+
+// Opts the single-block kernels in to their dynamic shared memory (above the default
+// 48 KB for 63-bit codes), once per process and device.
+template <class Kern>
+static grtError allowSmem(Kern kernel, size_t bytes) {
+    int dev = 0;
+    GRT_CUDA(cudaGetDevice(&dev));
+    static std::mutex m;
+    static std::unordered_map<size_t, bool> done;
+    const size_t key = (size_t)(void*)kernel ^ ((size_t)dev << 56);
+    std::lock_guard<std::mutex> g(m);
+    if (done.count(key)) return GRT_SUCCESS;
+    GRT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done[key] = true;
+    return GRT_SUCCESS;
 }
 
 // The device pointers of a build of object o in temporary buffer t.
@@ -301,11 +338,17 @@ static BlockBuild blockBuildOf(Context* c, BvhObject* o, const BuildLayout& L, c
 }
 
 static grtError launchSmallBuild(const BlockBuild& B, cudaStream_t s) {
-    const size_t smem = blockBuildSmemWords(kSmallBuildThreads) * sizeof(uint32_t);
-    if (B.bits == 30)
+    if (B.bits == 30) {
+        const size_t smem = smallBuildSmemBytes<uint32_t>();
+        grtError e = allowSmem(smallBuildKernel<uint32_t, 10>, smem);
+        if (e != GRT_SUCCESS) return e;
         smallBuildKernel<uint32_t, 10><<<1, kSmallBuildThreads, smem, s>>>(B);
-    else
+    } else {
+        const size_t smem = smallBuildSmemBytes<unsigned long long>();
+        grtError e = allowSmem(smallBuildKernel<unsigned long long, 21>, smem);
+        if (e != GRT_SUCCESS) return e;
         smallBuildKernel<unsigned long long, 21><<<1, kSmallBuildThreads, smem, s>>>(B);
+    }
     GRT_LAUNCH_CHECK();
     noteLaunches(1);
     return GRT_SUCCESS;
@@ -403,10 +446,10 @@ __global__ void __launch_bounds__(128) instanceSetupKernel(InstanceInput I) {
     reduceBounds(c, valid, I.bounds);
 }
 
-// A top level of at most kSmallBuild instances in one block and one launch: the bounds
+// A top level of at most kSmallScene instances in one block and one launch: the bounds
 // and fit counters initialised, the instance setup, then every LBVH step.
 template <typename K, int BITS>
-__global__ void __launch_bounds__(kSmallBuildThreads) smallSceneKernel(BlockBuild B, InstanceInput I) {
+__global__ void __launch_bounds__(kSmallSceneThreads) smallSceneKernel(BlockBuild B, InstanceInput I) {
     extern __shared__ uint32_t smem[];
     if (threadIdx.x == 0) {
         B.bounds[0] = B.bounds[1] = B.bounds[2] = 0xFFFFFFFFu;
@@ -422,7 +465,7 @@ __global__ void __launch_bounds__(kSmallBuildThreads) smallSceneKernel(BlockBuil
     }
     reduceBoxBounds(mn, mx, B.bounds);
     __syncthreads();
-    buildWhole<K, BITS>(B, B.n, smem);
+    buildWhole<K, BITS>(B, B.n, smem, smallBuildSmemBytes<K>());
 }
 
 // ======================================================================= host drivers
@@ -923,15 +966,21 @@ grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* in
     I.bounds = (uint32_t*)(t + L.bounds);
     I.inv64 = o->inv64;
     I.fwd32 = o->fwd32;
-    if (n <= kSmallBuild) {
+    if (n <= kSmallScene) {
         BlockBuild B = blockBuildOf(c, o, L, t, 2u);
         B.instBoxes = I.boxes;
         B.instRecords = I.records;
-        const size_t smem = blockBuildSmemWords(kSmallBuildThreads) * sizeof(uint32_t);
-        if (B.bits == 30)
-            smallSceneKernel<uint32_t, 10><<<1, kSmallBuildThreads, smem, s>>>(B, I);
-        else
-            smallSceneKernel<unsigned long long, 21><<<1, kSmallBuildThreads, smem, s>>>(B, I);
+        if (B.bits == 30) {
+            const size_t smem = smallBuildSmemBytes<uint32_t>();
+            e = allowSmem(smallSceneKernel<uint32_t, 10>, smem);
+            if (e != GRT_SUCCESS) return e;
+            smallSceneKernel<uint32_t, 10><<<1, kSmallSceneThreads, smem, s>>>(B, I);
+        } else {
+            const size_t smem = smallBuildSmemBytes<unsigned long long>();
+            e = allowSmem(smallSceneKernel<unsigned long long, 21>, smem);
+            if (e != GRT_SUCCESS) return e;
+            smallSceneKernel<unsigned long long, 21><<<1, kSmallSceneThreads, smem, s>>>(B, I);
+        }
         GRT_LAUNCH_CHECK();
         noteLaunches(1);
         o->built = true;

@@ -169,9 +169,13 @@ __device__ __forceinline__ int commonPrefix(const K* __restrict__ keys, int n, i
 // One thread per internal node i in [0, n-2]: direction, range end, split; writes
 // the node's child indices (word 3 of the node) and each child's parent entry
 // (parent << 1 | side).
+//
+// With sChild / sParent (a single-block build) the child words and parent entries are
+// also written to those shared-memory copies.
 template <bool CG, typename K>
 __device__ __forceinline__ void karrasNode(const K* __restrict__ keys, int n, int i, float4* __restrict__ nodes,
-                                           uint32_t* __restrict__ parents) {
+                                           uint32_t* __restrict__ parents, uint2* sChild = nullptr,
+                                           uint32_t* sParent = nullptr) {
     const int d = (commonPrefix<CG>(keys, n, i, i + 1) - commonPrefix<CG>(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     const int dmin = commonPrefix<CG>(keys, n, i, i - d);
     int lmax = 2;
@@ -193,9 +197,17 @@ __device__ __forceinline__ void karrasNode(const K* __restrict__ keys, int n, in
     const uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
     nodes[4 * (size_t)i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.f, 0.f);
     const uint32_t leafBase = (uint32_t)n - 1u;
-    parents[(left & kLeafBit) ? leafBase + (left & ~kLeafBit) : left] = ((uint32_t)i << 1) | 0u;
-    parents[(right & kLeafBit) ? leafBase + (right & ~kLeafBit) : right] = ((uint32_t)i << 1) | 1u;
+    const uint32_t pl = (left & kLeafBit) ? leafBase + (left & ~kLeafBit) : left;
+    const uint32_t pr = (right & kLeafBit) ? leafBase + (right & ~kLeafBit) : right;
+    parents[pl] = ((uint32_t)i << 1) | 0u;
+    parents[pr] = ((uint32_t)i << 1) | 1u;
     if (i == 0) parents[0] = kInvalid;
+    if (sChild) {
+        sChild[i] = make_uint2(left, right);
+        sParent[pl] = ((uint32_t)i << 1) | 0u;
+        sParent[pr] = ((uint32_t)i << 1) | 1u;
+        if (i == 0) sParent[0] = kInvalid;
+    }
 }
 
 // ======================================================================= bottom-up fit (A6) + leaf layout (A7)
@@ -249,8 +261,13 @@ __device__ __forceinline__ void writeWidePair(float4* wide, uint32_t w, uint32_t
 // so its release orders only the binary box the sibling's thread reads. Traversal starts
 // at wide node 0 and only reaches the wide nodes of binary nodes at even depth; the
 // others are written all the same.
-template <int KIND>  // 0 triangles, 1 AABB list, 2 instances
-__device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
+//
+// BLOCK: every leaf of the build is walked by a thread of one block (the single-block
+// build). The visit counters are then `blockFlags` in shared memory and the box
+// hand-off is ordered at block scope (fence, shared atomic, fence), so a walk's steps
+// stay in the SM instead of making a round trip to L2 per level.
+template <int KIND, bool BLOCK = false>  // KIND: 0 triangles, 1 AABB list, 2 instances
+__device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k, uint32_t* blockFlags = nullptr) {
     Box3 b;
     if (KIND == 0) {
         float4* rec = reinterpret_cast<float4*>(P.leaves) + 3 * (size_t)k;
@@ -290,20 +307,35 @@ __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
         P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
         return;
     }
-    uint32_t pe = __ldcg(P.parents + P.n - 1 + k);
+    uint32_t pe = BLOCK ? P.parents[P.n - 1 + k] : __ldcg(P.parents + P.n - 1 + k);
     for (;;) {
         const uint32_t p = pe >> 1, side = pe & 1u;
         writeChildBox(P.nodes, p, side, b);
-        // acquire-release at GPU scope: releases this box to the sibling's thread if it
-        // comes second, and acquires the sibling's box if this thread comes second
         uint32_t prev;
-        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(P.flags + p) : "memory");
-        if (prev == 0) return;  // the sibling is still on its way up
-        const float4 bx = __ldcg(&P.nodes[4 * (size_t)p + 0]);
-        const float4 by = __ldcg(&P.nodes[4 * (size_t)p + 1]);
-        const float4 bz = __ldcg(&P.nodes[4 * (size_t)p + 2]);
-        const float4 bc = __ldcg(&P.nodes[4 * (size_t)p + 3]);
-        const uint32_t ge = p == 0 ? kInvalid : __ldcg(&P.parents[p]);
+        float4 bx, by, bz, bc;
+        uint32_t ge;
+        if (BLOCK) {
+            // message passing at block scope: box store, fence, counter; counter, fence, loads
+            __threadfence_block();
+            prev = atomicAdd(blockFlags + p, 1u);
+            if (prev == 0) return;
+            __threadfence_block();
+            bx = P.nodes[4 * (size_t)p + 0];
+            by = P.nodes[4 * (size_t)p + 1];
+            bz = P.nodes[4 * (size_t)p + 2];
+            bc = P.nodes[4 * (size_t)p + 3];
+            ge = p == 0 ? kInvalid : P.parents[p];
+        } else {
+            // acquire-release at GPU scope: releases this box to the sibling's thread if it
+            // comes second, and acquires the sibling's box if this thread comes second
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(P.flags + p) : "memory");
+            if (prev == 0) return;  // the sibling is still on its way up
+            bx = __ldcg(&P.nodes[4 * (size_t)p + 0]);
+            by = __ldcg(&P.nodes[4 * (size_t)p + 1]);
+            bz = __ldcg(&P.nodes[4 * (size_t)p + 2]);
+            bc = __ldcg(&P.nodes[4 * (size_t)p + 3]);
+            ge = p == 0 ? kInvalid : __ldcg(&P.parents[p]);
+        }
         const uint32_t c0 = __float_as_uint(bc.x), c1 = __float_as_uint(bc.y);
         const float3 lo0 = make_float3(bx.x, by.x, bz.x), hi0 = make_float3(bx.y, by.y, bz.y);
         const float3 lo1 = make_float3(bx.z, by.z, bz.z), hi1 = make_float3(bx.w, by.w, bz.w);
@@ -320,6 +352,134 @@ __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k) {
         }
         pe = ge;
     }
+}
+
+// The fit of a single-block build with every box kept in shared memory, in two steps.
+// Node j of the build (internal nodes 0..n-2, then leaf k as n-1+k) has its box in sBox
+// (six float arrays of 2n-1 entries: lo.x, lo.y, lo.z, hi.x, hi.y, hi.z), its parent
+// entry in sParent and, for internal nodes, its child words in sChild and a visit
+// counter in sFlag (zeroed).
+//  1. fitLeafShared: leaf k's thread stores its box and walks up while it is the second
+//     to reach a node, storing the union for the level above. Only shared memory is
+//     touched during the walk (hand-offs ordered at block scope: fence, shared atomic,
+//     fence), so no fence waits on a global store; the leaf record is written after.
+//  2. writeNodeShared, one thread per internal node after a block barrier: binary node
+//     p (child boxes and child words, as emission and the fit write them) and 4-wide
+//     node p (p's children, each internal child replaced by its two children).
+struct SharedFit {
+    float* sBox;  // 6 x (2n-1)
+    uint32_t* sParent;
+    const uint2* sChild;
+    uint32_t* sFlag;
+};
+
+__device__ __forceinline__ void storeBoxShared(const SharedFit& F, uint32_t total, uint32_t j, const Box3& b) {
+    F.sBox[0 * total + j] = b.lo.x, F.sBox[1 * total + j] = b.lo.y, F.sBox[2 * total + j] = b.lo.z;
+    F.sBox[3 * total + j] = b.hi.x, F.sBox[4 * total + j] = b.hi.y, F.sBox[5 * total + j] = b.hi.z;
+}
+
+__device__ __forceinline__ Box3 loadBoxShared(const SharedFit& F, uint32_t total, uint32_t j) {
+    Box3 b;
+    b.lo = make_float3(F.sBox[j], F.sBox[total + j], F.sBox[2 * total + j]);
+    b.hi = make_float3(F.sBox[3 * total + j], F.sBox[4 * total + j], F.sBox[5 * total + j]);
+    return b;
+}
+
+// Node index (0..2n-2) of child word c.
+__device__ __forceinline__ uint32_t nodeOfChild(uint32_t c, uint32_t n) {
+    return (c & kLeafBit) ? n - 1 + (c & ~kLeafBit) : c;
+}
+
+template <int KIND>
+__device__ __forceinline__ void fitLeafShared(const FitParams& P, uint32_t k, const SharedFit& F) {
+    const uint32_t n = P.n, total = 2 * n - 1;
+    Box3 b;
+    uint32_t prim = P.sortedPrims[k];
+    float3 v[3];
+    if (KIND == 2) {
+        const float4 lo = P.instBoxes[2 * (size_t)prim], hi = P.instBoxes[2 * (size_t)prim + 1];
+        b.lo = make_float3(lo.x, lo.y, lo.z);
+        b.hi = make_float3(hi.x, hi.y, hi.z);
+    } else {
+        b = primBox(P.src, prim, v);
+    }
+    uint32_t j = n - 1 + k;
+    for (;;) {
+        storeBoxShared(F, total, j, b);
+        if (j == 0) {
+            P.header->rootLo[0] = b.lo.x, P.header->rootLo[1] = b.lo.y, P.header->rootLo[2] = b.lo.z;
+            P.header->rootHi[0] = b.hi.x, P.header->rootHi[1] = b.hi.y, P.header->rootHi[2] = b.hi.z;
+            break;
+        }
+        const uint32_t p = F.sParent[j] >> 1;
+        __threadfence_block();
+        if (atomicAdd(F.sFlag + p, 1u) == 0) break;  // the sibling is still on its way up
+        __threadfence_block();
+        const uint2 c = F.sChild[p];
+        const Box3 b0 = loadBoxShared(F, total, nodeOfChild(c.x, n)), b1 = loadBoxShared(F, total, nodeOfChild(c.y, n));
+        b.lo = make_float3(fminf(b0.lo.x, b1.lo.x), fminf(b0.lo.y, b1.lo.y), fminf(b0.lo.z, b1.lo.z));
+        b.hi = make_float3(fmaxf(b0.hi.x, b1.hi.x), fmaxf(b0.hi.y, b1.hi.y), fmaxf(b0.hi.z, b1.hi.z));
+        j = p;
+    }
+    if (KIND == 0) {
+        float4* rec = reinterpret_cast<float4*>(P.leaves) + 3 * (size_t)k;
+        rec[0] = make_float4(v[0].x, v[0].y, v[0].z, __uint_as_float(prim));
+        // w slots: L1 norms of the edges v1-v0 and v2-v0 (scale of the traversal's error bounds)
+        const float e1 = fabsf(v[1].x - v[0].x) + fabsf(v[1].y - v[0].y) + fabsf(v[1].z - v[0].z);
+        const float e2 = fabsf(v[2].x - v[0].x) + fabsf(v[2].y - v[0].y) + fabsf(v[2].z - v[0].z);
+        rec[1] = make_float4(v[1].x, v[1].y, v[1].z, e1);
+        rec[2] = make_float4(v[2].x, v[2].y, v[2].z, e2);
+        P.primToLeaf[prim] = k;
+    } else if (KIND == 1) {
+        reinterpret_cast<uint32_t*>(P.leaves)[k] = prim;
+    } else {
+        reinterpret_cast<InstanceRecord*>(P.leaves)[k] = P.instRecords[prim];
+        P.primToLeaf[prim] = k;
+    }
+}
+
+// Component `comp` (0..5: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z) of node j's box.
+__device__ __forceinline__ float boxComp(const SharedFit& F, uint32_t total, uint32_t j, uint32_t comp) {
+    return F.sBox[((comp & 1u) ? 3u : 0u) * total + (comp >> 1) * total + j];
+}
+
+// Row r of binary node p (0..2: the x, y, z rows (c0.lo, c0.hi, c1.lo, c1.hi); 3: the
+// child words and two zero words), from the shared boxes and child words.
+__device__ __forceinline__ float4 binaryRowShared(const SharedFit& F, uint32_t n, uint32_t p, uint32_t r) {
+    const uint32_t total = 2 * n - 1;
+    const uint2 c = F.sChild[p];
+    if (r == 3) return make_float4(__uint_as_float(c.x), __uint_as_float(c.y), 0.f, 0.f);
+    const uint32_t j0 = nodeOfChild(c.x, n), j1 = nodeOfChild(c.y, n);
+    return make_float4(boxComp(F, total, j0, 2 * r), boxComp(F, total, j0, 2 * r + 1), boxComp(F, total, j1, 2 * r),
+                       boxComp(F, total, j1, 2 * r + 1));
+}
+
+// Row r of 4-wide node p (0..5: component r of the four slots; 6: the four child words;
+// 7: zero): slots 2s and 2s+1 hold child s's two children, or child s itself (a leaf)
+// and an empty slot (child word kInvalid, box +inf / -inf).
+__device__ __forceinline__ float4 wideRowShared(const SharedFit& F, uint32_t n, uint32_t p, uint32_t r) {
+    const uint32_t total = 2 * n - 1;
+    if (r == 7) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint2 c = F.sChild[p];
+    const uint32_t cw[2] = {c.x, c.y};
+    float out[4];
+#pragma unroll
+    for (uint32_t s = 0; s < 2; ++s) {
+        uint32_t a, b;
+        if (cw[s] & kLeafBit) {
+            a = cw[s], b = kInvalid;
+        } else {
+            const uint2 g = F.sChild[cw[s]];
+            a = g.x, b = g.y;
+        }
+        if (r == 6) {
+            out[2 * s] = __uint_as_float(a), out[2 * s + 1] = __uint_as_float(b);
+        } else {
+            out[2 * s] = boxComp(F, total, nodeOfChild(a, n), r);
+            out[2 * s + 1] = b == kInvalid ? ((r & 1u) ? -INFINITY : INFINITY) : boxComp(F, total, nodeOfChild(b, n), r);
+        }
+    }
+    return make_float4(out[0], out[1], out[2], out[3]);
 }
 
 // Host: checks a geometry build input and returns its primitive count; the device-side

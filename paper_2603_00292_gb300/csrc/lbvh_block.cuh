@@ -300,13 +300,236 @@ __device__ __noinline__ void rankSortShared(const BlockBuild& S, uint32_t* smem)
     }
 }
 
+// Smallest power of two >= n (n >= 1).
+__host__ __device__ constexpr uint32_t pow2Ceil(uint32_t n) {
+    uint32_t m = 1;
+    while (m < n) m <<= 1;
+    return m;
+}
+
+// Up to this many primitives the on-chip path of a single-block build also keeps the
+// fit's boxes, parent entries and child words in shared memory (fitLeafShared).
+constexpr uint32_t kSharedFitMax = 2048;
+
+// Shared memory of a single-block build's sort: m = pow2Ceil(n) elements of 8 bytes
+// ((code << 32) | index for 30-bit codes) or 12 bytes (64-bit code, then index).
+// Elements of the bitonic sort of n codes: a power of two, at least 64 (one chunk of
+// two elements per lane of a warp).
+__host__ __device__ constexpr uint32_t sortElems(uint32_t n) { return pow2Ceil(n) < 64u ? 64u : pow2Ceil(n); }
+
+template <typename K>
+__host__ __device__ constexpr size_t sharedSortBytes(uint32_t n) {
+    return (size_t)sortElems(n) * (sizeof(K) == 4 ? 8 : 12);
+}
+
+// Shared memory of the on-chip path of a single-block build of n primitives, in bytes.
+// n <= kSharedFitMax: [sort pairs, later the six box arrays of 2n-1 floats] [parent
+// entries, 2n-1] [child words, n-1 pairs] [visit counters, n-1]. Larger n: [sort pairs]
+// [visit counters, n].
+__host__ __device__ constexpr size_t alignSmem(size_t b) { return (b + 15) & ~(size_t)15; }
+template <typename K>
+__host__ __device__ constexpr size_t sharedBuildBytes(uint32_t n) {
+    return n <= kSharedFitMax
+               ? alignSmem(sharedSortBytes<K>(n) > 24 * (2 * (size_t)n - 1) ? sharedSortBytes<K>(n)
+                                                                           : 24 * (2 * (size_t)n - 1)) +
+                     alignSmem(4 * (2 * (size_t)n - 1)) + alignSmem(8 * (size_t)n) + 4 * (size_t)n
+               : alignSmem(sharedSortBytes<K>(n)) + 4 * (size_t)n;
+}
+
+// Stable sort of a small build's Morton codes in shared memory by Batcher's bitonic
+// network (Batcher, "Sorting networks and their applications", 1968) over (code,
+// index) pairs: the index breaks ties between equal codes, so the order is the stable
+// order the radix passes produce. The pairs are padded to a power of two m with
+// all-ones elements, which sort last. Each step compares m/2 disjoint pairs, one per
+// thread. Afterwards the sorted codes are the first n entries of smem (as K) for
+// emission, and codes and indices also go to the final ping-pong buffers
+// (keys[passes & 1], vals[passes & 1]) as after the radix passes.
+template <typename K, int BITS>
+__device__ __noinline__ void bitonicSortShared(const BlockBuild& S, uint32_t* smem, uint32_t m) {
+    const uint32_t n = S.n;
+    uint32_t b[6];
+    loadBounds(S, b);
+    K* kout = static_cast<K*>(S.keys[S.passes & 1u]);
+    uint32_t* vout = S.vals[S.passes & 1u];
+    if constexpr (sizeof(K) == 4) {
+        // Elements (code << 32) | index. Chunk q holds elements [64q, 64q + 64): lane l of
+        // the warp that owns it keeps elements 64q + l and 64q + 32 + l in registers, so
+        // the steps with j <= 32 run in registers (j = 32 within a lane, j < 32 between
+        // lanes by shuffles) and only those with j >= 64 go through shared memory.
+        unsigned long long* e = reinterpret_cast<unsigned long long*>(smem);
+        const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+        const uint32_t chunks = m >> 6, owned = (chunks + warps - 1 - warp) / warps;  // chunks of this warp
+        constexpr uint32_t kChunks = 4;  // m <= 8 blockDim.x
+        unsigned long long x[kChunks][2];
+#pragma unroll
+        for (uint32_t c = 0; c < kChunks; ++c)
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+                const uint32_t i = 64u * (warp + c * warps) + 32u * h + lane;
+                x[c][h] = (c < owned && i < n)
+                              ? ((unsigned long long)mortonCode<K, BITS>(__ldcg(S.centroids + i), b) << 32) | i
+                              : ~0ull;
+            }
+        for (uint32_t k = 2; k <= m; k <<= 1) {
+            if (k > 64) {
+                __syncthreads();  // every thread has read the previous shared step's results
+#pragma unroll
+                for (uint32_t c = 0; c < kChunks; ++c)
+                    if (c < owned) e[64u * (warp + c * warps) + lane] = x[c][0], e[64u * (warp + c * warps) + 32u + lane] = x[c][1];
+                __syncthreads();
+                for (uint32_t j = k >> 1; j >= 64; j >>= 1) {
+                    for (uint32_t t = threadIdx.x; t < (m >> 1); t += blockDim.x) {
+                        const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1)), l = i | j;
+                        const unsigned long long a = e[i], c = e[l];
+                        if ((a > c) == ((i & k) == 0)) e[i] = c, e[l] = a;  // ascending where bit k of i is clear
+                    }
+                    __syncthreads();
+                }
+#pragma unroll
+                for (uint32_t c = 0; c < kChunks; ++c)
+                    if (c < owned) x[c][0] = e[64u * (warp + c * warps) + lane], x[c][1] = e[64u * (warp + c * warps) + 32u + lane];
+            }
+            for (uint32_t j = (k >> 1) < 32u ? (k >> 1) : 32u; j > 0; j >>= 1) {
+#pragma unroll
+                for (uint32_t c = 0; c < kChunks; ++c) {
+                    if (c >= owned) continue;  // warp-uniform
+                    const uint32_t i0 = 64u * (warp + c * warps) + lane;
+                    if (j == 32) {  // elements i0 and i0 + 32 of this lane (same bit k: k >= 64)
+                        const unsigned long long lo = min(x[c][0], x[c][1]), hi = max(x[c][0], x[c][1]);
+                        const bool asc = (i0 & k) == 0;
+                        x[c][0] = asc ? lo : hi;
+                        x[c][1] = asc ? hi : lo;
+                    } else {
+                        const bool lower = (lane & j) == 0;
+#pragma unroll
+                        for (uint32_t h = 0; h < 2; ++h) {
+                            const unsigned long long y = __shfl_xor_sync(0xffffffffu, x[c][h], j);
+                            const bool asc = ((i0 + 32u * h) & k) == 0;
+                            x[c][h] = (lower == asc) ? min(x[c][h], y) : max(x[c][h], y);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (uint32_t c = 0; c < kChunks; ++c)
+            if (c < owned) e[64u * (warp + c * warps) + lane] = x[c][0], e[64u * (warp + c * warps) + 32u + lane] = x[c][1];
+        __syncthreads();
+        // unpack: the codes to the front of smem as K (through registers: the packed
+        // elements are read before any code is written over them)
+        constexpr uint32_t kMaxPer = 8;  // m / blockDim.x <= 4096 / 512
+        unsigned long long mine[kMaxPer];
+        uint32_t c = 0;
+        for (uint32_t i = threadIdx.x; i < n && c < kMaxPer; i += blockDim.x) mine[c++] = e[i];
+        __syncthreads();
+        K* keys = reinterpret_cast<K*>(smem);
+        c = 0;
+        for (uint32_t i = threadIdx.x; i < n && c < kMaxPer; i += blockDim.x, ++c) {
+            const K code = (K)(mine[c] >> 32);
+            keys[i] = code;
+            kout[i] = code;
+            vout[i] = (uint32_t)mine[c];
+        }
+    } else {
+        K* keys = reinterpret_cast<K*>(smem);
+        uint32_t* idx = reinterpret_cast<uint32_t*>(keys + m);
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+            keys[i] = i < n ? mortonCode<K, BITS>(__ldcg(S.centroids + i), b) : ~(K)0;
+            idx[i] = i < n ? i : kInvalid;
+        }
+        __syncthreads();
+        for (uint32_t k = 2; k <= m; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t t = threadIdx.x; t < (m >> 1); t += blockDim.x) {
+                    const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1)), l = i | j;
+                    const K ki = keys[i], kl = keys[l];
+                    const uint32_t ii = idx[i], il = idx[l];
+                    const bool greater = ki > kl || (ki == kl && ii > il);
+                    if (greater == ((i & k) == 0)) {
+                        keys[i] = kl, keys[l] = ki;
+                        idx[i] = il, idx[l] = ii;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            kout[i] = keys[i];
+            vout[i] = idx[i];
+        }
+    }
+}
+
+// The bottom-up fit of a single-block build, counters in shared memory (flags, n - 1
+// words, zeroed).
+static __device__ __noinline__ void fitRangeBlock(const BlockBuild& S, uint32_t* flags) {
+    FitParams P{};
+    P.src = S.src;
+    P.n = S.n;
+    P.sortedPrims = S.vals[S.passes & 1u];
+    P.nodes = S.nodes;
+    P.wide = S.wide;
+    P.leaves = S.leaves;
+    P.primToLeaf = S.primToLeaf;
+    P.parents = S.parents;
+    P.flags = S.flags;
+    P.header = S.header;
+    P.instBoxes = S.instBoxes;
+    P.instRecords = S.instRecords;
+    for (uint32_t k = threadIdx.x; k < S.n; k += blockDim.x) {
+        if (S.kind == 0)
+            fitLeaf<0, true>(P, k, flags);
+        else if (S.kind == 1)
+            fitLeaf<1, true>(P, k, flags);
+        else
+            fitLeaf<2, true>(P, k, flags);
+    }
+}
+
+// The fit of a single-block build of at most kSharedFitMax primitives, all in shared
+// memory (fitLeafShared).
+static __device__ __noinline__ void fitRangeShared(const BlockBuild& S, const SharedFit& F) {
+    FitParams P{};
+    P.src = S.src;
+    P.n = S.n;
+    P.sortedPrims = S.vals[S.passes & 1u];
+    P.nodes = S.nodes;
+    P.wide = S.wide;
+    P.leaves = S.leaves;
+    P.primToLeaf = S.primToLeaf;
+    P.header = S.header;
+    P.instBoxes = S.instBoxes;
+    P.instRecords = S.instRecords;
+    for (uint32_t k = threadIdx.x; k < S.n; k += blockDim.x) {
+        if (S.kind == 0)
+            fitLeafShared<0>(P, k, F);
+        else if (S.kind == 1)
+            fitLeafShared<1>(P, k, F);
+        else
+            fitLeafShared<2>(P, k, F);
+    }
+    __syncthreads();  // every box is in shared memory
+    // the node arrays, one float4 row per thread and step, so that a warp's stores are
+    // contiguous (binary nodes: 4 rows each; 4-wide nodes: 8 rows each)
+    const uint32_t n = S.n;
+    for (uint32_t q = threadIdx.x; q < 4 * (n - 1); q += blockDim.x) S.nodes[q] = binaryRowShared(F, n, q >> 2, q & 3u);
+    for (uint32_t q = threadIdx.x; q < kWideWords * (n - 1); q += blockDim.x)
+        S.wide[q] = wideRowShared(F, n, q / kWideWords, q % kWideWords);
+}
+
 // The whole build of a small scene by one block, phase after phase.
 template <typename K, int BITS>
 // Every step's global writes are read by other threads of the same block after a
 // block barrier, which orders them at block scope; no wider fence is needed here. Triangle
 // and box builds start from uninitialised bounds and fit counters; an instance build
 // expects both prepared with the centroids (its setup runs first).
-__device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys, uint32_t* smem) {
+// With smemBytes >= sharedBuildBytes<K>(n) the sort, emission and fit run on chip
+// (bitonicSortShared, emission from the shared codes, fitRangeBlock); otherwise the
+// codes are ranked in shared memory (n <= kRankSortMax) or radix-sorted through the
+// build temporary, and the fit uses the global counters.
+__device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys, uint32_t* smem,
+                                        size_t smemBytes = 0) {
     if (S.n == 0) return;
     if (S.kind != 2) {
         if (threadIdx.x == 0) {
@@ -317,6 +540,39 @@ __device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys,
         prepRange(S, 0, S.n);
     }
     __syncthreads();
+    if (S.n >= 2 && sharedBuildBytes<K>(S.n) <= smemBytes && sortElems(S.n) <= blockDim.x * 8u) {
+        const uint32_t n = S.n, m = sortElems(n);
+        bitonicSortShared<K, BITS>(S, smem, m);
+        __syncthreads();
+        const K* sorted = reinterpret_cast<const K*>(smem);
+        char* base = reinterpret_cast<char*>(smem);
+        if (n <= kSharedFitMax) {
+            const size_t boxBytes = alignSmem(sharedSortBytes<K>(n) > 24 * (2 * (size_t)n - 1)
+                                                  ? sharedSortBytes<K>(n)
+                                                  : 24 * (2 * (size_t)n - 1));
+            SharedFit F;
+            F.sBox = reinterpret_cast<float*>(base);  // over the sort pairs, once emission is done
+            F.sParent = reinterpret_cast<uint32_t*>(base + boxBytes);
+            uint2* child = reinterpret_cast<uint2*>(base + boxBytes + alignSmem(4 * (2 * (size_t)n - 1)));
+            F.sChild = child;
+            F.sFlag = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(child) + alignSmem(8 * (size_t)n));
+            for (uint32_t i = threadIdx.x; i + 1 < n; i += blockDim.x) {
+                karrasNode<false>(sorted, (int)n, (int)i, S.nodes, S.parents, child, F.sParent);
+                F.sFlag[i] = 0u;
+            }
+            __syncthreads();
+            fitRangeShared(S, F);
+            return;
+        }
+        uint32_t* flags = reinterpret_cast<uint32_t*>(base + alignSmem(sharedSortBytes<K>(n)));
+        for (uint32_t i = threadIdx.x; i + 1 < n; i += blockDim.x) {
+            karrasNode<false>(sorted, (int)n, (int)i, S.nodes, S.parents);
+            flags[i] = 0u;
+        }
+        __syncthreads();
+        fitRangeBlock(S, flags);
+        return;
+    }
     const bool ranked = S.n <= kRankSortMax && blockDim.x >= 64 &&
                         (size_t)S.n * (sizeof(K) + 4) <= blockBuildSmemWords(blockDim.x) * sizeof(uint32_t);
     if (ranked) {

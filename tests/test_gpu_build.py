@@ -35,9 +35,9 @@ def _case(name):
     if name == "spheres":
         s = scenegen.spheres(50_003, half=20.0, config=91)
         return dict(boxes=scenegen.sphere_aabbs(s))
-    if name == "dupes":  # many primitives sharing one centroid -> equal Morton codes
+    if name in ("dupes", "dupes_small"):  # many primitives sharing one centroid -> equal Morton codes
         rng = np.random.default_rng(4)
-        c = rng.integers(0, 4, (9000, 3)).astype(np.float32)
+        c = rng.integers(0, 4, (9000 if name == "dupes" else 3000, 3)).astype(np.float32)
         b = np.concatenate([c - 0.25, c + 0.25], axis=1).astype(np.float32)
         return dict(boxes=b)
     if name.startswith("n"):
@@ -185,8 +185,8 @@ def check_refit_traces(gpu, g, case, seed):
     assert rep.matched > n // 2, rep.summary()
 
 
-@pytest.mark.parametrize("name", ["icosphere", "terrain", "flat", "spheres", "dupes", "n1", "n2", "n3", "n17",
-                                  "n4097"])
+@pytest.mark.parametrize("name", ["icosphere", "terrain", "flat", "spheres", "dupes", "dupes_small", "n1", "n2", "n3",
+                                  "n17", "n513", "n1025", "n2048", "n2049", "n4096", "n4097"])
 @pytest.mark.parametrize("bits", [30, 63])
 def test_build_matches_oracle_bit_exact(gpu, name, bits):
     case = _case(name)

@@ -47,9 +47,21 @@ def _gpu_backward(gpu, d, g, n, hits, vis, gimg):
     return gc.cpu().numpy().astype(np.float64), gl.cpu().numpy().astype(np.float64), gp.cpu().numpy().astype(np.float64)
 
 
-def _rel_ok(g, ref, rel=1e-3):
+U32 = 2.0 ** -24  # unit roundoff of float32
+
+
+def _rel_ok(g, ref, rel=1e-3, l1=None):
+    """|g - ref| <= 1e-3 max(|ref|, 1e-6 max|ref|), or, where the gradient's per-pixel terms
+    cancel, <= 32 u S1 with S1 the sum of |terms| (oracle.lambert_gradient_l1): the GPU
+    evaluates each term in float32 (a dozen rounded operations, <= 16u of the term
+    relative) and sums them in float32 (warp shuffles, then atomics; <= 16u of S1 for the
+    few hundred terms of a vertex). Where S1 / |ref| > 1e-3 / (32u), about 520, no float32
+    evaluation can reach 1e-3 of ref."""
     scale = np.abs(ref).max()
-    return np.abs(g - ref) <= rel * np.maximum(np.abs(ref), 1e-6 * scale) + 1e-12
+    tol = rel * np.maximum(np.abs(ref), 1e-6 * scale) + 1e-12
+    if l1 is not None:
+        tol = np.maximum(tol, 32 * U32 * l1)
+    return np.abs(g - ref) <= tol
 
 
 def test_forward_matches_oracle(gpu):
@@ -95,13 +107,21 @@ def test_backward_matches_oracle_gradient(gpu, recompute):
     exclude = _mismatched(hits, vis, R)
     assert exclude.sum() <= max(3, 1e-4 * n)
     _, dc, dl, dp = oracle.lambert_gradient(verts64, P.mesh.indices, cols64, l64, rays[~exclude], target[~exclude])
+    l1 = oracle.lambert_gradient_l1(verts64, P.mesh.indices, cols64, l64, rays[~exclude], target[~exclude])
     gimg = 2.0 * (R.image - target)
     gimg[exclude] = 0.0
     gc, gl, gp = _gpu_backward(gpu, d, g, n, None if recompute else hits, None if recompute else vis,
                                device_tensor(gimg.astype(np.float32)))
-    for got, ref in ((gc, dc), (gl, dl), (gp, dp)):
-        ok = _rel_ok(got, ref)
-        assert ok.all(), (np.nonzero(~ok), got[~ok][:5], ref[~ok][:5])
+    _check_every_gradient((gc, gl, gp), (dc, dl, dp), l1)
+
+
+def _check_every_gradient(got, ref, l1):
+    """Every element of the colour, light and position gradients within _rel_ok's bound
+    (the float32 floor can decide an element only where its terms cancel by more than
+    ~520x)."""
+    for name, a, b, s1 in zip(("colour", "light", "position"), got, ref, l1):
+        ok = _rel_ok(a, b, l1=s1)
+        assert ok.all(), (name, np.nonzero(~ok), a[~ok][:5], b[~ok][:5], s1[~ok][:5])
 
 
 @pytest.mark.parametrize("layout", ["global", "mixed"])
@@ -222,8 +242,10 @@ def test_full_size_gradient_against_central_differences(gpu):
         return [(int(p), k, a, b) for p, k, a, b in zip(params[~ok], kinds[~ok], grad[~ok], ref[~ok])][:8]
 
     _, dc, dl, dp = oracle.lambert_gradient(verts64, P.mesh.indices, cols64, l64, rays[~exclude], target[~exclude])
+    ac, al, ap = oracle.lambert_gradient_l1(verts64, P.mesh.indices, cols64, l64, rays[~exclude], target[~exclude])
     analytic = np.concatenate([dc.ravel(), dl, dp.ravel()])[params]
-    ok = _rel_ok(grad, analytic)
+    s1 = np.concatenate([ac.ravel(), al, ap.ravel()])[params]
+    ok = _rel_ok(grad, analytic, l1=s1)
     assert ok.all(), failures(ok, analytic)
 
     args = (verts64, P.mesh.indices, cols64, l64, rays, target)
@@ -278,12 +300,12 @@ def test_shadowed_scene_forward_and_gradient(gpu):
     assert exclude.sum() <= max(3, 1e-3 * lit.sum())
     _, dc, dl, dp = oracle.lambert_gradient(v64, idx, cols.astype(np.float64), light.astype(np.float64),
                                             rays[~exclude], target[~exclude])
+    l1 = oracle.lambert_gradient_l1(v64, idx, cols.astype(np.float64), light.astype(np.float64), rays[~exclude],
+                                    target[~exclude])
     gimg = 2.0 * (R.image - target)
     gimg[exclude] = 0.0
     gc, gl, gp = _gpu_backward(gpu, d, g, n, hits, vis, device_tensor(gimg.astype(np.float32)))
-    for got, ref in ((gc, dc), (gl, dl), (gp, dp)):
-        ok = _rel_ok(got, ref)
-        assert ok.all(), (np.nonzero(~ok), got[~ok][:5], ref[~ok][:5])
+    _check_every_gradient((gc, gl, gp), (dc, dl, dp), l1)
     assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
     g.close()
 

@@ -120,3 +120,29 @@ def test_shadow_closed_form_occluder_above_ground():
     assert np.all(R2.prim <= 1)  # only the ground is hit
     assert np.all(R2.vis[under] == 0) and np.all(R2.image[under] == 0)
     assert np.all(R2.vis[~under] == 1) and np.allclose(R2.image[~under], cols[0], rtol=0, atol=1e-15)
+
+
+def test_gradient_term_l1_norms():
+    """The per-parameter L1 norms of the gradient's per-pixel terms: at least |gradient|
+    (triangle inequality), equal to it for a single pixel, zero where the render meets
+    its target (every term carries the residual I - I*), and linear in a common scale of
+    the residual; the light's norm is the sum of the per-pixel |terms| of each pixel."""
+    mesh, verts, cols, light, rays, target = _setup()
+    _, dc, dl, dp = oracle.lambert_gradient(verts, mesh.indices, cols, light, rays, target)
+    ac, al, ap = oracle.lambert_gradient_l1(verts, mesh.indices, cols, light, rays, target)
+    for g, a in ((dc, ac), (dl, al), (dp, ap)):
+        assert np.all(a >= np.abs(g) - 1e-12 * (1 + np.abs(g)))
+    assert (ap > 10 * np.abs(dp)).any()  # some position gradients cancel strongly
+    R = oracle.lambert_forward(verts, mesh.indices, cols, light, rays)
+    p = int(np.nonzero((R.prim >= 0) & (R.sign > 0))[0][0])
+    one = rays[p:p + 1]
+    _, dc1, dl1, dp1 = oracle.lambert_gradient(verts, mesh.indices, cols, light, one, target[p:p + 1])
+    ac1, al1, ap1 = oracle.lambert_gradient_l1(verts, mesh.indices, cols, light, one, target[p:p + 1])
+    assert np.array_equal(ac1, np.abs(dc1)) and np.array_equal(al1, np.abs(dl1)) and np.array_equal(ap1, np.abs(dp1))
+    z = oracle.lambert_gradient_l1(verts, mesh.indices, cols, light, rays, R.image)
+    assert all(not a.any() for a in z)
+    # residual scaled by 2 about the render: every term doubles
+    t2 = R.image + 2.0 * (target - R.image)
+    ac2, al2, ap2 = oracle.lambert_gradient_l1(verts, mesh.indices, cols, light, rays, t2)
+    assert np.allclose(ac2, 2 * ac, rtol=1e-12) and np.allclose(ap2, 2 * ap, rtol=1e-12)
+    assert np.allclose(al2, 2 * al, rtol=1e-12)
