@@ -180,8 +180,8 @@ def source_hash(unit: str) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
+def ncu_record(kernel: str):
+    """The committed ncu record of `kernel` (profiles/ncu_traffic.json), if it was taken
     from the kernel's current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
@@ -192,7 +192,37 @@ def ncu_traffic(kernel: str):
     e = d.get(kernel)
     if not e or e.get("source_hash") != source_hash(KERNEL_UNITS[kernel]):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, if it was taken
+    from the kernel's current sources (else None)."""
+    e = ncu_record(kernel)
+    return None if e is None else e.get("dram_bytes_per_launch")
+
+
+# What bounds each traversal kernel when no current ncu record says so: the unit with
+# the highest ncu utilisation in the last capture (profiles/): instruction issue for
+# the terrain kernels, L1 for the sphere and icosphere traversals, DRAM for the batch.
+STATIC_BOUND = {"aoTraceKernel": "issue", "traceKernel<closest, scene>": "issue",
+                "traceKernel<closest, geometry> icosphere-512": "l1",
+                "traceKernel<closest, geometry> spheres-1m": "l1", "traceKernel<any, geometry> spheres-1m": "l1",
+                "shadeBackwardKernel<false, true>": "issue", "batchKernel": "issue"}
+
+
+def kernel_bound(kernel: str, peak_gbs: float):
+    """(bound, counters): the unit with the highest utilisation in the kernel's current
+    ncu record among L1, L2, DRAM and instruction issue, with those percentages; or the
+    static label and None without a current record."""
+    e = ncu_record(kernel)
+    if not e or "l1_pct" not in e:
+        return STATIC_BOUND.get(kernel, "hbm"), None
+    dram_pct = 100.0 * e["dram_bytes_per_launch"] / (e["duration_ns"] * 1e-9) / 1e9 / peak_gbs
+    util = {"l1": e["l1_pct"], "l2": e["l2_pct"], "hbm": round(dram_pct, 2), "issue": e["issue_pct"]}
+    counters = dict(util, memory_sol_pct=e.get("mem_sol_pct"), l2_hit_pct=e.get("l2_hit_pct"),
+                    warps_active_pct=e.get("warps_active_pct"), lanes_per_instruction=e.get("lanes_per_inst"))
+    return max(util, key=util.get), counters
 
 
 class ClockSampler:
@@ -399,6 +429,21 @@ def run_grt(args, rank, world, local):
                                                   None, sh))
     ms_all = timed(lambda: grt.grtTraceAllHits(ctx.handle, scene.handle, None, rays, npix, ahits, kmax, acount,
                                                None, None, sh))
+    # the same scene framed densely: the overview camera moved to 0.35 extent from the
+    # scene centre, where most pixels hit (closest hit + fused AO, as in the step)
+    import scenegen
+    dcam = scenegen.close_camera(sc, W, H).packed()
+    drays, dhits = new_rays(npix), new_hits(npix)
+    grt.grtGenerateCameraRays(ctx.handle, grt.camera(dcam[0:3], dcam[3:6], dcam[6:9]), W, H, drays, sh)
+    ms_dc = timed(lambda: grt.grtTraceClosest(ctx.handle, scene.handle, None, drays, npix, dhits, None, None, sh))
+    ms_da = timed(lambda: grt.grtTraceAmbientOcclusion(ctx.handle, scene.handle, drays, dhits, npix, spp, seed, length,
+                                                       ao, None, sh))
+    dhit = int((dhits[:, 1].view(torch.int32) != -1).sum().item())
+    dense = {"camera": "scene centre + (0, 0, 0.35 extent), looking down -z", "primary_hits": dhit,
+             "hit_fraction": round(dhit / npix, 4), "closest_ms": round(ms_dc, 4), "ao_ms": round(ms_da, 4),
+             "rays": npix + spp * dhit, "mrays_per_s": round((npix + spp * dhit) / (ms_dc + ms_da) / 1e3, 1),
+             "closest_mrays_per_s": round(npix / ms_dc / 1e3, 1),
+             "ao_mrays_per_s": round(spp * dhit / ms_da / 1e3, 1)}
     # the three build options of the terrain geometry (linear BVH, clustering with search
     # radius 8 and 32): build time, surface-area cost of the tree (sum of internal node
     # box areas over the root's), the closest + AO traces and the whole step over it
@@ -449,6 +494,7 @@ def run_grt(args, rank, world, local):
                 "filter_half_closest_ms": round(ms_filter, 4),
                 "all_hits_primary": {"ms": round(ms_all, 4), "hits_found": all_found,
                                      "mrays_per_s": round(npix / ms_all / 1e3, 1)},
+                "dense_view": dense,
                 "path_trace_nee": {"ms": round(ms_pt, 4), "max_depth": 3, "spp": 1,
                                    "mpaths_per_s": round(npix / ms_pt / 1e3, 1),
                                    "mean_radiance": round(float(pt_out.mean().item()), 5)},
@@ -473,14 +519,8 @@ def run_grt(args, rank, world, local):
             "ao": (statistics.mean(ao_ms), bytes_ao, "aoTraceKernel")}
     dom = max(kern, key=lambda k: kern[k][0])
     ms, nbytes, kname = kern[dom]
-    peaks, how = measured_peaks()
-    achieved = nbytes / (ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": how,
-                "traffic": ncu_traffic(kname), "algorithmic_bytes_per_launch": int(nbytes),
-                "launch_ms": round(ms, 4),
-                "per_ray": {k: round(v / max(1, (st_c if dom == "closest" else st_a)["rays"]), 3)
-                            for k, v in (st_c if dom == "closest" else st_a).items() if k != "rays"}}
+    roofline = roofline_entry(kname, nbytes, ms, st_c if dom == "closest" else st_a)
+    roofline_closest = roofline_entry(kern["closest"][2], kern["closest"][1], kern["closest"][0], st_c)
 
     # --------------------------------------------------- end to end through the C ABI, host buffers
     vh = torch.from_numpy(mesh.vertices).pin_memory()
@@ -525,7 +565,8 @@ def run_grt(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(WORKLOAD, rays_per_step=rays_per_step, primary_hits=nhit, l2="flushed between steps",
                            parallelism=f"replicas{world}"),
-            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": roofline, "roofline_closest": roofline_closest, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk,
             "kernel_ms": {"closest": round(statistics.mean(closest_ms), 4), "ao": round(statistics.mean(ao_ms), 4),
                           "blas_build": round(statistics.mean(blas_ms), 4),
                           "tlas_build": round(statistics.mean(tlas_ms), 4)},
@@ -663,18 +704,21 @@ class StepTimer:
         return statistics.mean(self.samples[name])
 
 
-def roofline_entry(kernel, nbytes, ms, bound, stats=None):
+def roofline_entry(kernel, nbytes, ms, stats=None):
     """The roofline object of one kernel: algorithmic bytes per launch over its measured
     duration against the measured HBM copy peak; traffic = ncu DRAM bytes per launch of
     the kernel's current sources (else null)."""
     peaks, how = measured_peaks()
     achieved = nbytes / (ms / 1e3) / 1e9
     traffic = ncu_traffic(kernel)
+    bound, counters = kernel_bound(kernel, peaks["hbm_gbs"])
     out = {"bound": bound, "kernel": kernel, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": how, "traffic": traffic,
            "algorithmic_bytes_per_launch": int(nbytes), "launch_ms": round(ms, 4)}
     if traffic:
         out["dram_share_of_algorithmic"] = round(traffic / nbytes, 4)
+    if counters:
+        out["ncu_pct"] = counters
     if stats:
         out["per_ray"] = {k: round(v / max(1, stats["rays"]), 3) for k, v in stats.items() if k != "rays"}
     return out
@@ -739,8 +783,7 @@ def run_icosphere(args, rank, world, local):
     grt.grtTraceClosest(ctx.handle, None, geom.handle, rays, n, new_hits(n), None, cnt, sh)
     st = grt.grtGetTraceStatistics(ctx.handle, sh)
     nbytes = n * (RAY_BYTES + HIT_BYTES) + NODE_BYTES * st["nodesVisited"] + TRI_BYTES * st["trianglesTested"]
-    # the 143 KB BVH stays in L1/L2: DRAM carries only the rays and the hit records
-    roofline = roofline_entry("traceKernel<closest, geometry> icosphere-512", nbytes, T.mean("closest"), "l1", st)
+    roofline = roofline_entry("traceKernel<closest, geometry> icosphere-512", nbytes, T.mean("closest"), st)
 
     # end to end: the mesh up from pinned host memory, the hit records back
     vh = torch.from_numpy(mesh.vertices).pin_memory()
@@ -899,8 +942,7 @@ def run_spheres(args, rank, world, local):
     kern = {"closest": ("traceKernel<closest, geometry> spheres-1m", st_c),
             "any": ("traceKernel<any, geometry> spheres-1m", st_a)}
     dom = max(kern, key=lambda k: T.mean(k))
-    # 64 MB of nodes and 16 MB of spheres fit the 126 MB L2 next to the streamed rays
-    roofline = roofline_entry(kern[dom][0], nbytes(kern[dom][1]), T.mean(dom), "l2", kern[dom][1])
+    roofline = roofline_entry(kern[dom][0], nbytes(kern[dom][1]), T.mean(dom), kern[dom][1])
     prims = SPHERES["spheres"]
 
     # end to end: spheres and boxes up from pinned host memory, both hit buffers back

@@ -208,8 +208,11 @@ grtError grtDestroyScene(grtContext ctx, grtScene scene);
 
 /* ---------------------------------------------------------------- custom intersection (Sec. 7.4) */
 typedef enum grtIntersectFunc {
-    GRT_INTERSECT_NONE = 0,  /* custom primitives of this (geomType, rayType) are never hit */
-    GRT_INTERSECT_SPHERE = 1 /* built-in: data = float4 {centre.xyz, radius} per primitive */
+    GRT_INTERSECT_NONE = 0,    /* custom primitives of this (geomType, rayType) are never hit */
+    GRT_INTERSECT_SPHERE = 1,  /* built-in: data = float4 {centre.xyz, radius} per primitive */
+    GRT_INTERSECT_USER = 0x100 /* this and higher IDs: user intersection code (Sec. 7.4), run only by
+                                  kernels that trace through grt_device.cuh with a functor, which
+                                  gets the ID; traces of libgrt.so reject a table naming one */
 } grtIntersectFunc;
 
 /* Intersection filters (Sec. 7.6): called on every hit the intersector (or the
@@ -217,8 +220,10 @@ typedef enum grtIntersectFunc {
  * filter rejects is skipped and traversal goes on, as for alpha masking. */
 typedef enum grtFilterFunc {
     GRT_FILTER_NONE = 0,          /* every hit stands */
-    GRT_FILTER_PRIMITIVE_MASK = 1 /* built-in: data = uint32 bit array over primitive IDs; a hit on
-                                     primitive p stands only when bit p (word p / 32, bit p % 32) is set */
+    GRT_FILTER_PRIMITIVE_MASK = 1, /* built-in: data = uint32 bit array over primitive IDs; a hit on
+                                      primitive p stands only when bit p (word p / 32, bit p % 32) is set */
+    GRT_FILTER_USER = 0x100        /* this and higher IDs: user filter code (Sec. 7.6), as for
+                                      GRT_INTERSECT_USER */
 } grtFilterFunc;
 
 typedef struct grtFuncDataSet {

@@ -16,6 +16,26 @@
  * GRT_ERROR_STACK_OVERFLOW in the context's error word. The records follow grtHit:
  * a miss has primID = instanceID = 0xFFFFFFFF and t = +inf.
  *
+ * User intersection and filter code (Sec. 7.4, 7.6) is a functor passed to these
+ * calls (after the ray mask), with members
+ *
+ *   __device__ bool intersect(uint32_t func, const grtRay& ray, const void* data, void* payload,
+ *                             grtHit& hit) const;
+ *   __device__ bool filter(uint32_t func, const grtRay& ray, const void* data, void* payload,
+ *                          const grtHit& hit) const;
+ *
+ * intersect is called for a custom primitive whose function-table entry names an ID
+ * func >= GRT_INTERSECT_USER: hit.primID and hit.instanceID are set, data is the
+ * entry's intersectFuncData, payload is what the caller passed. It returns true and
+ * sets hit.t (and u, v) for an intersection in [ray.minT, ray.maxT]. The ray is in the
+ * primitive's object space, with t measured along it as given (its origin may be
+ * moved along the line; the library converts t back). filter is called for every hit
+ * (triangles, built-in and user primitives) whose entry names a filter ID >=
+ * GRT_FILTER_USER, with hit.t on the same ray; returning false rejects the hit and
+ * traversal goes on. User functions get no FP64 fallback and their hits no FP64
+ * refinement: their float32 arithmetic is the user's. The functor is inlined into the
+ * traversal (no relocatable device code, no function pointers).
+ *
  * The traversal code is compiled into the user's kernel: compile with
  *   nvcc -gencode arch=compute_103a,code=sm_103a -I <repo>/include -I <package>/csrc
  * (the package's csrc directory holds traverse.cuh). No device symbol of libgrt.so is
@@ -54,14 +74,15 @@ __device__ __forceinline__ grt::TraceParams params(const grtDeviceTarget& T, uin
     return P;
 }
 
-template <bool ANY, int DEPTH>
+template <bool ANY, int DEPTH, class Fn>
 __device__ __forceinline__ grtHit trace(const grtDeviceTarget& T, float3 o, float3 d, float tmin, float tmax,
-                                        uint32_t rayMask) {
+                                        uint32_t rayMask, const Fn* fn, void* payload) {
     const grt::TraceParams P = params(T, rayMask);
     uint32_t entries[DEPTH];
     grt::Stack st{nullptr, entries, 0u, (uint32_t)DEPTH, 1u, 0u};
-    grt::Hit h = T.primType == grt::kPrimScene ? grt::traceRay<ANY, true>(P, st, o, d, tmin, tmax)
-                                               : grt::traceRay<ANY, false>(P, st, o, d, tmin, tmax);
+    grt::Hit h = T.primType == grt::kPrimScene
+                     ? grt::traceRay<ANY, true, false, Fn>(P, st, o, d, tmin, tmax, nullptr, fn, payload)
+                     : grt::traceRay<ANY, false, false, Fn>(P, st, o, d, tmin, tmax, nullptr, fn, payload);
     if (!ANY) grt::refineOne(P, o, d, tmin, tmax, h);
     grtHit r;
     r.instanceID = h.inst;
@@ -74,19 +95,25 @@ __device__ __forceinline__ grtHit trace(const grtDeviceTarget& T, float3 o, floa
 
 }  // namespace detail
 
+// The functor type of calls without user functions.
+using NoCustom = grt::NoUser;
+
 // Closest hit of the ray o + t d, t in [tmin, tmax]. rayMask: instances whose mask
-// shares no bit with it are skipped (0 = all bits set).
-template <int DEPTH = 64>
+// shares no bit with it are skipped (0 = all bits set). fn: user intersection / filter
+// code (see above), payload: handed to it.
+template <int DEPTH = 64, class Fn = NoCustom>
 __device__ __forceinline__ grtHit traceClosest(const grtDeviceTarget& T, float3 o, float3 d, float tmin, float tmax,
-                                               uint32_t rayMask = 0xFFFFFFFFu) {
-    return detail::trace<false, DEPTH>(T, o, d, tmin, tmax, rayMask);
+                                               uint32_t rayMask = 0xFFFFFFFFu, const Fn& fn = Fn{},
+                                               void* payload = nullptr) {
+    return detail::trace<false, DEPTH, Fn>(T, o, d, tmin, tmax, rayMask, &fn, payload);
 }
 
 // Some hit of the ray in [tmin, tmax] (the first found), or a miss.
-template <int DEPTH = 64>
+template <int DEPTH = 64, class Fn = NoCustom>
 __device__ __forceinline__ grtHit traceAnyHit(const grtDeviceTarget& T, float3 o, float3 d, float tmin, float tmax,
-                                              uint32_t rayMask = 0xFFFFFFFFu) {
-    return detail::trace<true, DEPTH>(T, o, d, tmin, tmax, rayMask);
+                                              uint32_t rayMask = 0xFFFFFFFFu, const Fn& fn = Fn{},
+                                              void* payload = nullptr) {
+    return detail::trace<true, DEPTH, Fn>(T, o, d, tmin, tmax, rayMask, &fn, payload);
 }
 
 // Every hit of one ray (Sec. 7.5's all-hits use of the any-hit traversal object):
@@ -96,13 +123,16 @@ __device__ __forceinline__ grtHit traceAnyHit(const grtDeviceTarget& T, float3 o
 // traversal order (not sorted by t), with t, u, v recomputed in FP64; then a miss
 // record. done() tells whether the walk is over (the paper's getCurrentState()). The
 // object holds its own stack of DEPTH entries: construct it where it is used; do not
-// copy it.
-template <int DEPTH = 64>
+// copy it. With user functions: AllHits<DEPTH, Fn> w(target, o, d, tmin, tmax, mask, fn,
+// payload) (the object keeps a copy of fn).
+template <int DEPTH = 64, class Fn = NoCustom>
 class AllHits {
   public:
     __device__ AllHits(const grtDeviceTarget& T, float3 o, float3 d, float tmin, float tmax,
-                       uint32_t rayMask = 0xFFFFFFFFu)
-        : P_(detail::params(T, rayMask)) {
+                       uint32_t rayMask = 0xFFFFFFFFu, const Fn& fn = Fn{}, void* payload = nullptr)
+        : P_(detail::params(T, rayMask)), fn_(fn) {
+        walk_.user = &fn_;
+        walk_.payload = payload;
         walk_.begin(P_, o, d, tmin, tmax);
     }
     AllHits(const AllHits&) = delete;
@@ -121,7 +151,8 @@ class AllHits {
 
   private:
     grt::TraceParams P_;
-    grt::AllHitsWalk<DEPTH> walk_;
+    Fn fn_;
+    grt::AllHitsWalk<DEPTH, Fn> walk_;
 };
 
 }  // namespace grt_device

@@ -60,6 +60,9 @@ def lib() -> ctypes.CDLL:
             L.oracle_scene_free.argtypes = [P]
             L.oracle_scene_add_mesh.argtypes = [P, P, i64, P, i64]
             L.oracle_scene_add_spheres.argtypes = [P, P, i64]
+            L.oracle_scene_add_discs.argtypes = [P, P, i64]
+            L.oracle_min_disc_margin.argtypes = [P, P]
+            L.oracle_min_disc_margin.restype = ctypes.c_double
             L.oracle_scene_add_instance.argtypes = [P, ctypes.c_int, P]
             L.oracle_scene_build.argtypes = [P]
             L.oracle_trace.argtypes = [P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, P, P, P,
@@ -318,6 +321,13 @@ class Scene:
         s = _c(spheres, np.float32).reshape(-1, 4)
         return int(self._L.oracle_scene_add_spheres(self._h, _p(s), s.shape[0]))
 
+    def add_discs(self, discs) -> int:
+        """Discs as float32 (n, 8): centre xyz, radius, normal xyz, unused (a custom
+        primitive; the oracle normalises the normal in FP64)."""
+        d = _c(discs, np.float32).reshape(-1, 8)
+        self._keep.append(d)
+        return self._L.oracle_scene_add_discs(self._h, _p(d), d.shape[0])
+
     def add_instance(self, geom: int, frame=None):
         if frame is None:
             self._L.oracle_scene_add_instance(self._h, geom, None)
@@ -395,6 +405,10 @@ class Scene:
     def min_edge_margin(self, ray) -> float:
         r = _c(ray, np.float32).reshape(8)
         return float(self._L.oracle_min_edge_margin(self._h, _p(r)))
+
+    def min_disc_margin(self, ray) -> float:
+        r = _c(ray, np.float32).reshape(8)
+        return float(self._L.oracle_min_disc_margin(self._h, _p(r)))
 
     def min_sphere_margin(self, ray) -> float:
         r = _c(ray, np.float32).reshape(8)

@@ -109,6 +109,21 @@ bool sphere(const RayD& r, V3 c, double rad, double& t) {
     return false;
 }
 
+// Disc (a custom primitive): centre c, unit normal n, radius rad. The ray meets the
+// disc's plane at t = ((c - o) . n) / (d . n) and hits the disc when that point lies
+// within rad of c (the rim included) and t is in range; a ray parallel to the plane
+// misses.
+bool disc(const RayD& r, V3 c, V3 n, double rad, double& t) {
+    const double den = dot(r.d, n);
+    if (den == 0.0) return false;
+    const double th = dot(c - r.o, n) / den;
+    if (!(th >= r.tmin && th <= r.tmax)) return false;
+    const V3 q = (r.o + r.d * th) - c;
+    if (dot(q, q) > rad * rad) return false;
+    t = th;
+    return true;
+}
+
 struct Box {
     V3 lo{INFINITY, INFINITY, INFINITY}, hi{-INFINITY, -INFINITY, -INFINITY};
     void grow(V3 p) {
@@ -147,9 +162,9 @@ bool box_hit(const Box& b, const RayD& r, double tmax) {
 }
 
 struct Geom {
-    int kind = 0;  // 0 triangles, 1 spheres
+    int kind = 0;  // 0 triangles, 1 spheres, 2 discs
     std::vector<V3> a, b, c;  // triangle vertices (object space)
-    std::vector<V3> centre;
+    std::vector<V3> centre, normal;
     std::vector<double> radius;
     size_t count() const { return kind == 0 ? a.size() : centre.size(); }
     Box prim_box(size_t i) const {
@@ -158,10 +173,18 @@ struct Geom {
             bx.grow(a[i]);
             bx.grow(b[i]);
             bx.grow(c[i]);
-        } else {
+        } else if (kind == 1) {
             const double r = radius[i];
             bx.grow(centre[i] - v3(r, r, r));
             bx.grow(centre[i] + v3(r, r, r));
+        } else {
+            // the disc spans rad * sqrt(1 - n_a^2) along axis a
+            const double r = radius[i];
+            const V3 n = normal[i];
+            const V3 e = v3(r * std::sqrt(std::max(0.0, 1.0 - n.x * n.x)), r * std::sqrt(std::max(0.0, 1.0 - n.y * n.y)),
+                            r * std::sqrt(std::max(0.0, 1.0 - n.z * n.z)));
+            bx.grow(centre[i] - e);
+            bx.grow(centre[i] + e);
         }
         return bx;
     }
@@ -173,6 +196,7 @@ struct Geom {
         if (!accepts(i)) return false;
         if (kind == 0) return mt(r, a[i], b[i], c[i], t, u, v);
         u = v = 0.0;
+        if (kind == 2) return disc(r, centre[i], normal[i], radius[i], t);
         return sphere(r, centre[i], radius[i], t);
     }
     // FP64 median-split BVH: nodes hold a box and either two children or a prim range.
@@ -406,6 +430,27 @@ int oracle_scene_add_mesh(void* s, const float* verts, int64_t nv, const uint32_
         g.c[(size_t)i] = V(t[2]);
     }
     (void)nv;
+    S->geoms.push_back(std::move(g));
+    S->built = false;
+    return (int)S->geoms.size() - 1;
+}
+
+// Adds discs given as 8 floats each: centre xyz, radius, normal xyz (normalised here in
+// FP64), unused.
+int oracle_scene_add_discs(void* s, const float* d, int64_t n) {
+    Scene* S = (Scene*)s;
+    Geom g;
+    g.kind = 2;
+    g.centre.resize((size_t)n);
+    g.normal.resize((size_t)n);
+    g.radius.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const float* e = d + 8 * i;
+        g.centre[(size_t)i] = v3(e[0], e[1], e[2]);
+        g.radius[(size_t)i] = e[3];
+        const V3 nn = v3(e[4], e[5], e[6]);
+        g.normal[(size_t)i] = nn * (1.0 / std::sqrt(dot(nn, nn)));
+    }
     S->geoms.push_back(std::move(g));
     S->built = false;
     return (int)S->geoms.size() - 1;
@@ -670,6 +715,33 @@ double oracle_min_sphere_margin(void* s, const float* ray) {
             const V3 l = f - r.d * along;
             const double r2 = g.radius[p] * g.radius[p];
             best = std::min(best, std::fabs(r2 - dot(l, l)) / (dot(f, f) + r2));
+        }
+    }
+    return best;
+}
+
+// Smallest relative rim gap | |p - c|^2 / rad^2 - 1 | over every disc whose plane the ray
+// meets at a t in [minT, maxT] (p that plane point), +inf if none; near 0 marks a ray
+// grazing a disc's rim. A ray within 1e-9 of parallel to a disc's plane counts as 0.
+double oracle_min_disc_margin(void* s, const float* ray) {
+    Scene* S = (Scene*)s;
+    const RayD w = load_ray(ray);
+    double best = INFINITY;
+    for (const Instance& I : S->inst) {
+        const Geom& g = S->geoms[(size_t)I.geom];
+        if (g.kind != 2) continue;
+        RayD r{I.inv.point(w.o), I.inv.vector(w.d), w.tmin, w.tmax};
+        const double dl = std::sqrt(dot(r.d, r.d));
+        for (size_t p = 0; p < g.count(); ++p) {
+            const double den = dot(r.d, g.normal[p]);
+            if (std::fabs(den) <= 1e-9 * dl) {
+                best = 0.0;
+                continue;
+            }
+            const double th = dot(g.centre[p] - r.o, g.normal[p]) / den;
+            if (!(th >= r.tmin && th <= r.tmax)) continue;
+            const V3 q = (r.o + r.d * th) - g.centre[p];
+            best = std::min(best, std::fabs(dot(q, q) / (g.radius[p] * g.radius[p]) - 1.0));
         }
     }
     return best;

@@ -38,8 +38,10 @@ GRT_BUILD_PREFER_HIGH_QUALITY = 2  # PLOC clustering, search radius 32
 GRT_INSTANCE_GEOMETRY = 0
 GRT_INTERSECT_NONE = 0
 GRT_INTERSECT_SPHERE = 1
+GRT_INTERSECT_USER = 0x100  # and above: user code, run only through grt_device.cuh functors
 GRT_FILTER_NONE = 0
 GRT_FILTER_PRIMITIVE_MASK = 1
+GRT_FILTER_USER = 0x100
 GRT_INVALID_ID = 0xFFFFFFFF
 GRT_LOG_NONE, GRT_LOG_ERROR, GRT_LOG_WARN, GRT_LOG_INFO = 0, 1, 2, 4
 

@@ -204,6 +204,7 @@ grtError grtCreateFuncTable(grtContext ctx, uint32_t numGeomTypes, uint32_t numR
     FuncTableObject* t = new FuncTableObject();
     t->numGeomTypes = numGeomTypes;
     t->numRayTypes = numRayTypes;
+    t->userEntry.assign((size_t)numGeomTypes * numRayTypes, 0);
     const size_t bytes = sizeof(FuncEntry) * numGeomTypes * numRayTypes;
     cudaError_t e = cudaMalloc(&t->dEntries, bytes);
     if (e == cudaSuccess) e = cudaMemset(t->dEntries, 0, bytes);
@@ -222,13 +223,20 @@ grtError grtCreateFuncTable(grtContext ctx, uint32_t numGeomTypes, uint32_t numR
 grtError grtSetFuncTable(grtContext ctx, grtFuncTable table, uint32_t geomType, uint32_t rayType, grtFuncDataSet set) {
     FuncTableObject* t = findFuncTable(table);
     if (!ctx || !t || geomType >= t->numGeomTypes || rayType >= t->numRayTypes) return GRT_ERROR_INVALID_PARAMETER;
-    if (set.intersectFunc > GRT_INTERSECT_SPHERE || set.filterFunc > GRT_FILTER_PRIMITIVE_MASK)
+    const bool userFunc = set.intersectFunc >= GRT_INTERSECT_USER, userFilter = set.filterFunc >= GRT_FILTER_USER;
+    if ((set.intersectFunc > GRT_INTERSECT_SPHERE && !userFunc) ||
+        (set.filterFunc > GRT_FILTER_PRIMITIVE_MASK && !userFilter))
         return GRT_ERROR_INVALID_PARAMETER;
-    if (set.filterFunc != GRT_FILTER_NONE && !set.filterFuncData) return GRT_ERROR_INVALID_PARAMETER;
+    if (set.filterFunc == GRT_FILTER_PRIMITIVE_MASK && !set.filterFuncData) return GRT_ERROR_INVALID_PARAMETER;
     FuncEntry e{set.intersectFunc, set.filterFunc, set.intersectFuncData, set.filterFuncData};
+    const size_t slot = (size_t)rayType * t->numGeomTypes + geomType;
     // Synchronous copy: the table may be used by work enqueued afterwards on any stream.
-    GRT_CUDA(cudaMemcpy(t->dEntries + (size_t)rayType * t->numGeomTypes + geomType, &e, sizeof(e),
-                        cudaMemcpyHostToDevice));
+    GRT_CUDA(cudaMemcpy(t->dEntries + slot, &e, sizeof(e), cudaMemcpyHostToDevice));
+    std::lock_guard<std::mutex> g(g_mutex);
+    const uint8_t user = (userFunc || userFilter) ? 1 : 0;
+    t->userEntries += user;
+    t->userEntries -= t->userEntry[slot];
+    t->userEntry[slot] = user;
     return GRT_SUCCESS;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <vector>
 
 #include "../../include/grt.h"
 
@@ -137,6 +138,8 @@ struct FuncTableObject {
     FuncEntry* dEntries;
     uint32_t numGeomTypes;
     uint32_t numRayTypes;
+    std::vector<uint8_t> userEntry;  // per entry: names a user intersector or filter
+    uint32_t userEntries = 0;        // how many do (libgrt.so's own traces reject such a table)
 };
 FuncTableObject* findFuncTable(grtFuncTable t);
 

@@ -537,6 +537,10 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     if (table) {
         FuncTableObject* t = findFuncTable(table);
         if (!t) return GRT_ERROR_INVALID_PARAMETER;
+        if (t->userEntries) {  // user code runs only in kernels that trace through grt_device.cuh
+            logf(GRT_LOG_ERROR, "the function table names user functions; trace through grt_device.cuh");
+            return GRT_ERROR_INVALID_PARAMETER;
+        }
         P.table = t->dEntries;
         P.numGeomTypes = t->numGeomTypes;
         P.rayType = opt ? opt->rayType : 0u;

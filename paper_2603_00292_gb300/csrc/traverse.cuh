@@ -22,6 +22,8 @@
 // FP64 runs far slower than FP32 on this GPU, so it is confined to these rare cases.
 #pragma once
 
+#include <type_traits>
+
 #include "grt_internal.cuh"
 
 namespace grt {
@@ -84,6 +86,16 @@ struct Hit {
     uint32_t inst, prim;
     float t, u, v;
 };
+
+// No user functions: the library's own kernels trace with this (the user branches
+// compile away). A user kernel tracing through grt_device.cuh may pass a functor U with
+//   bool intersect(uint32_t func, const grtRay& ray, const void* data, void* payload, grtHit& hit) const
+//   bool filter(uint32_t func, const grtRay& ray, const void* data, void* payload, const grtHit& hit) const
+// called for table entries naming user intersectors (func >= GRT_INTERSECT_USER) and
+// user filters (>= GRT_FILTER_USER); see grt_device.cuh.
+struct NoUser {};
+template <class U>
+constexpr bool kHasUser = !std::is_same<U, NoUser>::value;
 
 __device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -556,8 +568,20 @@ __device__ __forceinline__ bool enterInstance(const TraceParams& P, Stack& st, R
 
 // Tests leaf k of the current level against the ray (closest hit: only nearer than
 // the best so far). Returns true when it is a hit; s.best then holds it.
-template <bool ANY, bool SCENE, bool COUNT>
-__device__ __forceinline__ bool testLeaf(const TraceParams& P, RayState& s, uint32_t k, Visits* vis) {
+// The ray of level L as a grtRay over world parameters [a, b]: origin at world
+// parameter L.tOff, so that t on it is the world parameter minus L.tOff.
+__device__ __forceinline__ grtRay levelRay(const Level& L, float a, float b) {
+    grtRay r;
+    r.origin[0] = L.o.x, r.origin[1] = L.o.y, r.origin[2] = L.o.z;
+    r.direction[0] = L.d.x, r.direction[1] = L.d.y, r.direction[2] = L.d.z;
+    r.minT = a - L.tOff;
+    r.maxT = b - L.tOff;
+    return r;
+}
+
+template <bool ANY, bool SCENE, bool COUNT, class U = NoUser>
+__device__ __forceinline__ bool testLeaf(const TraceParams& P, RayState& s, uint32_t k, Visits* vis,
+                                         const U* user = nullptr, void* payload = nullptr) {
     const bool strict = s.found && !ANY;
     const float cur = (ANY || !s.found) ? s.tmax : s.best.t;
     float t = 0.f, u = 0.f, v = 0.f;
@@ -595,6 +619,16 @@ __device__ __forceinline__ bool testLeaf(const TraceParams& P, RayState& s, uint
                     res = r.w != 0.f ? 1 : 0;
                     t = r.x, u = r.y, v = r.z;
                 }
+            } else if constexpr (kHasUser<U>) {
+                if (fe.func >= GRT_INTERSECT_USER) {  // user code (Sec. 7.4): its t is on the level's ray
+                    if (COUNT) ++vis->customs;
+                    grtHit h;
+                    h.instanceID = s.instId, h.primID = prim, h.t = INFINITY, h.u = 0.f, h.v = 0.f;
+                    if (user->intersect(fe.func, levelRay(s.L, s.tmin, cur), fe.data, payload, h)) {
+                        const float tw = h.t + s.L.tOff;
+                        if (tw >= s.tmin && (strict ? tw < cur : tw <= cur)) res = 1, t = tw, u = h.u, v = h.v;
+                    }
+                }
             }
         }
     }
@@ -603,6 +637,12 @@ __device__ __forceinline__ bool testLeaf(const TraceParams& P, RayState& s, uint
         if (fe->filter == GRT_FILTER_PRIMITIVE_MASK) {
             const uint32_t* bits = static_cast<const uint32_t*>(fe->filterData);
             if (!((__ldg(bits + (prim >> 5)) >> (prim & 31u)) & 1u)) res = 0;
+        } else if constexpr (kHasUser<U>) {
+            if (fe->filter >= GRT_FILTER_USER) {
+                grtHit h;
+                h.instanceID = s.instId, h.primID = prim, h.t = t - s.L.tOff, h.u = u, h.v = v;
+                if (!user->filter(fe->filter, levelRay(s.L, s.tmin, cur), fe->filterData, payload, h)) res = 0;
+            }
         }
     }
     if (res == 1) {
@@ -659,8 +699,9 @@ __device__ __forceinline__ void orderChildren(const TraceParams& P, Stack& st, R
 
 // One traversal step: a node visit (with its leaf tests), an instance entry or an
 // instance exit. Returns true once the ray is finished (s.best is then final).
-template <bool ANY, bool SCENE, bool COUNT>
-__device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayState& s, Visits* vis) {
+template <bool ANY, bool SCENE, bool COUNT, class U = NoUser>
+__device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayState& s, Visits* vis,
+                                        const U* user = nullptr, void* payload = nullptr) {
     if (s.next == kNone) {
         if (st.sp == 0) return true;  // closest hits are refined in FP64 afterwards (refineKernel)
         s.next = st.pop();
@@ -694,7 +735,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
         for (int j = 0; j < 4; ++j) {
             if (!((m >> j) & 1u) || !(c[j] & kLeafBit)) continue;
             m &= ~(1u << j);
-            if (testLeaf<ANY, SCENE, COUNT>(P, s, c[j] & ~kLeafBit, vis) && ANY) return true;
+            if (testLeaf<ANY, SCENE, COUNT, U>(P, s, c[j] & ~kLeafBit, vis, user, payload) && ANY) return true;
         }
     }
     orderChildren(P, st, s, m, tn, c);
@@ -707,8 +748,9 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
 // (at most four per visit), or an instance entry or exit. Returns the number of hits
 // appended, or -1 once the walk is over. Each primitive of each instance sits in one
 // leaf, so each (instance, primitive) is reported at most once.
-template <bool SCENE>
-__device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState& s, Hit* found) {
+template <bool SCENE, class U = NoUser>
+__device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState& s, Hit* found,
+                                       const U* user = nullptr, void* payload = nullptr) {
     if (s.next == kNone) {
         if (st.sp == 0) return -1;
         s.next = st.pop();
@@ -743,7 +785,8 @@ __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState
         for (int j = 0; j < 4; ++j) {
             if (!((m >> j) & 1u) || !(c[j] & kLeafBit)) continue;
             m &= ~(1u << j);
-            if (testLeaf<true, SCENE, false>(P, s, c[j] & ~kLeafBit, nullptr)) found[added++] = s.best;
+            if (testLeaf<true, SCENE, false, U>(P, s, c[j] & ~kLeafBit, nullptr, user, payload))
+                found[added++] = s.best;
         }
     }
     orderChildren(P, st, s, m, tn, c);
@@ -752,12 +795,12 @@ __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState
 
 // One ray through the target, all steps in a row. Returns the hit (prim == kInvalid
 // on a miss).
-template <bool ANY, bool SCENE, bool COUNT = false>
+template <bool ANY, bool SCENE, bool COUNT = false, class U = NoUser>
 __device__ Hit traceRay(const TraceParams& P, Stack& st, float3 wo, float3 wd, float tmin, float tmax,
-                        Visits* vis = nullptr) {
+                        Visits* vis = nullptr, const U* user = nullptr, void* payload = nullptr) {
     RayState s;
     beginRay<SCENE>(P, st, s, wo, wd, tmin, tmax);
-    while (!stepRay<ANY, SCENE, COUNT>(P, st, s, vis)) {
+    while (!stepRay<ANY, SCENE, COUNT, U>(P, st, s, vis, user, payload)) {
     }
     return s.best;
 }
@@ -1099,7 +1142,7 @@ __device__ __forceinline__ void refineOne(const TraceParams& P, float3 wo, float
 // returns the ray's hits one at a time, in traversal order, each with t, u, v recomputed
 // in FP64, then a record with prim == kInvalid. The stack points into the object, so
 // an AllHitsWalk is used where it was begun and never copied.
-template <int DEPTH>
+template <int DEPTH, class U = NoUser>
 struct AllHitsWalk {
     RayState s;
     uint32_t entries[DEPTH];
@@ -1109,6 +1152,8 @@ struct AllHitsWalk {
     bool scene, finished;
     float3 o, d;
     float tmin, tmax;
+    const U* user = nullptr;
+    void* payload = nullptr;
 
     __device__ void begin(const TraceParams& P, float3 o_, float3 d_, float tmin_, float tmax_) {
         o = o_, d = d_, tmin = tmin_, tmax = tmax_;
@@ -1123,7 +1168,8 @@ struct AllHitsWalk {
     }
     __device__ Hit next(const TraceParams& P) {
         while (i == n && !finished) {
-            const int r = scene ? stepAll<true>(P, st, s, buf) : stepAll<false>(P, st, s, buf);
+            const int r = scene ? stepAll<true, U>(P, st, s, buf, user, payload)
+                                : stepAll<false, U>(P, st, s, buf, user, payload);
             if (r < 0)
                 finished = true;
             else

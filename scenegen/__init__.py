@@ -320,6 +320,23 @@ def look_down_z_camera(eye, width: int, height: int, vfov_deg: float = 60.0) -> 
                   np.array([0, th, 0], dtype=np.float32), width, height)
 
 
+def look_at_camera(eye, target, width: int, height: int, vfov_deg: float = 60.0, world_up=(0.0, 1.0, 0.0)) -> Camera:
+    """Camera at `eye` looking at `target` with the given vertical field of view: right
+    and up span the film at distance 1 (their cross product up x right points along the
+    view direction, the pinhole model's forward)."""
+    eye = np.asarray(eye, dtype=np.float64)
+    f = np.asarray(target, dtype=np.float64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.asarray(world_up, dtype=np.float64))
+    if np.linalg.norm(r) < 1e-6:  # looking along the world up: any perpendicular right
+        r = np.cross(f, [1.0, 0.0, 0.0])
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    th = math.tan(math.radians(vfov_deg) * 0.5)
+    return Camera(eye.astype(np.float32), (r * (width / height) * th).astype(np.float32),
+                  (u * th).astype(np.float32), width, height)
+
+
 # ----------------------------------------------------------------------------------
 # Workloads
 # ----------------------------------------------------------------------------------
@@ -353,6 +370,13 @@ def terrain_instances(num_instances: int = 64, cells: int = 256, amplitude: floa
 def overview_camera(scene: InstancedScene, width: int, height: int) -> Camera:
     """Camera at scene centre + (0,0,1.5*extent), looking at the centre, 60 deg vertical."""
     eye = scene.centre + np.array([0.0, 0.0, 1.5 * scene.extent])
+    return look_down_z_camera(eye, width, height)
+
+
+def close_camera(scene: InstancedScene, width: int, height: int, distance: float = 0.35) -> Camera:
+    """The overview camera moved to scene centre + (0,0,distance*extent): at 0.35 about
+    56% of a 1920x1080 image hits the 64-terrain scene (5.8% from 1.5 extent)."""
+    eye = scene.centre + np.array([0.0, 0.0, distance * scene.extent])
     return look_down_z_camera(eye, width, height)
 
 

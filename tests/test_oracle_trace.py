@@ -574,3 +574,70 @@ def test_uniform_rays_distribution():
     assert np.all(r[:, 3] == 0.0) and np.all(r[:, 7] == 4.0)
     assert np.array_equal(r, oracle.uniform_rays(lo, hi, 99, n, 0.0, 4.0))
     assert not np.array_equal(r[:100], oracle.uniform_rays(lo, hi, 100, 100, 0.0, 4.0))
+
+
+# ---------------------------------------------------------------- discs (a custom primitive for user code)
+def _disc_rows(c, r, n):
+    d = np.zeros((len(c), 8), np.float32)
+    d[:, 0:3], d[:, 3], d[:, 4:7] = c, r, n
+    return d
+
+
+def test_disc_closed_forms():
+    """The unit disc at the origin facing +z, hit straight down from (x, y, 5): t = 5 iff
+    x^2 + y^2 <= 1 (rim included); a tilted disc (normal (0, 0.6, 0.8), radius 0.5) hit
+    along its normal through points 0.49 and 0.51 from its centre; parallel rays and
+    planes behind the origin miss; the rim margin is 0 on the rim, 1 at the centre; a
+    uniform scale 2 doubles the world radius."""
+    S = oracle.Scene()
+    S.add_instance(S.add_discs(_disc_rows([[0, 0, 0]], [1.0], [[0, 0, 1]])))
+    def down(x, y, tmax=np.inf):
+        r = np.zeros((1, 8), np.float32)
+        r[0, 0:3], r[0, 4:7], r[0, 7] = (x, y, 5), (0, 0, -1), tmax
+        return r
+    for x, y, hit in ((0.0, 0.0, True), (0.0, 1.0, True), (0.6, 0.81, False), (-1.0, 0.0, True), (0.9, 0.5, False)):
+        h = S.trace(down(x, y), bvh=False)
+        assert (h.prim[0] != NONE) == hit, (x, y)
+        if hit:
+            assert h.t[0] == 5.0 and h.u[0] == 0.0 and h.v[0] == 0.0
+    assert S.trace(down(0, 0, tmax=4.5), bvh=False).prim[0] == NONE
+    assert S.min_disc_margin(down(0.0, 1.0)[0]) == 0.0 and S.min_disc_margin(down(0, 0)[0]) == 1.0
+    side = np.zeros((1, 8), np.float32)
+    side[0, 0:3], side[0, 4:7], side[0, 7] = (-3, 0, 0), (1, 0, 0), np.inf
+    assert S.trace(side, bvh=False).prim[0] == NONE and S.min_disc_margin(side[0]) == 0.0
+    up = down(0, 0)
+    up[0, 6] = 1.0  # pointing away from the plane
+    assert S.trace(up, bvh=False).prim[0] == NONE
+    c, n = np.array([1.0, 2.0, 3.0]), np.array([0.0, 0.6, 0.8])
+    T = oracle.Scene()
+    T.add_instance(T.add_discs(_disc_rows([c], [0.5], [n])))
+    inplane = np.array([1.0, 0.0, 0.0])
+    for off, hit in ((0.49, True), (0.51, False)):
+        r = np.zeros((1, 8), np.float32)
+        r[0, 0:3], r[0, 4:7], r[0, 7] = c + off * inplane + 3 * n, -n, np.inf
+        h = T.trace(r, bvh=False)
+        assert (h.prim[0] != NONE) == hit
+        if hit:
+            assert abs(h.t[0] - 3.0) < 1e-6
+    U = oracle.Scene()
+    U.add_instance(U.add_discs(_disc_rows([[0, 0, 0]], [1.0], [[0, 0, 1]])), [0, 0, 0, 1, 2, 2, 2, 0, 0, 0])
+    assert U.trace(down(1.9, 0.0), bvh=False).prim[0] == 0 and U.trace(down(2.1, 0.0), bvh=False).prim[0] == NONE
+
+
+def test_disc_bvh_equals_brute_force():
+    """Random discs of random orientation: the oracle BVH (disc boxes c +- r sqrt(1 - n_a^2))
+    finds the same closest hits as brute force, for a plain geometry and instances."""
+    rng = np.random.default_rng(5)
+    m = 3000
+    n = rng.normal(size=(m, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    d = _disc_rows(rng.uniform(-5, 5, (m, 3)), rng.uniform(0.05, 0.6, m), n)
+    S = oracle.Scene()
+    g = S.add_discs(d)
+    S.add_instance(g)
+    S.add_instance(g, [0.2, 0.1, 0.3, 0.92, 1.5, 0.7, 1.2, 3, -2, 1])
+    S.build()
+    rays = scenegen.random_rays(20_000, [-6] * 3, [6] * 3, config=97)
+    a, b = S.trace(rays, bvh=True), S.trace(rays, bvh=False)
+    assert (a.prim != NONE).sum() > 5000
+    assert np.array_equal(a.prim, b.prim) and np.array_equal(a.inst, b.inst) and np.array_equal(a.t, b.t)
