@@ -481,12 +481,43 @@ grtError grtShadeLambert(grtContext ctx, grtGeometry geom, const grtRay* rays, c
  * the hit's barycentrics on the fixed primary ray (interior hits: visibility and the
  * hit triangle are piecewise constant and contribute nothing). hits and visibility as
  * stored by the forward pass; hits = NULL recomputes the primary hits (refined in FP64)
- * and the visibility by tracing again, trading time for 21 bytes per pixel. */
+ * and the visibility by tracing again within the call (the closest-hit query and the
+ * forward's visibility pass into context memory held only during the call), trading
+ * about one forward pass for the 21 bytes per pixel kept between the passes. */
 grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay* rays, const grtHit* hits,
                                  const uint8_t* visibility, uint32_t pixelCount, const uint32_t* indices,
                                  const float* positions, const float* colours, const float* light,
                                  const float* gradImage, float* gradColours, float* gradLight, float* gradPositions,
                                  const grtTraceOptions* options, void* stream);
+
+/* Shading of a two-level scene (Sec. 6.2's instances under SRT frames), with shadows
+ * cast by every instance: grtShadeLambert in world space. hits come from grtTraceClosest
+ * on `scene`. The scene's meshes are one object-space mesh: indices (3 uint32 per
+ * triangle, vertex numbers into positions and colours, 3 float32 per vertex), and
+ * instanceTriangleOffset[i] (device, one uint32 per instance ID) is the first triangle
+ * of instance i's geometry in it, so that hit (i, prim) is triangle
+ * instanceTriangleOffset[i] + prim; instances of one geometry share its triangles and
+ * vertices. A triangle's world vertices are its object-space vertices under instance
+ * i's frame (the scene's float32 forward frame); n_f, s, c(u,v) and the image follow
+ * grtShadeLambert; the shadow ray from o + t d + 1e-4 n_f along l is an any-hit query
+ * through the whole scene (every instance occludes). A hit on an instance of custom
+ * primitives is not shaded (image 0). */
+grtError grtShadeLambertScene(grtContext ctx, grtScene scene, const grtRay* rays, const grtHit* hits,
+                              uint32_t pixelCount, const uint32_t* instanceTriangleOffset, const uint32_t* indices,
+                              const float* positions, const float* colours, const float* light, float* image,
+                              uint8_t* visibility, const grtTraceOptions* options, void* stream);
+
+/* Adjoint of grtShadeLambertScene, as grtShadeLambertBackward: ADDS dL/dcolours and
+ * dL/dpositions (object space, 3 per vertex of the shared mesh; world-space derivatives
+ * mapped back through each instance's frame, M^T g) and dL/dlight. vertexCount: the
+ * number of vertices in positions / colours (sizes the block-private accumulation).
+ * hits = NULL traces the primary hits and visibility again within the call. */
+grtError grtShadeLambertSceneBackward(grtContext ctx, grtScene scene, const grtRay* rays, const grtHit* hits,
+                                      const uint8_t* visibility, uint32_t pixelCount,
+                                      const uint32_t* instanceTriangleOffset, const uint32_t* indices,
+                                      const float* positions, uint32_t vertexCount, const float* colours,
+                                      const float* light, const float* gradImage, float* gradColours, float* gradLight,
+                                      float* gradPositions, const grtTraceOptions* options, void* stream);
 
 /* ---------------------------------------------------------------- batched build + trace */
 /* Many independent triangle geometries, each with its own ray batch, built and traced

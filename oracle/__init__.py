@@ -550,6 +550,71 @@ def lambert_gradient_l1(vertices, indices, colours, light, rays, target):
     return ac, al, ap
 
 
+class LambertScene:
+    """Lambert shading of a two-level scene (instances under SRT frames, Sec. 6.2) by the
+    plain oracle in world space. One object-space mesh (vertices, indices); instance i
+    is its triangles [tri_offset[i], tri_offset[i] + tri_count[i]) under frames[i]
+    (quaternion xyzw, scale, translation; the oracle's FP64 frame). The world mesh holds,
+    for each instance, every object vertex mapped by the instance's frame; shading,
+    visibility (every instance occludes) and the analytic gradient are the plain
+    oracle's on it. Gradients come back to object space: colours add up over instances,
+    positions as M_i^T g (M_i the linear part of instance i's frame)."""
+
+    def __init__(self, vertices, indices, tri_offset, tri_count, frames):
+        v = np.asarray(vertices, np.float64).reshape(-1, 3)
+        idx = np.asarray(indices, np.uint32).reshape(-1, 3)
+        self.nv = v.shape[0]
+        S = Scene()
+        g = S.add_mesh(v.astype(np.float32), idx)
+        frames = np.asarray(frames, np.float32).reshape(-1, 10)
+        for f in frames:
+            S.add_instance(g, f)
+        self.fwd = [S.instance_frames(i)[0] for i in range(frames.shape[0])]
+        self.world_vertices = np.concatenate([v @ F[:, :3].T + F[:, 3] for F in self.fwd])
+        tris, inst, prim = [], [], []
+        for i, (off, cnt) in enumerate(zip(tri_offset, tri_count)):
+            tris.append(idx[off:off + cnt].astype(np.int64) + i * self.nv)
+            inst.append(np.full(cnt, i, np.int64))
+            prim.append(np.arange(cnt, dtype=np.int64))
+        self.world_indices = np.concatenate(tris).astype(np.uint32)
+        self.tri_inst = np.concatenate(inst)
+        self.tri_prim = np.concatenate(prim)
+        self.ninst = frames.shape[0]
+
+    def _colours(self, colours):
+        return np.tile(np.asarray(colours, np.float64).reshape(-1, 3), (self.ninst, 1))
+
+    def forward(self, colours, light, rays):
+        """LambertResult with .inst and .iprim (instance and primitive within it, -1 on a
+        miss) added; .prim stays the world-mesh triangle."""
+        R = lambert_forward(self.world_vertices, self.world_indices, self._colours(colours), light, rays)
+        hit = R.prim >= 0
+        R.inst = np.where(hit, self.tri_inst[np.maximum(R.prim, 0)], -1)
+        R.iprim = np.where(hit, self.tri_prim[np.maximum(R.prim, 0)], -1)
+        return R
+
+    def _fold(self, dcw, dpw, absolute=False):
+        dc = sum(dcw[i * self.nv:(i + 1) * self.nv] for i in range(self.ninst))
+        dp = sum(dpw[i * self.nv:(i + 1) * self.nv] @ (np.abs(F[:, :3]) if absolute else F[:, :3])
+                 for i, F in enumerate(self.fwd))
+        return dc, dp
+
+    def gradient(self, colours, light, rays, target):
+        """(loss, dL/dcolours (V,3), dL/dlight (3,), dL/dpositions (V,3), object space)."""
+        loss, dcw, dl, dpw = lambert_gradient(self.world_vertices, self.world_indices, self._colours(colours), light,
+                                              rays, target)
+        dc, dp = self._fold(dcw, dpw)
+        return loss, dc, dl, dp
+
+    def gradient_l1(self, colours, light, rays, target):
+        """Bounds on the L1 norms of the per-pixel terms of gradient(): per instance the
+        world terms' norms mapped by |M_i|^T (a bound on the norm of the mapped terms)."""
+        acw, al, apw = lambert_gradient_l1(self.world_vertices, self.world_indices, self._colours(colours), light,
+                                           rays, target)
+        ac, ap = self._fold(acw, apw, absolute=True)
+        return ac, al, ap
+
+
 def lambert_fd(vertices, indices, colours, light, rays, target, params, h: float = 1e-4, exclude=None,
                return_unstable: bool = False):
     """Central differences (masked loss) for parameter ids: [0,3V) colours, [3V,3V+3) light,

@@ -195,6 +195,9 @@ _SIGS = {
     "grtShadeLambert": [_P, _P, _P, _P, _U32, _P, _P, _P, _P, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
     "grtShadeLambertBackward": [_P, _P, _P, _P, _P, _U32, _P, _P, _P, _P, _P, _P, _P, _P,
                                 ctypes.POINTER(grtTraceOptions), _P],
+    "grtShadeLambertScene": [_P, _P, _P, _P, _U32, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(grtTraceOptions), _P],
+    "grtShadeLambertSceneBackward": [_P, _P, _P, _P, _P, _U32, _P, _P, _P, _U32, _P, _P, _P, _P, _P, _P,
+                                     ctypes.POINTER(grtTraceOptions), _P],
     "grtGetLaunchCount": [ctypes.POINTER(ctypes.c_uint64)],
     "grtGetTraceStatistics": [_P, _P, ctypes.c_void_p],
     "grtSortTemporaryBufferSize": [_U32, _U32, ctypes.POINTER(ctypes.c_size_t)],
@@ -459,6 +462,25 @@ def grtShadeLambertBackward(ctx, geom, rays, hits, visibility, count, indices, p
                                         _ptr(grad_colours), _ptr(grad_light), _ptr(grad_positions),
                                         ctypes.byref(opts) if opts else None, _stream(stream)),
           "grtShadeLambertBackward")
+
+
+def grtShadeLambertScene(ctx, scene, rays, hits, count, tri_offset, indices, positions, colours, light, image,
+                         visibility=None, opts=None, stream=None):
+    """tri_offset: device uint32, the first triangle of each instance ID's geometry in indices."""
+    check(lib().grtShadeLambertScene(ctx, scene, _ptr(rays), _ptr(hits), count, _ptr(tri_offset), _ptr(indices),
+                                     _ptr(positions), _ptr(colours), _ptr(light), _ptr(image), _ptr(visibility),
+                                     ctypes.byref(opts) if opts else None, _stream(stream)), "grtShadeLambertScene")
+
+
+def grtShadeLambertSceneBackward(ctx, scene, rays, hits, visibility, count, tri_offset, indices, positions,
+                                 vertex_count, colours, light, grad_image, grad_colours, grad_light, grad_positions,
+                                 opts=None, stream=None):
+    check(lib().grtShadeLambertSceneBackward(ctx, scene, _ptr(rays), _ptr(hits), _ptr(visibility), count,
+                                             _ptr(tri_offset), _ptr(indices), _ptr(positions), vertex_count,
+                                             _ptr(colours), _ptr(light), _ptr(grad_image), _ptr(grad_colours),
+                                             _ptr(grad_light), _ptr(grad_positions),
+                                             ctypes.byref(opts) if opts else None, _stream(stream)),
+          "grtShadeLambertSceneBackward")
 
 
 def grtGetBvhInfo(ctx, geom=None, scene=None) -> grtBvhInfo:

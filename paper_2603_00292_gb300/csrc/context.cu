@@ -18,6 +18,8 @@ struct Context {
     unsigned nextSlot;
     void* scratch;        // traversal global-stack spill area (grown on demand)
     size_t scratchBytes;
+    void* aux;            // buffers passed between the launches of one call (grown on demand)
+    size_t auxBytes;
     std::mutex lock;
 };
 
@@ -25,6 +27,21 @@ unsigned long long* nextCounter(Context* c) {
     std::lock_guard<std::mutex> g(c->lock);
     const unsigned slot = c->nextSlot++ % kCounterSlots;
     return &c->dWork->counters[slot];
+}
+
+grtError contextAux(Context* c, size_t bytes, void** ptr) {
+    std::lock_guard<std::mutex> g(c->lock);
+    if (bytes > c->auxBytes) {
+        // Growing needs an idle device: the old area may still be in use by queued work.
+        GRT_CUDA(cudaDeviceSynchronize());
+        cudaFree(c->aux);
+        c->aux = nullptr;
+        c->auxBytes = 0;
+        GRT_CUDA(cudaMalloc(&c->aux, bytes));
+        c->auxBytes = bytes;
+    }
+    *ptr = c->aux;
+    return GRT_SUCCESS;
 }
 
 grtError contextScratch(Context* c, size_t bytes, void** ptr) {
@@ -137,6 +154,8 @@ grtError grtCreateContext(uint32_t apiVersion, const grtContextCreationInput* in
     c->nextSlot = 0;
     c->scratch = nullptr;
     c->scratchBytes = 0;
+    c->aux = nullptr;
+    c->auxBytes = 0;
     cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, input->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->dWork, sizeof(DeviceWorkspace));
     if (e == cudaSuccess) e = cudaMemset(c->dWork, 0, sizeof(DeviceWorkspace));
@@ -154,6 +173,7 @@ grtError grtDestroyContext(grtContext ctx) {
     Context* c = asContext(ctx);
     cudaFree(c->dWork);
     cudaFree(c->scratch);
+    cudaFree(c->aux);
     delete c;
     return GRT_SUCCESS;
 }

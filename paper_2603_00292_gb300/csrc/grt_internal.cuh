@@ -101,6 +101,9 @@ DeviceWorkspace* workspace(Context* c);
 unsigned long long* nextCounter(Context* c);  // a zeroed-on-use work counter slot
 // Caller-or-context global stack memory for traversal spills (grown on demand).
 grtError contextScratch(Context* c, size_t bytes, void** ptr);
+// Context memory for buffers one call passes between its own launches (grown on demand;
+// calls on one context must not overlap in time, as for the global stack).
+grtError contextAux(Context* c, size_t bytes, void** ptr);
 int smCount(Context* c);
 int deviceOf(Context* c);
 

@@ -161,6 +161,11 @@ __global__ void aoFinishKernel(const uint32_t* __restrict__ list, const uint32_t
 // 4.1; the Lambert BRDF c/pi of Sec. 5.2 with pi folded into the loss scale); V = 1
 // unless the shadow ray from p + 1e-4 n_f along l (any hit, t in [0, inf)) is blocked;
 // c(u,v) interpolates per-vertex colours; I = V s c(u,v), 0 for a miss.
+//
+// A scene is shaded the same way in world space: triangle (instance, prim) is triangle
+// triOffset[instance] + prim of the object-space mesh (idx, pos, col), its vertices are
+// mapped by the instance's forward frame (float32 rows), and the shadow ray is traced
+// through the whole scene.
 struct ShadeParams {
     const float4* rays;
     const uint32_t* hits;  // 5 words per pixel
@@ -169,7 +174,11 @@ struct ShadeParams {
     const float* pos;      // 3 per vertex
     const float* col;      // 3 per vertex
     const float* light;    // 3
-    float* image;          // 3 per pixel
+    const uint32_t* triOffset;  // scenes: first triangle of each instance ID's mesh
+    const float4* frames;       // scenes: kFrameRows float4 per instance ID (forward frame rows 0-2)
+    const InstanceRecord* sceneLeaves;  // scenes: instance records (to skip custom-primitive instances)
+    const uint32_t* scenePrimToLeaf;
+    float* image;          // 3 per pixel, or null (visibility only)
     uint8_t* vis;          // per pixel, or null
     const float* gimg;     // adjoint: dL/dI, 3 per pixel
     float* gcol;
@@ -178,18 +187,40 @@ struct ShadeParams {
 };
 
 struct ShadeHit {
-    float3 v0, v1, v2, o, d, nf;
+    float3 v0, v1, v2, o, d, nf;  // vertices in world space
     float nl, u, v, t;
     uint32_t i0, i1, i2;
+    float4 m0, m1, m2;  // scenes: the instance's forward frame rows
 };
 
 __device__ __forceinline__ float3 ld3(const float* p, uint32_t k) { return make_float3(p[3 * k], p[3 * k + 1], p[3 * k + 2]); }
 
-__device__ __forceinline__ ShadeHit shadeSetup(const ShadeParams& S, float4 ra, float4 rb, uint32_t prim, float t,
-                                               float u, float v, float3 l) {
+// Frame row applied to an object-space point: m.xyz . a + m.w.
+__device__ __forceinline__ float frameRow(float4 m, float3 a) { return fmaf(m.x, a.x, fmaf(m.y, a.y, fmaf(m.z, a.z, m.w))); }
+
+// Whether the hit record h names a shaded triangle: a hit at all, and in a scene one on
+// a triangle-mesh instance (hits on custom primitives are occluders only, image 0).
+template <bool SCENE>
+__device__ __forceinline__ bool shadedHit(const ShadeParams& S, const uint32_t* h) {
+    if (h[1] == kInvalid) return false;
+    if (!SCENE) return true;
+    return instPrimType(S.sceneLeaves[S.scenePrimToLeaf[h[0]]].typeBits) == GRT_PRIMITIVE_TRIANGLE_MESH;
+}
+
+template <bool SCENE>
+__device__ __forceinline__ ShadeHit shadeSetup(const ShadeParams& S, float4 ra, float4 rb, uint32_t inst, uint32_t prim,
+                                               float t, float u, float v, float3 l) {
     ShadeHit H;
-    H.i0 = S.idx[3 * (size_t)prim], H.i1 = S.idx[3 * (size_t)prim + 1], H.i2 = S.idx[3 * (size_t)prim + 2];
+    const size_t tri = SCENE ? (size_t)S.triOffset[inst] + prim : (size_t)prim;
+    H.i0 = S.idx[3 * tri], H.i1 = S.idx[3 * tri + 1], H.i2 = S.idx[3 * tri + 2];
     H.v0 = ld3(S.pos, H.i0), H.v1 = ld3(S.pos, H.i1), H.v2 = ld3(S.pos, H.i2);
+    if (SCENE) {
+        const float4* F = S.frames + kFrameRows * (size_t)inst;
+        H.m0 = F[0], H.m1 = F[1], H.m2 = F[2];
+        H.v0 = make_float3(frameRow(H.m0, H.v0), frameRow(H.m1, H.v0), frameRow(H.m2, H.v0));
+        H.v1 = make_float3(frameRow(H.m0, H.v1), frameRow(H.m1, H.v1), frameRow(H.m2, H.v1));
+        H.v2 = make_float3(frameRow(H.m0, H.v2), frameRow(H.m1, H.v2), frameRow(H.m2, H.v2));
+    }
     H.o = f3(ra), H.d = f3(rb);
     float3 n = normalize3(cross3(H.v1 - H.v0, H.v2 - H.v0));
     if (dot3(n, H.d) > 0.0f) n = n * -1.0f;
@@ -207,44 +238,48 @@ __device__ __forceinline__ float3 shadeColour(const ShadeParams& S, const ShadeH
 }
 
 // Items = pixels; a lit hit pixel traces its shadow ray, everything else is written at once.
+template <bool SCENE>
 struct ShadowSource {
     const ShadeParams* S;
     __device__ unsigned long long count() const { return S->n; }
-    __device__ bool begin(uint32_t i, const TraceParams& P, Stack& st, RayState& s) const {
+    __device__ ShadeHit setup(uint32_t i) const {
         const uint32_t* h = S->hits + 5 * (size_t)i;
-        const uint32_t prim = h[1];
-        if (prim != kInvalid) {
-            const float3 l = make_float3(S->light[0], S->light[1], S->light[2]);
-            const ShadeHit H = shadeSetup(*S, S->rays[2 * (size_t)i], S->rays[2 * (size_t)i + 1], prim,
-                                          __uint_as_float(h[2]), __uint_as_float(h[3]), __uint_as_float(h[4]), l);
+        const float3 l = make_float3(S->light[0], S->light[1], S->light[2]);
+        return shadeSetup<SCENE>(*S, S->rays[2 * (size_t)i], S->rays[2 * (size_t)i + 1], h[0], h[1],
+                                 __uint_as_float(h[2]), __uint_as_float(h[3]), __uint_as_float(h[4]), l);
+    }
+    __device__ bool begin(uint32_t i, const TraceParams& P, Stack& st, RayState& s) const {
+        if (shadedHit<SCENE>(*S, S->hits + 5 * (size_t)i)) {
+            const ShadeHit H = setup(i);
             if (H.nl > 0.0f) {
-                beginRay<false>(P, st, s, (H.o + H.d * H.t) + H.nf * 1e-4f, l, 0.0f, INFINITY);
+                const float3 l = make_float3(S->light[0], S->light[1], S->light[2]);
+                beginRay<SCENE>(P, st, s, (H.o + H.d * H.t) + H.nf * 1e-4f, l, 0.0f, INFINITY);
                 return true;
             }
         }
-        S->image[3 * (size_t)i] = 0.f, S->image[3 * (size_t)i + 1] = 0.f, S->image[3 * (size_t)i + 2] = 0.f;
+        if (S->image) S->image[3 * (size_t)i] = 0.f, S->image[3 * (size_t)i + 1] = 0.f, S->image[3 * (size_t)i + 2] = 0.f;
         if (S->vis) S->vis[i] = 1;
         return false;
     }
     __device__ void finish(uint32_t i, const RayState& s) const {
-        const uint32_t* h = S->hits + 5 * (size_t)i;
-        const float3 l = make_float3(S->light[0], S->light[1], S->light[2]);
-        const ShadeHit H = shadeSetup(*S, S->rays[2 * (size_t)i], S->rays[2 * (size_t)i + 1], h[1],
-                                      __uint_as_float(h[2]), __uint_as_float(h[3]), __uint_as_float(h[4]), l);
         const float V = s.best.prim == kInvalid ? 1.0f : 0.0f;
-        const float3 c = shadeColour(*S, H);
-        const float k = V * H.nl;
-        S->image[3 * (size_t)i] = k * c.x, S->image[3 * (size_t)i + 1] = k * c.y, S->image[3 * (size_t)i + 2] = k * c.z;
+        if (S->image) {
+            const ShadeHit H = setup(i);
+            const float3 c = shadeColour(*S, H);
+            const float k = V * H.nl;
+            S->image[3 * (size_t)i] = k * c.x, S->image[3 * (size_t)i + 1] = k * c.y, S->image[3 * (size_t)i + 2] = k * c.z;
+        }
         if (S->vis) S->vis[i] = (uint8_t)V;
     }
 };
 
+template <bool SCENE>
 __global__ void shadeForwardKernel(TraceParams P, ShadeParams S) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
-    ShadowSource src{&S};
-    refillLoop<true, false, false>(P, st, src);
+    ShadowSource<SCENE> src{&S};
+    refillLoop<true, SCENE, false>(P, st, src);
 }
 
 // One pixel's share of the adjoint: dL/dc_k and dL/dv_k for the hit triangle's three
@@ -257,38 +292,18 @@ struct PixelAdjoint {
     float3 dl;
 };
 
-template <bool RECOMPUTE>
-__device__ __forceinline__ PixelAdjoint pixelAdjoint(const TraceParams& P, const ShadeParams& S, Stack& st,
-                                                     uint32_t i, float3 l) {
+template <bool SCENE>
+__device__ __forceinline__ PixelAdjoint pixelAdjoint(const ShadeParams& S, uint32_t i, float3 l) {
     PixelAdjoint A;
     A.live = false;
-    uint32_t prim;
-    float t, u, v, V;
-    float4 ra, rb;
-    if (RECOMPUTE) {
-        ra = S.rays[2 * (size_t)i], rb = S.rays[2 * (size_t)i + 1];
-        Hit h = traceRay<false, false>(P, st, f3(ra), f3(rb), ra.w, rb.w);
-        prim = h.prim;
-        if (prim == kInvalid) return A;
-        const float4* rec = reinterpret_cast<const float4*>(P.target.leaves) + 3 * (size_t)P.targetPrimToLeaf[prim];
-        const float4 r = refine64(P.inv64, false, 0, f3(ra), f3(rb), rec, false, ra.w, rb.w);
-        if (r.w != 0.f) h.t = r.x, h.u = r.y, h.v = r.z;
-        t = h.t, u = h.u, v = h.v;
-    } else {
-        const uint32_t* h = S.hits + 5 * (size_t)i;
-        prim = h[1];
-        if (prim == kInvalid) return A;  // a miss reads nothing else
-        t = __uint_as_float(h[2]), u = __uint_as_float(h[3]), v = __uint_as_float(h[4]);
-        ra = S.rays[2 * (size_t)i], rb = S.rays[2 * (size_t)i + 1];
-    }
-    const ShadeHit H = shadeSetup(S, ra, rb, prim, t, u, v, l);
+    const uint32_t* h = S.hits + 5 * (size_t)i;
+    if (!shadedHit<SCENE>(S, h)) return A;  // a miss reads nothing else
+    const uint32_t prim = h[1];
+    const float t = __uint_as_float(h[2]), u = __uint_as_float(h[3]), v = __uint_as_float(h[4]);
+    const float4 ra = S.rays[2 * (size_t)i], rb = S.rays[2 * (size_t)i + 1];
+    const ShadeHit H = shadeSetup<SCENE>(S, ra, rb, h[0], prim, t, u, v, l);
     if (!(H.nl > 0.0f)) return A;  // unlit: I = 0 and no gradient
-    if (RECOMPUTE) {
-        const Hit sh = traceRay<true, false>(P, st, (H.o + H.d * H.t) + H.nf * 1e-4f, l, 0.0f, INFINITY);
-        V = sh.prim == kInvalid ? 1.0f : 0.0f;
-    } else {
-        V = S.vis ? (float)S.vis[i] : 1.0f;
-    }
+    const float V = S.vis ? (float)S.vis[i] : 1.0f;
     if (V == 0.0f) return A;
     const float3 g = make_float3(S.gimg[3 * (size_t)i], S.gimg[3 * (size_t)i + 1], S.gimg[3 * (size_t)i + 2]);
     const float w[3] = {1.0f - u - v, u, v};
@@ -320,6 +335,14 @@ __device__ __forceinline__ PixelAdjoint pixelAdjoint(const TraceParams& P, const
         const float3 y = (cross3(e2, nd) * gu + cross3(nd, e1) * gv) * (1.0f / det);
 #pragma unroll
         for (int k = 0; k < 3; ++k) A.dv[k] = A.dv[k] - y * w[k];
+    }
+    if (SCENE) {  // world vertex = M a + T: dL/da = M^T dL/dv
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float3 g = A.dv[k];
+            A.dv[k] = make_float3(H.m0.x * g.x + H.m1.x * g.y + H.m2.x * g.z, H.m0.y * g.x + H.m1.y * g.y + H.m2.y * g.z,
+                                  H.m0.z * g.x + H.m1.z * g.y + H.m2.z * g.z);
+        }
     }
     return A;
 }
@@ -379,23 +402,21 @@ __device__ __forceinline__ void scatterAdjoint(const PixelAdjoint& A, float* pri
 }
 
 // Adjoint: blocks take tiles of consecutive pixels (image rows) from a work counter;
-// one thread per pixel. With PRIV the colour and position gradients of every vertex (6
-// floats each) are summed in shared memory and each block adds its nonzero entries to
-// the output once at the end: a small mesh's gradients sit in a few hundred cache lines,
-// and per-pixel global atomics on them queue in a few L2 slices. With RECOMPUTE the
-// primary hit (refined in FP64) and the visibility are traced again instead of read.
-template <bool RECOMPUTE, bool PRIV>
+// one thread per pixel, reading the stored hit records and visibility. With PRIV the
+// colour and position gradients of every vertex (6 floats each) are summed in shared
+// memory and each block adds its nonzero entries to the output once at the end: a small
+// mesh's gradients sit in a few hundred cache lines, and per-pixel global atomics on
+// them queue in a few L2 slices.
+template <bool SCENE, bool PRIV>
 __global__ void shadeBackwardKernel(TraceParams P, ShadeParams S, uint32_t nv) {
     extern __shared__ uint32_t sstack[];
     __shared__ unsigned long long tile;
-    float* priv = reinterpret_cast<float*>(sstack + (RECOMPUTE ? blockDim.x * traceSmemWords(P.sharedDepth) : 0));
+    float* priv = reinterpret_cast<float*>(sstack);
     if (PRIV)
         for (uint32_t j = threadIdx.x; j < 6 * nv; j += blockDim.x) priv[j] = 0.0f;
-    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
     const float3 l = make_float3(S.light[0], S.light[1], S.light[2]);
     float3 gl = make_float3(0.f, 0.f, 0.f);
-    const uint32_t perTile = blockDim.x * (RECOMPUTE ? 2u : 8u);
+    const uint32_t perTile = blockDim.x * 8u;
     for (;;) {
         if (threadIdx.x == 0) tile = atomicAdd(P.counter, 1ull);
         __syncthreads();  // also orders the zeroing of priv before the first adds
@@ -405,7 +426,7 @@ __global__ void shadeBackwardKernel(TraceParams P, ShadeParams S, uint32_t nv) {
         for (uint32_t k = threadIdx.x; k < perTile; k += blockDim.x) {  // same trip count in every lane
             PixelAdjoint A;
             A.live = false;
-            if (first + k < S.n) A = pixelAdjoint<RECOMPUTE>(P, S, st, (uint32_t)(first + k), l);
+            if (first + k < S.n) A = pixelAdjoint<SCENE>(S, (uint32_t)(first + k), l);
             if (A.live) gl = gl + A.dl;
             scatterAdjoint<PRIV>(A, priv, S, nv);
         }
@@ -1145,51 +1166,141 @@ grtError grtPathTrace(grtContext ctx, grtScene scene, const grtRay* rays, uint32
 // Shared-memory budget of the adjoint's block-private gradient copy (4,096 vertices).
 static constexpr size_t kShadePrivateBytes = 96 * 1024;
 
-static grtError prepareShade(grtContext ctx, grtGeometry geom, const grtRay* rays, uint32_t n, const uint32_t* indices,
-                             const float* positions, const float* colours, const float* light,
-                             const grtTraceOptions* options, TraceParams& P, ShadeParams& S, int* bs) {
-    if (!ctx || !geom) return GRT_ERROR_INVALID_PARAMETER;
-    BvhObject* o = findBvh(geom);
-    if (!o || o->primType != GRT_PRIMITIVE_TRIANGLE_MESH) return GRT_ERROR_INVALID_PARAMETER;
+// The shading parameters of one call: the target (a triangle geometry, or a scene with
+// per-instance triangle offsets into the mesh arrays) and the mesh arrays.
+static grtError prepareShade(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, uint32_t n,
+                             const uint32_t* triOffset, const uint32_t* indices, const float* positions,
+                             const float* colours, const float* light, const grtTraceOptions* options, TraceParams& P,
+                             ShadeParams& S, int* bs) {
+    if (!ctx || (scene != nullptr) == (geom != nullptr)) return GRT_ERROR_INVALID_PARAMETER;
+    BvhObject* o = findBvh(scene ? (const void*)scene : (const void*)geom);
+    if (!o) return GRT_ERROR_INVALID_PARAMETER;
+    if (geom && o->primType != GRT_PRIMITIVE_TRIANGLE_MESH) return GRT_ERROR_INVALID_PARAMETER;
     bool isScene = false;
-    grtError e = prepareTrace(asContext(ctx), nullptr, geom, nullptr, options, P, &isScene, bs);
+    grtError e = prepareTrace(asContext(ctx), scene, geom, nullptr, options, P, &isScene, bs);
     if (e != GRT_SUCCESS) return e;
     if (n && (!rays || !indices || !positions || !colours || !light || ((uintptr_t)rays & 15)))
         return GRT_ERROR_INVALID_PARAMETER;
+    if (n && scene && !triOffset) return GRT_ERROR_INVALID_PARAMETER;
     S.rays = (const float4*)rays;
     S.n = n;
     S.idx = indices;
     S.pos = positions;
     S.col = colours;
     S.light = light;
+    if (scene) {
+        S.triOffset = triOffset;
+        S.frames = (const float4*)o->fwd32;
+        S.sceneLeaves = (const InstanceRecord*)o->leaves;
+        S.scenePrimToLeaf = o->primToLeaf;
+    }
     return GRT_SUCCESS;
+}
+
+// The forward shading launch (image and / or visibility from stored hits).
+static grtError launchShadeForward(Context* c, bool scene, TraceParams& P, const ShadeParams& S, int bs,
+                                   const grtTraceOptions* options, cudaStream_t s) {
+    void (*kernel)(TraceParams, ShadeParams) = scene ? shadeForwardKernel<true> : shadeForwardKernel<false>;
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
+    LaunchShape L = persistentShape(c, kernel, bs, smem);
+    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(S.n, bs));
+    grtError e = bindGlobalStack(c, options, L.blocks * bs, P);
+    if (e != GRT_SUCCESS) return e;
+    P.counter = nextCounter(c);
+    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
+    kernel<<<L.blocks, bs, smem, s>>>(P, S);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+// The adjoint. Without stored hits (hits = NULL) it first traces them again with the
+// library's closest-hit query and the forward's visibility pass, into context memory
+// that lives only for this call, then runs the stored-hit adjoint over them: the
+// recompute costs about one forward pass.
+static grtError shadeBackward(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, const grtHit* hits,
+                              const uint8_t* visibility, uint32_t n, const uint32_t* triOffset,
+                              const uint32_t* indices, const float* positions, uint32_t nv, const float* colours,
+                              const float* light, const float* gradImage, float* gradColours, float* gradLight,
+                              float* gradPositions, const grtTraceOptions* options, void* stream) {
+    TraceParams P{};
+    ShadeParams S{};
+    int bs = 128;
+    grtError e = prepareShade(ctx, scene, geom, rays, n, triOffset, indices, positions, colours, light, options, P,
+                              S, &bs);
+    if (e != GRT_SUCCESS || n == 0) return e;
+    if (!gradImage || !gradColours || !gradLight || !gradPositions) return GRT_ERROR_INVALID_PARAMETER;
+    Context* c = asContext(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!hits) {
+        void* aux = nullptr;
+        const size_t hitBytes = alignUp((size_t)n * sizeof(grtHit), 256);
+        e = contextAux(c, hitBytes + n, &aux);
+        if (e != GRT_SUCCESS) return e;
+        grtHit* th = (grtHit*)aux;
+        uint8_t* tv = (uint8_t*)aux + hitBytes;
+        e = launchTrace<false>(ctx, scene, geom, rays, n, th, nullptr, options, stream);
+        if (e != GRT_SUCCESS) return e;
+        TraceParams Pv = P;
+        ShadeParams Sv = S;
+        Sv.hits = (const uint32_t*)th;
+        Sv.image = nullptr;
+        Sv.vis = tv;
+        e = launchShadeForward(c, scene != nullptr, Pv, Sv, bs, options, s);
+        if (e != GRT_SUCCESS) return e;
+        hits = th;
+        visibility = tv;
+    }
+    S.hits = (const uint32_t*)hits;
+    S.vis = const_cast<uint8_t*>(visibility);
+    S.gimg = gradImage;
+    S.gcol = gradColours;
+    S.glight = gradLight;
+    S.gpos = gradPositions;
+    // block-private gradient copy when the mesh's vertex count is known and its 24 bytes
+    // per vertex fit the budget
+    const bool priv = nv > 0 && (size_t)nv * 24 <= kShadePrivateBytes;
+    void (*kernel)(TraceParams, ShadeParams, uint32_t) =
+        scene ? (priv ? shadeBackwardKernel<true, true> : shadeBackwardKernel<true, false>)
+              : (priv ? shadeBackwardKernel<false, true> : shadeBackwardKernel<false, false>);
+    const size_t smem = priv ? (size_t)nv * 24 : 0;
+    if (smem > 48 * 1024) GRT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchShape L = persistentShape(c, kernel, bs, smem);
+    // the adjoint traces nothing: 8 blocks per SM keep each block's share of pixels large
+    // next to its pass over the private copy
+    L.blocks = std::min(L.blocks, 8 * smCount(c));
+    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(n, bs));
+    P.counter = nextCounter(c);
+    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
+    kernel<<<L.blocks, bs, smem, s>>>(P, S, priv ? nv : 0u);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(1);
+    return GRT_SUCCESS;
+}
+
+static grtError shadeForward(grtContext ctx, grtScene scene, grtGeometry geom, const grtRay* rays, const grtHit* hits,
+                             uint32_t n, const uint32_t* triOffset, const uint32_t* indices, const float* positions,
+                             const float* colours, const float* light, float* image, uint8_t* visibility,
+                             const grtTraceOptions* options, void* stream) {
+    TraceParams P{};
+    ShadeParams S{};
+    int bs = 128;
+    grtError e = prepareShade(ctx, scene, geom, rays, n, triOffset, indices, positions, colours, light, options, P,
+                              S, &bs);
+    if (e != GRT_SUCCESS || n == 0) return e;
+    if (!hits || !image) return GRT_ERROR_INVALID_PARAMETER;
+    S.hits = (const uint32_t*)hits;
+    S.image = image;
+    S.vis = visibility;
+    return launchShadeForward(asContext(ctx), scene != nullptr, P, S, bs, options, (cudaStream_t)stream);
 }
 
 grtError grtShadeLambert(grtContext ctx, grtGeometry geom, const grtRay* rays, const grtHit* hits, uint32_t pixelCount,
                          const uint32_t* indices, const float* positions, const float* colours, const float* light,
                          float* image, uint8_t* visibility, const grtTraceOptions* options, void* stream) {
-    TraceParams P{};
-    ShadeParams S{};
-    int bs = 128;
-    grtError e = prepareShade(ctx, geom, rays, pixelCount, indices, positions, colours, light, options, P, S, &bs);
-    if (e != GRT_SUCCESS || pixelCount == 0) return e;
-    if (!hits || !image) return GRT_ERROR_INVALID_PARAMETER;
-    S.hits = (const uint32_t*)hits;
-    S.image = image;
-    S.vis = visibility;
-    Context* c = asContext(ctx);
-    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
-    LaunchShape L = persistentShape(c, shadeForwardKernel, bs, smem);
-    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(pixelCount, bs));
-    e = bindGlobalStack(c, options, L.blocks * bs, P);
-    if (e != GRT_SUCCESS) return e;
-    cudaStream_t s = (cudaStream_t)stream;
-    P.counter = nextCounter(c);
-    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
-    shadeForwardKernel<<<L.blocks, bs, smem, s>>>(P, S);
-    GRT_LAUNCH_CHECK();
-    noteLaunches(1);
-    return GRT_SUCCESS;
+    if (!geom) return GRT_ERROR_INVALID_PARAMETER;
+    return shadeForward(ctx, nullptr, geom, rays, hits, pixelCount, nullptr, indices, positions, colours, light, image,
+                        visibility, options, stream);
 }
 
 grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay* rays, const grtHit* hits,
@@ -1197,43 +1308,32 @@ grtError grtShadeLambertBackward(grtContext ctx, grtGeometry geom, const grtRay*
                                  const float* positions, const float* colours, const float* light,
                                  const float* gradImage, float* gradColours, float* gradLight, float* gradPositions,
                                  const grtTraceOptions* options, void* stream) {
-    TraceParams P{};
-    ShadeParams S{};
-    int bs = 128;
-    grtError e = prepareShade(ctx, geom, rays, pixelCount, indices, positions, colours, light, options, P, S, &bs);
-    if (e != GRT_SUCCESS || pixelCount == 0) return e;
-    if (!gradImage || !gradColours || !gradLight || !gradPositions) return GRT_ERROR_INVALID_PARAMETER;
-    const bool recompute = hits == nullptr;
-    S.hits = (const uint32_t*)hits;
-    S.vis = const_cast<uint8_t*>(visibility);
-    S.gimg = gradImage;
-    S.gcol = gradColours;
-    S.glight = gradLight;
-    S.gpos = gradPositions;
-    Context* c = asContext(ctx);
-    // block-private gradient copy when the mesh's vertex count is known and its 24 bytes
-    // per vertex fit the budget
-    const uint32_t nv = findBvh(geom)->vertexCount;
-    const bool priv = nv > 0 && (size_t)nv * 24 <= kShadePrivateBytes;
-    void (*kernel)(TraceParams, ShadeParams, uint32_t) =
-        recompute ? (priv ? shadeBackwardKernel<true, true> : shadeBackwardKernel<true, false>)
-                  : (priv ? shadeBackwardKernel<false, true> : shadeBackwardKernel<false, false>);
-    const size_t smem = (recompute ? (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t) : 0) + (priv ? (size_t)nv * 24 : 0);
-    if (smem > 48 * 1024) GRT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LaunchShape L = persistentShape(c, kernel, bs, smem);
-    // replaying stored hits traces nothing: 8 blocks per SM keep each block's share of
-    // pixels large next to its pass over the private copy
-    if (!recompute) L.blocks = std::min(L.blocks, 8 * smCount(c));
-    L.blocks = std::min<int>(L.blocks, (int)ceilDiv(pixelCount, bs));
-    e = bindGlobalStack(c, options, L.blocks * bs, P);
-    if (e != GRT_SUCCESS) return e;
-    cudaStream_t s = (cudaStream_t)stream;
-    P.counter = nextCounter(c);
-    GRT_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned long long), s));
-    kernel<<<L.blocks, bs, smem, s>>>(P, S, priv ? nv : 0u);
-    GRT_LAUNCH_CHECK();
-    noteLaunches(1);
-    return GRT_SUCCESS;
+    BvhObject* o = geom ? findBvh(geom) : nullptr;
+    if (!o) return GRT_ERROR_INVALID_PARAMETER;
+    return shadeBackward(ctx, nullptr, geom, rays, hits, visibility, pixelCount, nullptr, indices, positions,
+                         o->vertexCount, colours, light, gradImage, gradColours, gradLight, gradPositions, options,
+                         stream);
+}
+
+grtError grtShadeLambertScene(grtContext ctx, grtScene scene, const grtRay* rays, const grtHit* hits,
+                              uint32_t pixelCount, const uint32_t* instanceTriangleOffset, const uint32_t* indices,
+                              const float* positions, const float* colours, const float* light, float* image,
+                              uint8_t* visibility, const grtTraceOptions* options, void* stream) {
+    if (!scene) return GRT_ERROR_INVALID_PARAMETER;
+    return shadeForward(ctx, scene, nullptr, rays, hits, pixelCount, instanceTriangleOffset, indices, positions,
+                        colours, light, image, visibility, options, stream);
+}
+
+grtError grtShadeLambertSceneBackward(grtContext ctx, grtScene scene, const grtRay* rays, const grtHit* hits,
+                                      const uint8_t* visibility, uint32_t pixelCount,
+                                      const uint32_t* instanceTriangleOffset, const uint32_t* indices,
+                                      const float* positions, uint32_t vertexCount, const float* colours,
+                                      const float* light, const float* gradImage, float* gradColours, float* gradLight,
+                                      float* gradPositions, const grtTraceOptions* options, void* stream) {
+    if (!scene) return GRT_ERROR_INVALID_PARAMETER;
+    return shadeBackward(ctx, scene, nullptr, rays, hits, visibility, pixelCount, instanceTriangleOffset, indices,
+                         positions, vertexCount, colours, light, gradImage, gradColours, gradLight, gradPositions,
+                         options, stream);
 }
 
 }  // extern "C"

@@ -346,3 +346,86 @@ def test_two_forwards_through_one_renderer(gpu):
     assert np.allclose(l_, gl, rtol=1e-4, atol=1e-4)
     assert np.allclose(p_, gp, rtol=1e-3, atol=1e-4)
     g.close()
+
+
+def test_two_level_scene_shading_and_adjoint(gpu):
+    """grtShadeLambertScene / grtShadeLambertSceneBackward on a two-level scene: an
+    icosphere instance (scaled, rotated) above a ground-quad instance, and a second
+    instance of the same icosphere mesh, light from above so the spheres shadow the
+    ground (shadow rays through the whole scene). Forward image and visibility against
+    the oracle's world-space composition (oracle.LambertScene); the adjoint, stored and
+    recomputed, against its gradient in object space (colours summed over the instances
+    sharing a vertex, positions through each frame's M^T): every gradient within the
+    bound of _rel_ok, pixels whose hit or visibility differ excluded."""
+    from paper_2603_00292_gb300.objects import Scene
+
+    W, H = 320, 180
+    ico = scenegen.icosphere(3)
+    ground = np.array([[-4, 0, -4], [4, 0, -4], [4, 0, 4], [-4, 0, 4]], np.float32)
+    nv_ico, nt = ico.vertices.shape[0], ico.indices.shape[0]
+    gidx = np.array([[0, 2, 1], [0, 3, 2]], np.uint32)
+    verts = np.concatenate([ico.vertices, ground]).astype(np.float32)
+    idx = np.concatenate([ico.indices, gidx + nv_ico]).astype(np.uint32)
+    frames = np.array([[0.1, 0.2, 0.0, 0.97, 0.7, 0.7, 0.7, 0.0, 0.2, 0.0], [0, 0, 0, 1, 1, 1, 1, 0, -1.2, 0],
+                       [0.0, 0.6, 0.3, 0.74, 0.5, 0.4, 0.45, 1.6, -0.3, 0.8]], np.float32)
+    offs, cnts = [0, nt, 0], [nt, 2, nt]
+    rng = np.random.default_rng(21)
+    cols = rng.uniform(0.2, 1.0, verts.shape).astype(np.float32)
+    tcols = (cols + rng.uniform(-0.05, 0.05, cols.shape)).astype(np.float32)
+    light = np.array([0.3, 1.0, 0.4], np.float64)
+    light = (light / np.linalg.norm(light)).astype(np.float32)
+    cam = scenegen.look_at_camera([0, 1.0, 5.0], [0, -0.4, 0], W, H)
+    rays = oracle.camera_rays(cam.packed(), W, H)
+    n = W * H
+    L = oracle.LambertScene(verts, idx, offs, cnts, frames)
+    l64, c64 = light.astype(np.float64), cols.astype(np.float64)
+    R = L.forward(c64, l64, rays)
+    target = L.forward(tcols.astype(np.float64), l64, rays).image
+
+    g_ico = Geometry(gpu, vertices=device_tensor(ico.vertices), indices=device_tensor(ico.indices)).build()
+    g_gnd = Geometry(gpu, vertices=device_tensor(ground), indices=device_tensor(gidx)).build()
+    sc = Scene(gpu, [g_ico.handle, g_gnd.handle, g_ico.handle], device_tensor(frames)).build()
+    d = dict(pos=device_tensor(verts), idx=device_tensor(idx), col=device_tensor(cols), light=device_tensor(light),
+             rays=device_tensor(rays), off=device_tensor(np.array(offs, np.uint32)))
+    hits = new_hits(n)
+    grt.grtTraceClosest(gpu.handle, sc.handle, None, d["rays"], n, hits)
+    img = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    vis = torch.empty(n, dtype=torch.uint8, device="cuda")
+    grt.grtShadeLambertScene(gpu.handle, sc.handle, d["rays"], hits, n, d["off"], d["idx"], d["pos"], d["col"],
+                             d["light"], img, vis)
+    torch.cuda.synchronize()
+    gi_, gp_ = hits_to_numpy(hits)[0:2]
+    same = (gp_.astype(np.int64) == np.where(R.iprim < 0, 0xFFFFFFFF, R.iprim)) & \
+           (np.where(gp_ == 0xFFFFFFFF, -1, gi_.astype(np.int64)) == np.where(R.iprim < 0, -1, R.inst))
+    assert (~same).sum() <= max(3, 1e-4 * n)
+    lit = same & (R.prim >= 0) & (R.sign > 0)
+    gv = vis.cpu().numpy()
+    shadowed = lit & (R.vis == 0)
+    assert shadowed.sum() > 300, shadowed.sum()  # the spheres' shadows on the ground
+    assert ((gv != R.vis.astype(np.uint8)) & lit).sum() <= max(3, 1e-3 * lit.sum())
+    ok_px = same & ~(lit & (gv != R.vis.astype(np.uint8)))
+    gimg_h = img.cpu().numpy()
+    assert np.abs(gimg_h[ok_px] - R.image[ok_px]).max() < 2e-5
+    assert np.all(gimg_h[shadowed & ok_px] == 0)
+
+    exclude = ~ok_px
+    _, dc, dl, dp = L.gradient(c64, l64, rays[~exclude], target[~exclude])
+    l1 = L.gradient_l1(c64, l64, rays[~exclude], target[~exclude])
+    gimg = 2.0 * (R.image - target)
+    gimg[exclude] = 0.0
+    gimg_d = device_tensor(gimg.astype(np.float32))
+    results = []
+    for stored in (True, False):
+        gc, gl, gp = torch.zeros_like(d["col"]), torch.zeros_like(d["light"]), torch.zeros_like(d["pos"])
+        grt.grtShadeLambertSceneBackward(gpu.handle, sc.handle, d["rays"], hits if stored else None,
+                                         vis if stored else None, n, d["off"], d["idx"], d["pos"], verts.shape[0],
+                                         d["col"], d["light"], gimg_d, gc, gl, gp)
+        torch.cuda.synchronize()
+        got = tuple(t.cpu().numpy().astype(np.float64) for t in (gc, gl, gp))
+        _check_every_gradient(got, (dc, dl, dp), l1)
+        results.append(got)
+    for a, b in zip(*results):  # recomputed hits are the stored ones: equal up to the order of float atomics
+        assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+    for obj in (sc, g_gnd, g_ico):
+        obj.close()

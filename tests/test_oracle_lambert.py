@@ -146,3 +146,100 @@ def test_gradient_term_l1_norms():
     ac2, al2, ap2 = oracle.lambert_gradient_l1(verts, mesh.indices, cols, light, rays, t2)
     assert np.allclose(ac2, 2 * ac, rtol=1e-12) and np.allclose(ap2, 2 * ap, rtol=1e-12)
     assert np.allclose(al2, 2 * al, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- two-level scenes
+def _two_level(light=(0.0, 1.0, 0.0), W=64, H=48, second=True):
+    """An icosphere (scale 0.7, rotated) above a 8x8 ground quad at y = -1.2, optionally a
+    second icosphere instance of the same mesh; camera from (0, 1, 5) toward the origin."""
+    ico = scenegen.icosphere(2)
+    ground = np.array([[-4, 0, -4], [4, 0, -4], [4, 0, 4], [-4, 0, 4]], np.float32)
+    nv = ico.vertices.shape[0]
+    verts = np.concatenate([ico.vertices, ground]).astype(np.float32)
+    idx = np.concatenate([ico.indices, np.array([[0, 2, 1], [0, 3, 2]], np.uint32) + nv]).astype(np.uint32)
+    nt = ico.indices.shape[0]
+    frames = [[0.1, 0.2, 0.0, 0.97, 0.7, 0.7, 0.7, 0.0, 0.2, 0.0], [0, 0, 0, 1, 1, 1, 1, 0, -1.2, 0]]
+    offs, cnts = [0, nt], [nt, 2]
+    if second:
+        frames.append([0.0, 0.6, 0.3, 0.74, 0.5, 0.4, 0.45, 1.6, -0.3, 0.8])
+        offs.append(0), cnts.append(nt)
+    rng = np.random.default_rng(8)
+    cols = rng.uniform(0.2, 1.0, verts.shape)
+    l = np.array(light, np.float64)
+    l /= np.linalg.norm(l)
+    cam = scenegen.look_at_camera([0, 1.0, 5.0], [0, -0.4, 0], W, H)
+    rays = oracle.camera_rays(cam.packed(), W, H)
+    return oracle.LambertScene(verts, idx, offs, cnts, np.array(frames, np.float32)), verts, idx, cols, l, rays
+
+
+def test_scene_identity_frame_equals_plain_oracle():
+    mesh, verts, cols, light, rays, target = _setup()
+    L = oracle.LambertScene(verts, mesh.indices, [0], [mesh.indices.shape[0]], [[0, 0, 0, 1, 1, 1, 1, 0, 0, 0]])
+    a = L.forward(cols, light, rays)
+    b = oracle.lambert_forward(verts, mesh.indices, cols, light, rays)
+    assert np.array_equal(a.image, b.image) and np.array_equal(a.iprim, b.prim) and np.all(a.inst[b.prim >= 0] == 0)
+    ga, gb = L.gradient(cols, light, rays, target), oracle.lambert_gradient(verts, mesh.indices, cols, light, rays,
+                                                                              target)
+    for x, y in zip(ga, gb):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_scene_shadow_cast_by_another_instance():
+    """Light straight up: a ground point whose vertical line passes within 0.9 x the
+    sphere's world radius of its centre is in shadow (the level-2 icosphere contains the
+    ball of radius 0.9), one farther than the radius is lit."""
+    L, verts, idx, cols, l, rays = _two_level(second=False)
+    R = L.forward(cols, l, rays)
+    on_ground = R.inst == 1
+    assert on_ground.sum() > 500
+    t = R.tuv[:, 0]
+    p = rays[:, 0:3].astype(np.float64) + t[:, None] * rays[:, 4:7].astype(np.float64)
+    centre, radius = np.array([0.0, 0.2, 0.0]), 0.7
+    horiz = np.hypot(p[:, 0] - centre[0], p[:, 2] - centre[2])
+    inside, outside = on_ground & (horiz < 0.9 * radius), on_ground & (horiz > radius)
+    assert inside.sum() > 20 and outside.sum() > 100
+    assert np.all(R.vis[inside] == 0) and np.all(R.image[inside] == 0)
+    assert np.all(R.vis[outside] == 1) and np.all(R.image[outside].max(axis=1) > 0)
+
+
+def test_scene_gradient_matches_central_differences():
+    """Object-space positions and colours of the shared mesh (two icosphere instances
+    under scaled, rotated frames, and the ground): FP64 central differences (h = 1e-6)
+    of the loss, recomputed from the perturbed object mesh, against the analytic gradient
+    mapped back through each frame. Parameters whose perturbation changes any pixel's
+    hit, visibility or sign of n.l are skipped."""
+    L, verts, idx, cols, l, rays = _two_level(light=(0.3, 1.0, 0.4))
+    tcols = cols + np.random.default_rng(9).uniform(-0.1, 0.1, cols.shape)
+    frames = np.array([[0.1, 0.2, 0.0, 0.97, 0.7, 0.7, 0.7, 0.0, 0.2, 0.0], [0, 0, 0, 1, 1, 1, 1, 0, -1.2, 0],
+                       [0.0, 0.6, 0.3, 0.74, 0.5, 0.4, 0.45, 1.6, -0.3, 0.8]], np.float32)
+    nt = idx.shape[0] - 2
+    target = L.forward(tcols, l, rays).image
+    _, dc, dl, dp = L.gradient(cols, l, rays, target)
+
+    def loss_state(v, c):
+        S = oracle.LambertScene(v, idx, [0, nt, 0], [nt, 2, nt], frames)
+        R = S.forward(c, l, rays)
+        return ((R.image - target) ** 2).sum(), np.stack([R.prim, R.vis, R.sign])
+
+    rng = np.random.default_rng(10)
+    used = np.unique(idx[:nt])
+    checked = 0
+    for vtx in rng.choice(used, 24, replace=False):
+        for a in range(3):
+            h = 1e-6
+            vp, vm = verts.astype(np.float64), verts.astype(np.float64)
+            vp[vtx, a] += h
+            vm[vtx, a] -= h
+            (lp, sp), (lm, sm) = loss_state(vp, cols), loss_state(vm, cols)
+            if not np.array_equal(sp, sm):
+                continue
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - dp[vtx, a]) <= 1e-4 * max(abs(fd), 1e-3), (vtx, a, fd, dp[vtx, a])
+            checked += 1
+    assert checked >= 30
+    for vtx in rng.choice(used, 6, replace=False):  # colours: the loss is quadratic in them
+        cp, cm = cols.copy(), cols.copy()
+        cp[vtx, 1] += 1e-3
+        cm[vtx, 1] -= 1e-3
+        fd = (loss_state(verts, cp)[0] - loss_state(verts, cm)[0]) / 2e-3
+        assert abs(fd - dc[vtx, 1]) <= 1e-8 * max(1.0, abs(fd))
