@@ -122,8 +122,14 @@ typedef struct grtGeometryBuildInput {
  *   BALANCED     bottom-up clustering (PLOC, Meister and Bittner 2018) over the same
  *                Morton order, nearest neighbours searched 8 positions either side;
  *   HIGH_QUALITY the same clustering with a 32-position search (the spatial-split
- *                builder the paper names for this flag is not provided).
- * All three give binary nodes, 4-wide nodes and leaves of the same layout, and all
+ *                builder the paper names for this flag is not provided);
+ *   CLUSTER_SUBTREES clustering inside the linear BVH's subtrees in one bottom-up pass
+ *                (the one-pass form of locally-ordered clustering, H-PLOC, that the paper
+ *                names for the balanced option, Sec. 8): every LBVH node merges its
+ *                children's clusters by mutual nearest neighbours (union surface area)
+ *                down to 16 and passes the rest up; the root merges to one. About the
+ *                quality of BALANCED at close to the LBVH's build cost.
+ * All four give binary nodes, 4-wide nodes and leaves of the same layout, and all
  * support GRT_BUILD_OPERATION_UPDATE. A geometry's flag is fixed by grtCreateGeometry;
  * grtGetGeometryBuildTemporaryBufferSize and grtBuildGeometry must be given the same
  * flag (the clustering builds need 68 more bytes of temporary memory per primitive).
@@ -132,7 +138,8 @@ typedef struct grtGeometryBuildInput {
 typedef enum grtBuildFlags {
     GRT_BUILD_PREFER_FAST = 0,
     GRT_BUILD_PREFER_BALANCED = 1,
-    GRT_BUILD_PREFER_HIGH_QUALITY = 2
+    GRT_BUILD_PREFER_HIGH_QUALITY = 2,
+    GRT_BUILD_CLUSTER_SUBTREES = 3
 } grtBuildFlags;
 
 typedef struct grtBuildOptions {
@@ -573,7 +580,10 @@ typedef struct grtBatchInfo {
 /* Plans the work items and allocates the batch's device memory (scratch for every
  * scene's build, the queue and the traversal stacks), so that a launch allocates
  * nothing. Every geometry must be a triangle-mesh geometry created from its input's
- * triangle count; the scenes' buffers must stay valid while the batch is used.
+ * triangle count; the scenes' buffers must stay valid while the batch is used. A
+ * geometry created with GRT_BUILD_CLUSTER_SUBTREES is built by that method (whatever its
+ * size, never by the single-block path), every other one as a linear BVH; either way
+ * the result equals grtBuildGeometry's for the subtree clustering and the linear BVH.
  * Errors: GRT_ERROR_INVALID_PARAMETER (bad option, input, geometry or buffer),
  * GRT_ERROR_OUT_OF_MEMORY. */
 grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sceneCount,

@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             L.oracle_topology.argtypes = [P, i64, ctypes.c_int, P, P, P, P]
             L.oracle_fit.argtypes = [P, P, i64, P, P, P, P]
             L.oracle_ploc.argtypes = [P, P, i64, ctypes.c_int, P, P, P, P, P]
+            L.oracle_subtree_cluster.argtypes = [P, P, i64, ctypes.c_int, P, P, P, P, P, P]
             L.oracle_sah_cost.argtypes = [P, P, i64]
             L.oracle_sah_cost.restype = ctypes.c_double
             L.oracle_xi.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
@@ -244,6 +245,34 @@ def ploc(leaf_lo, leaf_hi, centroids, bits_per_axis: int, radius: int):
     return dict(centroid_lo=clo, centroid_hi=chi, codes=codes, sorted_codes=sk, order=order, childL=cl,
                 childR=cr, parent_internal=pi, parent_leaf=pl, node_lo=nlo, node_hi=nhi, leaf_lo=slo,
                 leaf_hi=shi, iterations=iters)
+
+
+def subtree_cluster_topology(leaf_lo, leaf_hi, lbvh_childL, lbvh_childR, cap: int):
+    """Clustering inside the LBVH's subtrees (oracle_subtree_cluster): (childL, childR,
+    parent_internal, parent_leaf) in the format of topology()."""
+    lo = _c(leaf_lo, np.float32)
+    hi = _c(leaf_hi, np.float32)
+    n = lo.shape[0]
+    m = max(n - 1, 0)
+    cl = np.full(m, -1, np.int32)
+    cr = np.full(m, -1, np.int32)
+    pi = np.full(m, -1, np.int32)
+    pl = np.full(n, -1, np.int32)
+    if n >= 2:
+        L0, R0 = _c(lbvh_childL, np.int32), _c(lbvh_childR, np.int32)
+        lib().oracle_subtree_cluster(_p(lo), _p(hi), n, int(cap), _p(L0), _p(R0), _p(cl), _p(cr), _p(pi), _p(pl))
+    return cl, cr, pi, pl
+
+
+def subtree_cluster(leaf_lo, leaf_hi, centroids, bits_per_axis: int, cap: int):
+    """The whole subtree-clustering build reference: the LBVH (bounds, codes, stable sort,
+    Karras topology), clustering inside its subtrees with cluster cap `cap`, then the
+    fit. Returns a dict with the keys of lbvh() plus lbvh_childL / lbvh_childR."""
+    ref = lbvh(leaf_lo, leaf_hi, centroids, bits_per_axis)
+    cl, cr, pi, pl = subtree_cluster_topology(ref["leaf_lo"], ref["leaf_hi"], ref["childL"], ref["childR"], cap)
+    nlo, nhi = fit(cl, cr, ref["leaf_lo"], ref["leaf_hi"])
+    return dict(ref, lbvh_childL=ref["childL"], lbvh_childR=ref["childR"], childL=cl, childR=cr, parent_internal=pi,
+                parent_leaf=pl, node_lo=nlo, node_hi=nhi)
 
 
 def wide_nodes(ref):

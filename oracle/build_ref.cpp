@@ -22,6 +22,7 @@
 //
 // Compile with -ffp-contract=off so no multiply-add is fused.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -317,7 +318,117 @@ void oracle_ploc(const float* leaf_lo, const float* leaf_hi, int64_t n, int radi
     parent_internal[0] = -1;
 }
 
-// Surface-area cost of a binary BVH: sum over internal nodes of box area, divided by
+// Clustering inside the linear BVH's subtrees, bottom up (a one-pass form of the
+// locally-ordered clustering the paper names as HIPRT's balanced build, Sec. 8). Input:
+// n >= 2 leaves in sorted order (boxes) and the LBVH over them (lbvhL/lbvhR as from
+// oracle_topology). Every LBVH node p, children first, turns its children's cluster
+// lists into its own:
+//   1. L = the left child's clusters, then the right child's (a leaf child is the one
+//      cluster of that leaf); F = the unused internal-node numbers of both children and
+//      p itself, in descending order;
+//   2. while L holds more than `cap` clusters (more than 1 at the root, node 0): every
+//      cluster's nearest neighbour in L by union area, equal areas by the pair hash
+//      fmix32(fmix32(a) + b) of the list positions a < b, then the lower position; each
+//      mutual pair (a, b), a < b, becomes the internal node numbered by the next entry
+//      of F (pairs in order of a) with left child a, and takes position a; the others
+//      close ranks in order;
+//   3. L and the unused rest of F go to p's parent.
+// F always holds |L| - 1 numbers, so the root's last merge takes its own number 0.
+// Output in the format of oracle_topology.
+void oracle_subtree_cluster(const float* leaf_lo, const float* leaf_hi, int64_t n, int cap, const int32_t* lbvhL,
+                            const int32_t* lbvhR, int32_t* childL, int32_t* childR, int32_t* parent_internal,
+                            int32_t* parent_leaf) {
+    if (n < 2) return;
+    struct Cluster {
+        float lo[3], hi[3];
+        int32_t id;  // leaf: LEAF | sorted position; internal: node number
+    };
+    struct Out {
+        std::vector<Cluster> list;
+        std::vector<int32_t> free_ids;
+    };
+    auto link = [&](int32_t child, int32_t parent) {
+        if (child & LEAF)
+            parent_leaf[child & 0x7fffffff] = parent;
+        else
+            parent_internal[child] = parent;
+    };
+    auto leaf = [&](int32_t k) {
+        Out o;
+        Cluster c;
+        for (int a = 0; a < 3; ++a) c.lo[a] = leaf_lo[3 * (int64_t)k + a], c.hi[a] = leaf_hi[3 * (int64_t)k + a];
+        c.id = LEAF | k;
+        o.list.push_back(c);
+        return o;
+    };
+    std::vector<Out> done((size_t)(n - 1));
+    // children-first order: an explicit post-order walk of the LBVH from the root
+    std::vector<std::pair<int32_t, bool>> st{{0, false}};
+    while (!st.empty()) {
+        const auto [p, expanded] = st.back();
+        st.pop_back();
+        if (!expanded) {
+            st.push_back({p, true});
+            if (!(lbvhR[p] & LEAF)) st.push_back({lbvhR[p], false});
+            if (!(lbvhL[p] & LEAF)) st.push_back({lbvhL[p], false});
+            continue;
+        }
+        Out a = (lbvhL[p] & LEAF) ? leaf(lbvhL[p] & 0x7fffffff) : std::move(done[(size_t)lbvhL[p]]);
+        Out b = (lbvhR[p] & LEAF) ? leaf(lbvhR[p] & 0x7fffffff) : std::move(done[(size_t)lbvhR[p]]);
+        std::vector<Cluster> L = a.list;
+        L.insert(L.end(), b.list.begin(), b.list.end());
+        std::vector<int32_t> F = a.free_ids;
+        F.insert(F.end(), b.free_ids.begin(), b.free_ids.end());
+        F.push_back(p);
+        std::sort(F.begin(), F.end(), std::greater<int32_t>());
+        size_t next_free = 0;
+        const size_t target = p == 0 ? 1 : (size_t)cap;
+        while (L.size() > target) {
+            const int64_t m = (int64_t)L.size();
+            std::vector<int64_t> nearest((size_t)m);
+            for (int64_t i = 0; i < m; ++i) {
+                uint64_t best_key = ~0ull;
+                int64_t best = -1;
+                for (int64_t j = 0; j < m; ++j) {
+                    if (j == i) continue;
+                    const float area = union_area(L[(size_t)i].lo, L[(size_t)i].hi, L[(size_t)j].lo, L[(size_t)j].hi);
+                    uint32_t bits;
+                    std::memcpy(&bits, &area, 4);
+                    const uint32_t lo = (uint32_t)std::min(i, j), hi = (uint32_t)std::max(i, j);
+                    const uint64_t key = ((uint64_t)bits << 32) | fmix32(fmix32(lo) + hi);
+                    if (key < best_key) best_key = key, best = j;  // j ascends: ties keep the lower j
+                }
+                nearest[(size_t)i] = best;
+            }
+            std::vector<Cluster> next;
+            for (int64_t i = 0; i < m; ++i) {
+                const int64_t j = nearest[(size_t)i];
+                const bool mutual = nearest[(size_t)j] == i;
+                if (mutual && j < i) continue;  // merged into the cluster at j
+                if (!mutual) {
+                    next.push_back(L[(size_t)i]);
+                    continue;
+                }
+                const int32_t q = F[next_free++];
+                const Cluster &x = L[(size_t)i], &y = L[(size_t)j];
+                childL[q] = x.id;
+                childR[q] = y.id;
+                link(x.id, q);
+                link(y.id, q);
+                Cluster u;
+                for (int k = 0; k < 3; ++k) u.lo[k] = std::fmin(x.lo[k], y.lo[k]), u.hi[k] = std::fmax(x.hi[k], y.hi[k]);
+                u.id = q;
+                next.push_back(u);
+            }
+            L.swap(next);
+        }
+        done[(size_t)p].list = std::move(L);
+        done[(size_t)p].free_ids.assign(F.begin() + (std::ptrdiff_t)next_free, F.end());
+    }
+    parent_internal[0] = -1;
+}
+
+// Surface-area cost of a binary BVH: sum over internal nodes of box area, divided by// Surface-area cost of a binary BVH: sum over internal nodes of box area, divided by
 // the root box area (the quality measure of Sec. 6.2 "BVH Construction").
 double oracle_sah_cost(const float* node_lo, const float* node_hi, int64_t n_internal) {
     auto area = [&](int64_t k) {

@@ -35,6 +35,8 @@ GRT_BUILD_OPERATION_UPDATE = 1
 GRT_BUILD_PREFER_FAST = 0          # linear BVH (Morton order, Karras emission)
 GRT_BUILD_PREFER_BALANCED = 1      # PLOC clustering, search radius 8
 GRT_BUILD_PREFER_HIGH_QUALITY = 2  # PLOC clustering, search radius 32
+GRT_BUILD_CLUSTER_SUBTREES = 3     # clustering inside the linear BVH's subtrees, one bottom-up pass
+CLUSTER_CAP = 16                   # clusters a subtree passes up (the library's kClusterCap)
 GRT_INSTANCE_GEOMETRY = 0
 GRT_INTERSECT_NONE = 0
 GRT_INTERSECT_SPHERE = 1

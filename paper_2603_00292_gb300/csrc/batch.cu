@@ -18,6 +18,9 @@
 //   2 + 3P       bottom-up fit over leaf chunks
 //   3 + 3P       closest-hit trace over ray chunks (refill loop), then FP64 refinement
 // A smaller scene is built entirely by one block (phase 0) and traced in phase 1.
+// A scene whose geometry was created with GRT_BUILD_CLUSTER_SUBTREES (any size) has its
+// emission write the LBVH topology to scratch, then one more phase, the bottom-up
+// clustering walk over leaf chunks (cluster.cuh), before the fit; its trace is 4 + 3P.
 // An item of phase k waits until every item of phase k-1 of its scene has finished
 // (per-scene completion counters). The host orders the queue so that an item only
 // ever waits for items taken from the queue before it, so a waiting block never
@@ -33,6 +36,7 @@
 #include <mutex>
 #include <vector>
 
+#include "cluster.cuh"
 #include "lbvh_block.cuh"
 #include "traverse.cuh"
 
@@ -46,10 +50,48 @@ struct BatchSceneDev : BlockBuild {
     uint32_t rays;
     uint32_t small;       // built by one item
     uint32_t tracePhase;
-    uint32_t pad;
+    uint32_t cluster;     // built by subtree clustering
     const float4* rayBuf;
     uint32_t* hitBuf;
+    // subtree clustering scratch (cluster.cuh)
+    uint2* topoChild;
+    uint32_t* topoParent;
+    uint32_t* topoFirst;
+    float4* clusters;
+    uint32_t* freeIds;
+    uint32_t* clusterCount;
+    uint32_t* clusterFlags;
 };
+
+__device__ __forceinline__ ClusterParams clusterParamsOf(const BatchSceneDev& S) {
+    ClusterParams C{};
+    C.src = S.src;
+    C.n = S.n;
+    C.sortedPrims = S.vals[S.passes & 1u];
+    C.topoChild = S.topoChild;
+    C.topoParent = S.topoParent;
+    C.first = S.topoFirst;
+    C.clusters = S.clusters;
+    C.freeIds = S.freeIds;
+    C.count = S.clusterCount;
+    C.flags = S.clusterFlags;
+    C.nodes = S.nodes;
+    C.parents = S.parents;
+    C.error = S.error;
+    return C;
+}
+
+// Emission of a clustered scene: the LBVH topology of internal nodes [begin, end) into
+// the scratch (keys written by other blocks: L2 loads), arrival counters zeroed.
+template <typename K>
+__device__ __noinline__ void clusterTopologyRange(const BatchSceneDev& S, uint32_t begin, uint32_t end) {
+    const ClusterParams C = clusterParamsOf(S);
+    const K* keys = static_cast<const K*>(S.keys[S.passes & 1u]);
+    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        karrasTopology<true>(keys, (int)i, C);
+        C.flags[i] = 0u;
+    }
+}
 
 struct BatchItemDev {
     uint32_t scene;
@@ -217,12 +259,21 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
                 sortDownsweepChunk<uint32_t>(S, it.chunk, p, B.sortChunkKeys, smem);
             }
         } else if (it.phase == 3 * S.passes + 1) {
+            const uint32_t b0 = it.chunk * B.buildChunk, b1 = min(S.n - 1, b0 + B.buildChunk);
+            if (S.cluster) {
+                if (wide)
+                    clusterTopologyRange<unsigned long long>(S, b0, b1);
+                else
+                    clusterTopologyRange<uint32_t>(S, b0, b1);
+            } else if (wide) {
+                karrasRange<unsigned long long>(S, b0, b1);
+            } else {
+                karrasRange<uint32_t>(S, b0, b1);
+            }
+        } else if (S.cluster && it.phase == 3 * S.passes + 2) {
             const uint32_t b0 = it.chunk * B.buildChunk;
-            if (wide)
-                karrasRange<unsigned long long>(S, b0, min(S.n - 1, b0 + B.buildChunk));
-            else
-                karrasRange<uint32_t>(S, b0, min(S.n - 1, b0 + B.buildChunk));
-        } else if (it.phase == 3 * S.passes + 2) {
+            clusterRange(clusterParamsOf(S), b0, min(S.n, b0 + B.buildChunk), reinterpret_cast<ClusterWarpList*>(smem));
+        } else if (it.phase == 3 * S.passes + 2 + S.cluster) {
             const uint32_t b0 = it.chunk * B.buildChunk;
             fitRange(S, b0, min(S.n, b0 + B.buildChunk));
         } else {
@@ -336,10 +387,11 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         d.n = n;
         d.rays = in.rayCount;
         d.bits = o->mortonBits;
-        d.small = n <= opt.smallScenePrims;
+        d.cluster = (buildsBySubtreeClustering(o) && n >= 2) ? 1u : 0u;
+        d.small = n <= opt.smallScenePrims && !d.cluster;
         d.sortChunks = std::max(1u, ceilDiv(n, chunkKeys));
         d.passes = (d.bits + 7) / 8;
-        d.tracePhase = d.small ? 1u : 3u * d.passes + 3u;
+        d.tracePhase = d.small ? 1u : 3u * d.passes + 3u + d.cluster;
         d.rayBuf = (const float4*)in.rays;
         d.hitBuf = (uint32_t*)in.hits;
         d.nodes = (float4*)o->nodes;
@@ -353,6 +405,8 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         scratchOff[i] = scratch;
         scratch += 256 + alignUp(16 * nn, 256) + 2 * alignUp(kb * nn, 256) + 2 * alignUp(4 * nn, 256) +
                    alignUp(4 * (size_t)kBlockRadix * d.sortChunks, 256) + alignUp(4 * nn, 256);
+        if (d.cluster)  // LBVH child words, parent entries, range starts; clusters, numbers, counts, flags
+            scratch += 2 * alignUp(8 * nn, 256) + alignUp(4 * nn, 256) + alignUp(32 * nn, 256) + 3 * alignUp(4 * nn, 256);
     }
 
     // work items. Scenes go in groups of opt.sceneGroup, largest first: a group's build
@@ -370,7 +424,8 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (ph == 0) return ceilDiv(d.n, opt.buildChunk);
         if (ph <= 3 * d.passes) return (ph - 1) % 3 == 1 ? 1u : d.sortChunks;
         if (ph == 3 * d.passes + 1) return ceilDiv(d.n - 1, opt.buildChunk);
-        if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);
+        if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);               // clustering walk or fit
+        if (d.cluster && ph == 3 * d.passes + 3) return ceilDiv(d.n, opt.buildChunk);  // the fit after clustering
         return 0u;
     };
     for (uint32_t g0 = 0; g0 < sceneCount; g0 += opt.sceneGroup) {
@@ -407,7 +462,8 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
     b->blockSize = bs;
     const size_t stackSmem = (size_t)bs * traceSmemWords(opt.sharedStackDepth) * 4;
     const size_t sortSmem = ((size_t)warps * kBlockRadix + 2 * kBlockRadix) * 4;
-    b->smem = std::max<size_t>(std::max(stackSmem, sortSmem), 33 * 4);
+    const size_t clusterSmem = (size_t)warps * sizeof(ClusterWarpList);
+    b->smem = std::max<size_t>(std::max(std::max(stackSmem, sortSmem), clusterSmem), 33 * 4);
     int perSm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSm, batchKernel, (int)bs, b->smem) != cudaSuccess ||
         perSm < 1)
@@ -441,7 +497,16 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         d.vals[0] = (uint32_t*)p, p += alignUp(4 * nn, 256);
         d.vals[1] = (uint32_t*)p, p += alignUp(4 * nn, 256);
         d.counts = (uint32_t*)p, p += alignUp(4 * (size_t)kBlockRadix * d.sortChunks, 256);
-        d.flags = (uint32_t*)p;
+        d.flags = (uint32_t*)p, p += alignUp(4 * nn, 256);
+        if (d.cluster) {
+            d.topoChild = (uint2*)p, p += alignUp(8 * nn, 256);
+            d.topoParent = (uint32_t*)p, p += alignUp(8 * nn, 256);
+            d.topoFirst = (uint32_t*)p, p += alignUp(4 * nn, 256);
+            d.clusters = (float4*)p, p += alignUp(32 * nn, 256);
+            d.freeIds = (uint32_t*)p, p += alignUp(4 * nn, 256);
+            d.clusterCount = (uint32_t*)p, p += alignUp(4 * nn, 256);
+            d.clusterFlags = (uint32_t*)p;
+        }
     }
     cudaError_t ce = cudaSuccess;
     if (sceneCount)

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <unordered_map>
 
+#include "cluster.cuh"
 #include "lbvh_block.cuh"
 #include "ploc.cuh"
 
@@ -568,7 +569,7 @@ static void destroyBvhObject(BvhObject* o) {
 
 // Morton + sort + Karras over the centroids already in temp (count >= 1).
 static grtError sortAndEmit(Context* ctx, BvhObject* o, const BuildLayout& L, char* temp, cudaStream_t s,
-                            const uint32_t** sortedOut, bool emit = true) {
+                            const uint32_t** sortedOut, bool emit = true, const void** sortedKeysOut = nullptr) {
     const uint32_t n = o->primCount;
     const float4* cen = (const float4*)(temp + L.centroids);
     const uint32_t* bounds = (const uint32_t*)(temp + L.bounds);
@@ -598,6 +599,7 @@ static grtError sortAndEmit(Context* ctx, BvhObject* o, const BuildLayout& L, ch
         noteLaunches(1);
     }
     *sortedOut = (const uint32_t*)(temp + L.vals[fb]);
+    if (sortedKeysOut) *sortedKeysOut = sk;
     return GRT_SUCCESS;
 }
 
@@ -610,12 +612,15 @@ static grtError resetBuildScratch(const BuildLayout& L, char* temp, uint32_t n, 
 
 // ======================================================================= clustering builds
 // A geometry's build method is fixed when it is created: 0 = LBVH (GRT_BUILD_PREFER_FAST),
-// else PLOC with this search radius (ploc.cuh).
+// kSubtreeMethod = clustering inside the LBVH's subtrees (cluster.cuh), else PLOC with
+// this search radius (ploc.cuh).
+constexpr uint32_t kSubtreeMethod = 0xFFFFu;
 static uint32_t clusterRadius(const grtBuildOptions* opt) {
     if (!opt || opt->buildFlags == GRT_BUILD_PREFER_FAST) return 0;
+    if (opt->buildFlags == GRT_BUILD_CLUSTER_SUBTREES) return kSubtreeMethod;
     return opt->buildFlags == GRT_BUILD_PREFER_BALANCED ? 8u : 32u;
 }
-static bool validBuildFlags(const grtBuildOptions* opt) { return !opt || opt->buildFlags <= 2u; }
+static bool validBuildFlags(const grtBuildOptions* opt) { return !opt || opt->buildFlags <= 3u; }
 
 static std::mutex g_methodLock;
 static std::unordered_map<const BvhObject*, uint32_t> g_clusterRadius;  // objects with a PLOC build
@@ -625,6 +630,8 @@ static uint32_t radiusOf(const BvhObject* o) {
     auto it = g_clusterRadius.find(o);
     return it == g_clusterRadius.end() ? 0u : it->second;
 }
+
+bool buildsBySubtreeClustering(const BvhObject* o) { return radiusOf(o) == kSubtreeMethod; }
 
 // PLOC scratch after the LBVH layout: two cluster arrays (32 B per cluster), the
 // per-position neighbour words, per-block counts and the barrier words.
@@ -640,6 +647,76 @@ static PlocLayout plocLayout(const BuildLayout& L, uint32_t n) {
     P.sync = P.counts + alignUp(8 * (size_t)ceilDiv(m, kPlocThreads), 256);
     P.total = P.sync + 256;
     return P;
+}
+
+// Per-geometry build: the LBVH topology into the temporary arrays (one thread per
+// internal node), the arrival counters zeroed.
+template <typename K>
+__global__ void clusterTopologyKernel(ClusterParams C, const K* __restrict__ sortedKeys) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i + 1 >= C.n) return;
+    karrasTopology<false>(sortedKeys, (int)i, C);
+    C.flags[i] = 0u;
+}
+
+constexpr int kClusterThreads = 256;
+
+__global__ void __launch_bounds__(kClusterThreads) clusterWalkKernel(ClusterParams C) {
+    __shared__ ClusterWarpList lists[kClusterThreads / 32];
+    const uint32_t begin = blockIdx.x * blockDim.x;
+    clusterRange(C, begin, min(C.n, begin + blockDim.x), lists);
+}
+
+// Subtree-clustering scratch after the LBVH layout: the LBVH's child words, parent
+// entries and range starts, the per-position cluster and number arrays, per-node
+// counts and arrival counters (64 B per primitive).
+struct SubtreeLayout {
+    size_t child, parent, first, clusters, freeIds, count, flags, total;
+};
+static SubtreeLayout subtreeLayout(const BuildLayout& L, uint32_t n) {
+    SubtreeLayout Q{};
+    const size_t m = n ? n : 1;
+    Q.child = alignUp(L.total, 256);
+    Q.parent = Q.child + alignUp(8 * m, 256);
+    Q.first = Q.parent + alignUp(4 * 2 * m, 256);
+    Q.clusters = Q.first + alignUp(4 * m, 256);
+    Q.freeIds = Q.clusters + alignUp(32 * m, 256);
+    Q.count = Q.freeIds + alignUp(4 * m, 256);
+    Q.flags = Q.count + alignUp(4 * m, 256);
+    Q.total = Q.flags + alignUp(4 * m, 256);
+    return Q;
+}
+
+// The subtree clustering over the sorted leaves (n >= 2): the LBVH topology into the
+// scratch, then the bottom-up walk, which writes the final child words and parent links.
+static grtError launchSubtreeCluster(Context* c, BvhObject* o, const BuildLayout& L, char* t, const PrimSource& S,
+                                     const uint32_t* sorted, const void* sortedKeys, cudaStream_t s) {
+    const uint32_t n = o->primCount;
+    const SubtreeLayout Q = subtreeLayout(L, n);
+    ClusterParams C{};
+    C.src = S;
+    C.n = n;
+    C.sortedPrims = sorted;
+    C.topoChild = (uint2*)(t + Q.child);
+    C.topoParent = (uint32_t*)(t + Q.parent);
+    C.first = (uint32_t*)(t + Q.first);
+    C.clusters = (float4*)(t + Q.clusters);
+    C.freeIds = (uint32_t*)(t + Q.freeIds);
+    C.count = (uint32_t*)(t + Q.count);
+    C.flags = (uint32_t*)(t + Q.flags);
+    C.nodes = (float4*)o->nodes;
+    C.parents = (uint32_t*)o->parents;
+    C.error = &workspace(c)->error;
+    if (o->mortonBits == 30)
+        clusterTopologyKernel<uint32_t><<<ceilDiv(n - 1, 256), 256, 0, s>>>(C, (const uint32_t*)sortedKeys);
+    else
+        clusterTopologyKernel<unsigned long long><<<ceilDiv(n - 1, 256), 256, 0, s>>>(
+            C, (const unsigned long long*)sortedKeys);
+    GRT_LAUNCH_CHECK();
+    clusterWalkKernel<<<ceilDiv(n, kClusterThreads), kClusterThreads, 0, s>>>(C);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(2);
+    return GRT_SUCCESS;
 }
 
 // The clustering kernel over the sorted leaves: writes child words and parent links.
@@ -689,9 +766,13 @@ static grtError issueGeometryBuild(Context* c, BvhObject* o, uint32_t op, const 
         primCentroidKernel<<<ceilDiv(n, 256), 256, 0, s>>>(S, (float4*)(t + L.centroids), (uint32_t*)(t + L.bounds));
         GRT_LAUNCH_CHECK();
         noteLaunches(1);
-        e = sortAndEmit(c, o, L, t, s, &sorted, radius == 0);
+        const void* sortedKeys = nullptr;
+        e = sortAndEmit(c, o, L, t, s, &sorted, radius == 0, &sortedKeys);
         if (e != GRT_SUCCESS) return e;
-        if (radius != 0 && n >= 2) {
+        if (radius == kSubtreeMethod && n >= 2) {
+            e = launchSubtreeCluster(c, o, L, t, S, sorted, sortedKeys, s);
+            if (e != GRT_SUCCESS) return e;
+        } else if (radius != 0 && n >= 2) {
             e = launchPloc(c, o, L, t, S, sorted, radius, s);
             if (e != GRT_SUCCESS) return e;
         }
@@ -822,7 +903,8 @@ grtError grtGetGeometryBuildTemporaryBufferSize(grtContext ctx, const grtGeometr
     if (e != GRT_SUCCESS) return e;
     if (!validBuildFlags(options)) return GRT_ERROR_INVALID_PARAMETER;
     const BuildLayout L = buildLayout(n, resolveMortonBits(n, options), false);
-    *sizeBytes = clusterRadius(options) ? plocLayout(L, n).total : L.total;
+    const uint32_t method = clusterRadius(options);
+    *sizeBytes = method == kSubtreeMethod ? subtreeLayout(L, n).total : method ? plocLayout(L, n).total : L.total;
     return GRT_SUCCESS;
 }
 

@@ -1,0 +1,226 @@
+// Clustering inside the linear BVH's subtrees, in one bottom-up pass: the build behind
+// GRT_BUILD_CLUSTER_SUBTREES and the batched launch's clustered scenes. The paper names
+// locally-ordered clustering (H-PLOC) as HIPRT's balanced build (Sec. 8) and describes
+// bottom-up clustering by surface area (Sec. 6.2); this is a one-pass form of it that
+// needs no grid-wide barrier.
+//
+// The linear BVH's topology (Karras emission) goes to temporary arrays. Every LBVH node
+// p, once both its children are done, holds a list of clusters: its left child's, then
+// its right child's (a leaf is one cluster). While the list has more than kClusterCap
+// clusters (more than one at the root), mutual nearest neighbours by union surface area
+// merge (the clustering build's distance and tie order, ploc_common.cuh); the rest go to p's
+// parent. So clusters from both sides of a Morton split can pair up, which the LBVH's
+// fixed split cannot do.
+//
+// Numbering. Every LBVH node owns one internal-node number (its own). A node passes up,
+// with its list of m clusters, the m - 1 numbers its subtree did not use; its merges
+// take numbers from its children's unused ones and its own, largest first, so the
+// root's final merge takes 0. The tree is therefore a function of the input alone, and
+// equals oracle_subtree_cluster's.
+//
+// Walk. One thread per leaf walks up the LBVH; the second to arrive at a node (an
+// acquire-release atomic at GPU scope, as in the fit) hands it to its warp, which holds
+// the node's list, one cluster per lane (at most 2 kClusterCap = 32), and merges. A
+// node's list is stored in its own leaf range (32 B per position: {lo.xyz, word},
+// {hi.xyz, 0}), its unused numbers likewise, so siblings never overlap. Merges write the
+// final child words (row 3 of the binary node) and parent links; the fit computes the
+// boxes and 4-wide nodes afterwards.
+#pragma once
+
+#include "lbvh.cuh"
+#include "ploc_common.cuh"
+
+namespace grt {
+
+constexpr uint32_t kClusterCap = 16;
+
+struct ClusterParams {
+    PrimSource src;
+    uint32_t n;
+    const uint32_t* sortedPrims;  // sorted position -> primitive ID
+    uint2* topoChild;             // LBVH child words per internal node
+    uint32_t* topoParent;         // LBVH parent entry (parent << 1 | side) per node, internal then leaves
+    uint32_t* first;              // start of each internal node's leaf range
+    float4* clusters;             // 2 float4 per leaf position
+    uint32_t* freeIds;            // per leaf position
+    uint32_t* count;              // clusters passed up by each internal node
+    uint32_t* flags;              // arrival counters per internal node (zeroed)
+    float4* nodes;                // output: child words in row 3 of each binary node
+    uint32_t* parents;            // output: parent links
+    uint32_t* error;              // the context's device error word
+};
+
+// Internal node i of the LBVH into the temporary topology arrays.
+template <bool CG, typename K>
+__device__ __forceinline__ void karrasTopology(const K* __restrict__ keys, int i, const ClusterParams& C) {
+    uint32_t left, right;
+    int first;
+    karrasSplit<CG>(keys, (int)C.n, i, left, right, first);
+    C.topoChild[i] = make_uint2(left, right);
+    C.first[i] = (uint32_t)first;
+    C.topoParent[plocSlot(left, C.n)] = ((uint32_t)i << 1) | 0u;
+    C.topoParent[plocSlot(right, C.n)] = ((uint32_t)i << 1) | 1u;
+    if (i == 0) C.topoParent[0] = kInvalid;
+}
+
+// A warp's working list in shared memory: boxes and words of up to 32 clusters, the
+// node's unused numbers in descending order.
+struct ClusterWarpList {
+    float4 lo[32], hi[32];
+    uint32_t freeIds[32];
+};
+
+// The warp (all 32 lanes) turns LBVH node p's children's lists into p's, merging as
+// described above, and stores it (or, at the root, finishes the tree).
+static __device__ __noinline__ void clusterNode(const ClusterParams& C, uint32_t p, ClusterWarpList& W) {
+    const uint32_t lane = threadIdx.x & 31u, below = (1u << lane) - 1u, n = C.n;
+    const uint2 ch = __ldcg(C.topoChild + p);
+    const bool leafA = (ch.x & kLeafBit) != 0, leafB = (ch.y & kLeafBit) != 0;
+    const uint32_t fa = leafA ? (ch.x & ~kLeafBit) : __ldcg(C.first + ch.x);
+    const uint32_t fb = leafB ? (ch.y & ~kLeafBit) : __ldcg(C.first + ch.y);
+    const uint32_t na = leafA ? 1u : __ldcg(C.count + ch.x), nb = leafB ? 1u : __ldcg(C.count + ch.y);
+    if (na - 1u >= kClusterCap || nb - 1u >= kClusterCap) {  // never, given complete child lists
+        if (lane == 0) latchError(C.error, GRT_ERROR_INTERNAL);
+        return;
+    }
+    uint32_t m = na + nb;
+    // this lane's cluster (lanes below m)
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    uint32_t word = kInvalid;
+    if (lane < m) {
+        const bool inA = lane < na;
+        const bool isLeaf = inA ? leafA : leafB;
+        if (isLeaf) {
+            const uint32_t k = inA ? fa : fb;
+            float3 v[3];
+            const Box3 b = primBox(C.src, __ldcg(C.sortedPrims + k), v);
+            lo = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f), hi = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
+            word = kLeafBit | k;
+        } else {
+            const uint32_t pos = inA ? fa + lane : fb + (lane - na);
+            lo = __ldcg(C.clusters + 2 * (size_t)pos), hi = __ldcg(C.clusters + 2 * (size_t)pos + 1);
+            word = __float_as_uint(lo.w);
+        }
+    }
+    // unused numbers: the children's, then p; ranked descending (all distinct)
+    const uint32_t nfree = m - 1;
+    uint32_t fid = 0;
+    if (lane < nfree) {
+        if (lane < na - 1)
+            fid = __ldcg(C.freeIds + fa + lane);
+        else if (lane < na - 1 + nb - 1)
+            fid = __ldcg(C.freeIds + fb + (lane - (na - 1)));
+        else
+            fid = p;
+    }
+    uint32_t rank = 0;
+    for (uint32_t j = 0; j < 32; ++j) {
+        const uint32_t o = __shfl_sync(0xffffffffu, fid, j);
+        if (j < nfree && lane < nfree && o > fid) ++rank;
+    }
+    if (lane < nfree) W.freeIds[rank] = fid;
+    W.lo[lane] = lo, W.hi[lane] = hi;
+    __syncwarp();
+    uint32_t nextFree = 0;
+    const uint32_t target = p == 0 ? 1u : kClusterCap;
+    while (m > target) {
+        // nearest neighbour of this lane's cluster among the m of the list
+        PlocBest best{0u, 0u, kInvalid, false};
+        if (lane < m)
+            for (uint32_t j = 0; j < m; ++j) {
+                if (j == lane) continue;
+                plocConsider(best, lane, j, __float_as_uint(plocUnionArea(lo, hi, W.lo[j], W.hi[j])));
+            }
+        const uint32_t nn = best.j;
+        const uint32_t back = __shfl_sync(0xffffffffu, nn, nn & 31u);
+        const bool mutual = lane < m && back == lane;
+        const bool lead = mutual && lane < nn;
+        const uint32_t leads = __ballot_sync(0xffffffffu, lead);
+        const uint32_t otherWord = __shfl_sync(0xffffffffu, word, nn & 31u);
+        const float4 olo = W.lo[nn & 31u], ohi = W.hi[nn & 31u];
+        if (lead) {
+            const uint32_t q = W.freeIds[nextFree + __popc(leads & below)];
+            C.nodes[4 * (size_t)q + 3] = make_float4(__uint_as_float(word), __uint_as_float(otherWord), 0.f, 0.f);
+            C.parents[plocSlot(word, n)] = (q << 1) | 0u;
+            C.parents[plocSlot(otherWord, n)] = (q << 1) | 1u;
+            lo = make_float4(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z), 0.f);
+            hi = make_float4(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z), 0.f);
+            word = q;
+        }
+        nextFree += __popc(leads);
+        const bool keep = lane < m && !(mutual && nn < lane);
+        const uint32_t keeps = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();  // every lane has read the list before it is rewritten
+        if (keep) {
+            const uint32_t at = __popc(keeps & below);
+            W.lo[at] = lo, W.hi[at] = hi;
+        }
+        // the lanes take the compacted clusters in order
+        const uint32_t src = __fns(keeps, 0, (int)lane + 1);  // lane of the (lane+1)-th set bit
+        word = __shfl_sync(0xffffffffu, word, src & 31u);
+        m = __popc(keeps);
+        __syncwarp();
+        lo = W.lo[lane], hi = W.hi[lane];
+        if (lane >= m) word = kInvalid;
+    }
+    if (p == 0) {
+        if (lane == 0) C.parents[0] = kInvalid;
+        return;
+    }
+    const uint32_t fp = __ldcg(C.first + p);
+    if (lane < m) {
+        C.clusters[2 * (size_t)(fp + lane)] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(word));
+        C.clusters[2 * (size_t)(fp + lane) + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+    }
+    if (lane + 1 < m) C.freeIds[fp + lane] = W.freeIds[nextFree + lane];
+    if (lane == 0) C.count[p] = m;
+}
+
+// Leaves [begin, end) of the build: one thread per leaf walks up the LBVH. A thread that
+// arrives second at a node (its sibling's list is complete) queues the node; the warp
+// then processes its queued nodes one after another (clusterNode) and those threads walk
+// on. Every thread of the block calls this (the warp-wide steps need whole warps).
+// lists: one ClusterWarpList per warp of the block.
+static __device__ __noinline__ void clusterRange(const ClusterParams& C, uint32_t begin, uint32_t end,
+                                          ClusterWarpList* lists) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    ClusterWarpList& W = lists[warp];
+    for (uint32_t base = begin + (threadIdx.x & ~31u); base < end; base += blockDim.x) {
+        const uint32_t k = base + lane;
+        uint32_t cur = C.n - 1 + k;  // the last node this thread finished (first its leaf)
+        bool walking = k < end;
+        for (;;) {
+            uint32_t pending = kInvalid;
+            if (walking) {
+                const uint32_t pe = __ldcg(C.topoParent + cur);
+                if (pe == kInvalid) {
+                    walking = false;  // cur was the root
+                } else {
+                    // acquire-release at GPU scope: releases this warp's list of cur, acquires
+                    // the sibling's when this thread arrives second
+                    uint32_t prev;
+                    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                                 : "=r"(prev)
+                                 : "l"(C.flags + (pe >> 1))
+                                 : "memory");
+                    if (prev == 0)
+                        walking = false;  // the sibling's thread will take the node
+                    else
+                        pending = pe >> 1;
+                }
+            }
+            if (!__any_sync(0xffffffffu, walking)) break;
+            for (uint32_t ready = __ballot_sync(0xffffffffu, pending != kInvalid); ready; ready &= ready - 1) {
+                const uint32_t leader = (uint32_t)__ffs(ready) - 1u;
+                const uint32_t p = __shfl_sync(0xffffffffu, pending, (int)leader);
+                __syncwarp();  // the leader's acquire orders the other lanes' loads too
+                clusterNode(C, p, W);
+                __threadfence();  // this warp's list of p before the leader's next arrival
+                __syncwarp();
+                if (lane == leader) cur = p;
+            }
+        }
+    }
+}
+
+}  // namespace grt

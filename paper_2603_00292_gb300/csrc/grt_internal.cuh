@@ -145,6 +145,8 @@ struct FuncTableObject {
     uint32_t userEntries = 0;        // how many do (libgrt.so's own traces reject such a table)
 };
 FuncTableObject* findFuncTable(grtFuncTable t);
+// Whether geometry o was created with GRT_BUILD_CLUSTER_SUBTREES (build.cu).
+bool buildsBySubtreeClustering(const BvhObject* o);
 
 // Build-time temporary layout.
 struct BuildLayout {

@@ -172,10 +172,11 @@ __device__ __forceinline__ int commonPrefix(const K* __restrict__ keys, int n, i
 //
 // With sChild / sParent (a single-block build) the child words and parent entries are
 // also written to those shared-memory copies.
+// Internal node i's child words (leaf bit on leaf children) and the start of its leaf
+// range (Karras 2012: direction, range end, split).
 template <bool CG, typename K>
-__device__ __forceinline__ void karrasNode(const K* __restrict__ keys, int n, int i, float4* __restrict__ nodes,
-                                           uint32_t* __restrict__ parents, uint2* sChild = nullptr,
-                                           uint32_t* sParent = nullptr) {
+__device__ __forceinline__ void karrasSplit(const K* __restrict__ keys, int n, int i, uint32_t& left, uint32_t& right,
+                                            int& first) {
     const int d = (commonPrefix<CG>(keys, n, i, i + 1) - commonPrefix<CG>(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     const int dmin = commonPrefix<CG>(keys, n, i, i - d);
     int lmax = 2;
@@ -193,8 +194,18 @@ __device__ __forceinline__ void karrasNode(const K* __restrict__ keys, int n, in
     } while (t > 1);
     const int gamma = i + s * d + min(d, 0);
     const int lo = min(i, j), hi = max(i, j);
-    const uint32_t left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
-    const uint32_t right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
+    left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
+    right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
+    first = lo;
+}
+
+template <bool CG, typename K>
+__device__ __forceinline__ void karrasNode(const K* __restrict__ keys, int n, int i, float4* __restrict__ nodes,
+                                           uint32_t* __restrict__ parents, uint2* sChild = nullptr,
+                                           uint32_t* sParent = nullptr) {
+    uint32_t left, right;
+    int first;
+    karrasSplit<CG>(keys, n, i, left, right, first);
     nodes[4 * (size_t)i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.f, 0.f);
     const uint32_t leafBase = (uint32_t)n - 1u;
     const uint32_t pl = (left & kLeafBit) ? leafBase + (left & ~kLeafBit) : left;

@@ -44,15 +44,18 @@ def _bvh_arrays(g):
     return nodes, leaves, parents, wide
 
 
-def _run(gpu, work, opts, morton_bits=None):
-    """The batch over `work`, and the same scenes built and traced one by one."""
+def _run(gpu, work, opts, morton_bits=None, build_flags=None):
+    """The batch over `work`, and the same scenes built and traced one by one (each
+    geometry of both created with build_flags(k), default the linear BVH)."""
     batched, single = [], []
     for k, (s, rays) in enumerate(work):
         bits = 0 if morton_bits is None else morton_bits(k)
+        flags = 0 if build_flags is None else build_flags(k)
         v, i = device_tensor(s.mesh.vertices), device_tensor(s.mesh.indices)
         r = device_tensor(rays)
-        batched.append((Geometry(gpu, vertices=v, indices=i, morton_bits=bits), r, new_hits(rays.shape[0])))
-        g = Geometry(gpu, vertices=v, indices=i, morton_bits=bits).build()
+        batched.append((Geometry(gpu, vertices=v, indices=i, morton_bits=bits, build_flags=flags), r,
+                        new_hits(rays.shape[0])))
+        g = Geometry(gpu, vertices=v, indices=i, morton_bits=bits, build_flags=flags).build()
         h = new_hits(rays.shape[0])
         grt.grtTraceClosest(gpu.handle, None, g.handle, r, rays.shape[0], h)
         single.append((g, h))
@@ -156,3 +159,28 @@ def test_expired_wait_latches_timeout_and_the_context_stays_usable(gpu):
     stalled.close()
     B, batched, single = _run(gpu, work, grt.batch_options())
     _assert_identical(batched, single)
+
+
+def test_batch_with_subtree_clustered_scenes(gpu):
+    """Every other geometry created with GRT_BUILD_CLUSTER_SUBTREES (small and
+    multi-item, 30- and 63-bit codes): the batch builds those by the clustering phases
+    and the rest as linear BVHs; every geometry and hit record identical to the
+    per-scene build and trace with the same flag, and the clustered per-scene builds
+    bit-exact against the oracle."""
+    from test_gpu_build import check_bit_exact
+
+    work = _workload(20, nmax=120_000, rmax=30_000, seed=scenegen.MASTER_SEED + 5)
+    cl = grt.GRT_BUILD_CLUSTER_SUBTREES
+    B, batched, single = _run(gpu, work, grt.batch_options(), morton_bits=lambda k: 63 if k % 7 == 2 else 0,
+                              build_flags=lambda k: cl if k % 2 == 0 else 0)
+    info = B.info()
+    assert info.sceneCount == 20 and info.smallScenes < 10  # clustered scenes never take the one-block path
+    _assert_identical(batched, single)
+    sizes = [w[0].mesh.indices.shape[0] for w in work]
+    clustered = [k for k in range(20) if k % 2 == 0]
+    for k in (min(clustered, key=lambda k: sizes[k]), max(clustered, key=lambda k: sizes[k]), 2):
+        s = work[k][0]
+        bits = grt.grtGetBvhInfo(gpu.handle, geom=single[k][0].handle).mortonBits
+        check_bit_exact(single[k][0], dict(vertices=s.mesh.vertices, indices=s.mesh.indices), bits, subtree=True)
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+    B.close()

@@ -70,16 +70,18 @@ def check_wide(info, ref):
     assert np.array_equal(np.stack([w[:, 4:8], w[:, 12:16], w[:, 20:24]], axis=2), hi), "wide hi"
 
 
-def check_bit_exact(g, case, bits, radius: int = 0):
+def check_bit_exact(g, case, bits, radius: int = 0, subtree: bool = False):
     """The built geometry `g` of `case` equals the oracle's build bit for bit (the LBVH,
-    or with radius > 0 the clustering build of that search radius): sorted Morton codes
-    and order (from the build temporary), topology, child boxes, parent links and leaf
-    records."""
+    with radius > 0 the clustering build of that search radius, with subtree the
+    clustering inside the LBVH's subtrees): sorted Morton codes and order (from the build
+    temporary), topology, child boxes, parent links and leaf records."""
     torch.cuda.synchronize()
     info = g.info()
     n = info.primCount
     lo, hi, cen = _oracle_for(case)
-    if radius:
+    if subtree:
+        ref = oracle.subtree_cluster(lo, hi, cen, 10 if bits == 30 else 21, grt.CLUSTER_CAP)
+    elif radius:
         ref = oracle.ploc(lo, hi, cen, 10 if bits == 30 else 21, radius)
     else:
         ref = oracle.lbvh(lo, hi, cen, 10 if bits == 30 else 21)

@@ -186,11 +186,13 @@ def test_flag_validation(gpu):
                              None, g.handle)
     assert e.value.code == grt.GRT_ERROR_INVALID_PARAMETER
     with pytest.raises(grt.GrtError) as e:
-        grt.grtGetGeometryBuildTemporaryBufferSize(gpu.handle, g.input, grt.build_options(0, 3))
+        grt.grtGetGeometryBuildTemporaryBufferSize(gpu.handle, g.input, grt.build_options(0, 4))
     assert e.value.code == grt.GRT_ERROR_INVALID_PARAMETER
     fast = grt.grtGetGeometryBuildTemporaryBufferSize(gpu.handle, g.input, grt.build_options(0, 0))
     bal = grt.grtGetGeometryBuildTemporaryBufferSize(gpu.handle, g.input, grt.build_options(0, 1))
-    assert bal >= fast + 68 * m.indices.shape[0]
+    sub = grt.grtGetGeometryBuildTemporaryBufferSize(gpu.handle, g.input,
+                                                     grt.build_options(0, grt.GRT_BUILD_CLUSTER_SUBTREES))
+    assert bal >= fast + 68 * m.indices.shape[0] and sub >= fast + 64 * m.indices.shape[0]
     g.close()
 
 
