@@ -56,10 +56,9 @@ struct BatchSceneDev : BlockBuild {
     // subtree clustering scratch (cluster.cuh)
     uint2* topoChild;
     uint32_t* topoParent;
-    uint32_t* topoFirst;
+    uint4* topoRecord;
     float4* clusters;
     uint32_t* freeIds;
-    uint32_t* clusterCount;
     uint32_t* clusterFlags;
 };
 
@@ -70,10 +69,9 @@ __device__ __forceinline__ ClusterParams clusterParamsOf(const BatchSceneDev& S)
     C.sortedPrims = S.vals[S.passes & 1u];
     C.topoChild = S.topoChild;
     C.topoParent = S.topoParent;
-    C.first = S.topoFirst;
+    C.record = S.topoRecord;
     C.clusters = S.clusters;
     C.freeIds = S.freeIds;
-    C.count = S.clusterCount;
     C.flags = S.clusterFlags;
     C.nodes = S.nodes;
     C.parents = S.parents;
@@ -81,16 +79,14 @@ __device__ __forceinline__ ClusterParams clusterParamsOf(const BatchSceneDev& S)
     return C;
 }
 
-// Emission of a clustered scene: the LBVH topology of internal nodes [begin, end) into
-// the scratch (keys written by other blocks: L2 loads), arrival counters zeroed.
+// Emission of a clustered scene: the leaf clusters of sorted positions [begin, end) and
+// the LBVH topology of those internal nodes into the scratch (keys and order written by
+// other blocks: L2 loads).
 template <typename K>
 __device__ __noinline__ void clusterTopologyRange(const BatchSceneDev& S, uint32_t begin, uint32_t end) {
     const ClusterParams C = clusterParamsOf(S);
     const K* keys = static_cast<const K*>(S.keys[S.passes & 1u]);
-    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
-        karrasTopology<true>(keys, (int)i, C);
-        C.flags[i] = 0u;
-    }
+    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) karrasTopology<true>(keys, (int)i, C);
 }
 
 struct BatchItemDev {
@@ -259,7 +255,7 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
                 sortDownsweepChunk<uint32_t>(S, it.chunk, p, B.sortChunkKeys, smem);
             }
         } else if (it.phase == 3 * S.passes + 1) {
-            const uint32_t b0 = it.chunk * B.buildChunk, b1 = min(S.n - 1, b0 + B.buildChunk);
+            const uint32_t b0 = it.chunk * B.buildChunk, b1 = min(S.n - 1 + S.cluster, b0 + B.buildChunk);
             if (S.cluster) {
                 if (wide)
                     clusterTopologyRange<unsigned long long>(S, b0, b1);
@@ -406,7 +402,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         scratch += 256 + alignUp(16 * nn, 256) + 2 * alignUp(kb * nn, 256) + 2 * alignUp(4 * nn, 256) +
                    alignUp(4 * (size_t)kBlockRadix * d.sortChunks, 256) + alignUp(4 * nn, 256);
         if (d.cluster)  // LBVH child words, parent entries, range starts; clusters, numbers, counts, flags
-            scratch += 2 * alignUp(8 * nn, 256) + alignUp(4 * nn, 256) + alignUp(32 * nn, 256) + 3 * alignUp(4 * nn, 256);
+            scratch += 2 * alignUp(8 * nn, 256) + alignUp(16 * nn, 256) + alignUp(32 * nn, 256) + 2 * alignUp(4 * nn, 256);
     }
 
     // work items. Scenes go in groups of opt.sceneGroup, largest first: a group's build
@@ -423,7 +419,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (d.small) return ph == 0 ? 1u : 0u;
         if (ph == 0) return ceilDiv(d.n, opt.buildChunk);
         if (ph <= 3 * d.passes) return (ph - 1) % 3 == 1 ? 1u : d.sortChunks;
-        if (ph == 3 * d.passes + 1) return ceilDiv(d.n - 1, opt.buildChunk);
+        if (ph == 3 * d.passes + 1) return ceilDiv(d.n - 1 + d.cluster, opt.buildChunk);  // clustered: every leaf too
         if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);               // clustering walk or fit
         if (d.cluster && ph == 3 * d.passes + 3) return ceilDiv(d.n, opt.buildChunk);  // the fit after clustering
         return 0u;
@@ -501,10 +497,9 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (d.cluster) {
             d.topoChild = (uint2*)p, p += alignUp(8 * nn, 256);
             d.topoParent = (uint32_t*)p, p += alignUp(8 * nn, 256);
-            d.topoFirst = (uint32_t*)p, p += alignUp(4 * nn, 256);
+            d.topoRecord = (uint4*)p, p += alignUp(16 * nn, 256);
             d.clusters = (float4*)p, p += alignUp(32 * nn, 256);
             d.freeIds = (uint32_t*)p, p += alignUp(4 * nn, 256);
-            d.clusterCount = (uint32_t*)p, p += alignUp(4 * nn, 256);
             d.clusterFlags = (uint32_t*)p;
         }
     }

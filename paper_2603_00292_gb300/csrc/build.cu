@@ -654,9 +654,7 @@ static PlocLayout plocLayout(const BuildLayout& L, uint32_t n) {
 template <typename K>
 __global__ void clusterTopologyKernel(ClusterParams C, const K* __restrict__ sortedKeys) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i + 1 >= C.n) return;
-    karrasTopology<false>(sortedKeys, (int)i, C);
-    C.flags[i] = 0u;
+    if (i < C.n) karrasTopology<false>(sortedKeys, (int)i, C);
 }
 
 constexpr int kClusterThreads = 256;
@@ -668,21 +666,20 @@ __global__ void __launch_bounds__(kClusterThreads) clusterWalkKernel(ClusterPara
 }
 
 // Subtree-clustering scratch after the LBVH layout: the LBVH's child words, parent
-// entries and range starts, the per-position cluster and number arrays, per-node
-// counts and arrival counters (64 B per primitive).
+// entries, per-node records (leaf range, clusters passed up), the per-position cluster
+// and number arrays and arrival counters (72 B per primitive).
 struct SubtreeLayout {
-    size_t child, parent, first, clusters, freeIds, count, flags, total;
+    size_t child, parent, record, clusters, freeIds, flags, total;
 };
 static SubtreeLayout subtreeLayout(const BuildLayout& L, uint32_t n) {
     SubtreeLayout Q{};
     const size_t m = n ? n : 1;
     Q.child = alignUp(L.total, 256);
     Q.parent = Q.child + alignUp(8 * m, 256);
-    Q.first = Q.parent + alignUp(4 * 2 * m, 256);
-    Q.clusters = Q.first + alignUp(4 * m, 256);
+    Q.record = Q.parent + alignUp(4 * 2 * m, 256);
+    Q.clusters = Q.record + alignUp(16 * m, 256);
     Q.freeIds = Q.clusters + alignUp(32 * m, 256);
-    Q.count = Q.freeIds + alignUp(4 * m, 256);
-    Q.flags = Q.count + alignUp(4 * m, 256);
+    Q.flags = Q.freeIds + alignUp(4 * m, 256);
     Q.total = Q.flags + alignUp(4 * m, 256);
     return Q;
 }
@@ -699,18 +696,17 @@ static grtError launchSubtreeCluster(Context* c, BvhObject* o, const BuildLayout
     C.sortedPrims = sorted;
     C.topoChild = (uint2*)(t + Q.child);
     C.topoParent = (uint32_t*)(t + Q.parent);
-    C.first = (uint32_t*)(t + Q.first);
+    C.record = (uint4*)(t + Q.record);
     C.clusters = (float4*)(t + Q.clusters);
     C.freeIds = (uint32_t*)(t + Q.freeIds);
-    C.count = (uint32_t*)(t + Q.count);
     C.flags = (uint32_t*)(t + Q.flags);
     C.nodes = (float4*)o->nodes;
     C.parents = (uint32_t*)o->parents;
     C.error = &workspace(c)->error;
     if (o->mortonBits == 30)
-        clusterTopologyKernel<uint32_t><<<ceilDiv(n - 1, 256), 256, 0, s>>>(C, (const uint32_t*)sortedKeys);
+        clusterTopologyKernel<uint32_t><<<ceilDiv(n, 256), 256, 0, s>>>(C, (const uint32_t*)sortedKeys);
     else
-        clusterTopologyKernel<unsigned long long><<<ceilDiv(n - 1, 256), 256, 0, s>>>(
+        clusterTopologyKernel<unsigned long long><<<ceilDiv(n, 256), 256, 0, s>>>(
             C, (const unsigned long long*)sortedKeys);
     GRT_LAUNCH_CHECK();
     clusterWalkKernel<<<ceilDiv(n, kClusterThreads), kClusterThreads, 0, s>>>(C);

@@ -25,6 +25,12 @@
 // {hi.xyz, 0}), its unused numbers likewise, so siblings never overlap. Merges write the
 // final child words (row 3 of the binary node) and parent links; the fit computes the
 // boxes and 4-wide nodes afterwards.
+//
+// Small subtrees are not processed. A node of at most kClusterCap leaves never merges,
+// so its list is its leaves in order, and its unused numbers are all its subtree's: in
+// Karras's numbering a subtree over leaves [f, l] holds the internal nodes [f, l] minus
+// one end, l when its root is numbered f (a right child, or the root) and f when it is
+// numbered l (a left child). The first node above such a subtree reads both directly.
 #pragma once
 
 #include "lbvh.cuh"
@@ -39,28 +45,37 @@ struct ClusterParams {
     uint32_t n;
     const uint32_t* sortedPrims;  // sorted position -> primitive ID
     uint2* topoChild;             // LBVH child words per internal node
-    uint32_t* topoParent;         // LBVH parent entry (parent << 1 | side) per node, internal then leaves
-    uint32_t* first;              // start of each internal node's leaf range
+    uint32_t* topoParent;         // LBVH parent entry per node, internal then leaves: parent << 2, bit 1
+                                  // set when the parent has more than kClusterCap leaves, bit 0 the side
+    uint4* record;                // per internal node: leaf range first, last; clusters passed up
     float4* clusters;             // 2 float4 per leaf position
     uint32_t* freeIds;            // per leaf position
-    uint32_t* count;              // clusters passed up by each internal node
     uint32_t* flags;              // arrival counters per internal node (zeroed)
     float4* nodes;                // output: child words in row 3 of each binary node
     uint32_t* parents;            // output: parent links
     uint32_t* error;              // the context's device error word
 };
 
-// Internal node i of the LBVH into the temporary topology arrays.
+// Position i (0..n-1) of the sorted leaves: its cluster (box and leaf word), and for
+// i < n-1 internal node i of the LBVH into the temporary topology arrays, its arrival
+// counter zeroed.
 template <bool CG, typename K>
 __device__ __forceinline__ void karrasTopology(const K* __restrict__ keys, int i, const ClusterParams& C) {
+    float3 v[3];
+    const Box3 b = primBox(C.src, CG ? __ldcg(C.sortedPrims + i) : C.sortedPrims[i], v);
+    C.clusters[2 * (size_t)i] = make_float4(b.lo.x, b.lo.y, b.lo.z, __uint_as_float(kLeafBit | (uint32_t)i));
+    C.clusters[2 * (size_t)i + 1] = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
+    if ((uint32_t)i + 1 >= C.n) return;
     uint32_t left, right;
-    int first;
-    karrasSplit<CG>(keys, (int)C.n, i, left, right, first);
+    int first, last;
+    karrasSplit<CG>(keys, (int)C.n, i, left, right, first, &last);
     C.topoChild[i] = make_uint2(left, right);
-    C.first[i] = (uint32_t)first;
-    C.topoParent[plocSlot(left, C.n)] = ((uint32_t)i << 1) | 0u;
-    C.topoParent[plocSlot(right, C.n)] = ((uint32_t)i << 1) | 1u;
+    C.record[i] = make_uint4((uint32_t)first, (uint32_t)last, 0u, 0u);
+    const uint32_t big = (i == 0 || (uint32_t)(last - first) + 1u > kClusterCap) ? 2u : 0u;
+    C.topoParent[plocSlot(left, C.n)] = ((uint32_t)i << 2) | big | 0u;
+    C.topoParent[plocSlot(right, C.n)] = ((uint32_t)i << 2) | big | 1u;
     if (i == 0) C.topoParent[0] = kInvalid;
+    C.flags[i] = 0u;
 }
 
 // A warp's working list in shared memory: boxes and words of up to 32 clusters, the
@@ -75,10 +90,21 @@ struct ClusterWarpList {
 static __device__ __noinline__ void clusterNode(const ClusterParams& C, uint32_t p, ClusterWarpList& W) {
     const uint32_t lane = threadIdx.x & 31u, below = (1u << lane) - 1u, n = C.n;
     const uint2 ch = __ldcg(C.topoChild + p);
-    const bool leafA = (ch.x & kLeafBit) != 0, leafB = (ch.y & kLeafBit) != 0;
-    const uint32_t fa = leafA ? (ch.x & ~kLeafBit) : __ldcg(C.first + ch.x);
-    const uint32_t fb = leafB ? (ch.y & ~kLeafBit) : __ldcg(C.first + ch.y);
-    const uint32_t na = leafA ? 1u : __ldcg(C.count + ch.x), nb = leafB ? 1u : __ldcg(C.count + ch.y);
+    // each child: its leaf range, whether it was processed (more than kClusterCap
+    // leaves), its cluster count and the number of the unprocessed subtree's end that
+    // is not one of its internal nodes
+    uint32_t f[2], cnt[2], skip[2];
+    bool small[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint32_t w = c ? ch.y : ch.x;
+        const uint4 r = (w & kLeafBit) ? make_uint4(w & ~kLeafBit, w & ~kLeafBit, 0u, 0u) : __ldcg(C.record + w);
+        f[c] = r.x;
+        small[c] = r.y - r.x + 1u <= kClusterCap;
+        cnt[c] = small[c] ? r.y - r.x + 1u : r.z;
+        skip[c] = w == r.x ? r.y : r.x;
+    }
+    const uint32_t na = cnt[0], nb = cnt[1];
     if (na - 1u >= kClusterCap || nb - 1u >= kClusterCap) {  // never, given complete child lists
         if (lane == 0) latchError(C.error, GRT_ERROR_INTERNAL);
         return;
@@ -87,31 +113,25 @@ static __device__ __noinline__ void clusterNode(const ClusterParams& C, uint32_t
     // this lane's cluster (lanes below m)
     float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
     uint32_t word = kInvalid;
-    if (lane < m) {
-        const bool inA = lane < na;
-        const bool isLeaf = inA ? leafA : leafB;
-        if (isLeaf) {
-            const uint32_t k = inA ? fa : fb;
-            float3 v[3];
-            const Box3 b = primBox(C.src, __ldcg(C.sortedPrims + k), v);
-            lo = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f), hi = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
-            word = kLeafBit | k;
-        } else {
-            const uint32_t pos = inA ? fa + lane : fb + (lane - na);
-            lo = __ldcg(C.clusters + 2 * (size_t)pos), hi = __ldcg(C.clusters + 2 * (size_t)pos + 1);
-            word = __float_as_uint(lo.w);
-        }
+    if (lane < m) {  // a small subtree's positions still hold its leaves' clusters
+        const uint32_t pos = lane < na ? f[0] + lane : f[1] + (lane - na);
+        lo = __ldcg(C.clusters + 2 * (size_t)pos), hi = __ldcg(C.clusters + 2 * (size_t)pos + 1);
+        word = __float_as_uint(lo.w);
     }
     // unused numbers: the children's, then p; ranked descending (all distinct)
     const uint32_t nfree = m - 1;
     uint32_t fid = 0;
     if (lane < nfree) {
-        if (lane < na - 1)
-            fid = __ldcg(C.freeIds + fa + lane);
-        else if (lane < na - 1 + nb - 1)
-            fid = __ldcg(C.freeIds + fb + (lane - (na - 1)));
-        else
+        const int c = lane < na - 1 ? 0 : (lane < na - 1 + nb - 1 ? 1 : 2);
+        if (c == 2) {
             fid = p;
+        } else {
+            const uint32_t j = c ? lane - (na - 1) : lane;
+            if (small[c])  // the subtree's range without its non-internal end
+                fid = f[c] + j + (f[c] + j >= skip[c] ? 1u : 0u);
+            else
+                fid = __ldcg(C.freeIds + f[c] + j);
+        }
     }
     uint32_t rank = 0;
     for (uint32_t j = 0; j < 32; ++j) {
@@ -126,11 +146,13 @@ static __device__ __noinline__ void clusterNode(const ClusterParams& C, uint32_t
     while (m > target) {
         // nearest neighbour of this lane's cluster among the m of the list
         PlocBest best{0u, 0u, kInvalid, false};
-        if (lane < m)
+        if (lane < m) {
+#pragma unroll 4
             for (uint32_t j = 0; j < m; ++j) {
-                if (j == lane) continue;
-                plocConsider(best, lane, j, __float_as_uint(plocUnionArea(lo, hi, W.lo[j], W.hi[j])));
+                const float4 blo = W.lo[j], bhi = W.hi[j];
+                if (j != lane) plocConsider(best, lane, j, __float_as_uint(plocUnionArea(lo, hi, blo, bhi)));
             }
+        }
         const uint32_t nn = best.j;
         const uint32_t back = __shfl_sync(0xffffffffu, nn, nn & 31u);
         const bool mutual = lane < m && back == lane;
@@ -167,13 +189,13 @@ static __device__ __noinline__ void clusterNode(const ClusterParams& C, uint32_t
         if (lane == 0) C.parents[0] = kInvalid;
         return;
     }
-    const uint32_t fp = __ldcg(C.first + p);
+    const uint32_t fp = __ldcg(C.record + p).x;
     if (lane < m) {
         C.clusters[2 * (size_t)(fp + lane)] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(word));
         C.clusters[2 * (size_t)(fp + lane) + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
     }
     if (lane + 1 < m) C.freeIds[fp + lane] = W.freeIds[nextFree + lane];
-    if (lane == 0) C.count[p] = m;
+    if (lane == 0) C.record[p].z = m;
 }
 
 // Leaves [begin, end) of the build: one thread per leaf walks up the LBVH. A thread that
@@ -191,23 +213,27 @@ static __device__ __noinline__ void clusterRange(const ClusterParams& C, uint32_
         bool walking = k < end;
         for (;;) {
             uint32_t pending = kInvalid;
-            if (walking) {
+            while (walking) {
                 const uint32_t pe = __ldcg(C.topoParent + cur);
                 if (pe == kInvalid) {
                     walking = false;  // cur was the root
-                } else {
-                    // acquire-release at GPU scope: releases this warp's list of cur, acquires
-                    // the sibling's when this thread arrives second
-                    uint32_t prev;
-                    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
-                                 : "=r"(prev)
-                                 : "l"(C.flags + (pe >> 1))
-                                 : "memory");
-                    if (prev == 0)
-                        walking = false;  // the sibling's thread will take the node
-                    else
-                        pending = pe >> 1;
+                    break;
                 }
+                // acquire-release at GPU scope: releases this warp's list of cur (the
+                // warp's stores come before it through the warp barrier after
+                // clusterNode), acquires the sibling's when this thread arrives second
+                const uint32_t p = pe >> 2;
+                uint32_t prev;
+                asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(C.flags + p) : "memory");
+                if (prev == 0) {
+                    walking = false;  // the sibling's thread will take the node
+                    break;
+                }
+                if (pe & 2u) {
+                    pending = p;  // the warp processes it
+                    break;
+                }
+                cur = p;  // a small subtree: nothing to do, walk on
             }
             if (!__any_sync(0xffffffffu, walking)) break;
             for (uint32_t ready = __ballot_sync(0xffffffffu, pending != kInvalid); ready; ready &= ready - 1) {
@@ -215,8 +241,7 @@ static __device__ __noinline__ void clusterRange(const ClusterParams& C, uint32_
                 const uint32_t p = __shfl_sync(0xffffffffu, pending, (int)leader);
                 __syncwarp();  // the leader's acquire orders the other lanes' loads too
                 clusterNode(C, p, W);
-                __threadfence();  // this warp's list of p before the leader's next arrival
-                __syncwarp();
+                __syncwarp();  // every lane's stores of p's list before the leader's next arrival
                 if (lane == leader) cur = p;
             }
         }

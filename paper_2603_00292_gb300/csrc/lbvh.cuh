@@ -172,11 +172,11 @@ __device__ __forceinline__ int commonPrefix(const K* __restrict__ keys, int n, i
 //
 // With sChild / sParent (a single-block build) the child words and parent entries are
 // also written to those shared-memory copies.
-// Internal node i's child words (leaf bit on leaf children) and the start of its leaf
-// range (Karras 2012: direction, range end, split).
+// Internal node i's child words (leaf bit on leaf children) and its leaf range [first,
+// last] (Karras 2012: direction, range end, split).
 template <bool CG, typename K>
 __device__ __forceinline__ void karrasSplit(const K* __restrict__ keys, int n, int i, uint32_t& left, uint32_t& right,
-                                            int& first) {
+                                            int& first, int* last = nullptr) {
     const int d = (commonPrefix<CG>(keys, n, i, i + 1) - commonPrefix<CG>(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     const int dmin = commonPrefix<CG>(keys, n, i, i - d);
     int lmax = 2;
@@ -197,6 +197,7 @@ __device__ __forceinline__ void karrasSplit(const K* __restrict__ keys, int n, i
     left = (lo == gamma) ? (kLeafBit | (uint32_t)gamma) : (uint32_t)gamma;
     right = (hi == gamma + 1) ? (kLeafBit | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
     first = lo;
+    if (last) *last = hi;
 }
 
 template <bool CG, typename K>
