@@ -62,6 +62,13 @@ struct BatchSceneDev : BlockBuild {
     uint32_t* clusterFlags;
 };
 
+// Leaves per thread of a clustering-walk item. A walk item is much smaller than the
+// other build items: its per-leaf work is the merging of up to 32 clusters at every
+// node of more than 16 leaves that the leaf's thread reaches last, done by a whole
+// warp, and a large item would keep one block busy long after the rest of its scene's
+// walk has finished, holding up the scene's fit and trace items.
+constexpr uint32_t kWalkLeavesPerThread = 4;
+
 __device__ __forceinline__ ClusterParams clusterParamsOf(const BatchSceneDev& S) {
     ClusterParams C{};
     C.src = S.src;
@@ -267,8 +274,8 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
                 karrasRange<uint32_t>(S, b0, b1);
             }
         } else if (S.cluster && it.phase == 3 * S.passes + 2) {
-            const uint32_t b0 = it.chunk * B.buildChunk;
-            clusterRange(clusterParamsOf(S), b0, min(S.n, b0 + B.buildChunk), reinterpret_cast<ClusterWarpList*>(smem));
+            const uint32_t w = kWalkLeavesPerThread * blockDim.x, b0 = it.chunk * w;
+            clusterRange(clusterParamsOf(S), b0, min(S.n, b0 + w), reinterpret_cast<ClusterWarpList*>(smem));
         } else if (it.phase == 3 * S.passes + 2 + S.cluster) {
             const uint32_t b0 = it.chunk * B.buildChunk;
             fitRange(S, b0, min(S.n, b0 + B.buildChunk));
@@ -420,7 +427,8 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (ph == 0) return ceilDiv(d.n, opt.buildChunk);
         if (ph <= 3 * d.passes) return (ph - 1) % 3 == 1 ? 1u : d.sortChunks;
         if (ph == 3 * d.passes + 1) return ceilDiv(d.n - 1 + d.cluster, opt.buildChunk);  // clustered: every leaf too
-        if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);               // clustering walk or fit
+        if (d.cluster && ph == 3 * d.passes + 2) return ceilDiv(d.n, kWalkLeavesPerThread * opt.blockSize);
+        if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);  // the fit
         if (d.cluster && ph == 3 * d.passes + 3) return ceilDiv(d.n, opt.buildChunk);  // the fit after clustering
         return 0u;
     };

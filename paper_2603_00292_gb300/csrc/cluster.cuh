@@ -78,11 +78,14 @@ __device__ __forceinline__ void karrasTopology(const K* __restrict__ keys, int i
     C.flags[i] = 0u;
 }
 
-// A warp's working list in shared memory: boxes and words of up to 32 clusters, the
-// node's unused numbers in descending order.
+// A warp's working list in shared memory: boxes of up to 32 clusters, the node's unused
+// numbers in descending order, and the union-area bits of every pair of slots (rows
+// padded to 36 words: the lanes' row loads, row writes and mirrored writes are free of
+// bank conflicts).
 struct ClusterWarpList {
     float4 lo[32], hi[32];
     uint32_t freeIds[32];
+    uint32_t dist[32][36];
 };
 
 // The warp (all 32 lanes) turns LBVH node p's children's lists into p's, merging as
@@ -141,26 +144,74 @@ static __device__ __noinline__ void clusterNode(const ClusterParams& C, uint32_t
     if (lane < nfree) W.freeIds[rank] = fid;
     W.lo[lane] = lo, W.hi[lane] = hi;
     __syncwarp();
+    // Distances. The list keeps its slots: a merged cluster stays in its lower slot, the
+    // other slot is retired, so the slots' order is the list's order and a cluster's
+    // position is the number of live slots below it. The warp holds the union-area bits
+    // of every pair of live slots (retired slots and the diagonal at the largest key).
+    // The area is symmetric bit for bit, so each lane computes half its row and writes
+    // both entries; after a round only the merged clusters' rows are recomputed.
+    uint32_t alive = m == 32 ? ~0u : (1u << m) - 1u;
+    for (uint32_t k = 1; k <= 16; ++k) {
+        const uint32_t t = (lane + k) & 31u;
+        const float4 blo = W.lo[t], bhi = W.hi[t];
+        const uint32_t bits = lane < m && t < m ? __float_as_uint(plocUnionArea(lo, hi, blo, bhi)) : ~0u;
+        W.dist[lane][t] = bits;
+        W.dist[t][lane] = bits;
+    }
+    W.dist[lane][lane] = ~0u;
+    __syncwarp();
+    // nearest neighbour of this lane's cluster: the lowest slot of the smallest bits,
+    // and whether another slot has the same bits (then the pair hash decides, below)
+    uint32_t nn = 0, nnBits = ~0u;
+    bool tie = false;
+    auto consider = [&](uint32_t bits, uint32_t t) {
+        tie = bits == nnBits ? true : (bits < nnBits ? false : tie);
+        nn = bits < nnBits ? t : nn;
+        nnBits = min(bits, nnBits);
+    };
+    auto scanRow = [&]() {
+        nn = 0, nnBits = ~0u, tie = false;
+        const uint32_t chunks = (35u - __clz(alive)) >> 2;  // slots below the highest live one
+        for (uint32_t c = 0; c < chunks; ++c) {
+            const uint4 v = *reinterpret_cast<const uint4*>(&W.dist[lane][4 * c]);
+            consider(v.x, 4 * c), consider(v.y, 4 * c + 1), consider(v.z, 4 * c + 2), consider(v.w, 4 * c + 3);
+        }
+    };
+    // equal smallest bits (frequent where one cluster's box holds others): among the
+    // slots of those bits, in list order, the clustering order decides (pair hash of the
+    // positions, then the lower position)
+    auto breakTies = [&]() {
+        const bool mine = tie && ((alive >> lane) & 1u);
+        if (!__any_sync(0xffffffffu, mine) || !mine) return;
+        const uint32_t ps = __popc(alive & below), chunks = (35u - __clz(alive)) >> 2;
+        uint32_t bestHash = ~0u, bestT = kInvalid;
+        for (uint32_t c = 0; c < chunks; ++c) {
+            const uint4 v = *reinterpret_cast<const uint4*>(&W.dist[lane][4 * c]);
+            const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (uint32_t i = 0; i < 4; ++i) {
+                if (e[i] != nnBits) continue;
+                const uint32_t t = 4 * c + i, pt = __popc(alive & ((1u << t) - 1u));
+                const uint32_t h = pt < ps ? plocPairHash(pt, ps) : plocPairHash(ps, pt);
+                if (bestT == kInvalid || h < bestHash) bestHash = h, bestT = t;
+            }
+        }
+        nn = bestT;
+    };
+    if (lane < m) scanRow();
+    breakTies();
     uint32_t nextFree = 0;
     const uint32_t target = p == 0 ? 1u : kClusterCap;
     while (m > target) {
-        // nearest neighbour of this lane's cluster among the m of the list
-        PlocBest best{0u, 0u, kInvalid, false};
-        if (lane < m) {
-#pragma unroll 4
-            for (uint32_t j = 0; j < m; ++j) {
-                const float4 blo = W.lo[j], bhi = W.hi[j];
-                if (j != lane) plocConsider(best, lane, j, __float_as_uint(plocUnionArea(lo, hi, blo, bhi)));
-            }
-        }
-        const uint32_t nn = best.j;
+        const bool live = (alive >> lane) & 1u;
         const uint32_t back = __shfl_sync(0xffffffffu, nn, nn & 31u);
-        const bool mutual = lane < m && back == lane;
+        const bool mutual = live && back == lane;
         const bool lead = mutual && lane < nn;
         const uint32_t leads = __ballot_sync(0xffffffffu, lead);
+        const uint32_t gone = __ballot_sync(0xffffffffu, mutual && nn < lane);
         const uint32_t otherWord = __shfl_sync(0xffffffffu, word, nn & 31u);
-        const float4 olo = W.lo[nn & 31u], ohi = W.hi[nn & 31u];
-        if (lead) {
+        if (lead) {  // reads only retiring slots' boxes, writes only leading slots'
+            const float4 olo = W.lo[nn], ohi = W.hi[nn];
             const uint32_t q = W.freeIds[nextFree + __popc(leads & below)];
             C.nodes[4 * (size_t)q + 3] = make_float4(__uint_as_float(word), __uint_as_float(otherWord), 0.f, 0.f);
             C.parents[plocSlot(word, n)] = (q << 1) | 0u;
@@ -168,31 +219,38 @@ static __device__ __noinline__ void clusterNode(const ClusterParams& C, uint32_t
             lo = make_float4(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z), 0.f);
             hi = make_float4(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z), 0.f);
             word = q;
+            W.lo[lane] = lo, W.hi[lane] = hi;
         }
         nextFree += __popc(leads);
-        const bool keep = lane < m && !(mutual && nn < lane);
-        const uint32_t keeps = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();  // every lane has read the list before it is rewritten
-        if (keep) {
-            const uint32_t at = __popc(keeps & below);
-            W.lo[at] = lo, W.hi[at] = hi;
+        alive &= ~gone;
+        m -= __popc(leads);
+        if (m <= target) break;
+        __syncwarp();  // the merged boxes
+        // a lane whose neighbour merged looks again; the others compare the merged rows
+        const bool now = (alive >> lane) & 1u;
+        const bool rescan = lead || (now && (((leads | gone) >> nn) & 1u));
+        for (uint32_t g = gone; g; g &= g - 1u) W.dist[lane][__ffs(g) - 1] = ~0u;
+        for (uint32_t l = leads; l; l &= l - 1u) {
+            const uint32_t q = (uint32_t)__ffs(l) - 1u;
+            const float4 blo = W.lo[q], bhi = W.hi[q];
+            const uint32_t bits = now && lane != q ? __float_as_uint(plocUnionArea(lo, hi, blo, bhi)) : ~0u;
+            W.dist[q][lane] = bits;
+            if (lane != q) W.dist[lane][q] = bits;
+            if (now && !rescan) consider(bits, q);
         }
-        // the lanes take the compacted clusters in order
-        const uint32_t src = __fns(keeps, 0, (int)lane + 1);  // lane of the (lane+1)-th set bit
-        word = __shfl_sync(0xffffffffu, word, src & 31u);
-        m = __popc(keeps);
-        __syncwarp();
-        lo = W.lo[lane], hi = W.hi[lane];
-        if (lane >= m) word = kInvalid;
+        __syncwarp();  // the merged rows
+        if (__any_sync(0xffffffffu, rescan) && rescan) scanRow();
+        breakTies();
     }
     if (p == 0) {
         if (lane == 0) C.parents[0] = kInvalid;
         return;
     }
     const uint32_t fp = __ldcg(C.record + p).x;
-    if (lane < m) {
-        C.clusters[2 * (size_t)(fp + lane)] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(word));
-        C.clusters[2 * (size_t)(fp + lane) + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+    if ((alive >> lane) & 1u) {
+        const size_t at = fp + __popc(alive & below);
+        C.clusters[2 * at] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(word));
+        C.clusters[2 * at + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
     }
     if (lane + 1 < m) C.freeIds[fp + lane] = W.freeIds[nextFree + lane];
     if (lane == 0) C.record[p].z = m;
