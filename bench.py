@@ -74,6 +74,8 @@ def parse():
     p.add_argument("--scenes", type=int, default=256, help="batched workload: the first N soups (a smaller case)")
     p.add_argument("--no-sequential", action="store_true",
                    help="batched workload: skip the 256 sequential per-scene calls (e.g. under a profiler)")
+    p.add_argument("--no-clustered", action="store_true",
+                   help="batched workload: skip the second run with subtree-clustered builds")
     return p.parse_args()
 
 
@@ -444,15 +446,15 @@ def run_grt(args, rank, world, local):
              "rays": npix + spp * dhit, "mrays_per_s": round((npix + spp * dhit) / (ms_dc + ms_da) / 1e3, 1),
              "closest_mrays_per_s": round(npix / ms_dc / 1e3, 1),
              "ao_mrays_per_s": round(spp * dhit / ms_da / 1e3, 1)}
-    # the three build options of the terrain geometry (linear BVH, clustering with search
-    # radius 8 and 32): build time, surface-area cost of the tree (sum of internal node
-    # box areas over the root's), the closest + AO traces and the whole step over it
-    from paper_2603_00292_gb300.objects import read_device
+    # the build options of the terrain geometry (linear BVH, clustering with search
+    # radius 8 and 32, clustering inside the linear BVH's subtrees): build time,
+    # surface-area cost of the tree, the closest + AO traces and the whole step over it
     torch.cuda.synchronize()
     assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS  # the features above
     builds = {}
     for name, flags in (("fast_lbvh", grt.GRT_BUILD_PREFER_FAST), ("balanced_ploc8", grt.GRT_BUILD_PREFER_BALANCED),
-                        ("high_quality_ploc32", grt.GRT_BUILD_PREFER_HIGH_QUALITY)):
+                        ("high_quality_ploc32", grt.GRT_BUILD_PREFER_HIGH_QUALITY),
+                        ("subtree_cluster16", grt.GRT_BUILD_CLUSTER_SUBTREES)):
         gq = Geometry(ctx, vertices=verts, indices=idx, build_flags=flags).build(sh)
         sq = Scene(ctx, [gq.handle] * WORKLOAD["instances"], frames).build(sh)
         qhits = new_hits(npix)
@@ -471,12 +473,8 @@ def run_grt(args, rank, world, local):
         ms_t = timed(q_trace)
         ms_s = timed(q_step)
         torch.cuda.synchronize()
-        inf = gq.info()
-        nd = read_device(inf.nodes, inf.nodeCount * 64, np.float32).reshape(-1, 16).astype(np.float64)
-        ext = np.maximum(nd[:, [1, 5, 9]], nd[:, [3, 7, 11]]) - np.minimum(nd[:, [0, 4, 8]], nd[:, [2, 6, 10]])
-        area = ext[:, 0] * ext[:, 1] + ext[:, 1] * ext[:, 2] + ext[:, 2] * ext[:, 0]
         qhit = int((qhits[:, 1].view(torch.int32) != -1).sum().item())
-        builds[name] = {"blas_build_ms": round(ms_b, 4), "sah_cost": round(float(area.sum() / area[0]), 3),
+        builds[name] = {"blas_build_ms": round(ms_b, 4), "sah_cost": round(sah_cost(gq), 3),
                         "closest_plus_ao_ms": round(ms_t, 4), "step_ms": round(ms_s, 4),
                         "primary_hits": qhit}
         sq.close()
@@ -702,6 +700,20 @@ class StepTimer:
 
     def mean(self, name):
         return statistics.mean(self.samples[name])
+
+
+def sah_cost(geom) -> float:
+    """Surface-area cost of a built geometry's binary tree: the sum of the box areas of
+    its internal nodes over the root's (leaf costs left out; one primitive per leaf)."""
+    from paper_2603_00292_gb300.objects import read_device
+
+    inf = geom.info()
+    nd = read_device(inf.nodes, inf.nodeCount * 64, np.float32).reshape(-1, 16).astype(np.float64)
+    lo = np.minimum(nd[:, [0, 4, 8]], nd[:, [2, 6, 10]])
+    hi = np.maximum(nd[:, [1, 5, 9]], nd[:, [3, 7, 11]])
+    ext = hi - lo
+    area = ext[:, 0] * ext[:, 1] + ext[:, 1] * ext[:, 2] + ext[:, 2] * ext[:, 0]
+    return float(area.sum() / area[0]) if area[0] > 0 else 1.0
 
 
 def roofline_entry(kernel, nbytes, ms, stats=None):
@@ -1356,6 +1368,51 @@ def run_batched(args, rank, world, local):
                 "per_ray": {"nodes": round(st["nodesVisited"] / max(1, st["rays"]), 2),
                             "triangles": round(st["trianglesTested"] / max(1, st["rays"]), 2)}}
 
+    # the same work with every soup built by clustering inside the linear BVH's subtrees
+    # (the batch adds a clustering phase per scene), same launch options: batched against
+    # sequential, hit records compared, and the mean surface-area cost of both trees
+    clustered = None
+    if not args.no_clustered:
+        copt = grt.build_options(flags=grt.GRT_BUILD_CLUSTER_SUBTREES)
+        ctemp = empty_bytes(grt.grtGetGeometryBuildTemporaryBufferSize(
+            ctx.handle, grt.triangle_mesh_input(256, 256, triangle_count=nbig, vertex_count=3 * nbig), copt))
+        geo_cb, geo_cs, hits_cb, hits_cs = [], [], [], []
+        for (dv, di), r in zip(meshes, rays):
+            geo_cb.append(Geometry(ctx, vertices=dv, indices=di, temp=ctemp, build_flags=grt.GRT_BUILD_CLUSTER_SUBTREES))
+            geo_cs.append(Geometry(ctx, vertices=dv, indices=di, temp=ctemp, build_flags=grt.GRT_BUILD_CLUSTER_SUBTREES))
+            hits_cb.append(new_hits(r.shape[0]))
+            hits_cs.append(new_hits(r.shape[0]))
+        BC = Batch(ctx, list(zip(geo_cb, rays, hits_cb)), grt.batch_options(graph=True, **opts))
+
+        def sequential_clustered():
+            for g, r, h in zip(geo_cs, rays, hits_cs):
+                g.build(sh)
+                grt.grtTraceClosest(ctx.handle, None, g.handle, r, r.shape[0], h, None, None, sh)
+
+        cb_ms, cb_launches = timed(lambda: BC.run(sh))
+        if args.no_sequential:
+            sequential_clustered()
+            cs_ms = [float("nan")]
+        else:
+            cs_ms, _ = timed(sequential_clustered)
+        torch.cuda.synchronize()
+        assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+        c_ms, cseq_ms = max_over_ranks([statistics.mean(cb_ms), statistics.mean(cs_ms)], dist)
+        sah_l = [sah_cost(g) for g in geo_s]
+        sah_c = [sah_cost(g) for g in geo_cs]
+        clustered = {"build_flag": "GRT_BUILD_CLUSTER_SUBTREES", "ms": round(c_ms, 3),
+                     "sequential_ms": None if math.isnan(cseq_ms) else round(cseq_ms, 3),
+                     "speedup_vs_sequential": None if math.isnan(cseq_ms) else round(cseq_ms / c_ms, 3),
+                     "mrays_per_s": round(total_rays / (c_ms / 1e3) / 1e6, 1),
+                     "identical_to_sequential": bool(all(torch.equal(a, b) for a, b in zip(hits_cb, hits_cs))),
+                     "sah_cost_mean": round(statistics.mean(sah_c), 3),
+                     "lbvh_sah_cost_mean": round(statistics.mean(sah_l), 3),
+                     "gpu_launches": int(cb_launches)}
+        BC.close()
+        for g in geo_cb + geo_cs:
+            g.close()
+        del ctemp, hits_cb, hits_cs
+
     # end to end: meshes and rays up from pinned host memory, hit records back
     pin = [(torch.from_numpy(v).pin_memory(), torch.from_numpy(i.view(np.int32)).pin_memory(), r.cpu().pin_memory())
            for (v, i, _, _), r in zip(host, rays)]
@@ -1393,6 +1450,7 @@ def run_batched(args, rank, world, local):
             "batch": {"items": info.itemCount, "small_scenes": info.smallScenes, "blocks": info.blocks,
                       "block_size": info.blockSize, "device_bytes": int(info.deviceBytes)},
             "autotune": None if tune_report is None else {k: tune_report[k] for k in tune_report if k != "tried"},
+            "clustered": clustered,
             "roofline": roofline,
             "e2e": {"value": round(statistics.mean(e2e), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
