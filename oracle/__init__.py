@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
             L.oracle_subtree_cluster.argtypes = [P, P, i64, ctypes.c_int, P, P, P, P, P, P]
             L.oracle_sah_cost.argtypes = [P, P, i64]
             L.oracle_sah_cost.restype = ctypes.c_double
+            L.oracle_quantize_wide.argtypes = [P, P, P, i64, P]
             L.oracle_xi.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
             L.oracle_xi.restype = ctypes.c_double
             L.oracle_camera_rays.argtypes = [P, i64, i64, P]
@@ -311,6 +312,39 @@ def wide_nodes(ref):
 # ----------------------------------------------------------------------------------
 # Scenes and traces
 # ----------------------------------------------------------------------------------
+def quantized_wide_nodes(lo, hi, child) -> np.ndarray:
+    """Quantised 4-wide nodes (oracle_quantize_wide) of the wide nodes (lo, hi (m, 4, 3)
+    float32, child (m, 4) uint32) that wide_nodes returns: (m, 16) uint32 words per node,
+    p.xyz, biased exponents, the six plane words (slot j in byte j), the child words."""
+    lo, hi = _c(lo, np.float32), _c(hi, np.float32)
+    child = _c(child, np.uint32)
+    m = lo.shape[0]
+    out = np.zeros((m, 16), np.uint32)
+    if m:
+        lib().oracle_quantize_wide(_p(lo), _p(hi), _p(child), m, _p(out))
+    return out
+
+
+def dequantize_wide_nodes(q: np.ndarray):
+    """Decoded slot boxes of quantised nodes: plane = fl32(p + byte * 2^e), per axis.
+    Returns lo, hi (m, 4, 3) float32 (empty slots decode to whatever their bytes say)."""
+    q = np.asarray(q, np.uint32)
+    m = q.shape[0]
+    p = q[:, 0:3].copy().view(np.float32)  # (m, 3)
+    e = np.stack([(q[:, 3] >> (8 * a)) & 0xFF for a in range(3)], axis=1).astype(np.int32) - 127
+    step = np.ldexp(np.float32(1.0), e).astype(np.float32)  # (m, 3)
+    lo = np.zeros((m, 4, 3), np.float32)
+    hi = np.zeros((m, 4, 3), np.float32)
+    for a in range(3):
+        for j in range(4):
+            ql = ((q[:, 4 + 2 * a] >> (8 * j)) & 0xFF).astype(np.float32)
+            qh = ((q[:, 5 + 2 * a] >> (8 * j)) & 0xFF).astype(np.float32)
+            with np.errstate(over="ignore"):
+                lo[:, j, a] = p[:, a] + ql * step[:, a]
+                hi[:, j, a] = p[:, a] + qh * step[:, a]
+    return lo, hi
+
+
 class Hits:
     """Hit records in FP64: inst, prim (uint32; NONE on a miss), t (+inf on miss), u, v."""
 

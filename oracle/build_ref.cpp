@@ -428,7 +428,7 @@ void oracle_subtree_cluster(const float* leaf_lo, const float* leaf_hi, int64_t 
     parent_internal[0] = -1;
 }
 
-// Surface-area cost of a binary BVH: sum over internal nodes of box area, divided by// Surface-area cost of a binary BVH: sum over internal nodes of box area, divided by
+// Surface-area cost of a binary BVH: sum over internal nodes of box area, divided by
 // the root box area (the quality measure of Sec. 6.2 "BVH Construction").
 double oracle_sah_cost(const float* node_lo, const float* node_hi, int64_t n_internal) {
     auto area = [&](int64_t k) {
@@ -442,6 +442,85 @@ double oracle_sah_cost(const float* node_lo, const float* node_hi, int64_t n_int
     for (int64_t k = 0; k < n_internal; ++k) s += area(k);
     double r = area(0);
     return r > 0 ? s / r : 0.0;
+}
+
+// Quantised 4-wide nodes: the paper's wide trees (Sec. 6.2, branching factor 4) with
+// each child box stored as 8-bit planes relative to the node's own box, the compressed
+// wide node of Ylitie, Karras and Laine ("Efficient Incoherent Ray Traversal on GPUs
+// Through Compressed Wide BVHs", HPG 2017). Input: m wide nodes as wide_nodes gives
+// them (lo, hi: 4 slots x 3 floats each; child: 4 words, 0xFFFFFFFF = empty slot).
+// For every node and axis a, over the used slots:
+//   p_a  = the smallest slot lo_a,  H_a = the largest slot hi_a;
+//   e_a  = the least integer e in [-126, 127] with fl(p_a + 255 * 2^e) >= H_a;
+//   a slot's lower plane qlo = the largest q in [0, 255] with fl(p_a + q 2^e_a) <= lo_a,
+//   its upper plane   qhi = the smallest q in [0, 255] with fl(p_a + q 2^e_a) >= hi_a,
+// fl being float32 rounding to nearest (q 2^e is exact, so each value is rounded once).
+// Both conditions are monotone in q and e, so each choice is unique, and the decoded
+// box [fl(p + qlo 2^e), fl(p + qhi 2^e)] contains the slot's box. Output: 16 words per
+// node: p.x, p.y, p.z; the three biased exponents e_a + 127 in bytes 0-2 of word 3;
+// words 4-9 the planes qlo.x, qhi.x, qlo.y, qhi.y, qlo.z, qhi.z, slot j in byte j;
+// words 10-13 the child words; words 14-15 zero. An empty slot has qlo = 255, qhi = 0.
+// A node without a used slot has p = 0 and e = -126 on every axis.
+static float qdecode(float p, int q, int e) {
+    const float step = std::ldexp(1.0f, e);
+    const float off = (float)q * step;  // exact: q < 2^8 and step a power of two
+    return p + off;
+}
+
+void oracle_quantize_wide(const float* lo, const float* hi, const uint32_t* child, int64_t m, uint32_t* out) {
+    for (int64_t k = 0; k < m; ++k) {
+        const float* L = lo + 12 * k;  // [slot][axis]
+        const float* Hh = hi + 12 * k;
+        const uint32_t* C = child + 4 * k;
+        uint32_t* o = out + 16 * k;
+        std::memset(o, 0, 16 * sizeof(uint32_t));
+        bool used[4];
+        int nUsed = 0;
+        for (int j = 0; j < 4; ++j) nUsed += (used[j] = C[j] != 0xFFFFFFFFu);
+        uint32_t expWord = 0;
+        for (int a = 0; a < 3; ++a) {
+            float p = 0.0f, top = 0.0f;
+            if (nUsed) {
+                p = INFINITY, top = -INFINITY;
+                for (int j = 0; j < 4; ++j)
+                    if (used[j]) p = std::min(p, L[3 * j + a]), top = std::max(top, Hh[3 * j + a]);
+            }
+            // the least exponent whose 255th step reaches the top of the node's box
+            int e = -126;
+            if (nUsed) {
+                const double ext = (double)top - (double)p;
+                if (ext > 0) {
+                    int k2 = 0;
+                    std::frexp(ext / 255.0, &k2);  // ext / 255 < 2^k2
+                    e = std::max(-126, std::min(127, k2));
+                }
+                while (e > -126 && qdecode(p, 255, e - 1) >= top) --e;
+                while (e < 127 && qdecode(p, 255, e) < top) ++e;
+            }
+            uint32_t qlo = 0, qhi = 0;
+            for (int j = 0; j < 4; ++j) {
+                int ql = 255, qh = 0;
+                if (used[j]) {
+                    const float l = L[3 * j + a], h = Hh[3 * j + a];
+                    const double step = std::ldexp(1.0, e);
+                    ql = (int)std::max(0.0, std::min(255.0, std::floor(((double)l - p) / step)));
+                    while (ql > 0 && qdecode(p, ql, e) > l) --ql;
+                    while (ql < 255 && qdecode(p, ql + 1, e) <= l) ++ql;
+                    qh = (int)std::max(0.0, std::min(255.0, std::ceil(((double)h - p) / step)));
+                    while (qh < 255 && qdecode(p, qh, e) < h) ++qh;
+                    while (qh > 0 && qdecode(p, qh - 1, e) >= h) --qh;
+                }
+                qlo |= (uint32_t)ql << (8 * j);
+                qhi |= (uint32_t)qh << (8 * j);
+            }
+            std::memcpy(o + a, &p, 4);
+            expWord |= (uint32_t)(e + 127) << (8 * a);
+            o[4 + 2 * a] = qlo;
+            o[5 + 2 * a] = qhi;
+        }
+        o[3] = expWord;
+        for (int j = 0; j < 4; ++j) o[10 + j] = C[j];
+    }
 }
 
 }  // extern "C"

@@ -284,3 +284,116 @@ def test_wide_nodes_invariants(level):
         while parent[x] >= 0:
             x, d = parent[x], d + 1
         assert d % 2 == 0
+
+
+# ---------------------------------------------------------------- quantised 4-wide nodes
+def _golden_quantized(golden_dir):
+    nodes, slots = [], []
+    with open(os.path.join(golden_dir, "quantized_wide_nodes.txt")) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "slot":
+                slots.append(([float(x) for x in t[1:4]], [float(x) for x in t[4:7]], int(t[7], 16)))
+            elif t[0] == "words":
+                nodes.append((slots, [int(w, 16) for w in t[1:]]))
+                slots = []
+    return nodes
+
+
+def test_quantized_nodes_hand_derived(golden_dir):
+    """Three nodes worked by hand (tests/golden/quantized_wide_nodes.txt): an origin at 0
+    with a different exponent per axis and a flat slot, a negative origin, and planes near
+    1e6 where the float32 rounding of p + q 2^e (ties to even) decides the exponent and
+    the bytes."""
+    cases = _golden_quantized(golden_dir)
+    assert len(cases) == 3
+    for slots, words in cases:
+        lo = np.full((1, 4, 3), np.inf, np.float32)
+        hi = np.full((1, 4, 3), -np.inf, np.float32)
+        child = np.full((1, 4), oracle.NONE, np.uint32)
+        for j, (l, h, c) in enumerate(slots):
+            lo[0, j], hi[0, j], child[0, j] = l, h, c
+        got = oracle.quantized_wide_nodes(lo, hi, child)
+        assert [int(w) for w in got[0]] == words
+
+
+def _wide_of(kind, seed=0):
+    if kind == "terrain":
+        m = scenegen.terrain(cells=24, amplitude=0.2)
+        lo, hi, c = oracle.triangle_aabbs(m.vertices, m.indices)
+    elif kind == "spheres":
+        s = scenegen.spheres(3000, half=50.0, rmin=0.01, rmax=1.0, config=5)
+        b = scenegen.sphere_aabbs(s)
+        lo, hi = b[:, 0:3].copy(), b[:, 3:6].copy()
+        c = oracle.box_centroids(b)
+    elif kind == "far":  # tiny boxes far from the origin, both signs
+        rng = np.random.default_rng(seed)
+        ctr = rng.uniform(-1, 1, (800, 3)) * np.array([3e5, 1e4, 7e6]) + np.array([1e6, -5e3, 2e7])
+        ext = rng.uniform(0, 0.05, (800, 3))
+        lo, hi = (ctr - ext).astype(np.float32), (ctr + ext).astype(np.float32)
+        c = (0.5 * (lo + hi)).astype(np.float32)
+    elif kind == "flat":  # zero extent on y, boxes touching zero from both sides
+        rng = np.random.default_rng(seed)
+        x = rng.uniform(-1e-3, 1e-3, (500, 1))
+        lo = np.concatenate([x, np.zeros((500, 1)), -np.abs(x)], axis=1).astype(np.float32)
+        hi = np.concatenate([x + 1e-4, np.zeros((500, 1)), np.abs(x)], axis=1).astype(np.float32)
+        c = (0.5 * (lo + hi)).astype(np.float32)
+    else:  # clustered soup
+        m = scenegen.soup_scene(2, seed=9, nmin=3000, nmax=3000).mesh
+        lo, hi, c = oracle.triangle_aabbs(m.vertices, m.indices)
+    return oracle.wide_nodes(oracle.lbvh(lo, hi, c, 10))
+
+
+@pytest.mark.parametrize("kind", ["terrain", "spheres", "far", "flat", "soup"])
+def test_quantized_nodes_conservative_and_tight(kind):
+    """Every decoded slot box contains the slot's exact box (traversal stays
+    conservative), one step tighter on any plane would cut into it, the exponent is the
+    least that reaches the node's top, empty slots decode inverted (255 / 0) and the
+    child words are copied. The decoding here is numpy float32 arithmetic, not the
+    oracle's C code."""
+    wlo, whi, ch = _wide_of(kind, seed=3)
+    q = oracle.quantized_wide_nodes(wlo, whi, ch)
+    dlo, dhi = oracle.dequantize_wide_nodes(q)
+    used = ch != oracle.NONE
+    assert np.all(dlo[used] <= wlo[used]) and np.all(dhi[used] >= whi[used])
+    assert np.array_equal(q[:, 10:14], ch) and not q[:, 14:16].any()
+    p = q[:, 0:3].copy().view(np.float32)
+    e = np.stack([(q[:, 3] >> (8 * a)) & 0xFF for a in range(3)], axis=1).astype(np.int64) - 127
+    assert ((e >= -126) & (e <= 127)).all() and not (q[:, 3] >> 24).any()
+    m = q.shape[0]
+    for a in range(3):
+        lo_a = np.where(used, wlo[:, :, a], np.inf).min(axis=1)
+        top_a = np.where(used, whi[:, :, a], -np.inf).max(axis=1)
+        assert np.array_equal(p[:, a], lo_a.astype(np.float32))
+        dec = lambda qq, ee: (p[:, a] + np.float32(qq) * np.ldexp(np.float32(1), ee).astype(np.float32)).astype(np.float32)
+        # the least exponent: one less no longer reaches the top
+        smaller = e[:, a] > -126
+        ee = np.maximum(e[:, a] - 1, -126)
+        assert np.all(dec(255, ee)[smaller] < top_a[smaller])
+        step = np.ldexp(np.float32(1), e[:, a]).astype(np.float32)
+        for j in range(4):
+            ql = ((q[:, 4 + 2 * a] >> (8 * j)) & 0xFF).astype(np.float32)
+            qh = ((q[:, 5 + 2 * a] >> (8 * j)) & 0xFF).astype(np.float32)
+            u = used[:, j]
+            assert np.all(ql[~u] == 255) and np.all(qh[~u] == 0)
+            up = u & (ql < 255)
+            assert np.all((p[:, a] + (ql + 1) * step).astype(np.float32)[up] > wlo[up, j, a])
+            dn = u & (qh > 0)
+            assert np.all((p[:, a] + (qh - 1) * step).astype(np.float32)[dn] < whi[dn, j, a])
+    assert m == wlo.shape[0]
+
+
+def test_quantized_single_primitive_and_degenerate_node():
+    """A one-primitive geometry's node (leaf in slot 0, three empty slots) and a point
+    box: the origin is the box's corner, a zero extent takes the least exponent, and the
+    point decodes exactly."""
+    d = dict(leaf_lo=np.array([[1, 2, 3]], np.float32), leaf_hi=np.array([[4, 2, 3]], np.float32))
+    lo, hi, child = oracle.wide_nodes(d)
+    q = oracle.quantized_wide_nodes(lo, hi, child)
+    assert q[0, 0:3].view(np.float32).tolist() == [1, 2, 3]
+    assert [(int(q[0, 3]) >> (8 * a)) & 0xFF for a in range(3)] == [127 - 6, 1, 1]  # 255/64 >= 3 > 255/128
+    dlo, dhi = oracle.dequantize_wide_nodes(q)
+    assert dlo[0, 0].tolist() == [1, 2, 3] and dhi[0, 0].tolist() == [4, 2, 3]
+    assert q[0, 10] == 0x80000000 and (q[0, 11:14] == oracle.NONE).all()
