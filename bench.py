@@ -76,6 +76,8 @@ def parse():
                    help="batched workload: skip the 256 sequential per-scene calls (e.g. under a profiler)")
     p.add_argument("--no-clustered", action="store_true",
                    help="batched workload: skip the second run with subtree-clustered builds")
+    p.add_argument("--no-quantized", action="store_true",
+                   help="batched workload: skip the run with quantised 64-byte nodes")
     return p.parse_args()
 
 
@@ -454,7 +456,8 @@ def run_grt(args, rank, world, local):
     builds = {}
     for name, flags in (("fast_lbvh", grt.GRT_BUILD_PREFER_FAST), ("balanced_ploc8", grt.GRT_BUILD_PREFER_BALANCED),
                         ("high_quality_ploc32", grt.GRT_BUILD_PREFER_HIGH_QUALITY),
-                        ("subtree_cluster16", grt.GRT_BUILD_CLUSTER_SUBTREES)):
+                        ("subtree_cluster16", grt.GRT_BUILD_CLUSTER_SUBTREES),
+                        ("fast_lbvh_quantized_nodes", grt.GRT_BUILD_PREFER_FAST | grt.GRT_BUILD_QUANTIZED_NODES)):
         gq = Geometry(ctx, vertices=verts, indices=idx, build_flags=flags).build(sh)
         sq = Scene(ctx, [gq.handle] * WORKLOAD["instances"], frames).build(sh)
         qhits = new_hits(npix)
@@ -938,6 +941,41 @@ def run_spheres(args, rank, world, local):
             short_ms.append(e0.elapsed_time(e1))
     occl_short = int((hs[:, 1].view(torch.int32) != -1).sum().item())
 
+    # the same geometry with quantised 64-byte nodes (GRT_BUILD_QUANTIZED_NODES): build,
+    # closest and any hit (tmax infinite and 2.9), and how many hit records equal the
+    # 128-byte nodes' (the rest are equal-t ties)
+    geomq = Geometry(ctx, boxes=dbox, build_flags=grt.GRT_BUILD_QUANTIZED_NODES)
+    hqc, hqa, hqs = new_hits(n), new_hits(n), new_hits(n)
+    qruns = {"build": lambda: geomq.build(sh),
+             "closest": lambda: grt.grtTraceClosest(ctx.handle, None, geomq.handle, rays, n, hqc, table.handle, None, sh),
+             "any": lambda: grt.grtTraceAnyHit(ctx.handle, None, geomq.handle, rays, n, hqa, table.handle, None, sh),
+             "any_tmax_2.9": lambda: grt.grtTraceAnyHit(ctx.handle, None, geomq.handle, short, n, hqs, table.handle,
+                                                         None, sh)}
+    q_ms = {}
+    for name, fn in qruns.items():
+        vals = []
+        for k in range(3 + 5):
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 3:
+                vals.append(e0.elapsed_time(e1))
+        q_ms[name] = statistics.mean(vals)
+    torch.cuda.synchronize()
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+    quantized = {"build_ms": round(q_ms["build"], 4),
+                 "closest_ms": round(q_ms["closest"], 4), "any_ms": round(q_ms["any"], 4),
+                 "any_tmax_2.9_ms": round(q_ms["any_tmax_2.9"], 4),
+                 "closest_mrays_per_s": round(n / q_ms["closest"] / 1e3, 1),
+                 "any_mrays_per_s": round(n / q_ms["any"] / 1e3, 1),
+                 "closest_records_equal": int((hqc == hc).all(dim=1).sum().item()),
+                 "occluded_equal": int(((hqa[:, 1] != -1) == (ha[:, 1] != -1)).sum().item()),
+                 "occluded_tmax_2.9_equal": int(((hqs[:, 1] != -1) == (hs[:, 1] != -1)).sum().item()),
+                 "node_bytes": 64}
+    geomq.close()
+
     # algorithmic bytes per launch from counting passes: per ray the ray and the hit
     # record, per 4-wide node visit 112 B, per sphere test its leaf's primitive ID (4 B)
     # and its centre and radius (16 B)
@@ -985,6 +1023,7 @@ def run_spheres(args, rank, world, local):
                                   "any": round(n / T.mean("any") / 1e3, 1),
                                   "any_tmax_2.9": round(n / statistics.mean(short_ms) / 1e3, 1)},
             "occluded_tmax_2.9": occl_short,
+            "quantized_nodes": quantized,
             "build": {"ms": round(T.mean("build"), 4), "prims": prims,
                       "mprims_per_s": round(prims / T.mean("build") / 1e3, 1)},
             "kernel_ms": {k: round(T.mean(k), 4) for k in T.names},
@@ -1413,6 +1452,29 @@ def run_batched(args, rank, world, local):
             g.close()
         del ctemp, hits_cb, hits_cs
 
+    # the linear BVH with quantised 64-byte nodes (GRT_BUILD_QUANTIZED_NODES), same
+    # options: batched ms and how many hit records equal the 128-byte nodes' (the rest
+    # are equal-t ties)
+    quantized = None
+    if not args.no_quantized:
+        geo_q, hits_q = [], []
+        for (dv, di), r in zip(meshes, rays):
+            geo_q.append(Geometry(ctx, vertices=dv, indices=di, temp=temp, build_flags=grt.GRT_BUILD_QUANTIZED_NODES))
+            hits_q.append(new_hits(r.shape[0]))
+        BQ = Batch(ctx, list(zip(geo_q, rays, hits_q)), grt.batch_options(graph=True, **opts))
+        q_ms, q_launches = timed(lambda: BQ.run(sh))
+        torch.cuda.synchronize()
+        assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+        (qms,) = max_over_ranks([statistics.mean(q_ms)], dist)
+        equal = sum(int((a == b).all(dim=1).sum().item()) for a, b in zip(hits_q, hits_b))
+        quantized = {"build_flag": "GRT_BUILD_QUANTIZED_NODES", "ms": round(qms, 3),
+                     "mrays_per_s": round(total_rays / (qms / 1e3) / 1e6, 1), "records_equal": equal,
+                     "records": int(total_rays), "gpu_launches": int(q_launches)}
+        BQ.close()
+        for g in geo_q:
+            g.close()
+        del hits_q
+
     # end to end: meshes and rays up from pinned host memory, hit records back
     pin = [(torch.from_numpy(v).pin_memory(), torch.from_numpy(i.view(np.int32)).pin_memory(), r.cpu().pin_memory())
            for (v, i, _, _), r in zip(host, rays)]
@@ -1451,6 +1513,7 @@ def run_batched(args, rank, world, local):
                       "block_size": info.blockSize, "device_bytes": int(info.deviceBytes)},
             "autotune": None if tune_report is None else {k: tune_report[k] for k in tune_report if k != "tried"},
             "clustered": clustered,
+            "quantized_nodes": quantized,
             "roofline": roofline,
             "e2e": {"value": round(statistics.mean(e2e), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -139,8 +139,24 @@ typedef enum grtBuildFlags {
     GRT_BUILD_PREFER_FAST = 0,
     GRT_BUILD_PREFER_BALANCED = 1,
     GRT_BUILD_PREFER_HIGH_QUALITY = 2,
-    GRT_BUILD_CLUSTER_SUBTREES = 3
+    GRT_BUILD_CLUSTER_SUBTREES = 3,
+    GRT_BUILD_QUANTIZED_NODES = 0x100
 } grtBuildFlags;
+/* GRT_BUILD_QUANTIZED_NODES, ORed with any of the four: traversal reads 64-byte
+ * quantised 4-wide nodes instead of the 128-byte ones (the paper's wide trees, Sec. 6.2,
+ * stored compactly; the encoding of Ylitie, Karras and Laine, HPG 2017). Per node and
+ * axis, over the used slots: origin p = the least slot lo, step 2^e with e the least
+ * integer in [-126, 127] for which fl(p + 255 * 2^e) reaches the greatest slot hi;
+ * each slot's lower plane is the largest byte q with fl(p + q 2^e) <= lo, its upper
+ * plane the smallest with fl(p + q 2^e) >= hi (fl = float32 rounding to nearest), so
+ * the decoded box contains the exact one and results are those of the 128-byte nodes
+ * up to equal-t ties. Node words (16 x 32 bits): p.xyz; biased exponents e + 127 in
+ * bytes 0-2; qlo.x, qhi.x, qlo.y, qhi.y, qlo.z, qhi.z with slot j in byte j (an empty
+ * slot 255 / 0); the four child words; two zero words. The build writes them after the
+ * fit (and after each UPDATE), beside the 128-byte nodes (grtBvhInfo.quantNodes). Like
+ * the method, the bit is fixed by grtCreateGeometry; a grtBuildGeometry given options
+ * must repeat it. Scene (top-level) builds ignore it: their own nodes stay 128-byte,
+ * while instances of quantised geometries are traversed in their format. */
 
 typedef struct grtBuildOptions {
     uint32_t buildFlags; /* grtBuildFlags */
@@ -400,7 +416,7 @@ grtError grtTraceAnyHit(grtContext ctx, grtScene scene, grtGeometry geom, const 
  * kernel by value. Valid while the target, the table and the context live and the
  * target is not rebuilt with a different primitive count. */
 typedef struct grtDeviceTarget {
-    const void* nodes;            /* the target's 4-wide nodes (grtBvhInfo.wideNodes) */
+    const void* nodes;            /* the target's 4-wide nodes, in nodeFormat */
     const void* leaves;           /* triangle records / primitive IDs / instance records */
     const uint32_t* primToLeaf;   /* primitive (instance) ID -> sorted leaf position */
     const void* frames64;         /* scenes: FP64 inverse frame per instance ID, else NULL */
@@ -412,6 +428,7 @@ typedef struct grtDeviceTarget {
     uint32_t primCount;
     uint32_t numGeomTypes;        /* of the function table */
     uint32_t rayType;             /* function-table row used by the queries */
+    uint32_t nodeFormat;          /* 0: nodes are 128-byte 4-wide nodes; 1: 64-byte quantised ones */
 } grtDeviceTarget;
 
 /* Fills *out for exactly one of scene / geom (built), with an optional function table
@@ -633,7 +650,9 @@ typedef struct grtBvhInfo {
     uint32_t primCount;
     uint32_t primType;   /* grtPrimitiveType; 2 for a scene */
     uint32_t mortonBits; /* key width used by the last build */
-    const void* wideNodes; /* nodeCount x 128-byte 4-wide nodes, the ones traversal reads (layout below) */
+    const void* wideNodes; /* nodeCount x 128-byte 4-wide nodes (layout below), read by traversal unless quantised */
+    const void* quantNodes; /* nodeCount x 64-byte quantised 4-wide nodes (GRT_BUILD_QUANTIZED_NODES), read by
+                               traversal instead of wideNodes; NULL for other geometries and for scenes */
 } grtBvhInfo;
 /*
  * Node (64 bytes, 4 x float4): children c0 and c1 of internal node k

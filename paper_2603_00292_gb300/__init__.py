@@ -36,6 +36,7 @@ GRT_BUILD_PREFER_FAST = 0          # linear BVH (Morton order, Karras emission)
 GRT_BUILD_PREFER_BALANCED = 1      # PLOC clustering, search radius 8
 GRT_BUILD_PREFER_HIGH_QUALITY = 2  # PLOC clustering, search radius 32
 GRT_BUILD_CLUSTER_SUBTREES = 3     # clustering inside the linear BVH's subtrees, one bottom-up pass
+GRT_BUILD_QUANTIZED_NODES = 0x100  # ORed with a method: traversal reads 64-byte quantised 4-wide nodes
 CLUSTER_CAP = 16                   # clusters a subtree passes up (the library's kClusterCap)
 GRT_INSTANCE_GEOMETRY = 0
 GRT_INTERSECT_NONE = 0
@@ -106,7 +107,7 @@ class grtCamera(ctypes.Structure):
 class grtBvhInfo(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("parents", ctypes.c_void_p),
                 ("nodeCount", ctypes.c_uint32), ("primCount", ctypes.c_uint32), ("primType", ctypes.c_uint32),
-                ("mortonBits", ctypes.c_uint32), ("wideNodes", ctypes.c_void_p)]
+                ("mortonBits", ctypes.c_uint32), ("wideNodes", ctypes.c_void_p), ("quantNodes", ctypes.c_void_p)]
 
 
 class grtPathTraceInput(ctypes.Structure):
@@ -120,7 +121,8 @@ class grtDeviceTarget(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("primToLeaf", ctypes.c_void_p),
                 ("frames64", ctypes.c_void_p), ("frames32", ctypes.c_void_p), ("funcTable", ctypes.c_void_p),
                 ("deviceError", ctypes.c_void_p), ("primType", ctypes.c_uint32), ("geomType", ctypes.c_uint32),
-                ("primCount", ctypes.c_uint32), ("numGeomTypes", ctypes.c_uint32), ("rayType", ctypes.c_uint32)]
+                ("primCount", ctypes.c_uint32), ("numGeomTypes", ctypes.c_uint32), ("rayType", ctypes.c_uint32),
+                ("nodeFormat", ctypes.c_uint32)]
 
 
 class grtBatchScene(ctypes.Structure):

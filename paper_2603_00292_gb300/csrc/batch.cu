@@ -21,6 +21,9 @@
 // A scene whose geometry was created with GRT_BUILD_CLUSTER_SUBTREES (any size) has its
 // emission write the LBVH topology to scratch, then one more phase, the bottom-up
 // clustering walk over leaf chunks (cluster.cuh), before the fit; its trace is 4 + 3P.
+// A scene whose geometry has quantised nodes (GRT_BUILD_QUANTIZED_NODES) has one more
+// phase after the fit, the quantisation of its 4-wide nodes over node chunks, before
+// its trace; a scene built by one block quantises at the end of that block's build.
 // An item of phase k waits until every item of phase k-1 of its scene has finished
 // (per-scene completion counters). The host orders the queue so that an item only
 // ever waits for items taken from the queue before it, so a waiting block never
@@ -51,6 +54,7 @@ struct BatchSceneDev : BlockBuild {
     uint32_t small;       // built by one item
     uint32_t tracePhase;
     uint32_t cluster;     // built by subtree clustering
+    uint32_t quant;       // quantised 4-wide nodes written after the fit (one more phase)
     const float4* rayBuf;
     uint32_t* hitBuf;
     // subtree clustering scratch (cluster.cuh)
@@ -169,7 +173,8 @@ struct ChunkRaySource {
 __device__ __noinline__ void traceChunk(const BatchParams& B, const BatchSceneDev& S, uint32_t chunk, unsigned long long item,
                            uint32_t* smem) {
     TraceParams P{};
-    P.target.nodes = S.wide;
+    P.target.nodes = S.qnodes ? S.qnodes : S.wide;
+    P.target.quant = S.qnodes != nullptr;
     P.target.leaves = S.leaves;
     P.target.primType = GRT_PRIMITIVE_TRIANGLE_MESH;
     P.target.geomType = 0;
@@ -279,6 +284,10 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
         } else if (it.phase == 3 * S.passes + 2 + S.cluster) {
             const uint32_t b0 = it.chunk * B.buildChunk;
             fitRange(S, b0, min(S.n, b0 + B.buildChunk));
+        } else if (S.quant && it.phase == 3 * S.passes + 3 + S.cluster) {
+            const uint32_t m = S.n > 1 ? S.n - 1 : 1u, b1 = min(m, (it.chunk + 1) * B.buildChunk);
+            for (uint32_t k = it.chunk * B.buildChunk + threadIdx.x; k < b1; k += blockDim.x)
+                quantizeWideNode(S.wide + kWideWords * (size_t)k, S.qnodes + kQuantWords * (size_t)k);
         } else {
             traceChunk(B, S, it.chunk, item, smem);
         }
@@ -394,11 +403,13 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         d.small = n <= opt.smallScenePrims && !d.cluster;
         d.sortChunks = std::max(1u, ceilDiv(n, chunkKeys));
         d.passes = (d.bits + 7) / 8;
-        d.tracePhase = d.small ? 1u : 3u * d.passes + 3u + d.cluster;
+        d.quant = (o->quant && n > 0) ? 1u : 0u;
+        d.tracePhase = d.small ? 1u : 3u * d.passes + 3u + d.cluster + d.quant;
         d.rayBuf = (const float4*)in.rays;
         d.hitBuf = (uint32_t*)in.hits;
         d.nodes = (float4*)o->nodes;
         d.wide = (float4*)o->wide;
+        d.qnodes = (float4*)o->qnodes;
         d.leaves = o->leaves;
         d.parents = (uint32_t*)o->parents;
         d.primToLeaf = o->primToLeaf;
@@ -430,6 +441,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (d.cluster && ph == 3 * d.passes + 2) return ceilDiv(d.n, kWalkLeavesPerThread * opt.blockSize);
         if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);  // the fit
         if (d.cluster && ph == 3 * d.passes + 3) return ceilDiv(d.n, opt.buildChunk);  // the fit after clustering
+        if (d.quant && ph == 3 * d.passes + 3 + d.cluster) return ceilDiv(std::max(d.n - 1, 1u), opt.buildChunk);
         return 0u;
     };
     for (uint32_t g0 = 0; g0 < sceneCount; g0 += opt.sceneGroup) {

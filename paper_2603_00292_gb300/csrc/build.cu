@@ -9,6 +9,7 @@
 // range and split from the sorted codes alone, and leaves walk up to the root,
 // the second child to arrive at a node computing its box.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
@@ -262,6 +263,12 @@ __global__ void __launch_bounds__(256) fitKernel(FitParams P) {
     if (k < P.n) fitLeaf<KIND>(P, k);
 }
 
+// Quantised form of each of the m 4-wide nodes (the GRT_BUILD_QUANTIZED_NODES layout).
+__global__ void __launch_bounds__(256) quantizeKernel(const float4* wide, uint32_t m, float4* qnodes) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) quantizeWideNode(wide + kWideWords * (size_t)k, qnodes + kQuantWords * (size_t)k);
+}
+
 // ======================================================================= small builds
 // Up to kSmallBuild primitives (kSmallScene instances) a build runs in one block of
 // kSmallBuildThreads threads, as one launch, instead of a dozen grid-wide launches whose
@@ -322,6 +329,7 @@ static BlockBuild blockBuildOf(Context* c, BvhObject* o, const BuildLayout& L, c
     B.kind = kind;
     B.nodes = (float4*)o->nodes;
     B.wide = (float4*)o->wide;
+    B.qnodes = (float4*)o->qnodes;
     B.leaves = o->leaves;
     B.parents = (uint32_t*)o->parents;
     B.primToLeaf = o->primToLeaf;
@@ -409,7 +417,8 @@ __device__ __forceinline__ float3 setupInstance(const InstanceInput& I, uint32_t
     rec.nodes = g->nodes;
     rec.leaves = g->leaves;
     rec.instanceID = i;
-    rec.typeBits = (g->geomType & 0xFFFFFFu) | (g->primType << 24) | (g->primCount == 0 ? kInstEmpty : 0u);
+    rec.typeBits = (g->geomType & 0xFFFFFFu) | ((uint32_t)g->primType << 24) | (g->nodeFormat ? kInstQuant : 0u) |
+                   (g->primCount == 0 ? kInstEmpty : 0u);
     rec.geometry = g;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     if (g->primCount > 0) {
@@ -508,8 +517,13 @@ PrimSource primSource(const grtGeometryBuildInput* in, uint32_t count) {
     return S;
 }
 
+// Live geometries created with GRT_BUILD_QUANTIZED_NODES. While there are none, no walk
+// can meet quantised nodes, and traces run kernels without that form.
+static std::atomic<int> g_quantGeometries{0};
+bool anyQuantGeometry() { return g_quantGeometries.load(std::memory_order_relaxed) > 0; }
+
 static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geomType, uint32_t mortonBits,
-                                BvhObject** out) {
+                                BvhObject** out, bool quant = false) {
     BvhObject* o = new BvhObject();
     o->primCount = count;
     o->nodeCount = count == 0 ? 0 : std::max(count - 1, 1u);
@@ -517,10 +531,13 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     o->geomType = geomType;
     o->mortonBits = mortonBits;
     o->built = false;
+    o->quant = quant;
     size_t leafBytes = primType == GRT_PRIMITIVE_TRIANGLE_MESH ? 48 : (primType == kPrimScene ? 128 : 4);
     cudaError_t e = cudaMalloc(&o->dHeader, sizeof(BvhHeader));
     if (e == cudaSuccess && count) e = cudaMalloc(&o->nodes, (size_t)o->nodeCount * 64);
     if (e == cudaSuccess && count) e = cudaMalloc(&o->wide, (size_t)o->nodeCount * kWideWords * sizeof(float4));
+    if (e == cudaSuccess && count && quant)
+        e = cudaMalloc(&o->qnodes, (size_t)o->nodeCount * kQuantWords * sizeof(float4));
     if (e == cudaSuccess && count) e = cudaMalloc(&o->leaves, (size_t)count * leafBytes);
     if (e == cudaSuccess && count) e = cudaMalloc(&o->parents, (size_t)(2 * count - 1) * 4);
     if (e == cudaSuccess && count && primType != GRT_PRIMITIVE_AABB_LIST) e = cudaMalloc(&o->primToLeaf, (size_t)count * 4);
@@ -529,8 +546,9 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     BvhHeader h{};
     for (int a = 0; a < 3; ++a) h.rootLo[a] = INFINITY, h.rootHi[a] = -INFINITY;
     h.primCount = count;
-    h.primType = primType;
-    h.nodes = (const float4*)o->wide;
+    h.primType = (uint16_t)primType;
+    h.nodeFormat = quant ? 1 : 0;
+    h.nodes = (const float4*)(quant ? o->qnodes : o->wide);
     h.leaves = o->leaves;
     h.nodeCount = o->nodeCount;
     h.geomType = geomType;
@@ -540,6 +558,7 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
         cudaFree(o->dHeader);
         cudaFree(o->nodes);
         cudaFree(o->wide);
+        cudaFree(o->qnodes);
         cudaFree(o->leaves);
         cudaFree(o->parents);
         cudaFree(o->primToLeaf);
@@ -550,15 +569,18 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
         return GRT_ERROR_OUT_OF_MEMORY;
     }
     registerBvh(o);
+    if (quant) g_quantGeometries.fetch_add(1, std::memory_order_relaxed);
     *out = o;
     return GRT_SUCCESS;
 }
 
 static void destroyBvhObject(BvhObject* o) {
+    if (o->quant) g_quantGeometries.fetch_sub(1, std::memory_order_relaxed);
     unregisterBvh(o->dHeader);
     cudaFree(o->dHeader);
     cudaFree(o->nodes);
     cudaFree(o->wide);
+    cudaFree(o->qnodes);
     cudaFree(o->leaves);
     cudaFree(o->parents);
     cudaFree(o->primToLeaf);
@@ -615,12 +637,15 @@ static grtError resetBuildScratch(const BuildLayout& L, char* temp, uint32_t n, 
 // kSubtreeMethod = clustering inside the LBVH's subtrees (cluster.cuh), else PLOC with
 // this search radius (ploc.cuh).
 constexpr uint32_t kSubtreeMethod = 0xFFFFu;
+static uint32_t buildMethod(const grtBuildOptions* opt) { return opt ? opt->buildFlags & ~(uint32_t)GRT_BUILD_QUANTIZED_NODES : 0u; }
+static bool quantFlag(const grtBuildOptions* opt) { return opt && (opt->buildFlags & GRT_BUILD_QUANTIZED_NODES); }
 static uint32_t clusterRadius(const grtBuildOptions* opt) {
-    if (!opt || opt->buildFlags == GRT_BUILD_PREFER_FAST) return 0;
-    if (opt->buildFlags == GRT_BUILD_CLUSTER_SUBTREES) return kSubtreeMethod;
-    return opt->buildFlags == GRT_BUILD_PREFER_BALANCED ? 8u : 32u;
+    const uint32_t m = buildMethod(opt);
+    if (m == GRT_BUILD_PREFER_FAST) return 0;
+    if (m == GRT_BUILD_CLUSTER_SUBTREES) return kSubtreeMethod;
+    return m == GRT_BUILD_PREFER_BALANCED ? 8u : 32u;
 }
-static bool validBuildFlags(const grtBuildOptions* opt) { return !opt || opt->buildFlags <= 3u; }
+static bool validBuildFlags(const grtBuildOptions* opt) { return !opt || buildMethod(opt) <= 3u; }
 
 static std::mutex g_methodLock;
 static std::unordered_map<const BvhObject*, uint32_t> g_clusterRadius;  // objects with a PLOC build
@@ -790,6 +815,12 @@ static grtError issueGeometryBuild(Context* c, BvhObject* o, uint32_t op, const 
         fitKernel<1><<<ceilDiv(n, 256), 256, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
     noteLaunches(1);
+    if (o->qnodes) {
+        quantizeKernel<<<ceilDiv(o->nodeCount, 256), 256, 0, s>>>((const float4*)o->wide, o->nodeCount,
+                                                                  (float4*)o->qnodes);
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
+    }
     return GRT_SUCCESS;
 }
 
@@ -912,7 +943,7 @@ grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, c
     if (e != GRT_SUCCESS) return e;
     if (!validBuildFlags(options) || (clusterRadius(options) && n > kPlocIndex)) return GRT_ERROR_INVALID_PARAMETER;
     BvhObject* o = nullptr;
-    e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(n, options), &o);
+    e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(n, options), &o, quantFlag(options));
     if (e != GRT_SUCCESS) return e;
     if (clusterRadius(options)) {
         // the finishing block's shared memory is above the default limit
@@ -947,6 +978,7 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
         return GRT_ERROR_INVALID_PARAMETER;
     const uint32_t radius = radiusOf(o);
     if (!validBuildFlags(options) || (options && clusterRadius(options) != radius)) return GRT_ERROR_INVALID_PARAMETER;
+    if (options && quantFlag(options) != o->quant) return GRT_ERROR_INVALID_PARAMETER;
     Context* c = asContext(ctx);
     cudaStream_t s = (cudaStream_t)stream;
     o->geomType = input->geomType;

@@ -278,6 +278,7 @@ grtError grtGetBvhInfo(grtContext ctx, grtGeometry geom, grtScene scene, grtBvhI
     if (!o) return GRT_ERROR_INVALID_PARAMETER;
     info->nodes = o->nodes;
     info->wideNodes = o->wide;
+    info->quantNodes = o->quant ? o->qnodes : nullptr;
     info->leaves = o->leaves;
     info->parents = o->parents;
     info->nodeCount = o->nodeCount;

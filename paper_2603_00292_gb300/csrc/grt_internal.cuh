@@ -15,14 +15,16 @@ constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 constexpr uint32_t kPrimScene = 2;  // primType of a scene header
 constexpr int kWideWords = 8;       // float4 per 4-wide node (128 B)
+constexpr int kQuantWords = 4;      // float4 per quantised 4-wide node (64 B)
 
 // Device-resident header that a grtGeometry / grtScene handle points to (64 B).
 struct alignas(16) BvhHeader {
     float rootLo[3];      // box of everything below the root (written by the build)
     uint32_t primCount;
     float rootHi[3];
-    uint32_t primType;    // grtPrimitiveType, or kPrimScene
-    const float4* nodes;  // nodeCount 4-wide nodes (kWideWords float4 each), read by traversal
+    uint16_t primType;    // grtPrimitiveType, or kPrimScene
+    uint16_t nodeFormat;  // 0: nodes are 4-wide nodes (kWideWords float4); 1: quantised (kQuantWords)
+    const float4* nodes;  // nodeCount nodes in nodeFormat, read by traversal
     const void* leaves;   // triangle records / prim IDs / instance records
     uint32_t nodeCount;
     uint32_t geomType;
@@ -35,10 +37,10 @@ static_assert(sizeof(BvhHeader) == 64, "header size");
 // (bounds the parameter range inside it), and the geometry header.
 struct alignas(16) InstanceRecord {
     float4 inv[3];          // object = inv * world (rows; w = translation), rounded from FP64
-    const float4* nodes;    // bottom-level 4-wide nodes
+    const float4* nodes;    // bottom-level nodes (4-wide, or quantised with kInstQuant)
     const void* leaves;     // bottom-level leaves
     uint32_t instanceID;
-    uint32_t typeBits;      // geomType (bits 0-23) | primType << 24 | kInstEmpty
+    uint32_t typeBits;      // geomType (bits 0-23) | primType << 24 | kInstQuant | kInstEmpty
     const BvhHeader* geometry;
     float4 worldLo;         // xyz: world box (rounded outward)
     float4 worldHi;
@@ -51,9 +53,10 @@ struct InstanceFrames64 {
     double inv[3][4];  // object = inv * world, FP64 from the SRT frame
 };
 constexpr uint32_t kInstEmpty = 0x80000000u;
+constexpr uint32_t kInstQuant = 0x40000000u;  // the instance's geometry has quantised nodes
 constexpr int kFrameRows = 6;  // float4 rows per instance in BvhObject::fwd32
 __host__ __device__ inline uint32_t instGeomType(uint32_t bits) { return bits & 0xFFFFFFu; }
-__host__ __device__ inline uint32_t instPrimType(uint32_t bits) { return (bits >> 24) & 0x7Fu; }
+__host__ __device__ inline uint32_t instPrimType(uint32_t bits) { return (bits >> 24) & 0x3Fu; }
 static_assert(sizeof(InstanceRecord) == 128, "instance record size");
 
 // Device error word values are grtError codes; the first nonzero one latched wins
@@ -112,6 +115,7 @@ struct BvhObject {
     BvhHeader* dHeader;  // == handle
     void* nodes;  // binary nodes (64 B each)
     void* wide;   // 4-wide nodes (128 B each), one per binary node
+    void* qnodes; // quantised 4-wide nodes (64 B each), one per binary node, or null
     void* leaves;
     int32_t* parents;
     uint32_t* primToLeaf;  // primitive (instance) ID -> sorted position (triangles, scenes)
@@ -125,8 +129,10 @@ struct BvhObject {
     uint32_t mortonBits;
     uint32_t vertexCount;  // triangle meshes: the vertex count of the last build input
     bool built;
+    bool quant;  // built with GRT_BUILD_QUANTIZED_NODES (qnodes allocated when primCount > 0)
 };
 BvhObject* findBvh(const void* handle);
+bool anyQuantGeometry();  // whether a geometry with quantised nodes exists in the process
 grtError registerBvh(BvhObject* obj);
 void unregisterBvh(const void* handle);
 

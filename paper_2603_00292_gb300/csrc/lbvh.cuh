@@ -261,6 +261,91 @@ __device__ __forceinline__ void writeWidePair(float4* wide, uint32_t w, uint32_t
     reinterpret_cast<uint2*>(f)[12] = make_uint2(ca, cb);
 }
 
+// ======================================================================= quantised 4-wide nodes (A7)
+// Wide node w in 64 bytes (kQuantWords float4): each slot's box as 8-bit planes on a
+// per-axis grid of the node's own box (the compressed wide node of Ylitie, Karras and
+// Laine, HPG 2017; the paper's wide trees, Sec. 6.2). Per axis, over the used slots:
+// origin p = the least slot lo; step 2^e with e the least integer in [-126, 127] for
+// which fl(p + 255 2^e) reaches the greatest slot hi; a slot's lower plane is the largest
+// q in [0, 255] with fl(p + q 2^e) <= lo, its upper plane the smallest with
+// fl(p + q 2^e) >= hi (fl: float32 rounding to nearest; q 2^e is exact, so fl applies
+// once). Each condition is monotone, so every choice is unique whatever the starting
+// estimate, and the decoded box contains the exact one. Words: p.xyz; the biased
+// exponents e + 127 in bytes 0-2; qlo.x, qhi.x, qlo.y, qhi.y, qlo.z, qhi.z (slot j in
+// byte j; an empty slot 255 / 0); the four child words; two zero words.
+__device__ __forceinline__ float quantDecode(float p, uint32_t q, int e) {
+    return __fadd_rn(p, __fmul_rn((float)q, __uint_as_float((uint32_t)(e + 127) << 23)));
+}
+
+// Reads wide node W (7 float4, with L1-bypassing loads: it may have been written
+// earlier in the same launch) and writes its quantised form to Q.
+__device__ __forceinline__ void quantizeWideNode(const float4* W, float4* Q) {
+    float4 r[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r[i] = __ldcg(W + i);
+    const uint32_t c[4] = {__float_as_uint(r[6].x), __float_as_uint(r[6].y), __float_as_uint(r[6].z),
+                           __float_as_uint(r[6].w)};
+    bool used[4];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) any |= (used[j] = c[j] != kInvalid);
+    float p3[3];
+    uint32_t expWord = 0, planes[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo[4] = {r[2 * a].x, r[2 * a].y, r[2 * a].z, r[2 * a].w};
+        const float hi[4] = {r[2 * a + 1].x, r[2 * a + 1].y, r[2 * a + 1].z, r[2 * a + 1].w};
+        float p = 0.f, top = 0.f;
+        if (any) {
+            p = INFINITY, top = -INFINITY;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (used[j]) p = fminf(p, lo[j]), top = fmaxf(top, hi[j]);
+        }
+        int e = -126;
+        if (any) {
+            const float ext = __fsub_ru(top, p);
+            if (ext > 0.f) {  // a starting estimate: 255 2^e > ext
+                const int lg = ilogbf(ext * (1.0f / 255.0f));
+                e = lg >= 126 ? 127 : max(-126, lg + 1);
+            }
+            while (e > -126 && quantDecode(p, 255u, e - 1) >= top) --e;
+            while (e < 127 && quantDecode(p, 255u, e) < top) ++e;
+        }
+        const float inv = __uint_as_float((uint32_t)(127 - e) << 23);  // 2^-e, for the estimates (0 when e = 127)
+        uint32_t qlo = 0, qhi = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t ql = 255u, qh = 0u;
+            if (used[j]) {
+                const float l = lo[j], h = hi[j];
+                float g = floorf(__fmul_rn(__fsub_rd(l, p), inv));
+                int q = isnan(g) ? 0 : (int)fminf(fmaxf(g, 0.f), 255.f);
+                while (q > 0 && quantDecode(p, (uint32_t)q, e) > l) --q;
+                while (q < 255 && quantDecode(p, (uint32_t)q + 1u, e) <= l) ++q;
+                ql = (uint32_t)q;
+                g = ceilf(__fmul_rn(__fsub_ru(h, p), inv));
+                q = isnan(g) ? 255 : (int)fminf(fmaxf(g, 0.f), 255.f);
+                while (q < 255 && quantDecode(p, (uint32_t)q, e) < h) ++q;
+                while (q > 0 && quantDecode(p, (uint32_t)q - 1u, e) >= h) --q;
+                qh = (uint32_t)q;
+            }
+            qlo |= ql << (8 * j);
+            qhi |= qh << (8 * j);
+        }
+        p3[a] = p;
+        expWord |= (uint32_t)(e + 127) << (8 * a);
+        planes[2 * a] = qlo;
+        planes[2 * a + 1] = qhi;
+    }
+    Q[0] = make_float4(p3[0], p3[1], p3[2], __uint_as_float(expWord));
+    Q[1] = make_float4(__uint_as_float(planes[0]), __uint_as_float(planes[1]), __uint_as_float(planes[2]),
+                       __uint_as_float(planes[3]));
+    Q[2] = make_float4(__uint_as_float(planes[4]), __uint_as_float(planes[5]), __uint_as_float(c[0]),
+                       __uint_as_float(c[1]));
+    Q[3] = make_float4(__uint_as_float(c[2]), __uint_as_float(c[3]), 0.f, 0.f);
+}
+
 // Leaf k of the sorted order: writes the leaf record and walks up while this thread is
 // the second to reach a node, writing each box into its parent.
 //

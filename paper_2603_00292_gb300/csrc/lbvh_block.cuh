@@ -25,6 +25,7 @@ struct BlockBuild {
     uint32_t pad0;
     float4* nodes;
     float4* wide;
+    float4* qnodes;    // quantised 4-wide nodes, written after the fit when not null
     void* leaves;
     uint32_t* parents;
     uint32_t* primToLeaf;
@@ -528,9 +529,8 @@ template <typename K, int BITS>
 // (bitonicSortShared, emission from the shared codes, fitRangeBlock); otherwise the
 // codes are ranked in shared memory (n <= kRankSortMax) or radix-sorted through the
 // build temporary, and the fit uses the global counters.
-__device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys, uint32_t* smem,
-                                        size_t smemBytes = 0) {
-    if (S.n == 0) return;
+__device__ __noinline__ void buildWholeTree(const BlockBuild& S, uint32_t chunkKeys, uint32_t* smem,
+                                            size_t smemBytes) {
     if (S.kind != 2) {
         if (threadIdx.x == 0) {
             S.bounds[0] = S.bounds[1] = S.bounds[2] = 0xFFFFFFFFu;  // running minima start at the top
@@ -598,6 +598,20 @@ __device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys,
     }
     __syncthreads();
     fitRange(S, 0, S.n);
+}
+
+// buildWholeTree, then (with S.qnodes) the quantised form of every 4-wide node.
+template <typename K, int BITS>
+__device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys, uint32_t* smem,
+                                        size_t smemBytes = 0) {
+    if (S.n == 0) return;
+    buildWholeTree<K, BITS>(S, chunkKeys, smem, smemBytes);
+    if (!S.qnodes) return;
+    __threadfence();  // the wide nodes are read back through L2
+    __syncthreads();
+    const uint32_t m = S.n > 1 ? S.n - 1 : 1u;
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x)
+        quantizeWideNode(S.wide + kWideWords * (size_t)k, S.qnodes + kQuantWords * (size_t)k);
 }
 
 }  // namespace grt

@@ -11,13 +11,15 @@
 
 namespace grt {
 
-template <bool ANY, bool SCENE, bool COUNT>
+// QN: some level of the walk may have quantised nodes (checked per level); false when
+// none can (no such geometry exists), which compiles that form out.
+template <bool ANY, bool SCENE, bool COUNT, bool QN = false>
 __global__ void traceKernel(TraceParams P) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
     RayBufferSource<SCENE> src{P.count, &P};
-    refillLoop<ANY, SCENE, COUNT>(P, st, src);
+    refillLoop<ANY, SCENE, COUNT, QN>(P, st, src);
 }
 
 // The closest hits' t, u, v recomputed in FP64, one thread per ray after traversal so
@@ -135,14 +137,14 @@ struct AoSource {
 
 // 96 registers: 5 blocks of 128 threads per SM instead of 4, 7% faster on the terrain
 // AO workload despite a few spills (the closest-hit kernel is faster uncapped).
-template <bool COUNT>
+template <bool COUNT, bool QN = false>
 __global__ void __maxnreg__(96) aoTraceKernel(TraceParams P, const uint32_t* list, const uint32_t* listCount,
                                               uint32_t* counts, const float4* frames) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
     AoSource src{&P, list, listCount, counts, frames};
-    refillLoop<true, true, COUNT>(P, st, src);
+    refillLoop<true, true, COUNT, QN>(P, st, src);
 }
 
 __global__ void aoFinishKernel(const uint32_t* __restrict__ list, const uint32_t* __restrict__ listCount,
@@ -273,13 +275,13 @@ struct ShadowSource {
     }
 };
 
-template <bool SCENE>
+template <bool SCENE, bool QN = false>
 __global__ void shadeForwardKernel(TraceParams P, ShadeParams S) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
     ShadowSource<SCENE> src{&S};
-    refillLoop<true, SCENE, false>(P, st, src);
+    refillLoop<true, SCENE, false, QN>(P, st, src);
 }
 
 // One pixel's share of the adjoint: dL/dc_k and dL/dv_k for the hit triangle's three
@@ -538,7 +540,8 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     if (geom && o->primType == kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
     if (!o->built) return GRT_ERROR_NOT_BUILT;
     *isScene = scene != nullptr;
-    P.target.nodes = (const float4*)o->wide;
+    P.target.nodes = (const float4*)(o->qnodes ? o->qnodes : o->wide);
+    P.target.quant = o->qnodes != nullptr;
     P.target.leaves = o->leaves;
     P.target.primType = o->primType;
     P.target.geomType = o->geomType;
@@ -598,9 +601,16 @@ static grtError bindGlobalStack(Context* c, const grtTraceOptions* opt, int thre
     return e;
 }
 
+// Whether a walk over P's target can meet quantised nodes: a geometry's own flag; for a
+// scene, whether any quantised geometry exists (a scene instances live geometries only).
+static bool quantWalk(const TraceParams& P, bool scene) { return scene ? anyQuantGeometry() : P.target.quant != 0; }
+
 template <bool ANY, bool COUNT>
-static void traceKernelFor(bool scene, void (**k)(TraceParams)) {
-    *k = scene ? traceKernel<ANY, true, COUNT> : traceKernel<ANY, false, COUNT>;
+static void traceKernelFor(bool scene, bool quant, void (**k)(TraceParams)) {
+    if (quant)
+        *k = scene ? traceKernel<ANY, true, COUNT, true> : traceKernel<ANY, false, COUNT, true>;
+    else
+        *k = scene ? traceKernel<ANY, true, COUNT> : traceKernel<ANY, false, COUNT>;
 }
 
 template <bool ANY>
@@ -620,9 +630,9 @@ static grtError launchTrace(grtContext ctx, grtScene scene, grtGeometry geom, co
     P.count = n;
     void (*kernel)(TraceParams) = nullptr;
     if (count)
-        traceKernelFor<ANY, true>(isScene, &kernel);
+        traceKernelFor<ANY, true>(isScene, quantWalk(P, isScene), &kernel);
     else
-        traceKernelFor<ANY, false>(isScene, &kernel);
+        traceKernelFor<ANY, false>(isScene, quantWalk(P, isScene), &kernel);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
@@ -709,9 +719,9 @@ grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom
     P.count = rayCount;
     void (*kernel)(TraceParams) = nullptr;
     if (count)
-        traceKernelFor<false, true>(isScene, &kernel);
+        traceKernelFor<false, true>(isScene, quantWalk(P, isScene), &kernel);
     else
-        traceKernelFor<false, false>(isScene, &kernel);
+        traceKernelFor<false, false>(isScene, quantWalk(P, isScene), &kernel);
     const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(rayCount, bs));
@@ -737,13 +747,20 @@ grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* optio
     Context* c = asContext(ctx);
     const size_t smem = (size_t)bs * traceSmemWords(sh) * sizeof(uint32_t);
     int threads = 0;
-    void (*kernels[])(TraceParams) = {traceKernel<false, false, false>, traceKernel<false, true, false>,
-                                      traceKernel<true, false, false>,  traceKernel<true, true, false>,
-                                      traceKernel<false, false, true>,  traceKernel<false, true, true>,
-                                      traceKernel<true, false, true>,   traceKernel<true, true, true>};
+    void (*kernels[])(TraceParams) = {
+        traceKernel<false, false, false>,       traceKernel<false, true, false>,
+        traceKernel<true, false, false>,        traceKernel<true, true, false>,
+        traceKernel<false, false, true>,        traceKernel<false, true, true>,
+        traceKernel<true, false, true>,         traceKernel<true, true, true>,
+        traceKernel<false, false, false, true>, traceKernel<false, true, false, true>,
+        traceKernel<true, false, false, true>,  traceKernel<true, true, false, true>,
+        traceKernel<false, false, true, true>,  traceKernel<false, true, true, true>,
+        traceKernel<true, false, true, true>,   traceKernel<true, true, true, true>};
     for (auto k : kernels) threads = std::max(threads, persistentShape(c, k, bs, smem).blocks * bs);
     threads = std::max(threads, persistentShape(c, aoTraceKernel<false>, bs, smem).blocks * bs);
     threads = std::max(threads, persistentShape(c, aoTraceKernel<true>, bs, smem).blocks * bs);
+    threads = std::max(threads, persistentShape(c, aoTraceKernel<false, true>, bs, smem).blocks * bs);
+    threads = std::max(threads, persistentShape(c, aoTraceKernel<true, true>, bs, smem).blocks * bs);
     *sizeBytes = (size_t)threads * gl * sizeof(uint32_t);
     return GRT_SUCCESS;
 }
@@ -755,7 +772,8 @@ grtError grtGetDeviceTarget(grtContext ctx, grtScene scene, grtGeometry geom, gr
     if (!o || (scene != nullptr) != (o->primType == kPrimScene)) return GRT_ERROR_INVALID_PARAMETER;
     if (!o->built) return GRT_ERROR_NOT_BUILT;
     grtDeviceTarget t{};
-    t.nodes = o->wide;
+    t.nodes = o->qnodes ? o->qnodes : o->wide;
+    t.nodeFormat = o->qnodes != nullptr;
     t.leaves = o->leaves;
     t.primToLeaf = o->primToLeaf;
     t.frames64 = o->inv64;
@@ -882,7 +900,8 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
     if ((size_t)pixelCount * samplesPerPixel > 0xFFFFFFFEull) return GRT_ERROR_INVALID_PARAMETER;
     const bool count = options && (options->flags & GRT_TRACE_FLAG_COUNT);
     void (*kernel)(TraceParams, const uint32_t*, const uint32_t*, uint32_t*, const float4*) =
-        count ? aoTraceKernel<true> : aoTraceKernel<false>;
+        quantWalk(P, true) ? (count ? aoTraceKernel<true, true> : aoTraceKernel<false, true>)
+                           : (count ? aoTraceKernel<true> : aoTraceKernel<false>);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
@@ -1200,7 +1219,9 @@ static grtError prepareShade(grtContext ctx, grtScene scene, grtGeometry geom, c
 // The forward shading launch (image and / or visibility from stored hits).
 static grtError launchShadeForward(Context* c, bool scene, TraceParams& P, const ShadeParams& S, int bs,
                                    const grtTraceOptions* options, cudaStream_t s) {
-    void (*kernel)(TraceParams, ShadeParams) = scene ? shadeForwardKernel<true> : shadeForwardKernel<false>;
+    void (*kernel)(TraceParams, ShadeParams) =
+        quantWalk(P, scene) ? (scene ? shadeForwardKernel<true, true> : shadeForwardKernel<false, true>)
+                            : (scene ? shadeForwardKernel<true> : shadeForwardKernel<false>);
     const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(S.n, bs));

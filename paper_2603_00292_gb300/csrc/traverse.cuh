@@ -48,6 +48,7 @@ struct TraceTarget {
     uint32_t primType;  // of the geometry when tracing one directly
     uint32_t geomType;
     uint32_t empty;
+    uint32_t quant;  // the nodes are quantised 4-wide nodes (kQuantWords float4 each)
 };
 
 struct TraceParams {
@@ -178,6 +179,42 @@ __device__ __forceinline__ uint32_t slab4(const float4* nodes, uint32_t w, const
                       fmaxf((pz[j] - L.on.z) * L.id.z, tmin));
         const float tf = fminf(fminf((qx[j] - L.of.x) * L.id.x, (qy[j] - L.of.y) * L.id.y),
                                fminf((qz[j] - L.of.z) * L.id.z, tmax));
+        if (tn[j] <= tf * kFarScale && c[j] != kInvalid) m |= 1u << j;
+    }
+    return m;
+}
+
+// Byte j of w as a float: the byte becomes the low mantissa bits of 2^23, which is then
+// subtracted (exact).
+__device__ __forceinline__ float byteToFloat(uint32_t w, uint32_t j) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650u | j)) - 8388608.0f;
+}
+
+// slab4 for a quantised 4-wide node (kQuantWords float4: origin p.xyz and the biased
+// exponents; the lower and upper plane bytes of each axis; the child words). Each plane
+// the test uses is decoded as fl(p + q 2^e) (one FMA: q 2^e is exact), which is the box
+// the build made sure contains the child's box, and then tested exactly as in slab4.
+__device__ __forceinline__ uint32_t slab4q(const float4* nodes, uint32_t w, const Level& L, float tmin, float tmax,
+                                           float tn[4], uint32_t c[4]) {
+    const float4* Q = nodes + kQuantWords * (size_t)w;
+    const float4 h = __ldg(Q), a = __ldg(Q + 1), b = __ldg(Q + 2), d = __ldg(Q + 3);
+    const uint32_t ew = __float_as_uint(h.w);
+    const float sx = __uint_as_float((ew & 0xFFu) << 23), sy = __uint_as_float(((ew >> 8) & 0xFFu) << 23),
+                sz = __uint_as_float(((ew >> 16) & 0xFFu) << 23);
+    const bool px = L.id.x >= 0.f, py = L.id.y >= 0.f, pz = L.id.z >= 0.f;
+    const uint32_t nxw = __float_as_uint(px ? a.x : a.y), fxw = __float_as_uint(px ? a.y : a.x);
+    const uint32_t nyw = __float_as_uint(py ? a.z : a.w), fyw = __float_as_uint(py ? a.w : a.z);
+    const uint32_t nzw = __float_as_uint(pz ? b.x : b.y), fzw = __float_as_uint(pz ? b.y : b.x);
+    c[0] = __float_as_uint(b.z), c[1] = __float_as_uint(b.w), c[2] = __float_as_uint(d.x), c[3] = __float_as_uint(d.y);
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float nx = __fmaf_rn(byteToFloat(nxw, j), sx, h.x), fx = __fmaf_rn(byteToFloat(fxw, j), sx, h.x);
+        const float ny = __fmaf_rn(byteToFloat(nyw, j), sy, h.y), fy = __fmaf_rn(byteToFloat(fyw, j), sy, h.y);
+        const float nz = __fmaf_rn(byteToFloat(nzw, j), sz, h.z), fz = __fmaf_rn(byteToFloat(fzw, j), sz, h.z);
+        tn[j] = fmaxf(fmaxf((nx - L.on.x) * L.id.x, (ny - L.on.y) * L.id.y), fmaxf((nz - L.on.z) * L.id.z, tmin));
+        const float tf =
+            fminf(fminf((fx - L.of.x) * L.id.x, (fy - L.of.y) * L.id.y), fminf((fz - L.of.z) * L.id.z, tmax));
         if (tn[j] <= tf * kFarScale && c[j] != kInvalid) m |= 1u << j;
     }
     return m;
@@ -513,7 +550,16 @@ struct RayState {
     uint32_t steps, next;
     float lo, hi;  // [tmin, limit] on the current level (limit = tmax, or the best t so far)
     bool inBlas, found;
+    bool quant;    // the current level's nodes are quantised
 };
+
+// The slab test of the current node in the current level's node format. QN = false
+// compiles the quantised form out: the walk's levels are known to use 4-wide nodes.
+template <bool QN>
+__device__ __forceinline__ uint32_t slabNode(const RayState& s, float tn[4], uint32_t c[4]) {
+    return (QN && s.quant) ? slab4q(s.nodes, s.next, s.L, s.lo, s.hi, tn, c)
+                           : slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+}
 
 template <bool SCENE>
 __device__ __forceinline__ void beginRay(const TraceParams& P, Stack& st, RayState& s, float3 wo, float3 wd,
@@ -526,6 +572,7 @@ __device__ __forceinline__ void beginRay(const TraceParams& P, Stack& st, RaySta
     exactLevel(s.L, wo, wd);
     s.wid = s.L.id;
     s.nodes = P.target.nodes;
+    s.quant = P.target.quant != 0;
     s.leaves = P.target.leaves;
     s.primType = P.target.primType;
     s.geomType = P.target.geomType;
@@ -557,6 +604,7 @@ __device__ __forceinline__ bool enterInstance(const TraceParams& P, Stack& st, R
     s.lo = localLo(s.L, s.tmin);
     s.hi = localHi(s.L, lim);
     s.nodes = R->nodes;
+    s.quant = (bits & kInstQuant) != 0;
     s.leaves = R->leaves;
     s.primType = instPrimType(bits);
     s.geomType = instGeomType(bits);
@@ -699,7 +747,7 @@ __device__ __forceinline__ void orderChildren(const TraceParams& P, Stack& st, R
 
 // One traversal step: a node visit (with its leaf tests), an instance entry or an
 // instance exit. Returns true once the ray is finished (s.best is then final).
-template <bool ANY, bool SCENE, bool COUNT, class U = NoUser>
+template <bool ANY, bool SCENE, bool COUNT, class U = NoUser, bool QN = true>
 __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayState& s, Visits* vis,
                                         const U* user = nullptr, void* payload = nullptr) {
     if (s.next == kNone) {
@@ -710,6 +758,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
             s.lo = s.tmin;
             s.hi = (ANY || !s.found) ? s.tmax : s.best.t;
             s.nodes = P.target.nodes;
+            s.quant = P.target.quant != 0;
             s.inBlas = false;
             s.next = kNone;
             return false;
@@ -728,7 +777,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
     if (COUNT) ++vis->nodes;
     float tn[4];
     uint32_t c[4];
-    uint32_t m = slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+    uint32_t m = slabNode<QN>(s, tn, c);
     s.next = kNone;
     if (s.inBlas) {
 #pragma unroll
@@ -748,7 +797,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
 // (at most four per visit), or an instance entry or exit. Returns the number of hits
 // appended, or -1 once the walk is over. Each primitive of each instance sits in one
 // leaf, so each (instance, primitive) is reported at most once.
-template <bool SCENE, class U = NoUser>
+template <bool SCENE, class U = NoUser, bool QN = true>
 __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState& s, Hit* found,
                                        const U* user = nullptr, void* payload = nullptr) {
     if (s.next == kNone) {
@@ -759,6 +808,7 @@ __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState
             s.lo = s.tmin;
             s.hi = s.tmax;
             s.nodes = P.target.nodes;
+            s.quant = P.target.quant != 0;
             s.inBlas = false;
             s.next = kNone;
             return 0;
@@ -777,7 +827,7 @@ __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState
     }
     float tn[4];
     uint32_t c[4];
-    uint32_t m = slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+    uint32_t m = slabNode<QN>(s, tn, c);
     s.next = kNone;
     int added = 0;
     if (s.inBlas) {
@@ -877,7 +927,7 @@ __device__ __forceinline__ float3 aoDirection(const AoFrame& F, uint64_t seed, u
 // Refill loop with one traversal step per lane per iteration (node visits test their
 // leaves at once). Used for any-hit queries on a single geometry (shadow rays), which
 // stop at their first hit and so gain nothing from queueing leaves.
-template <bool ANY, bool SCENE, bool COUNT, class Src>
+template <bool ANY, bool SCENE, bool COUNT, bool QN = true, class Src>
 __device__ __forceinline__ void refillLoopPerRay(const TraceParams& P, Stack& st, Src& src) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t ltMask = (1u << lane) - 1u;
@@ -904,7 +954,7 @@ __device__ __forceinline__ void refillLoopPerRay(const TraceParams& P, Stack& st
             live = __ballot_sync(0xffffffffu, item != kNone);
         }
         if (live == 0) break;
-        if (item != kNone && stepRay<ANY, SCENE, COUNT>(P, st, s, &v)) {
+        if (item != kNone && stepRay<ANY, SCENE, COUNT, NoUser, QN>(P, st, s, &v)) {
             src.finish(item, s);
             if (COUNT) flushVisits(P.stats, v);
             item = kNone;
@@ -935,7 +985,7 @@ struct Pending {
 
 // Node visit that queues hit leaf children instead of testing them (inner children
 // and top-level leaves go on as in stepRay). Requires q.n <= kPendingCap - 4.
-template <bool ANY, bool SCENE, bool COUNT>
+template <bool ANY, bool SCENE, bool COUNT, bool QN = true>
 __device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RayState& s, Pending& q, Visits* vis) {
     if (++s.steps > P.maxSteps) {
         latchError(P.error, GRT_ERROR_STEP_LIMIT);
@@ -947,7 +997,7 @@ __device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RaySt
     if (COUNT) ++vis->nodes;
     float tn[4];
     uint32_t c[4];
-    uint32_t m = slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+    uint32_t m = slabNode<QN>(s, tn, c);
     s.next = kNone;
     if (s.inBlas) {
 #pragma unroll
@@ -975,6 +1025,7 @@ __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, R
             s.lo = s.tmin;
             s.hi = (ANY || !s.found) ? s.tmax : s.best.t;
             s.nodes = P.target.nodes;
+            s.quant = P.target.quant != 0;
             s.inBlas = false;
             continue;
         }
@@ -999,10 +1050,10 @@ __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, R
 //   count()             number of items (may be read from device memory)
 //   begin(i, P, st, s)  set up item i's ray in s; false if the item has no ray
 //   finish(i, s)        consume item i's result s.best
-template <bool ANY, bool SCENE, bool COUNT, class Src>
+template <bool ANY, bool SCENE, bool COUNT, bool QN = true, class Src>
 __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src& src) {
     if constexpr (ANY && !SCENE) {
-        refillLoopPerRay<ANY, SCENE, COUNT>(P, st, src);
+        refillLoopPerRay<ANY, SCENE, COUNT, QN>(P, st, src);
         return;
     }
     const uint32_t lane = threadIdx.x & 31;
@@ -1076,7 +1127,7 @@ __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src&
             }
         } else if (state == kStNode) {
             acted = true;
-            visitNode<ANY, SCENE, COUNT>(P, st, s, q, &v);
+            visitNode<ANY, SCENE, COUNT, QN>(P, st, s, q, &v);
         }
         if (acted) state = (ANY && s.found) ? kStDone : nextState<ANY, SCENE>(P, st, s, q);
         } while (tail && state != kStDone);
