@@ -70,6 +70,8 @@ def parse():
                    help="the two-level ambient-occlusion throughput workload (default), the single-icosphere "
                         "primary-ray one, the million-sphere custom-primitive one, the differentiable-shading one, "
                         "or the batched many-scenes one")
+    p.add_argument("--image", default=None, metavar="WxH",
+                   help="terrain workload: another image size (a smaller case, e.g. for a profiler)")
     p.add_argument("--no-autotune", action="store_true", help="batched workload: default launch options")
     p.add_argument("--scenes", type=int, default=256, help="batched workload: the first N soups (a smaller case)")
     p.add_argument("--no-sequential", action="store_true",
@@ -1575,6 +1577,9 @@ def spawn_ranks(args) -> int:
 
 def main():
     args = parse()
+    if args.image:
+        w, h = (int(x) for x in args.image.lower().split("x"))
+        WORKLOAD.update(width=w, height=h)
     rank, world, local = dist_env()
     if "WORLD_SIZE" not in os.environ and args.gpus > 1:
         sys.exit(spawn_ranks(args))
