@@ -224,7 +224,9 @@ def kernel_bound(kernel: str, peak_gbs: float):
     e = ncu_record(kernel)
     if not e or "l1_pct" not in e:
         return STATIC_BOUND.get(kernel, "hbm"), None
-    dram_pct = 100.0 * e["dram_bytes_per_launch"] / (e["duration_ns"] * 1e-9) / 1e9 / peak_gbs
+    dram_pct = e.get("dram_pct")  # recorded where the capture was scaled to a larger launch
+    if dram_pct is None:
+        dram_pct = 100.0 * e["dram_bytes_per_launch"] / (e["duration_ns"] * 1e-9) / 1e9 / peak_gbs
     util = {"l1": e["l1_pct"], "l2": e["l2_pct"], "hbm": round(dram_pct, 2), "issue": e["issue_pct"]}
     counters = dict(util, memory_sol_pct=e.get("mem_sol_pct"), l2_hit_pct=e.get("l2_hit_pct"),
                     warps_active_pct=e.get("warps_active_pct"), lanes_per_instruction=e.get("lanes_per_inst"))
