@@ -312,6 +312,47 @@ def wide_nodes(ref):
 # ----------------------------------------------------------------------------------
 # Scenes and traces
 # ----------------------------------------------------------------------------------
+def wide8_nodes(ref):
+    """8-wide nodes from a binary LBVH (the dict of lbvh()), by definition: wide node k has
+    binary node k's descendants three levels down. Slots 4s..4s+3 come from child s: if it
+    is a leaf, slot 4s holds it and 4s+1..4s+3 are empty; otherwise each of its children t
+    fills slots 4s+2t and 4s+2t+1 with its own two children, or with itself (a leaf) and
+    an empty slot. Empty slots: index 0xFFFFFFFF, box lo = +inf, hi = -inf. Returns lo, hi
+    (m, 8, 3) float32 and child (m, 8) uint32, m = max(n - 1, 1). Child words use the
+    binary format (bit 31 set = leaf, low bits = sorted position). A walk from node 0 only
+    meets the nodes of binary depth divisible by 3."""
+    n = ref["leaf_lo"].shape[0]
+    m = max(n - 1, 1)
+    lo = np.full((m, 8, 3), np.inf, np.float32)
+    hi = np.full((m, 8, 3), -np.inf, np.float32)
+    child = np.full((m, 8), NONE, np.uint32)
+    if n == 1:  # a single primitive: one node, the leaf in slot 0
+        lo[0, 0], hi[0, 0], child[0, 0] = ref["leaf_lo"][0], ref["leaf_hi"][0], LEAF_BIT
+        return lo, hi, child
+    cl = ref["childL"].view(np.uint32)
+    cr = ref["childR"].view(np.uint32)
+    all_lo = np.concatenate([ref["node_lo"], ref["leaf_lo"]])  # internal nodes, then leaves
+    all_hi = np.concatenate([ref["node_hi"], ref["leaf_hi"]])
+
+    def put(k, slot, w):
+        child[k, slot] = w
+        row = n - 1 + (w & 0x7FFFFFFF) if w & LEAF_BIT else w
+        lo[k, slot], hi[k, slot] = all_lo[row], all_hi[row]
+
+    for k in range(n - 1):
+        for s_, c in enumerate((int(cl[k]), int(cr[k]))):
+            if c & LEAF_BIT:
+                put(k, 4 * s_, c)
+                continue
+            for t, g in enumerate((int(cl[c]), int(cr[c]))):
+                if g & LEAF_BIT:
+                    put(k, 4 * s_ + 2 * t, g)
+                else:
+                    put(k, 4 * s_ + 2 * t, int(cl[g]))
+                    put(k, 4 * s_ + 2 * t + 1, int(cr[g]))
+    return lo, hi, child
+
+
 def quantized_wide_nodes(lo, hi, child) -> np.ndarray:
     """Quantised 4-wide nodes (oracle_quantize_wide) of the wide nodes (lo, hi (m, 4, 3)
     float32, child (m, 4) uint32) that wide_nodes returns: (m, 16) uint32 words per node,

@@ -397,3 +397,67 @@ def test_quantized_single_primitive_and_degenerate_node():
     dlo, dhi = oracle.dequantize_wide_nodes(q)
     assert dlo[0, 0].tolist() == [1, 2, 3] and dhi[0, 0].tolist() == [4, 2, 3]
     assert q[0, 10] == 0x80000000 and (q[0, 11:14] == oracle.NONE).all()
+
+
+# ---------------------------------------------------------------- 8-wide nodes
+def test_wide8_nodes_hand_derived(golden_dir):
+    """Karras's eight-key example (tests/golden/karras_example_tree.txt): node 0 =
+    (N3, N4), N3 = (N1, N2), N1 = (L0, L1), N2 = (L2, L3), N4 = (L4, N5), N5 = (N6, L7),
+    N6 = (L5, L6). Three levels below node 0: N3's grandchildren L0-L3 fill slots 0-3;
+    N4's children are L4 (slot 4, slot 5 empty) and N5, whose children N6 and L7 fill
+    slots 6 and 7. N6 (depth 3) holds its leaf children L5 in slot 0 and L6 in slot 4."""
+    keys, _ = _read_tree(os.path.join(golden_dir, "karras_example_tree.txt"))
+    cl, cr, _, _ = oracle.topology(np.array(keys, np.uint64), 32)
+    leaf_lo = np.array([[i, 0, 0] for i in range(8)], np.float32)
+    leaf_hi = leaf_lo + np.float32(0.5)
+    lo, hi, child = oracle.wide8_nodes(_tree_dict(cl, cr, leaf_lo, leaf_hi))
+    L, E = 0x80000000, 0xFFFFFFFF
+    assert child[0].tolist() == [L | 0, L | 1, L | 2, L | 3, L | 4, E, 6, L | 7]
+    assert child[6].tolist() == [L | 5, E, E, E, L | 6, E, E, E]
+    assert lo[0, 6].tolist() == [5, 0, 0] and hi[0, 6].tolist() == [6.5, 0.5, 0.5]  # N6 = leaves 5-6
+    assert lo[0, 7].tolist() == [7, 0, 0] and np.all(lo[0, 5] == np.inf) and np.all(hi[0, 5] == -np.inf)
+
+
+def test_wide8_nodes_single_primitive():
+    d = dict(leaf_lo=np.array([[1, 2, 3]], np.float32), leaf_hi=np.array([[4, 5, 6]], np.float32))
+    lo, hi, child = oracle.wide8_nodes(d)
+    assert child.tolist() == [[0x80000000] + [0xFFFFFFFF] * 7]
+    assert lo[0, 0].tolist() == [1, 2, 3] and np.all(lo[0, 1:] == np.inf)
+
+
+@pytest.mark.parametrize("level", [1, 3])
+def test_wide8_nodes_invariants(level):
+    """Used slots cover exactly the binary node's box; a walk from node 0 reaches every
+    leaf exactly once, through nodes of binary depth divisible by 3 only."""
+    mesh = scenegen.icosphere(level)
+    tlo, thi, c = oracle.triangle_aabbs(mesh.vertices, mesh.indices)
+    r = oracle.lbvh(tlo, thi, c, 10)
+    n = tlo.shape[0]
+    lo, hi, child = oracle.wide8_nodes(r)
+    assert child.shape == (n - 1, 8)
+    for k in range(n - 1):
+        used = child[k] != 0xFFFFFFFF
+        assert np.array_equal(lo[k][used].min(axis=0), r["node_lo"][k])
+        assert np.array_equal(hi[k][used].max(axis=0), r["node_hi"][k])
+        assert used[0] and used[4]
+    parent = np.full(n - 1, -1)
+    for k in range(n - 1):
+        for cc in (r["childL"][k], r["childR"][k]):
+            if cc >= 0:
+                parent[cc] = k
+    seen = np.zeros(n, int)
+    stack = [0]
+    while stack:
+        k = stack.pop()
+        d, x = 0, k
+        while parent[x] >= 0:
+            x, d = parent[x], d + 1
+        assert d % 3 == 0
+        for cc in child[k]:
+            if cc == 0xFFFFFFFF:
+                continue
+            if cc & 0x80000000:
+                seen[cc & 0x7FFFFFFF] += 1
+            else:
+                stack.append(int(cc))
+    assert (seen == 1).all()
