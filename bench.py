@@ -461,9 +461,11 @@ def run_grt(args, rank, world, local):
     for name, flags in (("fast_lbvh", grt.GRT_BUILD_PREFER_FAST), ("balanced_ploc8", grt.GRT_BUILD_PREFER_BALANCED),
                         ("high_quality_ploc32", grt.GRT_BUILD_PREFER_HIGH_QUALITY),
                         ("subtree_cluster16", grt.GRT_BUILD_CLUSTER_SUBTREES),
-                        ("fast_lbvh_quantized_nodes", grt.GRT_BUILD_PREFER_FAST | grt.GRT_BUILD_QUANTIZED_NODES)):
+                        ("fast_lbvh_quantized_nodes", grt.GRT_BUILD_PREFER_FAST | grt.GRT_BUILD_QUANTIZED_NODES),
+                        ("fast_lbvh_wide8_nodes", grt.GRT_BUILD_PREFER_FAST | grt.GRT_BUILD_WIDE8_NODES)):
         gq = Geometry(ctx, vertices=verts, indices=idx, build_flags=flags).build(sh)
-        sq = Scene(ctx, [gq.handle] * WORKLOAD["instances"], frames).build(sh)
+        sq = Scene(ctx, [gq.handle] * WORKLOAD["instances"], frames,
+                   build_flags=flags & grt.GRT_BUILD_WIDE8_NODES).build(sh)
         qhits = new_hits(npix)
 
         def q_trace(sq=sq, qhits=qhits):
@@ -945,40 +947,16 @@ def run_spheres(args, rank, world, local):
             short_ms.append(e0.elapsed_time(e1))
     occl_short = int((hs[:, 1].view(torch.int32) != -1).sum().item())
 
-    # the same geometry with quantised 64-byte nodes (GRT_BUILD_QUANTIZED_NODES): build,
-    # closest and any hit (tmax infinite and 2.9), and how many hit records equal the
-    # 128-byte nodes' (the rest are equal-t ties)
-    geomq = Geometry(ctx, boxes=dbox, build_flags=grt.GRT_BUILD_QUANTIZED_NODES)
-    hqc, hqa, hqs = new_hits(n), new_hits(n), new_hits(n)
-    qruns = {"build": lambda: geomq.build(sh),
-             "closest": lambda: grt.grtTraceClosest(ctx.handle, None, geomq.handle, rays, n, hqc, table.handle, None, sh),
-             "any": lambda: grt.grtTraceAnyHit(ctx.handle, None, geomq.handle, rays, n, hqa, table.handle, None, sh),
-             "any_tmax_2.9": lambda: grt.grtTraceAnyHit(ctx.handle, None, geomq.handle, short, n, hqs, table.handle,
-                                                         None, sh)}
-    q_ms = {}
-    for name, fn in qruns.items():
-        vals = []
-        for k in range(3 + 5):
-            flush.zero_()
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            if k >= 3:
-                vals.append(e0.elapsed_time(e1))
-        q_ms[name] = statistics.mean(vals)
-    torch.cuda.synchronize()
-    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
-    quantized = {"build_ms": round(q_ms["build"], 4),
-                 "closest_ms": round(q_ms["closest"], 4), "any_ms": round(q_ms["any"], 4),
-                 "any_tmax_2.9_ms": round(q_ms["any_tmax_2.9"], 4),
-                 "closest_mrays_per_s": round(n / q_ms["closest"] / 1e3, 1),
-                 "any_mrays_per_s": round(n / q_ms["any"] / 1e3, 1),
-                 "closest_records_equal": int((hqc == hc).all(dim=1).sum().item()),
-                 "occluded_equal": int(((hqa[:, 1] != -1) == (ha[:, 1] != -1)).sum().item()),
-                 "occluded_tmax_2.9_equal": int(((hqs[:, 1] != -1) == (hs[:, 1] != -1)).sum().item()),
-                 "node_bytes": 64}
-    geomq.close()
+    # the same geometry with quantised 64-byte nodes (GRT_BUILD_QUANTIZED_NODES) and with
+    # 256-byte 8-wide nodes (GRT_BUILD_WIDE8_NODES): build, closest and any hit (tmax
+    # infinite and 2.9), and how many hit records equal the 128-byte 4-wide nodes' (the
+    # rest are equal-t ties)
+    node_formats = {}
+    for fname, fflag, fbytes in (("quantized_nodes", grt.GRT_BUILD_QUANTIZED_NODES, 64),
+                                 ("wide8_nodes", grt.GRT_BUILD_WIDE8_NODES, 256)):
+        node_formats[fname] = sphere_node_format(grt, ctx, table, dbox, fflag, fbytes, n, rays, short, hc, ha, hs,
+                                                 flush, stream, sh)
+
 
     # algorithmic bytes per launch from counting passes: per ray the ray and the hit
     # record, per 4-wide node visit 112 B, per sphere test its leaf's primitive ID (4 B)
@@ -1027,7 +1005,7 @@ def run_spheres(args, rank, world, local):
                                   "any": round(n / T.mean("any") / 1e3, 1),
                                   "any_tmax_2.9": round(n / statistics.mean(short_ms) / 1e3, 1)},
             "occluded_tmax_2.9": occl_short,
-            "quantized_nodes": quantized,
+            "node_formats": node_formats,
             "build": {"ms": round(T.mean("build"), 4), "prims": prims,
                       "mprims_per_s": round(prims / T.mean("build") / 1e3, 1)},
             "kernel_ms": {k: round(T.mean(k), 4) for k in T.names},
@@ -1045,6 +1023,47 @@ def run_spheres(args, rank, world, local):
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def sphere_node_format(grt, ctx, table, dbox, flag, node_bytes, n, rays, short, hc, ha, hs, flush, stream, sh):
+    """The sphere geometry built with another node format (`flag`): build, closest and any
+    hit (tmax infinite and 2.9) timed with CUDA events after an L2 flush (mean of 5 after
+    3 warm-up runs), and how many hit records equal those of the 128-byte 4-wide nodes
+    (hc, ha, hs; the rest are equal-t ties)."""
+    import torch
+
+    from paper_2603_00292_gb300.objects import Geometry, new_hits
+
+    g = Geometry(ctx, boxes=dbox, build_flags=flag)
+    qc, qa, qs = new_hits(n), new_hits(n), new_hits(n)
+    runs = {"build": lambda: g.build(sh),
+            "closest": lambda: grt.grtTraceClosest(ctx.handle, None, g.handle, rays, n, qc, table.handle, None, sh),
+            "any": lambda: grt.grtTraceAnyHit(ctx.handle, None, g.handle, rays, n, qa, table.handle, None, sh),
+            "any_tmax_2.9": lambda: grt.grtTraceAnyHit(ctx.handle, None, g.handle, short, n, qs, table.handle, None,
+                                                       sh)}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = {}
+    for name, fn in runs.items():
+        vals = []
+        for k in range(3 + 5):
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 3:
+                vals.append(e0.elapsed_time(e1))
+        ms[name] = statistics.mean(vals)
+    torch.cuda.synchronize()
+    assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+    out = {"node_bytes": node_bytes, "build_ms": round(ms["build"], 4), "closest_ms": round(ms["closest"], 4),
+           "any_ms": round(ms["any"], 4), "any_tmax_2.9_ms": round(ms["any_tmax_2.9"], 4),
+           "closest_mrays_per_s": round(n / ms["closest"] / 1e3, 1), "any_mrays_per_s": round(n / ms["any"] / 1e3, 1),
+           "closest_records_equal": int((qc == hc).all(dim=1).sum().item()),
+           "occluded_equal": int(((qa[:, 1] != -1) == (ha[:, 1] != -1)).sum().item()),
+           "occluded_tmax_2.9_equal": int(((qs[:, 1] != -1) == (hs[:, 1] != -1)).sum().item())}
+    g.close()
+    return out
 
 
 def cpu_spheres(sph, target_s: float):

@@ -140,7 +140,8 @@ typedef enum grtBuildFlags {
     GRT_BUILD_PREFER_BALANCED = 1,
     GRT_BUILD_PREFER_HIGH_QUALITY = 2,
     GRT_BUILD_CLUSTER_SUBTREES = 3,
-    GRT_BUILD_QUANTIZED_NODES = 0x100
+    GRT_BUILD_QUANTIZED_NODES = 0x100,
+    GRT_BUILD_WIDE8_NODES = 0x200
 } grtBuildFlags;
 /* GRT_BUILD_QUANTIZED_NODES, ORed with any of the four: traversal reads 64-byte
  * quantised 4-wide nodes instead of the 128-byte ones (the paper's wide trees, Sec. 6.2,
@@ -156,7 +157,24 @@ typedef enum grtBuildFlags {
  * fit (and after each UPDATE), beside the 128-byte nodes (grtBvhInfo.quantNodes). Like
  * the method, the bit is fixed by grtCreateGeometry; a grtBuildGeometry given options
  * must repeat it. Scene (top-level) builds ignore it: their own nodes stay 128-byte,
- * while instances of quantised geometries are traversed in their format. */
+ * while instances of quantised geometries are traversed in their format.
+ *
+ * GRT_BUILD_WIDE8_NODES, ORed with any of the four (not with QUANTIZED_NODES), for
+ * geometries and scenes: traversal reads 256-byte 8-wide nodes (the branching factor 8
+ * the paper names beside 4, Sec. 6.2), written after the fit (and after each UPDATE)
+ * beside the 4-wide ones (grtBvhInfo.wide8Nodes). The 8-wide node of binary node k holds
+ * k's descendants three levels down: slots 4s..4s+3 come from child s, a leaf child in
+ * slot 4s alone, an internal child's children t in slots 4s+2t and 4s+2t+1 (their own
+ * two children, or the leaf itself and an empty slot); a walk from node 0 meets the
+ * nodes of binary depth divisible by 3. Layout (16 float4): row 4a + 2 side + half =
+ * axis a's lower (side 0) or upper (side 1) planes of slots 4 half .. 4 half + 3; rows
+ * 12 and 13 the child words (0xFFFFFFFF = empty, box +inf / -inf); rows 14-15 zero. A
+ * scene built with the bit has an 8-wide top level and walks its instances' 8-wide
+ * nodes: every instanced geometry must have them (an instance of another geometry is
+ * left empty and latches GRT_ERROR_INVALID_PARAMETER for grtGetLastDeviceError). A
+ * scene without the bit walks the 4-wide (or quantised) nodes of every geometry,
+ * 8-wide ones included. The batched launch builds the 8-wide nodes of such geometries
+ * and traces them through their 4-wide nodes. */
 
 typedef struct grtBuildOptions {
     uint32_t buildFlags; /* grtBuildFlags */
@@ -428,7 +446,7 @@ typedef struct grtDeviceTarget {
     uint32_t primCount;
     uint32_t numGeomTypes;        /* of the function table */
     uint32_t rayType;             /* function-table row used by the queries */
-    uint32_t nodeFormat;          /* 0: nodes are 128-byte 4-wide nodes; 1: 64-byte quantised ones */
+    uint32_t nodeFormat;          /* 0: nodes are 128-byte 4-wide nodes; 1: 64-byte quantised ones; 2: 8-wide */
 } grtDeviceTarget;
 
 /* Fills *out for exactly one of scene / geom (built), with an optional function table
@@ -653,6 +671,8 @@ typedef struct grtBvhInfo {
     const void* wideNodes; /* nodeCount x 128-byte 4-wide nodes (layout below), read by traversal unless quantised */
     const void* quantNodes; /* nodeCount x 64-byte quantised 4-wide nodes (GRT_BUILD_QUANTIZED_NODES), read by
                                traversal instead of wideNodes; NULL for other geometries and for scenes */
+    const void* wide8Nodes; /* nodeCount x 256-byte 8-wide nodes (GRT_BUILD_WIDE8_NODES), read by traversal
+                               instead of wideNodes; NULL otherwise */
 } grtBvhInfo;
 /*
  * Node (64 bytes, 4 x float4): children c0 and c1 of internal node k

@@ -37,6 +37,7 @@ GRT_BUILD_PREFER_BALANCED = 1      # PLOC clustering, search radius 8
 GRT_BUILD_PREFER_HIGH_QUALITY = 2  # PLOC clustering, search radius 32
 GRT_BUILD_CLUSTER_SUBTREES = 3     # clustering inside the linear BVH's subtrees, one bottom-up pass
 GRT_BUILD_QUANTIZED_NODES = 0x100  # ORed with a method: traversal reads 64-byte quantised 4-wide nodes
+GRT_BUILD_WIDE8_NODES = 0x200      # ORed with a method: traversal reads 256-byte 8-wide nodes
 CLUSTER_CAP = 16                   # clusters a subtree passes up (the library's kClusterCap)
 GRT_INSTANCE_GEOMETRY = 0
 GRT_INTERSECT_NONE = 0
@@ -107,7 +108,8 @@ class grtCamera(ctypes.Structure):
 class grtBvhInfo(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("parents", ctypes.c_void_p),
                 ("nodeCount", ctypes.c_uint32), ("primCount", ctypes.c_uint32), ("primType", ctypes.c_uint32),
-                ("mortonBits", ctypes.c_uint32), ("wideNodes", ctypes.c_void_p), ("quantNodes", ctypes.c_void_p)]
+                ("mortonBits", ctypes.c_uint32), ("wideNodes", ctypes.c_void_p), ("quantNodes", ctypes.c_void_p),
+                ("wide8Nodes", ctypes.c_void_p)]
 
 
 class grtPathTraceInput(ctypes.Structure):

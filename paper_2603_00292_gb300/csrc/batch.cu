@@ -21,9 +21,12 @@
 // A scene whose geometry was created with GRT_BUILD_CLUSTER_SUBTREES (any size) has its
 // emission write the LBVH topology to scratch, then one more phase, the bottom-up
 // clustering walk over leaf chunks (cluster.cuh), before the fit; its trace is 4 + 3P.
-// A scene whose geometry has quantised nodes (GRT_BUILD_QUANTIZED_NODES) has one more
-// phase after the fit, the quantisation of its 4-wide nodes over node chunks, before
-// its trace; a scene built by one block quantises at the end of that block's build.
+// A scene whose geometry has quantised or 8-wide nodes (GRT_BUILD_QUANTIZED_NODES,
+// GRT_BUILD_WIDE8_NODES) has one more phase after the fit, writing them over node
+// chunks, before its trace; a scene built by one block writes them at the end of that
+// block's build. Traces read the quantised nodes, or the 4-wide ones of 8-wide
+// geometries (the persistent kernel keeps one 4-slot traversal to stay within its
+// register budget).
 // An item of phase k waits until every item of phase k-1 of its scene has finished
 // (per-scene completion counters). The host orders the queue so that an item only
 // ever waits for items taken from the queue before it, so a waiting block never
@@ -55,6 +58,7 @@ struct BatchSceneDev : BlockBuild {
     uint32_t tracePhase;
     uint32_t cluster;     // built by subtree clustering
     uint32_t quant;       // quantised 4-wide nodes written after the fit (one more phase)
+    uint32_t wide8;       // 8-wide nodes written after the fit (the same added phase)
     const float4* rayBuf;
     uint32_t* hitBuf;
     // subtree clustering scratch (cluster.cuh)
@@ -173,8 +177,8 @@ struct ChunkRaySource {
 __device__ __noinline__ void traceChunk(const BatchParams& B, const BatchSceneDev& S, uint32_t chunk, unsigned long long item,
                            uint32_t* smem) {
     TraceParams P{};
-    P.target.nodes = S.qnodes ? S.qnodes : S.wide;
-    P.target.quant = S.qnodes != nullptr;
+    P.target.nodes = S.qnodes ? S.qnodes : S.wide;  // 8-wide geometries are traced through their 4-wide nodes
+    P.target.fmt = S.qnodes ? 1u : 0u;
     P.target.leaves = S.leaves;
     P.target.primType = GRT_PRIMITIVE_TRIANGLE_MESH;
     P.target.geomType = 0;
@@ -197,7 +201,7 @@ __device__ __noinline__ void traceChunk(const BatchParams& B, const BatchSceneDe
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{smem + threadIdx.x, B.globalStack + gtid, B.sharedDepth, B.globalDepth, B.globalStride, 0};
     ChunkRaySource src{&P, base, n};
-    refillLoop<false, false, false>(P, st, src);
+    refillLoop<false, false, false, kFmQuant>(P, st, src);
     __syncthreads();  // hit records of the chunk complete
     for (uint32_t r = base + threadIdx.x; r < base + n; r += blockDim.x) refineHit(P, r);
 }
@@ -284,10 +288,12 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
         } else if (it.phase == 3 * S.passes + 2 + S.cluster) {
             const uint32_t b0 = it.chunk * B.buildChunk;
             fitRange(S, b0, min(S.n, b0 + B.buildChunk));
-        } else if (S.quant && it.phase == 3 * S.passes + 3 + S.cluster) {
+        } else if ((S.quant | S.wide8) && it.phase == 3 * S.passes + 3 + S.cluster) {
             const uint32_t m = S.n > 1 ? S.n - 1 : 1u, b1 = min(m, (it.chunk + 1) * B.buildChunk);
-            for (uint32_t k = it.chunk * B.buildChunk + threadIdx.x; k < b1; k += blockDim.x)
-                quantizeWideNode(S.wide + kWideWords * (size_t)k, S.qnodes + kQuantWords * (size_t)k);
+            for (uint32_t k = it.chunk * B.buildChunk + threadIdx.x; k < b1; k += blockDim.x) {
+                if (S.quant) quantizeWideNode(S.wide + kWideWords * (size_t)k, S.qnodes + kQuantWords * (size_t)k);
+                if (S.wide8) wide8Node(S.nodes, S.n, k, S.w8nodes);
+            }
         } else {
             traceChunk(B, S, it.chunk, item, smem);
         }
@@ -404,12 +410,14 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         d.sortChunks = std::max(1u, ceilDiv(n, chunkKeys));
         d.passes = (d.bits + 7) / 8;
         d.quant = (o->quant && n > 0) ? 1u : 0u;
-        d.tracePhase = d.small ? 1u : 3u * d.passes + 3u + d.cluster + d.quant;
+        d.wide8 = (o->wide8 && n > 0) ? 1u : 0u;
+        d.tracePhase = d.small ? 1u : 3u * d.passes + 3u + d.cluster + (d.quant | d.wide8);
         d.rayBuf = (const float4*)in.rays;
         d.hitBuf = (uint32_t*)in.hits;
         d.nodes = (float4*)o->nodes;
         d.wide = (float4*)o->wide;
         d.qnodes = (float4*)o->qnodes;
+        d.w8nodes = (float4*)o->w8nodes;
         d.leaves = o->leaves;
         d.parents = (uint32_t*)o->parents;
         d.primToLeaf = o->primToLeaf;
@@ -441,7 +449,8 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (d.cluster && ph == 3 * d.passes + 2) return ceilDiv(d.n, kWalkLeavesPerThread * opt.blockSize);
         if (ph == 3 * d.passes + 2) return ceilDiv(d.n, opt.buildChunk);  // the fit
         if (d.cluster && ph == 3 * d.passes + 3) return ceilDiv(d.n, opt.buildChunk);  // the fit after clustering
-        if (d.quant && ph == 3 * d.passes + 3 + d.cluster) return ceilDiv(std::max(d.n - 1, 1u), opt.buildChunk);
+        if ((d.quant | d.wide8) && ph == 3 * d.passes + 3 + d.cluster)
+            return ceilDiv(std::max(d.n - 1, 1u), opt.buildChunk);
         return 0u;
     };
     for (uint32_t g0 = 0; g0 < sceneCount; g0 += opt.sceneGroup) {

@@ -269,6 +269,30 @@ __global__ void __launch_bounds__(256) quantizeKernel(const float4* wide, uint32
     if (k < m) quantizeWideNode(wide + kWideWords * (size_t)k, qnodes + kQuantWords * (size_t)k);
 }
 
+// The 8-wide node of each of the m binary nodes of an n-primitive tree (the
+// GRT_BUILD_WIDE8_NODES layout).
+__global__ void __launch_bounds__(256) wide8Kernel(const float4* nodes, uint32_t n, uint32_t m, float4* w8) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) wide8Node(nodes, n, k, w8);
+}
+
+// The extra node formats of object o, after its fit.
+static grtError launchNodeFormats(const BvhObject* o, cudaStream_t s) {
+    if (o->qnodes) {
+        quantizeKernel<<<ceilDiv(o->nodeCount, 256), 256, 0, s>>>((const float4*)o->wide, o->nodeCount,
+                                                                  (float4*)o->qnodes);
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
+    }
+    if (o->w8nodes) {
+        wide8Kernel<<<ceilDiv(o->nodeCount, 256), 256, 0, s>>>((const float4*)o->nodes, o->primCount, o->nodeCount,
+                                                               (float4*)o->w8nodes);
+        GRT_LAUNCH_CHECK();
+        noteLaunches(1);
+    }
+    return GRT_SUCCESS;
+}
+
 // ======================================================================= small builds
 // Up to kSmallBuild primitives (kSmallScene instances) a build runs in one block of
 // kSmallBuildThreads threads, as one launch, instead of a dozen grid-wide launches whose
@@ -330,6 +354,7 @@ static BlockBuild blockBuildOf(Context* c, BvhObject* o, const BuildLayout& L, c
     B.nodes = (float4*)o->nodes;
     B.wide = (float4*)o->wide;
     B.qnodes = (float4*)o->qnodes;
+    B.w8nodes = (float4*)o->w8nodes;
     B.leaves = o->leaves;
     B.parents = (uint32_t*)o->parents;
     B.primToLeaf = o->primToLeaf;
@@ -374,6 +399,8 @@ struct InstanceInput {
     float4* fwd32;             // kFrameRows rows per instance ID
     float4* centroids;
     uint32_t* bounds;
+    uint32_t wide8;            // the scene has 8-wide nodes: so must every instanced geometry
+    uint32_t* error;           // the context's device error word
 };
 
 // Per instance: frame M = T R S and its inverse S^-1 R^T (x - T) in FP64 (rounded to
@@ -414,11 +441,17 @@ __device__ __forceinline__ float3 setupInstance(const InstanceInput& I, uint32_t
                                                  __double2float_rn(F[r][2]), __double2float_rn(F[r][3]));
         for (int q = 0; q < 4; ++q) I.inv64[i].inv[r][q] = G[r][q];
     }
-    rec.nodes = g->nodes;
+    // an 8-wide top level walks 8-wide bottom levels; a 4-wide one the geometry's 4-wide
+    // (or quantised) nodes. An 8-wide scene instancing a geometry without 8-wide nodes
+    // latches GRT_ERROR_INVALID_PARAMETER and leaves that instance empty.
+    const bool missing8 = I.wide8 && g->primCount > 0 && g->nodes8 == nullptr;
+    if (missing8) latchError(I.error, GRT_ERROR_INVALID_PARAMETER);
+    rec.nodes = I.wide8 ? g->nodes8 : g->nodes;
     rec.leaves = g->leaves;
     rec.instanceID = i;
-    rec.typeBits = (g->geomType & 0xFFFFFFu) | ((uint32_t)g->primType << 24) | (g->nodeFormat ? kInstQuant : 0u) |
-                   (g->primCount == 0 ? kInstEmpty : 0u);
+    rec.typeBits = (g->geomType & 0xFFFFFFu) | ((uint32_t)g->primType << 24) |
+                   (I.wide8 ? kInstWide8 : g->nodeFormat == 1 ? kInstQuant : 0u) |
+                   ((g->primCount == 0 || missing8) ? kInstEmpty : 0u);
     rec.geometry = g;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     if (g->primCount > 0) {
@@ -517,13 +550,13 @@ PrimSource primSource(const grtGeometryBuildInput* in, uint32_t count) {
     return S;
 }
 
-// Live geometries created with GRT_BUILD_QUANTIZED_NODES. While there are none, no walk
-// can meet quantised nodes, and traces run kernels without that form.
+// Live geometries created with GRT_BUILD_QUANTIZED_NODES. While there are none, no
+// 4-wide walk can meet quantised nodes, and traces run kernels without that form.
 static std::atomic<int> g_quantGeometries{0};
 bool anyQuantGeometry() { return g_quantGeometries.load(std::memory_order_relaxed) > 0; }
 
 static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geomType, uint32_t mortonBits,
-                                BvhObject** out, bool quant = false) {
+                                BvhObject** out, bool quant = false, bool wide8 = false) {
     BvhObject* o = new BvhObject();
     o->primCount = count;
     o->nodeCount = count == 0 ? 0 : std::max(count - 1, 1u);
@@ -532,12 +565,15 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     o->mortonBits = mortonBits;
     o->built = false;
     o->quant = quant;
+    o->wide8 = wide8;
     size_t leafBytes = primType == GRT_PRIMITIVE_TRIANGLE_MESH ? 48 : (primType == kPrimScene ? 128 : 4);
     cudaError_t e = cudaMalloc(&o->dHeader, sizeof(BvhHeader));
     if (e == cudaSuccess && count) e = cudaMalloc(&o->nodes, (size_t)o->nodeCount * 64);
     if (e == cudaSuccess && count) e = cudaMalloc(&o->wide, (size_t)o->nodeCount * kWideWords * sizeof(float4));
     if (e == cudaSuccess && count && quant)
         e = cudaMalloc(&o->qnodes, (size_t)o->nodeCount * kQuantWords * sizeof(float4));
+    if (e == cudaSuccess && count && wide8)
+        e = cudaMalloc(&o->w8nodes, (size_t)o->nodeCount * kWide8Words * sizeof(float4));
     if (e == cudaSuccess && count) e = cudaMalloc(&o->leaves, (size_t)count * leafBytes);
     if (e == cudaSuccess && count) e = cudaMalloc(&o->parents, (size_t)(2 * count - 1) * 4);
     if (e == cudaSuccess && count && primType != GRT_PRIMITIVE_AABB_LIST) e = cudaMalloc(&o->primToLeaf, (size_t)count * 4);
@@ -549,6 +585,7 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     h.primType = (uint16_t)primType;
     h.nodeFormat = quant ? 1 : 0;
     h.nodes = (const float4*)(quant ? o->qnodes : o->wide);
+    h.nodes8 = (const float4*)o->w8nodes;
     h.leaves = o->leaves;
     h.nodeCount = o->nodeCount;
     h.geomType = geomType;
@@ -559,6 +596,7 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
         cudaFree(o->nodes);
         cudaFree(o->wide);
         cudaFree(o->qnodes);
+        cudaFree(o->w8nodes);
         cudaFree(o->leaves);
         cudaFree(o->parents);
         cudaFree(o->primToLeaf);
@@ -581,6 +619,7 @@ static void destroyBvhObject(BvhObject* o) {
     cudaFree(o->nodes);
     cudaFree(o->wide);
     cudaFree(o->qnodes);
+    cudaFree(o->w8nodes);
     cudaFree(o->leaves);
     cudaFree(o->parents);
     cudaFree(o->primToLeaf);
@@ -637,15 +676,20 @@ static grtError resetBuildScratch(const BuildLayout& L, char* temp, uint32_t n, 
 // kSubtreeMethod = clustering inside the LBVH's subtrees (cluster.cuh), else PLOC with
 // this search radius (ploc.cuh).
 constexpr uint32_t kSubtreeMethod = 0xFFFFu;
-static uint32_t buildMethod(const grtBuildOptions* opt) { return opt ? opt->buildFlags & ~(uint32_t)GRT_BUILD_QUANTIZED_NODES : 0u; }
+static uint32_t buildMethod(const grtBuildOptions* opt) {
+    return opt ? opt->buildFlags & ~(uint32_t)(GRT_BUILD_QUANTIZED_NODES | GRT_BUILD_WIDE8_NODES) : 0u;
+}
 static bool quantFlag(const grtBuildOptions* opt) { return opt && (opt->buildFlags & GRT_BUILD_QUANTIZED_NODES); }
+static bool wide8Flag(const grtBuildOptions* opt) { return opt && (opt->buildFlags & GRT_BUILD_WIDE8_NODES); }
 static uint32_t clusterRadius(const grtBuildOptions* opt) {
     const uint32_t m = buildMethod(opt);
     if (m == GRT_BUILD_PREFER_FAST) return 0;
     if (m == GRT_BUILD_CLUSTER_SUBTREES) return kSubtreeMethod;
     return m == GRT_BUILD_PREFER_BALANCED ? 8u : 32u;
 }
-static bool validBuildFlags(const grtBuildOptions* opt) { return !opt || buildMethod(opt) <= 3u; }
+static bool validBuildFlags(const grtBuildOptions* opt) {
+    return !opt || (buildMethod(opt) <= 3u && !(quantFlag(opt) && wide8Flag(opt)));
+}
 
 static std::mutex g_methodLock;
 static std::unordered_map<const BvhObject*, uint32_t> g_clusterRadius;  // objects with a PLOC build
@@ -815,13 +859,7 @@ static grtError issueGeometryBuild(Context* c, BvhObject* o, uint32_t op, const 
         fitKernel<1><<<ceilDiv(n, 256), 256, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
     noteLaunches(1);
-    if (o->qnodes) {
-        quantizeKernel<<<ceilDiv(o->nodeCount, 256), 256, 0, s>>>((const float4*)o->wide, o->nodeCount,
-                                                                  (float4*)o->qnodes);
-        GRT_LAUNCH_CHECK();
-        noteLaunches(1);
-    }
-    return GRT_SUCCESS;
+    return launchNodeFormats(o, s);
 }
 
 // Repeated BUILDs of a geometry from the same buffers replay a CUDA graph of the launch
@@ -943,7 +981,8 @@ grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, c
     if (e != GRT_SUCCESS) return e;
     if (!validBuildFlags(options) || (clusterRadius(options) && n > kPlocIndex)) return GRT_ERROR_INVALID_PARAMETER;
     BvhObject* o = nullptr;
-    e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(n, options), &o, quantFlag(options));
+    e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(n, options), &o, quantFlag(options),
+                        wide8Flag(options));
     if (e != GRT_SUCCESS) return e;
     if (clusterRadius(options)) {
         // the finishing block's shared memory is above the default limit
@@ -978,7 +1017,8 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
         return GRT_ERROR_INVALID_PARAMETER;
     const uint32_t radius = radiusOf(o);
     if (!validBuildFlags(options) || (options && clusterRadius(options) != radius)) return GRT_ERROR_INVALID_PARAMETER;
-    if (options && quantFlag(options) != o->quant) return GRT_ERROR_INVALID_PARAMETER;
+    if (options && (quantFlag(options) != o->quant || wide8Flag(options) != o->wide8))
+        return GRT_ERROR_INVALID_PARAMETER;
     Context* c = asContext(ctx);
     cudaStream_t s = (cudaStream_t)stream;
     o->geomType = input->geomType;
@@ -1040,7 +1080,9 @@ grtError grtCreateScene(grtContext ctx, const grtSceneBuildInput* input, const g
     grtError e = validateSceneInput(input);
     if (e != GRT_SUCCESS) return e;
     BvhObject* o = nullptr;
-    e = createBvhObject(input->instanceCount, kPrimScene, 0, resolveMortonBits(input->instanceCount, options), &o);
+    if (!validBuildFlags(options)) return GRT_ERROR_INVALID_PARAMETER;
+    e = createBvhObject(input->instanceCount, kPrimScene, 0, resolveMortonBits(input->instanceCount, options), &o,
+                        false, wide8Flag(options));
     if (e != GRT_SUCCESS) return e;
     *out = reinterpret_cast<grtScene>(o->dHeader);
     return GRT_SUCCESS;
@@ -1056,7 +1098,7 @@ grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* in
     if (op != GRT_BUILD_OPERATION_BUILD && op != GRT_BUILD_OPERATION_UPDATE) return GRT_ERROR_INVALID_PARAMETER;
     const uint32_t n = o->primCount;
     if (n > 0 && (!temp || ((uintptr_t)temp & 15))) return GRT_ERROR_INVALID_PARAMETER;
-    (void)options;
+    if (options && (!validBuildFlags(options) || wide8Flag(options) != o->wide8)) return GRT_ERROR_INVALID_PARAMETER;
     Context* c = asContext(ctx);
     cudaStream_t s = (cudaStream_t)stream;
     if (n == 0) {
@@ -1076,6 +1118,8 @@ grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* in
     I.bounds = (uint32_t*)(t + L.bounds);
     I.inv64 = o->inv64;
     I.fwd32 = o->fwd32;
+    I.wide8 = o->wide8 ? 1u : 0u;
+    I.error = &workspace(c)->error;
     if (n <= kSmallScene) {
         BlockBuild B = blockBuildOf(c, o, L, t, 2u);
         B.instBoxes = I.boxes;
@@ -1119,6 +1163,8 @@ grtError grtBuildScene(grtContext ctx, uint32_t op, const grtSceneBuildInput* in
     fitKernel<2><<<ceilDiv(n, 256), 256, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
     noteLaunches(1);
+    e = launchNodeFormats(o, s);
+    if (e != GRT_SUCCESS) return e;
     o->built = true;
     return GRT_SUCCESS;
 }

@@ -279,6 +279,7 @@ grtError grtGetBvhInfo(grtContext ctx, grtGeometry geom, grtScene scene, grtBvhI
     info->nodes = o->nodes;
     info->wideNodes = o->wide;
     info->quantNodes = o->quant ? o->qnodes : nullptr;
+    info->wide8Nodes = o->wide8 ? o->w8nodes : nullptr;
     info->leaves = o->leaves;
     info->parents = o->parents;
     info->nodeCount = o->nodeCount;

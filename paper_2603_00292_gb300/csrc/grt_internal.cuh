@@ -16,21 +16,24 @@ constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 constexpr uint32_t kPrimScene = 2;  // primType of a scene header
 constexpr int kWideWords = 8;       // float4 per 4-wide node (128 B)
 constexpr int kQuantWords = 4;      // float4 per quantised 4-wide node (64 B)
+constexpr int kWide8Words = 16;     // float4 per 8-wide node (256 B)
 
-// Device-resident header that a grtGeometry / grtScene handle points to (64 B).
+// Device-resident header that a grtGeometry / grtScene handle points to (128 B).
 struct alignas(16) BvhHeader {
     float rootLo[3];      // box of everything below the root (written by the build)
     uint32_t primCount;
     float rootHi[3];
     uint16_t primType;    // grtPrimitiveType, or kPrimScene
-    uint16_t nodeFormat;  // 0: nodes are 4-wide nodes (kWideWords float4); 1: quantised (kQuantWords)
-    const float4* nodes;  // nodeCount nodes in nodeFormat, read by traversal
+    uint16_t nodeFormat;  // of `nodes`: 0 4-wide nodes (kWideWords float4), 1 quantised (kQuantWords)
+    const float4* nodes;  // nodeCount nodes in nodeFormat: what a 4-wide walk reads
     const void* leaves;   // triangle records / prim IDs / instance records
     uint32_t nodeCount;
     uint32_t geomType;
     const uint32_t* primToLeaf;  // primitive (or instance) ID -> sorted leaf position
+    const float4* nodes8;        // nodeCount 8-wide nodes (kWide8Words float4), or null: what an 8-wide walk reads
+    uint32_t pad[14];
 };
-static_assert(sizeof(BvhHeader) == 64, "header size");
+static_assert(sizeof(BvhHeader) == 128, "header size");
 
 // Instance record of a scene leaf (128 B): the float32 inverse frame and the bottom
 // level's arrays (read when a ray enters the instance), the instance's world box
@@ -54,9 +57,10 @@ struct InstanceFrames64 {
 };
 constexpr uint32_t kInstEmpty = 0x80000000u;
 constexpr uint32_t kInstQuant = 0x40000000u;  // the instance's geometry has quantised nodes
+constexpr uint32_t kInstWide8 = 0x20000000u;  // the instance's geometry has 8-wide nodes
 constexpr int kFrameRows = 6;  // float4 rows per instance in BvhObject::fwd32
 __host__ __device__ inline uint32_t instGeomType(uint32_t bits) { return bits & 0xFFFFFFu; }
-__host__ __device__ inline uint32_t instPrimType(uint32_t bits) { return (bits >> 24) & 0x3Fu; }
+__host__ __device__ inline uint32_t instPrimType(uint32_t bits) { return (bits >> 24) & 0x1Fu; }
 static_assert(sizeof(InstanceRecord) == 128, "instance record size");
 
 // Device error word values are grtError codes; the first nonzero one latched wins
@@ -116,6 +120,7 @@ struct BvhObject {
     void* nodes;  // binary nodes (64 B each)
     void* wide;   // 4-wide nodes (128 B each), one per binary node
     void* qnodes; // quantised 4-wide nodes (64 B each), one per binary node, or null
+    void* w8nodes; // 8-wide nodes (256 B each), one per binary node, or null
     void* leaves;
     int32_t* parents;
     uint32_t* primToLeaf;  // primitive (instance) ID -> sorted position (triangles, scenes)
@@ -130,6 +135,7 @@ struct BvhObject {
     uint32_t vertexCount;  // triangle meshes: the vertex count of the last build input
     bool built;
     bool quant;  // built with GRT_BUILD_QUANTIZED_NODES (qnodes allocated when primCount > 0)
+    bool wide8;  // built with GRT_BUILD_WIDE8_NODES (w8nodes allocated when primCount > 0)
 };
 BvhObject* findBvh(const void* handle);
 bool anyQuantGeometry();  // whether a geometry with quantised nodes exists in the process

@@ -346,6 +346,81 @@ __device__ __forceinline__ void quantizeWideNode(const float4* W, float4* Q) {
     Q[3] = make_float4(__uint_as_float(c[2]), __uint_as_float(c[3]), 0.f, 0.f);
 }
 
+// ======================================================================= 8-wide nodes (A7)
+// The 8-wide node of binary node k (kWide8Words float4): k's descendants three levels
+// down. Slots 4s..4s+3 come from child s: a leaf child fills slot 4s (4s+1..4s+3 empty);
+// an internal child's children t fill slots 4s+2t and 4s+2t+1 with their own two
+// children, or with themselves (a leaf) and an empty slot. Rows 4a + 2 side + half hold
+// axis a's lower (side 0) or upper (side 1) planes of slots 4 half .. 4 half + 3, rows 12
+// and 13 the child words (binary format; kInvalid = empty, box +inf / -inf), rows 14-15
+// zero. Built from the binary nodes (read with L1-bypassing loads: they may have been
+// written earlier in the same launch). n = the primitive count (1: node 0 holds its leaf
+// as both children; the 8-wide node holds it once).
+__device__ __forceinline__ void binaryChildren(const float4* nodes, uint32_t k, float lo[2][3], float hi[2][3],
+                                               uint32_t w[2]) {
+    const float4* N = nodes + 4 * (size_t)k;
+    const float4 x = __ldcg(N), y = __ldcg(N + 1), z = __ldcg(N + 2), c = __ldcg(N + 3);
+    lo[0][0] = x.x, hi[0][0] = x.y, lo[1][0] = x.z, hi[1][0] = x.w;
+    lo[0][1] = y.x, hi[0][1] = y.y, lo[1][1] = y.z, hi[1][1] = y.w;
+    lo[0][2] = z.x, hi[0][2] = z.y, lo[1][2] = z.z, hi[1][2] = z.w;
+    w[0] = __float_as_uint(c.x), w[1] = __float_as_uint(c.y);
+}
+
+__device__ __forceinline__ void wide8Node(const float4* nodes, uint32_t n, uint32_t k, float4* out) {
+    float S[8][6];  // per slot lo.xyz, hi.xyz
+    uint32_t W[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        W[j] = kInvalid;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) S[j][a] = INFINITY, S[j][3 + a] = -INFINITY;
+    }
+    auto put = [&](int j, uint32_t w, const float* l, const float* h) {
+        W[j] = w;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) S[j][a] = l[a], S[j][3 + a] = h[a];
+    };
+    float cl[2][3], ch[2][3];
+    uint32_t cw[2];
+    binaryChildren(nodes, k, cl, ch, cw);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (s == 1 && n == 1) break;
+        if (cw[s] & kLeafBit) {
+            put(4 * s, cw[s], cl[s], ch[s]);
+            continue;
+        }
+        float gl[2][3], gh[2][3];
+        uint32_t gw[2];
+        binaryChildren(nodes, cw[s], gl, gh, gw);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (gw[t] & kLeafBit) {
+                put(4 * s + 2 * t, gw[t], gl[t], gh[t]);
+                continue;
+            }
+            float hl[2][3], hh[2][3];
+            uint32_t hw[2];
+            binaryChildren(nodes, gw[t], hl, hh, hw);
+            put(4 * s + 2 * t, hw[0], hl[0], hh[0]);
+            put(4 * s + 2 * t + 1, hw[1], hl[1], hh[1]);
+        }
+    }
+    float4* O = out + kWide8Words * (size_t)k;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int side = 0; side < 2; ++side)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = 3 * side + a;
+                O[4 * a + 2 * side + h] = make_float4(S[4 * h][q], S[4 * h + 1][q], S[4 * h + 2][q], S[4 * h + 3][q]);
+            }
+    O[12] = make_float4(__uint_as_float(W[0]), __uint_as_float(W[1]), __uint_as_float(W[2]), __uint_as_float(W[3]));
+    O[13] = make_float4(__uint_as_float(W[4]), __uint_as_float(W[5]), __uint_as_float(W[6]), __uint_as_float(W[7]));
+    O[14] = O[15] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Leaf k of the sorted order: writes the leaf record and walks up while this thread is
 // the second to reach a node, writing each box into its parent.
 //

@@ -26,6 +26,7 @@ struct BlockBuild {
     float4* nodes;
     float4* wide;
     float4* qnodes;    // quantised 4-wide nodes, written after the fit when not null
+    float4* w8nodes;   // 8-wide nodes, written after the fit when not null
     void* leaves;
     uint32_t* parents;
     uint32_t* primToLeaf;
@@ -600,18 +601,21 @@ __device__ __noinline__ void buildWholeTree(const BlockBuild& S, uint32_t chunkK
     fitRange(S, 0, S.n);
 }
 
-// buildWholeTree, then (with S.qnodes) the quantised form of every 4-wide node.
+// buildWholeTree, then (with S.qnodes) the quantised form of every 4-wide node, (with
+// S.w8nodes) every 8-wide node.
 template <typename K, int BITS>
 __device__ __noinline__ void buildWhole(const BlockBuild& S, uint32_t chunkKeys, uint32_t* smem,
                                         size_t smemBytes = 0) {
     if (S.n == 0) return;
     buildWholeTree<K, BITS>(S, chunkKeys, smem, smemBytes);
-    if (!S.qnodes) return;
-    __threadfence();  // the wide nodes are read back through L2
+    if (!S.qnodes && !S.w8nodes) return;
+    __threadfence();  // the wide and binary nodes are read back through L2
     __syncthreads();
     const uint32_t m = S.n > 1 ? S.n - 1 : 1u;
-    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x)
-        quantizeWideNode(S.wide + kWideWords * (size_t)k, S.qnodes + kQuantWords * (size_t)k);
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+        if (S.qnodes) quantizeWideNode(S.wide + kWideWords * (size_t)k, S.qnodes + kQuantWords * (size_t)k);
+        if (S.w8nodes) wide8Node(S.nodes, S.n, k, S.w8nodes);
+    }
 }
 
 }  // namespace grt

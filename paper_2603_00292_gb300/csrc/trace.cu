@@ -11,15 +11,15 @@
 
 namespace grt {
 
-// QN: some level of the walk may have quantised nodes (checked per level); false when
-// none can (no such geometry exists), which compiles that form out.
-template <bool ANY, bool SCENE, bool COUNT, bool QN = false>
+// FM: the node formats the walk may meet (traverse.cuh): kFmPlain (4-wide only),
+// kFmQuant (4-wide or quantised, read per level) or kFmWide8 (8-wide on every level).
+template <bool ANY, bool SCENE, bool COUNT, int FM = kFmPlain>
 __global__ void traceKernel(TraceParams P) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
     RayBufferSource<SCENE> src{P.count, &P};
-    refillLoop<ANY, SCENE, COUNT, QN>(P, st, src);
+    refillLoop<ANY, SCENE, COUNT, FM>(P, st, src);
 }
 
 // The closest hits' t, u, v recomputed in FP64, one thread per ray after traversal so
@@ -137,14 +137,14 @@ struct AoSource {
 
 // 96 registers: 5 blocks of 128 threads per SM instead of 4, 7% faster on the terrain
 // AO workload despite a few spills (the closest-hit kernel is faster uncapped).
-template <bool COUNT, bool QN = false>
+template <bool COUNT, int FM = kFmPlain>
 __global__ void __maxnreg__(96) aoTraceKernel(TraceParams P, const uint32_t* list, const uint32_t* listCount,
                                               uint32_t* counts, const float4* frames) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
     AoSource src{&P, list, listCount, counts, frames};
-    refillLoop<true, true, COUNT, QN>(P, st, src);
+    refillLoop<true, true, COUNT, FM>(P, st, src);
 }
 
 __global__ void aoFinishKernel(const uint32_t* __restrict__ list, const uint32_t* __restrict__ listCount,
@@ -275,13 +275,13 @@ struct ShadowSource {
     }
 };
 
-template <bool SCENE, bool QN = false>
+template <bool SCENE, int FM = kFmPlain>
 __global__ void shadeForwardKernel(TraceParams P, ShadeParams S) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
     ShadowSource<SCENE> src{&S};
-    refillLoop<true, SCENE, false, QN>(P, st, src);
+    refillLoop<true, SCENE, false, FM>(P, st, src);
 }
 
 // One pixel's share of the adjoint: dL/dc_k and dL/dv_k for the hit triangle's three
@@ -540,8 +540,8 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     if (geom && o->primType == kPrimScene) return GRT_ERROR_INVALID_PARAMETER;
     if (!o->built) return GRT_ERROR_NOT_BUILT;
     *isScene = scene != nullptr;
-    P.target.nodes = (const float4*)(o->qnodes ? o->qnodes : o->wide);
-    P.target.quant = o->qnodes != nullptr;
+    P.target.nodes = (const float4*)(o->qnodes ? o->qnodes : o->w8nodes ? o->w8nodes : o->wide);
+    P.target.fmt = o->qnodes ? 1u : o->w8nodes ? 2u : 0u;
     P.target.leaves = o->leaves;
     P.target.primType = o->primType;
     P.target.geomType = o->geomType;
@@ -601,14 +601,23 @@ static grtError bindGlobalStack(Context* c, const grtTraceOptions* opt, int thre
     return e;
 }
 
-// Whether a walk over P's target can meet quantised nodes: a geometry's own flag; for a
-// scene, whether any quantised geometry exists (a scene instances live geometries only).
-static bool quantWalk(const TraceParams& P, bool scene) { return scene ? anyQuantGeometry() : P.target.quant != 0; }
+// The node formats a walk over P's target can meet (the kernel variant to launch): a
+// geometry's own format; an 8-wide scene walks 8-wide levels only (its instances must be
+// 8-wide); a 4-wide scene walks the 4-wide or quantised nodes of its instances, and can
+// meet quantised ones only while such a geometry exists (a scene instances live
+// geometries only).
+static int walkFormats(const TraceParams& P, bool scene) {
+    if (P.target.fmt == 2) return kFmWide8;
+    if (P.target.fmt == 1 || (scene && anyQuantGeometry())) return kFmQuant;
+    return kFmPlain;
+}
 
 template <bool ANY, bool COUNT>
-static void traceKernelFor(bool scene, bool quant, void (**k)(TraceParams)) {
-    if (quant)
-        *k = scene ? traceKernel<ANY, true, COUNT, true> : traceKernel<ANY, false, COUNT, true>;
+static void traceKernelFor(bool scene, int fm, void (**k)(TraceParams)) {
+    if (fm == kFmWide8)
+        *k = scene ? traceKernel<ANY, true, COUNT, kFmWide8> : traceKernel<ANY, false, COUNT, kFmWide8>;
+    else if (fm == kFmQuant)
+        *k = scene ? traceKernel<ANY, true, COUNT, kFmQuant> : traceKernel<ANY, false, COUNT, kFmQuant>;
     else
         *k = scene ? traceKernel<ANY, true, COUNT> : traceKernel<ANY, false, COUNT>;
 }
@@ -630,11 +639,11 @@ static grtError launchTrace(grtContext ctx, grtScene scene, grtGeometry geom, co
     P.count = n;
     void (*kernel)(TraceParams) = nullptr;
     if (count)
-        traceKernelFor<ANY, true>(isScene, quantWalk(P, isScene), &kernel);
+        traceKernelFor<ANY, true>(isScene, walkFormats(P, isScene), &kernel);
     else
-        traceKernelFor<ANY, false>(isScene, quantWalk(P, isScene), &kernel);
+        traceKernelFor<ANY, false>(isScene, walkFormats(P, isScene), &kernel);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth, slotsOf(walkFormats(P, isScene))) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(n, bs));
     e = bindGlobalStack(c, opt, L.blocks * bs, P);
@@ -719,10 +728,10 @@ grtError grtTraceClosestNoAlloc(grtContext ctx, grtScene scene, grtGeometry geom
     P.count = rayCount;
     void (*kernel)(TraceParams) = nullptr;
     if (count)
-        traceKernelFor<false, true>(isScene, quantWalk(P, isScene), &kernel);
+        traceKernelFor<false, true>(isScene, walkFormats(P, isScene), &kernel);
     else
-        traceKernelFor<false, false>(isScene, quantWalk(P, isScene), &kernel);
-    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
+        traceKernelFor<false, false>(isScene, walkFormats(P, isScene), &kernel);
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth, slotsOf(walkFormats(P, isScene))) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(rayCount, bs));
     L.blocks = std::max(1, std::min<int>(L.blocks, (int)(capacity / perBlock)));  // the grid shrinks to fit
@@ -745,22 +754,27 @@ grtError grtGetTraceGlobalStackSize(grtContext ctx, const grtTraceOptions* optio
     grtError e = resolveOptions(options, &bs, &sh, &gl);
     if (e != GRT_SUCCESS) return e;
     Context* c = asContext(ctx);
-    const size_t smem = (size_t)bs * traceSmemWords(sh) * sizeof(uint32_t);
     int threads = 0;
-    void (*kernels[])(TraceParams) = {
-        traceKernel<false, false, false>,       traceKernel<false, true, false>,
-        traceKernel<true, false, false>,        traceKernel<true, true, false>,
-        traceKernel<false, false, true>,        traceKernel<false, true, true>,
-        traceKernel<true, false, true>,         traceKernel<true, true, true>,
-        traceKernel<false, false, false, true>, traceKernel<false, true, false, true>,
-        traceKernel<true, false, false, true>,  traceKernel<true, true, false, true>,
-        traceKernel<false, false, true, true>,  traceKernel<false, true, true, true>,
-        traceKernel<true, false, true, true>,   traceKernel<true, true, true, true>};
-    for (auto k : kernels) threads = std::max(threads, persistentShape(c, k, bs, smem).blocks * bs);
-    threads = std::max(threads, persistentShape(c, aoTraceKernel<false>, bs, smem).blocks * bs);
-    threads = std::max(threads, persistentShape(c, aoTraceKernel<true>, bs, smem).blocks * bs);
-    threads = std::max(threads, persistentShape(c, aoTraceKernel<false, true>, bs, smem).blocks * bs);
-    threads = std::max(threads, persistentShape(c, aoTraceKernel<true, true>, bs, smem).blocks * bs);
+    // every variant a launch may choose, each with its own shared memory
+    auto most = [&](auto k, int w) {
+        const size_t sm = (size_t)bs * traceSmemWords(sh, w) * sizeof(uint32_t);
+        threads = std::max(threads, persistentShape(c, k, bs, sm).blocks * bs);
+    };
+    most(traceKernel<false, false, false>, 4), most(traceKernel<false, true, false>, 4);
+    most(traceKernel<true, false, false>, 4), most(traceKernel<true, true, false>, 4);
+    most(traceKernel<false, false, true>, 4), most(traceKernel<false, true, true>, 4);
+    most(traceKernel<true, false, true>, 4), most(traceKernel<true, true, true>, 4);
+    most(traceKernel<false, false, false, kFmWide8>, 8), most(traceKernel<false, true, false, kFmWide8>, 8);
+    most(traceKernel<true, false, false, kFmWide8>, 8), most(traceKernel<true, true, false, kFmWide8>, 8);
+    most(traceKernel<false, false, true, kFmWide8>, 8), most(traceKernel<false, true, true, kFmWide8>, 8);
+    most(traceKernel<true, false, true, kFmWide8>, 8), most(traceKernel<true, true, true, kFmWide8>, 8);
+    most(traceKernel<false, false, false, kFmQuant>, 4), most(traceKernel<false, true, false, kFmQuant>, 4);
+    most(traceKernel<true, false, false, kFmQuant>, 4), most(traceKernel<true, true, false, kFmQuant>, 4);
+    most(traceKernel<false, false, true, kFmQuant>, 4), most(traceKernel<false, true, true, kFmQuant>, 4);
+    most(traceKernel<true, false, true, kFmQuant>, 4), most(traceKernel<true, true, true, kFmQuant>, 4);
+    most(aoTraceKernel<false>, 4), most(aoTraceKernel<true>, 4);
+    most(aoTraceKernel<false, kFmWide8>, 8), most(aoTraceKernel<true, kFmWide8>, 8);
+    most(aoTraceKernel<false, kFmQuant>, 4), most(aoTraceKernel<true, kFmQuant>, 4);
     *sizeBytes = (size_t)threads * gl * sizeof(uint32_t);
     return GRT_SUCCESS;
 }
@@ -772,8 +786,8 @@ grtError grtGetDeviceTarget(grtContext ctx, grtScene scene, grtGeometry geom, gr
     if (!o || (scene != nullptr) != (o->primType == kPrimScene)) return GRT_ERROR_INVALID_PARAMETER;
     if (!o->built) return GRT_ERROR_NOT_BUILT;
     grtDeviceTarget t{};
-    t.nodes = o->qnodes ? o->qnodes : o->wide;
-    t.nodeFormat = o->qnodes != nullptr;
+    t.nodes = o->qnodes ? o->qnodes : o->w8nodes ? o->w8nodes : o->wide;
+    t.nodeFormat = o->qnodes ? 1u : o->w8nodes ? 2u : 0u;
     t.leaves = o->leaves;
     t.primToLeaf = o->primToLeaf;
     t.frames64 = o->inv64;
@@ -900,10 +914,11 @@ grtError grtTraceAmbientOcclusion(grtContext ctx, grtScene scene, const grtRay* 
     if ((size_t)pixelCount * samplesPerPixel > 0xFFFFFFFEull) return GRT_ERROR_INVALID_PARAMETER;
     const bool count = options && (options->flags & GRT_TRACE_FLAG_COUNT);
     void (*kernel)(TraceParams, const uint32_t*, const uint32_t*, uint32_t*, const float4*) =
-        quantWalk(P, true) ? (count ? aoTraceKernel<true, true> : aoTraceKernel<false, true>)
-                           : (count ? aoTraceKernel<true> : aoTraceKernel<false>);
+        walkFormats(P, true) == kFmWide8 ? (count ? aoTraceKernel<true, kFmWide8> : aoTraceKernel<false, kFmWide8>)
+        : walkFormats(P, true) == kFmQuant ? (count ? aoTraceKernel<true, kFmQuant> : aoTraceKernel<false, kFmQuant>)
+                                           : (count ? aoTraceKernel<true> : aoTraceKernel<false>);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth, slotsOf(walkFormats(P, true))) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     // scratch after the global stack: the hit count (256 B), the list of hit pixels and
     // their AO frames (48 B each)
@@ -1220,9 +1235,12 @@ static grtError prepareShade(grtContext ctx, grtScene scene, grtGeometry geom, c
 static grtError launchShadeForward(Context* c, bool scene, TraceParams& P, const ShadeParams& S, int bs,
                                    const grtTraceOptions* options, cudaStream_t s) {
     void (*kernel)(TraceParams, ShadeParams) =
-        quantWalk(P, scene) ? (scene ? shadeForwardKernel<true, true> : shadeForwardKernel<false, true>)
-                            : (scene ? shadeForwardKernel<true> : shadeForwardKernel<false>);
-    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth) * sizeof(uint32_t);
+        walkFormats(P, scene) == kFmWide8
+            ? (scene ? shadeForwardKernel<true, kFmWide8> : shadeForwardKernel<false, kFmWide8>)
+        : walkFormats(P, scene) == kFmQuant
+            ? (scene ? shadeForwardKernel<true, kFmQuant> : shadeForwardKernel<false, kFmQuant>)
+            : (scene ? shadeForwardKernel<true> : shadeForwardKernel<false>);
+    const size_t smem = (size_t)bs * traceSmemWords(P.sharedDepth, slotsOf(walkFormats(P, scene))) * sizeof(uint32_t);
     LaunchShape L = persistentShape(c, kernel, bs, smem);
     L.blocks = std::min<int>(L.blocks, (int)ceilDiv(S.n, bs));
     grtError e = bindGlobalStack(c, options, L.blocks * bs, P);

@@ -30,10 +30,18 @@ namespace grt {
 
 constexpr uint32_t kSentinel = 0xFFFFFFFEu;  // stack marker: leave the current instance
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr uint32_t kPendingCap = 8;  // queued leaves per lane (phased traversal)
+// Node formats a walk may meet, as a template argument (FM): 0 = 4-wide nodes only;
+// 1 = 4-wide or quantised, read per level; 2 = 8-wide nodes (kWide8Words float4) on
+// every level; 3 = any of the three, read per level (user kernels, which cannot know).
+// W(FM) = slots per visit.
+constexpr int kFmPlain = 0, kFmQuant = 1, kFmWide8 = 2, kFmMixed = 3;
+__host__ __device__ constexpr int slotsOf(int fm) { return (fm & 2) ? 8 : 4; }
+// queued leaves per lane (phased traversal): a node visit may queue W more while at most
+// 4 are pending
+__host__ __device__ constexpr uint32_t pendingCap(int w) { return w == 8 ? 12u : 8u; }
 // Shared memory per thread of a kernel that runs refillLoop, in words: its stack slice
 // of `depth` entries and its queue of pending leaves.
-__host__ __device__ constexpr uint32_t traceSmemWords(uint32_t depth) { return depth + kPendingCap; }
+__host__ __device__ constexpr uint32_t traceSmemWords(uint32_t depth, int w = 4) { return depth + pendingCap(w); }
 constexpr float kEps = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of float32
 // 1 + 2*gamma(3) rounded up, gamma(n) = n*eps/(1 - n*eps)
 constexpr float kFarScale = 1.0000005f;
@@ -48,7 +56,7 @@ struct TraceTarget {
     uint32_t primType;  // of the geometry when tracing one directly
     uint32_t geomType;
     uint32_t empty;
-    uint32_t quant;  // the nodes are quantised 4-wide nodes (kQuantWords float4 each)
+    uint32_t fmt;  // node format: 0 4-wide (kWideWords float4), 1 quantised 4-wide (kQuantWords), 2 8-wide
 };
 
 struct TraceParams {
@@ -216,6 +224,39 @@ __device__ __forceinline__ uint32_t slab4q(const float4* nodes, uint32_t w, cons
         const float tf =
             fminf(fminf((fx - L.of.x) * L.id.x, (fy - L.of.y) * L.id.y), fminf((fz - L.of.z) * L.id.z, tmax));
         if (tn[j] <= tf * kFarScale && c[j] != kInvalid) m |= 1u << j;
+    }
+    return m;
+}
+
+// Slab test of the eight slots of 8-wide node w (kWide8Words float4): rows 4a + 2 side
+// + half hold axis a's lower (side 0) or upper (side 1) planes of slots 4 half .. 4 half
+// + 3, rows 12 and 13 the child words. The same certified test as slab4, per slot.
+__device__ __forceinline__ uint32_t slab8(const float4* nodes, uint32_t w, const Level& L, float tmin, float tmax,
+                                          float tn[8], uint32_t c[8]) {
+    const float4* N = nodes + kWide8Words * (size_t)w;
+    const uint32_t sx = L.id.x >= 0.f ? 0u : 2u, sy = L.id.y >= 0.f ? 0u : 2u, sz = L.id.z >= 0.f ? 0u : 2u;
+    uint32_t m = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float4 nx = __ldg(N + sx + h), fx = __ldg(N + (2u - sx) + h);
+        const float4 ny = __ldg(N + 4 + sy + h), fy = __ldg(N + 4 + (2u - sy) + h);
+        const float4 nz = __ldg(N + 8 + sz + h), fz = __ldg(N + 8 + (2u - sz) + h);
+        const float4 cw = __ldg(N + 12 + h);
+        const float px[4] = {nx.x, nx.y, nx.z, nx.w}, qx[4] = {fx.x, fx.y, fx.z, fx.w};
+        const float py[4] = {ny.x, ny.y, ny.z, ny.w}, qy[4] = {fy.x, fy.y, fy.z, fy.w};
+        const float pz[4] = {nz.x, nz.y, nz.z, nz.w}, qz[4] = {fz.x, fz.y, fz.z, fz.w};
+        const uint32_t cc[4] = {__float_as_uint(cw.x), __float_as_uint(cw.y), __float_as_uint(cw.z),
+                                __float_as_uint(cw.w)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = 4 * h + j;
+            c[k] = cc[j];
+            tn[k] = fmaxf(fmaxf((px[j] - L.on.x) * L.id.x, (py[j] - L.on.y) * L.id.y),
+                          fmaxf((pz[j] - L.on.z) * L.id.z, tmin));
+            const float tf = fminf(fminf((qx[j] - L.of.x) * L.id.x, (qy[j] - L.of.y) * L.id.y),
+                                   fminf((qz[j] - L.of.z) * L.id.z, tmax));
+            if (tn[k] <= tf * kFarScale && cc[j] != kInvalid) m |= 1u << k;
+        }
     }
     return m;
 }
@@ -550,15 +591,28 @@ struct RayState {
     uint32_t steps, next;
     float lo, hi;  // [tmin, limit] on the current level (limit = tmax, or the best t so far)
     bool inBlas, found;
-    bool quant;    // the current level's nodes are quantised
+    uint32_t fmt;  // the current level's node format (TraceTarget::fmt)
 };
 
-// The slab test of the current node in the current level's node format. QN = false
-// compiles the quantised form out: the walk's levels are known to use 4-wide nodes.
-template <bool QN>
-__device__ __forceinline__ uint32_t slabNode(const RayState& s, float tn[4], uint32_t c[4]) {
-    return (QN && s.quant) ? slab4q(s.nodes, s.next, s.L, s.lo, s.hi, tn, c)
+// The slab test of the current node in the current level's node format, over the W =
+// slotsOf(FM) entries of tn and c; a 4-wide level in a W = 8 walk fills the first four
+// and marks the rest empty.
+template <int FM>
+__device__ __forceinline__ uint32_t slabNode(const RayState& s, float* tn, uint32_t* c) {
+    if constexpr (FM == kFmPlain) {
+        return slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+    } else if constexpr (FM == kFmWide8) {
+        return slab8(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+    } else if constexpr (FM == kFmQuant) {
+        return s.fmt == 1u ? slab4q(s.nodes, s.next, s.L, s.lo, s.hi, tn, c)
                            : slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+    } else {
+        if (s.fmt == 2u) return slab8(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+#pragma unroll
+        for (int j = 4; j < 8; ++j) c[j] = kInvalid, tn[j] = INFINITY;
+        return s.fmt == 1u ? slab4q(s.nodes, s.next, s.L, s.lo, s.hi, tn, c)
+                           : slab4(s.nodes, s.next, s.L, s.lo, s.hi, tn, c);
+    }
 }
 
 template <bool SCENE>
@@ -572,7 +626,7 @@ __device__ __forceinline__ void beginRay(const TraceParams& P, Stack& st, RaySta
     exactLevel(s.L, wo, wd);
     s.wid = s.L.id;
     s.nodes = P.target.nodes;
-    s.quant = P.target.quant != 0;
+    s.fmt = P.target.fmt;
     s.leaves = P.target.leaves;
     s.primType = P.target.primType;
     s.geomType = P.target.geomType;
@@ -604,7 +658,7 @@ __device__ __forceinline__ bool enterInstance(const TraceParams& P, Stack& st, R
     s.lo = localLo(s.L, s.tmin);
     s.hi = localHi(s.L, lim);
     s.nodes = R->nodes;
-    s.quant = (bits & kInstQuant) != 0;
+    s.fmt = (bits & kInstQuant) ? 1u : (bits & kInstWide8) ? 2u : 0u;
     s.leaves = R->leaves;
     s.primType = instPrimType(bits);
     s.geomType = instGeomType(bits);
@@ -745,9 +799,61 @@ __device__ __forceinline__ void orderChildren(const TraceParams& P, Stack& st, R
     s.next = pick4(c, k[0] & 3u);
 }
 
+template <class T>
+__device__ __forceinline__ T pick8(const T v[8], uint32_t j) {
+    T r = v[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) r = j == (uint32_t)i ? v[i] : r;
+    return r;
+}
+
+// orderChildren for an 8-wide visit: one or two slots as there; three or more through
+// Batcher's odd-even merge network for eight keys (19 comparators) on (entry distance,
+// slot) keys, the slot in the three low bits.
+__device__ __forceinline__ void orderChildren8(const TraceParams& P, Stack& st, RayState& s, uint32_t m,
+                                               const float tn[8], const uint32_t c[8]) {
+    if (m == 0) return;
+    if ((m & (m - 1u)) == 0) {
+        s.next = pick8(c, (uint32_t)__ffs(m) - 1u);
+        return;
+    }
+    if (__popc(m) == 2) {
+        const uint32_t a = (uint32_t)__ffs(m) - 1u, b = 31u - (uint32_t)__clz(m);
+        const uint32_t ca = pick8(c, a), cb = pick8(c, b);
+        const bool swap = pick8(tn, b) < pick8(tn, a);
+        if (!st.push(swap ? ca : cb)) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+        s.next = swap ? cb : ca;
+        return;
+    }
+    uint32_t k[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) k[j] = ((m >> j) & 1u) ? ((floatToOrdered(tn[j]) & ~7u) | (uint32_t)j) : kInvalid;
+    sort2(k[0], k[1]), sort2(k[2], k[3]), sort2(k[4], k[5]), sort2(k[6], k[7]);
+    sort2(k[0], k[2]), sort2(k[1], k[3]), sort2(k[4], k[6]), sort2(k[5], k[7]);
+    sort2(k[1], k[2]), sort2(k[5], k[6]);
+    sort2(k[0], k[4]), sort2(k[1], k[5]), sort2(k[2], k[6]), sort2(k[3], k[7]);
+    sort2(k[2], k[4]), sort2(k[3], k[5]);
+    sort2(k[1], k[2]), sort2(k[3], k[4]), sort2(k[5], k[6]);
+    bool ok = true;
+#pragma unroll
+    for (int j = 7; j >= 1; --j)
+        if (k[j] != kInvalid) ok &= st.push(pick8(c, k[j] & 7u));
+    if (!ok) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+    s.next = pick8(c, k[0] & 7u);
+}
+
+template <int W>
+__device__ __forceinline__ void orderSlots(const TraceParams& P, Stack& st, RayState& s, uint32_t m, const float* tn,
+                                           const uint32_t* c) {
+    if constexpr (W == 8)
+        orderChildren8(P, st, s, m, tn, c);
+    else
+        orderChildren(P, st, s, m, tn, c);
+}
+
 // One traversal step: a node visit (with its leaf tests), an instance entry or an
 // instance exit. Returns true once the ray is finished (s.best is then final).
-template <bool ANY, bool SCENE, bool COUNT, class U = NoUser, bool QN = true>
+template <bool ANY, bool SCENE, bool COUNT, class U = NoUser, int FM = kFmMixed>
 __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayState& s, Visits* vis,
                                         const U* user = nullptr, void* payload = nullptr) {
     if (s.next == kNone) {
@@ -758,7 +864,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
             s.lo = s.tmin;
             s.hi = (ANY || !s.found) ? s.tmax : s.best.t;
             s.nodes = P.target.nodes;
-            s.quant = P.target.quant != 0;
+            s.fmt = P.target.fmt;
             s.inBlas = false;
             s.next = kNone;
             return false;
@@ -775,29 +881,39 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
         return true;
     }
     if (COUNT) ++vis->nodes;
-    float tn[4];
-    uint32_t c[4];
-    uint32_t m = slabNode<QN>(s, tn, c);
+    constexpr int W = slotsOf(FM);
+    float tn[W];
+    uint32_t c[W];
+    uint32_t m = slabNode<FM>(s, tn, c);
     s.next = kNone;
-    if (s.inBlas) {
+    if (s.inBlas) {  // one copy of the leaf test (a large inlined body), over the hit leaf slots
+        uint32_t lm = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!((m >> j) & 1u) || !(c[j] & kLeafBit)) continue;
-            m &= ~(1u << j);
-            if (testLeaf<ANY, SCENE, COUNT, U>(P, s, c[j] & ~kLeafBit, vis, user, payload) && ANY) return true;
+        for (int j = 0; j < W; ++j) lm |= (c[j] & kLeafBit) ? (1u << j) : 0u;
+        lm &= m;
+        m &= ~lm;
+        while (lm) {
+            const uint32_t j = (uint32_t)__ffs(lm) - 1u;
+            lm &= lm - 1u;
+            uint32_t cj;
+            if constexpr (W == 8)
+                cj = pick8(c, j);
+            else
+                cj = pick4(c, j);
+            if (testLeaf<ANY, SCENE, COUNT, U>(P, s, cj & ~kLeafBit, vis, user, payload) && ANY) return true;
         }
     }
-    orderChildren(P, st, s, m, tn, c);
+    orderSlots<W>(P, st, s, m, tn, c);
     return false;
 }
 
 // One step of an all-hits walk (Sec. 7.5: every intersection, found by asking the
 // any-hit traversal for its next hit until it is done): a node visit that tests every
 // leaf it reaches against the whole range [tmin, tmax] and appends each hit to `found`
-// (at most four per visit), or an instance entry or exit. Returns the number of hits
+// (at most W = slotsOf(FM) per visit), or an instance entry or exit. Returns the number of hits
 // appended, or -1 once the walk is over. Each primitive of each instance sits in one
 // leaf, so each (instance, primitive) is reported at most once.
-template <bool SCENE, class U = NoUser, bool QN = true>
+template <bool SCENE, class U = NoUser, int FM = kFmMixed>
 __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState& s, Hit* found,
                                        const U* user = nullptr, void* payload = nullptr) {
     if (s.next == kNone) {
@@ -808,7 +924,7 @@ __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState
             s.lo = s.tmin;
             s.hi = s.tmax;
             s.nodes = P.target.nodes;
-            s.quant = P.target.quant != 0;
+            s.fmt = P.target.fmt;
             s.inBlas = false;
             s.next = kNone;
             return 0;
@@ -825,21 +941,30 @@ __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState
         latchError(P.error, GRT_ERROR_STEP_LIMIT);
         return -1;
     }
-    float tn[4];
-    uint32_t c[4];
-    uint32_t m = slabNode<QN>(s, tn, c);
+    constexpr int W = slotsOf(FM);
+    float tn[W];
+    uint32_t c[W];
+    uint32_t m = slabNode<FM>(s, tn, c);
     s.next = kNone;
     int added = 0;
     if (s.inBlas) {
+        uint32_t lm = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!((m >> j) & 1u) || !(c[j] & kLeafBit)) continue;
-            m &= ~(1u << j);
-            if (testLeaf<true, SCENE, false, U>(P, s, c[j] & ~kLeafBit, nullptr, user, payload))
-                found[added++] = s.best;
+        for (int j = 0; j < W; ++j) lm |= (c[j] & kLeafBit) ? (1u << j) : 0u;
+        lm &= m;
+        m &= ~lm;
+        while (lm) {  // one copy of the leaf test, over the hit leaf slots
+            const uint32_t j = (uint32_t)__ffs(lm) - 1u;
+            lm &= lm - 1u;
+            uint32_t cj;
+            if constexpr (W == 8)
+                cj = pick8(c, j);
+            else
+                cj = pick4(c, j);
+            if (testLeaf<true, SCENE, false, U>(P, s, cj & ~kLeafBit, nullptr, user, payload)) found[added++] = s.best;
         }
     }
-    orderChildren(P, st, s, m, tn, c);
+    orderSlots<W>(P, st, s, m, tn, c);
     return added;
 }
 
@@ -927,7 +1052,7 @@ __device__ __forceinline__ float3 aoDirection(const AoFrame& F, uint64_t seed, u
 // Refill loop with one traversal step per lane per iteration (node visits test their
 // leaves at once). Used for any-hit queries on a single geometry (shadow rays), which
 // stop at their first hit and so gain nothing from queueing leaves.
-template <bool ANY, bool SCENE, bool COUNT, bool QN = true, class Src>
+template <bool ANY, bool SCENE, bool COUNT, int FM = kFmMixed, class Src>
 __device__ __forceinline__ void refillLoopPerRay(const TraceParams& P, Stack& st, Src& src) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t ltMask = (1u << lane) - 1u;
@@ -954,7 +1079,7 @@ __device__ __forceinline__ void refillLoopPerRay(const TraceParams& P, Stack& st
             live = __ballot_sync(0xffffffffu, item != kNone);
         }
         if (live == 0) break;
-        if (item != kNone && stepRay<ANY, SCENE, COUNT, NoUser, QN>(P, st, s, &v)) {
+        if (item != kNone && stepRay<ANY, SCENE, COUNT, NoUser, FM>(P, st, s, &v)) {
             src.finish(item, s);
             if (COUNT) flushVisits(P.stats, v);
             item = kNone;
@@ -970,8 +1095,8 @@ __device__ __forceinline__ void refillLoopPerRay(const TraceParams& P, Stack& st
 enum : uint32_t { kStNode = 0, kStEnter = 1, kStFlush = 2, kStDone = 3 };
 
 // Leaves of the current bottom level whose boxes the ray hit, waiting to be tested:
-// at most kPendingCap, in shared memory after the lane's stack slice (entry i at
-// buf[i * blockDim.x]). Kernels running refillLoop reserve traceSmemWords(depth)
+// at most pendingCap(W), in shared memory after the lane's stack slice (entry i at
+// buf[i * blockDim.x]). Kernels running refillLoop reserve traceSmemWords(depth, W)
 // words of shared memory per thread.
 struct Pending {
     uint32_t* buf;
@@ -984,8 +1109,8 @@ struct Pending {
 };
 
 // Node visit that queues hit leaf children instead of testing them (inner children
-// and top-level leaves go on as in stepRay). Requires q.n <= kPendingCap - 4.
-template <bool ANY, bool SCENE, bool COUNT, bool QN = true>
+// and top-level leaves go on as in stepRay). Requires q.n <= pendingCap(W) - W.
+template <bool ANY, bool SCENE, bool COUNT, int FM = kFmMixed>
 __device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RayState& s, Pending& q, Visits* vis) {
     if (++s.steps > P.maxSteps) {
         latchError(P.error, GRT_ERROR_STEP_LIMIT);
@@ -995,27 +1120,28 @@ __device__ __forceinline__ void visitNode(const TraceParams& P, Stack& st, RaySt
         return;
     }
     if (COUNT) ++vis->nodes;
-    float tn[4];
-    uint32_t c[4];
-    uint32_t m = slabNode<QN>(s, tn, c);
+    constexpr int W = slotsOf(FM);
+    float tn[W];
+    uint32_t c[W];
+    uint32_t m = slabNode<FM>(s, tn, c);
     s.next = kNone;
     if (s.inBlas) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < W; ++j)
             if (((m >> j) & 1u) && (c[j] & kLeafBit)) q.add(c[j] & ~kLeafBit), m &= ~(1u << j);
     }
-    orderChildren(P, st, s, m, tn, c);
+    orderSlots<W>(P, st, s, m, tn, c);
 }
 
 // The lane's next action after its last one: pops the stack (leaving an instance
 // when its marker comes up) until there is a node to visit or an instance to enter,
 // but not past a marker or the end while leaves of the level are still pending.
-template <bool ANY, bool SCENE>
+template <bool ANY, bool SCENE, int W = 4>
 __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, RayState& s, const Pending& q) {
     for (;;) {
         if (s.next != kNone) {
             if (SCENE && !s.inBlas && (s.next & kLeafBit)) return kStEnter;
-            return q.n > kPendingCap - 4 ? kStFlush : kStNode;
+            return q.n > pendingCap(W) - (uint32_t)W ? kStFlush : kStNode;
         }
         if (st.sp == 0) return q.n ? kStFlush : kStDone;
         if (SCENE && st.top() == kSentinel) {
@@ -1025,7 +1151,7 @@ __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, R
             s.lo = s.tmin;
             s.hi = (ANY || !s.found) ? s.tmax : s.best.t;
             s.nodes = P.target.nodes;
-            s.quant = P.target.quant != 0;
+            s.fmt = P.target.fmt;
             s.inBlas = false;
             continue;
         }
@@ -1050,12 +1176,13 @@ __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, R
 //   count()             number of items (may be read from device memory)
 //   begin(i, P, st, s)  set up item i's ray in s; false if the item has no ray
 //   finish(i, s)        consume item i's result s.best
-template <bool ANY, bool SCENE, bool COUNT, bool QN = true, class Src>
+template <bool ANY, bool SCENE, bool COUNT, int FM = kFmMixed, class Src>
 __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src& src) {
     if constexpr (ANY && !SCENE) {
-        refillLoopPerRay<ANY, SCENE, COUNT, QN>(P, st, src);
+        refillLoopPerRay<ANY, SCENE, COUNT, FM>(P, st, src);
         return;
     }
+    constexpr int W = slotsOf(FM);
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t ltMask = (1u << lane) - 1u;
     const unsigned long long total = src.count();
@@ -1078,7 +1205,7 @@ __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src&
                     item = (uint32_t)mine;
                     if (COUNT) v = Visits{};
                     q.n = 0;
-                    state = nextState<ANY, SCENE>(P, st, s, q);
+                    state = nextState<ANY, SCENE, W>(P, st, s, q);
                     if (state == kStDone) {  // nothing to traverse (an empty target)
                         src.finish(item, s);
                         if (COUNT) flushVisits(P.stats, v);
@@ -1127,9 +1254,9 @@ __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src&
             }
         } else if (state == kStNode) {
             acted = true;
-            visitNode<ANY, SCENE, COUNT, QN>(P, st, s, q, &v);
+            visitNode<ANY, SCENE, COUNT, FM>(P, st, s, q, &v);
         }
-        if (acted) state = (ANY && s.found) ? kStDone : nextState<ANY, SCENE>(P, st, s, q);
+        if (acted) state = (ANY && s.found) ? kStDone : nextState<ANY, SCENE, W>(P, st, s, q);
         } while (tail && state != kStDone);
         if (state == kStDone) {
             src.finish(item, s);
@@ -1198,7 +1325,7 @@ struct AllHitsWalk {
     RayState s;
     uint32_t entries[DEPTH];
     Stack st;
-    Hit buf[4];
+    Hit buf[slotsOf(kFmMixed)];  // the hits of one visit
     int n, i;
     bool scene, finished;
     float3 o, d;

@@ -49,7 +49,9 @@ class Context:
 
 class Geometry:
     """A bottom-level BVH over an indexed triangle mesh or an AABB list. build_flags:
-    GRT_BUILD_PREFER_FAST (linear BVH), _BALANCED or _HIGH_QUALITY (PLOC clustering)."""
+    GRT_BUILD_PREFER_FAST (linear BVH), _BALANCED or _HIGH_QUALITY (PLOC clustering) or
+    GRT_BUILD_CLUSTER_SUBTREES, optionally ORed with GRT_BUILD_QUANTIZED_NODES or
+    GRT_BUILD_WIDE8_NODES (the node format traversal reads)."""
 
     def __init__(self, ctx: Context, *, vertices=None, indices=None, boxes=None, geom_type: int = 0,
                  morton_bits: int = 0, temp: torch.Tensor | None = None, vertex_count: int | None = None,
@@ -93,14 +95,16 @@ def instance_records(geometry_handles, masks=None) -> np.ndarray:
 
 class Scene:
     """A top-level BVH over instances of geometries with SRT frames (float32 (I,10):
-    quaternion xyzw, scale xyz, translation xyz)."""
+    quaternion xyzw, scale xyz, translation xyz). build_flags: GRT_BUILD_WIDE8_NODES gives
+    the top level 8-wide nodes (other bits are ignored for scenes)."""
 
-    def __init__(self, ctx: Context, geometry_handles, frames: torch.Tensor, morton_bits: int = 0, masks=None):
+    def __init__(self, ctx: Context, geometry_handles, frames: torch.Tensor, morton_bits: int = 0, masks=None,
+                 build_flags: int = 0):
         self.ctx = ctx
         self.instances = device_tensor(instance_records(geometry_handles, masks))
         self.frames = frames
         self.input = scene_input(self.instances, self.frames, count=len(geometry_handles))
-        self.options = build_options(morton_bits)
+        self.options = build_options(morton_bits, build_flags)
         self.temp_bytes = grtGetSceneBuildTemporaryBufferSize(ctx.handle, self.input, self.options)
         self.temp = empty_bytes(self.temp_bytes)
         self.handle = grtCreateScene(ctx.handle, self.input, self.options)
