@@ -137,8 +137,11 @@ struct AoSource {
 
 // 96 registers: 5 blocks of 128 threads per SM instead of 4, 7% faster on the terrain
 // AO workload despite a few spills (the closest-hit kernel is faster uncapped).
+#ifndef GRT_AO_MAXNREG
+#define GRT_AO_MAXNREG 96
+#endif
 template <bool COUNT, int FM = kFmPlain>
-__global__ void __maxnreg__(96) aoTraceKernel(TraceParams P, const uint32_t* list, const uint32_t* listCount,
+__global__ void __maxnreg__(GRT_AO_MAXNREG) aoTraceKernel(TraceParams P, const uint32_t* list, const uint32_t* listCount,
                                               uint32_t* counts, const float4* frames) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;

@@ -1176,9 +1176,12 @@ __device__ __forceinline__ uint32_t nextState(const TraceParams& P, Stack& st, R
 //   count()             number of items (may be read from device memory)
 //   begin(i, P, st, s)  set up item i's ray in s; false if the item has no ray
 //   finish(i, s)        consume item i's result s.best
+// Any-hit queries (shadow and ambient-occlusion rays) take the per-ray form instead: with
+// one copy of the leaf test per step it measured faster for them (terrain AO 0.758 ->
+// 0.728 ms); closest hits keep the phased form (1M spheres 5.20 against 5.62 ms).
 template <bool ANY, bool SCENE, bool COUNT, int FM = kFmMixed, class Src>
 __device__ __forceinline__ void refillLoop(const TraceParams& P, Stack& st, Src& src) {
-    if constexpr (ANY && !SCENE) {
+    if constexpr (ANY) {
         refillLoopPerRay<ANY, SCENE, COUNT, FM>(P, st, src);
         return;
     }
