@@ -237,7 +237,9 @@ typedef struct grtSceneBuildInput {
 grtError grtGetSceneBuildTemporaryBufferSize(grtContext ctx, const grtSceneBuildInput* input,
                                              const grtBuildOptions* options, size_t* sizeBytes);
 /* Allocates the library-owned top level for `input`'s instance count: nodes, instance
- * records and the FP64 frames. The build flag is ignored (top levels are linear BVHs). */
+ * records and the FP64 frames. Top levels are linear BVHs whatever the method bits;
+ * GRT_BUILD_WIDE8_NODES gives them 8-wide nodes (and then needs 8-wide instances), and
+ * grtBuildScene must be given the same bit. */
 grtError grtCreateScene(grtContext ctx, const grtSceneBuildInput* input, const grtBuildOptions* options,
                         grtScene* out);
 /* Builds the top level over the instances' world boxes. The instances' geometries
@@ -338,7 +340,7 @@ grtError grtTraceClosest(grtContext ctx, grtScene scene, grtGeometry geom, const
 /* Every hit of each ray (Sec. 7.5: all intersections, as repeated getNextHit() calls on
  * the any-hit traversal object return them): each (instance, primitive) whose exact
  * intersection lies in [minT, maxT], once. Ray r's first maxHitsPerRay hits, in
- * traversal order (not sorted by t) with t, u, v recomputed in FP64, go to
+ * traversal order (not sorted by t) with t, u, v recomputed to ~48 bits, go to
  * hits[r * maxHitsPerRay ...]; its remaining slots are set to misses; hitCounts[r]
  * (device, rayCount uint32) gets the number of hits found, which may exceed
  * maxHitsPerRay. Instance masks, the ray mask and intersection filters apply as for
@@ -522,7 +524,7 @@ grtError grtShadeLambert(grtContext ctx, grtGeometry geom, const grtRay* rays, c
  * caller's buffers. Positions are differentiated through the face normal and through
  * the hit's barycentrics on the fixed primary ray (interior hits: visibility and the
  * hit triangle are piecewise constant and contribute nothing). hits and visibility as
- * stored by the forward pass; hits = NULL recomputes the primary hits (refined in FP64)
+ * stored by the forward pass; hits = NULL recomputes the primary hits (refined as grtTraceClosest does)
  * and the visibility by tracing again within the call (the closest-hit query and the
  * forward's visibility pass into context memory held only during the call), trading
  * about one forward pass for the 21 bytes per pixel kept between the passes. */

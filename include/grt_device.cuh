@@ -11,7 +11,7 @@
  *   grt_device::AllHits<DEPTH>(target, origin, direction, minT, maxT).getNextHit()
  *
  * which run the library's own traversal (the same certified float32 tests with their
- * FP64 fallback; closest hits get t, u, v recomputed in FP64) on a per-thread stack of
+ * FP64 fallback; closest hits get t, u, v recomputed in double-float) on a per-thread stack of
  * DEPTH entries in local memory. A ray needing more entries stops early and latches
  * GRT_ERROR_STACK_OVERFLOW in the context's error word. The records follow grtHit:
  * a miss has primID = instanceID = 0xFFFFFFFF and t = +inf.
@@ -121,7 +121,7 @@ __device__ __forceinline__ grtHit traceAnyHit(const grtDeviceTarget& T, float3 o
 //   grt_device::AllHits<> w(target, o, d, tmin, tmax);
 //   for (grtHit h = w.getNextHit(); h.primID != 0xFFFFFFFF; h = w.getNextHit()) ...
 // Each (instance, primitive) whose intersection lies in [tmin, tmax] comes once, in
-// traversal order (not sorted by t), with t, u, v recomputed in FP64; then a miss
+// traversal order (not sorted by t), with t, u, v recomputed in double-float; then a miss
 // record. done() tells whether the walk is over (the paper's getCurrentState()). The
 // object holds its own stack of DEPTH entries: construct it where it is used; do not
 // copy it. With user functions: AllHits<DEPTH, Fn> w(target, o, d, tmin, tmax, mask, fn,

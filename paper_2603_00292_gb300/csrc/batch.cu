@@ -16,7 +16,7 @@
 //   3 + 3p       radix pass p, stable scatter per chunk
 //   1 + 3P       Karras emission over internal-node chunks
 //   2 + 3P       bottom-up fit over leaf chunks
-//   3 + 3P       closest-hit trace over ray chunks (refill loop), then FP64 refinement
+//   3 + 3P       closest-hit trace over ray chunks (refill loop), then the hits' refinement
 // A smaller scene is built entirely by one block (phase 0) and traced in phase 1.
 // A scene whose geometry was created with GRT_BUILD_CLUSTER_SUBTREES (any size) has its
 // emission write the LBVH topology to scratch, then one more phase, the bottom-up

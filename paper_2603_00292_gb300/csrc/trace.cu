@@ -22,7 +22,7 @@ __global__ void traceKernel(TraceParams P) {
     refillLoop<ANY, SCENE, COUNT, FM>(P, st, src);
 }
 
-// The closest hits' t, u, v recomputed in FP64, one thread per ray after traversal so
+// The closest hits' t, u, v recomputed in double-float, one thread per ray after traversal so
 // that every lane of a warp takes part (FP64 is far slower than FP32 on this GPU).
 // One thread per ray: the hit records are read with every load in flight at once, and
 // the FP64 work of the hits (a few percent of the rays on a camera view) stays dense in
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) refineKernel(TraceParams P) {
 }
 
 // Every hit of each ray (Sec. 7.5): one thread per ray walks it on a local stack of
-// kAllHitsDepth entries and stores its first maxHits hits (traversal order, FP64-refined)
+// kAllHitsDepth entries and stores its first maxHits hits (traversal order, refined in double-float)
 // in hits[r * maxHits ...], the rest of the ray's slots as misses, and the number of
 // hits found in counts[r].
 constexpr int kAllHitsDepth = 96;

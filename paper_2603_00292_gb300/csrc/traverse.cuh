@@ -18,7 +18,7 @@
 //    object-space ray's transform error;
 //  * a triangle or sphere test whose float32 edge functions (or discriminant) lie
 //    within their rounding bound of zero is decided again in FP64;
-//  * the closest hit's t, u, v are recomputed once in FP64.
+//  * the closest hit's t, u, v are recomputed once in double-float arithmetic (refineFF).
 // FP64 runs far slower than FP32 on this GPU, so it is confined to these rare cases.
 #pragma once
 
@@ -317,20 +317,6 @@ __device__ __forceinline__ bool triangleTest64(D3 o, D3 d, float3 v0f, float3 v1
 }
 
 // FP64 barycentrics and distance of a known hit (no acceptance test).
-__device__ __forceinline__ bool triangleRefine64(D3 o, D3 d, float3 v0f, float3 v1f, float3 v2f, double& t, double& u,
-                                              double& v) {
-    const D3 v0 = d3(v0f), e1 = d3(v1f) - v0, e2 = d3(v2f) - v0;
-    const D3 P = crossd(d, e2);
-    const double det = dotd(e1, P);
-    if (det == 0.0) return false;
-    const double inv = 1.0 / det;
-    const D3 T = o - v0;
-    const D3 Q = crossd(T, e1);
-    u = dotd(T, P) * inv;
-    v = dotd(d, Q) * inv;
-    t = dotd(e2, Q) * inv;
-    return true;
-}
 
 // Float32 sphere test. Returns 0 = miss, 1 = hit (world t set), 2 = undecided.
 __device__ __forceinline__ int sphereTest(const Level& L, const float4& s, float tmin, float tmax, bool strict, float& t) {
@@ -433,24 +419,6 @@ static __device__ __noinline__ float4 decide64(const InstanceFrames64* inv64, bo
     return make_float4((float)t64, (float)u64, (float)v64, 1.f);
 }
 
-// The closest hit's distance and barycentrics recomputed in FP64: (t, u, v, 1), or
-// w = 0 when FP64 cannot evaluate them (the float32 values then stand).
-static __device__ __noinline__ float4 refine64(const InstanceFrames64* inv64, bool inInstance, uint32_t inst, float3 wo,
-                                        float3 wd, const float4* rec, bool sphere, float tmin, float tmax) {
-    D3 o, d;
-    ray64(inv64, inInstance, inst, wo, wd, o, d);
-    if (sphere) {
-        double t64;
-        if (sphereTest64(o, d, __ldg(rec), (double)tmin, (double)tmax, false, t64))
-            return make_float4((float)t64, 0.f, 0.f, 1.f);
-        return make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    double t64, u64, v64;
-    if (triangleRefine64(o, d, f3(__ldg(rec)), f3(__ldg(rec + 1)), f3(__ldg(rec + 2)), t64, u64, v64))
-        return make_float4((float)t64, (float)u64, (float)v64, 1.f);
-    return make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
 // Error-free transformations (Dekker; Knuth): a*b = p + e and a + b = s + e exactly.
 __device__ __forceinline__ float2 twoProd(float a, float b) {
     const float p = __fmul_rn(a, b);
@@ -493,6 +461,113 @@ __device__ __forceinline__ float3 instanceOriginFF(const float4* hi, const float
         o[k] = __fadd_rn(ah, al);
     }
     return make_float3(o[0], o[1], o[2]);
+}
+
+// ---------------------------------------------------------------- double-float refinement
+// Closest hits get t, u, v recomputed in double-float arithmetic (hi + lo floats, about
+// 48 significant bits) on the float32 pipes, FP64 running at a small fraction of their
+// rate on this GPU. Addition and multiplication are the accurate double-word algorithms
+// of Joldes, Muller and Popescu ("Tight and Rigorous Error Bounds for Basic Building
+// Blocks of Double-Word Arithmetic", ACM TOMS 2017: relative errors of a few u^2), built
+// on Dekker's and Knuth's error-free transformations; division and square root take one
+// Newton correction of the float32 quotient or root.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ffOf(float a) { return FF{a, 0.f}; }
+__device__ __forceinline__ FF ffFast(float a, float b) {  // |a| >= |b| (or a = 0)
+    const float s = __fadd_rn(a, b);
+    return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ffAdd(FF a, FF b) {
+    const float2 s = twoSum(a.hi, b.hi), t = twoSum(a.lo, b.lo);
+    const FF v = ffFast(s.x, __fadd_rn(s.y, t.x));
+    return ffFast(v.hi, __fadd_rn(t.y, v.lo));
+}
+__device__ __forceinline__ FF ffSub(FF a, FF b) { return ffAdd(a, FF{-b.hi, -b.lo}); }
+__device__ __forceinline__ FF ffMul(FF a, FF b) {
+    const float2 c = twoProd(a.hi, b.hi);
+    const float tl = fmaf(a.lo, b.hi, __fmul_rn(a.hi, b.lo));
+    return ffFast(c.x, __fadd_rn(c.y, tl));
+}
+__device__ __forceinline__ FF ffDiv(FF a, FF b) {
+    const float q = __fdiv_rn(a.hi, b.hi);
+    const FF r = ffSub(a, ffMul(b, ffOf(q)));  // the remainder of the float32 quotient
+    return ffFast(q, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ FF ffSqrt(FF a) {
+    if (!(a.hi > 0.f)) return FF{0.f, 0.f};
+    const float r = sqrtf(a.hi);
+    const FF e = ffSub(a, ffMul(ffOf(r), ffOf(r)));
+    return ffFast(r, __fdiv_rn(e.hi, __fmul_rn(2.f, r)));
+}
+__device__ __forceinline__ float ffRound(FF a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ FF ffDot(const FF a[3], const FF b[3]) {
+    return ffAdd(ffAdd(ffMul(a[0], b[0]), ffMul(a[1], b[1])), ffMul(a[2], b[2]));
+}
+__device__ __forceinline__ void ffCross(const FF a[3], const FF b[3], FF c[3]) {
+    c[0] = ffSub(ffMul(a[1], b[2]), ffMul(a[2], b[1]));
+    c[1] = ffSub(ffMul(a[2], b[0]), ffMul(a[0], b[2]));
+    c[2] = ffSub(ffMul(a[0], b[1]), ffMul(a[1], b[0]));
+}
+
+// The ray at the hit's level in double-float: the world ray itself, or its image under
+// the instance's inverse frame held as float32 rows (hi) plus low parts (lo), hi + lo
+// being the FP64 frame to 2^-48.
+__device__ __forceinline__ void rayFF(const float4* hi, const float4* lo, float3 wo, float3 wd, FF o[3], FF d[3]) {
+    if (!hi) {
+        o[0] = ffOf(wo.x), o[1] = ffOf(wo.y), o[2] = ffOf(wo.z);
+        d[0] = ffOf(wd.x), d[1] = ffOf(wd.y), d[2] = ffOf(wd.z);
+        return;
+    }
+    const float w[3] = {wo.x, wo.y, wo.z}, v[3] = {wd.x, wd.y, wd.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 H = __ldg(hi + k), L = __ldg(lo + k);
+        const FF g[3] = {FF{H.x, L.x}, FF{H.y, L.y}, FF{H.z, L.z}};
+        FF ok = FF{H.w, L.w}, dk = FF{0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            ok = ffAdd(ok, ffMul(g[j], ffOf(w[j])));
+            dk = ffAdd(dk, ffMul(g[j], ffOf(v[j])));
+        }
+        o[k] = ok, d[k] = dk;
+    }
+}
+
+// The closest hit's (t, u, v, 1) recomputed in double-float (Moller-Trumbore on the
+// level's ray, or the sphere quadratic's root in [tmin, tmax]); w = 0 when it cannot
+// be evaluated (the float32 values then stand).
+static __device__ __noinline__ float4 refineFF(const float4* hi, const float4* lo, float3 wo, float3 wd,
+                                              const float4* rec, bool sphere, float tmin, float tmax) {
+    FF o[3], d[3];
+    rayFF(hi, lo, wo, wd, o, d);
+    if (sphere) {
+        const float4 sp = __ldg(rec);
+        const FF f[3] = {ffAdd(o[0], ffOf(-sp.x)), ffAdd(o[1], ffOf(-sp.y)), ffAdd(o[2], ffOf(-sp.z))};
+        const FF a = ffDot(d, d), b = ffDot(f, d);
+        const FF c = ffSub(ffDot(f, f), ffMul(ffOf(sp.w), ffOf(sp.w)));
+        const FF disc = ffSub(ffMul(b, b), ffMul(a, c));
+        if (disc.hi < 0.f || a.hi == 0.f) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const FF q = ffSqrt(disc), nb = FF{-b.hi, -b.lo};
+        const float t0 = ffRound(ffDiv(ffSub(nb, q), a)), t1 = ffRound(ffDiv(ffAdd(nb, q), a));
+        if (t0 >= tmin && t0 <= tmax) return make_float4(t0, 0.f, 0.f, 1.f);
+        if (t1 >= tmin && t1 <= tmax) return make_float4(t1, 0.f, 0.f, 1.f);
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 A = __ldg(rec), B = __ldg(rec + 1), C = __ldg(rec + 2);
+    const float2 x1 = twoSum(B.x, -A.x), y1 = twoSum(B.y, -A.y), z1 = twoSum(B.z, -A.z);
+    const float2 x2 = twoSum(C.x, -A.x), y2 = twoSum(C.y, -A.y), z2 = twoSum(C.z, -A.z);
+    const FF e1[3] = {FF{x1.x, x1.y}, FF{y1.x, y1.y}, FF{z1.x, z1.y}};
+    const FF e2[3] = {FF{x2.x, x2.y}, FF{y2.x, y2.y}, FF{z2.x, z2.y}};
+    FF P[3], Q[3];
+    ffCross(d, e2, P);
+    const FF det = ffDot(e1, P);
+    if (det.hi == 0.f) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const FF T[3] = {ffAdd(o[0], ffOf(-A.x)), ffAdd(o[1], ffOf(-A.y)), ffAdd(o[2], ffOf(-A.z))};
+    ffCross(T, e1, Q);
+    return make_float4(ffRound(ffDiv(ffDot(e2, Q), det)), ffRound(ffDiv(ffDot(T, P), det)),
+                       ffRound(ffDiv(ffDot(d, Q), det)), 1.f);
 }
 
 // Enter an instance. The object-space origin is placed where the world ray enters the
@@ -857,7 +932,7 @@ template <bool ANY, bool SCENE, bool COUNT, class U = NoUser, int FM = kFmMixed>
 __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayState& s, Visits* vis,
                                         const U* user = nullptr, void* payload = nullptr) {
     if (s.next == kNone) {
-        if (st.sp == 0) return true;  // closest hits are refined in FP64 afterwards (refineKernel)
+        if (st.sp == 0) return true;  // closest hits are refined afterwards (refineKernel)
         s.next = st.pop();
         if (SCENE && s.next == kSentinel) {  // back to the top level
             exactLevel(s.L, s.wo, s.wd);
@@ -1283,7 +1358,7 @@ struct RayBufferSource {
     __device__ void finish(uint32_t i, const RayState& s) const { storeHit(P->hits, i, s.best); }
 };
 
-// Hit h of the ray (wo, wd, [tmin, tmax]): its t, u, v recomputed in FP64 (kept when
+// Hit h of the ray (wo, wd, [tmin, tmax]): its t, u, v recomputed in double-float (kept when
 // the FP64 test does not confirm the hit).
 __device__ __forceinline__ void refineOne(const TraceParams& P, float3 wo, float3 wd, float tmin, float tmax, Hit& h) {
     if (h.prim == kInvalid) return;
@@ -1315,13 +1390,20 @@ __device__ __forceinline__ void refineOne(const TraceParams& P, float3 wo, float
         }
     }
     if (!rec) return;
-    const float4 res = refine64(P.inv64, scene, h.inst, wo, wd, rec, sphere, tmin, tmax);
+    const float4* hi = nullptr;
+    const float4* lo = nullptr;
+    if (scene) {  // the instance's inverse frame: record rows plus their low parts
+        const InstanceRecord* R = P.sceneLeaves + P.scenePrimToLeaf[h.inst];
+        hi = R->inv;
+        lo = P.fwd32 + kFrameRows * (size_t)h.inst + 3;
+    }
+    const float4 res = refineFF(hi, lo, wo, wd, rec, sphere, tmin, tmax);
     if (res.w != 0.f) h.t = res.x, h.u = res.y, h.v = res.z;
 }
 
 // The state of an all-hits walk of one ray on a per-thread stack of DEPTH entries: next()
 // returns the ray's hits one at a time, in traversal order, each with t, u, v recomputed
-// in FP64, then a record with prim == kInvalid. The stack points into the object, so
+// in double-float, then a record with prim == kInvalid. The stack points into the object, so
 // an AllHitsWalk is used where it was begun and never copied.
 template <int DEPTH, class U = NoUser>
 struct AllHitsWalk {
@@ -1364,7 +1446,7 @@ struct AllHitsWalk {
     __device__ bool done() const { return finished && i == n; }
 };
 
-// Ray r's closest hit: t, u, v recomputed in FP64 (the hit record is updated in place).
+// Ray r's closest hit: t, u, v recomputed in double-float (the hit record is updated in place).
 __device__ __forceinline__ void refineHit(const TraceParams& P, uint32_t r) {
     uint32_t* p = P.hits + 5 * (size_t)r;
     Hit h{p[0], p[1], __uint_as_float(p[2]), __uint_as_float(p[3]), __uint_as_float(p[4])};
