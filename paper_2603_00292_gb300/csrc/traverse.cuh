@@ -926,6 +926,36 @@ __device__ __forceinline__ void orderSlots(const TraceParams& P, Stack& st, RayS
         orderChildren(P, st, s, m, tn, c);
 }
 
+// An any-hit step takes the hit children in slot order, without sorting them by entry
+// distance: any hit ends the walk, and the sort cost more than its early exits saved
+// (1M spheres any hit 2.80 -> 2.72 ms, terrain AO 0.726 -> 0.723 ms, dense-view AO 6.75
+// -> 6.67 ms). Closest hits keep the near-first order.
+template <int W, bool ANY>
+__device__ __forceinline__ void orderSlotsQ(const TraceParams& P, Stack& st, RayState& s, uint32_t m, const float* tn,
+                                            const uint32_t* c) {
+    if constexpr (ANY) {
+        if (m == 0) return;
+        const uint32_t first = (uint32_t)__ffs(m) - 1u;
+        m &= m - 1u;
+        bool ok = true;
+        while (m) {
+            const uint32_t j = 31u - (uint32_t)__clz(m);
+            m &= ~(1u << j);
+            if constexpr (W == 8)
+                ok &= st.push(pick8(c, j));
+            else
+                ok &= st.push(pick4(c, j));
+        }
+        if (!ok) latchError(P.error, GRT_ERROR_STACK_OVERFLOW);
+        if constexpr (W == 8)
+            s.next = pick8(c, first);
+        else
+            s.next = pick4(c, first);
+    } else {
+        orderSlots<W>(P, st, s, m, tn, c);
+    }
+}
+
 // One traversal step: a node visit (with its leaf tests), an instance entry or an
 // instance exit. Returns true once the ray is finished (s.best is then final).
 template <bool ANY, bool SCENE, bool COUNT, class U = NoUser, int FM = kFmMixed>
@@ -978,7 +1008,7 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
             if (testLeaf<ANY, SCENE, COUNT, U>(P, s, cj & ~kLeafBit, vis, user, payload) && ANY) return true;
         }
     }
-    orderSlots<W>(P, st, s, m, tn, c);
+    orderSlotsQ<W, ANY>(P, st, s, m, tn, c);
     return false;
 }
 
