@@ -9,9 +9,10 @@ vertical field of view; at every primary hit 8 cosine-weighted hemisphere rays o
 length 0.05 * extent traced as any-hit queries.
 
 One step = the whole hot path: bottom-level LBVH build (primitive boxes, centroid
-bounds, Morton codes, radix sort, Karras emission, bottom-up fit), top-level build
-over the instances, camera ray generation, closest-hit traversal of the primary
-rays, and the fused ambient-occlusion kernel (ray generation + any-hit traversal).
+bounds, Morton codes, radix sort, Karras emission, bottom-up fit, 8-wide nodes),
+top-level build over the instances (8-wide nodes), camera ray generation, closest-hit
+traversal of the primary rays, and the fused ambient-occlusion kernel (ray generation +
+any-hit traversal).
 value = (primary rays + AO rays) / step time, in Mrays/s, all ranks together; each
 rank runs its own replica (the path shards by independent replicas, so no collective
 touches the data path). L2 is flushed (512 MB write) between timed steps, outside the
@@ -54,6 +55,7 @@ WORKLOAD = dict(workload="terrain64-ao-1080p", instances=64, terrain_cells=256, 
                 width=1920, height=1080, ao_samples=8, ao_length="0.05*extent", seed=20260301)
 RAY_BYTES, HIT_BYTES = 32, 20
 NODE_BYTES, TRI_BYTES, INST_BYTES = 112, 48, 128  # a 4-wide node visit reads 7 of its 8 float4
+NODE8_BYTES = 224  # an 8-wide node visit reads 14 of its 16 float4
 
 
 def parse():
@@ -311,8 +313,11 @@ def run_grt(args, rank, world, local):
     verts = device_tensor(mesh.vertices)
     idx = device_tensor(mesh.indices)
     frames = device_tensor(sc.frames.packed())
-    geom = Geometry(ctx, vertices=verts, indices=idx)
-    scene = Scene(ctx, [geom.handle] * WORKLOAD["instances"], frames)
+    # the terrain and its instances in 8-wide nodes (GRT_BUILD_WIDE8_NODES): measured faster
+    # than 4-wide on this workload for both queries (features.build_options)
+    W8 = grt.GRT_BUILD_WIDE8_NODES
+    geom = Geometry(ctx, vertices=verts, indices=idx, build_flags=W8)
+    scene = Scene(ctx, [geom.handle] * WORKLOAD["instances"], frames, build_flags=W8)
     rays = new_rays(npix)
     hits = new_hits(npix)
     ao = torch.empty(npix, dtype=torch.float32, device="cuda")
@@ -397,7 +402,7 @@ def run_grt(args, rank, world, local):
         return statistics.median(out)
 
     masked = Scene(ctx, [geom.handle] * WORKLOAD["instances"], frames,
-                   masks=[1 + (k & 1) for k in range(WORKLOAD["instances"])]).build(sh)
+                   masks=[1 + (k & 1) for k in range(WORKLOAD["instances"])], build_flags=W8).build(sh)
     mopt = grt.trace_options(ray_mask=1)
     mhits = new_hits(npix)
 
@@ -417,11 +422,11 @@ def run_grt(args, rank, world, local):
     # three path vertices, one sample per pixel from the camera rays
     quad_v = device_tensor(np.array([[-1, 0, -1], [1, 0, -1], [1, 0, 1], [-1, 0, 1]], np.float32))
     quad_i = device_tensor(np.array([[0, 1, 2], [0, 2, 3]], np.uint32))
-    quad = Geometry(ctx, vertices=quad_v, indices=quad_i).build(sh)
+    quad = Geometry(ctx, vertices=quad_v, indices=quad_i, build_flags=W8).build(sh)
     ctr = 0.5 * (sc.lo + sc.hi)
     light_frame = np.array([0, 0, 0, 1, 2, 1, 2, ctr[0], sc.hi[1] + 0.5 * sc.extent, ctr[2]], np.float32)
     pt_frames = device_tensor(np.concatenate([sc.frames.packed(), light_frame[None, :]]))
-    pt_scene = Scene(ctx, [geom.handle] * WORKLOAD["instances"] + [quad.handle], pt_frames).build(sh)
+    pt_scene = Scene(ctx, [geom.handle] * WORKLOAD["instances"] + [quad.handle], pt_frames, build_flags=W8).build(sh)
     ntri = mesh.indices.shape[0]
     pt_alb = device_tensor(np.concatenate([np.full((ntri, 3), 0.7), np.zeros((2, 3))]).astype(np.float32))
     pt_emi = device_tensor(np.concatenate([np.zeros((ntri, 3)), np.full((2, 3), 20.0)]).astype(np.float32))
@@ -481,11 +486,15 @@ def run_grt(args, rank, world, local):
         ms_b = timed(lambda gq=gq: gq.build(sh))
         ms_t = timed(q_trace)
         ms_s = timed(q_step)
+        ms_c = timed(lambda sq=sq, qhits=qhits: grt.grtTraceClosest(ctx.handle, sq.handle, None, rays, npix, qhits,
+                                                                     None, None, sh))
+        ms_a = timed(lambda sq=sq, qhits=qhits: grt.grtTraceAmbientOcclusion(ctx.handle, sq.handle, rays, qhits, npix,
+                                                                              spp, seed, length, ao, None, sh))
         torch.cuda.synchronize()
         qhit = int((qhits[:, 1].view(torch.int32) != -1).sum().item())
         builds[name] = {"blas_build_ms": round(ms_b, 4), "sah_cost": round(sah_cost(gq), 3),
-                        "closest_plus_ao_ms": round(ms_t, 4), "step_ms": round(ms_s, 4),
-                        "primary_hits": qhit}
+                        "closest_plus_ao_ms": round(ms_t, 4), "closest_ms": round(ms_c, 4), "ao_ms": round(ms_a, 4),
+                        "step_ms": round(ms_s, 4), "primary_hits": qhit}
         sq.close()
         gq.close()
     torch.cuda.synchronize()
@@ -515,12 +524,12 @@ def run_grt(args, rank, world, local):
     st_c = grt.grtGetTraceStatistics(ctx.handle, sh)
     grt.grtTraceAmbientOcclusion(ctx.handle, scene.handle, rays, hits, npix, spp, seed, length, ao, cnt, sh)
     st_a = grt.grtGetTraceStatistics(ctx.handle, sh)
-    bytes_closest = (npix * (RAY_BYTES + HIT_BYTES) + NODE_BYTES * st_c["nodesVisited"] +
+    bytes_closest = (npix * (RAY_BYTES + HIT_BYTES) + NODE8_BYTES * st_c["nodesVisited"] +
                      TRI_BYTES * st_c["trianglesTested"] + INST_BYTES * st_c["instancesEntered"])
     # AO: per pixel the primary ray and hit in, the AO value out; per hit pixel the
     # instance record, geometry header, leaf index, triangle record and frame rows
     bytes_ao = (npix * (RAY_BYTES + HIT_BYTES + 4) + nhit * (128 + 64 + 4 + 48 + 48) +
-                NODE_BYTES * st_a["nodesVisited"] + TRI_BYTES * st_a["trianglesTested"] +
+                NODE8_BYTES * st_a["nodesVisited"] + TRI_BYTES * st_a["trianglesTested"] +
                 INST_BYTES * st_a["instancesEntered"])
     kern = {"closest": (statistics.mean(closest_ms), bytes_closest, "traceKernel<closest, scene>"),
             "ao": (statistics.mean(ao_ms), bytes_ao, "aoTraceKernel")}
@@ -570,7 +579,8 @@ def run_grt(args, rank, world, local):
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(WORKLOAD, rays_per_step=rays_per_step, primary_hits=nhit, l2="flushed between steps",
+            "config": dict(WORKLOAD, node_format="8-wide (GRT_BUILD_WIDE8_NODES)", rays_per_step=rays_per_step,
+                           primary_hits=nhit, l2="flushed between steps",
                            parallelism=f"replicas{world}"),
             "roofline": roofline, "roofline_closest": roofline_closest, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk,
