@@ -13,15 +13,8 @@ namespace grt {
 
 // FM: the node formats the walk may meet (traverse.cuh): kFmPlain (4-wide only),
 // kFmQuant (4-wide or quantised, read per level) or kFmWide8 (8-wide on every level).
-#ifndef GRT_TRACE_MAXNREG
-#define GRT_TRACE_MAXNREG 0  // no cap
-#endif
 template <bool ANY, bool SCENE, bool COUNT, int FM = kFmPlain>
-__global__ void
-#if GRT_TRACE_MAXNREG
-__maxnreg__(GRT_TRACE_MAXNREG)
-#endif
-traceKernel(TraceParams P) {
+__global__ void traceKernel(TraceParams P) {
     extern __shared__ uint32_t sstack[];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     Stack st{sstack + threadIdx.x, P.globalStack + gtid, P.sharedDepth, P.globalDepth, P.globalStride, 0};
