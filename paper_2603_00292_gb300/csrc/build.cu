@@ -115,7 +115,12 @@ __global__ void __launch_bounds__(kScanThreads) sortScan(uint32_t* __restrict__ 
     }
 }
 
-template <typename K>
+// Up to kFusedScanBlocks blocks the downsweep derives its digit offsets from the raw
+// per-block counts itself (every block reads all kRadix x blocks counts from L2), so a
+// radix pass is two launches instead of three; the offsets are those sortScan gives.
+constexpr uint32_t kFusedScanBlocks = 64;
+
+template <typename K, bool FUSED = false>
 __global__ void __launch_bounds__(kSortThreads) sortDownsweep(const K* __restrict__ keysIn,
                                                               const uint32_t* __restrict__ valsIn,
                                                               K* __restrict__ keysOut, uint32_t* __restrict__ valsOut,
@@ -127,10 +132,36 @@ __global__ void __launch_bounds__(kSortThreads) sortDownsweep(const K* __restric
     __shared__ uint32_t tileTotal[kRadix];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t ltMask = (1u << lane) - 1u;
-    for (int d = tid; d < kRadix; d += kSortThreads) {
-        digitBase[d] = offsets[(size_t)d * blocks + blockIdx.x];
+    if constexpr (FUSED) {
+        static_assert(kSortThreads == kRadix, "one thread per digit");
+        // offsets[d * blocks + b] are the raw counts: this block's base for digit d is the
+        // sum of all counts of smaller digits plus those of earlier blocks in digit d
+        uint32_t total = 0, before = 0;
+        for (uint32_t b = 0; b < blocks; ++b) {
+            const uint32_t c = offsets[(size_t)tid * blocks + b];
+            total += c;
+            before += b < blockIdx.x ? c : 0u;
+        }
+        uint32_t incl = total;  // exclusive scan of the digit totals over the block
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) warpHist[w][d] = 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) tileTotal[warp] = incl;
+        __syncthreads();
+        uint32_t warpBase = 0;
+        for (int w = 0; w < warp; ++w) warpBase += tileTotal[w];
+        __syncthreads();
+        digitBase[tid] = warpBase + incl - total + before;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) warpHist[w][tid] = 0;
+    } else {
+        for (int d = tid; d < kRadix; d += kSortThreads) {
+            digitBase[d] = offsets[(size_t)d * blocks + blockIdx.x];
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) warpHist[w][d] = 0;
+        }
     }
     __syncthreads();
     const unsigned t0 = blockIdx.x * tilesPerBlock;
@@ -200,11 +231,17 @@ static grtError radixSortT(Context* ctx, K* keys0, K* keys1, uint32_t* vals0, ui
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         sortUpsweep<K><<<g.blocks, kSortThreads, 0, s>>>(kin, n, shift, g.tilesPerBlock, hist, g.blocks);
-        sortScan<<<1, kScanThreads, 0, s>>>(hist, kRadix * g.blocks);
-        sortDownsweep<K><<<g.blocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, g.tilesPerBlock, g.tiles,
-                                                            hist, g.blocks);
+        if (g.blocks <= kFusedScanBlocks) {
+            sortDownsweep<K, true><<<g.blocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, g.tilesPerBlock,
+                                                                      g.tiles, hist, g.blocks);
+            noteLaunches(2);
+        } else {
+            sortScan<<<1, kScanThreads, 0, s>>>(hist, kRadix * g.blocks);
+            sortDownsweep<K><<<g.blocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, g.tilesPerBlock,
+                                                                g.tiles, hist, g.blocks);
+            noteLaunches(3);
+        }
         GRT_LAUNCH_CHECK();
-        noteLaunches(3);
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
