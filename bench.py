@@ -1212,12 +1212,7 @@ def run_adjoint(args, rank, world, local):
     # colour and position gradients written once (a few tens of KB)
     tables = P.mesh.indices.nbytes + P.mesh.vertices.nbytes + P.colours.nbytes
     nbytes = n * HIT_BYTES + nhit * (RAY_BYTES + 1 + 12) + tables + 2 * P.mesh.vertices.nbytes
-    peaks, how = measured_peaks()
-    achieved = nbytes / (bwd_store_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "shadeBackwardKernel<false, true>", "achieved": round(achieved, 1),
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "peak_source": how, "traffic": ncu_traffic("shadeBackwardKernel<false, true>"),
-                "algorithmic_bytes_per_launch": int(nbytes), "launch_ms": round(bwd_store_ms, 4)}
+    roofline = roofline_entry("shadeBackwardKernel<false, true>", nbytes, bwd_store_ms)
 
     # end to end: parameters up from pinned host memory, image and gradients back
     ch = torch.from_numpy(P.colours).pin_memory()
@@ -1431,14 +1426,10 @@ def run_batched(args, rank, world, local):
     bits = [grt.grtGetBvhInfo(ctx.handle, geom=g.handle).mortonBits for g in geo_s]
     build_bytes = sum(build_bytes_per_prim(b) * m[1].shape[0] for b, m in zip(bits, meshes))
     nbytes = trace_bytes + build_bytes
-    peaks, how = measured_peaks()
-    achieved = nbytes / (batched_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "batchKernel", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": how,
-                "traffic": ncu_traffic("batchKernel"), "algorithmic_bytes_per_launch": int(nbytes),
-                "build_bytes": int(build_bytes), "trace_bytes": int(trace_bytes), "launch_ms": round(batched_ms, 4),
-                "per_ray": {"nodes": round(st["nodesVisited"] / max(1, st["rays"]), 2),
-                            "triangles": round(st["trianglesTested"] / max(1, st["rays"]), 2)}}
+    roofline = roofline_entry("batchKernel", nbytes, batched_ms)
+    roofline.update({"build_bytes": int(build_bytes), "trace_bytes": int(trace_bytes),
+                     "per_ray": {"nodes": round(st["nodesVisited"] / max(1, st["rays"]), 2),
+                                 "triangles": round(st["trianglesTested"] / max(1, st["rays"]), 2)}})
 
     # the same work with every soup built by clustering inside the linear BVH's subtrees
     # (the batch adds a clustering phase per scene), same launch options: batched against
