@@ -121,8 +121,9 @@ typedef struct grtGeometryBuildInput {
  *   FAST         linear BVH: Morton codes, radix sort, Karras emission, bottom-up fit;
  *   BALANCED     bottom-up clustering (PLOC, Meister and Bittner 2018) over the same
  *                Morton order, nearest neighbours searched 8 positions either side;
- *   HIGH_QUALITY the same clustering with a 32-position search (the spatial-split
- *                builder the paper names for this flag is not provided);
+ *   HIGH_QUALITY the same clustering with a 32-position search (spatial splits, which
+ *                the paper names for this option, are the separate bit
+ *                GRT_BUILD_SPLIT_TRIANGLES below, combinable with any method);
  *   CLUSTER_SUBTREES clustering inside the linear BVH's subtrees in one bottom-up pass
  *                (the one-pass form of locally-ordered clustering, H-PLOC, that the paper
  *                names for the balanced option, Sec. 8): every LBVH node merges its
@@ -130,7 +131,7 @@ typedef struct grtGeometryBuildInput {
  *                down to 16 and passes the rest up; the root merges to one. About the
  *                quality of BALANCED at close to the LBVH's build cost.
  * All four give binary nodes, 4-wide nodes and leaves of the same layout, and all
- * support GRT_BUILD_OPERATION_UPDATE. A geometry's flag is fixed by grtCreateGeometry;
+ * support GRT_BUILD_OPERATION_UPDATE (not with GRT_BUILD_SPLIT_TRIANGLES). A geometry's flag is fixed by grtCreateGeometry;
  * grtGetGeometryBuildTemporaryBufferSize and grtBuildGeometry must be given the same
  * flag (the clustering builds need 68 more bytes of temporary memory per primitive).
  * Scene (top-level) builds always use the linear BVH. Other values are rejected with
@@ -141,7 +142,8 @@ typedef enum grtBuildFlags {
     GRT_BUILD_PREFER_HIGH_QUALITY = 2,
     GRT_BUILD_CLUSTER_SUBTREES = 3,
     GRT_BUILD_QUANTIZED_NODES = 0x100,
-    GRT_BUILD_WIDE8_NODES = 0x200
+    GRT_BUILD_WIDE8_NODES = 0x200,
+    GRT_BUILD_SPLIT_TRIANGLES = 0x400
 } grtBuildFlags;
 /* GRT_BUILD_QUANTIZED_NODES, ORed with any of the four: traversal reads 64-byte
  * quantised 4-wide nodes instead of the 128-byte ones (the paper's wide trees, Sec. 6.2,
@@ -174,11 +176,50 @@ typedef enum grtBuildFlags {
  * left empty and latches GRT_ERROR_INVALID_PARAMETER for grtGetLastDeviceError). A
  * scene without the bit walks the 4-wide (or quantised) nodes of every geometry,
  * 8-wide ones included. The batched launch builds the 8-wide nodes of such geometries
- * and traces them through their 4-wide nodes. */
+ * and traces them through their 4-wide nodes.
+ *
+ * GRT_BUILD_SPLIT_TRIANGLES, ORed with any method and node format, for triangle meshes
+ * (other geometries and scenes: GRT_ERROR_INVALID_PARAMETER for geometries, ignored by
+ * scene builds): spatial splits, the paper's high-quality option (Sec. 8, SBVH), made
+ * before the build as in Karras and Aila (HPG 2013): a triangle may be referenced by
+ * several leaves, each bounding the part of it on one side of a set of cutting planes.
+ * S = floor(splitFactor * triangleCount) extra references (splitFactor in [0, 1],
+ * 0 = 0.5) are shared out by priority; the build then runs over exactly
+ * triangleCount + S leaves (grtBvhInfo.leafCount). Per triangle t, in this order:
+ *   box B_t of its vertices; G = union of all B_t; per axis a grid of 1024 cells over G,
+ *   q(x) = (x - G.lo) * (1024 / (G.hi - G.lo)) in double; a box [lo, hi] spans cells
+ *   cl = floor(q(lo+)) to ch = max(cl, ceil(q(hi-)) - 1), clamped to [0, 1023], lo+ and
+ *   hi- the next floats inward (all 0 on an axis of zero extent); level(B) = the
+ *   largest bit length of cl xor ch over the axes;
+ *   weight w_t = floor(2^22 * sqrt(sqrt(2^level(B_t) * max(0, A(B_t) - A_t) / A(G)))),
+ *   A(B) = dx dy + dy dz + dz dx, A_t = (|c.x| + |c.y| + |c.z|) / 2, c = (v1-v0) x (v2-v0),
+ *   all in double rounded to nearest; W = sum of w_t (exact, 64-bit);
+ *   splits s_t = min(31, floor(S w_t / W)) (0 when W = 0); the R = S - sum s_t left over
+ *   go one each to triangles 0 .. R-1;
+ *   the box is cut recursively, s splits at a time: the plane is, over the axes with
+ *   cl != ch, the grid line j = (ch >> b) << b (b the highest bit of cl xor ch) of the
+ *   largest b (ties: longer box extent, then lower axis), at G.lo + j (G.hi - G.lo) /
+ *   1024 rounded to float; with no such axis, the midpoint of the longest axis. Each
+ *   side's box is the box of the triangle's vertices on that side (<= / >= the plane)
+ *   and of its edges' crossings of the plane (double; widened by 2^-47 times the larger
+ *   endpoint magnitude; rounded outward to float), intersected with the box being cut;
+ *   an empty side copies the other side's box and takes no splits. Of the s - 1 splits
+ *   left, the left side takes floor((s - 1) wL / (wL + wR) + 0.5) (w = longest extent,
+ *   double; (s - 1) / 2 when both are 0), the right side the rest; the left side's
+ *   references come first.
+ * References are numbered triangle by triangle; each triangle's first one is the leaf
+ * that primToLeaf names. Closest-hit and any-hit queries return each primitive at most
+ * once as before (the leaf record is the whole triangle); an all-hits query skips a
+ * split geometry (GRT_ERROR_INVALID_PARAMETER: on the host for grtTraceAllHits on the
+ * geometry itself, latched for grtGetLastDeviceError for instances of it), and an
+ * intersection filter may be called more than once for one primitive. UPDATE of a
+ * split geometry and batched launches that include one are GRT_ERROR_INVALID_PARAMETER;
+ * a BUILD from new vertex data re-splits. */
 
 typedef struct grtBuildOptions {
     uint32_t buildFlags; /* grtBuildFlags */
-    uint32_t mortonBits; /* 30 or 63; 0 = 30 when count <= 2^20, else 63 */
+    uint32_t mortonBits; /* 30 or 63; 0 = 30 when the leaf count <= 2^20, else 63 */
+    float splitFactor;   /* GRT_BUILD_SPLIT_TRIANGLES: extra references per triangle, in [0, 1]; 0 = 0.5 */
 } grtBuildOptions;
 
 typedef enum grtBuildOperation {
@@ -448,7 +489,8 @@ typedef struct grtDeviceTarget {
     uint32_t primCount;
     uint32_t numGeomTypes;        /* of the function table */
     uint32_t rayType;             /* function-table row used by the queries */
-    uint32_t nodeFormat;          /* 0: nodes are 128-byte 4-wide nodes; 1: 64-byte quantised ones; 2: 8-wide */
+    uint32_t nodeFormat;          /* bits 0-7: 0 nodes are 128-byte 4-wide nodes, 1 64-byte quantised ones,
+                                     2 8-wide; bit 8: a geometry built with GRT_BUILD_SPLIT_TRIANGLES */
 } grtDeviceTarget;
 
 /* Fills *out for exactly one of scene / geom (built), with an optional function table
@@ -675,6 +717,9 @@ typedef struct grtBvhInfo {
                                traversal instead of wideNodes; NULL for other geometries and for scenes */
     const void* wide8Nodes; /* nodeCount x 256-byte 8-wide nodes (GRT_BUILD_WIDE8_NODES), read by traversal
                                instead of wideNodes; NULL otherwise */
+    uint32_t leafCount;     /* leaves: primCount, or primCount + S with GRT_BUILD_SPLIT_TRIANGLES (the
+                               leaf, parent and node arrays above are sized by it instead of primCount) */
+    uint32_t reserved;
 } grtBvhInfo;
 /*
  * Node (64 bytes, 4 x float4): children c0 and c1 of internal node k

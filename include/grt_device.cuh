@@ -54,7 +54,8 @@ __device__ __forceinline__ grt::TraceParams params(const grtDeviceTarget& T, uin
     grt::TraceParams P{};
     P.rayMask = rayMask ? rayMask : 0xFFFFFFFFu;
     P.target.nodes = static_cast<const float4*>(T.nodes);
-    P.target.fmt = T.nodeFormat;
+    P.target.fmt = T.nodeFormat & 0xFFu;
+    P.target.split = (T.nodeFormat >> 8) & 1u;
     P.target.leaves = T.leaves;
     P.target.primType = T.primType;
     P.target.geomType = T.geomType;

@@ -16,6 +16,7 @@ oracle's BVH, the paper's plane/edge formula vs Moller-Trumbore, BVH invariants.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -23,7 +24,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["build_ref.cpp", "trace_ref.cpp", "shade_ref.cpp", "lambert_ref.cpp"]
+_SRCS = ["build_ref.cpp", "trace_ref.cpp", "shade_ref.cpp", "lambert_ref.cpp", "split_ref.cpp"]
 _LIB_PATH = os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -94,6 +95,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_sah_cost.argtypes = [P, P, i64]
             L.oracle_sah_cost.restype = ctypes.c_double
             L.oracle_quantize_wide.argtypes = [P, P, P, i64, P]
+            L.oracle_split_triangles.argtypes = [P, i64, ctypes.c_uint32, ctypes.c_int, P, P, P, P, P]
+            L.oracle_split_triangles.restype = ctypes.c_int64
             L.oracle_xi.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
             L.oracle_xi.restype = ctypes.c_double
             L.oracle_camera_rays.argtypes = [P, i64, i64, P]
@@ -192,6 +195,37 @@ def fit(childL, childR, leaf_lo, leaf_hi):
     if n >= 2:
         lib().oracle_fit(_p(cl), _p(cr), n, _p(lo), _p(hi), _p(nlo), _p(nhi))
     return nlo, nhi
+
+
+SPLIT_MAX = 31  # splits a triangle takes from the budget by priority (one more may come from the remainder)
+
+
+def split_budget(count: int, factor: float) -> int:
+    """Extra references of a split build of `count` triangles: floor(factor * count) in
+    double, factor the float32 split factor (0 selects 0.5)."""
+    f = float(np.float32(factor)) if factor else 0.5
+    return int(math.floor(f * float(count)))
+
+
+def split_triangles(vertices: np.ndarray, indices: np.ndarray, budget: int, max_splits: int = SPLIT_MAX):
+    """Spatial splits of the triangles before a build (split_ref.cpp): (lo, hi) float32
+    (m,3) reference boxes, prim uint32 (m,), owner bool (m,) and the per-triangle split
+    counts, with m = n + budget references numbered triangle by triangle."""
+    v = _c(vertices, np.float32)
+    idx = _c(indices, np.uint32)
+    n = idx.shape[0]
+    tris = np.ascontiguousarray(v[idx.reshape(-1)].reshape(n, 9), np.float32)
+    m = n + int(budget)
+    lo = np.empty((m, 3), np.float32)
+    hi = np.empty((m, 3), np.float32)
+    prim = np.empty(m, np.uint32)
+    owner = np.empty(m, np.uint8)
+    splits = np.empty(n, np.uint32)
+    got = lib().oracle_split_triangles(_p(tris), n, int(budget), int(max_splits), _p(lo), _p(hi), _p(prim),
+                                       _p(owner), _p(splits))
+    if got != m:
+        raise ValueError("split budget above the triangle count")
+    return lo, hi, prim, owner.astype(bool), splits
 
 
 def sah_cost(node_lo, node_hi) -> float:

@@ -38,6 +38,7 @@ GRT_BUILD_PREFER_HIGH_QUALITY = 2  # PLOC clustering, search radius 32
 GRT_BUILD_CLUSTER_SUBTREES = 3     # clustering inside the linear BVH's subtrees, one bottom-up pass
 GRT_BUILD_QUANTIZED_NODES = 0x100  # ORed with a method: traversal reads 64-byte quantised 4-wide nodes
 GRT_BUILD_WIDE8_NODES = 0x200      # ORed with a method: traversal reads 256-byte 8-wide nodes
+GRT_BUILD_SPLIT_TRIANGLES = 0x400  # ORed with a method: spatial splits of triangles before the build
 CLUSTER_CAP = 16                   # clusters a subtree passes up (the library's kClusterCap)
 GRT_INSTANCE_GEOMETRY = 0
 GRT_INTERSECT_NONE = 0
@@ -80,7 +81,7 @@ class grtGeometryBuildInput(ctypes.Structure):
 
 
 class grtBuildOptions(ctypes.Structure):
-    _fields_ = [("buildFlags", ctypes.c_uint32), ("mortonBits", ctypes.c_uint32)]
+    _fields_ = [("buildFlags", ctypes.c_uint32), ("mortonBits", ctypes.c_uint32), ("splitFactor", ctypes.c_float)]
 
 
 class grtSceneBuildInput(ctypes.Structure):
@@ -109,7 +110,7 @@ class grtBvhInfo(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("leaves", ctypes.c_void_p), ("parents", ctypes.c_void_p),
                 ("nodeCount", ctypes.c_uint32), ("primCount", ctypes.c_uint32), ("primType", ctypes.c_uint32),
                 ("mortonBits", ctypes.c_uint32), ("wideNodes", ctypes.c_void_p), ("quantNodes", ctypes.c_void_p),
-                ("wide8Nodes", ctypes.c_void_p)]
+                ("wide8Nodes", ctypes.c_void_p), ("leafCount", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class grtPathTraceInput(ctypes.Structure):
@@ -297,8 +298,8 @@ def aabb_list_input(boxes, count=None, stride=24, geom_type=0) -> grtGeometryBui
                                  grtAABBListPrimitive(n, stride, _ptr(boxes)))
 
 
-def build_options(morton_bits: int = 0, flags: int = GRT_BUILD_PREFER_FAST) -> grtBuildOptions:
-    return grtBuildOptions(flags, morton_bits)
+def build_options(morton_bits: int = 0, flags: int = GRT_BUILD_PREFER_FAST, split_factor: float = 0.0) -> grtBuildOptions:
+    return grtBuildOptions(flags, morton_bits, split_factor)
 
 
 def grtGetGeometryBuildTemporaryBufferSize(ctx, inp, opts) -> int:

@@ -395,7 +395,7 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (e != GRT_SUCCESS) return e;
         BvhObject* o = findBvh(in.geometry);
         if (!o || o->primType != GRT_PRIMITIVE_TRIANGLE_MESH || in.input.type != GRT_PRIMITIVE_TRIANGLE_MESH ||
-            o->primCount != n)
+            o->primCount != n || o->split)
             return GRT_ERROR_INVALID_PARAMETER;
         if (in.rayCount && (!in.rays || !in.hits || ((uintptr_t)in.rays & 15) || ((uintptr_t)in.hits & 3)))
             return GRT_ERROR_INVALID_PARAMETER;

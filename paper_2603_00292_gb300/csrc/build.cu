@@ -17,6 +17,7 @@
 #include "cluster.cuh"
 #include "lbvh_block.cuh"
 #include "ploc.cuh"
+#include "split.cuh"
 
 namespace grt {
 
@@ -322,7 +323,7 @@ static grtError launchNodeFormats(const BvhObject* o, cudaStream_t s) {
         noteLaunches(1);
     }
     if (o->w8nodes) {
-        wide8Kernel<<<ceilDiv(o->nodeCount, 256), 256, 0, s>>>((const float4*)o->nodes, o->primCount, o->nodeCount,
+        wide8Kernel<<<ceilDiv(o->nodeCount, 256), 256, 0, s>>>((const float4*)o->nodes, o->leafCount, o->nodeCount,
                                                                (float4*)o->w8nodes);
         GRT_LAUNCH_CHECK();
         noteLaunches(1);
@@ -383,7 +384,7 @@ static grtError allowSmem(Kern kernel, size_t bytes) {
 // The device pointers of a build of object o in temporary buffer t.
 static BlockBuild blockBuildOf(Context* c, BvhObject* o, const BuildLayout& L, char* t, uint32_t kind) {
     BlockBuild B{};
-    B.n = o->primCount;
+    B.n = o->leafCount;
     B.bits = o->mortonBits;
     B.sortChunks = 1;
     B.passes = (o->mortonBits + 7) / 8;
@@ -488,6 +489,7 @@ __device__ __forceinline__ float3 setupInstance(const InstanceInput& I, uint32_t
     rec.instanceID = i;
     rec.typeBits = (g->geomType & 0xFFFFFFu) | ((uint32_t)g->primType << 24) |
                    (I.wide8 ? kInstWide8 : g->nodeFormat == 1 ? kInstQuant : 0u) |
+                   ((g->flags & kHeaderSplit) ? kInstSplit : 0u) |
                    ((g->primCount == 0 || missing8) ? kInstEmpty : 0u);
     rec.geometry = g;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -592,11 +594,13 @@ PrimSource primSource(const grtGeometryBuildInput* in, uint32_t count) {
 static std::atomic<int> g_quantGeometries{0};
 bool anyQuantGeometry() { return g_quantGeometries.load(std::memory_order_relaxed) > 0; }
 
+// count primitives over leafCount leaves (more than count only with split triangles).
 static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geomType, uint32_t mortonBits,
-                                BvhObject** out, bool quant = false, bool wide8 = false) {
+                                BvhObject** out, bool quant = false, bool wide8 = false, uint32_t leafCount = 0) {
     BvhObject* o = new BvhObject();
     o->primCount = count;
-    o->nodeCount = count == 0 ? 0 : std::max(count - 1, 1u);
+    o->leafCount = count == 0 ? 0 : std::max(leafCount, count);
+    o->nodeCount = count == 0 ? 0 : std::max(o->leafCount - 1, 1u);
     o->primType = primType;
     o->geomType = geomType;
     o->mortonBits = mortonBits;
@@ -611,8 +615,8 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
         e = cudaMalloc(&o->qnodes, (size_t)o->nodeCount * kQuantWords * sizeof(float4));
     if (e == cudaSuccess && count && wide8)
         e = cudaMalloc(&o->w8nodes, (size_t)o->nodeCount * kWide8Words * sizeof(float4));
-    if (e == cudaSuccess && count) e = cudaMalloc(&o->leaves, (size_t)count * leafBytes);
-    if (e == cudaSuccess && count) e = cudaMalloc(&o->parents, (size_t)(2 * count - 1) * 4);
+    if (e == cudaSuccess && count) e = cudaMalloc(&o->leaves, (size_t)o->leafCount * leafBytes);
+    if (e == cudaSuccess && count) e = cudaMalloc(&o->parents, (size_t)(2 * (size_t)o->leafCount - 1) * 4);
     if (e == cudaSuccess && count && primType != GRT_PRIMITIVE_AABB_LIST) e = cudaMalloc(&o->primToLeaf, (size_t)count * 4);
     if (e == cudaSuccess && count && primType == kPrimScene) e = cudaMalloc(&o->inv64, (size_t)count * sizeof(InstanceFrames64));
     if (e == cudaSuccess && count && primType == kPrimScene) e = cudaMalloc(&o->fwd32, (size_t)count * kFrameRows * sizeof(float4));
@@ -627,6 +631,7 @@ static grtError createBvhObject(uint32_t count, uint32_t primType, uint32_t geom
     h.nodeCount = o->nodeCount;
     h.geomType = geomType;
     h.primToLeaf = o->primToLeaf;
+    h.flags = o->leafCount > count ? kHeaderSplit : 0u;
     if (e == cudaSuccess) e = cudaMemcpy(o->dHeader, &h, sizeof(h), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(o->dHeader);
@@ -668,7 +673,7 @@ static void destroyBvhObject(BvhObject* o) {
 // Morton + sort + Karras over the centroids already in temp (count >= 1).
 static grtError sortAndEmit(Context* ctx, BvhObject* o, const BuildLayout& L, char* temp, cudaStream_t s,
                             const uint32_t** sortedOut, bool emit = true, const void** sortedKeysOut = nullptr) {
-    const uint32_t n = o->primCount;
+    const uint32_t n = o->leafCount;
     const float4* cen = (const float4*)(temp + L.centroids);
     const uint32_t* bounds = (const uint32_t*)(temp + L.bounds);
     void* k0 = temp + L.keys[0];
@@ -714,7 +719,9 @@ static grtError resetBuildScratch(const BuildLayout& L, char* temp, uint32_t n, 
 // this search radius (ploc.cuh).
 constexpr uint32_t kSubtreeMethod = 0xFFFFu;
 static uint32_t buildMethod(const grtBuildOptions* opt) {
-    return opt ? opt->buildFlags & ~(uint32_t)(GRT_BUILD_QUANTIZED_NODES | GRT_BUILD_WIDE8_NODES) : 0u;
+    return opt ? opt->buildFlags &
+                     ~(uint32_t)(GRT_BUILD_QUANTIZED_NODES | GRT_BUILD_WIDE8_NODES | GRT_BUILD_SPLIT_TRIANGLES)
+               : 0u;
 }
 static bool quantFlag(const grtBuildOptions* opt) { return opt && (opt->buildFlags & GRT_BUILD_QUANTIZED_NODES); }
 static bool wide8Flag(const grtBuildOptions* opt) { return opt && (opt->buildFlags & GRT_BUILD_WIDE8_NODES); }
@@ -726,6 +733,18 @@ static uint32_t clusterRadius(const grtBuildOptions* opt) {
 }
 static bool validBuildFlags(const grtBuildOptions* opt) {
     return !opt || (buildMethod(opt) <= 3u && !(quantFlag(opt) && wide8Flag(opt)));
+}
+static bool splitFlag(const grtBuildOptions* opt) { return opt && (opt->buildFlags & GRT_BUILD_SPLIT_TRIANGLES); }
+// The split bit is for triangle meshes, with a factor in [0, 1] (0 = 0.5).
+static bool validSplit(const grtBuildOptions* opt, uint32_t primType) {
+    if (!splitFlag(opt)) return true;
+    return primType == GRT_PRIMITIVE_TRIANGLE_MESH && opt->splitFactor >= 0.f && opt->splitFactor <= 1.f;
+}
+// Extra references of a split build of n triangles: floor(factor * n).
+static uint32_t splitBudgetOf(uint32_t n, const grtBuildOptions* opt) {
+    if (!splitFlag(opt)) return 0;
+    const double f = opt->splitFactor == 0.f ? 0.5 : (double)opt->splitFactor;
+    return (uint32_t)std::floor(f * (double)n);
 }
 
 static std::mutex g_methodLock;
@@ -794,7 +813,7 @@ static SubtreeLayout subtreeLayout(const BuildLayout& L, uint32_t n) {
 // scratch, then the bottom-up walk, which writes the final child words and parent links.
 static grtError launchSubtreeCluster(Context* c, BvhObject* o, const BuildLayout& L, char* t, const PrimSource& S,
                                      const uint32_t* sorted, const void* sortedKeys, cudaStream_t s) {
-    const uint32_t n = o->primCount;
+    const uint32_t n = o->leafCount;
     const SubtreeLayout Q = subtreeLayout(L, n);
     ClusterParams C{};
     C.src = S;
@@ -824,7 +843,7 @@ static grtError launchSubtreeCluster(Context* c, BvhObject* o, const BuildLayout
 // The clustering kernel over the sorted leaves: writes child words and parent links.
 static grtError launchPloc(Context* c, BvhObject* o, const BuildLayout& L, char* t, const PrimSource& S,
                            const uint32_t* sorted, uint32_t radius, cudaStream_t s) {
-    const uint32_t n = o->primCount;
+    const uint32_t n = o->leafCount;
     const PlocLayout Q = plocLayout(L, n);
     PlocParams P{};
     P.src = S;
@@ -854,20 +873,89 @@ static grtError launchPloc(Context* c, BvhObject* o, const BuildLayout& L, char*
     return GRT_SUCCESS;
 }
 
+// Bytes of the method's temporary layout for leaf count n (the LBVH layout L plus the
+// clustering scratch).
+static size_t methodTempBytes(const BuildLayout& L, uint32_t n, uint32_t radius) {
+    return radius == kSubtreeMethod ? subtreeLayout(L, n).total : radius ? plocLayout(L, n).total : L.total;
+}
+
+// Triangle-splitting scratch after the method's: the scene bounds and the two totals,
+// per-triangle counts, per-block sums and the references (32 B each).
+struct SplitLayout {
+    size_t misc, counts, weightSums, blockSums, refs, total;
+};
+static SplitLayout splitLayout(size_t base, uint32_t n, uint32_t m) {
+    SplitLayout Q{};
+    const size_t blocks = ceilDiv(std::max(n, 1u), kSplitThreads);
+    Q.misc = alignUp(base, 256);
+    Q.counts = Q.misc + 256;
+    Q.weightSums = Q.counts + alignUp(4 * (size_t)std::max(n, 1u), 256);
+    Q.blockSums = Q.weightSums + alignUp(8 * blocks, 256);
+    Q.refs = Q.blockSums + alignUp(4 * blocks, 256);
+    Q.total = Q.refs + alignUp(32 * (size_t)std::max(m, 1u), 256);
+    return Q;
+}
+static SplitLayout splitLayoutOf(const BvhObject* o, const BuildLayout& L, uint32_t radius) {
+    return splitLayout(methodTempBytes(L, o->leafCount, radius), o->primCount, o->leafCount);
+}
+
+// The splitting launches of a split build (o->primCount >= 1 triangles): references,
+// their centroids and the centroid bounds, in the scratch the rest of the build reads.
+static grtError launchSplit(Context* c, BvhObject* o, const BuildLayout& L, char* t, const PrimSource& S,
+                            uint32_t radius, cudaStream_t s) {
+    const SplitLayout Q = splitLayoutOf(o, L, radius);
+    SplitParams P{};
+    P.src = S;
+    P.n = o->primCount;
+    P.budget = o->splitBudget;
+    P.sceneBounds = (uint32_t*)(t + Q.misc);
+    P.totals = (unsigned long long*)(t + Q.misc + 32);
+    P.counts = (uint32_t*)(t + Q.counts);
+    P.weightSums = (unsigned long long*)(t + Q.weightSums);
+    P.blockSums = (uint32_t*)(t + Q.blockSums);
+    P.blocks = ceilDiv(P.n, kSplitThreads);
+    P.refs = (float4*)(t + Q.refs);
+    P.centroids = (float4*)(t + L.centroids);
+    P.centroidBounds = (uint32_t*)(t + L.bounds);
+    P.error = &workspace(c)->error;
+    GRT_CUDA(cudaMemsetAsync(t + Q.misc, 0xFF, 12, s));       // running minima start at the top
+    GRT_CUDA(cudaMemsetAsync(t + Q.misc + 12, 0x00, 36, s));  // maxima at the bottom, totals at 0
+    splitBoundsKernel<<<P.blocks, kSplitThreads, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    splitWeightKernel<<<P.blocks, kSplitThreads, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    splitScanWeightsKernel<<<1, kSplitScanThreads, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    splitCountKernel<<<P.blocks, kSplitThreads, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    splitScanKernel<<<1, kSplitScanThreads, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    splitEmitKernel<<<P.blocks, kSplitThreads, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(6);
+    return GRT_SUCCESS;
+}
+
 // The launch sequence of a geometry BUILD (above kSmallBuild) or UPDATE on stream s:
 // scratch reset, centroids and bounds, Morton codes, the radix passes, the hierarchy
 // (Karras emission, or PLOC clustering when radius > 0), the fit.
 static grtError issueGeometryBuild(Context* c, BvhObject* o, uint32_t op, const grtGeometryBuildInput* input,
                                    const BuildLayout& L, char* t, const PrimSource& S, cudaStream_t s,
                                    uint32_t radius = 0) {
-    const uint32_t n = o->primCount;
+    const uint32_t n = o->leafCount;
     grtError e = resetBuildScratch(L, t, n, s);
     if (e != GRT_SUCCESS) return e;
     const uint32_t* sorted = nullptr;
     if (op == GRT_BUILD_OPERATION_BUILD) {
-        primCentroidKernel<<<ceilDiv(n, 256), 256, 0, s>>>(S, (float4*)(t + L.centroids), (uint32_t*)(t + L.bounds));
-        GRT_LAUNCH_CHECK();
-        noteLaunches(1);
+        if (o->split) {
+            e = launchSplit(c, o, L, t, S, radius, s);
+            if (e != GRT_SUCCESS) return e;
+        } else {
+            primCentroidKernel<<<ceilDiv(n, 256), 256, 0, s>>>(S, (float4*)(t + L.centroids),
+                                                               (uint32_t*)(t + L.bounds));
+            GRT_LAUNCH_CHECK();
+            noteLaunches(1);
+        }
         const void* sortedKeys = nullptr;
         e = sortAndEmit(c, o, L, t, s, &sorted, radius == 0, &sortedKeys);
         if (e != GRT_SUCCESS) return e;
@@ -1003,10 +1091,11 @@ grtError grtGetGeometryBuildTemporaryBufferSize(grtContext ctx, const grtGeometr
     if (!ctx || !sizeBytes) return GRT_ERROR_INVALID_PARAMETER;
     grtError e = validateGeometryInput(input, &n);
     if (e != GRT_SUCCESS) return e;
-    if (!validBuildFlags(options)) return GRT_ERROR_INVALID_PARAMETER;
-    const BuildLayout L = buildLayout(n, resolveMortonBits(n, options), false);
-    const uint32_t method = clusterRadius(options);
-    *sizeBytes = method == kSubtreeMethod ? subtreeLayout(L, n).total : method ? plocLayout(L, n).total : L.total;
+    if (!validBuildFlags(options) || !validSplit(options, input->type)) return GRT_ERROR_INVALID_PARAMETER;
+    const uint32_t m = n + splitBudgetOf(n, options);
+    const BuildLayout L = buildLayout(m, resolveMortonBits(m, options), false);
+    const size_t bytes = methodTempBytes(L, m, clusterRadius(options));
+    *sizeBytes = splitFlag(options) ? splitLayout(bytes, n, m).total : bytes;
     return GRT_SUCCESS;
 }
 
@@ -1016,11 +1105,16 @@ grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, c
     if (!ctx || !out) return GRT_ERROR_INVALID_PARAMETER;
     grtError e = validateGeometryInput(input, &n);
     if (e != GRT_SUCCESS) return e;
-    if (!validBuildFlags(options) || (clusterRadius(options) && n > kPlocIndex)) return GRT_ERROR_INVALID_PARAMETER;
+    if (!validBuildFlags(options) || !validSplit(options, input->type)) return GRT_ERROR_INVALID_PARAMETER;
+    const uint32_t m = n + splitBudgetOf(n, options);
+    if (clusterRadius(options) && m > kPlocIndex) return GRT_ERROR_INVALID_PARAMETER;
     BvhObject* o = nullptr;
-    e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(n, options), &o, quantFlag(options),
-                        wide8Flag(options));
+    e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(m, options), &o, quantFlag(options),
+                        wide8Flag(options), m);
     if (e != GRT_SUCCESS) return e;
+    o->split = splitFlag(options);
+    o->splitFactor = o->split ? options->splitFactor : 0.f;
+    o->splitBudget = m - n;
     if (clusterRadius(options)) {
         // the finishing block's shared memory is above the default limit
         cudaError_t ce = cudaFuncSetAttribute(plocFinishKernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1049,8 +1143,11 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
         return GRT_ERROR_INVALID_PARAMETER;
     if (op != GRT_BUILD_OPERATION_BUILD && op != GRT_BUILD_OPERATION_UPDATE) return GRT_ERROR_INVALID_PARAMETER;
     if (op == GRT_BUILD_OPERATION_UPDATE && !o->built) return GRT_ERROR_NOT_BUILT;
+    if (op == GRT_BUILD_OPERATION_UPDATE && o->split) return GRT_ERROR_INVALID_PARAMETER;
     if (n > 0 && (!temp || ((uintptr_t)temp & 15))) return GRT_ERROR_INVALID_PARAMETER;
-    if (options && options->mortonBits && resolveMortonBits(n, options) != o->mortonBits)
+    if (options && options->mortonBits && resolveMortonBits(o->leafCount, options) != o->mortonBits)
+        return GRT_ERROR_INVALID_PARAMETER;
+    if (options && (splitFlag(options) != o->split || (o->split && options->splitFactor != o->splitFactor)))
         return GRT_ERROR_INVALID_PARAMETER;
     const uint32_t radius = radiusOf(o);
     if (!validBuildFlags(options) || (options && clusterRadius(options) != radius)) return GRT_ERROR_INVALID_PARAMETER;
@@ -1064,10 +1161,15 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
         o->built = true;
         return GRT_SUCCESS;
     }
-    const BuildLayout L = buildLayout(n, o->mortonBits, false);
+    const BuildLayout L = buildLayout(o->leafCount, o->mortonBits, false);
     char* t = (char*)temp;
-    const PrimSource S = primSource(input, n);
-    if (op == GRT_BUILD_OPERATION_BUILD && n <= kSmallBuild && radius == 0) {  // initialises its own scratch
+    PrimSource S = primSource(input, n);
+    if (o->split) {  // the build reads the references the splitting writes
+        S.kind = 2;
+        S.count = o->leafCount;
+        S.refs = (const float4*)(t + splitLayoutOf(o, L, radius).refs);
+    }
+    if (op == GRT_BUILD_OPERATION_BUILD && n <= kSmallBuild && radius == 0 && !o->split) {  // initialises its own scratch
         BlockBuild B = blockBuildOf(c, o, L, t, input->type == GRT_PRIMITIVE_TRIANGLE_MESH ? 0u : 1u);
         B.src = S;
         e = launchSmallBuild(B, s);

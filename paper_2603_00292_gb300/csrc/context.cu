@@ -284,6 +284,8 @@ grtError grtGetBvhInfo(grtContext ctx, grtGeometry geom, grtScene scene, grtBvhI
     info->parents = o->parents;
     info->nodeCount = o->nodeCount;
     info->primCount = o->primCount;
+    info->leafCount = o->leafCount;
+    info->reserved = 0;
     info->primType = o->primType;
     info->mortonBits = o->mortonBits;
     return o->built ? GRT_SUCCESS : GRT_ERROR_NOT_BUILT;
@@ -292,7 +294,7 @@ grtError grtGetBvhInfo(grtContext ctx, grtGeometry geom, grtScene scene, grtBvhI
 grtError grtGetBuildTemporaryLayout(uint32_t count, uint32_t mortonBits, size_t* sortedKeysOffset,
                                     size_t* sortedValuesOffset, size_t* centroidBoundsOffset) {
     if (!sortedKeysOffset || !sortedValuesOffset || !centroidBoundsOffset) return GRT_ERROR_INVALID_PARAMETER;
-    grtBuildOptions o{0, mortonBits};
+    grtBuildOptions o{0, mortonBits, 0.f};
     const BuildLayout L = buildLayout(count, resolveMortonBits(count, &o), false);
     *sortedKeysOffset = L.keys[L.finalBuf];
     *sortedValuesOffset = L.vals[L.finalBuf];

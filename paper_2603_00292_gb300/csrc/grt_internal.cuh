@@ -31,8 +31,10 @@ struct alignas(16) BvhHeader {
     uint32_t geomType;
     const uint32_t* primToLeaf;  // primitive (or instance) ID -> sorted leaf position
     const float4* nodes8;        // nodeCount 8-wide nodes (kWide8Words float4), or null: what an 8-wide walk reads
-    uint32_t pad[14];
+    uint32_t flags;              // kHeaderSplit
+    uint32_t pad[13];
 };
+constexpr uint32_t kHeaderSplit = 1u;  // triangles split over several leaves (GRT_BUILD_SPLIT_TRIANGLES)
 static_assert(sizeof(BvhHeader) == 128, "header size");
 
 // Instance record of a scene leaf (128 B): the float32 inverse frame and the bottom
@@ -43,7 +45,7 @@ struct alignas(16) InstanceRecord {
     const float4* nodes;    // bottom-level nodes (4-wide, or quantised with kInstQuant)
     const void* leaves;     // bottom-level leaves
     uint32_t instanceID;
-    uint32_t typeBits;      // geomType (bits 0-23) | primType << 24 | kInstQuant | kInstEmpty
+    uint32_t typeBits;      // geomType (bits 0-23) | primType << 24 | kInstSplit | kInstWide8 | kInstQuant | kInstEmpty
     const BvhHeader* geometry;
     float4 worldLo;         // xyz: world box (rounded outward)
     float4 worldHi;
@@ -58,9 +60,10 @@ struct InstanceFrames64 {
 constexpr uint32_t kInstEmpty = 0x80000000u;
 constexpr uint32_t kInstQuant = 0x40000000u;  // the instance's geometry has quantised nodes
 constexpr uint32_t kInstWide8 = 0x20000000u;  // the instance's geometry has 8-wide nodes
+constexpr uint32_t kInstSplit = 0x10000000u;  // the instance's geometry has split triangles (several leaves each)
 constexpr int kFrameRows = 6;  // float4 rows per instance in BvhObject::fwd32
 __host__ __device__ inline uint32_t instGeomType(uint32_t bits) { return bits & 0xFFFFFFu; }
-__host__ __device__ inline uint32_t instPrimType(uint32_t bits) { return (bits >> 24) & 0x1Fu; }
+__host__ __device__ inline uint32_t instPrimType(uint32_t bits) { return (bits >> 24) & 0x0Fu; }
 static_assert(sizeof(InstanceRecord) == 128, "instance record size");
 
 // Device error word values are grtError codes; the first nonzero one latched wins
@@ -128,7 +131,8 @@ struct BvhObject {
     float4* fwd32;            // scenes: per instance ID kFrameRows float4: forward frame rows 0-2, then
                               // the low parts of the inverse frame (FP64 minus the record's float32 rows)
     uint32_t primCount;
-    uint32_t nodeCount;
+    uint32_t leafCount;  // primCount, or primCount + splitBudget with split triangles
+    uint32_t nodeCount;  // max(leafCount - 1, 1) (0 when empty)
     uint32_t primType;
     uint32_t geomType;
     uint32_t mortonBits;
@@ -136,6 +140,9 @@ struct BvhObject {
     bool built;
     bool quant;  // built with GRT_BUILD_QUANTIZED_NODES (qnodes allocated when primCount > 0)
     bool wide8;  // built with GRT_BUILD_WIDE8_NODES (w8nodes allocated when primCount > 0)
+    bool split;  // built with GRT_BUILD_SPLIT_TRIANGLES
+    float splitFactor;     // as given at creation (0 = the default)
+    uint32_t splitBudget;  // extra references: floor(factor * primCount)
 };
 BvhObject* findBvh(const void* handle);
 bool anyQuantGeometry();  // whether a geometry with quantised nodes exists in the process

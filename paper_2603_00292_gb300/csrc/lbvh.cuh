@@ -34,23 +34,43 @@ __device__ __forceinline__ float3 boxCentroid(const Box3& b) {
 }
 
 struct PrimSource {
-    uint32_t kind;  // 0 triangles, 1 boxes at stride
-    uint32_t count;
+    uint32_t kind;  // 0 triangles, 1 boxes at stride, 2 references to split triangles
+    uint32_t count; // primitives (kind 2: references)
     const char* idx;
     uint32_t idxStride;
     const char* verts;
     uint32_t vertStride;
     const char* boxes;
     uint32_t boxStride;
+    const float4* refs;  // kind 2: two float4 per reference, {lo.xyz, triangle}, {hi.xyz, owner}
 };
 
+__device__ __forceinline__ void loadTriangle(const PrimSource& S, uint32_t t, float3* v) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(S.idx + (size_t)t * S.idxStride);
+    v[0] = load3(S.verts, (size_t)w[0] * S.vertStride);
+    v[1] = load3(S.verts, (size_t)w[1] * S.vertStride);
+    v[2] = load3(S.verts, (size_t)w[2] * S.vertStride);
+}
+
+// Triangle of reference i (kind 2), and whether i is that triangle's first reference.
+__device__ __forceinline__ uint32_t refTriangle(const PrimSource& S, uint32_t i, bool* owner) {
+    *owner = __float_as_uint(__ldg(&S.refs[2 * (size_t)i + 1].w)) != 0u;
+    return __float_as_uint(__ldg(&S.refs[2 * (size_t)i].w));
+}
+
+// Box of primitive (or reference) i; v receives a triangle's vertices (kinds 0 and 2).
 __device__ __forceinline__ Box3 primBox(const PrimSource& S, uint32_t i, float3* v) {
     if (S.kind == 0) {
-        const uint32_t* t = reinterpret_cast<const uint32_t*>(S.idx + (size_t)i * S.idxStride);
-        v[0] = load3(S.verts, (size_t)t[0] * S.vertStride);
-        v[1] = load3(S.verts, (size_t)t[1] * S.vertStride);
-        v[2] = load3(S.verts, (size_t)t[2] * S.vertStride);
+        loadTriangle(S, i, v);
         return triangleBox(v[0], v[1], v[2]);
+    }
+    if (S.kind == 2) {
+        const float4 a = S.refs[2 * (size_t)i], b = S.refs[2 * (size_t)i + 1];
+        loadTriangle(S, __float_as_uint(a.w), v);
+        Box3 r;
+        r.lo = make_float3(a.x, a.y, a.z);
+        r.hi = make_float3(b.x, b.y, b.z);
+        return r;
     }
     const float* b = reinterpret_cast<const float*>(S.boxes + (size_t)i * S.boxStride);
     Box3 r;
@@ -443,16 +463,18 @@ __device__ __forceinline__ void fitLeaf(const FitParams& P, uint32_t k, uint32_t
     Box3 b;
     if (KIND == 0) {
         float4* rec = reinterpret_cast<float4*>(P.leaves) + 3 * (size_t)k;
-        const uint32_t prim = P.sortedPrims ? __ldcg(P.sortedPrims + k) : __float_as_uint(rec[0].w);
+        const uint32_t item = P.sortedPrims ? __ldcg(P.sortedPrims + k) : __float_as_uint(rec[0].w);
         float3 v[3];
-        b = primBox(P.src, prim, v);
+        b = primBox(P.src, item, v);
+        bool owner = true;
+        const uint32_t prim = P.src.kind == 2 ? refTriangle(P.src, item, &owner) : item;
         rec[0] = make_float4(v[0].x, v[0].y, v[0].z, __uint_as_float(prim));
         // w slots: L1 norms of the edges v1-v0 and v2-v0 (scale of the traversal's error bounds)
         const float e1 = fabsf(v[1].x - v[0].x) + fabsf(v[1].y - v[0].y) + fabsf(v[1].z - v[0].z);
         const float e2 = fabsf(v[2].x - v[0].x) + fabsf(v[2].y - v[0].y) + fabsf(v[2].z - v[0].z);
         rec[1] = make_float4(v[1].x, v[1].y, v[1].z, e1);
         rec[2] = make_float4(v[2].x, v[2].y, v[2].z, e2);
-        P.primToLeaf[prim] = k;
+        if (owner) P.primToLeaf[prim] = k;
     } else if (KIND == 1) {
         uint32_t* ids = reinterpret_cast<uint32_t*>(P.leaves);
         const uint32_t prim = P.sortedPrims ? __ldcg(P.sortedPrims + k) : ids[k];

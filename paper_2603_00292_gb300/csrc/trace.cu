@@ -545,6 +545,7 @@ static grtError prepareTrace(Context* c, grtScene scene, grtGeometry geom, grtFu
     *isScene = scene != nullptr;
     P.target.nodes = (const float4*)(o->qnodes ? o->qnodes : o->w8nodes ? o->w8nodes : o->wide);
     P.target.fmt = o->qnodes ? 1u : o->w8nodes ? 2u : 0u;
+    P.target.split = o->split ? 1u : 0u;
     P.target.leaves = o->leaves;
     P.target.primType = o->primType;
     P.target.geomType = o->geomType;
@@ -790,7 +791,7 @@ grtError grtGetDeviceTarget(grtContext ctx, grtScene scene, grtGeometry geom, gr
     if (!o->built) return GRT_ERROR_NOT_BUILT;
     grtDeviceTarget t{};
     t.nodes = o->qnodes ? o->qnodes : o->w8nodes ? o->w8nodes : o->wide;
-    t.nodeFormat = o->qnodes ? 1u : o->w8nodes ? 2u : 0u;
+    t.nodeFormat = (o->qnodes ? 1u : o->w8nodes ? 2u : 0u) | (o->split ? 0x100u : 0u);
     t.leaves = o->leaves;
     t.primToLeaf = o->primToLeaf;
     t.frames64 = o->inv64;
@@ -825,6 +826,8 @@ grtError grtTraceAllHits(grtContext ctx, grtScene scene, grtGeometry geom, const
                          const grtTraceOptions* options, void* stream) {
     if (!ctx || maxHitsPerRay == 0) return GRT_ERROR_INVALID_PARAMETER;
     if (rayCount && (!rays || !hits || !hitCounts || ((uintptr_t)rays & 15))) return GRT_ERROR_INVALID_PARAMETER;
+    const BvhObject* g = geom ? findBvh(geom) : nullptr;
+    if (g && g->split) return GRT_ERROR_INVALID_PARAMETER;  // a triangle would be met once per reference
     Context* c = asContext(ctx);
     TraceParams P{};
     bool isScene = false;

@@ -57,6 +57,7 @@ struct TraceTarget {
     uint32_t geomType;
     uint32_t empty;
     uint32_t fmt;  // node format: 0 4-wide (kWideWords float4), 1 quantised 4-wide (kQuantWords), 2 8-wide
+    uint32_t split;  // a geometry whose triangles are split over several leaves
 };
 
 struct TraceParams {
@@ -1017,7 +1018,9 @@ __device__ __forceinline__ bool stepRay(const TraceParams& P, Stack& st, RayStat
 // leaf it reaches against the whole range [tmin, tmax] and appends each hit to `found`
 // (at most W = slotsOf(FM) per visit), or an instance entry or exit. Returns the number of hits
 // appended, or -1 once the walk is over. Each primitive of each instance sits in one
-// leaf, so each (instance, primitive) is reported at most once.
+// leaf, so each (instance, primitive) is reported at most once; an instance of a geometry
+// with split triangles (several leaves per triangle) is skipped and latches
+// GRT_ERROR_INVALID_PARAMETER.
 template <bool SCENE, class U = NoUser, int FM = kFmMixed>
 __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState& s, Hit* found,
                                        const U* user = nullptr, void* payload = nullptr) {
@@ -1039,7 +1042,11 @@ __device__ __forceinline__ int stepAll(const TraceParams& P, Stack& st, RayState
         const uint32_t leaf = s.next & ~kLeafBit;
         s.next = kNone;
         s.found = false;
-        enterInstance<true, false>(P, st, s, reinterpret_cast<const InstanceRecord*>(P.target.leaves) + leaf, nullptr);
+        const InstanceRecord* R = reinterpret_cast<const InstanceRecord*>(P.target.leaves) + leaf;
+        if (R->typeBits & kInstSplit)
+            latchError(P.error, GRT_ERROR_INVALID_PARAMETER);
+        else
+            enterInstance<true, false>(P, st, s, R, nullptr);
         return 0;
     }
     if (++s.steps > P.maxSteps) {
@@ -1458,6 +1465,10 @@ struct AllHitsWalk {
             beginRay<false>(P, st, s, o, d, tmin, tmax);
         n = i = 0;
         finished = false;
+        if (!scene && P.target.split) {  // each triangle sits in several leaves
+            latchError(P.error, GRT_ERROR_INVALID_PARAMETER);
+            finished = true;
+        }
     }
     __device__ Hit next(const TraceParams& P) {
         while (i == n && !finished) {

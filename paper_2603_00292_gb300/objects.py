@@ -51,11 +51,12 @@ class Geometry:
     """A bottom-level BVH over an indexed triangle mesh or an AABB list. build_flags:
     GRT_BUILD_PREFER_FAST (linear BVH), _BALANCED or _HIGH_QUALITY (PLOC clustering) or
     GRT_BUILD_CLUSTER_SUBTREES, optionally ORed with GRT_BUILD_QUANTIZED_NODES or
-    GRT_BUILD_WIDE8_NODES (the node format traversal reads)."""
+    GRT_BUILD_WIDE8_NODES (the node format traversal reads) and GRT_BUILD_SPLIT_TRIANGLES
+    (spatial splits; split_factor = extra references per triangle, 0 = 0.5)."""
 
     def __init__(self, ctx: Context, *, vertices=None, indices=None, boxes=None, geom_type: int = 0,
                  morton_bits: int = 0, temp: torch.Tensor | None = None, vertex_count: int | None = None,
-                 build_flags: int = 0):
+                 build_flags: int = 0, split_factor: float = 0.0):
         self.ctx = ctx
         if boxes is not None:
             self.boxes = boxes
@@ -63,7 +64,7 @@ class Geometry:
         else:
             self.vertices, self.indices = vertices, indices
             self.input = triangle_mesh_input(indices, vertices, vertex_count=vertex_count, geom_type=geom_type)
-        self.options = build_options(morton_bits, build_flags)
+        self.options = build_options(morton_bits, build_flags, split_factor)
         self.temp_bytes = grtGetGeometryBuildTemporaryBufferSize(ctx.handle, self.input, self.options)
         self.temp = temp if temp is not None and temp.numel() >= self.temp_bytes else empty_bytes(self.temp_bytes)
         self.handle = grtCreateGeometry(ctx.handle, self.input, self.options)

@@ -55,7 +55,8 @@ def test_struct_layouts():
     assert ctypes.sizeof(grt.grtBatchInfo) == 32
     assert ctypes.sizeof(grt.grtBatchItemRecord) == 40
     assert ctypes.sizeof(grt.grtDeviceTarget) == 7 * 8 + 6 * 4
-    assert ctypes.sizeof(grt.grtBvhInfo) == 3 * 8 + 4 * 4 + 3 * 8
+    assert ctypes.sizeof(grt.grtBvhInfo) == 3 * 8 + 4 * 4 + 3 * 8 + 2 * 4
+    assert ctypes.sizeof(grt.grtBuildOptions) == 12
     assert ctypes.sizeof(grt.grtPathTraceInput) == 4 * 8 + 4 * 4 + 8 + 4 * 4
 
 

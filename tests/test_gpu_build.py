@@ -70,15 +70,20 @@ def check_wide(info, ref):
     assert np.array_equal(np.stack([w[:, 4:8], w[:, 12:16], w[:, 20:24]], axis=2), hi), "wide hi"
 
 
-def check_bit_exact(g, case, bits, radius: int = 0, subtree: bool = False):
+def check_bit_exact(g, case, bits, radius: int = 0, subtree: bool = False, split=None):
     """The built geometry `g` of `case` equals the oracle's build bit for bit (the LBVH,
     with radius > 0 the clustering build of that search radius, with subtree the
     clustering inside the LBVH's subtrees): sorted Morton codes and order (from the build
-    temporary), topology, child boxes, parent links and leaf records."""
+    temporary), topology, child boxes, parent links and leaf records. With `split` (the
+    oracle's split_triangles result) the build runs over its references."""
     torch.cuda.synchronize()
     info = g.info()
-    n = info.primCount
-    lo, hi, cen = _oracle_for(case)
+    n = info.leafCount
+    if split is None:
+        lo, hi, cen = _oracle_for(case)
+    else:
+        lo, hi = split[0], split[1]
+        cen = oracle.box_centroids(np.concatenate([lo, hi], axis=1))
     if subtree:
         ref = oracle.subtree_cluster(lo, hi, cen, 10 if bits == 30 else 21, grt.CLUSTER_CAP)
     elif radius:
@@ -92,15 +97,16 @@ def check_bit_exact(g, case, bits, radius: int = 0, subtree: bool = False):
     order = _tensor_bytes(g.temp, voff, n * 4, np.uint32)
     assert np.array_equal(keys.astype(np.uint64), ref["sorted_codes"]), "Morton codes / sort"
     assert np.array_equal(order, ref["order"]), "stable sort order"
-    check_tree(info, ref, case)
+    check_tree(info, ref, case, None if split is None else split[2])
 
 
-def check_tree(info, ref, case):
+def check_tree(info, ref, case, prim_of=None):
     """The geometry's binary nodes (both child boxes and child words), parent links,
     4-wide nodes and leaf records equal those of the oracle build `ref` of `case`, bit
     for bit. Triangle leaves hold the sorted triangles' vertices, the primitive ID and
-    the L1 norms |v1 - v0|_1 and |v2 - v0|_1 (summed x, y, z in float32)."""
-    n = info.primCount
+    the L1 norms |v1 - v0|_1 and |v2 - v0|_1 (summed x, y, z in float32). prim_of maps
+    the build's items to triangles (split references), identity by default."""
+    n = info.leafCount
     lo, hi = ref["leaf_lo"], ref["leaf_hi"]
     nodes = _read(info.nodes, info.nodeCount * 64, np.float32).reshape(-1, 16)
     children = nodes.view(np.uint32)[:, 12:14]
@@ -137,8 +143,9 @@ def check_tree(info, ref, case):
     if "indices" in case:
         rec = _read(info.leaves, n * 48, np.float32).reshape(n, 12)
         prim = rec[:, 3].view(np.uint32)
-        assert np.array_equal(prim, ref["order"])
-        v = case["vertices"][case["indices"][ref["order"]]]  # (n,3,3)
+        tri = ref["order"] if prim_of is None else prim_of[ref["order"]]
+        assert np.array_equal(prim, tri)
+        v = case["vertices"][case["indices"][tri]]  # (n,3,3)
         assert np.array_equal(rec[:, 0:3], v[:, 0]) and np.array_equal(rec[:, 4:7], v[:, 1])
         assert np.array_equal(rec[:, 8:11], v[:, 2])
         for j, col in ((1, 7), (2, 11)):
