@@ -185,28 +185,29 @@ typedef enum grtBuildFlags {
  * several leaves, each bounding the part of it on one side of a set of cutting planes.
  * S = floor(splitFactor * triangleCount) extra references (splitFactor in [0, 1],
  * 0 = 0.5) are shared out by priority; the build then runs over exactly
- * triangleCount + S leaves (grtBvhInfo.leafCount). Per triangle t, in this order:
- *   box B_t of its vertices; G = union of all B_t; per axis a grid of 1024 cells over G,
- *   q(x) = (x - G.lo) * (1024 / (G.hi - G.lo)) in double; a box [lo, hi] spans cells
- *   cl = floor(q(lo+)) to ch = max(cl, ceil(q(hi-)) - 1), clamped to [0, 1023], lo+ and
- *   hi- the next floats inward (all 0 on an axis of zero extent); level(B) = the
- *   largest bit length of cl xor ch over the axes;
- *   weight w_t = floor(2^22 * sqrt(sqrt(2^level(B_t) * max(0, A(B_t) - A_t) / A(G)))),
- *   A(B) = dx dy + dy dz + dz dx, A_t = (|c.x| + |c.y| + |c.z|) / 2, c = (v1-v0) x (v2-v0),
- *   all in double rounded to nearest; W = sum of w_t (exact, 64-bit);
- *   splits s_t = min(31, floor(S w_t / W)) (0 when W = 0); the R = S - sum s_t left over
- *   go one each to triangles 0 .. R-1;
+ * triangleCount + S leaves (grtBvhInfo.leafCount). In this order, in float32 rounded to
+ * nearest (the integer steps exact):
+ *   box B_t of triangle t's vertices; G = union of all B_t; per axis a grid of 1024 cells
+ *   over G, q(x) = (x - G.lo) * (1024 / (G.hi - G.lo)); a box [lo, hi] spans cells
+ *   cl = floor(q(lo + d)) to ch = max(cl, ceil(q(hi - d)) - 1), clamped to [0, 1023],
+ *   d = 2^-18 max(|lo|, |hi|) (all 0 on an axis of zero extent); level(B) = the largest
+ *   bit length of cl xor ch over the axes;
+ *   weight w_t = the integer cube root of 2^53 (max(0, A(B_t) - A_t) / A(G)) 2^level(B_t),
+ *   A(B) = (dx dy + dy dz) + dz dx, A_t = ((|c.x| + |c.y|) + |c.z|) / 2, c = (v1-v0) x
+ *   (v2-v0); W = sum of w_t; with C_t = w_0 + .. + w_{t-1}, triangle t takes
+ *   min(31, floor(S C_{t+1} / W) - floor(S C_t / W)) splits (0 when W = 0), and the
+ *   R = S - sum left over go one each to triangles 0 .. R-1;
  *   the box is cut recursively, s splits at a time: the plane is, over the axes with
  *   cl != ch, the grid line j = (ch >> b) << b (b the highest bit of cl xor ch) of the
- *   largest b (ties: longer box extent, then lower axis), at G.lo + j (G.hi - G.lo) /
- *   1024 rounded to float; with no such axis, the midpoint of the longest axis. Each
- *   side's box is the box of the triangle's vertices on that side (<= / >= the plane)
- *   and of its edges' crossings of the plane (double; widened by 2^-47 times the larger
- *   endpoint magnitude; rounded outward to float), intersected with the box being cut;
- *   an empty side copies the other side's box and takes no splits. Of the s - 1 splits
- *   left, the left side takes floor((s - 1) wL / (wL + wR) + 0.5) (w = longest extent,
- *   double; (s - 1) / 2 when both are 0), the right side the rest; the left side's
- *   references come first.
+ *   largest b (ties: longer box extent, then lower axis), at G.lo + j ((G.hi - G.lo) /
+ *   1024); with no such axis, (lo + hi) / 2 of the longest axis. Each side's box is the
+ *   box of the triangle's vertices on that side (<= / >= the plane), then of its edges'
+ *   crossings of the plane (t = (P - a_k) / (e_k - a_k), a_c + (e_c - a_c) t widened by
+ *   2^-19 max(|a_c|, |e_c|) + 2^-140, which bounds its rounding error), intersected with
+ *   the box being cut; an empty side copies the other side's box and takes no splits.
+ *   Of the s - 1 splits left, the left side takes floor((s - 1) wL / (wL + wR) + 0.5)
+ *   (w = longest extent; (s - 1) / 2 when both are 0), the right side the rest; the left
+ *   side's references come first.
  * References are numbered triangle by triangle; each triangle's first one is the leaf
  * that primToLeaf names. Closest-hit and any-hit queries return each primitive at most
  * once as before (the leaf record is the whole triangle); an all-hits query skips a

@@ -10,22 +10,21 @@
 // shared out by a per-triangle priority, and each triangle is cut recursively at the
 // most important plane of the scene's Morton grid that crosses its box.
 //
-// Steps, in this order (every double operation rounds to nearest; compile with
+// Steps, in this order (every operation is float32, rounded to nearest; compile with
 // -ffp-contract=off so no multiply-add is fused):
-//  1. B_t = the float box of triangle t's vertices; G = the union of all B_t.
-//  2. Grid: per axis a, ext_a = G.hi_a - G.lo_a, q(x) = (x - G.lo_a) (1024 / ext_a), and a
-//     box [lo, hi] spans the cells cl = floor(q(lo+)) to ch = max(cl, ceil(q(hi-)) - 1),
-//     both clamped to [0, 1023] (all cell 0 on an axis of zero extent), where lo+ and hi-
-//     are the next floats inward: a box that ends on a grid line, or one float step past
-//     it, does not reach the next cell. The level of a box is the largest bit length over
-//     the axes of cl xor ch (0..10).
-//  3. Priority: A(B) = dx dy + dy dz + dz dx (half the surface area); the triangle's own
-//     A_tri = (|c.x| + |c.y| + |c.z|) / 2 with c = (v1 - v0) x (v2 - v0) (its three
-//     axis projections, which no set of covering boxes can undercut); excess =
-//     max(0, A(B_t) - A_tri); r_t = 2^level(B_t) excess / A(G) (<= 1024); the priority is
-//     the published r_t^(1/3) (X = 2, Y = 1/3), taken exactly as the weight w_t = the
-//     integer cube root of floor(2^53 r_t) (the largest w with w^3 <= it; < 2^21), so the
-//     total W is an exact integer.
+//  1. B_t = the box of triangle t's vertices; G = the union of all B_t.
+//  2. Grid: per axis a, ext_a = G.hi_a - G.lo_a, inv_a = 1024 / ext_a, q(x) = (x - G.lo_a)
+//     inv_a. A box [lo, hi] spans the cells cl = floor(q(lo + d)) to ch = max(cl,
+//     ceil(q(hi - d)) - 1), clamped to [0, 1023] (all 0 on an axis of zero extent), where
+//     d = 2^-18 max(|lo|, |hi|) narrows the box by more than the widening of step 5: a box
+//     that ends on a grid line, or a crossing widened past one, does not reach the next
+//     cell. The level of a box is the largest bit length over the axes of cl xor ch (0..10).
+//  3. Priority: A(B) = (dx dy + dy dz) + dz dx (half the surface area); the triangle's own
+//     A_tri = ((|c.x| + |c.y|) + |c.z|) / 2 with c = (v1 - v0) x (v2 - v0) (its three axis
+//     projections, which no set of covering boxes can undercut); excess = max(0, A(B_t) -
+//     A_tri); r_t = (excess / A(G)) 2^level(B_t) (<= 1024); the priority is the published
+//     r_t^(1/3) (X = 2, Y = 1/3), taken exactly as the weight w_t = the integer cube root
+//     of r_t 2^53 (the largest w with w^3 <= it; < 2^21), so the total W is an exact integer.
 //  4. Splits: with C_t = w_0 + ... + w_{t-1} (C_n = W), triangle t's share of the budget S
 //     is s_t = min(maxSplits, floor(S C_{t+1} / W) - floor(S C_t / W)): each gets its fair
 //     share S w_t / W rounded down or up, and the shares add up to S (Karras and Aila
@@ -34,16 +33,19 @@
 //     (+1) references, so there are exactly n + S of them, numbered triangle by triangle.
 //  5. Splitting a box B with s splits left: none left -> emit B. Otherwise pick the plane:
 //     per axis the highest bit b where cl and ch differ names the grid line j = (ch >> b)
-//     << b, strictly inside the box, at G.lo + j ext / 1024 (rounded to float); the axis with
-//     the largest b wins (ties: the longer extent of B, then the lower axis). If no grid
-//     line crosses B, cut the longest axis at its midpoint. Each side's box is the box
-//     of the triangle's vertices on that side and of the points where its edges cross
-//     the plane (computed in double, widened by 2^-47 of the endpoints' magnitude and
-//     rounded outward to float, so it holds the exact crossing), intersected with B. An
-//     empty side takes a copy of the other side's box and no further splits. The s - 1
-//     splits left go to the sides in proportion to their longest extents (rounded to
-//     nearest), the left side first (depth first: all of the left side's references
-//     precede the right side's).
+//     << b, inside the box, at G.lo + j (ext / 1024); the axis with the largest b wins
+//     (ties: the longer extent hi - lo of B, then the lower axis). If no grid line crosses
+//     B, cut the longest axis at (lo + hi) / 2. Each side's box is the box of the
+//     triangle's vertices on that side (<= / >= the plane), then of the points where its
+//     edges cross the plane, intersected with B. A crossing of edge a-e is t = (P - a_k) /
+//     (e_k - a_k), q_c = a_c + (e_c - a_c) t on the other axes (P itself on the cut axis),
+//     widened to [q_c - pad, q_c + pad] with pad = max(|a_c|, |e_c|) 2^-19 + 2^-140: the
+//     rounding errors of q_c stay below 12 units in the last place of that magnitude (and
+//     of the widening subtraction below one more), so the interval holds the exact
+//     crossing. An empty side takes a copy of the other side's box and no further splits.
+//     The s - 1 splits left go to the sides in proportion to their longest extents w:
+//     the left side takes floor((s - 1) wL / (wL + wR) + 0.5) ((s - 1) / 2 when both are
+//     0); the left side's references come first (depth first).
 //  6. The first reference of each triangle is its owner (the one a primitive-to-leaf
 //     map points at).
 #include <algorithm>
@@ -57,41 +59,21 @@ struct FBox {
     float lo[3], hi[3];
 };
 
-float round_down(double d) {
-    float f = (float)d;
-    if ((double)f > d) f = std::nextafter(f, -INFINITY);
-    return f;
-}
-
-float round_up(double d) {
-    float f = (float)d;
-    if ((double)f < d) f = std::nextafter(f, INFINITY);
-    return f;
-}
-
 struct Grid {
-    double lo[3], ext[3], inv[3];
-    // the cell holding x (the higher one on a grid line) ...
-    int cell(double x, int a) const {
-        if (inv[a] == 0.0) return 0;
-        const double f = std::floor((x - lo[a]) * inv[a]);
-        if (!(f >= 0.0)) return 0;
-        if (f > 1023.0) return 1023;
+    float lo[3], ext[3], inv[3];
+    int cell(float x, int a, bool end) const {
+        if (inv[a] == 0.0f) return 0;
+        const float q = (x - lo[a]) * inv[a];
+        const float f = end ? std::ceil(q) - 1.0f : std::floor(q);
+        if (!(f >= 0.0f)) return 0;
+        if (f > 1023.0f) return 1023;
         return (int)f;
     }
-    // ... and the cell that a box ending at x reaches (the lower one on a grid line)
-    int cell_below(double x, int a) const {
-        if (inv[a] == 0.0) return 0;
-        const double f = std::ceil((x - lo[a]) * inv[a]) - 1.0;
-        if (!(f >= 0.0)) return 0;
-        if (f > 1023.0) return 1023;
-        return (int)f;
-    }
-    // first and last cell of the box's extent on axis a, the box narrowed by one float
-    // step at each end (a box widened outward by a step past a grid line does not cross it)
-    void span(const float* blo, const float* bhi, int a, int* cl, int* ch) const {
-        *cl = cell(std::nextafter(blo[a], INFINITY), a);
-        *ch = std::max(*cl, cell_below(std::nextafter(bhi[a], -INFINITY), a));
+    // first and last cell of the box's extent on axis a (narrowed by d at each end)
+    void span(const FBox& b, int a, int* cl, int* ch) const {
+        const float d = std::max(std::fabs(b.lo[a]), std::fabs(b.hi[a])) * 0x1p-18f;
+        *cl = cell(b.lo[a] + d, a, false);
+        *ch = std::max(*cl, cell(b.hi[a] - d, a, true));
     }
 };
 
@@ -113,22 +95,20 @@ int level(const Grid& g, const FBox& b) {
     int L = 0;
     for (int a = 0; a < 3; ++a) {
         int cl, ch;
-        g.span(b.lo, b.hi, a, &cl, &ch);
+        g.span(b, a, &cl, &ch);
         L = std::max(L, bit_length((uint32_t)(cl ^ ch)));
     }
     return L;
 }
 
-double half_area(const FBox& b) {
-    const double dx = (double)b.hi[0] - (double)b.lo[0];
-    const double dy = (double)b.hi[1] - (double)b.lo[1];
-    const double dz = (double)b.hi[2] - (double)b.lo[2];
+float half_area(const FBox& b) {
+    const float dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
     return (dx * dy + dy * dz) + dz * dx;
 }
 
-double longest(const FBox& b) {
-    double w = 0.0;
-    for (int a = 0; a < 3; ++a) w = std::max(w, (double)b.hi[a] - (double)b.lo[a]);
+float longest(const FBox& b) {
+    float w = 0.0f;
+    for (int a = 0; a < 3; ++a) w = std::max(w, b.hi[a] - b.lo[a]);
     return w;
 }
 
@@ -136,30 +116,29 @@ bool empty(const FBox& b) { return b.lo[0] > b.hi[0] || b.lo[1] > b.hi[1] || b.l
 
 // The plane that cuts box b: axis and coordinate (step 5).
 void choose_plane(const Grid& g, const FBox& b, int* axis, float* plane) {
-    int best = -1, bestBit = -1;
-    double bestExt = -1.0;
-    int bestJ = 0;
+    int best = -1, bestBit = -1, bestJ = 0;
+    float bestExt = -1.0f;
     for (int a = 0; a < 3; ++a) {
         int cl, ch;
-        g.span(b.lo, b.hi, a, &cl, &ch);
+        g.span(b, a, &cl, &ch);
         if (cl == ch) continue;
         const int bit = bit_length((uint32_t)(cl ^ ch)) - 1;
-        const double e = (double)b.hi[a] - (double)b.lo[a];
+        const float e = b.hi[a] - b.lo[a];
         if (bit > bestBit || (bit == bestBit && e > bestExt)) best = a, bestBit = bit, bestExt = e, bestJ = (ch >> bit) << bit;
     }
     if (best >= 0) {
         *axis = best;
-        *plane = (float)(g.lo[best] + (double)bestJ * (g.ext[best] * (1.0 / 1024.0)));
+        *plane = g.lo[best] + (float)bestJ * (g.ext[best] * 0x1p-10f);
         return;
     }
     int a0 = 0;
-    double e0 = (double)b.hi[0] - (double)b.lo[0];
+    float e0 = b.hi[0] - b.lo[0];
     for (int a = 1; a < 3; ++a) {
-        const double e = (double)b.hi[a] - (double)b.lo[a];
+        const float e = b.hi[a] - b.lo[a];
         if (e > e0) a0 = a, e0 = e;
     }
     *axis = a0;
-    *plane = (float)(0.5 * ((double)b.lo[a0] + (double)b.hi[a0]));
+    *plane = 0.5f * (b.lo[a0] + b.hi[a0]);
 }
 
 // Box of the part of triangle v on one side of the plane x_axis = P, intersected with b.
@@ -176,16 +155,16 @@ FBox clip_side(const float v[3][3], int axis, float P, bool left, const FBox& b)
         const float* e = v[(i + 1) % 3];
         const bool crosses = (a[axis] < P && e[axis] > P) || (a[axis] > P && e[axis] < P);
         if (!crosses) continue;
-        const double t = ((double)P - (double)a[axis]) / ((double)e[axis] - (double)a[axis]);
+        const float t = (P - a[axis]) / (e[axis] - a[axis]);
         for (int c = 0; c < 3; ++c) {
             if (c == axis) {
                 r.lo[c] = std::min(r.lo[c], P), r.hi[c] = std::max(r.hi[c], P);
                 continue;
             }
-            const double q = (double)a[c] + ((double)e[c] - (double)a[c]) * t;
-            const double pad = std::max(std::fabs((double)a[c]), std::fabs((double)e[c])) * 0x1p-47;
-            r.lo[c] = std::min(r.lo[c], round_down(q - pad));
-            r.hi[c] = std::max(r.hi[c], round_up(q + pad));
+            const float q = a[c] + (e[c] - a[c]) * t;
+            const float pad = std::max(std::fabs(a[c]), std::fabs(e[c])) * 0x1p-19f + 0x1p-140f;
+            r.lo[c] = std::min(r.lo[c], q - pad);
+            r.hi[c] = std::max(r.hi[c], q + pad);
         }
     }
     for (int c = 0; c < 3; ++c) r.lo[c] = std::max(r.lo[c], b.lo[c]), r.hi[c] = std::min(r.hi[c], b.hi[c]);
@@ -213,9 +192,9 @@ void split_box(const Grid& g, const float v[3][3], const FBox& b, int s, std::ve
         R = L;
         sL = rest;
     } else {
-        const double wL = longest(L), wR = longest(R);
-        if (wL + wR > 0.0)
-            sL = (int)std::floor(((double)rest * wL) / (wL + wR) + 0.5);
+        const float wL = longest(L), wR = longest(R);
+        if (wL + wR > 0.0f)
+            sL = (int)std::floor((float)rest * wL / (wL + wR) + 0.5f);
         else
             sL = rest / 2;
         sL = std::min(sL, rest);
@@ -250,24 +229,24 @@ int64_t oracle_split_triangles(const float* tris, int64_t n, uint32_t budget, in
     Grid g;
     for (int a = 0; a < 3; ++a) {
         g.lo[a] = G.lo[a];
-        g.ext[a] = (double)G.hi[a] - (double)G.lo[a];
-        g.inv[a] = g.ext[a] > 0.0 ? 1024.0 / g.ext[a] : 0.0;
+        g.ext[a] = G.hi[a] - G.lo[a];
+        g.inv[a] = g.ext[a] > 0.0f ? 1024.0f / g.ext[a] : 0.0f;
     }
-    const double areaG = half_area(G);
+    const float areaG = half_area(G);
     std::vector<uint32_t> w(n);
     uint64_t W = 0;
     for (int64_t t = 0; t < n; ++t) {
         const float* v = tris + 9 * t;
-        const double e1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
-        const double e2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
-        const double cx = e1[1] * e2[2] - e1[2] * e2[1];
-        const double cy = e1[2] * e2[0] - e1[0] * e2[2];
-        const double cz = e1[0] * e2[1] - e1[1] * e2[0];
-        const double tri = 0.5 * ((std::fabs(cx) + std::fabs(cy)) + std::fabs(cz));
-        double excess = half_area(box[t]) - tri;
-        if (!(excess > 0.0)) excess = 0.0;
-        const double r = areaG > 0.0 ? std::ldexp(excess / areaG, level(g, box[t])) : 0.0;
-        w[t] = integer_cube_root((uint64_t)std::ldexp(r, 53));
+        const float e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
+        const float e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+        const float cx = e1[1] * e2[2] - e1[2] * e2[1];
+        const float cy = e1[2] * e2[0] - e1[0] * e2[2];
+        const float cz = e1[0] * e2[1] - e1[1] * e2[0];
+        const float tri = 0.5f * ((std::fabs(cx) + std::fabs(cy)) + std::fabs(cz));
+        float excess = half_area(box[t]) - tri;
+        if (!(excess > 0.0f)) excess = 0.0f;
+        const float r = areaG > 0.0f ? (excess / areaG) * (float)(1u << level(g, box[t])) : 0.0f;
+        w[t] = integer_cube_root((uint64_t)(r * 0x1p53f));
         W += w[t];
     }
     std::vector<uint32_t> s(n, 0);

@@ -882,16 +882,18 @@ static size_t methodTempBytes(const BuildLayout& L, uint32_t n, uint32_t radius)
 // Triangle-splitting scratch after the method's: the scene bounds and the two totals,
 // per-triangle counts, per-block sums and the references (32 B each).
 struct SplitLayout {
-    size_t misc, counts, weightSums, blockSums, refs, total;
+    size_t misc, counts, firstSlot, weightSums, blockSums, slotTriangle, refs, total;
 };
 static SplitLayout splitLayout(size_t base, uint32_t n, uint32_t m) {
     SplitLayout Q{};
     const size_t blocks = ceilDiv(std::max(n, 1u), kSplitThreads);
     Q.misc = alignUp(base, 256);
     Q.counts = Q.misc + 256;
-    Q.weightSums = Q.counts + alignUp(4 * (size_t)std::max(n, 1u), 256);
+    Q.firstSlot = Q.counts + alignUp(4 * (size_t)std::max(n, 1u), 256);
+    Q.weightSums = Q.firstSlot + alignUp(4 * (size_t)std::max(n, 1u), 256);
     Q.blockSums = Q.weightSums + alignUp(8 * blocks, 256);
-    Q.refs = Q.blockSums + alignUp(4 * blocks, 256);
+    Q.slotTriangle = Q.blockSums + alignUp(4 * blocks, 256);
+    Q.refs = Q.slotTriangle + alignUp(4 * (size_t)std::max(m, 1u), 256);
     Q.total = Q.refs + alignUp(32 * (size_t)std::max(m, 1u), 256);
     return Q;
 }
@@ -913,6 +915,8 @@ static grtError launchSplit(Context* c, BvhObject* o, const BuildLayout& L, char
     P.counts = (uint32_t*)(t + Q.counts);
     P.weightSums = (unsigned long long*)(t + Q.weightSums);
     P.blockSums = (uint32_t*)(t + Q.blockSums);
+    P.firstSlot = (uint32_t*)(t + Q.firstSlot);
+    P.slotTriangle = (uint32_t*)(t + Q.slotTriangle);
     P.blocks = ceilDiv(P.n, kSplitThreads);
     P.refs = (float4*)(t + Q.refs);
     P.centroids = (float4*)(t + L.centroids);
@@ -930,9 +934,11 @@ static grtError launchSplit(Context* c, BvhObject* o, const BuildLayout& L, char
     GRT_LAUNCH_CHECK();
     splitScanKernel<<<1, kSplitScanThreads, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
-    splitEmitKernel<<<P.blocks, kSplitThreads, 0, s>>>(P);
+    splitSlotsKernel<<<P.blocks, kSplitThreads, 0, s>>>(P);
     GRT_LAUNCH_CHECK();
-    noteLaunches(6);
+    splitEmitKernel<<<ceilDiv((size_t)P.n + P.budget, kSplitThreads), kSplitThreads, 0, s>>>(P);
+    GRT_LAUNCH_CHECK();
+    noteLaunches(7);
     return GRT_SUCCESS;
 }
 

@@ -6,15 +6,19 @@
 // plane of a 1024-cell grid over the scene that crosses its box. The build then runs
 // over the n + S references (PrimSource kind 2) exactly as over primitives.
 //
-// Six launches, one thread per triangle where not said: the scene box; the weights
+// Seven launches, one thread per triangle where not said: the scene box; the weights
 // (integer cube roots of the priority) and their per-block sums; one block's exclusive
 // scan of those sums (and the total W); each triangle's share of the budget from its
 // place in the running sum of weights, floor(S C_{t+1} / W) - floor(S C_t / W), and
-// per-block sums of the shares; one block's scan of those; the cuts themselves, which
-// write the references, their centroids and the centroid bounds. Every double operation
-// is an explicit round-to-nearest intrinsic (nothing is fused), min / max are written
-// as selections and the integer steps are exact, so the results are bit-for-bit those
-// of any sequential IEEE-754 evaluation of the same steps.
+// per-block sums of the shares; one block's scan of those; each triangle's first slot
+// and the triangle of every slot; then one thread per reference, which walks down its
+// triangle's cut tree to its leaf and writes the reference, its centroid and the
+// centroid bounds. A thread per reference keeps the lanes of a warp busy however
+// unevenly the splits fall (a thread per triangle would wait on the most-split one).
+// The arithmetic is float32 (GB300's FP64 rate is a small fraction of its FP32 rate),
+// every operation an explicit round-to-nearest intrinsic (nothing is fused), min / max
+// written as selections and the integer steps exact, so the results are bit-for-bit
+// those of any sequential IEEE-754 evaluation of the same steps.
 #pragma once
 
 #include "lbvh.cuh"
@@ -22,7 +26,6 @@
 namespace grt {
 
 constexpr int kSplitMax = 31;               // splits one triangle takes by priority (+1 from the remainder)
-constexpr int kSplitStack = kSplitMax + 3;  // pending right sides of one triangle's cuts (<= its splits)
 constexpr int kSplitThreads = 256;
 constexpr int kSplitScanThreads = 1024;
 
@@ -31,7 +34,7 @@ struct SplitParams {
     uint32_t n;                    // triangles
     uint32_t budget;               // S
     uint32_t* sceneBounds;         // 6 ordered words: union of the triangle boxes
-    unsigned long long* totals;    // [0] sum of the weights W, [1] splits handed out by priority
+    unsigned long long* totals;    // [0] sum of the weights W, [1] splits handed out by priority, [2] 1 / W (double)
     uint32_t* counts;              // per triangle: its weight, then its priority splits
     unsigned long long* weightSums;  // per block of kSplitThreads triangles: weights, then their exclusive prefix
     uint32_t* blockSums;           // per block: splits, then their exclusive prefix
@@ -39,6 +42,8 @@ struct SplitParams {
     float4* refs;                  // (n + S) x {lo.xyz, triangle}, {hi.xyz, owner}
     float4* centroids;             // (n + S)
     uint32_t* centroidBounds;      // 6 ordered words
+    uint32_t* firstSlot;           // per triangle: its first reference
+    uint32_t* slotTriangle;        // per reference: its triangle
     uint32_t* error;               // device error word
 };
 
@@ -48,22 +53,20 @@ struct SBox {
 
 __device__ __forceinline__ float selMin(float a, float b) { return b < a ? b : a; }
 __device__ __forceinline__ float selMax(float a, float b) { return a < b ? b : a; }
-__device__ __forceinline__ double dSelMax(double a, double b) { return a < b ? b : a; }
 
 struct SplitGrid {
-    double lo[3], ext[3], inv[3];
-    float glo[3], ghi[3];
+    float lo[3], ext[3], inv[3];
+    float ghi[3];
 };
 
 __device__ __forceinline__ SplitGrid loadSplitGrid(const uint32_t* b6) {
     SplitGrid g;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        g.glo[a] = orderedToFloat(b6[a]);
+        g.lo[a] = orderedToFloat(b6[a]);
         g.ghi[a] = orderedToFloat(b6[3 + a]);
-        g.lo[a] = (double)g.glo[a];
-        g.ext[a] = __dsub_rn((double)g.ghi[a], (double)g.glo[a]);
-        g.inv[a] = g.ext[a] > 0.0 ? __ddiv_rn(1024.0, g.ext[a]) : 0.0;
+        g.ext[a] = __fsub_rn(g.ghi[a], g.lo[a]);
+        g.inv[a] = g.ext[a] > 0.0f ? __fdiv_rn(1024.0f, g.ext[a]) : 0.0f;
     }
     return g;
 }
@@ -71,36 +74,40 @@ __device__ __forceinline__ SplitGrid loadSplitGrid(const uint32_t* b6) {
 // Cell of coordinate x on axis a: floor(q), or ceil(q) - 1 for the end of a box
 // (a box ending on a grid line does not reach the next cell), clamped to [0, 1023].
 __device__ __forceinline__ int gridCell(const SplitGrid& g, float x, int a, bool end) {
-    if (g.inv[a] == 0.0) return 0;
-    const double q = __dmul_rn(__dsub_rn((double)x, g.lo[a]), g.inv[a]);
-    const double f = end ? __dsub_rn(ceil(q), 1.0) : floor(q);
-    if (!(f >= 0.0)) return 0;
-    if (f > 1023.0) return 1023;
+    if (g.inv[a] == 0.0f) return 0;
+    const float q = __fmul_rn(__fsub_rn(x, g.lo[a]), g.inv[a]);
+    const float f = end ? __fsub_rn(ceilf(q), 1.0f) : floorf(q);
+    if (!(f >= 0.0f)) return 0;
+    if (f > 1023.0f) return 1023;
     return (int)f;
 }
 
-// First and last cell of box b on axis a, the box narrowed by one float step at each end.
+// First and last cell of box b on axis a, the box narrowed at each end by 2^-18 of its
+// coordinates' magnitude (more than the widening of a crossing).
 __device__ __forceinline__ void gridSpan(const SplitGrid& g, const SBox& b, int a, int* cl, int* ch) {
-    *cl = gridCell(g, nextafterf(b.lo[a], INFINITY), a, false);
-    const int e = gridCell(g, nextafterf(b.hi[a], -INFINITY), a, true);
+    const float d = __fmul_rn(selMax(fabsf(b.lo[a]), fabsf(b.hi[a])), 0x1p-18f);
+    *cl = gridCell(g, __fadd_rn(b.lo[a], d), a, false);
+    const int e = gridCell(g, __fsub_rn(b.hi[a], d), a, true);
     *ch = e > *cl ? e : *cl;
 }
 
 __device__ __forceinline__ int bitLength(uint32_t x) { return 32 - __clz(x); }
 
-// Largest w with w^3 <= N (N <= 2^63): a double estimate, then exact integer steps.
+// Largest w with w^3 <= N (N <= 2^63): a float estimate (within one of the root), then
+// exact integer steps.
 __device__ __forceinline__ uint32_t integerCubeRoot(unsigned long long N) {
-    unsigned long long w = (unsigned long long)cbrt((double)N);
+    unsigned long long w = (unsigned long long)cbrtf((float)N);
     for (int i = 0; i < 4 && w > 0 && w * w * w > N; ++i) --w;
     for (int i = 0; i < 4 && (w + 1) * (w + 1) * (w + 1) <= N; ++i) ++w;
     return (uint32_t)w;
 }
 
-// floor(S X / W) exactly, for 0 < W < 2^63 and X <= W: a double estimate (off by at most
-// one) corrected against the 128-bit product S X.
-__device__ __forceinline__ unsigned long long mulDivFloor(uint32_t S, unsigned long long X, unsigned long long W) {
+// floor(S X / W) exactly, for 0 < W < 2^63 and X <= W, given invW ~ 1 / W: a double
+// estimate (off by at most one) corrected against the 128-bit product S X.
+__device__ __forceinline__ unsigned long long mulDivFloor(uint32_t S, unsigned long long X, unsigned long long W,
+                                                          double invW) {
     const unsigned long long ph = __umul64hi((unsigned long long)S, X), pl = (unsigned long long)S * X;
-    unsigned long long q = (unsigned long long)floor(__ddiv_rn(__dmul_rn((double)S, (double)X), (double)W));
+    unsigned long long q = (unsigned long long)__dmul_rn(__dmul_rn((double)S, (double)X), invW);
     for (int i = 0; i < 4; ++i) {  // q W <= S X
         const unsigned long long h = __umul64hi(q, W), l = q * W;
         if (q > 0 && (h > ph || (h == ph && l > pl)))
@@ -118,17 +125,15 @@ __device__ __forceinline__ unsigned long long mulDivFloor(uint32_t S, unsigned l
     return q;
 }
 
-__device__ __forceinline__ double halfArea(const SBox& b) {
-    const double dx = __dsub_rn((double)b.hi[0], (double)b.lo[0]);
-    const double dy = __dsub_rn((double)b.hi[1], (double)b.lo[1]);
-    const double dz = __dsub_rn((double)b.hi[2], (double)b.lo[2]);
-    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dy), __dmul_rn(dy, dz)), __dmul_rn(dz, dx));
+__device__ __forceinline__ float halfArea(const SBox& b) {
+    const float dx = __fsub_rn(b.hi[0], b.lo[0]), dy = __fsub_rn(b.hi[1], b.lo[1]), dz = __fsub_rn(b.hi[2], b.lo[2]);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx));
 }
 
-__device__ __forceinline__ double longestExtent(const SBox& b) {
-    double w = 0.0;
+__device__ __forceinline__ float longestExtent(const SBox& b) {
+    float w = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) w = dSelMax(w, __dsub_rn((double)b.hi[a], (double)b.lo[a]));
+    for (int a = 0; a < 3; ++a) w = selMax(w, __fsub_rn(b.hi[a], b.lo[a]));
     return w;
 }
 
@@ -148,48 +153,52 @@ __device__ __forceinline__ void splitTriangle(const PrimSource& S, uint32_t t, f
     }
 }
 
-// The cutting plane of box b: the grid line of the highest level strictly inside it
-// (ties: longer extent, then lower axis), else the midpoint of its longest axis.
+// The cutting plane of box b: the grid line of the highest level inside it (ties:
+// longer extent, then lower axis), else the midpoint of its longest axis.
 __device__ __forceinline__ void cutPlane(const SplitGrid& g, const SBox& b, int* axis, float* plane) {
     int best = -1, bestBit = -1, bestJ = 0;
-    double bestExt = -1.0;
+    float bestExt = -1.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         int cl, ch;
         gridSpan(g, b, a, &cl, &ch);
         if (cl == ch) continue;
         const int bit = bitLength((uint32_t)(cl ^ ch)) - 1;
-        const double e = __dsub_rn((double)b.hi[a], (double)b.lo[a]);
+        const float e = __fsub_rn(b.hi[a], b.lo[a]);
         if (bit > bestBit || (bit == bestBit && e > bestExt)) best = a, bestBit = bit, bestExt = e, bestJ = (ch >> bit) << bit;
     }
     if (best >= 0) {
         *axis = best;
-        *plane = __double2float_rn(__dadd_rn(g.lo[best], __dmul_rn((double)bestJ, __dmul_rn(g.ext[best], 1.0 / 1024.0))));
+        *plane = __fadd_rn(g.lo[best], __fmul_rn((float)bestJ, __fmul_rn(g.ext[best], 0x1p-10f)));
         return;
     }
     int a0 = 0;
-    double e0 = __dsub_rn((double)b.hi[0], (double)b.lo[0]);
+    float e0 = __fsub_rn(b.hi[0], b.lo[0]);
 #pragma unroll
     for (int a = 1; a < 3; ++a) {
-        const double e = __dsub_rn((double)b.hi[a], (double)b.lo[a]);
+        const float e = __fsub_rn(b.hi[a], b.lo[a]);
         if (e > e0) a0 = a, e0 = e;
     }
     *axis = a0;
-    *plane = __double2float_rn(__dmul_rn(0.5, __dadd_rn((double)b.lo[a0], (double)b.hi[a0])));
+    *plane = __fmul_rn(0.5f, __fadd_rn(b.lo[a0], b.hi[a0]));
 }
 
-// Box of the triangle's part on one side of x_axis = P (vertices on that side, edge
-// crossings widened by 2^-47 of the endpoint magnitude and rounded outward), within b.
-__device__ __forceinline__ SBox clipSide(const float v[3][3], int axis, float P, bool left, const SBox& b) {
-    SBox r;
+// Boxes of the triangle's parts on the two sides of x_axis = P, each within b: the
+// vertices on that side (<= / >=), then the edge crossings, computed once for both sides
+// and widened by pad = 2^-19 of the endpoints' magnitude (+ 2^-140): the float rounding
+// of a crossing stays below 12 units in the last place of that magnitude, so the
+// widened interval holds the exact crossing.
+__device__ __forceinline__ void clipBoth(const float v[3][3], int axis, float P, const SBox& b, SBox* L, SBox* R) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) r.lo[c] = INFINITY, r.hi[c] = -INFINITY;
+    for (int c = 0; c < 3; ++c) L->lo[c] = R->lo[c] = INFINITY, L->hi[c] = R->hi[c] = -INFINITY;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const bool in = left ? v[i][axis] <= P : v[i][axis] >= P;
-        if (!in) continue;
+        const bool l = v[i][axis] <= P, r = v[i][axis] >= P;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) r.lo[c] = selMin(r.lo[c], v[i][c]), r.hi[c] = selMax(r.hi[c], v[i][c]);
+        for (int c = 0; c < 3; ++c) {
+            if (l) L->lo[c] = selMin(L->lo[c], v[i][c]), L->hi[c] = selMax(L->hi[c], v[i][c]);
+            if (r) R->lo[c] = selMin(R->lo[c], v[i][c]), R->hi[c] = selMax(R->hi[c], v[i][c]);
+        }
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -197,22 +206,52 @@ __device__ __forceinline__ SBox clipSide(const float v[3][3], int axis, float P,
         const float* e = v[i == 2 ? 0 : i + 1];
         const bool crosses = (a[axis] < P && e[axis] > P) || (a[axis] > P && e[axis] < P);
         if (!crosses) continue;
-        const double t = __ddiv_rn(__dsub_rn((double)P, (double)a[axis]), __dsub_rn((double)e[axis], (double)a[axis]));
+        const float t = __fdiv_rn(__fsub_rn(P, a[axis]), __fsub_rn(e[axis], a[axis]));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            if (c == axis) {
-                r.lo[c] = selMin(r.lo[c], P), r.hi[c] = selMax(r.hi[c], P);
-                continue;
+            float lo = P, hi = P;
+            if (c != axis) {
+                const float q = __fadd_rn(a[c], __fmul_rn(__fsub_rn(e[c], a[c]), t));
+                const float pad = __fadd_rn(__fmul_rn(selMax(fabsf(a[c]), fabsf(e[c])), 0x1p-19f), 0x1p-140f);
+                lo = __fsub_rn(q, pad);
+                hi = __fadd_rn(q, pad);
             }
-            const double q = __dadd_rn((double)a[c], __dmul_rn(__dsub_rn((double)e[c], (double)a[c]), t));
-            const double pad = __dmul_rn(dSelMax(fabs((double)a[c]), fabs((double)e[c])), 0x1p-47);
-            r.lo[c] = selMin(r.lo[c], __double2float_rd(__dsub_rn(q, pad)));
-            r.hi[c] = selMax(r.hi[c], __double2float_ru(__dadd_rn(q, pad)));
+            L->lo[c] = selMin(L->lo[c], lo), L->hi[c] = selMax(L->hi[c], hi);
+            R->lo[c] = selMin(R->lo[c], lo), R->hi[c] = selMax(R->hi[c], hi);
         }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) r.lo[c] = selMax(r.lo[c], b.lo[c]), r.hi[c] = selMin(r.hi[c], b.hi[c]);
-    return r;
+    for (int c = 0; c < 3; ++c) {
+        L->lo[c] = selMax(L->lo[c], b.lo[c]), L->hi[c] = selMin(L->hi[c], b.hi[c]);
+        R->lo[c] = selMax(R->lo[c], b.lo[c]), R->hi[c] = selMin(R->hi[c], b.hi[c]);
+    }
+}
+
+// One cut of box `cur` (s >= 1 splits left): the two sides' boxes and the left side's
+// share sL of the s - 1 splits that remain.
+__device__ __forceinline__ void cutOnce(const SplitGrid& g, const float v[3][3], const SBox& cur, int s, SBox* L,
+                                        SBox* R, int* sL) {
+    int axis;
+    float plane;
+    cutPlane(g, cur, &axis, &plane);
+    clipBoth(v, axis, plane, cur, L, R);
+    const int rest = s - 1;
+    const bool eL = boxEmpty(*L), eR = boxEmpty(*R);
+    if (eL && eR) {
+        *L = *R = cur;
+        *sL = 0;
+    } else if (eL) {
+        *L = *R;
+        *sL = 0;
+    } else if (eR) {
+        *R = *L;
+        *sL = rest;
+    } else {
+        const float wL = longestExtent(*L), wR = longestExtent(*R);
+        const float sum = __fadd_rn(wL, wR);
+        int k = sum > 0.0f ? (int)floorf(__fadd_rn(__fdiv_rn(__fmul_rn((float)rest, wL), sum), 0.5f)) : rest / 2;
+        *sL = k < rest ? k : rest;
+    }
 }
 
 // ----------------------------------------------------------------------- kernels
@@ -266,23 +305,20 @@ __global__ void __launch_bounds__(kSplitThreads) splitWeightKernel(SplitParams P
             const int L = bitLength((uint32_t)(cl ^ ch));
             level = L > level ? L : level;
         }
-        double e1[3], e2[3];
+        float e1[3], e2[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            e1[a] = __dsub_rn((double)v[1][a], (double)v[0][a]);
-            e2[a] = __dsub_rn((double)v[2][a], (double)v[0][a]);
-        }
-        const double cx = __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1]));
-        const double cy = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
-        const double cz = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
-        const double tri = __dmul_rn(0.5, __dadd_rn(__dadd_rn(fabs(cx), fabs(cy)), fabs(cz)));
-        double excess = __dsub_rn(halfArea(b), tri);
-        if (!(excess > 0.0)) excess = 0.0;
+        for (int a = 0; a < 3; ++a) e1[a] = __fsub_rn(v[1][a], v[0][a]), e2[a] = __fsub_rn(v[2][a], v[0][a]);
+        const float cx = __fsub_rn(__fmul_rn(e1[1], e2[2]), __fmul_rn(e1[2], e2[1]));
+        const float cy = __fsub_rn(__fmul_rn(e1[2], e2[0]), __fmul_rn(e1[0], e2[2]));
+        const float cz = __fsub_rn(__fmul_rn(e1[0], e2[1]), __fmul_rn(e1[1], e2[0]));
+        const float tri = __fmul_rn(0.5f, __fadd_rn(__fadd_rn(fabsf(cx), fabsf(cy)), fabsf(cz)));
+        float excess = __fsub_rn(halfArea(b), tri);
+        if (!(excess > 0.0f)) excess = 0.0f;
         SBox G;
-        for (int a = 0; a < 3; ++a) G.lo[a] = g.glo[a], G.hi[a] = g.ghi[a];
-        const double areaG = halfArea(G);
-        const double r = areaG > 0.0 ? __dmul_rn(__ddiv_rn(excess, areaG), (double)(1u << level)) : 0.0;
-        w = integerCubeRoot((unsigned long long)__dmul_rn(r, 9007199254740992.0));  // r 2^53
+        for (int a = 0; a < 3; ++a) G.lo[a] = g.lo[a], G.hi[a] = g.ghi[a];
+        const float areaG = halfArea(G);
+        const float r = areaG > 0.0f ? __fmul_rn(__fdiv_rn(excess, areaG), (float)(1u << level)) : 0.0f;
+        w = integerCubeRoot((unsigned long long)__fmul_rn(r, 0x1p53f));  // r 2^53 <= 2^63
         P.counts[t] = w;
     }
     unsigned long long total;
@@ -331,6 +367,8 @@ __device__ __forceinline__ void scanBlockSums(T* v, uint32_t count, unsigned lon
 
 __global__ void __launch_bounds__(kSplitScanThreads) splitScanWeightsKernel(SplitParams P) {
     scanBlockSums<unsigned long long>(P.weightSums, P.blocks, P.totals);
+    if (threadIdx.x == 0 && P.totals[0])  // 1 / W for the estimates of the shares
+        reinterpret_cast<double*>(P.totals)[2] = __ddiv_rn(1.0, (double)P.totals[0]);
 }
 
 // Triangle t's splits by priority: its share of the budget between the running weight
@@ -345,7 +383,8 @@ __global__ void __launch_bounds__(kSplitThreads) splitCountKernel(SplitParams P)
         const unsigned long long W = P.totals[0];
         if (W) {
             const unsigned long long C = P.weightSums[blockIdx.x] + local;
-            const unsigned long long q = mulDivFloor(P.budget, C + w, W) - mulDivFloor(P.budget, C, W);
+            const double invW = reinterpret_cast<const double*>(P.totals)[2];
+            const unsigned long long q = mulDivFloor(P.budget, C + w, W, invW) - mulDivFloor(P.budget, C, W, invW);
             s = (uint32_t)(q < (unsigned long long)kSplitMax ? q : (unsigned long long)kSplitMax);
         }
         P.counts[t] = s;
@@ -363,80 +402,71 @@ __global__ void __launch_bounds__(kSplitScanThreads) splitScanKernel(SplitParams
     scanBlockSums<uint32_t>(P.blockSums, P.blocks, nullptr);
 }
 
-__device__ __forceinline__ void emitRef(const SplitParams& P, uint32_t slot, const SBox& b, uint32_t t, bool owner,
-                                        float mn[3], float mx[3]) {
-    if (slot >= P.n + P.budget) {  // cannot happen: the shares add up to at most the budget
-        latchError(P.error, GRT_ERROR_INTERNAL);
-        return;
-    }
-    P.refs[2 * (size_t)slot] = make_float4(b.lo[0], b.lo[1], b.lo[2], __uint_as_float(t));
-    P.refs[2 * (size_t)slot + 1] = make_float4(b.hi[0], b.hi[1], b.hi[2], __uint_as_float(owner ? 1u : 0u));
-    Box3 bb;
-    bb.lo = make_float3(b.lo[0], b.lo[1], b.lo[2]);
-    bb.hi = make_float3(b.hi[0], b.hi[1], b.hi[2]);
-    const float3 c = boxCentroid(bb);
-    P.centroids[slot] = make_float4(c.x, c.y, c.z, 0.f);
-    mn[0] = fminf(mn[0], c.x), mn[1] = fminf(mn[1], c.y), mn[2] = fminf(mn[2], c.z);
-    mx[0] = fmaxf(mx[0], c.x), mx[1] = fmaxf(mx[1], c.y), mx[2] = fmaxf(mx[2], c.z);
-}
-
-__global__ void __launch_bounds__(kSplitThreads) splitEmitKernel(SplitParams P) {
+// Each triangle's reference slots: its first slot (the running sum of the references
+// before it) and its final split count; the slots it owns are marked with its index.
+__global__ void __launch_bounds__(kSplitThreads) splitSlotsKernel(SplitParams P) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t mine = t < P.n ? P.counts[t] : 0u;
     uint32_t blockTotal;
     const uint32_t local = blockExclusive<uint32_t>(mine, &blockTotal);
+    if (t >= P.n) return;
+    const unsigned long long given = P.totals[1];
+    const unsigned long long left = given < P.budget ? (unsigned long long)P.budget - given : 0ull;
+    const uint32_t extra = (unsigned long long)t < left ? 1u : 0u;
+    const uint32_t first = t + P.blockSums[blockIdx.x] + local + (uint32_t)((unsigned long long)t < left ? t : left);
+    const uint32_t s = min(mine + extra, (uint32_t)kSplitMax + 1u);
+    P.counts[t] = s;
+    P.firstSlot[t] = first;
+    const uint32_t m = P.n + P.budget;
+    for (uint32_t j = 0; j <= s; ++j) {
+        if (first + j >= m) {  // cannot happen: the shares add up to at most the budget
+            latchError(P.error, GRT_ERROR_INTERNAL);
+            break;
+        }
+        P.slotTriangle[first + j] = t;
+    }
+}
+
+// Reference r (one thread each): the k-th leaf, left first, of its triangle's cut tree,
+// found by walking down from the triangle's box and cutting only the boxes on its path
+// (each cut as the depth-first order makes it); its box, triangle, owner flag and centroid.
+__global__ void __launch_bounds__(kSplitThreads) splitEmitKernel(SplitParams P) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    if (t < P.n) {
-        const unsigned long long given = P.totals[1];
-        const unsigned long long left = given < P.budget ? (unsigned long long)P.budget - given : 0ull;
-        const uint32_t extra = (unsigned long long)t < left ? 1u : 0u;
-        uint32_t slot = t + P.blockSums[blockIdx.x] + local + (uint32_t)((unsigned long long)t < left ? t : left);
-        const SplitGrid g = loadSplitGrid(P.sceneBounds);
-        float v[3][3];
-        SBox cur;
-        splitTriangle(P.src, t, v, &cur);
-        int s = (int)min(mine + extra, (uint32_t)kSplitMax + 1u);  // keeps the pending stack in bounds
-        SBox pendBox[kSplitStack];
-        int pendS[kSplitStack];
-        int sp = 0;
-        bool owner = true;
-        for (;;) {
-            if (s == 0) {
-                emitRef(P, slot++, cur, t, owner, mn, mx);
-                owner = false;
-                if (sp == 0) break;
-                --sp;
-                cur = pendBox[sp];
-                s = pendS[sp];
-                continue;
+    if (r < P.n + P.budget) {
+        const uint32_t t = P.slotTriangle[r];
+        uint32_t k = t < P.n ? r - P.firstSlot[t] : 0xFFFFFFFFu;
+        int s = t < P.n ? (int)P.counts[t] : 0;
+        if (t >= P.n || k > (uint32_t)s) {
+            latchError(P.error, GRT_ERROR_INTERNAL);
+        } else {
+            const SplitGrid g = loadSplitGrid(P.sceneBounds);
+            float v[3][3];
+            SBox cur;
+            splitTriangle(P.src, t, v, &cur);
+            const bool owner = k == 0;
+            while (s > 0) {
+                SBox L, R;
+                int sL;
+                cutOnce(g, v, cur, s, &L, &R, &sL);
+                if (k <= (uint32_t)sL) {
+                    cur = L;
+                    s = sL;
+                } else {
+                    cur = R;
+                    k -= (uint32_t)sL + 1u;
+                    s = s - 1 - sL;
+                }
             }
-            int axis;
-            float plane;
-            cutPlane(g, cur, &axis, &plane);
-            SBox L = clipSide(v, axis, plane, true, cur), R = clipSide(v, axis, plane, false, cur);
-            const int rest = s - 1;
-            int sL;
-            const bool eL = boxEmpty(L), eR = boxEmpty(R);
-            if (eL && eR) {
-                L = R = cur;
-                sL = 0;
-            } else if (eL) {
-                L = R;
-                sL = 0;
-            } else if (eR) {
-                R = L;
-                sL = rest;
-            } else {
-                const double wL = longestExtent(L), wR = longestExtent(R);
-                const double sum = __dadd_rn(wL, wR);
-                sL = sum > 0.0 ? (int)floor(__dadd_rn(__ddiv_rn(__dmul_rn((double)rest, wL), sum), 0.5)) : rest / 2;
-                sL = sL < rest ? sL : rest;
-            }
-            pendBox[sp] = R;  // s strictly decreases down every path, so sp stays below kSplitStack
-            pendS[sp] = rest - sL;
-            ++sp;
-            cur = L;
-            s = sL;
+            P.refs[2 * (size_t)r] = make_float4(cur.lo[0], cur.lo[1], cur.lo[2], __uint_as_float(t));
+            P.refs[2 * (size_t)r + 1] = make_float4(cur.hi[0], cur.hi[1], cur.hi[2], __uint_as_float(owner ? 1u : 0u));
+            Box3 bb;
+            bb.lo = make_float3(cur.lo[0], cur.lo[1], cur.lo[2]);
+            bb.hi = make_float3(cur.hi[0], cur.hi[1], cur.hi[2]);
+            const float3 c = boxCentroid(bb);
+            P.centroids[r] = make_float4(c.x, c.y, c.z, 0.f);
+            mn[0] = c.x, mn[1] = c.y, mn[2] = c.z;
+            mx[0] = c.x, mx[1] = c.y, mx[2] = c.z;
         }
     }
     reduceBoxBounds(mn, mx, P.centroidBounds);
