@@ -82,6 +82,8 @@ def parse():
                    help="batched workload: skip the second run with subtree-clustered builds")
     p.add_argument("--no-quantized", action="store_true",
                    help="batched workload: skip the run with quantised 64-byte nodes")
+    p.add_argument("--no-split", action="store_true",
+                   help="batched workload: skip the per-scene run with split triangles")
     return p.parse_args()
 
 
@@ -467,7 +469,9 @@ def run_grt(args, rank, world, local):
                         ("high_quality_ploc32", grt.GRT_BUILD_PREFER_HIGH_QUALITY),
                         ("subtree_cluster16", grt.GRT_BUILD_CLUSTER_SUBTREES),
                         ("fast_lbvh_quantized_nodes", grt.GRT_BUILD_PREFER_FAST | grt.GRT_BUILD_QUANTIZED_NODES),
-                        ("fast_lbvh_wide8_nodes", grt.GRT_BUILD_PREFER_FAST | grt.GRT_BUILD_WIDE8_NODES)):
+                        ("fast_lbvh_wide8_nodes", grt.GRT_BUILD_PREFER_FAST | grt.GRT_BUILD_WIDE8_NODES),
+                        ("fast_lbvh_wide8_split_triangles", grt.GRT_BUILD_PREFER_FAST | grt.GRT_BUILD_WIDE8_NODES |
+                         grt.GRT_BUILD_SPLIT_TRIANGLES)):
         gq = Geometry(ctx, vertices=verts, indices=idx, build_flags=flags).build(sh)
         sq = Scene(ctx, [gq.handle] * WORKLOAD["instances"], frames,
                    build_flags=flags & grt.GRT_BUILD_WIDE8_NODES).build(sh)
@@ -1499,6 +1503,46 @@ def run_batched(args, rank, world, local):
             g.close()
         del hits_q
 
+    # spatial splits (GRT_BUILD_SPLIT_TRIANGLES, one extra reference per triangle): the
+    # batched launch has no splitting phases, so the per-scene path is timed, against the
+    # per-scene linear BVH above; hit records compared (triangle IDs), mean surface-area cost
+    split = None
+    if not args.no_split:
+        sopt = grt.build_options(flags=grt.GRT_BUILD_SPLIT_TRIANGLES, split_factor=1.0)
+        stemp = empty_bytes(grt.grtGetGeometryBuildTemporaryBufferSize(
+            ctx.handle, grt.triangle_mesh_input(256, 256, triangle_count=nbig, vertex_count=3 * nbig), sopt))
+        geo_p, hits_p = [], []
+        for (dv, di), r in zip(meshes, rays):
+            geo_p.append(Geometry(ctx, vertices=dv, indices=di, temp=stemp, build_flags=grt.GRT_BUILD_SPLIT_TRIANGLES,
+                                  split_factor=1.0))
+            hits_p.append(new_hits(r.shape[0]))
+
+        def sequential_split():
+            for g, r, h in zip(geo_p, rays, hits_p):
+                g.build(sh)
+                grt.grtTraceClosest(ctx.handle, None, g.handle, r, r.shape[0], h, None, None, sh)
+
+        p_ms, p_launches = timed(sequential_split)
+        build_only, _ = timed(lambda: [g.build(sh) for g in geo_p])
+        lbvh_build, _ = timed(lambda: [g.build(sh) for g in geo_s])
+        torch.cuda.synchronize()
+        assert grt.grtGetLastDeviceError(ctx.handle, sh) == grt.GRT_SUCCESS
+        pms, pb, lb = max_over_ranks([statistics.mean(p_ms), statistics.mean(build_only), statistics.mean(lbvh_build)],
+                                     dist)
+        same = sum(int((a[:, 1] == b[:, 1]).sum().item()) for a, b in zip(hits_p, hits_s))
+        split = {"build_flag": "GRT_BUILD_SPLIT_TRIANGLES", "split_factor": 1.0, "path": "per-scene",
+                 "sequential_ms": round(pms, 3),
+                 "sequential_lbvh_ms": None if math.isnan(seq_ms) else round(seq_ms, 3),
+                 "builds_ms": round(pb, 3), "lbvh_builds_ms": round(lb, 3),
+                 "traces_ms": round(pms - pb, 3),
+                 "lbvh_traces_ms": None if math.isnan(seq_ms) else round(seq_ms - lb, 3),
+                 "sah_cost_mean": round(statistics.mean(sah_cost(g) for g in geo_p), 3),
+                 "lbvh_sah_cost_mean": round(statistics.mean(sah_cost(g) for g in geo_s), 3),
+                 "primitive_ids_equal": same, "records": int(total_rays), "gpu_launches": int(p_launches)}
+        for g in geo_p:
+            g.close()
+        del stemp, hits_p
+
     # end to end: meshes and rays up from pinned host memory, hit records back
     pin = [(torch.from_numpy(v).pin_memory(), torch.from_numpy(i.view(np.int32)).pin_memory(), r.cpu().pin_memory())
            for (v, i, _, _), r in zip(host, rays)]
@@ -1538,6 +1582,7 @@ def run_batched(args, rank, world, local):
             "autotune": None if tune_report is None else {k: tune_report[k] for k in tune_report if k != "tried"},
             "clustered": clustered,
             "quantized_nodes": quantized,
+            "split_triangles": split,
             "roofline": roofline,
             "e2e": {"value": round(statistics.mean(e2e), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
