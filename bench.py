@@ -1431,6 +1431,14 @@ def run_batched(args, rank, world, local):
     build_bytes = sum(build_bytes_per_prim(b) * m[1].shape[0] for b, m in zip(bits, meshes))
     nbytes = trace_bytes + build_bytes
     roofline = roofline_entry("batchKernel", nbytes, batched_ms)
+    if len(soups) != BATCHED["scenes"]:
+        # the record holds the full launch's bytes (scaled from a 16-soup capture): a smaller
+        # case reports the captured 16-soup bytes where they are its own, else nothing
+        t = (ncu_record("batchKernel") or {}).get("captured_dram_bytes") if len(soups) == 16 else None
+        roofline["traffic"] = t
+        roofline.pop("dram_share_of_algorithmic", None)
+        if t:
+            roofline["dram_share_of_algorithmic"] = round(t / nbytes, 4)
     roofline.update({"build_bytes": int(build_bytes), "trace_bytes": int(trace_bytes),
                      "per_ray": {"nodes": round(st["nodesVisited"] / max(1, st["rays"]), 2),
                                  "triangles": round(st["trianglesTested"] / max(1, st["rays"]), 2)}})
