@@ -184,7 +184,9 @@ typedef enum grtBuildFlags {
  * before the build as in Karras and Aila (HPG 2013): a triangle may be referenced by
  * several leaves, each bounding the part of it on one side of a set of cutting planes.
  * S = floor(splitFactor * triangleCount) extra references (splitFactor in [0, 1],
- * 0 = 0.5) are shared out by priority; the build then runs over exactly
+ * 0 = 0.5; triangleCount + S must stay below 2^31) are shared out by priority; a
+ * grtBuildGeometry given options must repeat the creation's bit and factor (0 and 0.5
+ * are the same factor). The build then runs over exactly
  * triangleCount + S leaves (grtBvhInfo.leafCount). In this order, in float32 rounded to
  * nearest (the integer steps exact):
  *   box B_t of triangle t's vertices; G = union of all B_t; per axis a grid of 1024 cells
@@ -744,7 +746,9 @@ grtError grtGetBvhInfo(grtContext ctx, grtGeometry geom, grtScene scene, grtBvhI
 
 /* Offsets (bytes) inside the build temporary buffer where, after a geometry build
  * of `count` primitives, the sorted Morton keys (uint32 for 30-bit, uint64 for
- * 63-bit) and the sorted primitive indices (uint32) are left. */
+ * 63-bit) and the sorted primitive indices (uint32) are left. For a build with split
+ * triangles, count is the leaf count (grtBvhInfo.leafCount) and the indices are those of
+ * the references (numbered triangle by triangle). */
 grtError grtGetBuildTemporaryLayout(uint32_t count, uint32_t mortonBits, size_t* sortedKeysOffset,
                                     size_t* sortedValuesOffset, size_t* centroidBoundsOffset);
 

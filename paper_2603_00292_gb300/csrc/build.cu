@@ -740,11 +740,21 @@ static bool validSplit(const grtBuildOptions* opt, uint32_t primType) {
     if (!splitFlag(opt)) return true;
     return primType == GRT_PRIMITIVE_TRIANGLE_MESH && opt->splitFactor >= 0.f && opt->splitFactor <= 1.f;
 }
-// Extra references of a split build of n triangles: floor(factor * n).
+// The split factor of a split build (0 selects 0.5), and its extra references for n
+// triangles: floor(factor * n).
+static double splitFactorOf(const grtBuildOptions* opt) {
+    return opt->splitFactor == 0.f ? 0.5 : (double)opt->splitFactor;
+}
 static uint32_t splitBudgetOf(uint32_t n, const grtBuildOptions* opt) {
     if (!splitFlag(opt)) return 0;
-    const double f = opt->splitFactor == 0.f ? 0.5 : (double)opt->splitFactor;
-    return (uint32_t)std::floor(f * (double)n);
+    return (uint32_t)std::floor(splitFactorOf(opt) * (double)n);
+}
+// Leaf count of a build: the primitives plus the split references; false past 2^31 - 2.
+static bool leafCountOf(uint32_t n, const grtBuildOptions* opt, uint32_t* m) {
+    const uint64_t total = (uint64_t)n + splitBudgetOf(n, opt);
+    if (total >= 0x7FFFFFFFull) return false;
+    *m = (uint32_t)total;
+    return true;
 }
 
 static std::mutex g_methodLock;
@@ -1097,8 +1107,9 @@ grtError grtGetGeometryBuildTemporaryBufferSize(grtContext ctx, const grtGeometr
     if (!ctx || !sizeBytes) return GRT_ERROR_INVALID_PARAMETER;
     grtError e = validateGeometryInput(input, &n);
     if (e != GRT_SUCCESS) return e;
-    if (!validBuildFlags(options) || !validSplit(options, input->type)) return GRT_ERROR_INVALID_PARAMETER;
-    const uint32_t m = n + splitBudgetOf(n, options);
+    uint32_t m = 0;
+    if (!validBuildFlags(options) || !validSplit(options, input->type) || !leafCountOf(n, options, &m))
+        return GRT_ERROR_INVALID_PARAMETER;
     const BuildLayout L = buildLayout(m, resolveMortonBits(m, options), false);
     const size_t bytes = methodTempBytes(L, m, clusterRadius(options));
     *sizeBytes = splitFlag(options) ? splitLayout(bytes, n, m).total : bytes;
@@ -1111,15 +1122,16 @@ grtError grtCreateGeometry(grtContext ctx, const grtGeometryBuildInput* input, c
     if (!ctx || !out) return GRT_ERROR_INVALID_PARAMETER;
     grtError e = validateGeometryInput(input, &n);
     if (e != GRT_SUCCESS) return e;
-    if (!validBuildFlags(options) || !validSplit(options, input->type)) return GRT_ERROR_INVALID_PARAMETER;
-    const uint32_t m = n + splitBudgetOf(n, options);
+    uint32_t m = 0;
+    if (!validBuildFlags(options) || !validSplit(options, input->type) || !leafCountOf(n, options, &m))
+        return GRT_ERROR_INVALID_PARAMETER;
     if (clusterRadius(options) && m > kPlocIndex) return GRT_ERROR_INVALID_PARAMETER;
     BvhObject* o = nullptr;
     e = createBvhObject(n, input->type, input->geomType, resolveMortonBits(m, options), &o, quantFlag(options),
                         wide8Flag(options), m);
     if (e != GRT_SUCCESS) return e;
     o->split = splitFlag(options);
-    o->splitFactor = o->split ? options->splitFactor : 0.f;
+    o->splitFactor = o->split ? (float)splitFactorOf(options) : 0.f;
     o->splitBudget = m - n;
     if (clusterRadius(options)) {
         // the finishing block's shared memory is above the default limit
@@ -1153,7 +1165,7 @@ grtError grtBuildGeometry(grtContext ctx, uint32_t op, const grtGeometryBuildInp
     if (n > 0 && (!temp || ((uintptr_t)temp & 15))) return GRT_ERROR_INVALID_PARAMETER;
     if (options && options->mortonBits && resolveMortonBits(o->leafCount, options) != o->mortonBits)
         return GRT_ERROR_INVALID_PARAMETER;
-    if (options && (splitFlag(options) != o->split || (o->split && options->splitFactor != o->splitFactor)))
+    if (options && (splitFlag(options) != o->split || (o->split && (float)splitFactorOf(options) != o->splitFactor)))
         return GRT_ERROR_INVALID_PARAMETER;
     const uint32_t radius = radiusOf(o);
     if (!validBuildFlags(options) || (options && clusterRadius(options) != radius)) return GRT_ERROR_INVALID_PARAMETER;

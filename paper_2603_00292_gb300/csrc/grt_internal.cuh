@@ -141,7 +141,7 @@ struct BvhObject {
     bool quant;  // built with GRT_BUILD_QUANTIZED_NODES (qnodes allocated when primCount > 0)
     bool wide8;  // built with GRT_BUILD_WIDE8_NODES (w8nodes allocated when primCount > 0)
     bool split;  // built with GRT_BUILD_SPLIT_TRIANGLES
-    float splitFactor;     // as given at creation (0 = the default)
+    float splitFactor;     // the creation's factor (0 resolved to 0.5)
     uint32_t splitBudget;  // extra references: floor(factor * primCount)
 };
 BvhObject* findBvh(const void* handle);

@@ -228,6 +228,9 @@ def test_split_rejections(gpu):
     for opts in (grt.build_options(), grt.build_options(flags=SPLIT, split_factor=0.25)):  # must repeat the creation's
         with pytest.raises(grt.GrtError):
             grt.grtBuildGeometry(gpu.handle, grt.GRT_BUILD_OPERATION_BUILD, g.input, opts, g.temp, None, g.handle)
+    # the factor 0 of the creation is 0.5: naming it explicitly is the same build
+    grt.grtBuildGeometry(gpu.handle, grt.GRT_BUILD_OPERATION_BUILD, g.input, grt.build_options(flags=SPLIT, split_factor=0.5),
+                         g.temp, None, g.handle)
     rays = device_tensor(scenegen.random_rays(64, [-1] * 3, [1] * 3, config=96))
     with pytest.raises(grt.GrtError) as e:  # each triangle would be met once per reference
         grt.grtTraceAllHits(gpu.handle, None, g.handle, rays, 64, new_hits(64 * 4), 4,
