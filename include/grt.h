@@ -216,8 +216,9 @@ typedef enum grtBuildFlags {
  * split geometry (GRT_ERROR_INVALID_PARAMETER: on the host for grtTraceAllHits on the
  * geometry itself, latched for grtGetLastDeviceError for instances of it), and an
  * intersection filter may be called more than once for one primitive. UPDATE of a
- * split geometry and batched launches that include one are GRT_ERROR_INVALID_PARAMETER;
- * a BUILD from new vertex data re-splits. */
+ * split geometry is GRT_ERROR_INVALID_PARAMETER; a BUILD from new vertex data re-splits.
+ * The batched launch splits such geometries in seven phases of its own before their
+ * build (never by one block) and leaves them as grtBuildGeometry does. */
 
 typedef struct grtBuildOptions {
     uint32_t buildFlags; /* grtBuildFlags */

@@ -21,6 +21,11 @@
 // A scene whose geometry was created with GRT_BUILD_CLUSTER_SUBTREES (any size) has its
 // emission write the LBVH topology to scratch, then one more phase, the bottom-up
 // clustering walk over leaf chunks (cluster.cuh), before the fit; its trace is 4 + 3P.
+// A scene whose geometry has split triangles (GRT_BUILD_SPLIT_TRIANGLES) first runs
+// kSplitPhases splitting phases (split.cuh): the scene box, the weights, their scan (one
+// item), the shares, their scan (one item), the slots, then the references over chunks
+// of references; its prep and every later phase then run over the references, numbered
+// from kSplitPhases on. Such a scene is never built by one block.
 // A scene whose geometry has quantised or 8-wide nodes (GRT_BUILD_QUANTIZED_NODES,
 // GRT_BUILD_WIDE8_NODES) has one more phase after the fit, writing them over node
 // chunks, before its trace; a scene built by one block writes them at the end of that
@@ -44,11 +49,13 @@
 
 #include "cluster.cuh"
 #include "lbvh_block.cuh"
+#include "split.cuh"
 #include "traverse.cuh"
 
 namespace grt {
 
-constexpr uint32_t kBatchPhases = 32;
+constexpr uint32_t kBatchPhases = 40;
+constexpr uint32_t kSplitPhases = 7;  // phases before prep of a scene with split triangles
 constexpr uint32_t kBatchWaitSpins = 1u << 25;  // a wait polls at most this many times
 
 // A scene of the batch: its build (BlockBuild) plus its rays and the trace phase.
@@ -59,6 +66,9 @@ struct BatchSceneDev : BlockBuild {
     uint32_t cluster;     // built by subtree clustering
     uint32_t quant;       // quantised 4-wide nodes written after the fit (one more phase)
     uint32_t wide8;       // 8-wide nodes written after the fit (the same added phase)
+    uint32_t splitPhases; // kSplitPhases for a geometry with split triangles, else 0
+    uint32_t splitChunks; // chunks of its triangles in the splitting phases
+    SplitParams split;    // its splitting (split.cuh): triangles, budget, scratch
     const float4* rayBuf;
     uint32_t* hitBuf;
     // subtree clustering scratch (cluster.cuh)
@@ -206,6 +216,26 @@ __device__ __noinline__ void traceChunk(const BatchParams& B, const BatchSceneDe
     for (uint32_t r = base + threadIdx.x; r < base + n; r += blockDim.x) refineHit(P, r);
 }
 
+// ------------------------------------------------------------------ splitting phases
+// Phase `phase` (< kSplitPhases) of a scene with split triangles, over chunk `chunk` of
+// its triangles (of its references in the last phase); the two scans are one item each.
+__device__ __noinline__ void splitPhase(const BatchParams& B, const BatchSceneDev& S, uint32_t phase, uint32_t chunk) {
+    const SplitParams& P = S.split;
+    const uint32_t b0 = chunk * B.buildChunk, b1 = min(P.n, b0 + B.buildChunk);
+    switch (phase) {
+        case 0: splitBoundsRange(P, b0, b1); break;
+        case 1: splitWeightRange(P, chunk, b0, b1); break;
+        case 2: splitScanWeights(P, S.splitChunks); break;
+        case 3: splitCountRange(P, chunk, b0, b1); break;
+        case 4: scanBlockSums<uint32_t>(P.blockSums, S.splitChunks, nullptr); break;
+        case 5: splitSlotsRange(P, chunk, b0, b1); break;
+        default: {
+            const uint32_t m = P.n + P.budget;
+            splitEmitRange<false>(P, b0, min(m, b0 + B.buildChunk));  // the prep phase takes the centroids
+        }
+    }
+}
+
 // ------------------------------------------------------------------ the persistent kernel
 __global__ void batchInitKernel(BatchParams B) {
     const size_t doneWords = (size_t)B.sceneCount * kBatchPhases;
@@ -217,6 +247,12 @@ __global__ void batchInitKernel(BatchParams B) {
             uint32_t* b = B.scenes[i].bounds;
             b[0] = b[1] = b[2] = 0xFFFFFFFFu;  // running minima start at the top
             b[3] = b[4] = b[5] = 0u;           // running maxima at the bottom
+            if (B.scenes[i].splitPhases) {     // the splitting's scene box and totals
+                const SplitParams& q = B.scenes[i].split;
+                q.sceneBounds[0] = q.sceneBounds[1] = q.sceneBounds[2] = 0xFFFFFFFFu;
+                q.sceneBounds[3] = q.sceneBounds[4] = q.sceneBounds[5] = 0u;
+                q.totals[0] = q.totals[1] = 0ull;
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *B.head = 0ull, *B.abort = 0u;
@@ -242,6 +278,7 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
         }
         __syncthreads();
         const bool wide = S.bits != 30;
+        const uint32_t ph = it.phase - S.splitPhases;  // the phase among the build's own (after the splitting)
         if (skipS) {
             // aborted launch: the item only counts as done
         } else if (S.small) {
@@ -253,11 +290,13 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
             } else {
                 traceChunk(B, S, it.chunk, item, smem);
             }
-        } else if (it.phase == 0) {
+        } else if (it.phase < S.splitPhases) {
+            splitPhase(B, S, it.phase, it.chunk);
+        } else if (ph == 0) {
             const uint32_t b0 = it.chunk * B.buildChunk;
             prepRange(S, b0, min(S.n, b0 + B.buildChunk));
-        } else if (it.phase <= 3 * S.passes) {
-            const uint32_t p = (it.phase - 1) / 3, step = (it.phase - 1) % 3;
+        } else if (ph <= 3 * S.passes) {
+            const uint32_t p = (ph - 1) / 3, step = (ph - 1) % 3;
             if (step == 0) {
                 if (wide)
                     sortUpsweepChunk<unsigned long long, 21>(S, it.chunk, p, B.sortChunkKeys, smem);
@@ -270,7 +309,7 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
             } else {
                 sortDownsweepChunk<uint32_t>(S, it.chunk, p, B.sortChunkKeys, smem);
             }
-        } else if (it.phase == 3 * S.passes + 1) {
+        } else if (ph == 3 * S.passes + 1) {
             const uint32_t b0 = it.chunk * B.buildChunk, b1 = min(S.n - 1 + S.cluster, b0 + B.buildChunk);
             if (S.cluster) {
                 if (wide)
@@ -282,13 +321,13 @@ __global__ void __launch_bounds__(256, 2) batchKernel(BatchParams B) {
             } else {
                 karrasRange<uint32_t>(S, b0, b1);
             }
-        } else if (S.cluster && it.phase == 3 * S.passes + 2) {
+        } else if (S.cluster && ph == 3 * S.passes + 2) {
             const uint32_t w = kWalkLeavesPerThread * blockDim.x, b0 = it.chunk * w;
             clusterRange(clusterParamsOf(S), b0, min(S.n, b0 + w), reinterpret_cast<ClusterWarpList*>(smem));
-        } else if (it.phase == 3 * S.passes + 2 + S.cluster) {
+        } else if (ph == 3 * S.passes + 2 + S.cluster) {
             const uint32_t b0 = it.chunk * B.buildChunk;
             fitRange(S, b0, min(S.n, b0 + B.buildChunk));
-        } else if ((S.quant | S.wide8) && it.phase == 3 * S.passes + 3 + S.cluster) {
+        } else if ((S.quant | S.wide8) && ph == 3 * S.passes + 3 + S.cluster) {
             const uint32_t m = S.n > 1 ? S.n - 1 : 1u, b1 = min(m, (it.chunk + 1) * B.buildChunk);
             for (uint32_t k = it.chunk * B.buildChunk + threadIdx.x; k < b1; k += blockDim.x) {
                 if (S.quant) quantizeWideNode(S.wide + kWideWords * (size_t)k, S.qnodes + kQuantWords * (size_t)k);
@@ -395,23 +434,37 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         if (e != GRT_SUCCESS) return e;
         BvhObject* o = findBvh(in.geometry);
         if (!o || o->primType != GRT_PRIMITIVE_TRIANGLE_MESH || in.input.type != GRT_PRIMITIVE_TRIANGLE_MESH ||
-            o->primCount != n || o->split)
+            o->primCount != n)
             return GRT_ERROR_INVALID_PARAMETER;
         if (in.rayCount && (!in.rays || !in.hits || ((uintptr_t)in.rays & 15) || ((uintptr_t)in.hits & 3)))
             return GRT_ERROR_INVALID_PARAMETER;
         BatchSceneDev& d = S[i];
+        const bool split = o->split && n > 0;
+        const uint32_t m = n == 0 ? 0u : o->leafCount;  // leaves: the triangles, or their references
         d.src = primSource(&in.input, n);
         d.kind = 0;  // triangles
-        d.n = n;
+        d.n = m;
         d.rays = in.rayCount;
         d.bits = o->mortonBits;
-        d.cluster = (buildsBySubtreeClustering(o) && n >= 2) ? 1u : 0u;
-        d.small = n <= opt.smallScenePrims && !d.cluster;
-        d.sortChunks = std::max(1u, ceilDiv(n, chunkKeys));
+        d.cluster = (buildsBySubtreeClustering(o) && m >= 2) ? 1u : 0u;
+        d.small = n <= opt.smallScenePrims && !d.cluster && !split;
+        d.sortChunks = std::max(1u, ceilDiv(m, chunkKeys));
         d.passes = (d.bits + 7) / 8;
         d.quant = (o->quant && n > 0) ? 1u : 0u;
         d.wide8 = (o->wide8 && n > 0) ? 1u : 0u;
-        d.tracePhase = d.small ? 1u : 3u * d.passes + 3u + d.cluster + (d.quant | d.wide8);
+        d.splitPhases = split ? kSplitPhases : 0u;
+        d.splitChunks = split ? ceilDiv(n, opt.buildChunk) : 0u;
+        d.split = SplitParams{};
+        if (split) {
+            d.split.src = d.src;  // the triangles (kind 0)
+            d.split.n = n;
+            d.split.budget = o->splitBudget;
+            d.split.blocks = d.splitChunks;
+            d.split.error = &workspace(c)->error;
+            d.src.kind = 2;  // the build reads the references (pointer set below)
+            d.src.count = m;
+        }
+        d.tracePhase = d.small ? 1u : d.splitPhases + 3u * d.passes + 3u + d.cluster + (d.quant | d.wide8);
         d.rayBuf = (const float4*)in.rays;
         d.hitBuf = (uint32_t*)in.hits;
         d.nodes = (float4*)o->nodes;
@@ -423,12 +476,15 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
         d.primToLeaf = o->primToLeaf;
         d.header = o->dHeader;
         d.error = &workspace(c)->error;
-        const size_t kb = d.bits == 30 ? 4 : 8, nn = std::max(n, 1u);
+        const size_t kb = d.bits == 30 ? 4 : 8, nn = std::max(m, 1u);  // per leaf (reference)
         scratchOff[i] = scratch;
         scratch += 256 + alignUp(16 * nn, 256) + 2 * alignUp(kb * nn, 256) + 2 * alignUp(4 * nn, 256) +
                    alignUp(4 * (size_t)kBlockRadix * d.sortChunks, 256) + alignUp(4 * nn, 256);
         if (d.cluster)  // LBVH child words, parent entries, range starts; clusters, numbers, counts, flags
             scratch += 2 * alignUp(8 * nn, 256) + alignUp(16 * nn, 256) + alignUp(32 * nn, 256) + 2 * alignUp(4 * nn, 256);
+        if (split)  // scene box and totals; weights / shares, first slots; chunk sums; slot triangles; references
+            scratch += 256 + 2 * alignUp(4 * (size_t)n, 256) + alignUp(8 * (size_t)d.splitChunks, 256) +
+                       alignUp(4 * (size_t)d.splitChunks, 256) + alignUp(4 * nn, 256) + alignUp(32 * nn, 256);
     }
 
     // work items. Scenes go in groups of opt.sceneGroup, largest first: a group's build
@@ -443,6 +499,9 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
     auto phaseItems = [&](const BatchSceneDev& d, uint32_t ph) -> uint32_t {
         if (ph == d.tracePhase) return ceilDiv(d.rays, opt.traceChunk);
         if (d.small) return ph == 0 ? 1u : 0u;
+        if (ph < d.splitPhases)  // the two scans are one item; the references have chunks of their own
+            return (ph == 2 || ph == 4) ? 1u : ph == kSplitPhases - 1 ? ceilDiv(d.n, opt.buildChunk) : d.splitChunks;
+        ph -= d.splitPhases;
         if (ph == 0) return ceilDiv(d.n, opt.buildChunk);
         if (ph <= 3 * d.passes) return (ph - 1) % 3 == 1 ? 1u : d.sortChunks;
         if (ph == 3 * d.passes + 1) return ceilDiv(d.n - 1 + d.cluster, opt.buildChunk);  // clustered: every leaf too
@@ -529,7 +588,20 @@ grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sc
             d.topoRecord = (uint4*)p, p += alignUp(16 * nn, 256);
             d.clusters = (float4*)p, p += alignUp(32 * nn, 256);
             d.freeIds = (uint32_t*)p, p += alignUp(4 * nn, 256);
-            d.clusterFlags = (uint32_t*)p;
+            d.clusterFlags = (uint32_t*)p, p += alignUp(4 * nn, 256);
+        }
+        if (d.splitPhases) {
+            SplitParams& q = d.split;
+            const size_t nt = q.n;
+            q.sceneBounds = (uint32_t*)p;
+            q.totals = (unsigned long long*)(p + 32), p += 256;
+            q.counts = (uint32_t*)p, p += alignUp(4 * nt, 256);
+            q.firstSlot = (uint32_t*)p, p += alignUp(4 * nt, 256);
+            q.weightSums = (unsigned long long*)p, p += alignUp(8 * (size_t)d.splitChunks, 256);
+            q.blockSums = (uint32_t*)p, p += alignUp(4 * (size_t)d.splitChunks, 256);
+            q.slotTriangle = (uint32_t*)p, p += alignUp(4 * nn, 256);
+            q.refs = (float4*)p;
+            d.src.refs = q.refs;
         }
     }
     cudaError_t ce = cudaSuccess;

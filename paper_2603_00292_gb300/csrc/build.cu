@@ -911,6 +911,51 @@ static SplitLayout splitLayoutOf(const BvhObject* o, const BuildLayout& L, uint3
     return splitLayout(methodTempBytes(L, o->leafCount, radius), o->primCount, o->leafCount);
 }
 
+// Splitting kernels of per-geometry builds (split.cuh): a chunk of kSplitThreads
+// triangles (references) per block.
+__device__ __forceinline__ void chunkOf(uint32_t count, uint32_t* b0, uint32_t* b1) {
+    *b0 = blockIdx.x * blockDim.x;
+    *b1 = min(count, *b0 + blockDim.x);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) splitBoundsKernel(SplitParams P) {
+    uint32_t b0, b1;
+    chunkOf(P.n, &b0, &b1);
+    splitBoundsRange(P, b0, b1);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) splitWeightKernel(SplitParams P) {
+    uint32_t b0, b1;
+    chunkOf(P.n, &b0, &b1);
+    splitWeightRange(P, blockIdx.x, b0, b1);
+}
+
+__global__ void __launch_bounds__(kSplitScanThreads) splitScanWeightsKernel(SplitParams P) {
+    splitScanWeights(P, P.blocks);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) splitCountKernel(SplitParams P) {
+    uint32_t b0, b1;
+    chunkOf(P.n, &b0, &b1);
+    splitCountRange(P, blockIdx.x, b0, b1);
+}
+
+__global__ void __launch_bounds__(kSplitScanThreads) splitScanKernel(SplitParams P) {
+    scanBlockSums<uint32_t>(P.blockSums, P.blocks, nullptr);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) splitSlotsKernel(SplitParams P) {
+    uint32_t b0, b1;
+    chunkOf(P.n, &b0, &b1);
+    splitSlotsRange(P, blockIdx.x, b0, b1);
+}
+
+__global__ void __launch_bounds__(kSplitThreads) splitEmitKernel(SplitParams P) {
+    uint32_t r0, r1;
+    chunkOf(P.n + P.budget, &r0, &r1);
+    splitEmitRange<true>(P, r0, r1);
+}
+
 // The splitting launches of a split build (o->primCount >= 1 triangles): references,
 // their centroids and the centroid bounds, in the scratch the rest of the build reads.
 static grtError launchSplit(Context* c, BvhObject* o, const BuildLayout& L, char* t, const PrimSource& S,

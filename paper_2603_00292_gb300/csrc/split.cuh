@@ -63,8 +63,8 @@ __device__ __forceinline__ SplitGrid loadSplitGrid(const uint32_t* b6) {
     SplitGrid g;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        g.lo[a] = orderedToFloat(b6[a]);
-        g.ghi[a] = orderedToFloat(b6[3 + a]);
+        g.lo[a] = orderedToFloat(__ldcg(b6 + a));
+        g.ghi[a] = orderedToFloat(__ldcg(b6 + 3 + a));
         g.ext[a] = __fsub_rn(g.ghi[a], g.lo[a]);
         g.inv[a] = g.ext[a] > 0.0f ? __fdiv_rn(1024.0f, g.ext[a]) : 0.0f;
     }
@@ -254,24 +254,20 @@ __device__ __forceinline__ void cutOnce(const SplitGrid& g, const float v[3][3],
     }
 }
 
-// ----------------------------------------------------------------------- kernels
-__global__ void __launch_bounds__(kSplitThreads) splitBoundsKernel(SplitParams P) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    if (t < P.n) {
-        float v[3][3];
-        SBox b;
-        splitTriangle(P.src, t, v, &b);
-        for (int a = 0; a < 3; ++a) mn[a] = b.lo[a], mx[a] = b.hi[a];
-    }
-    reduceBoxBounds(mn, mx, P.sceneBounds);
-}
+// ----------------------------------------------------------------------- chunk ranges
+// Each step is written over a chunk of triangles (or of references) and run by a whole
+// block of any size (a multiple of 32), so that the per-geometry kernels below (a chunk
+// of 256 triangles per block) and the batched launch's work items (larger chunks) run
+// the same code. Sums and scans are exact integers: the chunking changes no result.
+// Data an earlier step wrote (in the batched launch: another block of the same launch)
+// is read with L1-bypassing loads.
 
-// Exclusive prefix of x over the block (kSplitThreads threads), and the block's total.
+// Exclusive prefix of x over the block and the block's total (every thread calls it;
+// its shared words may be reused after a __syncthreads).
 template <typename T>
 __device__ __forceinline__ T blockExclusive(T x, T* total) {
-    __shared__ T warpSums[kSplitThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ T warpSums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     T inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -281,7 +277,7 @@ __device__ __forceinline__ T blockExclusive(T x, T* total) {
     if (lane == 31) warpSums[warp] = inc;
     __syncthreads();
     T before = inc - x, all = 0;
-    for (int w = 0; w < kSplitThreads / 32; ++w) {
+    for (int w = 0; w < warps; ++w) {
         if (w < warp) before += warpSums[w];
         all += warpSums[w];
     }
@@ -289,55 +285,78 @@ __device__ __forceinline__ T blockExclusive(T x, T* total) {
     return before;
 }
 
-__global__ void __launch_bounds__(kSplitThreads) splitWeightKernel(SplitParams P) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t w = 0;
-    if (t < P.n) {
-        const SplitGrid g = loadSplitGrid(P.sceneBounds);
+// Scene box over triangles [b0, b1).
+__device__ __forceinline__ void splitBoundsRange(const SplitParams& P, uint32_t b0, uint32_t b1) {
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (uint32_t t = b0 + threadIdx.x; t < b1; t += blockDim.x) {
         float v[3][3];
         SBox b;
         splitTriangle(P.src, t, v, &b);
-        int level = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            int cl, ch;
-            gridSpan(g, b, a, &cl, &ch);
-            const int L = bitLength((uint32_t)(cl ^ ch));
-            level = L > level ? L : level;
-        }
-        float e1[3], e2[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) e1[a] = __fsub_rn(v[1][a], v[0][a]), e2[a] = __fsub_rn(v[2][a], v[0][a]);
-        const float cx = __fsub_rn(__fmul_rn(e1[1], e2[2]), __fmul_rn(e1[2], e2[1]));
-        const float cy = __fsub_rn(__fmul_rn(e1[2], e2[0]), __fmul_rn(e1[0], e2[2]));
-        const float cz = __fsub_rn(__fmul_rn(e1[0], e2[1]), __fmul_rn(e1[1], e2[0]));
-        const float tri = __fmul_rn(0.5f, __fadd_rn(__fadd_rn(fabsf(cx), fabsf(cy)), fabsf(cz)));
-        float excess = __fsub_rn(halfArea(b), tri);
-        if (!(excess > 0.0f)) excess = 0.0f;
-        SBox G;
-        for (int a = 0; a < 3; ++a) G.lo[a] = g.lo[a], G.hi[a] = g.ghi[a];
-        const float areaG = halfArea(G);
-        const float r = areaG > 0.0f ? __fmul_rn(__fdiv_rn(excess, areaG), (float)(1u << level)) : 0.0f;
-        w = integerCubeRoot((unsigned long long)__fmul_rn(r, 0x1p53f));  // r 2^53 <= 2^63
-        P.counts[t] = w;
+        for (int a = 0; a < 3; ++a) mn[a] = selMin(mn[a], b.lo[a]), mx[a] = selMax(mx[a], b.hi[a]);
     }
-    unsigned long long total;
-    blockExclusive<unsigned long long>(w, &total);
-    if (threadIdx.x == 0) P.weightSums[blockIdx.x] = total;
+    reduceBoxBounds(mn, mx, P.sceneBounds);
 }
 
-// One block: exclusive prefix sums of `count` per-block values, in place; the total
+// The weight of triangle t (the integer cube root of its priority, 2^53 scaled).
+__device__ __forceinline__ uint32_t splitWeight(const SplitParams& P, const SplitGrid& g, uint32_t t) {
+    float v[3][3];
+    SBox b;
+    splitTriangle(P.src, t, v, &b);
+    int level = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int cl, ch;
+        gridSpan(g, b, a, &cl, &ch);
+        const int L = bitLength((uint32_t)(cl ^ ch));
+        level = L > level ? L : level;
+    }
+    float e1[3], e2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) e1[a] = __fsub_rn(v[1][a], v[0][a]), e2[a] = __fsub_rn(v[2][a], v[0][a]);
+    const float cx = __fsub_rn(__fmul_rn(e1[1], e2[2]), __fmul_rn(e1[2], e2[1]));
+    const float cy = __fsub_rn(__fmul_rn(e1[2], e2[0]), __fmul_rn(e1[0], e2[2]));
+    const float cz = __fsub_rn(__fmul_rn(e1[0], e2[1]), __fmul_rn(e1[1], e2[0]));
+    const float tri = __fmul_rn(0.5f, __fadd_rn(__fadd_rn(fabsf(cx), fabsf(cy)), fabsf(cz)));
+    float excess = __fsub_rn(halfArea(b), tri);
+    if (!(excess > 0.0f)) excess = 0.0f;
+    SBox G;
+    for (int a = 0; a < 3; ++a) G.lo[a] = g.lo[a], G.hi[a] = g.ghi[a];
+    const float areaG = halfArea(G);
+    const float r = areaG > 0.0f ? __fmul_rn(__fdiv_rn(excess, areaG), (float)(1u << level)) : 0.0f;
+    return integerCubeRoot((unsigned long long)__fmul_rn(r, 0x1p53f));  // r 2^53 <= 2^63
+}
+
+// Weights of triangles [b0, b1) and their sum, weightSums[chunk].
+__device__ __forceinline__ void splitWeightRange(const SplitParams& P, uint32_t chunk, uint32_t b0, uint32_t b1) {
+    const SplitGrid g = loadSplitGrid(P.sceneBounds);
+    unsigned long long sum = 0;
+    for (uint32_t base = b0; base < b1; base += blockDim.x) {
+        const uint32_t t = base + threadIdx.x;
+        uint32_t w = 0;
+        if (t < b1) {
+            w = splitWeight(P, g, t);
+            P.counts[t] = w;
+        }
+        unsigned long long roundTotal;
+        blockExclusive<unsigned long long>(w, &roundTotal);
+        __syncthreads();
+        sum += roundTotal;
+    }
+    if (threadIdx.x == 0) P.weightSums[chunk] = sum;
+}
+
+// One block: exclusive prefix sums of `count` per-chunk values, in place; the total
 // goes to *total.
 template <typename T>
 __device__ __forceinline__ void scanBlockSums(T* v, uint32_t count, unsigned long long* total) {
-    __shared__ T warpSums[kSplitScanThreads / 32];
+    __shared__ T warpSums[32];
     __shared__ T carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t base = 0; base < count; base += kSplitScanThreads) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    for (uint32_t base = 0; base < count; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
-        const T x = i < count ? v[i] : (T)0;
+        const T x = i < count ? __ldcg(v + i) : (T)0;
         T inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -347,129 +366,146 @@ __device__ __forceinline__ void scanBlockSums(T* v, uint32_t count, unsigned lon
         if (lane == 31) warpSums[warp] = inc;
         __syncthreads();
         if (warp == 0) {
-            T ws = warpSums[lane];
+            T ws = lane < warps ? warpSums[lane] : (T)0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const T y = __shfl_up_sync(0xffffffffu, ws, o);
                 if (lane >= o) ws += y;
             }
-            warpSums[lane] = ws;  // inclusive over warps
+            if (lane < warps) warpSums[lane] = ws;  // inclusive over warps
         }
         __syncthreads();
         const T before = carry + (warp ? warpSums[warp - 1] : (T)0) + inc - x;
         if (i < count) v[i] = before;
         __syncthreads();
-        if (threadIdx.x == 0) carry += warpSums[kSplitScanThreads / 32 - 1];
+        if (threadIdx.x == 0) carry += warpSums[warps - 1];
         __syncthreads();
     }
     if (threadIdx.x == 0 && total) *total = (unsigned long long)carry;
 }
 
-__global__ void __launch_bounds__(kSplitScanThreads) splitScanWeightsKernel(SplitParams P) {
-    scanBlockSums<unsigned long long>(P.weightSums, P.blocks, P.totals);
+// The weight scan over `chunks` chunks, W and 1 / W.
+__device__ __forceinline__ void splitScanWeights(const SplitParams& P, uint32_t chunks) {
+    scanBlockSums<unsigned long long>(P.weightSums, chunks, P.totals);
+    __syncthreads();
     if (threadIdx.x == 0 && P.totals[0])  // 1 / W for the estimates of the shares
         reinterpret_cast<double*>(P.totals)[2] = __ddiv_rn(1.0, (double)P.totals[0]);
 }
 
-// Triangle t's splits by priority: its share of the budget between the running weight
-// sums before and after it, capped at kSplitMax.
-__global__ void __launch_bounds__(kSplitThreads) splitCountKernel(SplitParams P) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned long long w = t < P.n ? P.counts[t] : 0ull;
-    unsigned long long blockTotal;
-    const unsigned long long local = blockExclusive<unsigned long long>(w, &blockTotal);
-    uint32_t s = 0;
-    if (t < P.n) {
-        const unsigned long long W = P.totals[0];
-        if (W) {
-            const unsigned long long C = P.weightSums[blockIdx.x] + local;
-            const double invW = reinterpret_cast<const double*>(P.totals)[2];
-            const unsigned long long q = mulDivFloor(P.budget, C + w, W, invW) - mulDivFloor(P.budget, C, W, invW);
-            s = (uint32_t)(q < (unsigned long long)kSplitMax ? q : (unsigned long long)kSplitMax);
+// Splits by priority of triangles [b0, b1): each one's share of the budget between the
+// running weight sums before and after it, capped at kSplitMax; their sum blockSums[chunk].
+__device__ __forceinline__ void splitCountRange(const SplitParams& P, uint32_t chunk, uint32_t b0, uint32_t b1) {
+    const unsigned long long W = __ldcg(P.totals);
+    const double invW = W ? __ldcg(reinterpret_cast<const double*>(P.totals) + 2) : 0.0;
+    unsigned long long carry = __ldcg(P.weightSums + chunk);
+    uint32_t sum = 0;
+    for (uint32_t base = b0; base < b1; base += blockDim.x) {
+        const uint32_t t = base + threadIdx.x;
+        const unsigned long long w = t < b1 ? __ldcg(P.counts + t) : 0ull;
+        unsigned long long roundTotal;
+        const unsigned long long local = blockExclusive<unsigned long long>(w, &roundTotal);
+        uint32_t s = 0;
+        if (t < b1) {
+            if (W) {
+                const unsigned long long C = carry + local;
+                const unsigned long long q = mulDivFloor(P.budget, C + w, W, invW) - mulDivFloor(P.budget, C, W, invW);
+                s = (uint32_t)(q < (unsigned long long)kSplitMax ? q : (unsigned long long)kSplitMax);
+            }
+            P.counts[t] = s;
         }
-        P.counts[t] = s;
+        carry += roundTotal;
+        __syncthreads();
+        uint32_t roundSplits;
+        blockExclusive<uint32_t>(s, &roundSplits);
+        __syncthreads();
+        sum += roundSplits;
     }
-    __syncthreads();  // the block's shared partial sums are reused below
-    uint32_t sum;
-    blockExclusive<uint32_t>(s, &sum);
     if (threadIdx.x == 0) {
-        P.blockSums[blockIdx.x] = sum;
+        P.blockSums[chunk] = sum;
         if (sum) atomicAdd(P.totals + 1, (unsigned long long)sum);
     }
 }
 
-__global__ void __launch_bounds__(kSplitScanThreads) splitScanKernel(SplitParams P) {
-    scanBlockSums<uint32_t>(P.blockSums, P.blocks, nullptr);
-}
-
-// Each triangle's reference slots: its first slot (the running sum of the references
-// before it) and its final split count; the slots it owns are marked with its index.
-__global__ void __launch_bounds__(kSplitThreads) splitSlotsKernel(SplitParams P) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t mine = t < P.n ? P.counts[t] : 0u;
-    uint32_t blockTotal;
-    const uint32_t local = blockExclusive<uint32_t>(mine, &blockTotal);
-    if (t >= P.n) return;
-    const unsigned long long given = P.totals[1];
+// Reference slots of triangles [b0, b1): each one's first slot (the references before
+// it) and final split count, and its index on every slot it owns.
+__device__ __forceinline__ void splitSlotsRange(const SplitParams& P, uint32_t chunk, uint32_t b0, uint32_t b1) {
+    const unsigned long long given = __ldcg(P.totals + 1);
     const unsigned long long left = given < P.budget ? (unsigned long long)P.budget - given : 0ull;
-    const uint32_t extra = (unsigned long long)t < left ? 1u : 0u;
-    const uint32_t first = t + P.blockSums[blockIdx.x] + local + (uint32_t)((unsigned long long)t < left ? t : left);
-    const uint32_t s = min(mine + extra, (uint32_t)kSplitMax + 1u);
-    P.counts[t] = s;
-    P.firstSlot[t] = first;
     const uint32_t m = P.n + P.budget;
-    for (uint32_t j = 0; j <= s; ++j) {
-        if (first + j >= m) {  // cannot happen: the shares add up to at most the budget
-            latchError(P.error, GRT_ERROR_INTERNAL);
-            break;
+    uint32_t carry = __ldcg(P.blockSums + chunk);
+    for (uint32_t base = b0; base < b1; base += blockDim.x) {
+        const uint32_t t = base + threadIdx.x;
+        const uint32_t mine = t < b1 ? __ldcg(P.counts + t) : 0u;
+        uint32_t roundTotal;
+        const uint32_t local = blockExclusive<uint32_t>(mine, &roundTotal);
+        if (t < b1) {
+            const uint32_t extra = (unsigned long long)t < left ? 1u : 0u;
+            const uint32_t first = t + carry + local + (uint32_t)((unsigned long long)t < left ? t : left);
+            const uint32_t s = min(mine + extra, (uint32_t)kSplitMax + 1u);
+            P.counts[t] = s;
+            P.firstSlot[t] = first;
+            for (uint32_t j = 0; j <= s; ++j) {
+                if (first + j >= m) {  // cannot happen: the shares add up to at most the budget
+                    latchError(P.error, GRT_ERROR_INTERNAL);
+                    break;
+                }
+                P.slotTriangle[first + j] = t;
+            }
         }
-        P.slotTriangle[first + j] = t;
+        carry += roundTotal;
+        __syncthreads();
     }
 }
 
-// Reference r (one thread each): the k-th leaf, left first, of its triangle's cut tree,
-// found by walking down from the triangle's box and cutting only the boxes on its path
-// (each cut as the depth-first order makes it); its box, triangle, owner flag and centroid.
-__global__ void __launch_bounds__(kSplitThreads) splitEmitKernel(SplitParams P) {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+// References [r0, r1), one thread each: the k-th leaf, left first, of its triangle's cut
+// tree, found by walking down from the triangle's box and cutting only the boxes on its
+// path (each cut as the depth-first order makes it); its box, triangle and owner flag,
+// and with CENTROIDS its centroid and the centroid bounds (the batched launch takes
+// those from its prep step instead).
+template <bool CENTROIDS>
+__device__ __forceinline__ void splitEmitRange(const SplitParams& P, uint32_t r0, uint32_t r1) {
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    if (r < P.n + P.budget) {
-        const uint32_t t = P.slotTriangle[r];
-        uint32_t k = t < P.n ? r - P.firstSlot[t] : 0xFFFFFFFFu;
-        int s = t < P.n ? (int)P.counts[t] : 0;
-        if (t >= P.n || k > (uint32_t)s) {
+    const SplitGrid g = loadSplitGrid(P.sceneBounds);
+    for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const uint32_t t = __ldcg(P.slotTriangle + r);
+        uint32_t k = t < P.n ? r - __ldcg(P.firstSlot + t) : 0xFFFFFFFFu;
+        int s = t < P.n ? (int)__ldcg(P.counts + t) : 0;
+        if (t >= P.n || k > (uint32_t)s) {  // cannot happen; leave an empty reference of triangle 0
             latchError(P.error, GRT_ERROR_INTERNAL);
-        } else {
-            const SplitGrid g = loadSplitGrid(P.sceneBounds);
-            float v[3][3];
-            SBox cur;
-            splitTriangle(P.src, t, v, &cur);
-            const bool owner = k == 0;
-            while (s > 0) {
-                SBox L, R;
-                int sL;
-                cutOnce(g, v, cur, s, &L, &R, &sL);
-                if (k <= (uint32_t)sL) {
-                    cur = L;
-                    s = sL;
-                } else {
-                    cur = R;
-                    k -= (uint32_t)sL + 1u;
-                    s = s - 1 - sL;
-                }
+            P.refs[2 * (size_t)r] = make_float4(INFINITY, INFINITY, INFINITY, __uint_as_float(0u));
+            P.refs[2 * (size_t)r + 1] = make_float4(-INFINITY, -INFINITY, -INFINITY, __uint_as_float(0u));
+            continue;
+        }
+        float v[3][3];
+        SBox cur;
+        splitTriangle(P.src, t, v, &cur);
+        const bool owner = k == 0;
+        while (s > 0) {
+            SBox L, R;
+            int sL;
+            cutOnce(g, v, cur, s, &L, &R, &sL);
+            if (k <= (uint32_t)sL) {
+                cur = L;
+                s = sL;
+            } else {
+                cur = R;
+                k -= (uint32_t)sL + 1u;
+                s = s - 1 - sL;
             }
-            P.refs[2 * (size_t)r] = make_float4(cur.lo[0], cur.lo[1], cur.lo[2], __uint_as_float(t));
-            P.refs[2 * (size_t)r + 1] = make_float4(cur.hi[0], cur.hi[1], cur.hi[2], __uint_as_float(owner ? 1u : 0u));
+        }
+        P.refs[2 * (size_t)r] = make_float4(cur.lo[0], cur.lo[1], cur.lo[2], __uint_as_float(t));
+        P.refs[2 * (size_t)r + 1] = make_float4(cur.hi[0], cur.hi[1], cur.hi[2], __uint_as_float(owner ? 1u : 0u));
+        if (CENTROIDS) {
             Box3 bb;
             bb.lo = make_float3(cur.lo[0], cur.lo[1], cur.lo[2]);
             bb.hi = make_float3(cur.hi[0], cur.hi[1], cur.hi[2]);
             const float3 c = boxCentroid(bb);
             P.centroids[r] = make_float4(c.x, c.y, c.z, 0.f);
-            mn[0] = c.x, mn[1] = c.y, mn[2] = c.z;
-            mx[0] = c.x, mx[1] = c.y, mx[2] = c.z;
+            mn[0] = fminf(mn[0], c.x), mn[1] = fminf(mn[1], c.y), mn[2] = fminf(mn[2], c.z);
+            mx[0] = fmaxf(mx[0], c.x), mx[1] = fmaxf(mx[1], c.y), mx[2] = fmaxf(mx[2], c.z);
         }
     }
-    reduceBoxBounds(mn, mx, P.centroidBounds);
+    if (CENTROIDS) reduceBoxBounds(mn, mx, P.centroidBounds);
 }
 
 }  // namespace grt

@@ -34,7 +34,7 @@ def _workload(count, nmax, rmax, seed=scenegen.MASTER_SEED):
 
 def _bvh_arrays(g):
     info = g.info()
-    n = info.primCount
+    n = info.leafCount
     nodes = read_device(info.nodes, 64 * info.nodeCount, np.uint32)
     leaves = read_device(info.leaves, 48 * n, np.uint32)
     # a one-primitive hierarchy has no parent links (its leaf sits in node 0)
@@ -44,18 +44,20 @@ def _bvh_arrays(g):
     return nodes, leaves, parents, wide
 
 
-def _run(gpu, work, opts, morton_bits=None, build_flags=None):
+def _run(gpu, work, opts, morton_bits=None, build_flags=None, split_factor=None):
     """The batch over `work`, and the same scenes built and traced one by one (each
-    geometry of both created with build_flags(k), default the linear BVH)."""
+    geometry of both created with build_flags(k), default the linear BVH, and
+    split_factor(k))."""
     batched, single = [], []
     for k, (s, rays) in enumerate(work):
         bits = 0 if morton_bits is None else morton_bits(k)
         flags = 0 if build_flags is None else build_flags(k)
+        f = 0.0 if split_factor is None else split_factor(k)
         v, i = device_tensor(s.mesh.vertices), device_tensor(s.mesh.indices)
         r = device_tensor(rays)
-        batched.append((Geometry(gpu, vertices=v, indices=i, morton_bits=bits, build_flags=flags), r,
+        batched.append((Geometry(gpu, vertices=v, indices=i, morton_bits=bits, build_flags=flags, split_factor=f), r,
                         new_hits(rays.shape[0])))
-        g = Geometry(gpu, vertices=v, indices=i, morton_bits=bits, build_flags=flags).build()
+        g = Geometry(gpu, vertices=v, indices=i, morton_bits=bits, build_flags=flags, split_factor=f).build()
         h = new_hits(rays.shape[0])
         grt.grtTraceClosest(gpu.handle, None, g.handle, r, rays.shape[0], h)
         single.append((g, h))
@@ -182,5 +184,33 @@ def test_batch_with_subtree_clustered_scenes(gpu):
         s = work[k][0]
         bits = grt.grtGetBvhInfo(gpu.handle, geom=single[k][0].handle).mortonBits
         check_bit_exact(single[k][0], dict(vertices=s.mesh.vertices, indices=s.mesh.indices), bits, subtree=True)
+    assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
+    B.close()
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(block_size=64, build_chunk=1024, small_scene_prims=2000)])
+def test_batch_with_split_scenes(gpu, opts):
+    """Geometries with split triangles (factors 1, 0.5, 0.1) among plain ones, some also
+    subtree-clustered, 8-wide or with 63-bit codes: the batch runs their splitting
+    phases (chunk scans over several rounds with the small chunks) and builds and traces
+    them exactly as grtBuildGeometry and grtTraceClosest do; the largest split scene
+    bit-exact against the oracle's split and build."""
+    from test_gpu_build import check_bit_exact
+
+    work = _workload(14, nmax=120_000, rmax=20_000, seed=scenegen.MASTER_SEED + 9)
+    sp = grt.GRT_BUILD_SPLIT_TRIANGLES
+    flags = lambda k: ((sp if k % 3 != 2 else 0) | (grt.GRT_BUILD_CLUSTER_SUBTREES if k % 4 == 1 else 0) |
+                       (grt.GRT_BUILD_WIDE8_NODES if k % 5 == 3 else 0))
+    B, batched, single = _run(gpu, work, grt.batch_options(**opts), morton_bits=lambda k: 63 if k % 6 == 4 else 0,
+                              build_flags=flags, split_factor=lambda k: (1.0, 0.5, 0.1)[k % 3])
+    _assert_identical(batched, single)
+    split = [k for k in range(14) if flags(k) & sp and not flags(k) & grt.GRT_BUILD_CLUSTER_SUBTREES]
+    k = max(split, key=lambda k: work[k][0].mesh.indices.shape[0])
+    s = work[k][0]
+    info = grt.grtGetBvhInfo(gpu.handle, geom=batched[k][0].handle)
+    n = s.mesh.indices.shape[0]
+    ref = oracle.split_triangles(s.mesh.vertices, s.mesh.indices, oracle.split_budget(n, (1.0, 0.5, 0.1)[k % 3]))
+    assert info.leafCount == ref[0].shape[0]
+    check_bit_exact(single[k][0], dict(vertices=s.mesh.vertices, indices=s.mesh.indices), info.mortonBits, split=ref)
     assert grt.grtGetLastDeviceError(gpu.handle) == grt.GRT_SUCCESS
     B.close()

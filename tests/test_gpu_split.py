@@ -3,8 +3,8 @@ option, Sec. 8) vs the oracle: the references (boxes, triangles, owners) and the
 build over them (Morton codes, sort, topology, boxes, parent links, leaf records, 4-wide,
 8-wide and quantised nodes) bit-exact for the linear BVH and both clustering builds;
 closest and any hits through split geometries, one level and instanced, vs the oracle's
-hits on the unsplit mesh; primitive-to-leaf map; rejections (UPDATE, all hits, batches,
-AABB lists, factors out of range)."""
+hits on the unsplit mesh; primitive-to-leaf map; rejections (UPDATE, all hits, AABB lists,
+factors out of range). The batched launch with split geometries: tests/test_gpu_batch.py."""
 import numpy as np
 import pytest
 import torch
@@ -12,7 +12,7 @@ import torch
 import oracle
 import paper_2603_00292_gb300 as grt
 import scenegen
-from paper_2603_00292_gb300.objects import Batch, Geometry, Scene, device_tensor, hits_to_numpy, new_hits, read_device
+from paper_2603_00292_gb300.objects import Geometry, Scene, device_tensor, hits_to_numpy, new_hits, read_device
 from parity import check_any_hit_records, compare_any, compare_closest
 from test_gpu_build import _read, check_bit_exact
 
@@ -236,8 +236,6 @@ def test_split_rejections(gpu):
         grt.grtTraceAllHits(gpu.handle, None, g.handle, rays, 64, new_hits(64 * 4), 4,
                             torch.zeros(64, dtype=torch.int32, device="cuda"))
     assert e.value.code == grt.GRT_ERROR_INVALID_PARAMETER
-    with pytest.raises(grt.GrtError):  # the batched launch has no splitting phases
-        Batch(gpu, [(g, rays, new_hits(64))])
     _ok(gpu)
 
 
