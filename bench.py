@@ -1512,8 +1512,9 @@ def run_batched(args, rank, world, local):
         del hits_q
 
     # spatial splits (GRT_BUILD_SPLIT_TRIANGLES, one extra reference per triangle): the
-    # batched launch has no splitting phases, so the per-scene path is timed, against the
-    # per-scene linear BVH above; hit records compared (triangle IDs), mean surface-area cost
+    # per-scene path against the per-scene linear BVH above (hit records compared by
+    # triangle ID, mean surface-area cost), and the batched launch of the split geometries
+    # against the linear-BVH launch (its hits equal to the per-scene split path's)
     split = None
     if not args.no_split:
         sopt = grt.build_options(flags=grt.GRT_BUILD_SPLIT_TRIANGLES, split_factor=1.0)
@@ -1531,6 +1532,12 @@ def run_batched(args, rank, world, local):
                 grt.grtTraceClosest(ctx.handle, None, g.handle, r, r.shape[0], h, None, None, sh)
 
         p_ms, p_launches = timed(sequential_split)
+        # the same split geometries in one batched launch (its splitting phases), same options
+        hits_pb = [new_hits(r.shape[0]) for r in rays]
+        geo_pb = [Geometry(ctx, vertices=dv, indices=di, temp=stemp, build_flags=grt.GRT_BUILD_SPLIT_TRIANGLES,
+                           split_factor=1.0) for (dv, di) in meshes]
+        BP = Batch(ctx, list(zip(geo_pb, rays, hits_pb)), grt.batch_options(graph=True, **opts))
+        pb_ms, pb_launches = timed(lambda: BP.run(sh))
         build_only, _ = timed(lambda: [g.build(sh) for g in geo_p])
         lbvh_build, _ = timed(lambda: [g.build(sh) for g in geo_s])
         torch.cuda.synchronize()
@@ -1538,6 +1545,8 @@ def run_batched(args, rank, world, local):
         pms, pb, lb = max_over_ranks([statistics.mean(p_ms), statistics.mean(build_only), statistics.mean(lbvh_build)],
                                      dist)
         same = sum(int((a[:, 1] == b[:, 1]).sum().item()) for a, b in zip(hits_p, hits_s))
+        (pbms,) = max_over_ranks([statistics.mean(pb_ms)], dist)
+        batch_identical = bool(all(torch.equal(a, b) for a, b in zip(hits_pb, hits_p)))
         split = {"build_flag": "GRT_BUILD_SPLIT_TRIANGLES", "split_factor": 1.0, "path": "per-scene",
                  "sequential_ms": round(pms, 3),
                  "sequential_lbvh_ms": None if math.isnan(seq_ms) else round(seq_ms, 3),
@@ -1546,10 +1555,13 @@ def run_batched(args, rank, world, local):
                  "lbvh_traces_ms": None if math.isnan(seq_ms) else round(seq_ms - lb, 3),
                  "sah_cost_mean": round(statistics.mean(sah_cost(g) for g in geo_p), 3),
                  "lbvh_sah_cost_mean": round(statistics.mean(sah_cost(g) for g in geo_s), 3),
-                 "primitive_ids_equal": same, "records": int(total_rays), "gpu_launches": int(p_launches)}
-        for g in geo_p:
+                 "primitive_ids_equal": same, "records": int(total_rays), "gpu_launches": int(p_launches),
+                 "batched_ms": round(pbms, 3), "batched_lbvh_ms": round(batched_ms, 3),
+                 "batched_identical_to_per_scene": batch_identical, "batched_gpu_launches": int(pb_launches)}
+        BP.close()
+        for g in geo_p + geo_pb:
             g.close()
-        del stemp, hits_p
+        del stemp, hits_p, hits_pb
 
     # end to end: meshes and rays up from pinned host memory, hit records back
     pin = [(torch.from_numpy(v).pin_memory(), torch.from_numpy(i.view(np.int32)).pin_memory(), r.cpu().pin_memory())
