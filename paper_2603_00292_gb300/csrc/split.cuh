@@ -6,11 +6,12 @@
 // plane of a 1024-cell grid over the scene that crosses its box. The build then runs
 // over the n + S references (PrimSource kind 2) exactly as over primitives.
 //
-// Seven launches, one thread per triangle where not said: the scene box; the weights
-// (integer cube roots of the priority) and their per-block sums; one block's exclusive
+// Seven steps (launches of build.cu's per-geometry kernels, or phases of the batched
+// launch), one thread per triangle where not said: the scene box; the weights
+// (integer cube roots of the priority) and their per-chunk sums; one block's exclusive
 // scan of those sums (and the total W); each triangle's share of the budget from its
 // place in the running sum of weights, floor(S C_{t+1} / W) - floor(S C_t / W), and
-// per-block sums of the shares; one block's scan of those; each triangle's first slot
+// per-chunk sums of the shares; one block's scan of those; each triangle's first slot
 // and the triangle of every slot; then one thread per reference, which walks down its
 // triangle's cut tree to its leaf and writes the reference, its centroid and the
 // centroid bounds. A thread per reference keeps the lanes of a warp busy however
