@@ -197,3 +197,66 @@ def test_priority_prefers_large_diagonal_triangles():
     S = oracle.split_budget(2100, 0.1)
     _, _, _, _, splits = oracle.split_triangles(v, idx, S)
     assert splits[:100].sum() >= 0.8 * S and splits[:100].min() >= 1 and splits[100:].max() <= 1
+
+
+def _mt(o, d, v0, v1, v2):
+    """Moller-Trumbore in double for one ray against triangles (arrays (k,3)): t, or inf."""
+    e1, e2 = v1 - v0, v2 - v0
+    p = np.cross(d, e2)
+    det = np.einsum("ij,ij->i", e1, p)
+    ok = np.abs(det) > 1e-300
+    inv = np.where(ok, 1.0 / np.where(ok, det, 1.0), 0.0)
+    s = o - v0
+    u = np.einsum("ij,ij->i", s, p) * inv
+    q = np.cross(s, e1)
+    w = (q @ d) * inv
+    t = np.einsum("ij,ij->i", e2, q) * inv
+    hit = ok & (u >= 0) & (w >= 0) & (u + w <= 1) & (t >= 0)
+    return np.where(hit, t, np.inf)
+
+
+def test_closest_hits_through_the_split_tree_equal_brute_force():
+    """End to end on the CPU: the linear BVH over the split references (the oracle's own
+    build), walked with a plain slab test, finds for every ray the same closest triangle
+    and t as testing all triangles: no cut loses a part of a triangle that a ray can hit."""
+    n = 300
+    v, idx = _soup(n, 21, big=0.9)
+    lo, hi, prim, owner, splits = oracle.split_triangles(v, idx, oracle.split_budget(n, 1.0))
+    assert splits.max() >= 3
+    ref = oracle.lbvh(lo, hi, oracle.box_centroids(np.concatenate([lo, hi], axis=1)), 10)
+    order, cl, cr = ref["order"], ref["childL"].view(np.uint32), ref["childR"].view(np.uint32)
+    nlo, nhi = ref["node_lo"].astype(np.float64), ref["node_hi"].astype(np.float64)
+    llo, lhi = ref["leaf_lo"].astype(np.float64), ref["leaf_hi"].astype(np.float64)
+    tri = v[idx].astype(np.float64)
+    rng = np.random.default_rng(22)
+    eps = 1e-9
+
+    def enters(o, inv, blo, bhi):
+        t0, t1 = (blo - eps - o) * inv, (bhi + eps - o) * inv
+        return np.minimum(t0, t1).max() <= max(np.maximum(t0, t1).min(), 0.0) and np.maximum(t0, t1).min() >= 0
+
+    for _ in range(400):
+        o = rng.uniform(-1.5, 1.5, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        inv = 1.0 / np.where(d == 0, 1e-300, d)
+        tb = _mt(o, d, tri[:, 0], tri[:, 1], tri[:, 2])
+        want = (tb.min(), int(np.argmin(tb))) if np.isfinite(tb.min()) else (np.inf, -1)
+        cand, stack = set(), [0]
+        while stack:
+            k = stack.pop()
+            for c in (cl[k], cr[k]):
+                if c & 0x80000000:
+                    leaf = int(c & 0x7FFFFFFF)
+                    if enters(o, inv, llo[leaf], lhi[leaf]):
+                        cand.add(int(prim[order[leaf]]))
+                else:
+                    if enters(o, inv, nlo[c], nhi[c]):
+                        stack.append(int(c))
+        got = (np.inf, -1)
+        if cand:
+            c = np.array(sorted(cand))
+            tc = _mt(o, d, tri[c, 0], tri[c, 1], tri[c, 2])
+            if np.isfinite(tc.min()):
+                got = (tc.min(), int(c[np.argmin(tc)]))
+        assert got == want, (got, want)
