@@ -667,6 +667,8 @@ typedef struct grtBatchInfo {
  * geometry created with GRT_BUILD_CLUSTER_SUBTREES is built by that method (whatever its
  * size, never by the single-block path), every other one as a linear BVH; either way
  * the result equals grtBuildGeometry's for the subtree clustering and the linear BVH.
+ * A geometry created with GRT_BUILD_SPLIT_TRIANGLES is split first, in seven phases of
+ * its own (never by the single-block path), into the references grtBuildGeometry makes.
  * Errors: GRT_ERROR_INVALID_PARAMETER (bad option, input, geometry or buffer),
  * GRT_ERROR_OUT_OF_MEMORY. */
 grtError grtCreateBatch(grtContext ctx, const grtBatchScene* scenes, uint32_t sceneCount,
