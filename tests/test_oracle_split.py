@@ -141,6 +141,20 @@ def test_references_cover_their_triangle_and_stay_in_its_box(seed, factor):
     assert cover.all(), np.argwhere(~cover)[:5]
 
 
+@pytest.mark.parametrize("scale,offset", [(1e-38, 0.0), (1e25, 0.0), (1.0, 3e6), (1e-3, 100.0)])
+def test_references_stay_conservative_at_extreme_scales(scale, offset):
+    """Tiny, huge and far-off coordinates: the widening scales with the endpoints'
+    magnitude (plus 2^-140 for subnormals), so coverage holds; at the extreme scales the
+    float32 areas of the priority leave the range, the weights vanish and the budget goes
+    by the remainder rule (one cut each), which is still a valid split."""
+    v, idx = _soup(800, 31, big=0.8)
+    v = (v.astype(np.float64) * scale + offset).astype(np.float32)
+    lo, hi, prim, owner, splits = oracle.split_triangles(v, idx, oracle.split_budget(800, 1.0))
+    tlo, thi, _ = oracle.triangle_aabbs(v, idx)
+    assert np.all(lo <= hi) and np.all(lo >= tlo[prim]) and np.all(hi <= thi[prim])
+    assert _inside_some_reference(v, idx, lo, hi, prim, _samples()).all()
+
+
 def test_axis_aligned_grid_mesh_is_covered():
     """A flat grid of right triangles whose vertices and edge crossings fall on grid lines
     (the exact coincidences the widening and the one-step narrowing are for)."""
