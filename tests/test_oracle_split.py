@@ -42,7 +42,7 @@ def _mesh(tris):
 
 def test_split_hand_derived_cases(golden_dir):
     """Four cases worked by hand (tests/golden/split_triangles.txt): a grid-line cut with
-    widened crossings, a second cut on another axis after the narrowing by one float step,
+    widened crossings, a second cut on another axis after the narrowing of the box,
     the remainder of a zero total weight, and the midpoint cut of a box inside one cell."""
     cases = _golden(golden_dir)
     assert [c["name"] for c in cases] == ["single", "diagonal", "degenerate", "midpoint"]
@@ -157,7 +157,7 @@ def test_references_stay_conservative_at_extreme_scales(scale, offset):
 
 def test_axis_aligned_grid_mesh_is_covered():
     """A flat grid of right triangles whose vertices and edge crossings fall on grid lines
-    (the exact coincidences the widening and the one-step narrowing are for)."""
+    (the exact coincidences the widening and the narrowing are for)."""
     k = 16
     xs = np.linspace(0.0, 1.0, k + 1, dtype=np.float32)
     X, Z = np.meshgrid(xs, xs, indexing="ij")
